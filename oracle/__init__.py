@@ -1,0 +1,290 @@
+"""CPU oracle of the multi-component unstructured-mesh compressor (Gong et al.,
+Sec. III-IV, Algorithms 3 and 4), as a ctypes binding over ``mcc_oracle.c``.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package. It shares no code with
+the CUDA library and never imports it. Everything here is plain single-threaded
+C on host arrays; the library's product path never falls back to it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mcc_oracle.c")
+_HDR = os.path.join(_HERE, "mcc_oracle.h")
+_LIB = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, INVALID_ARG, CUDA, OOM, RANGE, CORRUPT, CAPACITY, TIMEOUT, UNSUPPORTED = range(9)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"oracle {what} failed with status {status}")
+        self.status = status
+
+
+def build(force: bool = False) -> str:
+    """Compile liborc.so with gcc (plain C11, no FMA contraction)."""
+    stale = force or not os.path.exists(_LIB) or any(
+        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
+    if stale:
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call([
+            "gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+            "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int32 * 3), ("lo", C.c_double * 3),
+                ("h", C.c_double * 3), ("inv_h", C.c_double * 3)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("dtype", C.c_int), ("eb_mode", C.c_int), ("eb", C.c_double),
+                ("grid_fraction", C.c_double), ("R1", C.c_int), ("R2", C.c_int),
+                ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int)]
+
+
+class _Field(C.Structure):
+    _fields_ = [("lo", C.c_double), ("hi", C.c_double), ("M", C.c_double),
+                ("tau", C.c_double), ("tau1", C.c_double), ("tau2", C.c_double),
+                ("s1", C.c_double), ("s2", C.c_double), ("inv2", C.c_double),
+                ("K", C.c_int64), ("Qhi", C.c_int64), ("fill_u", C.c_int64),
+                ("rho21_q", C.c_int64), ("rho12_q", C.c_int64),
+                ("rho21_f", C.c_float), ("rho12_f", C.c_float), ("guard", C.c_int)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.c_void_p
+            lib.orc_grid_resolve.argtypes = [C.c_int, C.c_int64, P, P, P, P, C.POINTER(_Grid)]
+            lib.orc_point_in_simplex.argtypes = [C.POINTER(_Grid), P, P, P, P]
+            lib.orc_locate.argtypes = [C.POINTER(_Grid), C.c_int64, P, C.c_int64, P, C.c_int, P]
+            lib.orc_plan_tables.argtypes = [C.POINTER(_Grid), C.c_int64, P, P, P, P, P, P, P, P]
+            lib.orc_field_params.argtypes = [C.POINTER(_Params), C.c_int64, P, C.POINTER(_Field)]
+            lib.orc_compress_bound.argtypes = [C.POINTER(_Grid), C.c_int64, C.POINTER(_Params)]
+            lib.orc_compress_bound.restype = C.c_size_t
+            lib.orc_compress.argtypes = [C.POINTER(_Grid), C.c_int64, P, P, P, P, P,
+                                         C.POINTER(_Params), P, C.c_size_t,
+                                         C.POINTER(C.c_size_t), P, P, P, P]
+            lib.orc_decompress.argtypes = [C.POINTER(_Grid), C.c_int64, P, P, P, C.c_size_t, P, P]
+            lib.orc_huffman_lengths.argtypes = [P, C.c_int, C.c_int, P]
+            lib.orc_canonical_codes.argtypes = [P, C.c_int, P]
+            lib.orc_lorenzo.argtypes = [C.c_int, P, P, P]
+            lib.orc_lorenzo_inverse.argtypes = [C.c_int, P, P, P]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# --------------------------------------------------------------------------- #
+# grid and plan
+# --------------------------------------------------------------------------- #
+class Grid:
+    """Resolved rectilinear grid (corners, spacing) -- Sec. IV-C."""
+
+    def __init__(self, coords, n, lo=None, hi=None):
+        coords = _c(coords, np.float64)
+        dim = coords.shape[1]
+        nn = np.ones(3, dtype=np.int32)
+        nn[:dim] = n
+        lo3 = np.zeros(3); hi3 = np.zeros(3)  # lo >= hi selects the mesh bounding box
+        if lo is not None:
+            lo3[:dim] = lo
+            hi3[:dim] = hi
+        g = _Grid()
+        st = _load().orc_grid_resolve(dim, coords.shape[0], _ptr(coords), _ptr(nn),
+                                      _ptr(lo3), _ptr(hi3), C.byref(g))
+        if st:
+            raise OracleError(st, "grid_resolve")
+        self._g = g
+        self.dim = dim
+        self.n = tuple(int(v) for v in g.n)
+        self.lo = np.array(g.lo[:])
+        self.h = np.array(g.h[:])
+        self.n_g = int(np.prod(self.n))
+
+
+def point_in_simplex(grid: Grid, coords, cell, idx):
+    coords = _c(coords, np.float64)
+    cell = _c(cell, np.int32)
+    idx3 = np.zeros(3, dtype=np.int32)
+    idx3[: len(idx)] = idx
+    lam = np.zeros(4)
+    inside = _load().orc_point_in_simplex(C.byref(grid._g), _ptr(coords), _ptr(cell),
+                                          _ptr(idx3), _ptr(lam))
+    return bool(inside), lam[: grid.dim + 1]
+
+
+def locate(grid: Grid, coords, cells, brute=False):
+    coords = _c(coords, np.float64)
+    cells = _c(cells, np.int32)
+    owner = np.empty(grid.n_g, dtype=np.int32)
+    st = _load().orc_locate(C.byref(grid._g), coords.shape[0], _ptr(coords), cells.shape[0],
+                            _ptr(cells), 1 if brute else 0, _ptr(owner))
+    if st:
+        raise OracleError(st, "locate")
+    return owner
+
+
+class Plan:
+    """Mesh -> grid mapping tables: per grid point vertex ids ``vid``
+    [(dim+1), n_g] (vid[0] = -1 outside the mesh) and u16 weights ``lam``
+    [dim, n_g]; per vertex the cell index ``cell`` [n_v] and u16 local
+    coordinates ``frac`` [dim, n_v]."""
+
+    def __init__(self, coords, cells, n, lo=None, hi=None, brute=False):
+        coords = _c(coords, np.float64)
+        cells = _c(cells, np.int32)
+        self.grid = Grid(coords, n, lo, hi)
+        g = self.grid
+        self.dim = g.dim
+        self.n_v = coords.shape[0]
+        self.n_g = g.n_g
+        self.owner = locate(g, coords, cells, brute)
+        self.vid = np.empty((g.dim + 1, g.n_g), dtype=np.int32)
+        self.lam = np.empty((g.dim, g.n_g), dtype=np.uint16)
+        self.lam64 = np.empty((g.dim + 1, g.n_g), dtype=np.float64)
+        self.cell = np.empty(self.n_v, dtype=np.uint32)
+        self.frac = np.empty((g.dim, self.n_v), dtype=np.uint16)
+        st = _load().orc_plan_tables(C.byref(g._g), self.n_v, _ptr(coords), _ptr(cells),
+                                     _ptr(self.owner), _ptr(self.vid), _ptr(self.lam),
+                                     _ptr(self.lam64), _ptr(self.cell), _ptr(self.frac))
+        if st:
+            raise OracleError(st, "plan_tables")
+
+
+# --------------------------------------------------------------------------- #
+# compression
+# --------------------------------------------------------------------------- #
+DEFAULTS = dict(eb_mode="rel", eb=1e-4, grid_fraction=0.5, R1=512, R2=512, C1=128, C2=128,
+                lmax=24)
+
+
+def make_params(dtype, **kw):
+    p = dict(DEFAULTS)
+    p.update(kw)
+    out = _Params()
+    out.dtype = 0 if np.dtype(dtype) == np.float64 else 1
+    out.eb_mode = 1 if p["eb_mode"] in ("rel", 1) else 0
+    out.eb = float(p["eb"])
+    out.grid_fraction = float(p["grid_fraction"])
+    for k in ("R1", "R2", "C1", "C2", "lmax"):
+        setattr(out, k, int(p[k]))
+    return out
+
+
+def field_params(x, **kw):
+    x = np.ascontiguousarray(x)
+    p = make_params(x.dtype, **kw)
+    f = _Field()
+    st = _load().orc_field_params(C.byref(p), x.size, _ptr(x), C.byref(f))
+    if st:
+        raise OracleError(st, "field_params")
+    return {k: getattr(f, k) for k, _ in _Field._fields_}
+
+
+def compress_bound(plan: Plan, dtype, **kw):
+    p = make_params(dtype, **kw)
+    return int(_load().orc_compress_bound(C.byref(plan.grid._g), plan.n_v, C.byref(p)))
+
+
+def compress(plan: Plan, x, debug=False, **kw):
+    """Algorithm 3 (closed loop). Returns the stream as a uint8 array, plus a
+    dict of intermediates (Q, q1, sym1, sym2) when ``debug``."""
+    x = np.ascontiguousarray(x)
+    if x.dtype not in (np.float64, np.float32):
+        raise TypeError("values must be float64 or float32")
+    p = make_params(x.dtype, **kw)
+    cap = compress_bound(plan, x.dtype, **kw)
+    out = np.zeros(cap, dtype=np.uint8)
+    size = C.c_size_t(0)
+    dbg = None
+    if debug:
+        dbg = dict(Q=np.empty(plan.n_v, np.int32), q1=np.empty(plan.n_g, np.int32),
+                   sym1=np.empty(plan.n_g, np.uint16), sym2=np.empty(plan.n_v, np.uint16))
+    st = _load().orc_compress(C.byref(plan.grid._g), plan.n_v, _ptr(plan.vid), _ptr(plan.lam),
+                              _ptr(plan.cell), _ptr(plan.frac), _ptr(x), C.byref(p), _ptr(out),
+                              cap, C.byref(size),
+                              _ptr(dbg["Q"]) if dbg else None, _ptr(dbg["q1"]) if dbg else None,
+                              _ptr(dbg["sym1"]) if dbg else None,
+                              _ptr(dbg["sym2"]) if dbg else None)
+    if st:
+        raise OracleError(st, "compress")
+    out = out[: size.value].copy()
+    return (out, dbg) if debug else out
+
+
+def decompress(plan: Plan, stream, debug=False):
+    """Algorithm 4. Returns the reconstructed vertex values (dtype from the
+    stream header), plus the decoded grid codes when ``debug``."""
+    stream = np.ascontiguousarray(stream, dtype=np.uint8)
+    dtype = np.float64
+    if stream.size >= 16 and int(stream[12:16].view(np.uint32)[0]) == 1:
+        dtype = np.float32
+    x = np.empty(plan.n_v, dtype=dtype)
+    q1 = np.empty(plan.n_g, np.int32) if debug else None
+    st = _load().orc_decompress(C.byref(plan.grid._g), plan.n_v, _ptr(plan.cell),
+                                _ptr(plan.frac), _ptr(stream), stream.size, _ptr(x), _ptr(q1))
+    if st:
+        raise OracleError(st, "decompress")
+    return (x, q1) if debug else x
+
+
+# --------------------------------------------------------------------------- #
+# building blocks (pin tests)
+# --------------------------------------------------------------------------- #
+def huffman_lengths(counts, lmax=24):
+    counts = _c(counts, np.uint64)
+    ln = np.zeros(counts.size, dtype=np.uint8)
+    st = _load().orc_huffman_lengths(_ptr(counts), counts.size, lmax, _ptr(ln))
+    if st:
+        raise OracleError(st, "huffman_lengths")
+    return ln
+
+
+def canonical_codes(lengths):
+    lengths = _c(lengths, np.uint8)
+    code = np.zeros(lengths.size, dtype=np.uint32)
+    _load().orc_canonical_codes(_ptr(lengths), lengths.size, _ptr(code))
+    return code
+
+
+def lorenzo(q):
+    q = _c(q, np.int32)
+    dim = q.ndim
+    n = np.ones(3, dtype=np.int32)
+    n[:dim] = q.shape[::-1]  # array is [z][y][x] / [y][x]; x fastest
+    d = np.empty_like(q)
+    _load().orc_lorenzo(dim, _ptr(n), _ptr(q), _ptr(d))
+    return d
+
+
+def lorenzo_inverse(d):
+    d = _c(d, np.int32)
+    dim = d.ndim
+    n = np.ones(3, dtype=np.int32)
+    n[:dim] = d.shape[::-1]
+    q = np.empty_like(d)
+    _load().orc_lorenzo_inverse(dim, _ptr(n), _ptr(d), _ptr(q))
+    return q

@@ -1,0 +1,105 @@
+/*
+ * mcc_oracle.h -- CPU oracle of the multi-component unstructured-mesh
+ * compressor (Gong et al., Sec. III-IV, Algorithms 3 and 4).
+ *
+ * TEST INFRASTRUCTURE ONLY. Plain, single-threaded C; slow on purpose. It
+ * shares no code, header or table with the CUDA library; only the tests, the
+ * package smoke check and the benchmark's CPU-baseline leg may call it.
+ * All arrays are host memory owned by the caller.
+ */
+#ifndef MCC_ORACLE_H
+#define MCC_ORACLE_H
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes (numerically equal to the library's, compared in tests) */
+enum {
+  ORC_OK = 0, ORC_ERR_INVALID_ARG = 1, ORC_ERR_CUDA = 2, ORC_ERR_OOM = 3,
+  ORC_ERR_RANGE = 4, ORC_ERR_CORRUPT = 5, ORC_ERR_CAPACITY = 6,
+  ORC_ERR_TIMEOUT = 7, ORC_ERR_UNSUPPORTED = 8
+};
+
+/* ---- plan (mesh -> grid mapping) ---------------------------------------- */
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int32_t n[3];            /* grid points per axis (n[2] = 1 in 2D) */
+  double lo[3], h[3], inv_h[3];
+} orc_grid;
+
+/* Resolve the grid: lo/hi given, or the mesh bounding box when lo >= hi on
+ * any axis (Sec. IV-C: corners from the vertex min / max). */
+int orc_grid_resolve(int dim, int64_t n_v, const double *coords,
+                     const int32_t n[3], const double lo[3], const double hi[3],
+                     orc_grid *g);
+
+/* Inside test of one grid point against one simplex; returns 1 when the point
+ * lies in the simplex (FP32 pre-filter, then FP64 barycentric test) and writes
+ * the FP64 barycentric coordinates lam[0..dim]. */
+int orc_point_in_simplex(const orc_grid *g, const double *coords, const int32_t *cell,
+                         const int32_t idx[3], double lam[4]);
+
+/* Owner (minimum simplex id containing the point, -1 if none) of every grid
+ * point. brute = 1: every simplex against every point; brute = 0: each
+ * simplex against the grid points of its bounding box. */
+int orc_locate(const orc_grid *g, int64_t n_v, const double *coords, int64_t n_c,
+               const int32_t *cells, int brute, int32_t *owner);
+
+/* Plan tables from owners: per grid point vid[(dim+1)][n_g] (vid[0] = -1 for
+ * points outside the mesh) and lam[dim][n_g] (u16, 2^-15 units); per vertex
+ * cell[n_v] and frac[dim][n_v] (u16, 2^-15 units). lam64 (optional, may be
+ * NULL) receives the FP64 barycentric coordinates [(dim+1)][n_g]. */
+int orc_plan_tables(const orc_grid *g, int64_t n_v, const double *coords,
+                    const int32_t *cells, const int32_t *owner,
+                    int32_t *vid, uint16_t *lam, double *lam64,
+                    uint32_t *cell, uint16_t *frac);
+
+/* ---- compression --------------------------------------------------------- */
+typedef struct {
+  int dtype;          /* 0 = float64, 1 = float32 */
+  int eb_mode;        /* 0 = absolute, 1 = relative to the value range */
+  double eb;
+  double grid_fraction; /* tau1 = f tau, tau2 = (1 - f) tau */
+  int R1, R2;         /* quantisation radii (alphabet 2R) */
+  int C1, C2;         /* symbols per lane chunk */
+  int lmax;           /* Huffman length limit */
+} orc_params;
+
+/* Per-field scalars derived from the values (Sec. III bound split). */
+typedef struct {
+  double lo, hi, M, tau, tau1, tau2, s1, s2, inv2;
+  int64_t K, Qhi, fill_u, rho21_q, rho12_q;
+  float rho21_f, rho12_f;
+  int guard;
+} orc_field;
+
+int orc_field_params(const orc_params *p, int64_t n_v, const void *x, orc_field *f);
+
+size_t orc_compress_bound(const orc_grid *g, int64_t n_v, const orc_params *p);
+
+/* Compress x (n_v values of p->dtype) into out (capacity bytes).
+ * Intermediate arrays are optional debug outputs (NULL to skip):
+ * Q[n_v] node codes, q1[n_g] grid codes, sym1[n_g], sym2[n_v]. */
+int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint16_t *lam,
+                 const uint32_t *cell, const uint16_t *frac, const void *x,
+                 const orc_params *p, uint8_t *out, size_t capacity, size_t *out_size,
+                 int32_t *Q, int32_t *q1, uint16_t *sym1, uint16_t *sym2);
+
+/* Decompress a stream into x (n_v values of the stream's dtype). q1 optional. */
+int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell,
+                   const uint16_t *frac, const uint8_t *in, size_t size, void *x,
+                   int32_t *q1);
+
+/* ---- building blocks exposed for the pin tests -------------------------- */
+int orc_huffman_lengths(const uint64_t *count, int nsym, int lmax, uint8_t *len);
+int orc_canonical_codes(const uint8_t *len, int nsym, uint32_t *code);
+void orc_lorenzo(int dim, const int32_t n[3], const int32_t *q, int32_t *delta);
+void orc_lorenzo_inverse(int dim, const int32_t n[3], const int32_t *delta, int32_t *q);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
