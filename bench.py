@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 multi-component compressor.
+
+Metric: compress + decompress GB/s of input values (n_v x sizeof(value) bytes
+per field) at relative bound 1e-4 (grid / residual split 0.5), together with
+the compression ratio, on the 2D graded workload: 2,000,000 vertices with
+density ~ exp(-4 |p - c|) around c = (0.3, 0.6), Delaunay triangulated, a
+float64 field of 20 Gaussian bumps plus 6-octave value noise, on a 1024^2
+grid (the stand-in for the paper's OpenFOAM airfoil-large, Table I). The
+plan (mesh -> grid mapping) is built once and excluded, as in Sec. IV-A.
+
+One step = mcc_compress + mcc_decompress of one device-resident field. The L2
+(129 MB) is flushed (256 MiB write, untimed) before every step; each step is
+timed with CUDA events on the launch stream. Under torchrun every rank runs an
+independent replica on its own GPU (the method has no exchange step); value is
+the sum over ranks of the input bytes divided by the slowest rank's time.
+
+``--impl reference`` times the CPU oracle (single core) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+# algorithmic HBM bytes per launch, per kernel (measurement)
+def algorithmic_bytes(dim, n_v, n_g, vsz, w1, w2, cbytes):
+    k1 = dim + 1
+    return {
+        "k_reduce": vsz * n_v,
+        "k_prequant": (vsz + 4) * n_v,
+        "k_grid2d": (4 * k1 + 2 * dim + 4 + 2) * n_g,
+        "k_grid3d": (4 * k1 + 2 * dim + 4 + 2) * n_g,
+        "k_node": (4 + 2 * dim + 4 + 2) * n_v,
+        "k_codebook": 0,
+        "k_group_len": 2 * (n_g + n_v),
+        "k_scan": 0,
+        "k_pack": 2 * (n_g + n_v) + cbytes,
+        "k_dec_prep": 0,
+        "k_dec_grid": 4 * w1 + 4 * n_g,
+        "k_scan_rows": 8 * n_g,
+        "k_scan_axis": 12 * n_g,
+        "k_dec_res": 4 * w2 + (4 + 2 * dim) * n_v + vsz * n_v,
+    }
+
+
+def load_workload(config):
+    if config == "c2":
+        coords, cells = synth.mesh2d_graded()
+        x = synth.field_bumps_noise(coords)
+        return dict(name="2d-graded-2M-delaunay-grid1024^2", coords=coords, cells=cells, x=x,
+                    n=(1024, 1024))
+    if config == "c1":
+        coords, cells = synth.mesh2d_jittered()
+        return dict(name="2d-jittered-20k-grid128^2", coords=coords, cells=cells,
+                    x=synth.field_sincos(coords), n=(128, 128))
+    if config == "c3":
+        coords, cells = synth.mesh3d_annulus()
+        return dict(name="3d-annulus-8M-tets39M-grid256^3", coords=coords, cells=cells,
+                    x=synth.field_vortex(coords), n=(256, 256, 256))
+    raise SystemExit(f"unknown config {config}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                p = [v.strip() for v in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def run_reference(args, wl):
+    """The CPU oracle (single-threaded C) timed on the same workload."""
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    plan = oracle.Plan(wl["coords"], wl["cells"], wl["n"])
+    x = wl["x"]
+    kw = dict(eb=args.eb, grid_fraction=0.5)
+    for _ in range(args.warmup):
+        oracle.decompress(plan, oracle.compress(plan, x, **kw))
+    times = []
+    size = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        s = oracle.compress(plan, x, **kw)
+        oracle.decompress(plan, s)
+        times.append(time.perf_counter() - t0)
+        size = s.size
+    t = statistics.mean(times)
+    gbs = x.nbytes / t / 1e9
+    line = {
+        "impl": "reference", "metric": "compress+decompress GB/s at eb=1e-4 rel",
+        "value": gbs, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "eb_rel": args.eb, "grid_fraction": 0.5,
+                   "compression_ratio": x.nbytes / size},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"full workload, {args.steps} steps"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(wl, eb, budget_s=12.0):
+    """Oracle compress+decompress repeated over a bounded time budget."""
+    import oracle
+    plan = oracle.Plan(wl["coords"], wl["cells"], wl["n"])
+    x = wl["x"]
+    reps, t_total = 0, 0.0
+    while t_total < budget_s and reps < 200:
+        t0 = time.perf_counter()
+        s = oracle.compress(plan, x, eb=eb)
+        oracle.decompress(plan, s)
+        t_total += time.perf_counter() - t0
+        reps += 1
+    return {"value": x.nbytes * reps / t_total / 1e9, "unit": "GB/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{reps} x compress+decompress of the full {x.size}-vertex field, "
+                      f"{t_total:.1f} s, plan excluded"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mcc", choices=["mcc", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--eb", type=float, default=1e-4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = load_workload(args.config)
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2501_06910_gb300 as mcc
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    coords = torch.from_numpy(wl["coords"]).to(dev)
+    cells = torch.from_numpy(wl["cells"]).to(dev)
+    plan = mcc.plan_create(coords, cells, wl["n"])
+    x_np = wl["x"]
+    x = torch.from_numpy(x_np).to(dev)
+    prm = mcc.params_default(dtype=mcc.F64, eb=args.eb, grid_fraction=0.5)
+    wsc = plan.workspace(prm, "compress")
+    wsd = plan.workspace(prm, "decompress")
+    cap = mcc.compress_bound(plan, prm)
+    out = torch.zeros(cap, dtype=torch.uint8, device=dev)
+    y = torch.empty_like(x)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        mcc.compress(plan, x, prm, wsc, out, sync=False)
+        mcc.decompress(plan, out, cap, y, wsd, sync=False)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    st, size = mcc.workspace_result(wsc)
+    st2, _ = mcc.workspace_result(wsd)
+    if st != 0 or st2 != 0:
+        raise SystemExit(f"device status {st}/{st2}")
+    lo, hi = float(x.min()), float(x.max())
+    tau = args.eb * (hi - lo)
+    err = float((y - x).abs().max())
+    if not err <= tau:
+        raise SystemExit(f"bound violated: {err} > {tau}")
+
+    # timed region: K steps, each bracketed by events, L2 flushed before each
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+
+    # per-kernel device times (a second pass with event brackets per launch)
+    mcc.profile_reset()
+    mcc.profile_enable(True)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        step()
+    prof = mcc.profile_read()
+    mcc.profile_enable(False)
+    launches_per_step = sum(n for _, n in prof.values()) / args.steps
+
+    # end to end through the API with host buffers (pinned)
+    x_host = torch.from_numpy(x_np).pin_memory()
+    out_host = torch.empty(cap, dtype=torch.uint8).pin_memory()
+    y_host = torch.empty_like(x_host).pin_memory()
+    x_dev = torch.empty_like(x)
+    in_dev = torch.empty_like(out)
+    e2e_ms = []
+    h2d = d2h = 0
+    for k in range(args.warmup + args.steps):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x_dev.copy_(x_host, non_blocking=True)
+        n_out = mcc.compress(plan, x_dev, prm, wsc, out, sync=True)
+        out_host[:n_out].copy_(out[:n_out])
+        in_dev[:n_out].copy_(out_host[:n_out], non_blocking=True)
+        mcc.decompress(plan, in_dev, n_out, y, wsd, sync=False)
+        y_host.copy_(y)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        h2d, d2h = x_np.nbytes + n_out, n_out + x_np.nbytes
+    if not torch.equal(y_host, y.cpu()):
+        raise SystemExit("e2e mismatch")
+    e2e = statistics.mean(e2e_ms)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    nbytes = x_np.nbytes
+    # roofline of the dominant kernel
+    W1 = int(out[168:176].cpu().numpy().view(np.uint64)[0])
+    W2 = int(out[176:184].cpu().numpy().view(np.uint64)[0])
+    alg = algorithmic_bytes(len(wl["n"]), x_np.size, int(np.prod(wl["n"])), 8, W1, W2, size)
+    per_kernel = {k: {"ms_per_launch": v[0] / v[1], "launches_per_step": v[1] / args.steps,
+                      "share": v[0] / sum(t for t, _ in prof.values())}
+                  for k, v in prof.items() if v[1]}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_per_launch"] * per_kernel[k]["launches_per_step"])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = alg.get(dom, 0) / (per_kernel[dom]["ms_per_launch"] * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if os.path.exists(tfile):
+        traffic = json.load(open(tfile)).get(dom)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
+                "peak_source": "measured" if peaks else "fallback"}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(wl, args.eb)
+    line = {
+        "metric": "compress+decompress GB/s at eb=1e-4 rel",
+        "value": world * nbytes / (ms * 1e-3) / 1e9,
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "n_vertices": int(x_np.size),
+                   "grid": list(wl["n"]), "eb_rel": args.eb, "grid_fraction": 0.5,
+                   "compression_ratio": nbytes / size, "stream_bytes": int(size),
+                   "max_abs_err_over_tau": err / tau, "l2": "flushed before every step (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "kernels": per_kernel,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * nbytes / (e2e * 1e-3) / 1e9, "unit": "GB/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * mcc.h -- C ABI of the GB300 (sm_103a) multi-component compressor for data on
+ * unstructured triangle / tetrahedral meshes, after Gong et al., "A General
+ * Framework for Error-controlled Unstructured Scientific Data Compression".
+ *
+ * The method (Sec. III-IV): vertex values x are approximated on a rectilinear
+ * grid, x1 = f(x) (barycentric interpolation, Sec. IV-D); the residual
+ * x2 = x - g(x1') at every vertex uses the decompressed grid x1' and the
+ * bilinear / trilinear operator g (Sec. III: piecewise-linear g has
+ * sum |a_j| = 1, so the bound splits as tau = tau1 + tau2); both components
+ * are compressed by an error-bounded compressor C (here: dual quantisation,
+ * N-D Lorenzo prediction for the grid, canonical Huffman for both;
+ * Algorithm 3) and reconstructed as x' = g(x1') + x2' (Algorithm 4).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are DEVICE pointers (current device), owned by the
+ *     caller; the library never frees or retains them past the call. Host
+ *     pointers are plain C pointers, also caller owned.
+ *   - Work is enqueued on the given stream; calls return after enqueueing
+ *     unless documented to synchronise. No call allocates device memory
+ *     except mcc_plan_create (the plan owns its tables until
+ *     mcc_plan_destroy).
+ *   - No exception, exit, abort or device trap crosses this boundary. Errors
+ *     found on the host are returned at once; errors found on the device
+ *     (range overflow, corrupt stream, capacity) are recorded in the
+ *     workspace's status word and returned by the synchronising calls.
+ *   - One call may use a workspace at a time: two calls in flight on the same
+ *     workspace race.
+ */
+#ifndef MCC_H
+#define MCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mcc_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  MCC_OK = 0,
+  MCC_ERR_INVALID_ARG = 1, /* bad pointer, size, mesh index or parameter */
+  MCC_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed */
+  MCC_ERR_OOM = 3,         /* plan tables could not be allocated */
+  MCC_ERR_RANGE = 4,       /* bound too small for the value range: a code would
+                              overflow (node codes need range/(2 tau2) < 2^29,
+                              grid codes |q1| < 2^27) */
+  MCC_ERR_CORRUPT = 5,     /* stream fails validation (magic, version, sizes,
+                              tables, codes); nothing read out of bounds */
+  MCC_ERR_CAPACITY = 6,    /* output or workspace buffer too small */
+  MCC_ERR_TIMEOUT = 7,     /* a bounded device wait gave up */
+  MCC_ERR_UNSUPPORTED = 8  /* parameter outside what this build supports */
+} mcc_status;
+
+enum { MCC_F64 = 0, MCC_F32 = 1 };   /* value types */
+enum { MCC_ABS = 0, MCC_REL = 1 };   /* bound modes: absolute, or x (max - min) */
+
+/* Unstructured mesh (Sec. IV-C input: vertex coordinates {p_i} and
+ * connectivity {c_j}). Triangles for dim 2, tetrahedra for dim 3. */
+typedef struct {
+  int dim;                /* 2 or 3 */
+  int64_t n_vertices;     /* >= 1 */
+  const double *coords;   /* device, [n_vertices][dim], row major */
+  int64_t n_cells;        /* >= 1 */
+  const int32_t *cells;   /* device, [n_cells][dim + 1] vertex ids in [0, n_vertices) */
+} mcc_mesh;
+
+/* Rectilinear grid layout S (Sec. IV-C): n[d] points per axis (2..32768;
+ * n[2] ignored for dim 2), corners lo/hi. If lo[d] >= hi[d] on any axis the
+ * corners are the mesh bounding box (Grid_Init, Algorithm 1: min/max of the
+ * vertex coordinates). */
+typedef struct {
+  int32_t n[3];
+  double lo[3], hi[3];
+} mcc_grid_spec;
+
+/* Compression parameters. The error bound tau (absolute, or relative to the
+ * value range max(x) - min(x); a constant field uses eb itself) splits into
+ * tau1 = grid_fraction * tau for the grid component and tau2 = (1 -
+ * grid_fraction) * tau for the residuals (Sec. III, tau1 + tau2 <= tau). */
+typedef struct {
+  int dtype;             /* MCC_F64 or MCC_F32 */
+  int eb_mode;           /* MCC_ABS or MCC_REL */
+  double eb;             /* > 0 */
+  double grid_fraction;  /* in [0.001, 0.999] */
+  int R1, R2;            /* quantisation radii: alphabets of 2R symbols, 4..2048 */
+  int C1, C2;            /* symbols per lane chunk (32 lanes per group), 1..256 */
+  int lmax;              /* Huffman code length limit, 1..24 */
+} mcc_params;
+
+typedef struct mcc_plan_s *mcc_plan;
+
+typedef struct {
+  int dim;
+  int32_t n[3];
+  double lo[3], h[3];
+  int64_t n_vertices, n_grid;
+  int64_t n_outside;     /* grid points in no simplex (filled with zero) */
+} mcc_plan_info;
+
+/* Defaults: F64, REL, eb 1e-4, grid_fraction 0.5, R1 = R2 = 512,
+ * C1 = C2 = 128, lmax 24. */
+void mcc_params_default(mcc_params *p);
+
+/* Build the mesh -> grid mapping once per mesh (Sec. IV-B: reused across
+ * variables and timesteps; excluded from the compression ratio, Sec. IV-A).
+ * Per grid point: the minimum-id simplex containing it and its barycentric
+ * weights (points in no simplex take the value zero, as the hollow regions
+ * of Fig. 1); per vertex: its grid cell and local coordinates. Synchronises
+ * the stream. The plan allocates and owns its device tables. */
+mcc_status mcc_plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, mcc_stream stream,
+                           mcc_plan *out);
+void mcc_plan_destroy(mcc_plan plan);
+mcc_status mcc_plan_get_info(mcc_plan plan, mcc_plan_info *info);
+
+/* Copy the plan tables to caller buffers (device pointers, any may be NULL):
+ * vid [(dim+1)][n_grid] int32 (vid[0][j] = -1 outside the mesh), lam
+ * [dim][n_grid] u16 (weights of vertices 1..dim in 2^-15 units), cell
+ * [n_vertices] u32 (linear index of the cell's lower corner), frac
+ * [dim][n_vertices] u16 (local coordinates in 2^-15 units). */
+mcc_status mcc_plan_copy_tables(mcc_plan plan, int32_t *d_vid, uint16_t *d_lam, uint32_t *d_cell,
+                                uint16_t *d_frac, mcc_stream stream);
+
+/* Workspace bytes needed by mcc_compress / mcc_decompress for this plan. */
+mcc_status mcc_workspace_size(mcc_plan plan, const mcc_params *p, size_t *compress_bytes,
+                              size_t *decompress_bytes);
+
+/* Upper bound of the compressed size for any field on this plan. */
+mcc_status mcc_compress_bound(mcc_plan plan, const mcc_params *p, size_t *max_bytes);
+
+/* Algorithm 3 (closed loop): compress n_vertices values of p->dtype at
+ * d_values into d_out (capacity bytes, 8-byte aligned). The stream's size
+ * is written to its header (bytes 184..191, u64) and to the workspace. If
+ * out_size is non-NULL the call synchronises the stream and returns the size
+ * together with any device-side error; otherwise it returns after enqueueing
+ * (read the result later with mcc_workspace_result). */
+mcc_status mcc_compress(mcc_plan plan, const void *d_values, const mcc_params *p,
+                        void *d_workspace, size_t workspace_bytes, void *d_out, size_t capacity,
+                        size_t *out_size, mcc_stream stream);
+
+/* Algorithm 4: reconstruct x' = g(x1') + x2' at every vertex into d_values
+ * (n_vertices values of type dtype, which must equal the stream's). The
+ * stream (in_bytes at d_in, 4-byte aligned) is validated on the device: a
+ * corrupt or mismatched stream records MCC_ERR_CORRUPT and nothing is read
+ * or written out of bounds. If sync is nonzero the call synchronises and
+ * returns device-side errors. */
+mcc_status mcc_decompress(mcc_plan plan, const void *d_in, size_t in_bytes, void *d_values,
+                          int dtype, void *d_workspace, size_t workspace_bytes, int sync,
+                          mcc_stream stream);
+
+/* Synchronise the stream and read the status (and, after a compression, the
+ * stream size; may be NULL) that the last call recorded in the workspace. */
+mcc_status mcc_workspace_result(const void *d_workspace, mcc_stream stream, size_t *out_size);
+
+const char *mcc_status_string(mcc_status s);
+
+/* Diagnostics (no counterpart in the paper): per-kernel device timing. When
+ * enabled, every kernel that mcc_compress / mcc_decompress launches is
+ * bracketed by CUDA events recorded on its stream. mcc_profile_read
+ * synchronises on the recorded events and fills up to max_entries rows of
+ * (kernel name, total milliseconds, launches), sorted by name; it returns
+ * the number of rows. mcc_profile_reset drops all accumulated rows.
+ * Host-side state is process wide and guarded by a mutex. */
+void mcc_profile_enable(int on);
+void mcc_profile_reset(void);
+int mcc_profile_read(char (*names)[32], double *ms, long long *launches, int max_entries);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCC_H */

@@ -1,0 +1,260 @@
+"""GB300 (sm_103a) multi-component compressor for data on unstructured
+meshes, after Gong et al., "A General Framework for Error-controlled
+Unstructured Scientific Data Compression" (Sec. III-IV, Algorithms 3-4).
+
+A thin ctypes binding over the C ABI of ``include/mcc.h`` (``libmcc.so``).
+Functions carry the C names without the ``mcc_`` prefix; arguments are
+marshalled from torch tensors (device memory, streams) and every step of the
+compressor runs in the library's CUDA kernels. There is no CPU fallback: if
+the library or a CUDA device is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from .native_build import LIB, build
+
+__all__ = [
+    "MCCError", "Params", "Plan", "load", "build", "params_default", "plan_create",
+    "compress", "decompress", "compress_bound", "workspace_size", "workspace_result",
+    "status_string", "profile_enable", "profile_reset", "profile_read",
+]
+
+OK, INVALID_ARG, CUDA, OOM, RANGE, CORRUPT, CAPACITY, TIMEOUT, UNSUPPORTED = range(9)
+F64, F32 = 0, 1
+ABS, REL = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MCCError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = int(status)
+        msg = status_string(status) if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} (status {status})")
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_vertices", C.c_int64), ("coords", C.c_void_p),
+                ("n_cells", C.c_int64), ("cells", C.c_void_p)]
+
+
+class _GridSpec(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+
+
+class Params(C.Structure):
+    """mcc_params: dtype, eb_mode, eb, grid_fraction, R1, R2, C1, C2, lmax."""
+    _fields_ = [("dtype", C.c_int), ("eb_mode", C.c_int), ("eb", C.c_double),
+                ("grid_fraction", C.c_double), ("R1", C.c_int), ("R2", C.c_int),
+                ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class _PlanInfo(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int32 * 3), ("lo", C.c_double * 3),
+                ("h", C.c_double * 3), ("n_vertices", C.c_int64), ("n_grid", C.c_int64),
+                ("n_outside", C.c_int64)]
+
+
+def load():
+    """Load libmcc.so (building it first when stale). Raises when no CUDA
+    device is present: the library has no host fallback."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                build()
+            lib = C.CDLL(LIB)
+            P, S = C.c_void_p, C.c_size_t
+            lib.mcc_params_default.argtypes = [C.POINTER(Params)]
+            lib.mcc_params_default.restype = None
+            lib.mcc_status_string.argtypes = [C.c_int]
+            lib.mcc_status_string.restype = C.c_char_p
+            lib.mcc_plan_create.argtypes = [C.POINTER(_Mesh), C.POINTER(_GridSpec), P, C.POINTER(P)]
+            lib.mcc_plan_destroy.argtypes = [P]
+            lib.mcc_plan_destroy.restype = None
+            lib.mcc_plan_get_info.argtypes = [P, C.POINTER(_PlanInfo)]
+            lib.mcc_plan_copy_tables.argtypes = [P, P, P, P, P, P]
+            lib.mcc_workspace_size.argtypes = [P, C.POINTER(Params), C.POINTER(S), C.POINTER(S)]
+            lib.mcc_compress_bound.argtypes = [P, C.POINTER(Params), C.POINTER(S)]
+            lib.mcc_compress.argtypes = [P, P, C.POINTER(Params), P, S, P, S, C.POINTER(S), P]
+            lib.mcc_decompress.argtypes = [P, P, S, P, C.c_int, P, S, C.c_int, P]
+            lib.mcc_workspace_result.argtypes = [P, P, C.POINTER(S)]
+            lib.mcc_profile_enable.argtypes = [C.c_int]
+            lib.mcc_profile_enable.restype = None
+            lib.mcc_profile_reset.argtypes = []
+            lib.mcc_profile_reset.restype = None
+            lib.mcc_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
+            lib.mcc_profile_read.restype = C.c_int
+            for fn in ("mcc_plan_create", "mcc_plan_get_info", "mcc_plan_copy_tables",
+                       "mcc_workspace_size", "mcc_compress_bound", "mcc_compress",
+                       "mcc_decompress", "mcc_workspace_result"):
+                getattr(lib, fn).restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load().mcc_status_string(int(status)).decode()
+
+
+def _check(status, what):
+    if status != OK:
+        raise MCCError(status, what)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t: torch.Tensor):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def params_default(**overrides) -> Params:
+    p = Params()
+    load().mcc_params_default(C.byref(p))
+    for k, v in overrides.items():
+        if k == "dtype" and not isinstance(v, int):
+            v = F64 if v in (torch.float64, "float64", "f64") else F32
+        if k == "eb_mode" and isinstance(v, str):
+            v = REL if v == "rel" else ABS
+        setattr(p, k, v)
+    return p
+
+
+class Plan:
+    """Owner of an ``mcc_plan`` (mesh -> grid mapping tables on the device)."""
+
+    def __init__(self, handle, info):
+        self._h = handle
+        self.dim = info.dim
+        self.n = tuple(info.n[: info.dim])
+        self.lo = tuple(info.lo[: info.dim])
+        self.h = tuple(info.h[: info.dim])
+        self.n_vertices = info.n_vertices
+        self.n_grid = info.n_grid
+        self.n_outside = info.n_outside
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().mcc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def copy_tables(self, stream=None):
+        """Device copies of the plan tables (vid, lam, cell, frac)."""
+        d, ng, nv = self.dim, self.n_grid, self.n_vertices
+        dev = torch.device("cuda")
+        vid = torch.empty((d + 1, ng), dtype=torch.int32, device=dev)
+        lam = torch.empty((d, ng), dtype=torch.int16, device=dev)
+        cell = torch.empty(nv, dtype=torch.int32, device=dev)
+        frac = torch.empty((d, nv), dtype=torch.int16, device=dev)
+        _check(load().mcc_plan_copy_tables(self._h, _dptr(vid), _dptr(lam), _dptr(cell),
+                                           _dptr(frac), _stream(stream)), "plan_copy_tables")
+        return dict(vid=vid, lam=lam, cell=cell, frac=frac)
+
+    def workspace(self, params: Params, which="compress"):
+        c, d = workspace_size(self, params)
+        return torch.empty(c if which == "compress" else d, dtype=torch.uint8, device="cuda")
+
+
+def plan_create(coords: torch.Tensor, cells: torch.Tensor, n, lo=None, hi=None,
+                stream=None) -> Plan:
+    """mcc_plan_create: coords float64 [n_v, dim], cells int32 [n_c, dim+1],
+    both on the device; n grid points per axis; lo/hi corners (None: the mesh
+    bounding box)."""
+    dim = coords.shape[1]
+    m = _Mesh(dim, coords.shape[0], _dptr(coords).value, cells.shape[0], _dptr(cells).value)
+    g = _GridSpec()
+    for d in range(3):
+        g.n[d] = n[d] if d < dim else 1
+        g.lo[d] = lo[d] if lo is not None and d < dim else 0.0
+        g.hi[d] = hi[d] if hi is not None and d < dim else 0.0
+    h = C.c_void_p()
+    _check(load().mcc_plan_create(C.byref(m), C.byref(g), _stream(stream), C.byref(h)),
+           "plan_create")
+    info = _PlanInfo()
+    _check(load().mcc_plan_get_info(h, C.byref(info)), "plan_get_info")
+    return Plan(h, info)
+
+
+def workspace_size(plan: Plan, params: Params):
+    c, d = C.c_size_t(), C.c_size_t()
+    _check(load().mcc_workspace_size(plan.handle, C.byref(params), C.byref(c), C.byref(d)),
+           "workspace_size")
+    return c.value, d.value
+
+
+def compress_bound(plan: Plan, params: Params) -> int:
+    b = C.c_size_t()
+    _check(load().mcc_compress_bound(plan.handle, C.byref(params), C.byref(b)), "compress_bound")
+    return b.value
+
+
+def compress(plan: Plan, x: torch.Tensor, params: Params, workspace: torch.Tensor,
+             out: torch.Tensor, sync: bool = True, stream=None):
+    """mcc_compress. Returns the stream size when ``sync`` (synchronises),
+    else None (size later from ``workspace_result``)."""
+    size = C.c_size_t(0)
+    st = load().mcc_compress(plan.handle, _dptr(x), C.byref(params), _dptr(workspace),
+                             workspace.numel(), _dptr(out), out.numel(),
+                             C.byref(size) if sync else None, _stream(stream))
+    _check(st, "compress")
+    return size.value if sync else None
+
+
+def decompress(plan: Plan, stream_bytes: torch.Tensor, nbytes: int, out: torch.Tensor,
+               workspace: torch.Tensor, sync: bool = True, stream=None):
+    """mcc_decompress into ``out`` (float64 or float32, n_vertices values)."""
+    dtype = F64 if out.dtype == torch.float64 else F32
+    st = load().mcc_decompress(plan.handle, _dptr(stream_bytes), int(nbytes), _dptr(out), dtype,
+                               _dptr(workspace), workspace.numel(), 1 if sync else 0,
+                               _stream(stream))
+    _check(st, "decompress")
+
+
+def workspace_result(workspace: torch.Tensor, stream=None):
+    size = C.c_size_t(0)
+    st = load().mcc_workspace_result(_dptr(workspace), _stream(stream), C.byref(size))
+    return st, size.value
+
+
+def profile_enable(on: bool = True):
+    """mcc_profile_enable: bracket every library kernel with CUDA events."""
+    load().mcc_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    load().mcc_profile_reset()
+
+
+def profile_read(max_entries: int = 64):
+    """mcc_profile_read: {kernel name: (total ms, launches)} (synchronises)."""
+    names = (C.c_char * 32 * max_entries)()
+    ms = (C.c_double * max_entries)()
+    n = (C.c_longlong * max_entries)()
+    k = load().mcc_profile_read(C.cast(names, C.c_void_p), ms, n, max_entries)
+    return {bytes(names[i]).split(b"\0")[0].decode(): (ms[i], n[i]) for i in range(k)}

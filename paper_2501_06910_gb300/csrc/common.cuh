@@ -1,0 +1,290 @@
+// common.cuh -- internal definitions shared by the library's translation units:
+// stream format, per-field parameters, workspace layout and the device
+// arithmetic that compression and decompression must evaluate identically.
+//
+// Floating point: every .cu file is compiled with -fmad=false; the few fused
+// multiply-adds of the predictor are written out as __fmaf_rn. FP64 is used
+// only where the bound needs it (the vertex code Q = round(x / s2) and the
+// reconstruction x' = s2 * Q); interpolation runs in FP32 on integer codes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/mcc.h"
+
+namespace mcc {
+
+// ---------------------------------------------------------------------------
+// stream format
+// ---------------------------------------------------------------------------
+constexpr uint32_t kMagic = 0x3143434Du;  // bytes 'M' 'C' 'C' '1'
+constexpr uint32_t kVersion = 1;
+constexpr uint32_t kHeaderBytes = 384;
+constexpr int kRhoBits = 40;               // bin-width ratios in 2^-40 fixed point
+constexpr double kBinShrink = 1.0 - 1.0 / 1048576.0;  // bins are 2 tau (1 - 2^-20)
+constexpr int kMaxR = 2048;
+constexpr int kMaxC = 256;
+constexpr int kMaxLen = 24;
+constexpr int kLutBits = 11;               // first-level decode table
+
+// header byte offsets
+enum : uint32_t {
+  H_MAGIC = 0, H_VERSION = 4, H_HBYTES = 8, H_DTYPE = 12, H_DIM = 16, H_FLAGS = 20, H_R1 = 24,
+  H_R2 = 28, H_C1 = 32, H_C2 = 36, H_LMAX = 40, H_NX = 44, H_NY = 48, H_NZ = 52, H_NV = 56,
+  H_NG = 64, H_TAU = 72, H_TAU1 = 80, H_TAU2 = 88, H_S1 = 96, H_S2 = 104, H_K = 112,
+  H_RHO21 = 120, H_RHO12 = 128, H_FILL = 136, H_NOUT1 = 144, H_NOUT2 = 152, H_NRAW = 160,
+  H_W1 = 168, H_W2 = 176, H_TOTAL = 184
+};
+
+__host__ __device__ inline uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+__host__ __device__ inline int64_t ngroups(int64_t n, int C) {
+  return n == 0 ? 0 : (n + 32 * (int64_t)C - 1) / (32 * (int64_t)C);
+}
+
+// Section offsets of a stream. Order: header | code lengths 1, 2 | group word
+// offsets 1, 2 | group escape prefixes 1, 2 | group raw prefix 2 | lane bit
+// lengths 1, 2 | escape values 1, 2 (int32) | raw values | bitstreams 1, 2.
+struct Layout {
+  uint64_t lens1, lens2, gtab1, gtab2, etab1, etab2, rtab2, ltab1, ltab2, out1, out2, raw, bits1,
+      bits2, total;
+};
+
+__host__ __device__ inline Layout make_layout(int R1, int R2, int64_t ng1, int64_t ng2,
+                                              uint64_t nout1, uint64_t nout2, uint64_t nraw,
+                                              uint64_t vsz, uint64_t w1, uint64_t w2) {
+  Layout L;
+  uint64_t o = kHeaderBytes;
+  L.lens1 = o; o += 2 * (uint64_t)R1;
+  L.lens2 = o; o += 2 * (uint64_t)R2;
+  o = align_up(o, 4);
+  L.gtab1 = o; o += 4 * (uint64_t)(ng1 + 1);
+  L.gtab2 = o; o += 4 * (uint64_t)(ng2 + 1);
+  L.etab1 = o; o += 4 * (uint64_t)(ng1 + 1);
+  L.etab2 = o; o += 4 * (uint64_t)(ng2 + 1);
+  L.rtab2 = o; o += 4 * (uint64_t)(ng2 + 1);
+  L.ltab1 = o; o += 64 * (uint64_t)ng1;
+  L.ltab2 = o; o += 64 * (uint64_t)ng2;
+  L.out1 = o; o += 4 * nout1;
+  L.out2 = o; o += 4 * nout2;
+  o = align_up(o, 8);
+  L.raw = o; o += vsz * nraw;
+  o = align_up(o, 4);
+  L.bits1 = o; o += 4 * w1;
+  L.bits2 = o; o += 4 * w2;
+  L.total = o;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// plan (device view)
+// ---------------------------------------------------------------------------
+struct PlanView {
+  int dim;
+  int32_t nx, ny, nz;
+  int64_t n_v, n_g;
+  const int32_t *vid;   // [(dim+1)][n_g]
+  const uint16_t *lam;  // [dim][n_g]
+  const uint32_t *cell; // [n_v]
+  const uint16_t *frac; // [dim][n_v]
+};
+
+// ---------------------------------------------------------------------------
+// per-field parameters, computed on the device from the values
+// ---------------------------------------------------------------------------
+struct FieldParams {
+  double lo, hi, M, tau, tau1, tau2, s1, s2, inv2;
+  long long K, Qhi, fill_u, rho21_q, rho12_q;
+  float rho21_f, rho12_f;
+  int guard;
+  int pad;
+};
+
+// Workspace status block (first 1 KiB of every workspace).
+struct Status {
+  unsigned int err;          // first error (mcc_status), 0 = OK
+  unsigned int done_blocks;  // reduction completion counter
+  unsigned long long out_size;
+  unsigned long long key_lo, key_hi;  // ordered keys of min / max
+  unsigned int nout1, nout2, nraw;    // escape counts (atomics)
+  unsigned int pad0;
+  unsigned long long w1, w2;          // bitstream words per component
+  Layout L;                            // stream layout of the current call
+  FieldParams f;
+};
+static_assert(sizeof(Status) <= 1024, "status block");
+constexpr size_t kStatusBytes = 1024;
+
+__device__ inline void set_error(Status *st, unsigned int code) { atomicCAS(&st->err, 0u, code); }
+
+// Ordered 64-bit key of a double: monotone for all non-NaN values.
+__host__ __device__ inline unsigned long long order_key(double v) {
+  unsigned long long b;
+#ifdef __CUDA_ARCH__
+  b = (unsigned long long)__double_as_longlong(v);
+#else
+  memcpy(&b, &v, 8);
+#endif
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ inline double key_value(unsigned long long k) {
+  unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double v;
+  memcpy(&v, &b, 8);
+  return v;
+#endif
+}
+
+// ---------------------------------------------------------------------------
+// predictor arithmetic (must match between compression and decompression)
+// ---------------------------------------------------------------------------
+// round(rho * (a + acc)), rho = rq 2^-40: integer part of a*rho from the exact
+// 128-bit product, 40-bit fraction plus FP32 correction acc*rho, one fused
+// multiply-add, round to nearest even.
+__device__ __forceinline__ long long rescale(long long a, float acc, long long rq, float rf) {
+  const unsigned long long ua = (unsigned long long)(a < 0 ? -a : a);
+  const unsigned long long ur = (unsigned long long)rq;
+  const unsigned long long lo64 = ua * ur;
+  const unsigned long long hi64 = __umul64hi(ua, ur);
+  const unsigned long long mask = (1ull << kRhoBits) - 1;
+  unsigned long long q = (hi64 << (64 - kRhoBits)) | (lo64 >> kRhoBits);
+  unsigned long long r = lo64 & mask;
+  long long hi;
+  unsigned long long lo;
+  if (a >= 0) { hi = (long long)q; lo = r; }
+  else if (r == 0) { hi = -(long long)q; lo = 0; }
+  else { hi = -(long long)q - 1; lo = (1ull << kRhoBits) - r; }
+  const float base = __fmul_rn(__ull2float_rn(lo), 0x1p-40f);
+  const float t = __fmaf_rn(acc, rf, base);
+  return hi + (long long)rintf(t);
+}
+
+__device__ __forceinline__ int wsub(int a, int b) { return (int)((unsigned)a - (unsigned)b); }
+__device__ __forceinline__ int wadd(int a, int b) { return (int)((unsigned)a + (unsigned)b); }
+
+// Grid -> vertex interpolation g (bilinear / trilinear on the grid codes of
+// the vertex's cell), returned in node units P = round(rho12 * g).
+template <int DIM>
+__device__ __forceinline__ long long predict_vertex(const int *__restrict__ q1, uint32_t c,
+                                                    float fx, float fy, float fz, int nx,
+                                                    int64_t sxy, long long rq, float rf) {
+  const int c000 = __ldg(q1 + c), c100 = __ldg(q1 + c + 1);
+  const int c010 = __ldg(q1 + c + nx), c110 = __ldg(q1 + c + nx + 1);
+  const int d100 = wsub(c100, c000), d010 = wsub(c010, c000);
+  const int d110 = wadd(wsub(wsub(c110, c100), c010), c000);
+  float acc;
+  if (DIM == 2) {
+    acc = __fmul_rn(fx, __int2float_rn(d100));
+    acc = __fmaf_rn(fy, __int2float_rn(d010), acc);
+    const float fxy = __fmul_rn(fx, fy);
+    acc = __fmaf_rn(fxy, __int2float_rn(d110), acc);
+  } else {
+    const int c001 = __ldg(q1 + c + sxy), c101 = __ldg(q1 + c + sxy + 1);
+    const int c011 = __ldg(q1 + c + sxy + nx), c111 = __ldg(q1 + c + sxy + nx + 1);
+    const int d001 = wsub(c001, c000);
+    const int d101 = wadd(wsub(wsub(c101, c100), c001), c000);
+    const int d011 = wadd(wsub(wsub(c011, c010), c001), c000);
+    int d111 = wsub(c111, c110);
+    d111 = wsub(d111, c101);
+    d111 = wsub(d111, c011);
+    d111 = wadd(d111, c100);
+    d111 = wadd(d111, c010);
+    d111 = wadd(d111, c001);
+    d111 = wsub(d111, c000);
+    acc = __fmul_rn(fx, __int2float_rn(d100));
+    acc = __fmaf_rn(fy, __int2float_rn(d010), acc);
+    acc = __fmaf_rn(fz, __int2float_rn(d001), acc);
+    const float fxy = __fmul_rn(fx, fy), fxz = __fmul_rn(fx, fz), fyz = __fmul_rn(fy, fz);
+    const float fxyz = __fmul_rn(fxy, fz);
+    acc = __fmaf_rn(fxy, __int2float_rn(d110), acc);
+    acc = __fmaf_rn(fxz, __int2float_rn(d101), acc);
+    acc = __fmaf_rn(fyz, __int2float_rn(d011), acc);
+    acc = __fmaf_rn(fxyz, __int2float_rn(d111), acc);
+  }
+  return rescale(c000, acc, rq, rf);
+}
+
+// ---------------------------------------------------------------------------
+// canonical Huffman helpers
+// ---------------------------------------------------------------------------
+// Per-length symbol counts and first codes (deflate-style canonical order:
+// codes increase with (length, symbol)).
+struct CanonTables {
+  unsigned int count[kMaxLen + 2];
+  unsigned int first[kMaxLen + 2];
+  unsigned int offset[kMaxLen + 2];
+};
+
+// Rank of every symbol among the symbols of equal length with a smaller id,
+// computed by one CTA (blockDim multiple of 32, <= 1024). rank[] in shared
+// memory, wcount is scratch [32][kMaxLen+1].
+__device__ inline void canonical_ranks(const unsigned char *len, int nsym, unsigned short *rank,
+                                       unsigned int (*wcount)[kMaxLen + 1]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int seg = (nsym + nw - 1) / nw;
+  const int s0 = warp * seg, s1 = min(nsym, s0 + seg);
+  if (lane <= kMaxLen) wcount[warp][lane] = 0;
+  __syncwarp();
+  for (int base = s0; base < s1; base += 32) {
+    const int s = base + lane;
+    const int L = s < s1 ? len[s] : 0;
+    const unsigned same = __match_any_sync(0xffffffffu, L);
+    const unsigned lt = (1u << lane) - 1;
+    const unsigned r = __popc(same & lt);
+    unsigned int running = 0;
+    if (L > 0 && s < s1) running = wcount[warp][L];
+    __syncwarp();
+    if (L > 0 && s < s1) rank[s] = (unsigned short)(running + r);
+    // the highest lane of each group advances the running count
+    if (L > 0 && s < s1 && (same >> lane) == 1u) wcount[warp][L] = running + r + 1;
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive prefix over warps, per length
+  if (threadIdx.x <= kMaxLen) {
+    const int L = threadIdx.x;
+    unsigned int acc = 0;
+    for (int w = 0; w < nw; w++) {
+      const unsigned int c = wcount[w][L];
+      wcount[w][L] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < nsym; s += blockDim.x) {
+    const int L = len[s];
+    if (L > 0) {
+      const int w = min(s / seg, nw - 1);
+      rank[s] = (unsigned short)(rank[s] + wcount[w][L]);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ inline void canonical_tables(const unsigned char *len, int nsym, CanonTables *t) {
+  if (threadIdx.x <= kMaxLen + 1) t->count[threadIdx.x] = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < nsym; s += blockDim.x)
+    if (len[s]) atomicAdd(&t->count[len[s]], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int code = 0, off = 0;
+    t->count[0] = 0;
+    for (int l = 1; l <= kMaxLen; l++) {
+      t->first[l] = code;
+      t->offset[l] = off;
+      off += t->count[l];
+      code = (code + t->count[l]) << 1;
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace mcc
+
+// Device view of a plan's tables (defined in plan.cu).
+mcc::PlanView mcc_plan_view(mcc_plan P);

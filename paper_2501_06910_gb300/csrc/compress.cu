@@ -1,0 +1,947 @@
+// compress.cu -- Algorithm 3 of Gong et al. (multi-component compression),
+// closed loop, as a chain of kernels on one stream:
+//
+//   k_reduce     min / max / finiteness of x; the last block derives the
+//                bound split tau = tau1 + tau2 (Sec. III) and the bin widths
+//   k_prequant   vertex codes Q = round(x / s2) - K            (FP64, 2 ops)
+//   k_grid       x1 = f(x): barycentric interpolation of Q at every grid
+//                point (Sec. IV-D), grid codes q1, N-D Lorenzo difference,
+//                symbols + histogram (C(x1))
+//   k_node       g(x1'): multilinear interpolation of q1 at every vertex,
+//                residual code q2 = Q - P, bound guard, symbols + histogram
+//                (C(x2), residuals serialised 1-D, Sec. IV-B)
+//   k_codebook   canonical Huffman code books (one CTA per component)
+//   k_group_len  bit length of every lane chunk, escapes per group
+//   k_scan       group offsets, section layout, header
+//   k_pack       bit packing through shared memory, escape / raw values
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "workspace.cuh"
+#include "prof.cuh"
+
+using namespace mcc;
+
+namespace {
+
+constexpr int kRawNone = 0xFFFF;
+
+struct RParams {
+  int dtype, eb_mode;
+  double eb, frac;
+};
+
+// Error check taken once per block, so every thread of the block agrees
+// (an error may be recorded concurrently by another block).
+__device__ __forceinline__ bool block_failed(const Status *st) {
+  __shared__ int failed;
+  if (threadIdx.x == 0) failed = *(volatile const unsigned int *)&st->err != 0;
+  __syncthreads();
+  return failed != 0;
+}
+
+__device__ __forceinline__ unsigned long long value_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+
+// ---------------------------------------------------------------------------
+// k_reduce: min / max of x (ordered integer keys, no FP64 compares), finite
+// check, and -- in the last block to finish -- the per-field parameters.
+// ---------------------------------------------------------------------------
+__device__ void field_params(Status *st, RParams rp) {
+  FieldParams f;
+  memset(&f, 0, sizeof(f));
+  const unsigned long long klo = ~atomicAdd(&st->key_lo, 0ull);
+  const unsigned long long khi = atomicAdd(&st->key_hi, 0ull);
+  const double lo = key_value(klo), hi = key_value(khi);
+  f.lo = lo;
+  f.hi = hi;
+  f.M = fabs(lo) > fabs(hi) ? fabs(lo) : fabs(hi);
+  double tau = rp.eb;
+  if (rp.eb_mode == 1 && hi > lo) tau = __dmul_rn(rp.eb, __dsub_rn(hi, lo));
+  f.tau = tau;
+  f.tau1 = __dmul_rn(rp.frac, tau);
+  f.tau2 = __dmul_rn(__dsub_rn(1.0, rp.frac), tau);
+  if (!isfinite(tau) || !(f.tau1 >= 1e-290) || !(f.tau2 >= 1e-290)) { set_error(st, MCC_ERR_RANGE); return; }
+  f.s1 = __dmul_rn(__dmul_rn(2.0, f.tau1), kBinShrink);
+  f.s2 = __dmul_rn(__dmul_rn(2.0, f.tau2), kBinShrink);
+  if (!isfinite(f.s1) || !isfinite(f.s2)) { set_error(st, MCC_ERR_RANGE); return; }
+  f.inv2 = __ddiv_rn(1.0, f.s2);
+  const double kd = rint(__dmul_rn(lo, f.inv2));
+  const double hd = rint(__dmul_rn(hi, f.inv2));
+  if (!(fabs(kd) < 4611686018427387904.0) || !(fabs(hd) < 4611686018427387904.0)) {
+    set_error(st, MCC_ERR_RANGE);
+    return;
+  }
+  f.K = (long long)kd;
+  f.Qhi = (long long)hd - f.K;
+  if (f.Qhi >= (1ll << 29)) { set_error(st, MCC_ERR_RANGE); return; }
+  f.fill_u = -f.K;
+  if (f.fill_u < 0) f.fill_u = 0;
+  if (f.fill_u > f.Qhi) f.fill_u = f.Qhi;
+  const double r21 = rint(__dmul_rn(__ddiv_rn(f.s2, f.s1), 1099511627776.0));
+  const double r12 = rint(__dmul_rn(__ddiv_rn(f.s1, f.s2), 1099511627776.0));
+  if (!(r21 >= 1.0 && r21 < 1125899906842624.0) || !(r12 >= 1.0 && r12 < 1125899906842624.0)) {
+    set_error(st, MCC_ERR_INVALID_ARG);
+    return;
+  }
+  f.rho21_q = (long long)r21;
+  f.rho12_q = (long long)r12;
+  f.rho21_f = __fmul_rn(__ll2float_rn(f.rho21_q), 0x1p-40f);
+  f.rho12_f = __fmul_rn(__ll2float_rn(f.rho12_q), 0x1p-40f);
+  f.guard = (rp.dtype == MCC_F32) || !(f.M <= __dmul_rn(f.tau2, 268435456.0));
+  st->f = f;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_reduce(const T *__restrict__ x, int64_t n, Status *st,
+                                                RParams rp, unsigned int *hist, int nhist) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nhist; i += gridDim.x * blockDim.x)
+    hist[i] = 0;
+  unsigned long long mn = 0, mx = 0;  // mn holds ~key (max of ~key = min key)
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) v[u] = (double)__ldcs(x + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const unsigned long long b = value_bits(v[u]);
+      bad |= ((b >> 52) & 0x7FF) == 0x7FF;
+      const unsigned long long k = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+      mn = max(mn, ~k);
+      mx = max(mx, k);
+    }
+  }
+  for (; i < n; i += stride) {
+    const unsigned long long b = value_bits((double)__ldcs(x + i));
+    bad |= ((b >> 52) & 0x7FF) == 0x7FF;
+    const unsigned long long k = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    mn = max(mn, ~k);
+    mx = max(mx, k);
+  }
+  for (int o = 16; o; o >>= 1) {
+    mn = max(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  __shared__ unsigned long long smn[8], smx[8];
+  __shared__ int sbad;
+  if (threadIdx.x == 0) sbad = 0;
+  __syncthreads();
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    smn[w] = mn;
+    smx[w] = mx;
+    if (bad) sbad = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+      mn = max(mn, smn[k]);
+      mx = max(mx, smx[k]);
+    }
+    if (sbad) set_error(st, MCC_ERR_INVALID_ARG);
+    atomicMax(&st->key_lo, mn);
+    atomicMax(&st->key_hi, mx);
+    __threadfence();
+    const unsigned int ticket = atomicAdd(&st->done_blocks, 1u);
+    if (ticket == gridDim.x - 1) {
+      __threadfence();
+      if (atomicAdd(&st->err, 0u) == 0) field_params(st, rp);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_prequant: Q = round(x * (1 / s2)) - K
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_prequant(const T *__restrict__ x, int64_t n,
+                                                  const Status *__restrict__ st, int *__restrict__ Q) {
+  if (st->err) return;
+  const double inv2 = st->f.inv2;
+  const long long K = st->f.K;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double v = (double)__ldg(x + i);
+    Q[i] = (int)(__double2ll_rn(__dmul_rn(v, inv2)) - K);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// grid codes: x1 = f(x) on the vertex codes, rescaled to grid bins
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ int grid_code(int64_t j, const PlanView &pv, const int *__restrict__ Q,
+                                         const FieldParams &f, Status *st) {
+  const int v0 = __ldg(pv.vid + j);
+  long long a;
+  float acc = 0.0f;
+  if (v0 < 0) {
+    a = f.fill_u;
+  } else {
+    const int qa = __ldg(Q + v0);
+    a = qa;
+#pragma unroll
+    for (int k = 1; k <= DIM; k++) {
+      const int dk = wsub(__ldg(Q + __ldg(pv.vid + k * pv.n_g + j)), qa);
+      const float lf = __fmul_rn(__uint2float_rn(__ldg(pv.lam + (k - 1) * pv.n_g + j)), 0x1p-15f);
+      acc = k == 1 ? __fmul_rn(__int2float_rn(dk), lf) : __fmaf_rn(__int2float_rn(dk), lf, acc);
+    }
+  }
+  const long long q = rescale(a, acc, f.rho21_q, f.rho21_f);
+  if (q <= -(1ll << 27) || q >= (1ll << 27)) {
+    set_error(st, MCC_ERR_RANGE);
+    return 0;
+  }
+  return (int)q;
+}
+
+// Shared-memory histogram add, aggregated over lanes holding the same symbol.
+__device__ __forceinline__ void hist_add(unsigned int *sh, int sym, bool valid) {
+  const int key = valid ? sym : -1;
+  const unsigned same = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  if (valid && (__ffs(same) - 1) == lane) atomicAdd(sh + sym, (unsigned)__popc(same));
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(256) k_grid2d(PlanView pv, const int *__restrict__ Q,
+                                                Status *st, int R1, int *__restrict__ q1,
+                                                unsigned short *__restrict__ sym1,
+                                                int *__restrict__ val1, unsigned int *hist1) {
+  extern __shared__ unsigned int shist[];
+  __shared__ int s[TY + 1][TX + 1];
+  if (block_failed(st)) return;
+  const int nsym = 2 * R1;
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x) shist[i] = 0;
+  const FieldParams f = st->f;
+  const int nx = pv.nx, ny = pv.ny;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  for (int idx = threadIdx.x; idx < (TY + 1) * (TX + 1); idx += blockDim.x) {
+    const int ly = idx / (TX + 1), lx = idx - ly * (TX + 1);
+    const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+    int q = 0;
+    if (gx >= 0 && gy >= 0 && gx < nx && gy < ny) {
+      const int64_t j = gx + (int64_t)nx * gy;
+      q = grid_code<2>(j, pv, Q, f, st);
+      if (lx > 0 && ly > 0) q1[j] = q;
+    }
+    s[ly][lx] = q;
+  }
+  __syncthreads();
+  unsigned int nesc = 0;
+  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
+    const int ly = idx / TX, lx = idx - ly * TX;
+    const int gx = x0 + lx, gy = y0 + ly;
+    const bool valid = gx < nx && gy < ny;
+    int sym = 0;
+    if (valid) {
+      const int d = wadd(wsub(wsub(s[ly + 1][lx + 1], s[ly + 1][lx]), s[ly][lx + 1]), s[ly][lx]);
+      const int64_t j = gx + (int64_t)nx * gy;
+      if (d >= -(R1 - 1) && d <= R1 - 2) {
+        sym = d + R1;
+      } else {
+        sym = 0;
+        val1[j] = d;
+        nesc++;
+      }
+      sym1[j] = (unsigned short)sym;
+    }
+    hist_add(shist, sym, valid);
+  }
+  if (nesc) atomicAdd(&st->nout1, nesc);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x)
+    if (shist[i]) atomicAdd(hist1 + i, shist[i]);
+}
+
+// 3D: tiles of TX x TY points walking a segment of SZ planes in z; the plane
+// below the segment is recomputed as halo.
+template <int TX, int TY, int SZ>
+__global__ void __launch_bounds__(TX *TY) k_grid3d(PlanView pv, const int *__restrict__ Q,
+                                                   Status *st, int R1, int *__restrict__ q1,
+                                                   unsigned short *__restrict__ sym1,
+                                                   int *__restrict__ val1, unsigned int *hist1) {
+  extern __shared__ unsigned int shist[];
+  __shared__ int s[2][TY + 1][TX + 1];
+  if (block_failed(st)) return;
+  const int nsym = 2 * R1;
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x) shist[i] = 0;
+  const FieldParams f = st->f;
+  const int nx = pv.nx, ny = pv.ny, nz = pv.nz;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * SZ;
+  const int64_t sxy = (int64_t)nx * ny;
+  unsigned int nesc = 0;
+  int cur = 0;
+  for (int z = z0 - 1; z < min(z0 + SZ, nz); z++) {
+    for (int idx = threadIdx.x; idx < (TY + 1) * (TX + 1); idx += blockDim.x) {
+      const int ly = idx / (TX + 1), lx = idx - ly * (TX + 1);
+      const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+      int q = 0;
+      if (z >= 0 && gx >= 0 && gy >= 0 && gx < nx && gy < ny) {
+        const int64_t j = gx + (int64_t)nx * gy + sxy * z;
+        q = grid_code<3>(j, pv, Q, f, st);
+        if (lx > 0 && ly > 0 && z >= z0) q1[j] = q;
+      }
+      s[cur][ly][lx] = q;
+    }
+    __syncthreads();
+    if (z >= z0) {
+      const int prv = cur ^ 1;
+      for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
+        const int ly = idx / TX, lx = idx - ly * TX;
+        const int gx = x0 + lx, gy = y0 + ly;
+        const bool valid = gx < nx && gy < ny;
+        int sym = 0;
+        if (valid) {
+          int d = s[cur][ly + 1][lx + 1];
+          d = wsub(d, s[cur][ly + 1][lx]);
+          d = wsub(d, s[cur][ly][lx + 1]);
+          d = wsub(d, s[prv][ly + 1][lx + 1]);
+          d = wadd(d, s[cur][ly][lx]);
+          d = wadd(d, s[prv][ly + 1][lx]);
+          d = wadd(d, s[prv][ly][lx + 1]);
+          d = wsub(d, s[prv][ly][lx]);
+          const int64_t j = gx + (int64_t)nx * gy + sxy * z;
+          if (d >= -(R1 - 1) && d <= R1 - 2) {
+            sym = d + R1;
+          } else {
+            sym = 0;
+            val1[j] = d;
+            nesc++;
+          }
+          sym1[j] = (unsigned short)sym;
+        }
+        hist_add(shist, sym, valid);
+      }
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  if (nesc) atomicAdd(&st->nout1, nesc);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x)
+    if (shist[i]) atomicAdd(hist1 + i, shist[i]);
+}
+
+// ---------------------------------------------------------------------------
+// k_node: residual codes at the vertices
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_node(PlanView pv, const T *__restrict__ x,
+                                              const int *__restrict__ Q, const int *__restrict__ q1,
+                                              Status *st, int R2, unsigned short *__restrict__ sym2,
+                                              int *__restrict__ val2, unsigned int *hist2) {
+  extern __shared__ unsigned int shist[];
+  if (block_failed(st)) return;
+  const int nsym = 2 * R2;
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x) shist[i] = 0;
+  __syncthreads();
+  const FieldParams f = st->f;
+  const int64_t n = pv.n_v;
+  const int nx = pv.nx;
+  const int64_t sxy = (int64_t)pv.nx * pv.ny;
+  const int rawsym = 2 * R2 - 1;
+  unsigned int nesc = 0, nraw = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nloop = (n + stride - 1) / stride * stride;  // uniform trip count per warp
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nloop; i += stride) {
+    const bool valid = i < n;
+    int sym = 0;
+    if (valid) {
+      const uint32_t c = __ldg(pv.cell + i);
+      const float fx = __fmul_rn(__uint2float_rn(__ldg(pv.frac + i)), 0x1p-15f);
+      const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + i)), 0x1p-15f);
+      const float fz = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + i)), 0x1p-15f) : 0.0f;
+      const int Qi = __ldg(Q + i);
+      const long long P = predict_vertex<DIM>(q1, c, fx, fy, fz, nx, sxy, f.rho12_q, f.rho12_f);
+      const long long q2 = (long long)Qi - P;
+      bool raw = q2 < -2147483648ll || q2 > 2147483647ll;
+      if (f.guard) {
+        const double v = (double)__ldg(x + i);
+        const double xr = __dmul_rn(f.s2, (double)((long long)Qi + f.K));
+        const double xo = sizeof(T) == 8 ? xr : (double)__double2float_rn(xr);
+        if (fabs(__dsub_rn(v, xo)) > f.tau2) raw = true;
+      }
+      if (raw) {
+        sym = rawsym;
+        nraw++;
+      } else if (q2 >= -(R2 - 1) && q2 <= R2 - 2) {
+        sym = (int)q2 + R2;
+      } else {
+        sym = 0;
+        val2[i] = (int)q2;
+        nesc++;
+      }
+      sym2[i] = (unsigned short)sym;
+    }
+    hist_add(shist, sym, valid);
+  }
+  if (nesc) atomicAdd(&st->nout2, nesc);
+  if (nraw) atomicAdd(&st->nraw, nraw);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x)
+    if (shist[i]) atomicAdd(hist2 + i, shist[i]);
+}
+
+// ---------------------------------------------------------------------------
+// k_codebook: canonical Huffman code book of one component per CTA.
+// Two-queue construction over the leaves sorted by (count, symbol) -- leaves
+// win ties, internal nodes leave in creation order -- depths by pointer
+// jumping; counts halved (c -> max(1, c >> 1)) while a code exceeds lmax.
+// ---------------------------------------------------------------------------
+struct CodebookArgs {
+  const unsigned int *hist;
+  int nsym;
+  unsigned int *code;
+  unsigned char *len;
+  unsigned char *stream_lens;
+};
+
+__global__ void __launch_bounds__(1024) k_codebook(CodebookArgs a1, CodebookArgs a2, int lmax,
+                                                   Status *st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (block_failed(st)) return;
+  const CodebookArgs A = blockIdx.x == 0 ? a1 : a2;
+  const int nsym = A.nsym;
+  int npow = 1;
+  while (npow < nsym) npow <<= 1;
+  // shared memory carve-up
+  unsigned long long *keys = (unsigned long long *)smem;                 // [npow]
+  unsigned long long *Iw = keys + npow;                                  // [nsym]
+  unsigned int *cnt = (unsigned int *)(Iw + nsym);                       // [nsym]
+  unsigned short *anc0 = (unsigned short *)(cnt + nsym);                 // [2 nsym]
+  unsigned short *anc1 = anc0 + 2 * nsym;                                // [2 nsym]
+  unsigned short *dep0 = anc1 + 2 * nsym;                                // [2 nsym]
+  unsigned short *dep1 = dep0 + 2 * nsym;                                // [2 nsym]
+  unsigned short *rank = dep1 + 2 * nsym;                                // [nsym]
+  unsigned char *lens = (unsigned char *)(rank + nsym);                  // [nsym]
+  __shared__ unsigned int wcount[32][kMaxLen + 1];
+  __shared__ CanonTables ct;
+  __shared__ int m_sh, kpos, maxlen;
+
+  const int tid = threadIdx.x;
+  if (tid == 0) m_sh = 0;
+  __syncthreads();
+  for (int s = tid; s < nsym; s += blockDim.x) {
+    cnt[s] = A.hist[s];
+    lens[s] = 0;
+    if (cnt[s]) atomicAdd(&m_sh, 1);
+  }
+  __syncthreads();
+  const int m = m_sh;
+  if (m == 1) {
+    for (int s = tid; s < nsym; s += blockDim.x)
+      if (cnt[s]) lens[s] = 1;
+  }
+  while (m >= 2) {
+    if (tid == 0) { kpos = 0; maxlen = 0; }
+    __syncthreads();
+    for (int s = tid; s < nsym; s += blockDim.x)
+      if (cnt[s]) keys[atomicAdd(&kpos, 1)] = ((unsigned long long)cnt[s] << 32) | (unsigned)s;
+    for (int s = m + tid; s < npow; s += blockDim.x) keys[s] = ~0ull;
+    __syncthreads();
+    // bitonic sort, ascending
+    for (int k = 2; k <= npow; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < npow; i += blockDim.x) {
+          const int p = i ^ j;
+          if (p > i) {
+            const unsigned long long a = keys[i], b = keys[p];
+            const bool up = (i & k) == 0;
+            if ((a > b) == up) { keys[i] = b; keys[p] = a; }
+          }
+        }
+        __syncthreads();
+      }
+    // two-queue merge (one thread): node ids 0..m-1 leaves in sorted order,
+    // m..2m-2 internal nodes in creation order
+    if (tid == 0) {
+      int a = 0, b = 0, c = 0;
+      while (c < m - 1) {
+        int id[2];
+        unsigned long long w[2];
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+          const bool leaf = a < m && (b >= c || (keys[a] >> 32) <= Iw[b]);
+          if (leaf) { id[r] = a; w[r] = keys[a] >> 32; a++; }
+          else { id[r] = m + b; w[r] = Iw[b]; b++; }
+        }
+        Iw[c] = w[0] + w[1];
+        anc0[id[0]] = (unsigned short)(m + c);
+        anc0[id[1]] = (unsigned short)(m + c);
+        c++;
+      }
+      anc0[2 * m - 2] = (unsigned short)(2 * m - 2);
+    }
+    __syncthreads();
+    const int N = 2 * m - 1, root = 2 * m - 2;
+    for (int v = tid; v < N; v += blockDim.x) dep0[v] = v == root ? 0 : 1;
+    __syncthreads();
+    unsigned short *ac = anc0, *an = anc1, *dc = dep0, *dn = dep1;
+    for (int span = 1; span < N; span <<= 1) {
+      for (int v = tid; v < N; v += blockDim.x) {
+        const unsigned short p = ac[v];
+        dn[v] = (unsigned short)(dc[v] + dc[p]);
+        an[v] = ac[p];
+      }
+      __syncthreads();
+      unsigned short *t = ac; ac = an; an = t;
+      t = dc; dc = dn; dn = t;
+    }
+    for (int v = tid; v < m; v += blockDim.x) atomicMax(&maxlen, (int)dc[v]);
+    __syncthreads();
+    if (maxlen <= lmax) {
+      for (int v = tid; v < m; v += blockDim.x) lens[keys[v] & 0xFFFF] = (unsigned char)dc[v];
+      __syncthreads();
+      break;
+    }
+    for (int s = tid; s < nsym; s += blockDim.x)
+      if (cnt[s]) cnt[s] = max(1u, cnt[s] >> 1);
+    __syncthreads();
+  }
+  __syncthreads();
+  canonical_tables(lens, nsym, &ct);
+  canonical_ranks(lens, nsym, rank, wcount);
+  for (int s = tid; s < nsym; s += blockDim.x) {
+    const int L = lens[s];
+    A.len[s] = (unsigned char)L;
+    A.stream_lens[s] = (unsigned char)L;
+    A.code[s] = L ? ct.first[L] + rank[s] : 0u;
+  }
+}
+
+size_t codebook_smem(int nsym) {
+  int npow = 1;
+  while (npow < nsym) npow <<= 1;
+  return 8 * (size_t)npow + 8 * (size_t)nsym + 4 * (size_t)nsym + 2 * 8 * (size_t)nsym +
+         2 * (size_t)nsym + (size_t)nsym + 16;
+}
+
+// ---------------------------------------------------------------------------
+// k_group_len: lane bit lengths (written into the stream), per-group words,
+// escapes and raw values.
+// ---------------------------------------------------------------------------
+struct GroupArgs {
+  const unsigned short *sym1, *sym2;
+  const unsigned char *len1, *len2;
+  int64_t n1, n2, ng1, ng2;
+  int C1, C2, nsym1, nsym2;
+  unsigned short *ltab1, *ltab2;  // in the output stream
+  unsigned int *gw, *ge, *gr;     // workspace [ng1 + ng2]
+};
+
+__global__ void __launch_bounds__(256) k_group_len(GroupArgs a, const Status *st) {
+  __shared__ unsigned char l1[2 * kMaxR], l2[2 * kMaxR];
+  if (block_failed(st)) return;
+  for (int i = threadIdx.x; i < a.nsym1; i += blockDim.x) l1[i] = a.len1[i];
+  for (int i = threadIdx.x; i < a.nsym2; i += blockDim.x) l2[i] = a.len2[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t gi = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gi >= a.ng1 + a.ng2) return;
+  const bool c1 = gi < a.ng1;
+  const int64_t g = c1 ? gi : gi - a.ng1;
+  const int C = c1 ? a.C1 : a.C2;
+  const int64_t n = c1 ? a.n1 : a.n2;
+  const unsigned short *sym = c1 ? a.sym1 : a.sym2;
+  const unsigned char *L = c1 ? l1 : l2;
+  const int rawsym = c1 ? kRawNone : a.nsym2 - 1;
+  unsigned int bits = 0, esc = 0, raw = 0;
+  const int64_t base = g * 32 * (int64_t)C + lane;
+  for (int k = 0; k < C; k++) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (p >= n) break;
+    const int s = __ldg(sym + p);
+    bits += L[s];
+    esc += s == 0;
+    raw += s == rawsym;
+  }
+  (c1 ? a.ltab1 : a.ltab2)[g * 32 + lane] = (unsigned short)bits;
+  for (int o = 16; o; o >>= 1) {
+    bits += __shfl_xor_sync(0xffffffffu, bits, o);
+    esc += __shfl_xor_sync(0xffffffffu, esc, o);
+    raw += __shfl_xor_sync(0xffffffffu, raw, o);
+  }
+  if (lane == 0) {
+    a.gw[gi] = (bits + 31) / 32;
+    a.ge[gi] = esc;
+    a.gr[gi] = raw;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_scan: exclusive prefixes over groups, layout and header (one CTA)
+// ---------------------------------------------------------------------------
+__device__ unsigned long long block_exclusive_scan(const unsigned int *in, int64_t n,
+                                                   unsigned int *out, unsigned int *swarp) {
+  // writes out[0..n] (out[n] = total); returns the total
+  unsigned long long carry = 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t base = 0; base < n; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const unsigned int v = i < n ? in[i] : 0u;
+    unsigned int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) swarp[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      unsigned int t = lane < nw ? swarp[lane] : 0u;
+      unsigned int s = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int u = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += u;
+      }
+      if (lane < nw) swarp[lane] = s - t;  // exclusive warp offsets
+      if (lane == 31) swarp[32] = s;      // block total
+    }
+    __syncthreads();
+    if (i < n) out[i] = (unsigned int)(carry + swarp[w] + incl - v);
+    carry += swarp[32];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = (unsigned int)carry;
+  __syncthreads();
+  return carry;
+}
+
+struct ScanArgs {
+  const unsigned int *gw, *ge, *gr;
+  int64_t ng1, ng2;
+  unsigned char *out;
+  uint64_t capacity;
+  Layout fixed;  // fixed-size part (lens .. ltab2)
+  int dtype, dim, R1, R2, C1, C2, lmax;
+  int nx, ny, nz;
+  int64_t n_v, n_g;
+};
+
+__device__ __forceinline__ void put32(unsigned char *p, uint32_t v) { *(uint32_t *)p = v; }
+__device__ __forceinline__ void put64(unsigned char *p, uint64_t v) { *(uint64_t *)p = v; }
+
+__global__ void __launch_bounds__(1024) k_scan(ScanArgs a, Status *st) {
+  __shared__ unsigned int swarp[33];
+  if (block_failed(st)) return;
+  const Layout F = a.fixed;
+  unsigned char *o = a.out;
+  const unsigned long long w1 = block_exclusive_scan(a.gw, a.ng1, (unsigned int *)(o + F.gtab1), swarp);
+  const unsigned long long w2 = block_exclusive_scan(a.gw + a.ng1, a.ng2, (unsigned int *)(o + F.gtab2), swarp);
+  const unsigned long long e1 = block_exclusive_scan(a.ge, a.ng1, (unsigned int *)(o + F.etab1), swarp);
+  const unsigned long long e2 = block_exclusive_scan(a.ge + a.ng1, a.ng2, (unsigned int *)(o + F.etab2), swarp);
+  const unsigned long long r2 = block_exclusive_scan(a.gr + a.ng1, a.ng2, (unsigned int *)(o + F.rtab2), swarp);
+  if (threadIdx.x != 0) return;
+  const uint64_t vsz = a.dtype == MCC_F64 ? 8 : 4;
+  const Layout L = make_layout(a.R1, a.R2, a.ng1, a.ng2, e1, e2, r2, vsz, w1, w2);
+  st->L = L;
+  st->w1 = w1;
+  st->w2 = w2;
+  st->out_size = L.total;
+  if (L.total > a.capacity) { set_error(st, MCC_ERR_CAPACITY); return; }
+  const FieldParams &f = st->f;
+  for (int i = 0; i < (int)kHeaderBytes; i += 8) put64(o + i, 0);
+  put32(o + H_MAGIC, kMagic);
+  put32(o + H_VERSION, kVersion);
+  put32(o + H_HBYTES, kHeaderBytes);
+  put32(o + H_DTYPE, (uint32_t)a.dtype);
+  put32(o + H_DIM, (uint32_t)a.dim);
+  put32(o + H_FLAGS, f.guard ? 1u : 0u);
+  put32(o + H_R1, (uint32_t)a.R1);
+  put32(o + H_R2, (uint32_t)a.R2);
+  put32(o + H_C1, (uint32_t)a.C1);
+  put32(o + H_C2, (uint32_t)a.C2);
+  put32(o + H_LMAX, (uint32_t)a.lmax);
+  put32(o + H_NX, (uint32_t)a.nx);
+  put32(o + H_NY, (uint32_t)a.ny);
+  put32(o + H_NZ, (uint32_t)a.nz);
+  put64(o + H_NV, (uint64_t)a.n_v);
+  put64(o + H_NG, (uint64_t)a.n_g);
+  put64(o + H_TAU, (uint64_t)__double_as_longlong(f.tau));
+  put64(o + H_TAU1, (uint64_t)__double_as_longlong(f.tau1));
+  put64(o + H_TAU2, (uint64_t)__double_as_longlong(f.tau2));
+  put64(o + H_S1, (uint64_t)__double_as_longlong(f.s1));
+  put64(o + H_S2, (uint64_t)__double_as_longlong(f.s2));
+  put64(o + H_K, (uint64_t)f.K);
+  put64(o + H_RHO21, (uint64_t)f.rho21_q);
+  put64(o + H_RHO12, (uint64_t)f.rho12_q);
+  put64(o + H_FILL, (uint64_t)f.fill_u);
+  put64(o + H_NOUT1, e1);
+  put64(o + H_NOUT2, e2);
+  put64(o + H_NRAW, r2);
+  put64(o + H_W1, w1);
+  put64(o + H_W2, w2);
+  put64(o + H_TOTAL, L.total);
+  // zero the alignment padding between sections
+  for (uint64_t p = F.lens2 + 2 * (uint64_t)a.R2; p < F.gtab1; p++) o[p] = 0;
+  for (uint64_t p = L.out2 + 4 * e2; p < L.raw; p++) o[p] = 0;
+  for (uint64_t p = L.raw + vsz * r2; p < L.bits1; p++) o[p] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// k_pack: bit packing of one group per warp through shared memory
+// ---------------------------------------------------------------------------
+struct PackArgs {
+  const unsigned short *sym1, *sym2;
+  const unsigned int *code1, *code2;
+  const unsigned char *len1, *len2;
+  const int *val1, *val2;
+  const void *x;
+  int64_t n1, n2, ng1, ng2;
+  int C1, C2, nsym1, nsym2, vsz;
+  unsigned char *out;
+  int words_per_warp;
+};
+
+__global__ void __launch_bounds__(128) k_pack(PackArgs a, const Status *st) {
+  extern __shared__ unsigned int stage[];
+  if (block_failed(st)) return;
+  const Layout L = st->L;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t gi = blockIdx.x * (int64_t)(blockDim.x >> 5) + w;
+  if (gi >= a.ng1 + a.ng2) return;
+  const bool c1 = gi < a.ng1;
+  const int64_t g = c1 ? gi : gi - a.ng1;
+  const int C = c1 ? a.C1 : a.C2;
+  const int64_t n = c1 ? a.n1 : a.n2;
+  const unsigned short *sym = c1 ? a.sym1 : a.sym2;
+  const unsigned int *code = c1 ? a.code1 : a.code2;
+  const unsigned char *len = c1 ? a.len1 : a.len2;
+  const int *val = c1 ? a.val1 : a.val2;
+  const int rawsym = c1 ? kRawNone : a.nsym2 - 1;
+  unsigned char *o = a.out;
+  const unsigned int *gtab = (const unsigned int *)(o + (c1 ? L.gtab1 : L.gtab2));
+  const unsigned int *etab = (const unsigned int *)(o + (c1 ? L.etab1 : L.etab2));
+  const unsigned int *rtab = (const unsigned int *)(o + L.rtab2);
+  const unsigned short *ltab = (const unsigned short *)(o + (c1 ? L.ltab1 : L.ltab2));
+  int *outv = (int *)(o + (c1 ? L.out1 : L.out2));
+  unsigned int *bits = (unsigned int *)(o + (c1 ? L.bits1 : L.bits2));
+  unsigned int *sm = stage + w * a.words_per_warp;
+
+  const unsigned int w0 = gtab[g], nw = gtab[g + 1] - w0;
+  for (unsigned int i = lane; i < nw; i += 32) sm[i] = 0;
+  // exclusive scan of lane bit lengths
+  const unsigned int lb = ltab[g * 32 + lane];
+  unsigned int incl = lb;
+  for (int s = 1; s < 32; s <<= 1) {
+    const unsigned int t = __shfl_up_sync(0xffffffffu, incl, s);
+    if (lane >= s) incl += t;
+  }
+  unsigned int pos = incl - lb;
+  __syncwarp();
+  unsigned int e_run = etab[g], r_run = c1 ? 0u : rtab[g];
+  const unsigned lt = (1u << lane) - 1;
+  const int64_t base = g * 32 * (int64_t)C + lane;
+  for (int k = 0; k < C; k++) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (g * 32 * (int64_t)C + 32 * (int64_t)k >= n) break;  // warp-uniform
+    const bool valid = p < n;
+    const int s = valid ? (int)__ldg(sym + p) : -1;
+    if (valid) {
+      const unsigned int cl = len[s];
+      const unsigned long long v =
+          ((unsigned long long)code[s] << (64 - cl)) >> (pos & 31);
+      atomicOr(sm + (pos >> 5), (unsigned int)(v >> 32));
+      if ((pos & 31) + cl > 32) atomicOr(sm + (pos >> 5) + 1, (unsigned int)v);
+      pos += cl;
+    }
+    const unsigned em = __ballot_sync(0xffffffffu, s == 0);
+    if (s == 0) outv[e_run + __popc(em & lt)] = __ldg(val + p);
+    e_run += __popc(em);
+    if (!c1) {
+      const unsigned rm = __ballot_sync(0xffffffffu, s == rawsym);
+      if (s == rawsym) {
+        unsigned char *dst = o + L.raw + (uint64_t)a.vsz * (r_run + __popc(rm & lt));
+        if (a.vsz == 8) *(unsigned long long *)dst = ((const unsigned long long *)a.x)[p];
+        else *(unsigned int *)dst = ((const unsigned int *)a.x)[p];
+      }
+      r_run += __popc(rm);
+    }
+  }
+  __syncwarp();
+  for (unsigned int i = lane; i < nw; i += 32) bits[w0 + i] = sm[i];
+}
+
+inline unsigned int nblk(int64_t n, int bs) {
+  const int64_t b = (n + bs - 1) / bs;
+  return (unsigned int)(b < 1 ? 1 : b);
+}
+
+int g_num_sms = 0;
+int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  return g_num_sms;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+mcc_status check_params(const mcc_params *p) {
+  if (!p) return MCC_ERR_INVALID_ARG;
+  if (p->dtype != MCC_F64 && p->dtype != MCC_F32) return MCC_ERR_INVALID_ARG;
+  if (p->eb_mode != MCC_ABS && p->eb_mode != MCC_REL) return MCC_ERR_INVALID_ARG;
+  if (!(p->eb > 0.0) || !std::isfinite(p->eb)) return MCC_ERR_INVALID_ARG;
+  if (!(p->grid_fraction >= 1e-3 && p->grid_fraction <= 1.0 - 1e-3)) return MCC_ERR_INVALID_ARG;
+  if (p->R1 < 4 || p->R1 > kMaxR || p->R2 < 4 || p->R2 > kMaxR) return MCC_ERR_UNSUPPORTED;
+  if (p->C1 < 1 || p->C1 > kMaxC || p->C2 < 1 || p->C2 > kMaxC) return MCC_ERR_UNSUPPORTED;
+  if (p->lmax < 1 || p->lmax > kMaxLen) return MCC_ERR_UNSUPPORTED;
+  return MCC_OK;
+}
+
+CompressWs compress_ws_layout(const PlanView &pv, const mcc_params *p) {
+  CompressWs w;
+  size_t o = kStatusBytes;
+  auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+  const int64_t ng1 = ngroups(pv.n_g, p->C1), ng2 = ngroups(pv.n_v, p->C2);
+  w.hist1 = take(4 * 2 * (size_t)p->R1);
+  w.hist2 = take(4 * 2 * (size_t)p->R2);
+  w.code1 = take(4 * 2 * (size_t)p->R1);
+  w.code2 = take(4 * 2 * (size_t)p->R2);
+  w.len1 = take(2 * (size_t)p->R1);
+  w.len2 = take(2 * (size_t)p->R2);
+  w.Q = take(4 * (size_t)pv.n_v);
+  w.q1 = take(4 * (size_t)pv.n_g);
+  w.sym1 = take(2 * (size_t)pv.n_g);
+  w.sym2 = take(2 * (size_t)pv.n_v);
+  w.val1 = take(4 * (size_t)pv.n_g);
+  w.val2 = take(4 * (size_t)pv.n_v);
+  w.gw = take(4 * (size_t)(ng1 + ng2));
+  w.ge = take(4 * (size_t)(ng1 + ng2));
+  w.gr = take(4 * (size_t)(ng1 + ng2));
+  w.total = o;
+  return w;
+}
+
+mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_params *p,
+                           unsigned char *ws, unsigned char *out, size_t capacity,
+                           cudaStream_t stream) {
+  const CompressWs W = compress_ws_layout(pv, p);
+  Status *st = (Status *)ws;
+  const int64_t n_v = pv.n_v, n_g = pv.n_g;
+  const int64_t ng1 = ngroups(n_g, p->C1), ng2 = ngroups(n_v, p->C2);
+  const int nsym1 = 2 * p->R1, nsym2 = 2 * p->R2;
+  const Layout F = make_layout(p->R1, p->R2, ng1, ng2, 0, 0, 0, 8, 0, 0);
+  if (capacity < F.out1) return MCC_ERR_CAPACITY;
+  unsigned int *hist1 = (unsigned int *)(ws + W.hist1), *hist2 = (unsigned int *)(ws + W.hist2);
+  int *Q = (int *)(ws + W.Q), *q1 = (int *)(ws + W.q1);
+  unsigned short *sym1 = (unsigned short *)(ws + W.sym1), *sym2 = (unsigned short *)(ws + W.sym2);
+  int *val1 = (int *)(ws + W.val1), *val2 = (int *)(ws + W.val2);
+  const int sms = num_sms();
+
+  if (cudaMemsetAsync(ws, 0, kStatusBytes, stream) != cudaSuccess) return MCC_ERR_CUDA;
+  // hist1 and hist2 are adjacent: zeroed together by k_reduce
+  const int nhist = (int)((W.hist2 - W.hist1) / 4 + nsym2);
+  RParams rp{p->dtype, p->eb_mode, p->eb, p->grid_fraction};
+  const unsigned int rblocks = (unsigned int)sms * 4;
+  if (p->dtype == MCC_F64) {
+    {
+      PROF_SCOPE("k_reduce", stream);
+      k_reduce<double><<<rblocks, 256, 0, stream>>>((const double *)d_values, n_v, st, rp, hist1, nhist);
+    }
+    {
+      PROF_SCOPE("k_prequant", stream);
+      k_prequant<double><<<(unsigned int)sms * 8, 256, 0, stream>>>((const double *)d_values, n_v, st, Q);
+    }
+  } else {
+    {
+      PROF_SCOPE("k_reduce", stream);
+      k_reduce<float><<<rblocks, 256, 0, stream>>>((const float *)d_values, n_v, st, rp, hist1, nhist);
+    }
+    {
+      PROF_SCOPE("k_prequant", stream);
+      k_prequant<float><<<(unsigned int)sms * 8, 256, 0, stream>>>((const float *)d_values, n_v, st, Q);
+    }
+  }
+  const size_t hsm1 = 4 * (size_t)nsym1, hsm2 = 4 * (size_t)nsym2;
+  if (pv.dim == 2) {
+    dim3 grid((pv.nx + 63) / 64, (pv.ny + 15) / 16);
+    {
+      PROF_SCOPE("k_grid2d", stream);
+      k_grid2d<64, 16><<<grid, 256, hsm1, stream>>>(pv, Q, st, p->R1, q1, sym1, val1, hist1);
+    }
+  } else {
+    dim3 grid((pv.nx + 31) / 32, (pv.ny + 7) / 8, (pv.nz + 7) / 8);
+    {
+      PROF_SCOPE("k_grid3d", stream);
+      k_grid3d<32, 8, 8><<<grid, 256, hsm1, stream>>>(pv, Q, st, p->R1, q1, sym1, val1, hist1);
+    }
+  }
+  const unsigned int nblocks_node = (unsigned int)sms * 8;
+  if (pv.dim == 2) {
+    if (p->dtype == MCC_F64)
+      {
+        PROF_SCOPE("k_node", stream);
+        k_node<2, double><<<nblocks_node, 256, hsm2, stream>>>(pv, (const double *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
+      }
+    else
+      {
+        PROF_SCOPE("k_node", stream);
+        k_node<2, float><<<nblocks_node, 256, hsm2, stream>>>(pv, (const float *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
+      }
+  } else {
+    if (p->dtype == MCC_F64)
+      {
+        PROF_SCOPE("k_node", stream);
+        k_node<3, double><<<nblocks_node, 256, hsm2, stream>>>(pv, (const double *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
+      }
+    else
+      {
+        PROF_SCOPE("k_node", stream);
+        k_node<3, float><<<nblocks_node, 256, hsm2, stream>>>(pv, (const float *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
+      }
+  }
+  CodebookArgs a1{hist1, nsym1, (unsigned int *)(ws + W.code1), ws + W.len1, out + F.lens1};
+  CodebookArgs a2{hist2, nsym2, (unsigned int *)(ws + W.code2), ws + W.len2, out + F.lens2};
+  const size_t cbsm = codebook_smem(nsym1 > nsym2 ? nsym1 : nsym2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  {
+    PROF_SCOPE("k_codebook", stream);
+    k_codebook<<<2, 1024, cbsm, stream>>>(a1, a2, p->lmax, st);
+  }
+  GroupArgs ga{sym1, sym2, ws + W.len1, ws + W.len2, n_g, n_v, ng1, ng2, p->C1, p->C2, nsym1, nsym2,
+               (unsigned short *)(out + F.ltab1), (unsigned short *)(out + F.ltab2),
+               (unsigned int *)(ws + W.gw), (unsigned int *)(ws + W.ge), (unsigned int *)(ws + W.gr)};
+  {
+    PROF_SCOPE("k_group_len", stream);
+    k_group_len<<<nblk(ng1 + ng2, 8), 256, 0, stream>>>(ga, st);
+  }
+  ScanArgs sa{(const unsigned int *)(ws + W.gw), (const unsigned int *)(ws + W.ge),
+              (const unsigned int *)(ws + W.gr), ng1, ng2, out, capacity, F, p->dtype, pv.dim,
+              p->R1, p->R2, p->C1, p->C2, p->lmax, pv.nx, pv.ny, pv.nz, n_v, n_g};
+  {
+    PROF_SCOPE("k_scan", stream);
+    k_scan<<<1, 1024, 0, stream>>>(sa, st);
+  }
+  const int cmax = p->C1 > p->C2 ? p->C1 : p->C2;
+  const int wpw = cmax * p->lmax;  // worst-case words of one group
+  PackArgs pa{sym1, sym2, (const unsigned int *)(ws + W.code1), (const unsigned int *)(ws + W.code2),
+              ws + W.len1, ws + W.len2, val1, val2, d_values, n_g, n_v, ng1, ng2, p->C1, p->C2,
+              nsym1, nsym2, p->dtype == MCC_F64 ? 8 : 4, out, wpw};
+  {
+    PROF_SCOPE("k_pack", stream);
+    k_pack<<<nblk(ng1 + ng2, 4), 128, 4 * (size_t)wpw * 4, stream>>>(pa, st);
+  }
+  if (cudaGetLastError() != cudaSuccess) return MCC_ERR_CUDA;
+  return MCC_OK;
+}

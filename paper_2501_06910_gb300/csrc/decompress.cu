@@ -1,0 +1,537 @@
+// decompress.cu -- Algorithm 4 of Gong et al. (multi-component
+// reconstruction): x1' = D(mu1), x2' = D(mu2), x' = g(x1') + x2'.
+//
+//   k_dec_prep    validate the header and the group tables' ends, build the
+//                 canonical decode tables of both components (one CTA each)
+//   k_dec_grid    Huffman decode of the grid symbols (one warp per group of
+//                 32 lane chunks), escapes, Lorenzo differences
+//   k_scan_rows / k_scan_axis
+//                 inverse Lorenzo: inclusive prefix sums along x, y (, z)
+//   k_dec_res     Huffman decode of the residual symbols fused with the
+//                 reconstruction x' = s2 (K + P + q2), P = round(rho12 g(q1))
+//
+// Every read of the stream is bounds-checked against the validated layout; a
+// corrupt stream records MCC_ERR_CORRUPT and the affected warp stops.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "workspace.cuh"
+#include "prof.cuh"
+
+using namespace mcc;
+
+namespace {
+
+__device__ __forceinline__ uint32_t ld32(const unsigned char *p) { return *(const uint32_t *)p; }
+__device__ __forceinline__ uint64_t ld64(const unsigned char *p) {
+  return (uint64_t)ld32(p) | ((uint64_t)ld32(p + 4) << 32);
+}
+
+__device__ __forceinline__ bool block_failed(const Status *st) {
+  __shared__ int failed;
+  if (threadIdx.x == 0) failed = *(volatile const unsigned int *)&st->err != 0;
+  __syncthreads();
+  return failed != 0;
+}
+
+// ---------------------------------------------------------------------------
+// k_dec_prep
+// ---------------------------------------------------------------------------
+struct PrepArgs {
+  const unsigned char *in;
+  uint64_t in_bytes;
+  int dtype;  // the caller's output type; the stream must match
+  int dim, nx, ny, nz;
+  int64_t n_v, n_g;
+  DecInfo *info;
+  DecTab *tab1, *tab2;
+};
+
+__device__ bool parse_header(const PrepArgs &a, DecInfo &I) {
+  const unsigned char *h = a.in;
+  if (a.in_bytes < kHeaderBytes) return false;
+  if (ld32(h + H_MAGIC) != kMagic || ld32(h + H_VERSION) != kVersion ||
+      ld32(h + H_HBYTES) != kHeaderBytes)
+    return false;
+  I.dtype = (int)ld32(h + H_DTYPE);
+  I.dim = (int)ld32(h + H_DIM);
+  if (I.dtype != a.dtype) return false;
+  if (I.dim != a.dim || (int)ld32(h + H_NX) != a.nx || (int)ld32(h + H_NY) != a.ny ||
+      (int)ld32(h + H_NZ) != a.nz)
+    return false;
+  if ((int64_t)ld64(h + H_NV) != a.n_v || (int64_t)ld64(h + H_NG) != a.n_g) return false;
+  I.R1 = (int)ld32(h + H_R1);
+  I.R2 = (int)ld32(h + H_R2);
+  I.C1 = (int)ld32(h + H_C1);
+  I.C2 = (int)ld32(h + H_C2);
+  I.lmax = (int)ld32(h + H_LMAX);
+  if (I.R1 < 4 || I.R1 > kMaxR || I.R2 < 4 || I.R2 > kMaxR) return false;
+  if (I.C1 < 1 || I.C1 > kMaxC || I.C2 < 1 || I.C2 > kMaxC) return false;
+  if (I.lmax < 1 || I.lmax > kMaxLen) return false;
+  I.s2 = __longlong_as_double((long long)ld64(h + H_S2));
+  if (!(I.s2 > 0.0) || !isfinite(I.s2)) return false;
+  I.K = (long long)ld64(h + H_K);
+  if (I.K <= -(1ll << 62) || I.K >= (1ll << 62)) return false;
+  I.rho12_q = (long long)ld64(h + H_RHO12);
+  if (!(I.rho12_q >= 1 && I.rho12_q < (1ll << 50))) return false;
+  I.rho12_f = __fmul_rn(__ll2float_rn(I.rho12_q), 0x1p-40f);
+  I.nout1 = ld64(h + H_NOUT1);
+  I.nout2 = ld64(h + H_NOUT2);
+  I.nraw = ld64(h + H_NRAW);
+  I.w1 = ld64(h + H_W1);
+  I.w2 = ld64(h + H_W2);
+  if (I.nout1 > (uint64_t)a.n_g || I.nout2 > (uint64_t)a.n_v || I.nraw > (uint64_t)a.n_v) return false;
+  I.ng1 = ngroups(a.n_g, I.C1);
+  I.ng2 = ngroups(a.n_v, I.C2);
+  if (I.w1 > (uint64_t)a.n_g * kMaxLen / 32 + I.ng1 + 1 ||
+      I.w2 > (uint64_t)a.n_v * kMaxLen / 32 + I.ng2 + 1)
+    return false;
+  const uint64_t vsz = I.dtype == MCC_F64 ? 8 : 4;
+  I.L = make_layout(I.R1, I.R2, I.ng1, I.ng2, I.nout1, I.nout2, I.nraw, vsz, I.w1, I.w2);
+  if (I.L.total != ld64(h + H_TOTAL) || I.L.total > a.in_bytes) return false;
+  const unsigned char *in = a.in;
+  if (ld32(in + I.L.gtab1) != 0 || ld32(in + I.L.gtab1 + 4 * I.ng1) != I.w1) return false;
+  if (ld32(in + I.L.gtab2) != 0 || ld32(in + I.L.gtab2 + 4 * I.ng2) != I.w2) return false;
+  if (ld32(in + I.L.etab1) != 0 || ld32(in + I.L.etab1 + 4 * I.ng1) != I.nout1) return false;
+  if (ld32(in + I.L.etab2) != 0 || ld32(in + I.L.etab2 + 4 * I.ng2) != I.nout2) return false;
+  if (ld32(in + I.L.rtab2) != 0 || ld32(in + I.L.rtab2 + 4 * I.ng2) != I.nraw) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_dec_prep(PrepArgs a, Status *st) {
+  __shared__ DecInfo I;
+  __shared__ int ok;
+  __shared__ unsigned char lens[2 * kMaxR];
+  __shared__ unsigned short rank[2 * kMaxR];
+  __shared__ unsigned int wcount[32][kMaxLen + 1];
+  __shared__ CanonTables ct;
+  __shared__ int bad;
+  if (threadIdx.x == 0) {
+    ok = parse_header(a, I) ? 1 : 0;
+    bad = 0;
+    if (!ok) set_error(st, MCC_ERR_CORRUPT);
+    else if (blockIdx.x == 0) *a.info = I;
+  }
+  __syncthreads();
+  if (!ok) return;
+  const int nsym = blockIdx.x == 0 ? 2 * I.R1 : 2 * I.R2;
+  const unsigned char *src = a.in + (blockIdx.x == 0 ? I.L.lens1 : I.L.lens2);
+  DecTab *T = blockIdx.x == 0 ? a.tab1 : a.tab2;
+  for (int s = threadIdx.x; s < nsym; s += blockDim.x) {
+    lens[s] = src[s];
+    if (lens[s] > I.lmax) bad = 1;
+  }
+  __syncthreads();
+  if (bad) { if (threadIdx.x == 0) set_error(st, MCC_ERR_CORRUPT); return; }
+  canonical_tables(lens, nsym, &ct);
+  if (threadIdx.x == 0) {
+    unsigned long long kraft = 0;
+    for (int l = 1; l <= kMaxLen; l++) kraft += (unsigned long long)ct.count[l] << (kMaxLen - l);
+    if (kraft > (1ull << kMaxLen)) bad = 1;
+  }
+  __syncthreads();
+  if (bad) { if (threadIdx.x == 0) set_error(st, MCC_ERR_CORRUPT); return; }
+  canonical_ranks(lens, nsym, rank, wcount);
+  for (int s = threadIdx.x; s < nsym; s += blockDim.x)
+    if (lens[s]) T->sorted[ct.offset[lens[s]] + rank[s]] = (unsigned short)s;
+  if (threadIdx.x <= kMaxLen + 1) {
+    T->first[threadIdx.x] = ct.first[threadIdx.x];
+    T->count[threadIdx.x] = ct.count[threadIdx.x];
+    T->offset[threadIdx.x] = ct.offset[threadIdx.x];
+  }
+  __syncthreads();
+  const int lb = I.lmax < kLutBits ? I.lmax : kLutBits;
+  for (int e = threadIdx.x; e < (1 << kLutBits); e += blockDim.x) {
+    unsigned int v = 0;
+    for (int l = 1; l <= lb; l++) {
+      const unsigned int c = (unsigned int)e >> (kLutBits - l);
+      if (c - ct.first[l] < ct.count[l]) {
+        v = ((unsigned int)T->sorted[ct.offset[l] + c - ct.first[l]] << 8) | (unsigned int)l;
+        break;
+      }
+    }
+    T->lut[e] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// bit reader over one component's words (reads past the section give zeros)
+// ---------------------------------------------------------------------------
+struct BitReader {
+  const unsigned int *w;
+  unsigned long long nwords;
+  unsigned long long buf;  // left aligned
+  int nb;                  // valid bits in buf
+  unsigned long long wi;   // next word
+  unsigned long long consumed;
+
+  __device__ __forceinline__ unsigned int word(unsigned long long i) const {
+    return i < nwords ? __ldg(w + i) : 0u;
+  }
+  __device__ __forceinline__ void init(const unsigned int *words, unsigned long long n,
+                                       unsigned long long bit) {
+    w = words;
+    nwords = n;
+    wi = bit >> 5;
+    buf = ((unsigned long long)word(wi) << 32) | word(wi + 1);
+    wi += 2;
+    const int sk = (int)(bit & 31);
+    buf <<= sk;
+    nb = 64 - sk;
+    consumed = 0;
+  }
+  __device__ __forceinline__ void refill() {
+    if (nb < 32) {
+      buf |= (unsigned long long)word(wi) << (32 - nb);
+      wi++;
+      nb += 32;
+    }
+  }
+};
+
+// Decode one symbol; returns -1 for an invalid code.
+__device__ __forceinline__ int decode_one(BitReader &r, const DecTab &T, int lmax) {
+  r.refill();
+  const unsigned int win = (unsigned int)(r.buf >> 32);
+  const unsigned int e = T.lut[win >> (32 - kLutBits)];
+  int len = (int)(e & 0xFF), sym;
+  if (len) {
+    sym = (int)(e >> 8);
+  } else {
+    sym = -1;
+    for (int l = kLutBits + 1; l <= lmax; l++) {
+      const unsigned int c = win >> (32 - l);
+      if (c - T.first[l] < T.count[l]) {
+        sym = T.sorted[T.offset[l] + c - T.first[l]];
+        len = l;
+        break;
+      }
+    }
+    if (sym < 0) return -1;
+  }
+  r.buf <<= len;
+  r.nb -= len;
+  r.consumed += (unsigned int)len;
+  return sym;
+}
+
+__device__ __forceinline__ void load_tab(DecTab *dst, const DecTab *src, int nsym) {
+  for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) dst->lut[i] = src->lut[i];
+  for (int i = threadIdx.x; i < kMaxLen + 2; i += blockDim.x) {
+    dst->first[i] = src->first[i];
+    dst->count[i] = src->count[i];
+    dst->offset[i] = src->offset[i];
+  }
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x) dst->sorted[i] = src->sorted[i];
+}
+
+// Per-warp group set-up shared by both decoders: validates the group's table
+// entries and positions every lane's reader. Returns false when corrupt.
+__device__ __forceinline__ bool group_setup(const unsigned char *in, uint64_t gtab_off,
+                                           uint64_t etab_off, uint64_t ltab_off, uint64_t bits_off,
+                                           unsigned long long words, unsigned long long nesc,
+                                           int64_t g, BitReader &r, unsigned int &lane_bits,
+                                           unsigned int &e0, unsigned int &e1) {
+  const int lane = threadIdx.x & 31;
+  const unsigned int w0 = ld32(in + gtab_off + 4 * g), w1 = ld32(in + gtab_off + 4 * (g + 1));
+  e0 = ld32(in + etab_off + 4 * g);
+  e1 = ld32(in + etab_off + 4 * (g + 1));
+  lane_bits = *(const unsigned short *)(in + ltab_off + 2 * (g * 32 + lane));
+  unsigned int incl = lane_bits;
+  for (int s = 1; s < 32; s <<= 1) {
+    const unsigned int t = __shfl_up_sync(0xffffffffu, incl, s);
+    if (lane >= s) incl += t;
+  }
+  const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+  const bool ok = w0 <= w1 && w1 <= words && e0 <= e1 && e1 <= nesc &&
+                  (unsigned long long)total <= 32ull * (w1 - w0);
+  r.init((const unsigned int *)(in + bits_off), words, 32ull * w0 + (incl - lane_bits));
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// k_dec_grid: grid symbols -> Lorenzo differences (with escapes)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_dec_grid(const unsigned char *__restrict__ in,
+                                                  const DecInfo *__restrict__ info,
+                                                  const DecTab *__restrict__ tab, int64_t n_g,
+                                                  int *__restrict__ delta, Status *st) {
+  __shared__ DecTab T;
+  if (block_failed(st)) return;
+  const DecInfo I = *info;
+  load_tab(&T, tab, 2 * I.R1);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < I.ng1;
+       g += wstride) {
+    BitReader r;
+    unsigned int lane_bits, e0, e1;
+    const bool ok = group_setup(in, I.L.gtab1, I.L.etab1, I.L.ltab1, I.L.bits1, I.w1, I.nout1, g,
+                                r, lane_bits, e0, e1);
+    if (!ok) {
+      if (lane == 0) set_error(st, MCC_ERR_CORRUPT);
+      return;
+    }
+    const int C = I.C1, R1 = I.R1, rawsym = 2 * I.R1 - 1;
+    const int *outv = (const int *)(in + I.L.out1);
+    const unsigned lt = (1u << lane) - 1;
+    unsigned int e_run = e0;
+    bool lane_bad = false;
+    for (int k = 0; k < C; k++) {
+      const int64_t p0 = g * 32 * (int64_t)C + 32 * (int64_t)k;
+      if (p0 >= n_g) break;
+      const int64_t p = p0 + lane;
+      const bool valid = p < n_g;
+      int sym = -2;
+      if (valid && !lane_bad) {
+        sym = decode_one(r, T, I.lmax);
+        if (sym < 0 || sym == rawsym) lane_bad = true;
+      }
+      const bool esc = valid && !lane_bad && sym == 0;
+      const unsigned em = __ballot_sync(0xffffffffu, esc);
+      int d = 0;
+      if (esc) {
+        const unsigned int idx = e_run + __popc(em & lt);
+        if (idx < e1) d = __ldg(outv + idx);
+        else lane_bad = true;
+      } else if (valid && !lane_bad) {
+        d = sym - R1;
+      }
+      e_run += __popc(em);
+      if (valid) delta[p] = d;
+    }
+    if (lane_bad || r.consumed != lane_bits) lane_bad = true;
+    if (__any_sync(0xffffffffu, lane_bad) || e_run != e1) {
+      if (lane == 0) set_error(st, MCC_ERR_CORRUPT);
+      return;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// inverse Lorenzo: inclusive prefix sums (wrapping int32 arithmetic)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_scan_rows(int *q, int nx, int64_t nrows, const Status *st) {
+  if (*(volatile const unsigned int *)&st->err) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= nrows) return;
+  int *r = q + row * nx;
+  unsigned int carry = 0;
+  for (int base = 0; base < nx; base += 32) {
+    const int i = base + lane;
+    unsigned int v = i < nx ? (unsigned int)r[i] : 0u;
+    for (int s = 1; s < 32; s <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, v, s);
+      if (lane >= s) v += t;
+    }
+    v += carry;
+    if (i < nx) r[i] = (int)v;
+    carry = __shfl_sync(0xffffffffu, v, 31);
+  }
+}
+
+// Inclusive scan along an axis of length L and stride S, for columns
+// base = outer * plane + inner (inner < n_inner contiguous). Block: 32
+// consecutive columns x 8 warps, each warp scanning one segment of the axis.
+__global__ void __launch_bounds__(256) k_scan_axis(int *q, int64_t n_inner, int64_t n_outer,
+                                                   int64_t plane, int L, int64_t S, const Status *st) {
+  __shared__ unsigned int part[8][33];
+  if (*(volatile const unsigned int *)&st->err) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t nblk_inner = (n_inner + 31) / 32;
+  const int64_t outer = blockIdx.x / nblk_inner;
+  const int64_t inner = (blockIdx.x % nblk_inner) * 32 + lane;
+  const bool valid = inner < n_inner && outer < n_outer;
+  int *col = q + outer * plane + inner;
+  const int seg = (L + 7) / 8;
+  const int t0 = w * seg, t1 = min(L, t0 + seg);
+  unsigned int sum = 0;
+  if (valid)
+    for (int t = t0; t < t1; t++) sum += (unsigned int)col[(int64_t)t * S];
+  part[w][lane] = sum;
+  __syncthreads();
+  unsigned int pre = 0;
+  for (int k = 0; k < w; k++) pre += part[k][lane];
+  if (valid)
+    for (int t = t0; t < t1; t++) {
+      pre += (unsigned int)col[(int64_t)t * S];
+      col[(int64_t)t * S] = (int)pre;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_dec_res: residual symbols -> x' at every vertex
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_dec_res(const unsigned char *__restrict__ in,
+                                                 const DecInfo *__restrict__ info,
+                                                 const DecTab *__restrict__ tab, PlanView pv,
+                                                 const int *__restrict__ q1, T *__restrict__ xo,
+                                                 Status *st) {
+  __shared__ DecTab Tb;
+  if (block_failed(st)) return;
+  const DecInfo I = *info;
+  load_tab(&Tb, tab, 2 * I.R2);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t n = pv.n_v;
+  const int C = I.C2, R2 = I.R2, rawsym = 2 * I.R2 - 1;
+  const int *outv = (const int *)(in + I.L.out2);
+  const T *rawv = (const T *)(in + I.L.raw);
+  const int nx = pv.nx;
+  const int64_t sxy = (int64_t)pv.nx * pv.ny;
+  const unsigned lt = (1u << lane) - 1;
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < I.ng2;
+       g += wstride) {
+    BitReader r;
+    unsigned int lane_bits, e0, e1;
+    bool ok = group_setup(in, I.L.gtab2, I.L.etab2, I.L.ltab2, I.L.bits2, I.w2, I.nout2, g, r,
+                          lane_bits, e0, e1);
+    const unsigned int r0 = ld32(in + I.L.rtab2 + 4 * g), r1 = ld32(in + I.L.rtab2 + 4 * (g + 1));
+    ok = ok && r0 <= r1 && r1 <= I.nraw;
+    if (!ok) {
+      if (lane == 0) set_error(st, MCC_ERR_CORRUPT);
+      return;
+    }
+    unsigned int e_run = e0, r_run = r0;
+    bool lane_bad = false;
+    for (int k = 0; k < C; k++) {
+      const int64_t p0 = g * 32 * (int64_t)C + 32 * (int64_t)k;
+      if (p0 >= n) break;
+      const int64_t p = p0 + lane;
+      const bool valid = p < n;
+      int sym = -2;
+      if (valid && !lane_bad) {
+        sym = decode_one(r, Tb, I.lmax);
+        if (sym < 0) lane_bad = true;
+      }
+      const bool ok_sym = valid && !lane_bad;
+      const bool esc = ok_sym && sym == 0;
+      const bool raw = ok_sym && sym == rawsym;
+      const unsigned em = __ballot_sync(0xffffffffu, esc);
+      const unsigned rm = __ballot_sync(0xffffffffu, raw);
+      long long q2 = 0;
+      T out = (T)0;
+      if (raw) {
+        const unsigned int idx = r_run + __popc(rm & lt);
+        if (idx < r1) out = rawv[idx];
+        else lane_bad = true;
+      } else if (ok_sym) {
+        if (esc) {
+          const unsigned int idx = e_run + __popc(em & lt);
+          if (idx < e1) q2 = __ldg(outv + idx);
+          else lane_bad = true;
+        } else {
+          q2 = sym - R2;
+        }
+        const uint32_t c = __ldg(pv.cell + p);
+        const float fx = __fmul_rn(__uint2float_rn(__ldg(pv.frac + p)), 0x1p-15f);
+        const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + p)), 0x1p-15f);
+        const float fz = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + p)), 0x1p-15f) : 0.0f;
+        const long long P = predict_vertex<DIM>(q1, c, fx, fy, fz, nx, sxy, I.rho12_q, I.rho12_f);
+        const double xr = __dmul_rn(I.s2, (double)(I.K + P + q2));
+        out = (T)xr;
+      }
+      e_run += __popc(em);
+      r_run += __popc(rm);
+      if (valid) xo[p] = out;
+    }
+    if (lane_bad || r.consumed != lane_bits) lane_bad = true;
+    if (__any_sync(0xffffffffu, lane_bad) || e_run != e1 || r_run != r1) {
+      if (lane == 0) set_error(st, MCC_ERR_CORRUPT);
+      return;
+    }
+  }
+}
+
+inline unsigned int nblk(int64_t n, int bs) {
+  const int64_t b = (n + bs - 1) / bs;
+  return (unsigned int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+DecompressWs decompress_ws_layout(const PlanView &pv) {
+  DecompressWs w;
+  size_t o = kStatusBytes;
+  auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+  w.info = take(sizeof(DecInfo));
+  w.tab1 = take(sizeof(DecTab));
+  w.tab2 = take(sizeof(DecTab));
+  w.q1 = take(4 * (size_t)pv.n_g);
+  w.total = o;
+  return w;
+}
+
+mcc_status launch_decompress(const PlanView &pv, const unsigned char *in, size_t in_bytes,
+                             void *d_values, int dtype, unsigned char *ws, cudaStream_t stream) {
+  const DecompressWs W = decompress_ws_layout(pv);
+  Status *st = (Status *)ws;
+  DecInfo *info = (DecInfo *)(ws + W.info);
+  DecTab *tab1 = (DecTab *)(ws + W.tab1), *tab2 = (DecTab *)(ws + W.tab2);
+  int *q1 = (int *)(ws + W.q1);
+  if (cudaMemsetAsync(ws, 0, kStatusBytes, stream) != cudaSuccess) return MCC_ERR_CUDA;
+  PrepArgs pa{in, in_bytes, dtype, pv.dim, pv.nx, pv.ny, pv.nz, pv.n_v, pv.n_g, info, tab1, tab2};
+  {
+    PROF_SCOPE("k_dec_prep", stream);
+    k_dec_prep<<<2, 256, 0, stream>>>(pa, st);
+  }
+  // group counts are bounded by the smallest chunk size: launch for C = 1 and
+  // let warps beyond the stream's group count exit
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t max_g1 = ngroups(pv.n_g, 1), max_g2 = ngroups(pv.n_v, 1);
+  const unsigned int cap = (unsigned int)sms * 4;  // resident blocks; warps stride over groups
+  const unsigned int gb1 = nblk(max_g1, 8) < cap ? nblk(max_g1, 8) : cap;
+  {
+    PROF_SCOPE("k_dec_grid", stream);
+    k_dec_grid<<<gb1, 256, 0, stream>>>(in, info, tab1, pv.n_g, q1, st);
+  }
+  const int64_t nrows = (int64_t)pv.ny * pv.nz;
+  {
+    PROF_SCOPE("k_scan_rows", stream);
+    k_scan_rows<<<nblk(nrows, 8), 256, 0, stream>>>(q1, pv.nx, nrows, st);
+  }
+  {  // y: columns (x, z), stride nx
+    const int64_t blocks = (pv.nx + 31) / 32 * (int64_t)pv.nz;
+    {
+      PROF_SCOPE("k_scan_axis", stream);
+      k_scan_axis<<<(unsigned int)blocks, 256, 0, stream>>>(q1, pv.nx, pv.nz, (int64_t)pv.nx * pv.ny,
+                                                           pv.ny, pv.nx, st);
+    }
+  }
+  if (pv.dim == 3) {  // z: columns (x, y), stride nx ny
+    const int64_t ninner = (int64_t)pv.nx * pv.ny;
+    {
+      PROF_SCOPE("k_scan_axis", stream);
+      k_scan_axis<<<(unsigned int)((ninner + 31) / 32), 256, 0, stream>>>(q1, ninner, 1, 0, pv.nz, ninner, st);
+    }
+  }
+  const unsigned int rb = nblk(max_g2, 8) < cap ? nblk(max_g2, 8) : cap;
+  if (pv.dim == 2) {
+    if (dtype == MCC_F64) {
+      PROF_SCOPE("k_dec_res", stream);
+      k_dec_res<2, double><<<rb, 256, 0, stream>>>(in, info, tab2, pv, q1, (double *)d_values, st);
+    }
+    else {
+      PROF_SCOPE("k_dec_res", stream);
+      k_dec_res<2, float><<<rb, 256, 0, stream>>>(in, info, tab2, pv, q1, (float *)d_values, st);
+    }
+  } else {
+    if (dtype == MCC_F64) {
+      PROF_SCOPE("k_dec_res", stream);
+      k_dec_res<3, double><<<rb, 256, 0, stream>>>(in, info, tab2, pv, q1, (double *)d_values, st);
+    }
+    else {
+      PROF_SCOPE("k_dec_res", stream);
+      k_dec_res<3, float><<<rb, 256, 0, stream>>>(in, info, tab2, pv, q1, (float *)d_values, st);
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) return MCC_ERR_CUDA;
+  return MCC_OK;
+}

@@ -1,0 +1,470 @@
+// plan.cu -- mesh -> grid mapping, built once per mesh and reused for every
+// field (Gong et al., Sec. IV-B: "the mesh-grid mapping can be pre-computed";
+// Sec. IV-C grid construction; excluded from the ratio, Sec. IV-A).
+//
+// Per grid point j: the minimum-id simplex that contains it (FP32 pre-filter,
+// then the FP64 barycentric test with tolerance 1e-12) and its barycentric
+// weights, stored as vertex ids + u16 weights of vertices 1..dim (the weight
+// of vertex 0 is implied). Points in no simplex take the value zero (the
+// hollow regions of Fig. 1). Per vertex: the lower corner of its grid cell and
+// its local coordinates (u16, 2^-15 units).
+//
+// Point location rasterises every simplex over the grid points of its
+// bounding box (thread per simplex) and keeps the minimum id with atomicMin,
+// so the result does not depend on scheduling.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cmath>
+#include <new>
+
+#include "common.cuh"
+
+using namespace mcc;
+
+struct mcc_plan_s {
+  int dim;
+  int32_t n[3];
+  double lo[3], h[3], inv_h[3];
+  int64_t n_v, n_g, n_outside;
+  int32_t *vid;
+  uint16_t *lam;
+  uint32_t *cell;
+  uint16_t *frac;
+};
+
+namespace {
+
+constexpr double kTol64 = 1e-12;
+constexpr float kTol32 = 0.05f;
+constexpr float kMargin32 = 0.01f;
+
+struct GridDev {
+  int dim;
+  int32_t n[3];
+  double lo[3], h[3], inv_h[3];
+  float hf[3];
+};
+
+// ---- barycentric coordinates (same operation order as the definition) ----
+__device__ __forceinline__ void bary2_f(const float *a, const float *b, const float *c,
+                                        const float *p, float *lam, float &den) {
+  const float v0x = __fsub_rn(b[0], a[0]), v0y = __fsub_rn(b[1], a[1]);
+  const float v1x = __fsub_rn(c[0], a[0]), v1y = __fsub_rn(c[1], a[1]);
+  const float v2x = __fsub_rn(p[0], a[0]), v2y = __fsub_rn(p[1], a[1]);
+  const float t1 = __fmul_rn(v0x, v1y), t2 = __fmul_rn(v1x, v0y);
+  den = __fsub_rn(t1, t2);
+  const float nb1 = __fmul_rn(v2x, v1y), nb2 = __fmul_rn(v1x, v2y);
+  const float nc1 = __fmul_rn(v0x, v2y), nc2 = __fmul_rn(v2x, v0y);
+  const float lb = __fdiv_rn(__fsub_rn(nb1, nb2), den);
+  const float lc = __fdiv_rn(__fsub_rn(nc1, nc2), den);
+  lam[0] = __fsub_rn(__fsub_rn(1.0f, lb), lc);
+  lam[1] = lb;
+  lam[2] = lc;
+}
+
+__device__ __forceinline__ void bary2_d(const double *a, const double *b, const double *c,
+                                        const double *p, double *lam, double &den) {
+  const double v0x = __dsub_rn(b[0], a[0]), v0y = __dsub_rn(b[1], a[1]);
+  const double v1x = __dsub_rn(c[0], a[0]), v1y = __dsub_rn(c[1], a[1]);
+  const double v2x = __dsub_rn(p[0], a[0]), v2y = __dsub_rn(p[1], a[1]);
+  const double t1 = __dmul_rn(v0x, v1y), t2 = __dmul_rn(v1x, v0y);
+  den = __dsub_rn(t1, t2);
+  const double nb1 = __dmul_rn(v2x, v1y), nb2 = __dmul_rn(v1x, v2y);
+  const double nc1 = __dmul_rn(v0x, v2y), nc2 = __dmul_rn(v2x, v0y);
+  const double lb = __ddiv_rn(__dsub_rn(nb1, nb2), den);
+  const double lc = __ddiv_rn(__dsub_rn(nc1, nc2), den);
+  lam[0] = __dsub_rn(__dsub_rn(1.0, lb), lc);
+  lam[1] = lb;
+  lam[2] = lc;
+}
+
+template <typename T>
+struct Ar;
+template <>
+struct Ar<float> {
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+};
+template <>
+struct Ar<double> {
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+};
+
+template <typename T>
+__device__ __forceinline__ void cross3(T ux, T uy, T uz, T wx, T wy, T wz, T &rx, T &ry, T &rz) {
+  using A = Ar<T>;
+  rx = A::sub(A::mul(uy, wz), A::mul(uz, wy));
+  ry = A::sub(A::mul(uz, wx), A::mul(ux, wz));
+  rz = A::sub(A::mul(ux, wy), A::mul(uy, wx));
+}
+template <typename T>
+__device__ __forceinline__ T dot3(T ux, T uy, T uz, T wx, T wy, T wz) {
+  using A = Ar<T>;
+  return A::add(A::add(A::mul(ux, wx), A::mul(uy, wy)), A::mul(uz, wz));
+}
+
+template <typename T>
+__device__ __forceinline__ void bary3(const T *A_, const T *B, const T *C, const T *D, const T *P,
+                                      T *lam, T &den) {
+  using A = Ar<T>;
+  const T v0x = A::sub(B[0], A_[0]), v0y = A::sub(B[1], A_[1]), v0z = A::sub(B[2], A_[2]);
+  const T v1x = A::sub(C[0], A_[0]), v1y = A::sub(C[1], A_[1]), v1z = A::sub(C[2], A_[2]);
+  const T v2x = A::sub(D[0], A_[0]), v2y = A::sub(D[1], A_[1]), v2z = A::sub(D[2], A_[2]);
+  const T vpx = A::sub(P[0], A_[0]), vpy = A::sub(P[1], A_[1]), vpz = A::sub(P[2], A_[2]);
+  T cx, cy, cz;
+  cross3<T>(v1x, v1y, v1z, v2x, v2y, v2z, cx, cy, cz);
+  den = dot3<T>(v0x, v0y, v0z, cx, cy, cz);
+  const T nb = dot3<T>(vpx, vpy, vpz, cx, cy, cz);
+  cross3<T>(vpx, vpy, vpz, v2x, v2y, v2z, cx, cy, cz);
+  const T nc = dot3<T>(v0x, v0y, v0z, cx, cy, cz);
+  cross3<T>(v1x, v1y, v1z, vpx, vpy, vpz, cx, cy, cz);
+  const T nd = dot3<T>(v0x, v0y, v0z, cx, cy, cz);
+  const T lb = A::div(nb, den), lc = A::div(nc, den), ld = A::div(nd, den);
+  lam[0] = A::sub(A::sub(A::sub((T)1, lb), lc), ld);
+  lam[1] = lb;
+  lam[2] = lc;
+  lam[3] = ld;
+}
+
+// FP32 pre-filter: 0 when the point is clearly outside the simplex.
+template <int DIM>
+__device__ __forceinline__ bool prefilter(const float (*vf)[3], const float *pf) {
+  float l[4], den;
+  if (DIM == 2) {
+    bary2_f(vf[0], vf[1], vf[2], pf, l, den);
+    if (den != 0.0f && (l[0] < -kTol32 || l[1] < -kTol32 || l[2] < -kTol32)) return false;
+  } else {
+    bary3<float>(vf[0], vf[1], vf[2], vf[3], pf, l, den);
+    if (den != 0.0f &&
+        (l[0] < -kTol32 || l[1] < -kTol32 || l[2] < -kTol32 || l[3] < -kTol32))
+      return false;
+  }
+  return true;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool inside64(const double (*V)[3], const double *P, double *lam) {
+  double den;
+  if (DIM == 2) {
+    bary2_d(V[0], V[1], V[2], P, lam, den);
+    if (den == 0.0) return false;
+    return lam[0] >= -kTol64 && lam[1] >= -kTol64 && lam[2] >= -kTol64;
+  }
+  bary3<double>(V[0], V[1], V[2], V[3], P, lam, den);
+  if (den == 0.0) return false;
+  return lam[0] >= -kTol64 && lam[1] >= -kTol64 && lam[2] >= -kTol64 && lam[3] >= -kTol64;
+}
+
+__device__ __forceinline__ uint16_t to_u16_unit(double v) {
+  if (!(v > 0.0)) return 0;
+  if (v >= 1.0) return 32768;
+  return (uint16_t)rint(__dmul_rn(v, 32768.0));
+}
+
+// ---- kernels ---------------------------------------------------------------
+__global__ void k_check_cells(const int32_t *cells, int64_t n, int64_t n_v, int *bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = cells[i];
+    if (v < 0 || v >= n_v) atomicExch(bad, 1);
+  }
+}
+
+__global__ void k_bbox(const double *coords, int64_t n_v, int dim, unsigned long long *keys) {
+  // keys[2d] = max of ~key (so ~result is the min key), keys[2d+1] = max key
+  unsigned long long mn[3] = {0, 0, 0}, mx[3] = {0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_v;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int d = 0; d < dim; d++) {
+      const unsigned long long k = order_key(coords[i * dim + d]);
+      mn[d] = max(mn[d], ~k);
+      mx[d] = max(mx[d], k);
+    }
+  for (int d = 0; d < dim; d++) {
+    for (int o = 16; o; o >>= 1) {
+      mn[d] = max(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+      mx[d] = max(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&keys[2 * d], mn[d]);
+      atomicMax(&keys[2 * d + 1], mx[d]);
+    }
+  }
+}
+
+// FP32 coordinates relative to the grid origin, 4 floats per vertex.
+__global__ void k_rel32(const double *coords, int64_t n_v, GridDev g, float4 *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_v;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float r[3] = {0.f, 0.f, 0.f};
+    for (int d = 0; d < g.dim; d++) r[d] = __double2float_rn(__dsub_rn(coords[i * g.dim + d], g.lo[d]));
+    out[i] = make_float4(r[0], r[1], r[2], 0.f);
+  }
+}
+
+template <int DIM>
+__global__ void k_raster(const double *__restrict__ coords, const int32_t *__restrict__ cells,
+                         int64_t n_c, const float4 *__restrict__ rel, GridDev g,
+                         unsigned int *owner) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_c) return;
+  int32_t v[DIM + 1];
+  float vf[4][3];
+  for (int k = 0; k <= DIM; k++) {
+    v[k] = cells[t * (DIM + 1) + k];
+    const float4 r = rel[v[k]];
+    vf[k][0] = r.x; vf[k][1] = r.y; vf[k][2] = r.z;
+  }
+  int32_t ilo[3] = {0, 0, 0}, ihi[3] = {0, 0, 0};
+  for (int d = 0; d < DIM; d++) {
+    float mn = vf[0][d], mx = vf[0][d];
+    for (int k = 1; k <= DIM; k++) {
+      mn = fminf(mn, vf[k][d]);
+      mx = fmaxf(mx, vf[k][d]);
+    }
+    float a = __fsub_rn(__fdiv_rn(mn, g.hf[d]), kMargin32);
+    float b = __fadd_rn(__fdiv_rn(mx, g.hf[d]), kMargin32);
+    const float top = (float)(g.n[d] - 1);
+    if (!(a <= top) || !(b >= 0.0f)) return;
+    a = ceilf(a);
+    b = floorf(b);
+    if (a < 0.0f) a = 0.0f;
+    if (b > top) b = top;
+    if (a > b) return;
+    ilo[d] = (int32_t)a;
+    ihi[d] = (int32_t)b;
+  }
+  bool have64 = false;
+  double V[4][3];
+  const int64_t nx = g.n[0], ny = g.n[1];
+  for (int32_t z = ilo[2]; z <= ihi[2]; z++)
+    for (int32_t y = ilo[1]; y <= ihi[1]; y++)
+      for (int32_t x = ilo[0]; x <= ihi[0]; x++) {
+        const int64_t j = x + nx * (y + ny * (int64_t)z);
+        if (owner[j] <= (unsigned int)t) continue;  // a smaller id already owns it
+        const int32_t idx[3] = {x, y, z};
+        float pf[3] = {0.f, 0.f, 0.f};
+        for (int d = 0; d < DIM; d++) pf[d] = __fmul_rn(__int2float_rn(idx[d]), g.hf[d]);
+        if (!prefilter<DIM>(vf, pf)) continue;
+        if (!have64) {
+          for (int k = 0; k <= DIM; k++)
+            for (int d = 0; d < 3; d++) V[k][d] = d < DIM ? coords[(int64_t)v[k] * DIM + d] : 0.0;
+          have64 = true;
+        }
+        double P[3] = {0.0, 0.0, 0.0}, lam[4];
+        for (int d = 0; d < DIM; d++) P[d] = __dadd_rn(g.lo[d], __dmul_rn((double)idx[d], g.h[d]));
+        if (inside64<DIM>(V, P, lam)) atomicMin(owner + j, (unsigned int)t);
+      }
+}
+
+template <int DIM>
+__global__ void k_grid_tables(const double *__restrict__ coords, const int32_t *__restrict__ cells,
+                              const unsigned int *__restrict__ owner, GridDev g, int64_t n_g,
+                              int32_t *vid, uint16_t *lam, unsigned long long *n_out) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n_g) return;
+  const unsigned int t = owner[j];
+  if (t == 0xFFFFFFFFu) {
+    vid[j] = -1;
+    for (int k = 1; k <= DIM; k++) vid[k * n_g + j] = 0;
+    for (int k = 0; k < DIM; k++) lam[k * n_g + j] = 0;
+    atomicAdd(n_out, 1ull);
+    return;
+  }
+  const int64_t nx = g.n[0], ny = g.n[1];
+  const int32_t idx[3] = {(int32_t)(j % nx), (int32_t)((j / nx) % ny), (int32_t)(j / (nx * ny))};
+  double V[4][3], P[3] = {0.0, 0.0, 0.0}, l[4];
+  for (int k = 0; k <= DIM; k++) {
+    const int32_t v = cells[(int64_t)t * (DIM + 1) + k];
+    vid[k * n_g + j] = v;
+    for (int d = 0; d < 3; d++) V[k][d] = d < DIM ? coords[(int64_t)v * DIM + d] : 0.0;
+  }
+  for (int d = 0; d < DIM; d++) P[d] = __dadd_rn(g.lo[d], __dmul_rn((double)idx[d], g.h[d]));
+  inside64<DIM>(V, P, l);
+  for (int k = 0; k < DIM; k++) lam[k * n_g + j] = to_u16_unit(l[k + 1]);
+}
+
+template <int DIM>
+__global__ void k_node_tables(const double *__restrict__ coords, int64_t n_v, GridDev g,
+                              uint32_t *cell, uint16_t *frac) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_v) return;
+  int64_t ci[3] = {0, 0, 0};
+  for (int d = 0; d < DIM; d++) {
+    const double dd = __dsub_rn(coords[i * DIM + d], g.lo[d]);
+    const double t = __dmul_rn(dd, g.inv_h[d]);
+    const double fl = floor(t);
+    int64_t c;
+    if (!(fl >= 0.0)) c = 0;
+    else if (fl > (double)(g.n[d] - 2)) c = g.n[d] - 2;
+    else c = (int64_t)fl;
+    ci[d] = c;
+    frac[(int64_t)d * n_v + i] = to_u16_unit(__dsub_rn(t, (double)c));
+  }
+  cell[i] = (uint32_t)(ci[0] + (int64_t)g.n[0] * (ci[1] + (int64_t)g.n[1] * ci[2]));
+}
+
+inline unsigned int nblocks(int64_t n, int bs) {
+  int64_t b = (n + bs - 1) / bs;
+  return (unsigned int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" mcc_status mcc_plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid,
+                                      mcc_stream stream_, mcc_plan *out) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (!out) return MCC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!mesh || !grid) return MCC_ERR_INVALID_ARG;
+  const int dim = mesh->dim;
+  if (dim != 2 && dim != 3) return MCC_ERR_INVALID_ARG;
+  if (mesh->n_vertices < 1 || mesh->n_vertices >= (int64_t)1 << 31 || mesh->n_cells < 1 ||
+      mesh->n_cells >= (int64_t)1 << 31 || !mesh->coords || !mesh->cells)
+    return MCC_ERR_INVALID_ARG;
+  int64_t n_g = 1;
+  bool use_bbox = false;
+  for (int d = 0; d < dim; d++) {
+    if (grid->n[d] < 2 || grid->n[d] > 32768) return MCC_ERR_INVALID_ARG;
+    n_g *= grid->n[d];
+    if (!(grid->lo[d] < grid->hi[d])) use_bbox = true;
+  }
+  if (n_g > ((int64_t)1 << 31)) return MCC_ERR_INVALID_ARG;
+  const int64_t n_v = mesh->n_vertices, n_c = mesh->n_cells;
+
+  mcc_plan_s *P = new (std::nothrow) mcc_plan_s();
+  if (!P) return MCC_ERR_OOM;
+  int *d_flag = nullptr;
+  unsigned long long *d_keys = nullptr;
+  unsigned int *d_owner = nullptr;
+  float4 *d_rel = nullptr;
+  mcc_status st = MCC_OK;
+  auto fail = [&](mcc_status s) {
+    cudaFree(d_flag); cudaFree(d_keys); cudaFree(d_owner); cudaFree(d_rel);
+    if (P) { cudaFree(P->vid); cudaFree(P->lam); cudaFree(P->cell); cudaFree(P->frac); delete P; }
+    return s;
+  };
+  if (cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&d_keys, 6 * sizeof(unsigned long long)) != cudaSuccess)
+    return fail(MCC_ERR_OOM);
+  cudaMemsetAsync(d_flag, 0, sizeof(int), stream);
+  cudaMemsetAsync(d_keys, 0, 6 * sizeof(unsigned long long), stream);
+  k_check_cells<<<1216, 256, 0, stream>>>(mesh->cells, n_c * (dim + 1), n_v, d_flag);
+  if (use_bbox) k_bbox<<<608, 256, 0, stream>>>(mesh->coords, n_v, dim, d_keys);
+  int h_flag = 0;
+  unsigned long long h_keys[6] = {0, 0, 0, 0, 0, 0};
+  if (cudaMemcpyAsync(&h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaMemcpyAsync(h_keys, d_keys, sizeof(h_keys), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return fail(MCC_ERR_CUDA);
+  if (h_flag) return fail(MCC_ERR_INVALID_ARG);
+
+  // grid corners and spacing: h = (hi - lo) / (n - 1), inv_h = 1 / h
+  GridDev g;
+  memset(&g, 0, sizeof(g));
+  g.dim = dim;
+  for (int d = 0; d < 3; d++) {
+    if (d < dim) {
+      double lo = grid->lo[d], hi = grid->hi[d];
+      if (use_bbox) { lo = key_value(~h_keys[2 * d]); hi = key_value(h_keys[2 * d + 1]); }
+      if (!(lo < hi) || !std::isfinite(lo) || !std::isfinite(hi)) return fail(MCC_ERR_INVALID_ARG);
+      g.n[d] = grid->n[d];
+      g.lo[d] = lo;
+      g.h[d] = (hi - lo) / (double)(grid->n[d] - 1);
+      g.inv_h[d] = 1.0 / g.h[d];
+    } else {
+      g.n[d] = 1; g.lo[d] = 0.0; g.h[d] = 1.0; g.inv_h[d] = 1.0;
+    }
+    g.hf[d] = (float)g.h[d];
+  }
+
+  P->dim = dim;
+  for (int d = 0; d < 3; d++) {
+    P->n[d] = g.n[d]; P->lo[d] = g.lo[d]; P->h[d] = g.h[d]; P->inv_h[d] = g.inv_h[d];
+  }
+  P->n_v = n_v;
+  P->n_g = n_g;
+  if (cudaMalloc(&P->vid, sizeof(int32_t) * (dim + 1) * n_g) != cudaSuccess ||
+      cudaMalloc(&P->lam, sizeof(uint16_t) * dim * n_g) != cudaSuccess ||
+      cudaMalloc(&P->cell, sizeof(uint32_t) * n_v) != cudaSuccess ||
+      cudaMalloc(&P->frac, sizeof(uint16_t) * dim * n_v) != cudaSuccess ||
+      cudaMalloc(&d_owner, sizeof(unsigned int) * n_g) != cudaSuccess ||
+      cudaMalloc(&d_rel, sizeof(float4) * n_v) != cudaSuccess)
+    return fail(MCC_ERR_OOM);
+  cudaMemsetAsync(d_owner, 0xFF, sizeof(unsigned int) * n_g, stream);
+  cudaMemsetAsync(d_keys, 0, sizeof(unsigned long long), stream);
+  k_rel32<<<nblocks(n_v, 256), 256, 0, stream>>>(mesh->coords, n_v, g, d_rel);
+  if (dim == 2) {
+    k_raster<2><<<nblocks(n_c, 128), 128, 0, stream>>>(mesh->coords, mesh->cells, n_c, d_rel, g, d_owner);
+    k_grid_tables<2><<<nblocks(n_g, 256), 256, 0, stream>>>(mesh->coords, mesh->cells, d_owner, g, n_g,
+                                                          P->vid, P->lam, d_keys);
+    k_node_tables<2><<<nblocks(n_v, 256), 256, 0, stream>>>(mesh->coords, n_v, g, P->cell, P->frac);
+  } else {
+    k_raster<3><<<nblocks(n_c, 128), 128, 0, stream>>>(mesh->coords, mesh->cells, n_c, d_rel, g, d_owner);
+    k_grid_tables<3><<<nblocks(n_g, 256), 256, 0, stream>>>(mesh->coords, mesh->cells, d_owner, g, n_g,
+                                                          P->vid, P->lam, d_keys);
+    k_node_tables<3><<<nblocks(n_v, 256), 256, 0, stream>>>(mesh->coords, n_v, g, P->cell, P->frac);
+  }
+  unsigned long long n_out = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&n_out, d_keys, sizeof(n_out), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return fail(MCC_ERR_CUDA);
+  P->n_outside = (int64_t)n_out;
+  cudaFree(d_flag); cudaFree(d_keys); cudaFree(d_owner); cudaFree(d_rel);
+  *out = P;
+  (void)st;
+  return MCC_OK;
+}
+
+extern "C" void mcc_plan_destroy(mcc_plan P) {
+  if (!P) return;
+  cudaFree(P->vid); cudaFree(P->lam); cudaFree(P->cell); cudaFree(P->frac);
+  delete P;
+}
+
+extern "C" mcc_status mcc_plan_get_info(mcc_plan P, mcc_plan_info *info) {
+  if (!P || !info) return MCC_ERR_INVALID_ARG;
+  memset(info, 0, sizeof(*info));
+  info->dim = P->dim;
+  for (int d = 0; d < 3; d++) { info->n[d] = P->n[d]; info->lo[d] = P->lo[d]; info->h[d] = P->h[d]; }
+  info->n_vertices = P->n_v;
+  info->n_grid = P->n_g;
+  info->n_outside = P->n_outside;
+  return MCC_OK;
+}
+
+extern "C" mcc_status mcc_plan_copy_tables(mcc_plan P, int32_t *d_vid, uint16_t *d_lam,
+                                           uint32_t *d_cell, uint16_t *d_frac, mcc_stream s) {
+  if (!P) return MCC_ERR_INVALID_ARG;
+  cudaStream_t stream = (cudaStream_t)s;
+  const int dim = P->dim;
+  cudaError_t e = cudaSuccess;
+  if (d_vid && e == cudaSuccess)
+    e = cudaMemcpyAsync(d_vid, P->vid, sizeof(int32_t) * (dim + 1) * P->n_g, cudaMemcpyDeviceToDevice, stream);
+  if (d_lam && e == cudaSuccess)
+    e = cudaMemcpyAsync(d_lam, P->lam, sizeof(uint16_t) * dim * P->n_g, cudaMemcpyDeviceToDevice, stream);
+  if (d_cell && e == cudaSuccess)
+    e = cudaMemcpyAsync(d_cell, P->cell, sizeof(uint32_t) * P->n_v, cudaMemcpyDeviceToDevice, stream);
+  if (d_frac && e == cudaSuccess)
+    e = cudaMemcpyAsync(d_frac, P->frac, sizeof(uint16_t) * dim * P->n_v, cudaMemcpyDeviceToDevice, stream);
+  return e == cudaSuccess ? MCC_OK : MCC_ERR_CUDA;
+}
+
+// internal accessor for the other translation units
+PlanView mcc_plan_view(mcc_plan P) {
+  PlanView v;
+  v.dim = P->dim;
+  v.nx = P->n[0]; v.ny = P->n[1]; v.nz = P->n[2];
+  v.n_v = P->n_v; v.n_g = P->n_g;
+  v.vid = P->vid; v.lam = P->lam; v.cell = P->cell; v.frac = P->frac;
+  return v;
+}

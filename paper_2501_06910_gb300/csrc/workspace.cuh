@@ -1,0 +1,47 @@
+// workspace.cuh -- workspace layouts and the launchers shared by api.cu.
+#pragma once
+
+#include "common.cuh"
+
+namespace mcc {
+
+// Compression workspace (byte offsets; the status block sits at 0).
+struct CompressWs {
+  size_t hist1, hist2, code1, code2, len1, len2, Q, q1, sym1, sym2, val1, val2, gw, ge, gr, total;
+};
+
+// Decode tables of one component: first-level table on kLutBits bits
+// (entry = symbol << 8 | length, length 0 = longer code) and the canonical
+// (first code, count, offset) per length with the symbols in canonical order.
+struct DecTab {
+  unsigned int lut[1 << kLutBits];
+  unsigned int first[kMaxLen + 2], count[kMaxLen + 2], offset[kMaxLen + 2];
+  unsigned short sorted[2 * kMaxR];
+};
+
+// Parsed and validated stream header.
+struct DecInfo {
+  int dtype, dim, R1, R2, C1, C2, lmax, pad;
+  long long K, rho12_q;
+  float rho12_f;
+  int pad2;
+  double s2;
+  unsigned long long nout1, nout2, nraw, w1, w2;
+  long long ng1, ng2;
+  Layout L;
+};
+
+struct DecompressWs {
+  size_t info, tab1, tab2, q1, total;
+};
+
+}  // namespace mcc
+
+mcc_status check_params(const mcc_params *p);
+mcc::CompressWs compress_ws_layout(const mcc::PlanView &pv, const mcc_params *p);
+mcc::DecompressWs decompress_ws_layout(const mcc::PlanView &pv);
+mcc_status launch_compress(const mcc::PlanView &pv, const void *d_values, const mcc_params *p,
+                           unsigned char *ws, unsigned char *out, size_t capacity,
+                           cudaStream_t stream);
+mcc_status launch_decompress(const mcc::PlanView &pv, const unsigned char *in, size_t in_bytes,
+                             void *d_values, int dtype, unsigned char *ws, cudaStream_t stream);
