@@ -766,7 +766,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     double v = load_value(x, p->dtype, i);
     double xr = f.s2 * (double)((int64_t)Q[i] + f.K);
     double xo = p->dtype == 0 ? xr : (double)(float)xr;
-    if (fabs(v - xo) > f.tau2 || q2 < INT32_MIN || q2 > INT32_MAX) {
+    if (fabs(v - xo) > f.tau2 || q2 <= INT32_MIN || q2 > INT32_MAX) {
       sym2[i] = (uint16_t)(2 * R2 - 1);
       nraw++;
     } else if (q2 >= -(R2 - 1) && q2 <= R2 - 2) {

@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(256) k_node(PlanView pv, const T *__restrict__
       const int Qi = __ldg(Q + i);
       const long long P = predict_vertex<DIM>(q1, c, fx, fy, fz, nx, sxy, f.rho12_q, f.rho12_f);
       const long long q2 = (long long)Qi - P;
-      bool raw = q2 < -2147483648ll || q2 > 2147483647ll;
+      bool raw = q2 <= -2147483648ll || q2 > 2147483647ll;  // INT32_MIN is reserved
       if (f.guard) {
         const double v = (double)__ldg(x + i);
         const double xr = __dmul_rn(f.s2, (double)((long long)Qi + f.K));
@@ -394,9 +394,18 @@ __global__ void __launch_bounds__(256) k_node(PlanView pv, const T *__restrict__
 
 // ---------------------------------------------------------------------------
 // k_codebook: canonical Huffman code book of one component per CTA.
-// Two-queue construction over the leaves sorted by (count, symbol) -- leaves
-// win ties, internal nodes leave in creation order -- depths by pointer
-// jumping; counts halved (c -> max(1, c >> 1)) while a code exceeds lmax.
+//
+// Code lengths follow the two-queue construction over the leaves sorted by
+// (count, symbol): each step takes the two lightest nodes, a leaf before an
+// internal node of equal weight, internal nodes in creation order. The pick
+// sequence is the sorted merge of the leaves and the internal nodes, and
+// internal node k is the sum of picks 2k and 2k+1; nodes created from picks
+// of weight >= t weigh >= 2t, so every queued node of weight <= 2t (t the
+// next pick) is picked before any node created from them. Rounds therefore
+// merge that whole batch in parallel (ranks by binary search), pair it into
+// new nodes, and fall back to single-thread steps when the batch is small.
+// Depths by pointer jumping; counts halved (c -> max(1, c >> 1)) while a code
+// exceeds lmax.
 // ---------------------------------------------------------------------------
 struct CodebookArgs {
   const unsigned int *hist;
@@ -406,27 +415,33 @@ struct CodebookArgs {
   unsigned char *stream_lens;
 };
 
+constexpr int kBatchMin = 24;
+
+__device__ __forceinline__ unsigned long long node_w(int e, int m, const unsigned long long *sk,
+                                                     const unsigned long long *Iw) {
+  return e < m ? (sk[e] >> 32) : Iw[e - m];
+}
+
 __global__ void __launch_bounds__(1024) k_codebook(CodebookArgs a1, CodebookArgs a2, int lmax,
                                                    Status *st) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (block_failed(st)) return;
   const CodebookArgs A = blockIdx.x == 0 ? a1 : a2;
   const int nsym = A.nsym;
-  int npow = 1;
-  while (npow < nsym) npow <<= 1;
-  // shared memory carve-up
-  unsigned long long *keys = (unsigned long long *)smem;                 // [npow]
-  unsigned long long *Iw = keys + npow;                                  // [nsym]
-  unsigned int *cnt = (unsigned int *)(Iw + nsym);                       // [nsym]
-  unsigned short *anc0 = (unsigned short *)(cnt + nsym);                 // [2 nsym]
-  unsigned short *anc1 = anc0 + 2 * nsym;                                // [2 nsym]
-  unsigned short *dep0 = anc1 + 2 * nsym;                                // [2 nsym]
-  unsigned short *dep1 = dep0 + 2 * nsym;                                // [2 nsym]
-  unsigned short *rank = dep1 + 2 * nsym;                                // [nsym]
-  unsigned char *lens = (unsigned char *)(rank + nsym);                  // [nsym]
+  unsigned int *cnt = (unsigned int *)smem;                                // [nsym]
+  unsigned long long *keyA = (unsigned long long *)(cnt + nsym);           // [nsym] (nsym even)
+  unsigned long long *sk = keyA + nsym;                                    // [nsym]
+  unsigned long long *Iw = sk + nsym;                                      // [nsym]
+  unsigned short *parent = (unsigned short *)(Iw + nsym);                  // [2 nsym]
+  unsigned short *anc1 = parent + 2 * nsym;                                // [2 nsym]
+  unsigned short *mid = anc1 + 2 * nsym;                                   // [2 nsym]
+  unsigned short *rank = mid + 2 * nsym;                                   // [nsym]
+  unsigned char *lens = (unsigned char *)(rank + nsym);                    // [nsym]
+  unsigned short *dep0 = (unsigned short *)keyA;                           // reuse [2 nsym]
+  unsigned short *dep1 = dep0 + 2 * nsym;                                  // reuse [2 nsym]
   __shared__ unsigned int wcount[32][kMaxLen + 1];
   __shared__ CanonTables ct;
-  __shared__ int m_sh, kpos, maxlen;
+  __shared__ int m_sh, kpos, maxlen, sa, sb, sc, snl, sni, snleaf;
 
   const int tid = threadIdx.x;
   if (tid == 0) m_sh = 0;
@@ -443,50 +458,105 @@ __global__ void __launch_bounds__(1024) k_codebook(CodebookArgs a1, CodebookArgs
       if (cnt[s]) lens[s] = 1;
   }
   while (m >= 2) {
-    if (tid == 0) { kpos = 0; maxlen = 0; }
+    if (tid == 0) { kpos = 0; maxlen = 0; sa = 0; sb = 0; sc = 0; }
     __syncthreads();
     for (int s = tid; s < nsym; s += blockDim.x)
-      if (cnt[s]) keys[atomicAdd(&kpos, 1)] = ((unsigned long long)cnt[s] << 32) | (unsigned)s;
-    for (int s = m + tid; s < npow; s += blockDim.x) keys[s] = ~0ull;
+      if (cnt[s]) keyA[atomicAdd(&kpos, 1)] = ((unsigned long long)cnt[s] << 32) | (unsigned)s;
     __syncthreads();
-    // bitonic sort, ascending
-    for (int k = 2; k <= npow; k <<= 1)
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int i = tid; i < npow; i += blockDim.x) {
-          const int p = i ^ j;
-          if (p > i) {
-            const unsigned long long a = keys[i], b = keys[p];
-            const bool up = (i & k) == 0;
-            if ((a > b) == up) { keys[i] = b; keys[p] = a; }
-          }
-        }
-        __syncthreads();
-      }
-    // two-queue merge (one thread): node ids 0..m-1 leaves in sorted order,
-    // m..2m-2 internal nodes in creation order
-    if (tid == 0) {
-      int a = 0, b = 0, c = 0;
-      while (c < m - 1) {
-        int id[2];
-        unsigned long long w[2];
-#pragma unroll
-        for (int r = 0; r < 2; r++) {
-          const bool leaf = a < m && (b >= c || (keys[a] >> 32) <= Iw[b]);
-          if (leaf) { id[r] = a; w[r] = keys[a] >> 32; a++; }
-          else { id[r] = m + b; w[r] = Iw[b]; b++; }
-        }
-        Iw[c] = w[0] + w[1];
-        anc0[id[0]] = (unsigned short)(m + c);
-        anc0[id[1]] = (unsigned short)(m + c);
-        c++;
-      }
-      anc0[2 * m - 2] = (unsigned short)(2 * m - 2);
+    // rank sort of the (count, symbol) keys (keys are distinct)
+    for (int i = tid; i < m; i += blockDim.x) {
+      const unsigned long long k = keyA[i];
+      int r = 0;
+      for (int j = 0; j < m; j++) r += keyA[j] < k;
+      sk[r] = k;
     }
     __syncthreads();
+    for (;;) {
+      if (tid == 0) {
+        const int a = sa, b = sb, c = sc;
+        int nl = 0, ni = 0;
+        if (c < m - 1) {
+          const bool leaf = a < m && (b >= c || (sk[a] >> 32) <= Iw[b]);
+          const unsigned long long T = 2 * (leaf ? (sk[a] >> 32) : Iw[b]);
+          int lo = a, hi = m;  // first leaf with weight > T
+          while (lo < hi) { const int md = (lo + hi) >> 1; if ((sk[md] >> 32) <= T) lo = md + 1; else hi = md; }
+          nl = lo - a;
+          lo = b; hi = c;      // first queued internal node with weight > T
+          while (lo < hi) { const int md = (lo + hi) >> 1; if (Iw[md] <= T) lo = md + 1; else hi = md; }
+          ni = lo - b;
+          if (nl + ni < kBatchMin) {
+            // small batch: single-thread two-queue steps over it (at least one)
+            int steps = (nl + ni) >> 1;
+            if (steps < 1) steps = 1;
+            int aa = a, bb = b, cc = c;
+            for (int s = 0; s < steps && cc < m - 1; s++) {
+              int id[2];
+              unsigned long long w[2];
+#pragma unroll
+              for (int r = 0; r < 2; r++) {
+                const bool lf = aa < m && (bb >= cc || (sk[aa] >> 32) <= Iw[bb]);
+                if (lf) { id[r] = aa; w[r] = sk[aa] >> 32; aa++; }
+                else { id[r] = m + bb; w[r] = Iw[bb]; bb++; }
+              }
+              Iw[cc] = w[0] + w[1];
+              parent[id[0]] = (unsigned short)(m + cc);
+              parent[id[1]] = (unsigned short)(m + cc);
+              cc++;
+            }
+            sa = aa; sb = bb; sc = cc;
+            nl = 0; ni = 0;
+          }
+        }
+        snl = nl; sni = ni; snleaf = 0;
+      }
+      __syncthreads();
+      const int a = sa, b = sb, c = sc, nl = snl, ni = sni;
+      __syncthreads();  // every thread holds the round state before it changes
+      if (c >= m - 1) break;
+      if (nl + ni == 0) continue;  // a sequential round ran
+      // parallel batch: merge ranks (leaf first on equal weight)
+      for (int i = tid; i < nl + ni; i += blockDim.x) {
+        int pos;
+        if (i < nl) {
+          const unsigned long long w = sk[a + i] >> 32;
+          int lo = 0, hi = ni;  // internal nodes with weight < w
+          while (lo < hi) { const int md = (lo + hi) >> 1; if (Iw[b + md] < w) lo = md + 1; else hi = md; }
+          pos = i + lo;
+          mid[pos] = (unsigned short)(a + i);
+        } else {
+          const int j = i - nl;
+          const unsigned long long w = Iw[b + j];
+          int lo = 0, hi = nl;  // leaves with weight <= w
+          while (lo < hi) { const int md = (lo + hi) >> 1; if ((sk[a + md] >> 32) <= w) lo = md + 1; else hi = md; }
+          pos = j + lo;
+          mid[pos] = (unsigned short)(m + b + j);
+        }
+      }
+      __syncthreads();
+      const int be = (nl + ni) & ~1;
+      for (int i = tid; i < be / 2; i += blockDim.x) {
+        const int e0 = mid[2 * i], e1 = mid[2 * i + 1];
+        Iw[c + i] = node_w(e0, m, sk, Iw) + node_w(e1, m, sk, Iw);
+        parent[e0] = (unsigned short)(m + c + i);
+        parent[e1] = (unsigned short)(m + c + i);
+        const int nlf = (e0 < m) + (e1 < m);
+        if (nlf) atomicAdd(&snleaf, nlf);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        sa = a + snleaf;
+        sb = b + (be - snleaf);
+        sc = c + be / 2;
+      }
+      __syncthreads();
+    }
+    // depths by pointer jumping from the root (node 2m-2)
     const int N = 2 * m - 1, root = 2 * m - 2;
+    if (tid == 0) parent[root] = (unsigned short)root;
+    __syncthreads();
     for (int v = tid; v < N; v += blockDim.x) dep0[v] = v == root ? 0 : 1;
     __syncthreads();
-    unsigned short *ac = anc0, *an = anc1, *dc = dep0, *dn = dep1;
+    unsigned short *ac = parent, *an = anc1, *dc = dep0, *dn = dep1;
     for (int span = 1; span < N; span <<= 1) {
       for (int v = tid; v < N; v += blockDim.x) {
         const unsigned short p = ac[v];
@@ -500,7 +570,7 @@ __global__ void __launch_bounds__(1024) k_codebook(CodebookArgs a1, CodebookArgs
     for (int v = tid; v < m; v += blockDim.x) atomicMax(&maxlen, (int)dc[v]);
     __syncthreads();
     if (maxlen <= lmax) {
-      for (int v = tid; v < m; v += blockDim.x) lens[keys[v] & 0xFFFF] = (unsigned char)dc[v];
+      for (int v = tid; v < m; v += blockDim.x) lens[sk[v] & 0xFFFF] = (unsigned char)dc[v];
       __syncthreads();
       break;
     }
@@ -520,16 +590,18 @@ __global__ void __launch_bounds__(1024) k_codebook(CodebookArgs a1, CodebookArgs
 }
 
 size_t codebook_smem(int nsym) {
-  int npow = 1;
-  while (npow < nsym) npow <<= 1;
-  return 8 * (size_t)npow + 8 * (size_t)nsym + 4 * (size_t)nsym + 2 * 8 * (size_t)nsym +
-         2 * (size_t)nsym + (size_t)nsym + 16;
+  return 4 * (size_t)nsym + 3 * 8 * (size_t)nsym + 3 * 4 * (size_t)nsym + 2 * (size_t)nsym +
+         (size_t)nsym + 16;
 }
 
 // ---------------------------------------------------------------------------
-// k_group_len: lane bit lengths (written into the stream), per-group words,
-// escapes and raw values.
+// k_group_len: one CTA per group of 32 lane chunks. Warp w covers steps
+// [w C / 8, (w+1) C / 8) of every lane; per (part, lane) bit sums and per part
+// escape / raw counts go to the workspace (k_pack uses them as offsets), lane
+// totals to the stream's lane table, group totals to gw / ge / gr.
 // ---------------------------------------------------------------------------
+constexpr int kParts = 8;
+
 struct GroupArgs {
   const unsigned short *sym1, *sym2;
   const unsigned char *len1, *len2;
@@ -537,44 +609,66 @@ struct GroupArgs {
   int C1, C2, nsym1, nsym2;
   unsigned short *ltab1, *ltab2;  // in the output stream
   unsigned int *gw, *ge, *gr;     // workspace [ng1 + ng2]
+  unsigned short *pb;             // workspace [ng1 + ng2][kParts][32]
+  unsigned int *pe, *pr;          // workspace [ng1 + ng2][kParts]
 };
 
 __global__ void __launch_bounds__(256) k_group_len(GroupArgs a, const Status *st) {
-  __shared__ unsigned char l1[2 * kMaxR], l2[2 * kMaxR];
+  __shared__ unsigned char L[2 * kMaxR];
+  __shared__ unsigned int sbits[kParts][32];
+  __shared__ unsigned int sesc[kParts], sraw[kParts];
   if (block_failed(st)) return;
-  for (int i = threadIdx.x; i < a.nsym1; i += blockDim.x) l1[i] = a.len1[i];
-  for (int i = threadIdx.x; i < a.nsym2; i += blockDim.x) l2[i] = a.len2[i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t gi = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (gi >= a.ng1 + a.ng2) return;
+  const int64_t gi = blockIdx.x;
   const bool c1 = gi < a.ng1;
   const int64_t g = c1 ? gi : gi - a.ng1;
   const int C = c1 ? a.C1 : a.C2;
   const int64_t n = c1 ? a.n1 : a.n2;
   const unsigned short *sym = c1 ? a.sym1 : a.sym2;
-  const unsigned char *L = c1 ? l1 : l2;
+  const int nsym = c1 ? a.nsym1 : a.nsym2;
+  const unsigned char *lsrc = c1 ? a.len1 : a.len2;
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x) L[i] = lsrc[i];
+  __syncthreads();
   const int rawsym = c1 ? kRawNone : a.nsym2 - 1;
-  unsigned int bits = 0, esc = 0, raw = 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k0 = (w * C) / kParts, k1 = ((w + 1) * C) / kParts;
   const int64_t base = g * 32 * (int64_t)C + lane;
-  for (int k = 0; k < C; k++) {
+  unsigned int bits = 0, esc = 0, raw = 0;
+#pragma unroll 4
+  for (int k = k0; k < k1; k++) {
     const int64_t p = base + 32 * (int64_t)k;
-    if (p >= n) break;
-    const int s = __ldg(sym + p);
-    bits += L[s];
-    esc += s == 0;
-    raw += s == rawsym;
+    if (p < n) {
+      const int sy = __ldg(sym + p);
+      bits += L[sy];
+      esc += sy == 0;
+      raw += sy == rawsym;
+    }
   }
-  (c1 ? a.ltab1 : a.ltab2)[g * 32 + lane] = (unsigned short)bits;
+  a.pb[(gi * kParts + w) * 32 + lane] = (unsigned short)bits;
+  sbits[w][lane] = bits;
   for (int o = 16; o; o >>= 1) {
-    bits += __shfl_xor_sync(0xffffffffu, bits, o);
     esc += __shfl_xor_sync(0xffffffffu, esc, o);
     raw += __shfl_xor_sync(0xffffffffu, raw, o);
   }
   if (lane == 0) {
-    a.gw[gi] = (bits + 31) / 32;
-    a.ge[gi] = esc;
-    a.gr[gi] = raw;
+    sesc[w] = esc;
+    sraw[w] = raw;
+    a.pe[gi * kParts + w] = esc;
+    a.pr[gi * kParts + w] = raw;
+  }
+  __syncthreads();
+  if (w == 0) {
+    unsigned int tot = 0;
+#pragma unroll
+    for (int q = 0; q < kParts; q++) tot += sbits[q][lane];
+    (c1 ? a.ltab1 : a.ltab2)[g * 32 + lane] = (unsigned short)tot;
+    for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) {
+      unsigned int e = 0, r = 0;
+      for (int q = 0; q < kParts; q++) { e += sesc[q]; r += sraw[q]; }
+      a.gw[gi] = (tot + 31) / 32;
+      a.ge[gi] = e;
+      a.gr[gi] = r;
+    }
   }
 }
 
@@ -688,7 +782,9 @@ __global__ void __launch_bounds__(1024) k_scan(ScanArgs a, Status *st) {
 }
 
 // ---------------------------------------------------------------------------
-// k_pack: bit packing of one group per warp through shared memory
+// k_pack: one CTA per group; every (part, lane) writes its codes MSB-first at
+// its bit offset into a shared-memory copy of the group's words, escape and
+// raw values go to their index-ordered slots, then the words are copied out.
 // ---------------------------------------------------------------------------
 struct PackArgs {
   const unsigned short *sym1, *sym2;
@@ -699,23 +795,25 @@ struct PackArgs {
   int64_t n1, n2, ng1, ng2;
   int C1, C2, nsym1, nsym2, vsz;
   unsigned char *out;
-  int words_per_warp;
+  const unsigned short *pb;
+  const unsigned int *pe, *pr;
 };
 
-__global__ void __launch_bounds__(128) k_pack(PackArgs a, const Status *st) {
+__global__ void __launch_bounds__(256) k_pack(PackArgs a, const Status *st) {
   extern __shared__ unsigned int stage[];
+  __shared__ unsigned int scode[2 * kMaxR];
+  __shared__ unsigned char slen[2 * kMaxR];
   if (block_failed(st)) return;
   const Layout L = st->L;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t gi = blockIdx.x * (int64_t)(blockDim.x >> 5) + w;
-  if (gi >= a.ng1 + a.ng2) return;
+  const int64_t gi = blockIdx.x;
   const bool c1 = gi < a.ng1;
   const int64_t g = c1 ? gi : gi - a.ng1;
   const int C = c1 ? a.C1 : a.C2;
   const int64_t n = c1 ? a.n1 : a.n2;
+  const int nsym = c1 ? a.nsym1 : a.nsym2;
   const unsigned short *sym = c1 ? a.sym1 : a.sym2;
-  const unsigned int *code = c1 ? a.code1 : a.code2;
-  const unsigned char *len = c1 ? a.len1 : a.len2;
+  const unsigned int *csrc = c1 ? a.code1 : a.code2;
+  const unsigned char *lsrc = c1 ? a.len1 : a.len2;
   const int *val = c1 ? a.val1 : a.val2;
   const int rawsym = c1 ? kRawNone : a.nsym2 - 1;
   unsigned char *o = a.out;
@@ -725,41 +823,50 @@ __global__ void __launch_bounds__(128) k_pack(PackArgs a, const Status *st) {
   const unsigned short *ltab = (const unsigned short *)(o + (c1 ? L.ltab1 : L.ltab2));
   int *outv = (int *)(o + (c1 ? L.out1 : L.out2));
   unsigned int *bits = (unsigned int *)(o + (c1 ? L.bits1 : L.bits2));
-  unsigned int *sm = stage + w * a.words_per_warp;
 
   const unsigned int w0 = gtab[g], nw = gtab[g + 1] - w0;
-  for (unsigned int i = lane; i < nw; i += 32) sm[i] = 0;
-  // exclusive scan of lane bit lengths
+  for (unsigned int i = threadIdx.x; i < nw; i += blockDim.x) stage[i] = 0;
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x) {
+    scode[i] = csrc[i];
+    slen[i] = lsrc[i];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // bit offset of (part w, lane): lanes before this one, then earlier parts
   const unsigned int lb = ltab[g * 32 + lane];
   unsigned int incl = lb;
-  for (int s = 1; s < 32; s <<= 1) {
-    const unsigned int t = __shfl_up_sync(0xffffffffu, incl, s);
-    if (lane >= s) incl += t;
+  for (int sft = 1; sft < 32; sft <<= 1) {
+    const unsigned int t = __shfl_up_sync(0xffffffffu, incl, sft);
+    if (lane >= sft) incl += t;
   }
   unsigned int pos = incl - lb;
-  __syncwarp();
   unsigned int e_run = etab[g], r_run = c1 ? 0u : rtab[g];
-  const unsigned lt = (1u << lane) - 1;
+  for (int q = 0; q < w; q++) {
+    pos += a.pb[(gi * kParts + q) * 32 + lane];
+    e_run += a.pe[gi * kParts + q];
+    r_run += a.pr[gi * kParts + q];
+  }
+  __syncthreads();
+  const int k0 = (w * C) / kParts, k1 = ((w + 1) * C) / kParts;
   const int64_t base = g * 32 * (int64_t)C + lane;
-  for (int k = 0; k < C; k++) {
+  const unsigned lt = (1u << lane) - 1;
+#pragma unroll 4
+  for (int k = k0; k < k1; k++) {
     const int64_t p = base + 32 * (int64_t)k;
-    if (g * 32 * (int64_t)C + 32 * (int64_t)k >= n) break;  // warp-uniform
     const bool valid = p < n;
-    const int s = valid ? (int)__ldg(sym + p) : -1;
+    const int sy = valid ? (int)__ldg(sym + p) : -1;
     if (valid) {
-      const unsigned int cl = len[s];
-      const unsigned long long v =
-          ((unsigned long long)code[s] << (64 - cl)) >> (pos & 31);
-      atomicOr(sm + (pos >> 5), (unsigned int)(v >> 32));
-      if ((pos & 31) + cl > 32) atomicOr(sm + (pos >> 5) + 1, (unsigned int)v);
+      const unsigned int cl = slen[sy];
+      const unsigned long long v = ((unsigned long long)scode[sy] << (64 - cl)) >> (pos & 31);
+      atomicOr(stage + (pos >> 5), (unsigned int)(v >> 32));
+      if ((pos & 31) + cl > 32) atomicOr(stage + (pos >> 5) + 1, (unsigned int)v);
       pos += cl;
     }
-    const unsigned em = __ballot_sync(0xffffffffu, s == 0);
-    if (s == 0) outv[e_run + __popc(em & lt)] = __ldg(val + p);
+    const unsigned em = __ballot_sync(0xffffffffu, sy == 0);
+    if (sy == 0) outv[e_run + __popc(em & lt)] = __ldg(val + p);
     e_run += __popc(em);
     if (!c1) {
-      const unsigned rm = __ballot_sync(0xffffffffu, s == rawsym);
-      if (s == rawsym) {
+      const unsigned rm = __ballot_sync(0xffffffffu, sy == rawsym);
+      if (sy == rawsym) {
         unsigned char *dst = o + L.raw + (uint64_t)a.vsz * (r_run + __popc(rm & lt));
         if (a.vsz == 8) *(unsigned long long *)dst = ((const unsigned long long *)a.x)[p];
         else *(unsigned int *)dst = ((const unsigned int *)a.x)[p];
@@ -767,8 +874,8 @@ __global__ void __launch_bounds__(128) k_pack(PackArgs a, const Status *st) {
       r_run += __popc(rm);
     }
   }
-  __syncwarp();
-  for (unsigned int i = lane; i < nw; i += 32) bits[w0 + i] = sm[i];
+  __syncthreads();
+  for (unsigned int i = threadIdx.x; i < nw; i += blockDim.x) bits[w0 + i] = stage[i];
 }
 
 inline unsigned int nblk(int64_t n, int bs) {
@@ -824,6 +931,9 @@ CompressWs compress_ws_layout(const PlanView &pv, const mcc_params *p) {
   w.gw = take(4 * (size_t)(ng1 + ng2));
   w.ge = take(4 * (size_t)(ng1 + ng2));
   w.gr = take(4 * (size_t)(ng1 + ng2));
+  w.pb = take(2 * kParts * 32 * (size_t)(ng1 + ng2));
+  w.pe = take(4 * kParts * (size_t)(ng1 + ng2));
+  w.pr = take(4 * kParts * (size_t)(ng1 + ng2));
   w.total = o;
   return w;
 }
@@ -921,10 +1031,11 @@ mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_p
   }
   GroupArgs ga{sym1, sym2, ws + W.len1, ws + W.len2, n_g, n_v, ng1, ng2, p->C1, p->C2, nsym1, nsym2,
                (unsigned short *)(out + F.ltab1), (unsigned short *)(out + F.ltab2),
-               (unsigned int *)(ws + W.gw), (unsigned int *)(ws + W.ge), (unsigned int *)(ws + W.gr)};
+               (unsigned int *)(ws + W.gw), (unsigned int *)(ws + W.ge), (unsigned int *)(ws + W.gr),
+               (unsigned short *)(ws + W.pb), (unsigned int *)(ws + W.pe), (unsigned int *)(ws + W.pr)};
   {
     PROF_SCOPE("k_group_len", stream);
-    k_group_len<<<nblk(ng1 + ng2, 8), 256, 0, stream>>>(ga, st);
+    k_group_len<<<(unsigned int)(ng1 + ng2), 256, 0, stream>>>(ga, st);
   }
   ScanArgs sa{(const unsigned int *)(ws + W.gw), (const unsigned int *)(ws + W.ge),
               (const unsigned int *)(ws + W.gr), ng1, ng2, out, capacity, F, p->dtype, pv.dim,
@@ -934,13 +1045,14 @@ mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_p
     k_scan<<<1, 1024, 0, stream>>>(sa, st);
   }
   const int cmax = p->C1 > p->C2 ? p->C1 : p->C2;
-  const int wpw = cmax * p->lmax;  // worst-case words of one group
+  const size_t stage_bytes = 4 * (size_t)cmax * p->lmax;  // worst-case words of one group
   PackArgs pa{sym1, sym2, (const unsigned int *)(ws + W.code1), (const unsigned int *)(ws + W.code2),
               ws + W.len1, ws + W.len2, val1, val2, d_values, n_g, n_v, ng1, ng2, p->C1, p->C2,
-              nsym1, nsym2, p->dtype == MCC_F64 ? 8 : 4, out, wpw};
+              nsym1, nsym2, p->dtype == MCC_F64 ? 8 : 4, out, (const unsigned short *)(ws + W.pb),
+              (const unsigned int *)(ws + W.pe), (const unsigned int *)(ws + W.pr)};
   {
     PROF_SCOPE("k_pack", stream);
-    k_pack<<<nblk(ng1 + ng2, 4), 128, 4 * (size_t)wpw * 4, stream>>>(pa, st);
+    k_pack<<<(unsigned int)(ng1 + ng2), 256, stage_bytes, stream>>>(pa, st);
   }
   if (cudaGetLastError() != cudaSuccess) return MCC_ERR_CUDA;
   return MCC_OK;

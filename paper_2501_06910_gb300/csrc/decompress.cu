@@ -3,16 +3,18 @@
 //
 //   k_dec_prep    validate the header and the group tables' ends, build the
 //                 canonical decode tables of both components (one CTA each)
-//   k_dec_grid    Huffman decode of the grid symbols (one warp per group of
-//                 32 lane chunks), escapes, Lorenzo differences
+//   k_dec_syms    Huffman decode of both components (one warp per group of
+//                 32 lane chunks): grid Lorenzo differences, residual codes,
+//                 escapes and raw values
 //   k_scan_rows / k_scan_axis
 //                 inverse Lorenzo: inclusive prefix sums along x, y (, z)
-//   k_dec_res     Huffman decode of the residual symbols fused with the
-//                 reconstruction x' = s2 (K + P + q2), P = round(rho12 g(q1))
+//   k_recon       reconstruction x' = s2 (K + P + q2), P = round(rho12 g(q1)),
+//                 fully parallel over the vertices
 //
 // Every read of the stream is bounds-checked against the validated layout; a
 // corrupt stream records MCC_ERR_CORRUPT and the affected warp stops.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -251,59 +253,95 @@ __device__ __forceinline__ bool group_setup(const unsigned char *in, uint64_t gt
 }
 
 // ---------------------------------------------------------------------------
-// k_dec_grid: grid symbols -> Lorenzo differences (with escapes)
+// k_dec_syms: Huffman decode of both components, one warp per group of 32
+// lane chunks (the first nb1 blocks take the grid component, the rest the
+// residual component; warps stride over their component's groups). Grid
+// symbols become Lorenzo differences (escape values from the escape list);
+// residual symbols become codes q2 (INT32_MIN marks a raw vertex, whose value
+// is written to the output here).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_dec_grid(const unsigned char *__restrict__ in,
+template <typename T>
+__global__ void __launch_bounds__(256) k_dec_syms(const unsigned char *__restrict__ in,
                                                   const DecInfo *__restrict__ info,
-                                                  const DecTab *__restrict__ tab, int64_t n_g,
-                                                  int *__restrict__ delta, Status *st) {
-  __shared__ DecTab T;
+                                                  const DecTab *__restrict__ tab1,
+                                                  const DecTab *__restrict__ tab2, int nb1,
+                                                  int64_t n_g, int64_t n_v, int *__restrict__ delta,
+                                                  int *__restrict__ q2s, T *__restrict__ xo,
+                                                  Status *st) {
+  __shared__ DecTab Tb;
   if (block_failed(st)) return;
   const DecInfo I = *info;
-  load_tab(&T, tab, 2 * I.R1);
+  const bool c1 = (int)blockIdx.x < nb1;
+  {  // blocks without a group skip the table load
+    const int64_t first = (c1 ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - nb1) * (blockDim.x >> 5);
+    if (first >= (c1 ? I.ng1 : I.ng2)) return;
+  }
+  load_tab(&Tb, c1 ? tab1 : tab2, c1 ? 2 * I.R1 : 2 * I.R2);
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < I.ng1;
-       g += wstride) {
+  const int64_t ng = c1 ? I.ng1 : I.ng2;
+  const int64_t n = c1 ? n_g : n_v;
+  const int C = c1 ? I.C1 : I.C2, R = c1 ? I.R1 : I.R2, rawsym = 2 * R - 1;
+  const int *outv = (const int *)(in + (c1 ? I.L.out1 : I.L.out2));
+  const T *rawv = (const T *)(in + I.L.raw);
+  int *dst = c1 ? delta : q2s;
+  const unsigned lt = (1u << lane) - 1;
+  const int64_t b0 = c1 ? blockIdx.x : blockIdx.x - nb1;
+  const int64_t nblocks = c1 ? nb1 : gridDim.x - nb1;
+  const int64_t wstride = nblocks * (blockDim.x >> 5);
+  for (int64_t g = b0 * (blockDim.x >> 5) + (threadIdx.x >> 5); g < ng; g += wstride) {
     BitReader r;
-    unsigned int lane_bits, e0, e1;
-    const bool ok = group_setup(in, I.L.gtab1, I.L.etab1, I.L.ltab1, I.L.bits1, I.w1, I.nout1, g,
-                                r, lane_bits, e0, e1);
+    unsigned int lane_bits, e0, e1, r0 = 0, r1 = 0;
+    bool ok = c1 ? group_setup(in, I.L.gtab1, I.L.etab1, I.L.ltab1, I.L.bits1, I.w1, I.nout1, g, r,
+                               lane_bits, e0, e1)
+                 : group_setup(in, I.L.gtab2, I.L.etab2, I.L.ltab2, I.L.bits2, I.w2, I.nout2, g, r,
+                               lane_bits, e0, e1);
+    if (!c1) {
+      r0 = ld32(in + I.L.rtab2 + 4 * g);
+      r1 = ld32(in + I.L.rtab2 + 4 * (g + 1));
+      ok = ok && r0 <= r1 && r1 <= I.nraw;
+    }
     if (!ok) {
       if (lane == 0) set_error(st, MCC_ERR_CORRUPT);
       return;
     }
-    const int C = I.C1, R1 = I.R1, rawsym = 2 * I.R1 - 1;
-    const int *outv = (const int *)(in + I.L.out1);
-    const unsigned lt = (1u << lane) - 1;
-    unsigned int e_run = e0;
+    unsigned int e_run = e0, r_run = r0;
     bool lane_bad = false;
     for (int k = 0; k < C; k++) {
       const int64_t p0 = g * 32 * (int64_t)C + 32 * (int64_t)k;
-      if (p0 >= n_g) break;
+      if (p0 >= n) break;
       const int64_t p = p0 + lane;
-      const bool valid = p < n_g;
+      const bool valid = p < n;
       int sym = -2;
       if (valid && !lane_bad) {
-        sym = decode_one(r, T, I.lmax);
-        if (sym < 0 || sym == rawsym) lane_bad = true;
+        sym = decode_one(r, Tb, I.lmax);
+        if (sym < 0 || (c1 && sym == rawsym)) lane_bad = true;
       }
-      const bool esc = valid && !lane_bad && sym == 0;
+      const bool good = valid && !lane_bad;
+      const bool esc = good && sym == 0;
+      const bool raw = good && !c1 && sym == rawsym;
       const unsigned em = __ballot_sync(0xffffffffu, esc);
-      int d = 0;
+      const unsigned rm = __ballot_sync(0xffffffffu, raw);
+      int v = 0;
       if (esc) {
         const unsigned int idx = e_run + __popc(em & lt);
-        if (idx < e1) d = __ldg(outv + idx);
+        if (idx < e1) v = __ldg(outv + idx);
         else lane_bad = true;
-      } else if (valid && !lane_bad) {
-        d = sym - R1;
+        if (!c1 && v == INT_MIN) lane_bad = true;  // never an escape value
+      } else if (raw) {
+        const unsigned int idx = r_run + __popc(rm & lt);
+        if (idx < r1) xo[p] = rawv[idx];
+        else lane_bad = true;
+        v = INT_MIN;
+      } else if (good) {
+        v = sym - R;
       }
       e_run += __popc(em);
-      if (valid) delta[p] = d;
+      r_run += __popc(rm);
+      if (valid) dst[p] = v;
     }
     if (lane_bad || r.consumed != lane_bits) lane_bad = true;
-    if (__any_sync(0xffffffffu, lane_bad) || e_run != e1) {
+    if (__any_sync(0xffffffffu, lane_bad) || e_run != e1 || r_run != r1) {
       if (lane == 0) set_error(st, MCC_ERR_CORRUPT);
       return;
     }
@@ -363,87 +401,32 @@ __global__ void __launch_bounds__(256) k_scan_axis(int *q, int64_t n_inner, int6
 }
 
 // ---------------------------------------------------------------------------
-// k_dec_res: residual symbols -> x' at every vertex
+// k_recon: x' = s2 (K + P + q2) at every vertex, P = round(rho12 g(x1'))
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
-__global__ void __launch_bounds__(256) k_dec_res(const unsigned char *__restrict__ in,
-                                                 const DecInfo *__restrict__ info,
-                                                 const DecTab *__restrict__ tab, PlanView pv,
-                                                 const int *__restrict__ q1, T *__restrict__ xo,
-                                                 Status *st) {
-  __shared__ DecTab Tb;
-  if (block_failed(st)) return;
+__global__ void __launch_bounds__(256) k_recon(const DecInfo *__restrict__ info, PlanView pv,
+                                               const int *__restrict__ q1,
+                                               const int *__restrict__ q2s, T *__restrict__ xo,
+                                               const Status *st) {
+  if (*(volatile const unsigned int *)&st->err) return;
   const DecInfo I = *info;
-  load_tab(&Tb, tab, 2 * I.R2);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
   const int64_t n = pv.n_v;
-  const int C = I.C2, R2 = I.R2, rawsym = 2 * I.R2 - 1;
-  const int *outv = (const int *)(in + I.L.out2);
-  const T *rawv = (const T *)(in + I.L.raw);
   const int nx = pv.nx;
   const int64_t sxy = (int64_t)pv.nx * pv.ny;
-  const unsigned lt = (1u << lane) - 1;
-  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < I.ng2;
-       g += wstride) {
-    BitReader r;
-    unsigned int lane_bits, e0, e1;
-    bool ok = group_setup(in, I.L.gtab2, I.L.etab2, I.L.ltab2, I.L.bits2, I.w2, I.nout2, g, r,
-                          lane_bits, e0, e1);
-    const unsigned int r0 = ld32(in + I.L.rtab2 + 4 * g), r1 = ld32(in + I.L.rtab2 + 4 * (g + 1));
-    ok = ok && r0 <= r1 && r1 <= I.nraw;
-    if (!ok) {
-      if (lane == 0) set_error(st, MCC_ERR_CORRUPT);
-      return;
-    }
-    unsigned int e_run = e0, r_run = r0;
-    bool lane_bad = false;
-    for (int k = 0; k < C; k++) {
-      const int64_t p0 = g * 32 * (int64_t)C + 32 * (int64_t)k;
-      if (p0 >= n) break;
-      const int64_t p = p0 + lane;
-      const bool valid = p < n;
-      int sym = -2;
-      if (valid && !lane_bad) {
-        sym = decode_one(r, Tb, I.lmax);
-        if (sym < 0) lane_bad = true;
-      }
-      const bool ok_sym = valid && !lane_bad;
-      const bool esc = ok_sym && sym == 0;
-      const bool raw = ok_sym && sym == rawsym;
-      const unsigned em = __ballot_sync(0xffffffffu, esc);
-      const unsigned rm = __ballot_sync(0xffffffffu, raw);
-      long long q2 = 0;
-      T out = (T)0;
-      if (raw) {
-        const unsigned int idx = r_run + __popc(rm & lt);
-        if (idx < r1) out = rawv[idx];
-        else lane_bad = true;
-      } else if (ok_sym) {
-        if (esc) {
-          const unsigned int idx = e_run + __popc(em & lt);
-          if (idx < e1) q2 = __ldg(outv + idx);
-          else lane_bad = true;
-        } else {
-          q2 = sym - R2;
-        }
-        const uint32_t c = __ldg(pv.cell + p);
-        const float fx = __fmul_rn(__uint2float_rn(__ldg(pv.frac + p)), 0x1p-15f);
-        const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + p)), 0x1p-15f);
-        const float fz = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + p)), 0x1p-15f) : 0.0f;
-        const long long P = predict_vertex<DIM>(q1, c, fx, fy, fz, nx, sxy, I.rho12_q, I.rho12_f);
-        const double xr = __dmul_rn(I.s2, (double)(I.K + P + q2));
-        out = (T)xr;
-      }
-      e_run += __popc(em);
-      r_run += __popc(rm);
-      if (valid) xo[p] = out;
-    }
-    if (lane_bad || r.consumed != lane_bits) lane_bad = true;
-    if (__any_sync(0xffffffffu, lane_bad) || e_run != e1 || r_run != r1) {
-      if (lane == 0) set_error(st, MCC_ERR_CORRUPT);
-      return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p0 < n; p0 += 2 * stride) {
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const int64_t p = p0 + u * stride;
+      if (p >= n) break;
+      const int q2 = __ldg(q2s + p);
+      if (q2 == INT_MIN) continue;  // raw value already in place
+      const uint32_t c = __ldg(pv.cell + p);
+      const float fx = __fmul_rn(__uint2float_rn(__ldg(pv.frac + p)), 0x1p-15f);
+      const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + p)), 0x1p-15f);
+      const float fz = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + p)), 0x1p-15f) : 0.0f;
+      const long long P = predict_vertex<DIM>(q1, c, fx, fy, fz, nx, sxy, I.rho12_q, I.rho12_f);
+      xo[p] = (T)__dmul_rn(I.s2, (double)(I.K + P + (long long)q2));
     }
   }
 }
@@ -463,6 +446,7 @@ DecompressWs decompress_ws_layout(const PlanView &pv) {
   w.tab1 = take(sizeof(DecTab));
   w.tab2 = take(sizeof(DecTab));
   w.q1 = take(4 * (size_t)pv.n_g);
+  w.q2 = take(4 * (size_t)pv.n_v);
   w.total = o;
   return w;
 }
@@ -480,17 +464,22 @@ mcc_status launch_decompress(const PlanView &pv, const unsigned char *in, size_t
     PROF_SCOPE("k_dec_prep", stream);
     k_dec_prep<<<2, 256, 0, stream>>>(pa, st);
   }
-  // group counts are bounded by the smallest chunk size: launch for C = 1 and
-  // let warps beyond the stream's group count exit
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int *q2s = (int *)(ws + W.q2);
+  // group counts depend on the stream's chunk sizes: size the decoder for the
+  // smallest chunk and let warps stride over the groups that exist
   const int64_t max_g1 = ngroups(pv.n_g, 1), max_g2 = ngroups(pv.n_v, 1);
-  const unsigned int cap = (unsigned int)sms * 4;  // resident blocks; warps stride over groups
-  const unsigned int gb1 = nblk(max_g1, 8) < cap ? nblk(max_g1, 8) : cap;
+  const unsigned int cap = (unsigned int)sms * 2;
+  const unsigned int nb1 = nblk(max_g1, 8) < cap ? nblk(max_g1, 8) : cap;
+  const unsigned int nb2 = nblk(max_g2, 8) < cap ? nblk(max_g2, 8) : cap;
   {
-    PROF_SCOPE("k_dec_grid", stream);
-    k_dec_grid<<<gb1, 256, 0, stream>>>(in, info, tab1, pv.n_g, q1, st);
+    PROF_SCOPE("k_dec_syms", stream);
+    if (dtype == MCC_F64)
+      k_dec_syms<double><<<nb1 + nb2, 256, 0, stream>>>(in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (double *)d_values, st);
+    else
+      k_dec_syms<float><<<nb1 + nb2, 256, 0, stream>>>(in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (float *)d_values, st);
   }
   const int64_t nrows = (int64_t)pv.ny * pv.nz;
   {
@@ -498,38 +487,25 @@ mcc_status launch_decompress(const PlanView &pv, const unsigned char *in, size_t
     k_scan_rows<<<nblk(nrows, 8), 256, 0, stream>>>(q1, pv.nx, nrows, st);
   }
   {  // y: columns (x, z), stride nx
+    PROF_SCOPE("k_scan_axis", stream);
     const int64_t blocks = (pv.nx + 31) / 32 * (int64_t)pv.nz;
-    {
-      PROF_SCOPE("k_scan_axis", stream);
-      k_scan_axis<<<(unsigned int)blocks, 256, 0, stream>>>(q1, pv.nx, pv.nz, (int64_t)pv.nx * pv.ny,
-                                                           pv.ny, pv.nx, st);
-    }
+    k_scan_axis<<<(unsigned int)blocks, 256, 0, stream>>>(q1, pv.nx, pv.nz, (int64_t)pv.nx * pv.ny,
+                                                         pv.ny, pv.nx, st);
   }
   if (pv.dim == 3) {  // z: columns (x, y), stride nx ny
+    PROF_SCOPE("k_scan_axis", stream);
     const int64_t ninner = (int64_t)pv.nx * pv.ny;
-    {
-      PROF_SCOPE("k_scan_axis", stream);
-      k_scan_axis<<<(unsigned int)((ninner + 31) / 32), 256, 0, stream>>>(q1, ninner, 1, 0, pv.nz, ninner, st);
-    }
+    k_scan_axis<<<(unsigned int)((ninner + 31) / 32), 256, 0, stream>>>(q1, ninner, 1, 0, pv.nz, ninner, st);
   }
-  const unsigned int rb = nblk(max_g2, 8) < cap ? nblk(max_g2, 8) : cap;
-  if (pv.dim == 2) {
-    if (dtype == MCC_F64) {
-      PROF_SCOPE("k_dec_res", stream);
-      k_dec_res<2, double><<<rb, 256, 0, stream>>>(in, info, tab2, pv, q1, (double *)d_values, st);
-    }
-    else {
-      PROF_SCOPE("k_dec_res", stream);
-      k_dec_res<2, float><<<rb, 256, 0, stream>>>(in, info, tab2, pv, q1, (float *)d_values, st);
-    }
-  } else {
-    if (dtype == MCC_F64) {
-      PROF_SCOPE("k_dec_res", stream);
-      k_dec_res<3, double><<<rb, 256, 0, stream>>>(in, info, tab2, pv, q1, (double *)d_values, st);
-    }
-    else {
-      PROF_SCOPE("k_dec_res", stream);
-      k_dec_res<3, float><<<rb, 256, 0, stream>>>(in, info, tab2, pv, q1, (float *)d_values, st);
+  {
+    PROF_SCOPE("k_recon", stream);
+    const unsigned int rb = (unsigned int)sms * 8;
+    if (pv.dim == 2) {
+      if (dtype == MCC_F64) k_recon<2, double><<<rb, 256, 0, stream>>>(info, pv, q1, q2s, (double *)d_values, st);
+      else k_recon<2, float><<<rb, 256, 0, stream>>>(info, pv, q1, q2s, (float *)d_values, st);
+    } else {
+      if (dtype == MCC_F64) k_recon<3, double><<<rb, 256, 0, stream>>>(info, pv, q1, q2s, (double *)d_values, st);
+      else k_recon<3, float><<<rb, 256, 0, stream>>>(info, pv, q1, q2s, (float *)d_values, st);
     }
   }
   if (cudaGetLastError() != cudaSuccess) return MCC_ERR_CUDA;

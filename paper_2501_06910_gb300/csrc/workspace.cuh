@@ -7,7 +7,8 @@ namespace mcc {
 
 // Compression workspace (byte offsets; the status block sits at 0).
 struct CompressWs {
-  size_t hist1, hist2, code1, code2, len1, len2, Q, q1, sym1, sym2, val1, val2, gw, ge, gr, total;
+  size_t hist1, hist2, code1, code2, len1, len2, Q, q1, sym1, sym2, val1, val2, gw, ge, gr, pb, pe,
+      pr, total;
 };
 
 // Decode tables of one component: first-level table on kLutBits bits
@@ -32,7 +33,7 @@ struct DecInfo {
 };
 
 struct DecompressWs {
-  size_t info, tab1, tab2, q1, total;
+  size_t info, tab1, tab2, q1, q2, total;
 };
 
 }  // namespace mcc
