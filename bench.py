@@ -9,7 +9,8 @@ float64 field of 20 Gaussian bumps plus 6-octave value noise, on a 1024^2
 grid (the stand-in for the paper's OpenFOAM airfoil-large, Table I). The
 plan (mesh -> grid mapping) is built once and excluded, as in Sec. IV-A.
 
-One step = mcc_compress + mcc_decompress of one device-resident field. The L2
+One step = mcc_compress + mcc_decompress of one device-resident field,
+enqueued without host synchronisation and replayed as one CUDA graph. The L2
 (129 MB) is flushed (256 MiB write, untimed) before every step; each step is
 timed with CUDA events on the launch stream. Under torchrun every rank runs an
 independent replica on its own GPU (the method has no exchange step); value is
@@ -35,8 +36,13 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-# algorithmic HBM bytes per launch, per kernel (measurement)
+METRIC = "compress+decompress GB/s at eb=1e-4 rel"
+
+
 def algorithmic_bytes(dim, n_v, n_g, vsz, w1, w2, cbytes):
+    """HBM bytes each kernel must move at least once per launch (inputs read,
+    outputs written). Gathers of the vertex codes and of the grid codes are
+    counted as cache hits: both arrays fit in L2."""
     k1 = dim + 1
     return {
         "k_reduce": vsz * n_v,
@@ -49,19 +55,18 @@ def algorithmic_bytes(dim, n_v, n_g, vsz, w1, w2, cbytes):
         "k_scan": 0,
         "k_pack": 2 * (n_g + n_v) + cbytes,
         "k_dec_prep": 0,
-        "k_dec_grid": 4 * w1 + 4 * n_g,
+        "k_dec_syms": 4 * (w1 + w2) + 4 * (n_g + n_v),
         "k_scan_rows": 8 * n_g,
         "k_scan_axis": 12 * n_g,
-        "k_dec_res": 4 * w2 + (4 + 2 * dim) * n_v + vsz * n_v,
+        "k_recon": 4 * n_v + (4 + 2 * dim) * n_v + vsz * n_v,
     }
 
 
 def load_workload(config):
     if config == "c2":
         coords, cells = synth.mesh2d_graded()
-        x = synth.field_bumps_noise(coords)
-        return dict(name="2d-graded-2M-delaunay-grid1024^2", coords=coords, cells=cells, x=x,
-                    n=(1024, 1024))
+        return dict(name="2d-graded-2M-delaunay-grid1024^2", coords=coords, cells=cells,
+                    x=synth.field_bumps_noise(coords), n=(1024, 1024))
     if config == "c1":
         coords, cells = synth.mesh2d_jittered()
         return dict(name="2d-jittered-20k-grid128^2", coords=coords, cells=cells,
@@ -74,7 +79,7 @@ def load_workload(config):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms into a file."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -90,14 +95,16 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "50", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
         except OSError:
             self.proc = None
         return self
 
     def __exit__(self, *a):
         if self.proc is not None:
+            time.sleep(0.1)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -114,28 +121,32 @@ class ClockSampler:
             os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "window": "0.5 s pre-roll of the same step plus the timed region"}
 
 
 def run_reference(args, wl):
     """The CPU oracle (single-threaded C) timed on the same workload."""
     import oracle
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     plan = oracle.Plan(wl["coords"], wl["cells"], wl["n"])
     x = wl["x"]
     kw = dict(eb=args.eb, grid_fraction=0.5)
     for _ in range(args.warmup):
         oracle.decompress(plan, oracle.compress(plan, x, **kw))
-    times = []
-    size = 0
+    times, size = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
         s = oracle.compress(plan, x, **kw)
@@ -144,22 +155,21 @@ def run_reference(args, wl):
         size = s.size
     t = statistics.mean(times)
     gbs = x.nbytes / t / 1e9
-    line = {
-        "impl": "reference", "metric": "compress+decompress GB/s at eb=1e-4 rel",
-        "value": gbs, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
         "config": {"workload": wl["name"], "eb_rel": args.eb, "grid_fraction": 0.5,
                    "compression_ratio": x.nbytes / size},
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"full workload, {args.steps} steps"},
+                         "sample": f"full workload, {args.steps} steps, plan excluded"},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+    }), flush=True)
 
 
 def cpu_baseline(wl, eb, budget_s=12.0):
-    """Oracle compress+decompress repeated over a bounded time budget."""
+    """The oracle's compress + decompress, repeated over a bounded time budget."""
     import oracle
     plan = oracle.Plan(wl["coords"], wl["cells"], wl["n"])
     x = wl["x"]
@@ -179,15 +189,18 @@ def cpu_baseline(wl, eb, budget_s=12.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mcc", choices=["mcc", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--eb", type=float, default=1e-4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-kernel-times", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--preroll", type=float, default=0.5, help="seconds of untimed steps")
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -204,9 +217,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    coords = torch.from_numpy(wl["coords"]).to(dev)
-    cells = torch.from_numpy(wl["cells"]).to(dev)
-    plan = mcc.plan_create(coords, cells, wl["n"])
+    plan = mcc.plan_create(torch.from_numpy(wl["coords"]).to(dev),
+                           torch.from_numpy(wl["cells"]).to(dev), wl["n"])
     x_np = wl["x"]
     x = torch.from_numpy(x_np).to(dev)
     prm = mcc.params_default(dtype=mcc.F64, eb=args.eb, grid_fraction=0.5)
@@ -229,70 +241,108 @@ def main():
     st2, _ = mcc.workspace_result(wsd)
     if st != 0 or st2 != 0:
         raise SystemExit(f"device status {st}/{st2}")
-    lo, hi = float(x.min()), float(x.max())
-    tau = args.eb * (hi - lo)
+    tau = args.eb * (float(x.max()) - float(x.min()))
     err = float((y - x).abs().max())
     if not err <= tau:
         raise SystemExit(f"bound violated: {err} > {tau}")
 
+    graph = None
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        torch.cuda.synchronize()
+
+    def run_step():
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        run_step()
+    y.zero_()
+    run_step()
+    torch.cuda.synchronize()
+    if float((y - x).abs().max()) != err:
+        raise SystemExit("graph replay differs from the eager step")
+
     # timed region: K steps, each bracketed by events, L2 flushed before each
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        t_end = time.perf_counter() + args.preroll
+        while time.perf_counter() < t_end:  # pre-roll under the same load
+            flush.fill_(3)
+            run_step()
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
         for k in range(args.steps):
             flush.fill_(k & 0xFF)
             starts[k].record(stream)
-            step()
+            run_step()
             ends[k].record(stream)
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = statistics.mean(step_ms)
+        if world > 1:
+            dist.barrier()
+    ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     clocks = clk.summary()
 
-    # per-kernel device times (a second pass with event brackets per launch)
-    mcc.profile_reset()
-    mcc.profile_enable(True)
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        step()
-    prof = mcc.profile_read()
-    mcc.profile_enable(False)
-    launches_per_step = sum(n for _, n in prof.values()) / args.steps
+    # per-kernel device times: the same step captured with an event pair
+    # around every kernel, replayed K times (L2 flushed before each)
+    prof = {}
+    if not args.no_kernel_times:
+        mcc.profile_reset()
+        mcc.profile_enable(True)
+        pgraph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(pgraph):
+            step()
+        mcc.profile_enable(False)
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            pgraph.replay()
+            torch.cuda.synchronize()
+            for name, (t, n) in mcc.profile_read().items():
+                a = prof.setdefault(name, [0.0, 0])
+                a[0] += t
+                a[1] += n
+        mcc.profile_reset()
+    launches_per_step = (sum(n for _, n in prof.values()) / args.steps) if prof else None
 
     # end to end through the API with host buffers (pinned)
-    x_host = torch.from_numpy(x_np).pin_memory()
-    out_host = torch.empty(cap, dtype=torch.uint8).pin_memory()
-    y_host = torch.empty_like(x_host).pin_memory()
-    x_dev = torch.empty_like(x)
-    in_dev = torch.empty_like(out)
-    e2e_ms = []
+    e2e = None
     h2d = d2h = 0
-    for k in range(args.warmup + args.steps):
-        flush.fill_(k & 0xFF)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x_dev.copy_(x_host, non_blocking=True)
-        n_out = mcc.compress(plan, x_dev, prm, wsc, out, sync=True)
-        out_host[:n_out].copy_(out[:n_out])
-        in_dev[:n_out].copy_(out_host[:n_out], non_blocking=True)
-        mcc.decompress(plan, in_dev, n_out, y, wsd, sync=False)
-        y_host.copy_(y)
-        torch.cuda.synchronize()
-        if k >= args.warmup:
-            e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        h2d, d2h = x_np.nbytes + n_out, n_out + x_np.nbytes
-    if not torch.equal(y_host, y.cpu()):
-        raise SystemExit("e2e mismatch")
-    e2e = statistics.mean(e2e_ms)
+    if not args.no_e2e:
+        x_host = torch.from_numpy(x_np).pin_memory()
+        out_host = torch.empty(cap, dtype=torch.uint8).pin_memory()
+        y_host = torch.empty_like(x_host).pin_memory()
+        x_dev = torch.empty_like(x)
+        in_dev = torch.empty_like(out)
+        e2e_ms = []
+        for k in range(args.warmup + args.steps):
+            flush.fill_(k & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x_dev.copy_(x_host, non_blocking=True)
+            n_out = mcc.compress(plan, x_dev, prm, wsc, out, sync=True)
+            out_host[:n_out].copy_(out[:n_out])
+            in_dev[:n_out].copy_(out_host[:n_out], non_blocking=True)
+            mcc.decompress(plan, in_dev, n_out, y, wsd, sync=False)
+            y_host.copy_(y)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            h2d, d2h = x_np.nbytes + n_out, n_out + x_np.nbytes
+        if not torch.equal(y_host, y.cpu()):
+            raise SystemExit("e2e mismatch")
+        e2e = statistics.mean(e2e_ms)
 
     if rank != 0:
         if world > 1:
@@ -300,28 +350,35 @@ def main():
         return
 
     nbytes = x_np.nbytes
-    # roofline of the dominant kernel
-    W1 = int(out[168:176].cpu().numpy().view(np.uint64)[0])
-    W2 = int(out[176:184].cpu().numpy().view(np.uint64)[0])
+    hdr = out[:192].cpu().numpy()
+    W1 = int(hdr[168:176].view(np.uint64)[0])
+    W2 = int(hdr[176:184].view(np.uint64)[0])
     alg = algorithmic_bytes(len(wl["n"]), x_np.size, int(np.prod(wl["n"])), 8, W1, W2, size)
-    per_kernel = {k: {"ms_per_launch": v[0] / v[1], "launches_per_step": v[1] / args.steps,
-                      "share": v[0] / sum(t for t, _ in prof.values())}
-                  for k, v in prof.items() if v[1]}
-    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_per_launch"] * per_kernel[k]["launches_per_step"])
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    per_kernel = {}
+    if prof:
+        tot = sum(t for t, _ in prof.values())
+        per_kernel = {k: {"ms_per_launch": v[0] / v[1], "launches_per_step": v[1] / args.steps,
+                          "share": v[0] / tot,
+                          "alg_GBps": alg.get(k, 0) / (v[0] / v[1] * 1e-3) / 1e9}
+                      for k, v in prof.items() if v[1]}
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    achieved = alg.get(dom, 0) / (per_kernel[dom]["ms_per_launch"] * 1e-3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    if os.path.exists(tfile):
-        traffic = json.load(open(tfile)).get(dom)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
-                "peak_source": "measured" if peaks else "fallback"}
+    roofline = None
+    if per_kernel:
+        dom = max(per_kernel,
+                  key=lambda k: per_kernel[k]["ms_per_launch"] * per_kernel[k]["launches_per_step"])
+        achieved = alg.get(dom, 0) / (per_kernel[dom]["ms_per_launch"] * 1e-3) / 1e9
+        traffic = None
+        tfile = os.path.join(ROOT, "profiles", "dram_traffic.json")
+        if os.path.exists(tfile):
+            traffic = json.load(open(tfile)).get(dom)
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
+                    "peak_source": "measured" if peaks else "fallback"}
     cpu = None if args.no_cpu_baseline else cpu_baseline(wl, args.eb)
     line = {
-        "metric": "compress+decompress GB/s at eb=1e-4 rel",
+        "metric": METRIC,
         "value": world * nbytes / (ms * 1e-3) / 1e9,
         "unit": "GB/s",
         "n_gpus": world,
@@ -336,14 +393,16 @@ def main():
         "config": {"workload": wl["name"], "n_vertices": int(x_np.size),
                    "grid": list(wl["n"]), "eb_rel": args.eb, "grid_fraction": 0.5,
                    "compression_ratio": nbytes / size, "stream_bytes": int(size),
-                   "max_abs_err_over_tau": err / tau, "l2": "flushed before every step (256 MiB write, untimed)",
-                   "parallelism": f"replicas x{world}"},
+                   "max_abs_err_over_tau": err / tau,
+                   "l2": "flushed before every step (256 MiB write, untimed)",
+                   "cuda_graph": graph is not None, "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "kernels": per_kernel,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * nbytes / (e2e * 1e-3) / 1e9, "unit": "GB/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "e2e": None if e2e is None else {
+            "value": world * nbytes / (e2e * 1e-3) / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": None if launches_per_step is None else int(round(launches_per_step * args.steps)),
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -156,13 +156,16 @@ mcc_status mcc_workspace_result(const void *d_workspace, mcc_stream stream, size
 
 const char *mcc_status_string(mcc_status s);
 
-/* Diagnostics (no counterpart in the paper): per-kernel device timing. When
+/* Diagnostics (no counterpart in the paper): per-kernel device timing. While
  * enabled, every kernel that mcc_compress / mcc_decompress launches is
- * bracketed by CUDA events recorded on its stream. mcc_profile_read
- * synchronises on the recorded events and fills up to max_entries rows of
- * (kernel name, total milliseconds, launches), sorted by name; it returns
- * the number of rows. mcc_profile_reset drops all accumulated rows.
- * Host-side state is process wide and guarded by a mutex. */
+ * bracketed by a pair of CUDA events recorded on its stream; pairs stay
+ * registered until mcc_profile_reset. mcc_profile_read synchronises on the
+ * pairs and fills up to max_entries rows of (kernel name, milliseconds,
+ * launches) summed over each pair's latest recording, sorted by name, and
+ * returns the number of rows. When the bracketed launches were captured into
+ * a CUDA graph, each replay re-records the captured pairs, so a read after a
+ * replay returns that replay's times. Host-side state is process wide and
+ * guarded by a mutex. */
 void mcc_profile_enable(int on);
 void mcc_profile_reset(void);
 int mcc_profile_read(char (*names)[32], double *ms, long long *launches, int max_entries);

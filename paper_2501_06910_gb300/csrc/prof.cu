@@ -1,4 +1,10 @@
 // prof.cu -- per-kernel event timing behind mcc_profile_* (diagnostics).
+// Every bracketed launch registers one (begin, end) event pair that stays
+// registered until mcc_profile_reset. A read sums, per kernel name, the
+// elapsed time of each pair's latest recording: for eager launches every
+// launch owns a pair; when the launches were captured into a CUDA graph, each
+// replay re-records the captured pairs and a read after a replay returns that
+// replay's times.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -14,58 +20,29 @@ namespace mcc {
 bool g_profile_on = false;
 
 namespace {
-struct Pending {
+struct Pair {
   std::string name;
   cudaEvent_t a, b;
-};
-struct Acc {
-  double ms = 0.0;
-  long long n = 0;
+  bool closed;
 };
 std::mutex g_mu;
-std::vector<Pending> g_pending;
-std::vector<cudaEvent_t> g_free;
-std::map<std::string, Acc> g_acc;
-std::map<std::string, size_t> g_open;  // name -> index in g_pending of an open pair
-
-cudaEvent_t take_event() {
-  if (!g_free.empty()) {
-    cudaEvent_t e = g_free.back();
-    g_free.pop_back();
-    return e;
-  }
-  cudaEvent_t e;
-  cudaEventCreate(&e);
-  return e;
-}
-
-void drain() {
-  for (auto &p : g_pending) {
-    float ms = 0.f;
-    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-      Acc &a = g_acc[p.name];
-      a.ms += ms;
-      a.n += 1;
-    }
-    g_free.push_back(p.a);
-    g_free.push_back(p.b);
-  }
-  g_pending.clear();
-  g_open.clear();
-}
+std::vector<Pair> g_pairs;
+std::map<std::string, size_t> g_open;  // name -> index of an open pair
 }  // namespace
 
 void prof_record(const char *name, cudaStream_t s, bool begin) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (begin) {
-    Pending p{name, take_event(), take_event()};
+    Pair p{name, nullptr, nullptr, false};
+    if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) return;
     cudaEventRecord(p.a, s);
-    g_open[name] = g_pending.size();
-    g_pending.push_back(p);
+    g_open[name] = g_pairs.size();
+    g_pairs.push_back(p);
   } else {
     auto it = g_open.find(name);
     if (it == g_open.end()) return;
-    cudaEventRecord(g_pending[it->second].b, s);
+    cudaEventRecord(g_pairs[it->second].b, s);
+    g_pairs[it->second].closed = true;
     g_open.erase(it);
   }
 }
@@ -78,20 +55,34 @@ extern "C" void mcc_profile_enable(int on) {
 
 extern "C" void mcc_profile_reset(void) {
   std::lock_guard<std::mutex> lk(mcc::g_mu);
-  mcc::drain();
-  mcc::g_acc.clear();
+  for (auto &p : mcc::g_pairs) {
+    cudaEventSynchronize(p.b);
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  mcc::g_pairs.clear();
+  mcc::g_open.clear();
 }
 
 extern "C" int mcc_profile_read(char (*names)[32], double *ms, long long *launches, int max_entries) {
   std::lock_guard<std::mutex> lk(mcc::g_mu);
-  mcc::drain();
+  std::map<std::string, std::pair<double, long long>> acc;
+  for (auto &p : mcc::g_pairs) {
+    if (!p.closed) continue;
+    float t = 0.f;
+    if (cudaEventSynchronize(p.b) != cudaSuccess || cudaEventElapsedTime(&t, p.a, p.b) != cudaSuccess)
+      continue;
+    auto &e = acc[p.name];
+    e.first += t;
+    e.second += 1;
+  }
   int i = 0;
-  for (auto &kv : mcc::g_acc) {
+  for (auto &kv : acc) {
     if (i >= max_entries) break;
     strncpy(names[i], kv.first.c_str(), 31);
     names[i][31] = 0;
-    ms[i] = kv.second.ms;
-    launches[i] = kv.second.n;
+    ms[i] = kv.second.first;
+    launches[i] = kv.second.second;
     i++;
   }
   return i;
