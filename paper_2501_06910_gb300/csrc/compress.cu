@@ -428,10 +428,12 @@ __global__ void __launch_bounds__(1024) k_codebook(CodebookArgs a1, CodebookArgs
   if (block_failed(st)) return;
   const CodebookArgs A = blockIdx.x == 0 ? a1 : a2;
   const int nsym = A.nsym;
+  int npn = 1;  // power of two >= nsym: room for the sort's padding
+  while (npn < nsym) npn <<= 1;
   unsigned int *cnt = (unsigned int *)smem;                                // [nsym]
   unsigned long long *keyA = (unsigned long long *)(cnt + nsym);           // [nsym] (nsym even)
-  unsigned long long *sk = keyA + nsym;                                    // [nsym]
-  unsigned long long *Iw = sk + nsym;                                      // [nsym]
+  unsigned long long *sk = keyA + nsym;                                    // [npn]
+  unsigned long long *Iw = sk + npn;                                       // [nsym]
   unsigned short *parent = (unsigned short *)(Iw + nsym);                  // [2 nsym]
   unsigned short *anc1 = parent + 2 * nsym;                                // [2 nsym]
   unsigned short *mid = anc1 + 2 * nsym;                                   // [2 nsym]
@@ -463,14 +465,22 @@ __global__ void __launch_bounds__(1024) k_codebook(CodebookArgs a1, CodebookArgs
     for (int s = tid; s < nsym; s += blockDim.x)
       if (cnt[s]) keyA[atomicAdd(&kpos, 1)] = ((unsigned long long)cnt[s] << 32) | (unsigned)s;
     __syncthreads();
-    // rank sort of the (count, symbol) keys (keys are distinct)
-    for (int i = tid; i < m; i += blockDim.x) {
-      const unsigned long long k = keyA[i];
-      int r = 0;
-      for (int j = 0; j < m; j++) r += keyA[j] < k;
-      sk[r] = k;
-    }
+    // bitonic sort of the (count, symbol) keys into sk (padding sorts last)
+    int npow = 1;
+    while (npow < m) npow <<= 1;
+    for (int i = tid; i < npow; i += blockDim.x) sk[i] = i < m ? keyA[i] : ~0ull;
     __syncthreads();
+    for (int kk = 2; kk <= npow; kk <<= 1)
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < npow; i += blockDim.x) {
+          const int q = i ^ j;
+          if (q > i) {
+            const unsigned long long x0 = sk[i], x1 = sk[q];
+            if ((x0 > x1) == ((i & kk) == 0)) { sk[i] = x1; sk[q] = x0; }
+          }
+        }
+        __syncthreads();
+      }
     for (;;) {
       if (tid == 0) {
         const int a = sa, b = sb, c = sc;
@@ -485,11 +495,11 @@ __global__ void __launch_bounds__(1024) k_codebook(CodebookArgs a1, CodebookArgs
           while (lo < hi) { const int md = (lo + hi) >> 1; if (Iw[md] <= T) lo = md + 1; else hi = md; }
           ni = lo - b;
           if (nl + ni < kBatchMin) {
-            // small batch: single-thread two-queue steps over it (at least one)
-            int steps = (nl + ni) >> 1;
-            if (steps < 1) steps = 1;
+            // small batches: single-thread two-queue steps until a large
+            // batch of leaves becomes available (a heuristic: any stopping
+            // point gives the same tree)
             int aa = a, bb = b, cc = c;
-            for (int s = 0; s < steps && cc < m - 1; s++) {
+            for (int s = 0; s < 512 && cc < m - 1; s++) {
               int id[2];
               unsigned long long w[2];
 #pragma unroll
@@ -502,6 +512,10 @@ __global__ void __launch_bounds__(1024) k_codebook(CodebookArgs a1, CodebookArgs
               parent[id[0]] = (unsigned short)(m + cc);
               parent[id[1]] = (unsigned short)(m + cc);
               cc++;
+              if (cc >= m - 1 || aa + kBatchMin >= m) continue;
+              const unsigned long long tn =
+                  (bb >= cc || (sk[aa] >> 32) <= Iw[bb]) ? (sk[aa] >> 32) : Iw[bb];
+              if ((sk[aa + kBatchMin] >> 32) <= 2 * tn) break;
             }
             sa = aa; sb = bb; sc = cc;
             nl = 0; ni = 0;
@@ -590,8 +604,10 @@ __global__ void __launch_bounds__(1024) k_codebook(CodebookArgs a1, CodebookArgs
 }
 
 size_t codebook_smem(int nsym) {
-  return 4 * (size_t)nsym + 3 * 8 * (size_t)nsym + 3 * 4 * (size_t)nsym + 2 * (size_t)nsym +
-         (size_t)nsym + 16;
+  size_t npn = 1;
+  while (npn < (size_t)nsym) npn <<= 1;
+  return 4 * (size_t)nsym + 8 * (size_t)nsym + 8 * npn + 8 * (size_t)nsym +
+         3 * 4 * (size_t)nsym + 2 * (size_t)nsym + (size_t)nsym + 16;
 }
 
 // ---------------------------------------------------------------------------
@@ -675,38 +691,34 @@ __global__ void __launch_bounds__(256) k_group_len(GroupArgs a, const Status *st
 // ---------------------------------------------------------------------------
 // k_scan: exclusive prefixes over groups, layout and header (one CTA)
 // ---------------------------------------------------------------------------
-__device__ unsigned long long block_exclusive_scan(const unsigned int *in, int64_t n,
-                                                   unsigned int *out, unsigned int *swarp) {
-  // writes out[0..n] (out[n] = total); returns the total
+// Exclusive prefix of n u32 values by one warp (out[0..n], out[n] = total);
+// every lane owns 8 consecutive values of each 256-value chunk.
+__device__ unsigned long long warp_exclusive_scan(const unsigned int *in, int64_t n,
+                                                  unsigned int *out) {
+  const int lane = threadIdx.x & 31;
   unsigned long long carry = 0;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t base = 0; base < n; base += blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    const unsigned int v = i < n ? in[i] : 0u;
-    unsigned int incl = v;
+  for (int64_t base = 0; base < n; base += 256) {
+    unsigned int v[8];
+    const int64_t i0 = base + 8 * lane;
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = i0 + j < n ? __ldg(in + i0 + j) : 0u;
+    unsigned int tot = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) tot += v[j];
+    unsigned int incl = tot;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += t;
     }
-    if (lane == 31) swarp[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-      unsigned int t = lane < nw ? swarp[lane] : 0u;
-      unsigned int s = t;
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int u = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= o) s += u;
-      }
-      if (lane < nw) swarp[lane] = s - t;  // exclusive warp offsets
-      if (lane == 31) swarp[32] = s;      // block total
+    unsigned int run = (unsigned int)carry + incl - tot;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      if (i0 + j < n) out[i0 + j] = run;
+      run += v[j];
     }
-    __syncthreads();
-    if (i < n) out[i] = (unsigned int)(carry + swarp[w] + incl - v);
-    carry += swarp[32];
-    __syncthreads();
+    carry += __shfl_sync(0xffffffffu, incl, 31);
   }
-  if (threadIdx.x == 0) out[n] = (unsigned int)carry;
-  __syncthreads();
+  if (lane == 0) out[n] = (unsigned int)carry;
   return carry;
 }
 
@@ -724,17 +736,21 @@ struct ScanArgs {
 __device__ __forceinline__ void put32(unsigned char *p, uint32_t v) { *(uint32_t *)p = v; }
 __device__ __forceinline__ void put64(unsigned char *p, uint64_t v) { *(uint64_t *)p = v; }
 
-__global__ void __launch_bounds__(1024) k_scan(ScanArgs a, Status *st) {
-  __shared__ unsigned int swarp[33];
+__global__ void __launch_bounds__(160) k_scan(ScanArgs a, Status *st) {
+  __shared__ unsigned long long tot[5];
   if (block_failed(st)) return;
   const Layout F = a.fixed;
   unsigned char *o = a.out;
-  const unsigned long long w1 = block_exclusive_scan(a.gw, a.ng1, (unsigned int *)(o + F.gtab1), swarp);
-  const unsigned long long w2 = block_exclusive_scan(a.gw + a.ng1, a.ng2, (unsigned int *)(o + F.gtab2), swarp);
-  const unsigned long long e1 = block_exclusive_scan(a.ge, a.ng1, (unsigned int *)(o + F.etab1), swarp);
-  const unsigned long long e2 = block_exclusive_scan(a.ge + a.ng1, a.ng2, (unsigned int *)(o + F.etab2), swarp);
-  const unsigned long long r2 = block_exclusive_scan(a.gr + a.ng1, a.ng2, (unsigned int *)(o + F.rtab2), swarp);
+  // five independent prefixes, one warp each
+  const int w = threadIdx.x >> 5;
+  const unsigned int *src[5] = {a.gw, a.gw + a.ng1, a.ge, a.ge + a.ng1, a.gr + a.ng1};
+  const uint64_t dst[5] = {F.gtab1, F.gtab2, F.etab1, F.etab2, F.rtab2};
+  const int64_t cnt[5] = {a.ng1, a.ng2, a.ng1, a.ng2, a.ng2};
+  const unsigned long long t = warp_exclusive_scan(src[w], cnt[w], (unsigned int *)(o + dst[w]));
+  if ((threadIdx.x & 31) == 0) tot[w] = t;
+  __syncthreads();
   if (threadIdx.x != 0) return;
+  const unsigned long long w1 = tot[0], w2 = tot[1], e1 = tot[2], e2 = tot[3], r2 = tot[4];
   const uint64_t vsz = a.dtype == MCC_F64 ? 8 : 4;
   const Layout L = make_layout(a.R1, a.R2, a.ng1, a.ng2, e1, e2, r2, vsz, w1, w2);
   st->L = L;
@@ -1042,7 +1058,7 @@ mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_p
               p->R1, p->R2, p->C1, p->C2, p->lmax, pv.nx, pv.ny, pv.nz, n_v, n_g};
   {
     PROF_SCOPE("k_scan", stream);
-    k_scan<<<1, 1024, 0, stream>>>(sa, st);
+    k_scan<<<1, 160, 0, stream>>>(sa, st);
   }
   const int cmax = p->C1 > p->C2 ? p->C1 : p->C2;
   const size_t stage_bytes = 4 * (size_t)cmax * p->lmax;  // worst-case words of one group

@@ -50,9 +50,7 @@ struct PrepArgs {
   DecTab *tab1, *tab2;
 };
 
-__device__ bool parse_header(const PrepArgs &a, DecInfo &I) {
-  const unsigned char *h = a.in;
-  if (a.in_bytes < kHeaderBytes) return false;
+__device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo &I) {
   if (ld32(h + H_MAGIC) != kMagic || ld32(h + H_VERSION) != kVersion ||
       ld32(h + H_HBYTES) != kHeaderBytes)
     return false;
@@ -109,8 +107,14 @@ __global__ void __launch_bounds__(256) k_dec_prep(PrepArgs a, Status *st) {
   __shared__ unsigned int wcount[32][kMaxLen + 1];
   __shared__ CanonTables ct;
   __shared__ int bad;
+  __shared__ __align__(16) unsigned char hdr[kHeaderBytes];
+  // the header in one round trip (the stream must be at least a header long)
+  const bool has_header = a.in_bytes >= kHeaderBytes;
+  if (has_header && threadIdx.x < kHeaderBytes / 4)
+    ((unsigned int *)hdr)[threadIdx.x] = __ldg((const unsigned int *)a.in + threadIdx.x);
+  __syncthreads();
   if (threadIdx.x == 0) {
-    ok = parse_header(a, I) ? 1 : 0;
+    ok = has_header && parse_header(a, hdr, I) ? 1 : 0;
     bad = 0;
     if (!ok) set_error(st, MCC_ERR_CORRUPT);
     else if (blockIdx.x == 0) *a.info = I;
@@ -255,11 +259,19 @@ __device__ __forceinline__ bool group_setup(const unsigned char *in, uint64_t gt
 // ---------------------------------------------------------------------------
 // k_dec_syms: Huffman decode of both components, one warp per group of 32
 // lane chunks (the first nb1 blocks take the grid component, the rest the
-// residual component; warps stride over their component's groups). Grid
-// symbols become Lorenzo differences (escape values from the escape list);
+// residual component; warps stride over their component's groups).
+//
+// Phase 1: every lane decodes its chunk into shared memory. When one symbol
+// owns the 1-bit code "0" (canonical order gives it the all-zero code), the
+// chunk is pre-filled with it and runs of it are skipped with a count of
+// leading zeros. Phase 2: the warp walks the steps of the group with 32
+// consecutive positions per step: grid symbols become Lorenzo differences,
 // residual symbols become codes q2 (INT32_MIN marks a raw vertex, whose value
-// is written to the output here).
+// is written to the output here); escapes and raw values take their slots
+// from the group's prefixes and a ballot rank.
 // ---------------------------------------------------------------------------
+constexpr int kDecRound = 64;  // steps decoded per shared-memory round
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_dec_syms(const unsigned char *__restrict__ in,
                                                   const DecInfo *__restrict__ info,
@@ -269,27 +281,32 @@ __global__ void __launch_bounds__(256) k_dec_syms(const unsigned char *__restric
                                                   int *__restrict__ q2s, T *__restrict__ xo,
                                                   Status *st) {
   __shared__ DecTab Tb;
+  extern __shared__ unsigned short sbuf[];  // [warps][kDecRound][32]
   if (block_failed(st)) return;
   const DecInfo I = *info;
   const bool c1 = (int)blockIdx.x < nb1;
+  const int64_t ng = c1 ? I.ng1 : I.ng2;
   {  // blocks without a group skip the table load
     const int64_t first = (c1 ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - nb1) * (blockDim.x >> 5);
-    if (first >= (c1 ? I.ng1 : I.ng2)) return;
+    if (first >= ng) return;
   }
   load_tab(&Tb, c1 ? tab1 : tab2, c1 ? 2 * I.R1 : 2 * I.R2);
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t ng = c1 ? I.ng1 : I.ng2;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t n = c1 ? n_g : n_v;
   const int C = c1 ? I.C1 : I.C2, R = c1 ? I.R1 : I.R2, rawsym = 2 * R - 1;
+  const int lmax = I.lmax;
   const int *outv = (const int *)(in + (c1 ? I.L.out1 : I.L.out2));
   const T *rawv = (const T *)(in + I.L.raw);
   int *dst = c1 ? delta : q2s;
   const unsigned lt = (1u << lane) - 1;
+  const bool fast = Tb.count[1] == 1;          // a symbol owns the code "0"
+  const unsigned short s0 = Tb.sorted[0];      // (the first canonical symbol)
+  unsigned short *buf = sbuf + (size_t)wid * kDecRound * 32;
   const int64_t b0 = c1 ? blockIdx.x : blockIdx.x - nb1;
   const int64_t nblocks = c1 ? nb1 : gridDim.x - nb1;
   const int64_t wstride = nblocks * (blockDim.x >> 5);
-  for (int64_t g = b0 * (blockDim.x >> 5) + (threadIdx.x >> 5); g < ng; g += wstride) {
+  for (int64_t g = b0 * (blockDim.x >> 5) + wid; g < ng; g += wstride) {
     BitReader r;
     unsigned int lane_bits, e0, e1, r0 = 0, r1 = 0;
     bool ok = c1 ? group_setup(in, I.L.gtab1, I.L.etab1, I.L.ltab1, I.L.bits1, I.w1, I.nout1, g, r,
@@ -305,46 +322,89 @@ __global__ void __launch_bounds__(256) k_dec_syms(const unsigned char *__restric
       if (lane == 0) set_error(st, MCC_ERR_CORRUPT);
       return;
     }
-    unsigned int e_run = e0, r_run = r0;
+    const int64_t gbase = g * 32 * (int64_t)C;
+    const int64_t left = n - gbase - lane;  // positions of this lane: gbase + lane + 32 k
+    const int cnt = left <= 0 ? 0 : (int)min((int64_t)C, (left + 31) / 32);
     bool lane_bad = false;
-    for (int k = 0; k < C; k++) {
-      const int64_t p0 = g * 32 * (int64_t)C + 32 * (int64_t)k;
-      if (p0 >= n) break;
-      const int64_t p = p0 + lane;
-      const bool valid = p < n;
-      int sym = -2;
-      if (valid && !lane_bad) {
-        sym = decode_one(r, Tb, I.lmax);
-        if (sym < 0 || (c1 && sym == rawsym)) lane_bad = true;
+    unsigned int used = 0, e_run = e0, r_run = r0;
+    int k = 0;
+    for (int kb = 0; kb < C; kb += kDecRound) {
+      const int kend = min(cnt, kb + kDecRound);
+      // ---- phase 1: decode this round of the lane's chunk into shared memory
+      if (fast)
+        for (int j = kb; j < kend; j++) buf[(j - kb) * 32 + lane] = s0;
+      while (k < kend && !lane_bad) {
+        r.refill();
+        const unsigned int win = (unsigned int)(r.buf >> 32);
+        if (fast && !(win >> 31)) {
+          int z = win ? __clz(win) : 32;  // a run of the symbol coded "0"
+          z = min(z, kend - k);
+          r.buf <<= z;
+          r.nb -= z;
+          used += z;
+          k += z;
+          continue;
+        }
+        const unsigned int e = Tb.lut[win >> (32 - kLutBits)];
+        int len = (int)(e & 0xFF), sym;
+        if (len) {
+          sym = (int)(e >> 8);
+        } else {
+          sym = -1;
+          for (int l = kLutBits + 1; l <= lmax; l++) {
+            const unsigned int c = win >> (32 - l);
+            if (c - Tb.first[l] < Tb.count[l]) {
+              sym = Tb.sorted[Tb.offset[l] + c - Tb.first[l]];
+              len = l;
+              break;
+            }
+          }
+          if (sym < 0) { lane_bad = true; break; }
+        }
+        r.buf <<= len;
+        r.nb -= len;
+        used += len;
+        buf[(k - kb) * 32 + lane] = (unsigned short)sym;
+        k++;
       }
-      const bool good = valid && !lane_bad;
-      const bool esc = good && sym == 0;
-      const bool raw = good && !c1 && sym == rawsym;
-      const unsigned em = __ballot_sync(0xffffffffu, esc);
-      const unsigned rm = __ballot_sync(0xffffffffu, raw);
-      int v = 0;
-      if (esc) {
-        const unsigned int idx = e_run + __popc(em & lt);
-        if (idx < e1) v = __ldg(outv + idx);
-        else lane_bad = true;
-        if (!c1 && v == INT_MIN) lane_bad = true;  // never an escape value
-      } else if (raw) {
-        const unsigned int idx = r_run + __popc(rm & lt);
-        if (idx < r1) xo[p] = rawv[idx];
-        else lane_bad = true;
-        v = INT_MIN;
-      } else if (good) {
-        v = sym - R;
+      __syncwarp();
+      // ---- phase 2: emit 32 consecutive positions per step
+      for (int kk = kb; kk < kb + kDecRound && kk < C; kk++) {
+        const int64_t p0 = gbase + 32 * (int64_t)kk;
+        if (p0 >= n) break;
+        const bool valid = kk < cnt;
+        const int sym = valid ? buf[(kk - kb) * 32 + lane] : -1;
+        const bool esc = sym == 0;
+        const bool raw = !c1 && sym == rawsym;
+        const unsigned em = __ballot_sync(0xffffffffu, esc);
+        const unsigned rm = __ballot_sync(0xffffffffu, raw);
+        int v = sym - R;
+        if (esc) {
+          const unsigned int idx = e_run + __popc(em & lt);
+          v = 0;
+          if (idx < e1) v = __ldg(outv + idx);
+          else lane_bad = true;
+          if (!c1 && v == INT_MIN) lane_bad = true;  // never an escape value
+        } else if (raw) {
+          const unsigned int idx = r_run + __popc(rm & lt);
+          if (idx < r1) xo[p0 + lane] = rawv[idx];
+          else lane_bad = true;
+          v = INT_MIN;
+        } else if (c1 && sym == rawsym) {
+          lane_bad = true;
+        }
+        e_run += __popc(em);
+        r_run += __popc(rm);
+        if (valid) dst[p0 + lane] = v;
       }
-      e_run += __popc(em);
-      r_run += __popc(rm);
-      if (valid) dst[p] = v;
+      __syncwarp();
     }
-    if (lane_bad || r.consumed != lane_bits) lane_bad = true;
+    if (used != lane_bits) lane_bad = true;
     if (__any_sync(0xffffffffu, lane_bad) || e_run != e1 || r_run != r1) {
       if (lane == 0) set_error(st, MCC_ERR_CORRUPT);
       return;
     }
+    __syncwarp();
   }
 }
 
@@ -476,10 +536,17 @@ mcc_status launch_decompress(const PlanView &pv, const unsigned char *in, size_t
   const unsigned int nb2 = nblk(max_g2, 8) < cap ? nblk(max_g2, 8) : cap;
   {
     PROF_SCOPE("k_dec_syms", stream);
+    const size_t sm = (size_t)8 * kDecRound * 32 * sizeof(unsigned short);  // [warps][round][32]
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_dec_syms<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_dec_syms<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
     if (dtype == MCC_F64)
-      k_dec_syms<double><<<nb1 + nb2, 256, 0, stream>>>(in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (double *)d_values, st);
+      k_dec_syms<double><<<nb1 + nb2, 256, sm, stream>>>(in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (double *)d_values, st);
     else
-      k_dec_syms<float><<<nb1 + nb2, 256, 0, stream>>>(in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (float *)d_values, st);
+      k_dec_syms<float><<<nb1 + nb2, 256, sm, stream>>>(in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (float *)d_values, st);
   }
   const int64_t nrows = (int64_t)pv.ny * pv.nz;
   {

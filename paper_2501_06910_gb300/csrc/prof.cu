@@ -30,18 +30,27 @@ std::vector<Pair> g_pairs;
 std::map<std::string, size_t> g_open;  // name -> index of an open pair
 }  // namespace
 
+// Inside stream capture an event record becomes a timing node of the graph
+// only with cudaEventRecordExternal.
+static void record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, s);
+}
+
 void prof_record(const char *name, cudaStream_t s, bool begin) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (begin) {
     Pair p{name, nullptr, nullptr, false};
     if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) return;
-    cudaEventRecord(p.a, s);
+    record(p.a, s);
     g_open[name] = g_pairs.size();
     g_pairs.push_back(p);
   } else {
     auto it = g_open.find(name);
     if (it == g_open.end()) return;
-    cudaEventRecord(g_pairs[it->second].b, s);
+    record(g_pairs[it->second].b, s);
     g_pairs[it->second].closed = true;
     g_open.erase(it);
   }
