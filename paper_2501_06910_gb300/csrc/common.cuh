@@ -12,6 +12,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <utility>
+
 #include "../../include/mcc.h"
 
 namespace mcc {
@@ -27,7 +29,7 @@ constexpr double kBinShrink = 1.0 - 1.0 / 1048576.0;  // bins are 2 tau (1 - 2^-
 constexpr int kMaxR = 2048;
 constexpr int kMaxC = 256;
 constexpr int kMaxLen = 24;
-constexpr int kLutBits = 11;               // first-level decode table
+constexpr int kLutBits = 12;               // first-level decode table (two symbols per entry)
 
 // header byte offsets
 enum : uint32_t {
@@ -288,3 +290,32 @@ __device__ inline void canonical_tables(const unsigned char *len, int nsym, Cano
 
 // Device view of a plan's tables (defined in plan.cu).
 mcc::PlanView mcc_plan_view(mcc_plan P);
+
+namespace mcc {
+// ---------------------------------------------------------------------------
+// programmatic dependent launch: every kernel of a compress / decompress chain
+// is launched with programmatic stream serialisation, lets its dependent
+// start launching at once (launch_dependents), and waits for its
+// predecessor's completion and memory (griddepcontrol.wait) before touching
+// anything the predecessor writes. Kernels launched without the attribute
+// pass through both instructions unchanged.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(std::forward<Args>(args))...);
+}
+}  // namespace mcc

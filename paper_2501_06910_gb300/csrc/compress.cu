@@ -100,6 +100,8 @@ __device__ void field_params(Status *st, RParams rp) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_reduce(const T *__restrict__ x, int64_t n, Status *st,
                                                 RParams rp, unsigned int *hist, int nhist) {
+  pdl_trigger();
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nhist; i += gridDim.x * blockDim.x)
     hist[i] = 0;
   unsigned long long mn = 0, mx = 0;  // mn holds ~key (max of ~key = min key)
@@ -165,6 +167,8 @@ __global__ void __launch_bounds__(256) k_reduce(const T *__restrict__ x, int64_t
 template <typename T>
 __global__ void __launch_bounds__(256) k_prequant(const T *__restrict__ x, int64_t n,
                                                   const Status *__restrict__ st, int *__restrict__ Q) {
+  pdl_trigger();
+  pdl_wait();
   if (st->err) return;
   const double inv2 = st->f.inv2;
   const long long K = st->f.K;
@@ -217,6 +221,8 @@ __global__ void __launch_bounds__(256) k_grid2d(PlanView pv, const int *__restri
                                                 Status *st, int R1, int *__restrict__ q1,
                                                 unsigned short *__restrict__ sym1,
                                                 int *__restrict__ val1, unsigned int *hist1) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ unsigned int shist[];
   __shared__ int s[TY + 1][TX + 1];
   if (block_failed(st)) return;
@@ -270,6 +276,8 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(PlanView pv, const int *__res
                                                    Status *st, int R1, int *__restrict__ q1,
                                                    unsigned short *__restrict__ sym1,
                                                    int *__restrict__ val1, unsigned int *hist1) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ unsigned int shist[];
   __shared__ int s[2][TY + 1][TX + 1];
   if (block_failed(st)) return;
@@ -340,6 +348,8 @@ __global__ void __launch_bounds__(256) k_node(PlanView pv, const T *__restrict__
                                               const int *__restrict__ Q, const int *__restrict__ q1,
                                               Status *st, int R2, unsigned short *__restrict__ sym2,
                                               int *__restrict__ val2, unsigned int *hist2) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ unsigned int shist[];
   if (block_failed(st)) return;
   const int nsym = 2 * R2;
@@ -422,8 +432,10 @@ __device__ __forceinline__ unsigned long long node_w(int e, int m, const unsigne
   return e < m ? (sk[e] >> 32) : Iw[e - m];
 }
 
-__global__ void __launch_bounds__(1024) k_codebook(CodebookArgs a1, CodebookArgs a2, int lmax,
+__global__ void __launch_bounds__(256) k_codebook(CodebookArgs a1, CodebookArgs a2, int lmax,
                                                    Status *st) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   if (block_failed(st)) return;
   const CodebookArgs A = blockIdx.x == 0 ? a1 : a2;
@@ -630,6 +642,8 @@ struct GroupArgs {
 };
 
 __global__ void __launch_bounds__(256) k_group_len(GroupArgs a, const Status *st) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ unsigned char L[2 * kMaxR];
   __shared__ unsigned int sbits[kParts][32];
   __shared__ unsigned int sesc[kParts], sraw[kParts];
@@ -737,6 +751,8 @@ __device__ __forceinline__ void put32(unsigned char *p, uint32_t v) { *(uint32_t
 __device__ __forceinline__ void put64(unsigned char *p, uint64_t v) { *(uint64_t *)p = v; }
 
 __global__ void __launch_bounds__(160) k_scan(ScanArgs a, Status *st) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ unsigned long long tot[5];
   if (block_failed(st)) return;
   const Layout F = a.fixed;
@@ -816,6 +832,8 @@ struct PackArgs {
 };
 
 __global__ void __launch_bounds__(256) k_pack(PackArgs a, const Status *st) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ unsigned int stage[];
   __shared__ unsigned int scode[2 * kMaxR];
   __shared__ unsigned char slen[2 * kMaxR];
@@ -982,7 +1000,7 @@ mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_p
     }
     {
       PROF_SCOPE("k_prequant", stream);
-      k_prequant<double><<<(unsigned int)sms * 8, 256, 0, stream>>>((const double *)d_values, n_v, st, Q);
+      launch_pdl(k_prequant<double>, dim3((unsigned int)sms * 8), dim3(256), 0, stream, (const double *)d_values, n_v, st, Q);
     }
   } else {
     {
@@ -991,7 +1009,7 @@ mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_p
     }
     {
       PROF_SCOPE("k_prequant", stream);
-      k_prequant<float><<<(unsigned int)sms * 8, 256, 0, stream>>>((const float *)d_values, n_v, st, Q);
+      launch_pdl(k_prequant<float>, dim3((unsigned int)sms * 8), dim3(256), 0, stream, (const float *)d_values, n_v, st, Q);
     }
   }
   const size_t hsm1 = 4 * (size_t)nsym1, hsm2 = 4 * (size_t)nsym2;
@@ -999,13 +1017,13 @@ mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_p
     dim3 grid((pv.nx + 63) / 64, (pv.ny + 15) / 16);
     {
       PROF_SCOPE("k_grid2d", stream);
-      k_grid2d<64, 16><<<grid, 256, hsm1, stream>>>(pv, Q, st, p->R1, q1, sym1, val1, hist1);
+      launch_pdl(k_grid2d<64, 16>, dim3(grid), dim3(256), hsm1, stream, pv, Q, st, p->R1, q1, sym1, val1, hist1);
     }
   } else {
     dim3 grid((pv.nx + 31) / 32, (pv.ny + 7) / 8, (pv.nz + 7) / 8);
     {
       PROF_SCOPE("k_grid3d", stream);
-      k_grid3d<32, 8, 8><<<grid, 256, hsm1, stream>>>(pv, Q, st, p->R1, q1, sym1, val1, hist1);
+      launch_pdl(k_grid3d<32, 8, 8>, dim3(grid), dim3(256), hsm1, stream, pv, Q, st, p->R1, q1, sym1, val1, hist1);
     }
   }
   const unsigned int nblocks_node = (unsigned int)sms * 8;
@@ -1013,23 +1031,23 @@ mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_p
     if (p->dtype == MCC_F64)
       {
         PROF_SCOPE("k_node", stream);
-        k_node<2, double><<<nblocks_node, 256, hsm2, stream>>>(pv, (const double *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
+        launch_pdl(k_node<2, double>, dim3(nblocks_node), dim3(256), hsm2, stream, pv, (const double *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
       }
     else
       {
         PROF_SCOPE("k_node", stream);
-        k_node<2, float><<<nblocks_node, 256, hsm2, stream>>>(pv, (const float *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
+        launch_pdl(k_node<2, float>, dim3(nblocks_node), dim3(256), hsm2, stream, pv, (const float *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
       }
   } else {
     if (p->dtype == MCC_F64)
       {
         PROF_SCOPE("k_node", stream);
-        k_node<3, double><<<nblocks_node, 256, hsm2, stream>>>(pv, (const double *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
+        launch_pdl(k_node<3, double>, dim3(nblocks_node), dim3(256), hsm2, stream, pv, (const double *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
       }
     else
       {
         PROF_SCOPE("k_node", stream);
-        k_node<3, float><<<nblocks_node, 256, hsm2, stream>>>(pv, (const float *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
+        launch_pdl(k_node<3, float>, dim3(nblocks_node), dim3(256), hsm2, stream, pv, (const float *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
       }
   }
   CodebookArgs a1{hist1, nsym1, (unsigned int *)(ws + W.code1), ws + W.len1, out + F.lens1};
@@ -1043,7 +1061,7 @@ mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_p
   }
   {
     PROF_SCOPE("k_codebook", stream);
-    k_codebook<<<2, 1024, cbsm, stream>>>(a1, a2, p->lmax, st);
+    launch_pdl(k_codebook, dim3(2), dim3(256), cbsm, stream, a1, a2, p->lmax, st);
   }
   GroupArgs ga{sym1, sym2, ws + W.len1, ws + W.len2, n_g, n_v, ng1, ng2, p->C1, p->C2, nsym1, nsym2,
                (unsigned short *)(out + F.ltab1), (unsigned short *)(out + F.ltab2),
@@ -1051,14 +1069,14 @@ mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_p
                (unsigned short *)(ws + W.pb), (unsigned int *)(ws + W.pe), (unsigned int *)(ws + W.pr)};
   {
     PROF_SCOPE("k_group_len", stream);
-    k_group_len<<<(unsigned int)(ng1 + ng2), 256, 0, stream>>>(ga, st);
+    launch_pdl(k_group_len, dim3((unsigned int)(ng1 + ng2)), dim3(256), 0, stream, ga, st);
   }
   ScanArgs sa{(const unsigned int *)(ws + W.gw), (const unsigned int *)(ws + W.ge),
               (const unsigned int *)(ws + W.gr), ng1, ng2, out, capacity, F, p->dtype, pv.dim,
               p->R1, p->R2, p->C1, p->C2, p->lmax, pv.nx, pv.ny, pv.nz, n_v, n_g};
   {
     PROF_SCOPE("k_scan", stream);
-    k_scan<<<1, 160, 0, stream>>>(sa, st);
+    launch_pdl(k_scan, dim3(1), dim3(160), 0, stream, sa, st);
   }
   const int cmax = p->C1 > p->C2 ? p->C1 : p->C2;
   const size_t stage_bytes = 4 * (size_t)cmax * p->lmax;  // worst-case words of one group
@@ -1068,7 +1086,7 @@ mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_p
               (const unsigned int *)(ws + W.pe), (const unsigned int *)(ws + W.pr)};
   {
     PROF_SCOPE("k_pack", stream);
-    k_pack<<<(unsigned int)(ng1 + ng2), 256, stage_bytes, stream>>>(pa, st);
+    launch_pdl(k_pack, dim3((unsigned int)(ng1 + ng2)), dim3(256), stage_bytes, stream, pa, st);
   }
   if (cudaGetLastError() != cudaSuccess) return MCC_ERR_CUDA;
   return MCC_OK;

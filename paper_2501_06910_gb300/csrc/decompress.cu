@@ -100,6 +100,8 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
 }
 
 __global__ void __launch_bounds__(256) k_dec_prep(PrepArgs a, Status *st) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ DecInfo I;
   __shared__ int ok;
   __shared__ unsigned char lens[2 * kMaxR];
@@ -147,6 +149,9 @@ __global__ void __launch_bounds__(256) k_dec_prep(PrepArgs a, Status *st) {
     T->offset[threadIdx.x] = ct.offset[threadIdx.x];
   }
   __syncthreads();
+  // first-level table: entry = l1 | l2 << 4 | sym1 << 8 | sym2 << 20 for the
+  // one or two complete codes at the front of a kLutBits-bit window (l1 = 0:
+  // the first code is longer than the window; l2 = 0: no second code fits)
   const int lb = I.lmax < kLutBits ? I.lmax : kLutBits;
   for (int e = threadIdx.x; e < (1 << kLutBits); e += blockDim.x) {
     unsigned int v = 0;
@@ -154,6 +159,14 @@ __global__ void __launch_bounds__(256) k_dec_prep(PrepArgs a, Status *st) {
       const unsigned int c = (unsigned int)e >> (kLutBits - l);
       if (c - ct.first[l] < ct.count[l]) {
         v = ((unsigned int)T->sorted[ct.offset[l] + c - ct.first[l]] << 8) | (unsigned int)l;
+        const unsigned int rest = ((unsigned int)e << l) & ((1u << kLutBits) - 1);
+        for (int l2 = 1; l2 <= lb && l + l2 <= kLutBits; l2++) {
+          const unsigned int c2 = rest >> (kLutBits - l2);
+          if (c2 - ct.first[l2] < ct.count[l2]) {
+            v |= ((unsigned int)T->sorted[ct.offset[l2] + c2 - ct.first[l2]] << 20) | ((unsigned int)l2 << 4);
+            break;
+          }
+        }
         break;
       }
     }
@@ -195,32 +208,6 @@ struct BitReader {
     }
   }
 };
-
-// Decode one symbol; returns -1 for an invalid code.
-__device__ __forceinline__ int decode_one(BitReader &r, const DecTab &T, int lmax) {
-  r.refill();
-  const unsigned int win = (unsigned int)(r.buf >> 32);
-  const unsigned int e = T.lut[win >> (32 - kLutBits)];
-  int len = (int)(e & 0xFF), sym;
-  if (len) {
-    sym = (int)(e >> 8);
-  } else {
-    sym = -1;
-    for (int l = kLutBits + 1; l <= lmax; l++) {
-      const unsigned int c = win >> (32 - l);
-      if (c - T.first[l] < T.count[l]) {
-        sym = T.sorted[T.offset[l] + c - T.first[l]];
-        len = l;
-        break;
-      }
-    }
-    if (sym < 0) return -1;
-  }
-  r.buf <<= len;
-  r.nb -= len;
-  r.consumed += (unsigned int)len;
-  return sym;
-}
 
 __device__ __forceinline__ void load_tab(DecTab *dst, const DecTab *src, int nsym) {
   for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) dst->lut[i] = src->lut[i];
@@ -280,6 +267,8 @@ __global__ void __launch_bounds__(256) k_dec_syms(const unsigned char *__restric
                                                   int64_t n_g, int64_t n_v, int *__restrict__ delta,
                                                   int *__restrict__ q2s, T *__restrict__ xo,
                                                   Status *st) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ DecTab Tb;
   extern __shared__ unsigned short sbuf[];  // [warps][kDecRound][32]
   if (block_failed(st)) return;
@@ -346,9 +335,16 @@ __global__ void __launch_bounds__(256) k_dec_syms(const unsigned char *__restric
           continue;
         }
         const unsigned int e = Tb.lut[win >> (32 - kLutBits)];
-        int len = (int)(e & 0xFF), sym;
+        int len = (int)(e & 15), sym;
         if (len) {
-          sym = (int)(e >> 8);
+          sym = (int)((e >> 8) & 0xFFF);
+          const int l2 = (int)((e >> 4) & 15);
+          if (l2 && k + 1 < kend) {  // a second complete code in the window
+            buf[(k - kb) * 32 + lane] = (unsigned short)sym;
+            k++;
+            sym = (int)(e >> 20);
+            len += l2;
+          }
         } else {
           sym = -1;
           for (int l = kLutBits + 1; l <= lmax; l++) {
@@ -412,6 +408,8 @@ __global__ void __launch_bounds__(256) k_dec_syms(const unsigned char *__restric
 // inverse Lorenzo: inclusive prefix sums (wrapping int32 arithmetic)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_scan_rows(int *q, int nx, int64_t nrows, const Status *st) {
+  pdl_trigger();
+  pdl_wait();
   if (*(volatile const unsigned int *)&st->err) return;
   const int lane = threadIdx.x & 31;
   const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -436,6 +434,8 @@ __global__ void __launch_bounds__(256) k_scan_rows(int *q, int nx, int64_t nrows
 // consecutive columns x 8 warps, each warp scanning one segment of the axis.
 __global__ void __launch_bounds__(256) k_scan_axis(int *q, int64_t n_inner, int64_t n_outer,
                                                    int64_t plane, int L, int64_t S, const Status *st) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ unsigned int part[8][33];
   if (*(volatile const unsigned int *)&st->err) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -468,6 +468,8 @@ __global__ void __launch_bounds__(256) k_recon(const DecInfo *__restrict__ info,
                                                const int *__restrict__ q1,
                                                const int *__restrict__ q2s, T *__restrict__ xo,
                                                const Status *st) {
+  pdl_trigger();
+  pdl_wait();
   if (*(volatile const unsigned int *)&st->err) return;
   const DecInfo I = *info;
   const int64_t n = pv.n_v;
@@ -544,35 +546,35 @@ mcc_status launch_decompress(const PlanView &pv, const unsigned char *in, size_t
       attr = true;
     }
     if (dtype == MCC_F64)
-      k_dec_syms<double><<<nb1 + nb2, 256, sm, stream>>>(in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (double *)d_values, st);
+      launch_pdl(k_dec_syms<double>, dim3(nb1 + nb2), dim3(256), sm, stream, in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (double *)d_values, st);
     else
-      k_dec_syms<float><<<nb1 + nb2, 256, sm, stream>>>(in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (float *)d_values, st);
+      launch_pdl(k_dec_syms<float>, dim3(nb1 + nb2), dim3(256), sm, stream, in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (float *)d_values, st);
   }
   const int64_t nrows = (int64_t)pv.ny * pv.nz;
   {
     PROF_SCOPE("k_scan_rows", stream);
-    k_scan_rows<<<nblk(nrows, 8), 256, 0, stream>>>(q1, pv.nx, nrows, st);
+    launch_pdl(k_scan_rows, dim3(nblk(nrows, 8)), dim3(256), 0, stream, q1, pv.nx, nrows, st);
   }
   {  // y: columns (x, z), stride nx
     PROF_SCOPE("k_scan_axis", stream);
     const int64_t blocks = (pv.nx + 31) / 32 * (int64_t)pv.nz;
-    k_scan_axis<<<(unsigned int)blocks, 256, 0, stream>>>(q1, pv.nx, pv.nz, (int64_t)pv.nx * pv.ny,
+    launch_pdl(k_scan_axis, dim3((unsigned int)blocks), dim3(256), 0, stream, q1, pv.nx, pv.nz, (int64_t)pv.nx * pv.ny,
                                                          pv.ny, pv.nx, st);
   }
   if (pv.dim == 3) {  // z: columns (x, y), stride nx ny
     PROF_SCOPE("k_scan_axis", stream);
     const int64_t ninner = (int64_t)pv.nx * pv.ny;
-    k_scan_axis<<<(unsigned int)((ninner + 31) / 32), 256, 0, stream>>>(q1, ninner, 1, 0, pv.nz, ninner, st);
+    launch_pdl(k_scan_axis, dim3((unsigned int)((ninner + 31) / 32)), dim3(256), 0, stream, q1, ninner, 1, 0, pv.nz, ninner, st);
   }
   {
     PROF_SCOPE("k_recon", stream);
     const unsigned int rb = (unsigned int)sms * 8;
     if (pv.dim == 2) {
-      if (dtype == MCC_F64) k_recon<2, double><<<rb, 256, 0, stream>>>(info, pv, q1, q2s, (double *)d_values, st);
-      else k_recon<2, float><<<rb, 256, 0, stream>>>(info, pv, q1, q2s, (float *)d_values, st);
+      if (dtype == MCC_F64) launch_pdl(k_recon<2, double>, dim3(rb), dim3(256), 0, stream, info, pv, q1, q2s, (double *)d_values, st);
+      else launch_pdl(k_recon<2, float>, dim3(rb), dim3(256), 0, stream, info, pv, q1, q2s, (float *)d_values, st);
     } else {
-      if (dtype == MCC_F64) k_recon<3, double><<<rb, 256, 0, stream>>>(info, pv, q1, q2s, (double *)d_values, st);
-      else k_recon<3, float><<<rb, 256, 0, stream>>>(info, pv, q1, q2s, (float *)d_values, st);
+      if (dtype == MCC_F64) launch_pdl(k_recon<3, double>, dim3(rb), dim3(256), 0, stream, info, pv, q1, q2s, (double *)d_values, st);
+      else launch_pdl(k_recon<3, float>, dim3(rb), dim3(256), 0, stream, info, pv, q1, q2s, (float *)d_values, st);
     }
   }
   if (cudaGetLastError() != cudaSuccess) return MCC_ERR_CUDA;
