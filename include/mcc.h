@@ -150,6 +150,35 @@ mcc_status mcc_decompress(mcc_plan plan, const void *d_in, size_t in_bytes, void
                           int dtype, void *d_workspace, size_t workspace_bytes, int sync,
                           mcc_stream stream);
 
+/* Batched form of Algorithms 3 and 4 for many variables / timesteps on one
+ * mesh (Sec. IV-B: the mapping is computed once and reused across variables
+ * and timesteps). Field f is compressed from d_values[f] (a HOST array of n
+ * device pointers) with per_field[f] (a host array; eb_mode, eb and
+ * grid_fraction may differ per field, dtype, R1, R2, C1, C2 and lmax must
+ * equal per_field[0]'s) into the slot d_out + f * slot_bytes (slot_bytes a
+ * multiple of 8 and >= mcc_compress_bound). Fields run in launch chains of up
+ * to 64 whose kernels carry a field dimension, so latency-bound stages (code
+ * books, decode tables, Huffman decoding) of different fields overlap and the
+ * fields share plan tiles in L2. The workspace holds one compression
+ * workspace (mcc_workspace_size) per field of a chain: workspace_bytes /
+ * that size fields per chain, at least one. If out_sizes (host, n entries) is
+ * non-NULL the call synchronises and fills it; device-side errors are then
+ * returned (the first one found). */
+mcc_status mcc_compress_batch(mcc_plan plan, int n, const void *const *d_values,
+                              const mcc_params *per_field, void *d_workspace,
+                              size_t workspace_bytes, void *d_out, size_t slot_bytes,
+                              size_t *out_sizes, mcc_stream stream);
+
+/* Batched Algorithm 4: field f decodes in_bytes[f] (host array) bytes at
+ * d_in + f * slot_bytes into d_values[f] (host array of n device pointers,
+ * n_vertices values of dtype each). The workspace holds one decompression
+ * workspace per field of a chain of up to 64. If sync is nonzero the call
+ * synchronises and returns the first device-side error. */
+mcc_status mcc_decompress_batch(mcc_plan plan, int n, const void *d_in, size_t slot_bytes,
+                                const size_t *in_bytes, void *const *d_values, int dtype,
+                                void *d_workspace, size_t workspace_bytes, int sync,
+                                mcc_stream stream);
+
 /* Synchronise the stream and read the status (and, after a compression, the
  * stream size; may be NULL) that the last call recorded in the workspace. */
 mcc_status mcc_workspace_result(const void *d_workspace, mcc_stream stream, size_t *out_size);

@@ -21,7 +21,8 @@ from .native_build import LIB, build
 __all__ = [
     "MCCError", "Params", "Plan", "load", "build", "params_default", "plan_create",
     "compress", "decompress", "compress_bound", "workspace_size", "workspace_result",
-    "status_string", "profile_enable", "profile_reset", "profile_read",
+    "status_string", "profile_enable", "profile_reset", "profile_read", "compress_batch",
+    "decompress_batch",
 ]
 
 OK, INVALID_ARG, CUDA, OOM, RANGE, CORRUPT, CAPACITY, TIMEOUT, UNSUPPORTED = range(9)
@@ -88,6 +89,12 @@ def load():
             lib.mcc_compress.argtypes = [P, P, C.POINTER(Params), P, S, P, S, C.POINTER(S), P]
             lib.mcc_decompress.argtypes = [P, P, S, P, C.c_int, P, S, C.c_int, P]
             lib.mcc_workspace_result.argtypes = [P, P, C.POINTER(S)]
+            lib.mcc_compress_batch.argtypes = [P, C.c_int, C.POINTER(P), C.POINTER(Params), P, S, P,
+                                               S, C.POINTER(S), P]
+            lib.mcc_decompress_batch.argtypes = [P, C.c_int, P, S, C.POINTER(S), C.POINTER(P),
+                                                 C.c_int, P, S, C.c_int, P]
+            lib.mcc_compress_batch.restype = C.c_int
+            lib.mcc_decompress_batch.restype = C.c_int
             lib.mcc_profile_enable.argtypes = [C.c_int]
             lib.mcc_profile_enable.restype = None
             lib.mcc_profile_reset.argtypes = []
@@ -258,3 +265,32 @@ def profile_read(max_entries: int = 64):
     n = (C.c_longlong * max_entries)()
     k = load().mcc_profile_read(C.cast(names, C.c_void_p), ms, n, max_entries)
     return {bytes(names[i]).split(b"\0")[0].decode(): (ms[i], n[i]) for i in range(k)}
+
+
+def compress_batch(plan: Plan, xs, params, workspace: torch.Tensor, out: torch.Tensor,
+                   slot_bytes: int, sync: bool = True, stream=None):
+    """mcc_compress_batch: field f of ``xs`` (device tensors) with ``params[f]``
+    into ``out[f * slot_bytes:]``. Returns the stream sizes when ``sync``."""
+    n = len(xs)
+    ptrs = (C.c_void_p * n)(*[_dptr(x).value for x in xs])
+    prm = (Params * n)(*params)
+    sizes = (C.c_size_t * n)()
+    st = load().mcc_compress_batch(plan.handle, n, ptrs, prm, _dptr(workspace), workspace.numel(),
+                                   _dptr(out), int(slot_bytes), sizes if sync else None,
+                                   _stream(stream))
+    _check(st, "compress_batch")
+    return [int(v) for v in sizes] if sync else None
+
+
+def decompress_batch(plan: Plan, stream_bytes: torch.Tensor, slot_bytes: int, in_bytes, outs,
+                     workspace: torch.Tensor, sync: bool = True, stream=None):
+    """mcc_decompress_batch: field f from ``stream_bytes[f * slot_bytes:]``
+    (``in_bytes[f]`` bytes) into ``outs[f]``."""
+    n = len(outs)
+    ptrs = (C.c_void_p * n)(*[_dptr(y).value for y in outs])
+    nb = (C.c_size_t * n)(*[int(v) for v in in_bytes])
+    dtype = F64 if outs[0].dtype == torch.float64 else F32
+    st = load().mcc_decompress_batch(plan.handle, n, _dptr(stream_bytes), int(slot_bytes), nb, ptrs,
+                                     dtype, _dptr(workspace), workspace.numel(), 1 if sync else 0,
+                                     _stream(stream))
+    _check(st, "decompress_batch")

@@ -3,6 +3,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <new>
+
 #include "common.cuh"
 #include "workspace.cuh"
 
@@ -109,5 +111,97 @@ extern "C" mcc_status mcc_decompress(mcc_plan plan, const void *d_in, size_t in_
                                           (unsigned char *)d_ws, stream);
   if (st) return st;
   if (sync) return read_status(d_ws, stream, nullptr);
+  return MCC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched forms
+// ---------------------------------------------------------------------------
+static mcc_status read_batch_status(const unsigned char *ws0, size_t wss, int n, cudaStream_t stream,
+                                    size_t *sizes) {
+  Status *h = new (std::nothrow) Status[n];
+  if (!h) return MCC_ERR_OOM;
+  mcc_status r = MCC_OK;
+  if (cudaMemcpy2DAsync(h, sizeof(Status), ws0, wss, sizeof(Status), (size_t)n,
+                        cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess) {
+    r = MCC_ERR_CUDA;
+  } else {
+    for (int f = 0; f < n; f++) {
+      if (sizes) sizes[f] = (size_t)h[f].out_size;
+      if (r == MCC_OK && h[f].err) r = (mcc_status)h[f].err;
+    }
+  }
+  delete[] h;
+  return r;
+}
+
+extern "C" mcc_status mcc_compress_batch(mcc_plan plan, int n, const void *const *d_values,
+                                         const mcc_params *per_field, void *d_ws, size_t ws_bytes,
+                                         void *d_out, size_t slot_bytes, size_t *out_sizes,
+                                         mcc_stream s) {
+  if (!plan || n < 1 || !d_values || !per_field || !d_ws || !d_out) return MCC_ERR_INVALID_ARG;
+  const mcc_params *p0 = per_field;
+  for (int f = 0; f < n; f++) {
+    const mcc_status st = check_params(per_field + f);
+    if (st) return st;
+    const mcc_params *p = per_field + f;
+    if (p->dtype != p0->dtype || p->R1 != p0->R1 || p->R2 != p0->R2 || p->C1 != p0->C1 ||
+        p->C2 != p0->C2 || p->lmax != p0->lmax)
+      return MCC_ERR_INVALID_ARG;
+    if (!d_values[f] || ((uintptr_t)d_values[f] & (p->dtype == MCC_F64 ? 7 : 3)))
+      return MCC_ERR_INVALID_ARG;
+  }
+  if (((uintptr_t)d_out & 7) || (slot_bytes & 7) || ((uintptr_t)d_ws & 255)) return MCC_ERR_INVALID_ARG;
+  const PlanView pv = mcc_plan_view(plan);
+  const size_t wss = compress_ws_layout(pv, p0).total;
+  int chain = (int)(ws_bytes / wss);
+  if (chain < 1) return MCC_ERR_CAPACITY;
+  if (chain > kMaxBatch) chain = kMaxBatch;
+  cudaStream_t stream = (cudaStream_t)s;
+  unsigned char *out = (unsigned char *)d_out;
+  for (int f0 = 0; f0 < n; f0 += chain) {
+    const int nf = n - f0 < chain ? n - f0 : chain;
+    const mcc_status st = launch_compress_batch(pv, nf, d_values + f0, per_field + f0,
+                                                (unsigned char *)d_ws, (int64_t)wss,
+                                                out + (size_t)f0 * slot_bytes, (int64_t)slot_bytes,
+                                                slot_bytes, stream);
+    if (st) return st;
+    if (out_sizes) {
+      const mcc_status r = read_batch_status((const unsigned char *)d_ws, wss, nf, stream, out_sizes + f0);
+      if (r) return r;
+    }
+  }
+  return MCC_OK;
+}
+
+extern "C" mcc_status mcc_decompress_batch(mcc_plan plan, int n, const void *d_in, size_t slot_bytes,
+                                           const size_t *in_bytes, void *const *d_values, int dtype,
+                                           void *d_ws, size_t ws_bytes, int sync, mcc_stream s) {
+  if (!plan || n < 1 || !d_in || !in_bytes || !d_values || !d_ws) return MCC_ERR_INVALID_ARG;
+  if (dtype != MCC_F64 && dtype != MCC_F32) return MCC_ERR_INVALID_ARG;
+  if (((uintptr_t)d_in & 7) || (slot_bytes & 7) || ((uintptr_t)d_ws & 255)) return MCC_ERR_INVALID_ARG;
+  for (int f = 0; f < n; f++)
+    if (!d_values[f] || ((uintptr_t)d_values[f] & (dtype == MCC_F64 ? 7 : 3)) || in_bytes[f] > slot_bytes)
+      return MCC_ERR_INVALID_ARG;
+  const PlanView pv = mcc_plan_view(plan);
+  const size_t wss = decompress_ws_layout(pv).total;
+  int chain = (int)(ws_bytes / wss);
+  if (chain < 1) return MCC_ERR_CAPACITY;
+  if (chain > kMaxBatch) chain = kMaxBatch;
+  cudaStream_t stream = (cudaStream_t)s;
+  for (int f0 = 0; f0 < n; f0 += chain) {
+    const int nf = n - f0 < chain ? n - f0 : chain;
+    uint64_t nb[kMaxBatch];
+    for (int f = 0; f < nf; f++) nb[f] = in_bytes[f0 + f];
+    const mcc_status st = launch_decompress_batch(
+        pv, nf, (const unsigned char *)d_in + (size_t)f0 * slot_bytes, (int64_t)slot_bytes, nb,
+        d_values + f0, dtype, (unsigned char *)d_ws, (int64_t)wss, stream);
+    if (st) return st;
+    if (sync) {
+      const mcc_status r = read_batch_status((const unsigned char *)d_ws, wss, nf, stream, nullptr);
+      if (r) return r;
+    }
+  }
   return MCC_OK;
 }

@@ -29,6 +29,7 @@ constexpr double kBinShrink = 1.0 - 1.0 / 1048576.0;  // bins are 2 tau (1 - 2^-
 constexpr int kMaxR = 2048;
 constexpr int kMaxC = 256;
 constexpr int kMaxLen = 24;
+constexpr int kMaxBatch = 64;               // fields per kernel launch
 constexpr int kLutBits = 12;               // first-level decode table (two symbols per entry)
 
 // header byte offsets

@@ -35,6 +35,59 @@ struct RParams {
   double eb, frac;
 };
 
+// Arguments shared by every compression kernel of one launch chain: the plan,
+// the workspace layout (one region of wss bytes per field), the output slots
+// (oss bytes per field) and the per-field inputs and bound parameters.
+struct CompArgs {
+  PlanView pv;
+  CompressWs W;
+  Layout F;  // fixed-size part of every stream (lens .. ltab2)
+  unsigned char *ws0, *out0;
+  int64_t wss, oss;
+  uint64_t capacity;  // per-field output bytes
+  int nf, dtype, R1, R2, C1, C2, lmax, nsym1, nsym2;
+  int64_t ng1, ng2;
+  const void *x[kMaxBatch];
+  RParams rp[kMaxBatch];
+};
+
+// Per-field pointers into the workspace and the output slot.
+struct Ctx {
+  Status *st;
+  unsigned int *hist1, *hist2, *code1, *code2, *gw, *ge, *gr, *pe, *pr;
+  unsigned char *len1, *len2, *out;
+  int *Q, *q1, *val1, *val2;
+  unsigned short *sym1, *sym2, *pb;
+  const void *x;
+};
+
+__device__ __forceinline__ Ctx ctx_of(const CompArgs &A, int f) {
+  Ctx c;
+  unsigned char *ws = A.ws0 + (int64_t)f * A.wss;
+  c.st = (Status *)ws;
+  c.hist1 = (unsigned int *)(ws + A.W.hist1);
+  c.hist2 = (unsigned int *)(ws + A.W.hist2);
+  c.code1 = (unsigned int *)(ws + A.W.code1);
+  c.code2 = (unsigned int *)(ws + A.W.code2);
+  c.len1 = ws + A.W.len1;
+  c.len2 = ws + A.W.len2;
+  c.Q = (int *)(ws + A.W.Q);
+  c.q1 = (int *)(ws + A.W.q1);
+  c.sym1 = (unsigned short *)(ws + A.W.sym1);
+  c.sym2 = (unsigned short *)(ws + A.W.sym2);
+  c.val1 = (int *)(ws + A.W.val1);
+  c.val2 = (int *)(ws + A.W.val2);
+  c.gw = (unsigned int *)(ws + A.W.gw);
+  c.ge = (unsigned int *)(ws + A.W.ge);
+  c.gr = (unsigned int *)(ws + A.W.gr);
+  c.pb = (unsigned short *)(ws + A.W.pb);
+  c.pe = (unsigned int *)(ws + A.W.pe);
+  c.pr = (unsigned int *)(ws + A.W.pr);
+  c.out = A.out0 + (int64_t)f * A.oss;
+  c.x = A.x[f];
+  return c;
+}
+
 // Error check taken once per block, so every thread of the block agrees
 // (an error may be recorded concurrently by another block).
 __device__ __forceinline__ bool block_failed(const Status *st) {
@@ -98,10 +151,16 @@ __device__ void field_params(Status *st, RParams rp) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_reduce(const T *__restrict__ x, int64_t n, Status *st,
-                                                RParams rp, unsigned int *hist, int nhist) {
+__global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
+  const Ctx c = ctx_of(A, blockIdx.y);
+  const T *__restrict__ x = (const T *)c.x;
+  const int64_t n = A.pv.n_v;
+  Status *st = c.st;
+  const RParams rp = A.rp[blockIdx.y];
+  unsigned int *hist = c.hist1;
+  const int nhist = (int)((A.W.hist2 - A.W.hist1) / 4 + A.nsym2);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nhist; i += gridDim.x * blockDim.x)
     hist[i] = 0;
   unsigned long long mn = 0, mx = 0;  // mn holds ~key (max of ~key = min key)
@@ -165,10 +224,14 @@ __global__ void __launch_bounds__(256) k_reduce(const T *__restrict__ x, int64_t
 // k_prequant: Q = round(x * (1 / s2)) - K
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_prequant(const T *__restrict__ x, int64_t n,
-                                                  const Status *__restrict__ st, int *__restrict__ Q) {
+__global__ void __launch_bounds__(256) k_prequant(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
+  const Ctx c = ctx_of(A, blockIdx.y);
+  const T *__restrict__ x = (const T *)c.x;
+  const int64_t n = A.pv.n_v;
+  const Status *st = c.st;
+  int *__restrict__ Q = c.Q;
   if (st->err) return;
   const double inv2 = st->f.inv2;
   const long long K = st->f.K;
@@ -217,12 +280,19 @@ __device__ __forceinline__ void hist_add(unsigned int *sh, int sym, bool valid) 
 }
 
 template <int TX, int TY>
-__global__ void __launch_bounds__(256) k_grid2d(PlanView pv, const int *__restrict__ Q,
-                                                Status *st, int R1, int *__restrict__ q1,
-                                                unsigned short *__restrict__ sym1,
-                                                int *__restrict__ val1, unsigned int *hist1) {
+__global__ void __launch_bounds__(256) k_grid2d(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
+  // blocks are field-fastest so that the fields of a batch share plan tiles in L2
+  const Ctx c = ctx_of(A, blockIdx.x);
+  const PlanView &pv = A.pv;
+  const int *__restrict__ Q = c.Q;
+  Status *st = c.st;
+  const int R1 = A.R1;
+  int *__restrict__ q1 = c.q1;
+  unsigned short *__restrict__ sym1 = c.sym1;
+  int *__restrict__ val1 = c.val1;
+  unsigned int *hist1 = c.hist1;
   extern __shared__ unsigned int shist[];
   __shared__ int s[TY + 1][TX + 1];
   if (block_failed(st)) return;
@@ -230,7 +300,7 @@ __global__ void __launch_bounds__(256) k_grid2d(PlanView pv, const int *__restri
   for (int i = threadIdx.x; i < nsym; i += blockDim.x) shist[i] = 0;
   const FieldParams f = st->f;
   const int nx = pv.nx, ny = pv.ny;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x0 = blockIdx.y * TX, y0 = blockIdx.z * TY;
   for (int idx = threadIdx.x; idx < (TY + 1) * (TX + 1); idx += blockDim.x) {
     const int ly = idx / (TX + 1), lx = idx - ly * (TX + 1);
     const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
@@ -272,12 +342,19 @@ __global__ void __launch_bounds__(256) k_grid2d(PlanView pv, const int *__restri
 // 3D: tiles of TX x TY points walking a segment of SZ planes in z; the plane
 // below the segment is recomputed as halo.
 template <int TX, int TY, int SZ>
-__global__ void __launch_bounds__(TX *TY) k_grid3d(PlanView pv, const int *__restrict__ Q,
-                                                   Status *st, int R1, int *__restrict__ q1,
-                                                   unsigned short *__restrict__ sym1,
-                                                   int *__restrict__ val1, unsigned int *hist1) {
+__global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
+  const Ctx c = ctx_of(A, blockIdx.x);
+  const PlanView &pv = A.pv;
+  const int *__restrict__ Q = c.Q;
+  Status *st = c.st;
+  const int R1 = A.R1;
+  int *__restrict__ q1 = c.q1;
+  unsigned short *__restrict__ sym1 = c.sym1;
+  int *__restrict__ val1 = c.val1;
+  unsigned int *hist1 = c.hist1;
+  const int txs = (A.pv.nx + TX - 1) / TX;
   extern __shared__ unsigned int shist[];
   __shared__ int s[2][TY + 1][TX + 1];
   if (block_failed(st)) return;
@@ -285,7 +362,7 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(PlanView pv, const int *__res
   for (int i = threadIdx.x; i < nsym; i += blockDim.x) shist[i] = 0;
   const FieldParams f = st->f;
   const int nx = pv.nx, ny = pv.ny, nz = pv.nz;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * SZ;
+  const int x0 = (blockIdx.y % txs) * TX, y0 = (blockIdx.y / txs) * TY, z0 = blockIdx.z * SZ;
   const int64_t sxy = (int64_t)nx * ny;
   unsigned int nesc = 0;
   int cur = 0;
@@ -344,12 +421,19 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(PlanView pv, const int *__res
 // k_node: residual codes at the vertices
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
-__global__ void __launch_bounds__(256) k_node(PlanView pv, const T *__restrict__ x,
-                                              const int *__restrict__ Q, const int *__restrict__ q1,
-                                              Status *st, int R2, unsigned short *__restrict__ sym2,
-                                              int *__restrict__ val2, unsigned int *hist2) {
+__global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
+  const Ctx c = ctx_of(A, blockIdx.x);
+  const PlanView &pv = A.pv;
+  const T *__restrict__ x = (const T *)c.x;
+  const int *__restrict__ Q = c.Q;
+  const int *__restrict__ q1 = c.q1;
+  Status *st = c.st;
+  const int R2 = A.R2;
+  unsigned short *__restrict__ sym2 = c.sym2;
+  int *__restrict__ val2 = c.val2;
+  unsigned int *hist2 = c.hist2;
   extern __shared__ unsigned int shist[];
   if (block_failed(st)) return;
   const int nsym = 2 * R2;
@@ -361,9 +445,9 @@ __global__ void __launch_bounds__(256) k_node(PlanView pv, const T *__restrict__
   const int64_t sxy = (int64_t)pv.nx * pv.ny;
   const int rawsym = 2 * R2 - 1;
   unsigned int nesc = 0, nraw = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (int64_t)gridDim.y * blockDim.x;
   const int64_t nloop = (n + stride - 1) / stride * stride;  // uniform trip count per warp
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nloop; i += stride) {
+  for (int64_t i = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i < nloop; i += stride) {
     const bool valid = i < n;
     int sym = 0;
     if (valid) {
@@ -432,13 +516,17 @@ __device__ __forceinline__ unsigned long long node_w(int e, int m, const unsigne
   return e < m ? (sk[e] >> 32) : Iw[e - m];
 }
 
-__global__ void __launch_bounds__(256) k_codebook(CodebookArgs a1, CodebookArgs a2, int lmax,
-                                                   Status *st) {
+__global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompArgs AA) {
   pdl_trigger();
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
+  const Ctx c = ctx_of(AA, blockIdx.y);
+  Status *st = c.st;
+  const int lmax = AA.lmax;
   if (block_failed(st)) return;
-  const CodebookArgs A = blockIdx.x == 0 ? a1 : a2;
+  const bool c1 = blockIdx.x == 0;
+  const CodebookArgs A{c1 ? c.hist1 : c.hist2, c1 ? AA.nsym1 : AA.nsym2, c1 ? c.code1 : c.code2,
+                       c1 ? c.len1 : c.len2, c.out + (c1 ? AA.F.lens1 : AA.F.lens2)};
   const int nsym = A.nsym;
   int npn = 1;  // power of two >= nsym: room for the sort's padding
   while (npn < nsym) npn <<= 1;
@@ -641,9 +729,14 @@ struct GroupArgs {
   unsigned int *pe, *pr;          // workspace [ng1 + ng2][kParts]
 };
 
-__global__ void __launch_bounds__(256) k_group_len(GroupArgs a, const Status *st) {
+__global__ void __launch_bounds__(256) k_group_len(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
+  const Ctx c = ctx_of(A, blockIdx.y);
+  const Status *st = c.st;
+  const GroupArgs a{c.sym1, c.sym2, c.len1, c.len2, A.pv.n_g, A.pv.n_v, A.ng1, A.ng2, A.C1, A.C2,
+                    A.nsym1, A.nsym2, (unsigned short *)(c.out + A.F.ltab1),
+                    (unsigned short *)(c.out + A.F.ltab2), c.gw, c.ge, c.gr, c.pb, c.pe, c.pr};
   __shared__ unsigned char L[2 * kMaxR];
   __shared__ unsigned int sbits[kParts][32];
   __shared__ unsigned int sesc[kParts], sraw[kParts];
@@ -750,9 +843,13 @@ struct ScanArgs {
 __device__ __forceinline__ void put32(unsigned char *p, uint32_t v) { *(uint32_t *)p = v; }
 __device__ __forceinline__ void put64(unsigned char *p, uint64_t v) { *(uint64_t *)p = v; }
 
-__global__ void __launch_bounds__(160) k_scan(ScanArgs a, Status *st) {
+__global__ void __launch_bounds__(160) k_scan(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
+  const Ctx c = ctx_of(A, blockIdx.x);
+  Status *st = c.st;
+  const ScanArgs a{c.gw, c.ge, c.gr, A.ng1, A.ng2, c.out, A.capacity, A.F, A.dtype, A.pv.dim,
+                   A.R1, A.R2, A.C1, A.C2, A.lmax, A.pv.nx, A.pv.ny, A.pv.nz, A.pv.n_v, A.pv.n_g};
   __shared__ unsigned long long tot[5];
   if (block_failed(st)) return;
   const Layout F = a.fixed;
@@ -831,9 +928,14 @@ struct PackArgs {
   const unsigned int *pe, *pr;
 };
 
-__global__ void __launch_bounds__(256) k_pack(PackArgs a, const Status *st) {
+__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
+  const Ctx c = ctx_of(A, blockIdx.y);
+  const Status *st = c.st;
+  const PackArgs a{c.sym1, c.sym2, c.code1, c.code2, c.len1, c.len2, c.val1, c.val2, c.x,
+                   A.pv.n_g, A.pv.n_v, A.ng1, A.ng2, A.C1, A.C2, A.nsym1, A.nsym2,
+                   A.dtype == MCC_F64 ? 8 : 4, c.out, c.pb, c.pe, c.pr};
   extern __shared__ unsigned int stage[];
   __shared__ unsigned int scode[2 * kMaxR];
   __shared__ unsigned char slen[2 * kMaxR];
@@ -972,122 +1074,112 @@ CompressWs compress_ws_layout(const PlanView &pv, const mcc_params *p) {
   return w;
 }
 
-mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_params *p,
-                           unsigned char *ws, unsigned char *out, size_t capacity,
-                           cudaStream_t stream) {
-  const CompressWs W = compress_ws_layout(pv, p);
-  Status *st = (Status *)ws;
-  const int64_t n_v = pv.n_v, n_g = pv.n_g;
-  const int64_t ng1 = ngroups(n_g, p->C1), ng2 = ngroups(n_v, p->C2);
-  const int nsym1 = 2 * p->R1, nsym2 = 2 * p->R2;
-  const Layout F = make_layout(p->R1, p->R2, ng1, ng2, 0, 0, 0, 8, 0, 0);
-  if (capacity < F.out1) return MCC_ERR_CAPACITY;
-  unsigned int *hist1 = (unsigned int *)(ws + W.hist1), *hist2 = (unsigned int *)(ws + W.hist2);
-  int *Q = (int *)(ws + W.Q), *q1 = (int *)(ws + W.q1);
-  unsigned short *sym1 = (unsigned short *)(ws + W.sym1), *sym2 = (unsigned short *)(ws + W.sym2);
-  int *val1 = (int *)(ws + W.val1), *val2 = (int *)(ws + W.val2);
+// Compress nf fields (nf <= kMaxBatch) of one plan: field f reads xs[f] with
+// bound parameters ps[f] (dtype, R, C and lmax taken from ps[0]), uses the
+// workspace region ws0 + f * wss and writes its stream to out0 + f * oss
+// (at most `capacity` bytes).
+mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *xs,
+                                 const mcc_params *ps, unsigned char *ws0, int64_t wss,
+                                 unsigned char *out0, int64_t oss, size_t capacity,
+                                 cudaStream_t stream) {
+  if (nf < 1 || nf > kMaxBatch) return MCC_ERR_INVALID_ARG;
+  const mcc_params *p = ps;
+  CompArgs A;  // launch arguments (passed by value as a grid constant)
+  memset(&A, 0, sizeof(A));
+  A.pv = pv;
+  A.W = compress_ws_layout(pv, p);
+  A.ws0 = ws0;
+  A.out0 = out0;
+  A.wss = wss;
+  A.oss = oss;
+  A.capacity = capacity;
+  A.nf = nf;
+  A.dtype = p->dtype;
+  A.R1 = p->R1;
+  A.R2 = p->R2;
+  A.C1 = p->C1;
+  A.C2 = p->C2;
+  A.lmax = p->lmax;
+  A.nsym1 = 2 * p->R1;
+  A.nsym2 = 2 * p->R2;
+  A.ng1 = ngroups(pv.n_g, p->C1);
+  A.ng2 = ngroups(pv.n_v, p->C2);
+  A.F = make_layout(p->R1, p->R2, A.ng1, A.ng2, 0, 0, 0, 8, 0, 0);
+  if (capacity < A.F.out1) return MCC_ERR_CAPACITY;
+  for (int f = 0; f < nf; f++) {
+    A.x[f] = xs[f];
+    A.rp[f] = RParams{ps[f].dtype, ps[f].eb_mode, ps[f].eb, ps[f].grid_fraction};
+  }
+  const int64_t ng = A.ng1 + A.ng2;
   const int sms = num_sms();
-
-  if (cudaMemsetAsync(ws, 0, kStatusBytes, stream) != cudaSuccess) return MCC_ERR_CUDA;
-  // hist1 and hist2 are adjacent: zeroed together by k_reduce
-  const int nhist = (int)((W.hist2 - W.hist1) / 4 + nsym2);
-  RParams rp{p->dtype, p->eb_mode, p->eb, p->grid_fraction};
-  const unsigned int rblocks = (unsigned int)sms * 4;
-  if (p->dtype == MCC_F64) {
-    {
-      PROF_SCOPE("k_reduce", stream);
-      k_reduce<double><<<rblocks, 256, 0, stream>>>((const double *)d_values, n_v, st, rp, hist1, nhist);
-    }
-    {
-      PROF_SCOPE("k_prequant", stream);
-      launch_pdl(k_prequant<double>, dim3((unsigned int)sms * 8), dim3(256), 0, stream, (const double *)d_values, n_v, st, Q);
-    }
-  } else {
-    {
-      PROF_SCOPE("k_reduce", stream);
-      k_reduce<float><<<rblocks, 256, 0, stream>>>((const float *)d_values, n_v, st, rp, hist1, nhist);
-    }
-    {
-      PROF_SCOPE("k_prequant", stream);
-      launch_pdl(k_prequant<float>, dim3((unsigned int)sms * 8), dim3(256), 0, stream, (const float *)d_values, n_v, st, Q);
-    }
-  }
-  const size_t hsm1 = 4 * (size_t)nsym1, hsm2 = 4 * (size_t)nsym2;
-  if (pv.dim == 2) {
-    dim3 grid((pv.nx + 63) / 64, (pv.ny + 15) / 16);
-    {
-      PROF_SCOPE("k_grid2d", stream);
-      launch_pdl(k_grid2d<64, 16>, dim3(grid), dim3(256), hsm1, stream, pv, Q, st, p->R1, q1, sym1, val1, hist1);
-    }
-  } else {
-    dim3 grid((pv.nx + 31) / 32, (pv.ny + 7) / 8, (pv.nz + 7) / 8);
-    {
-      PROF_SCOPE("k_grid3d", stream);
-      launch_pdl(k_grid3d<32, 8, 8>, dim3(grid), dim3(256), hsm1, stream, pv, Q, st, p->R1, q1, sym1, val1, hist1);
-    }
-  }
-  const unsigned int nblocks_node = (unsigned int)sms * 8;
-  if (pv.dim == 2) {
-    if (p->dtype == MCC_F64)
-      {
-        PROF_SCOPE("k_node", stream);
-        launch_pdl(k_node<2, double>, dim3(nblocks_node), dim3(256), hsm2, stream, pv, (const double *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
-      }
-    else
-      {
-        PROF_SCOPE("k_node", stream);
-        launch_pdl(k_node<2, float>, dim3(nblocks_node), dim3(256), hsm2, stream, pv, (const float *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
-      }
-  } else {
-    if (p->dtype == MCC_F64)
-      {
-        PROF_SCOPE("k_node", stream);
-        launch_pdl(k_node<3, double>, dim3(nblocks_node), dim3(256), hsm2, stream, pv, (const double *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
-      }
-    else
-      {
-        PROF_SCOPE("k_node", stream);
-        launch_pdl(k_node<3, float>, dim3(nblocks_node), dim3(256), hsm2, stream, pv, (const float *)d_values, Q, q1, st, p->R2, sym2, val2, hist2);
-      }
-  }
-  CodebookArgs a1{hist1, nsym1, (unsigned int *)(ws + W.code1), ws + W.len1, out + F.lens1};
-  CodebookArgs a2{hist2, nsym2, (unsigned int *)(ws + W.code2), ws + W.len2, out + F.lens2};
-  const size_t cbsm = codebook_smem(nsym1 > nsym2 ? nsym1 : nsym2);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
+  if (cudaMemset2DAsync(ws0, (size_t)wss, 0, kStatusBytes, (size_t)nf, stream) != cudaSuccess)
+    return MCC_ERR_CUDA;
+  const unsigned int bpf = (unsigned int)((sms * 4 + nf - 1) / nf);  // reduce blocks per field
+  const unsigned int ppf = (unsigned int)((sms * 8 + nf - 1) / nf);  // prequant / node blocks per field
+  {
+    PROF_SCOPE("k_reduce", stream);
+    if (p->dtype == MCC_F64) k_reduce<double><<<dim3(bpf, nf), 256, 0, stream>>>(A);
+    else k_reduce<float><<<dim3(bpf, nf), 256, 0, stream>>>(A);
+  }
+  {
+    PROF_SCOPE("k_prequant", stream);
+    if (p->dtype == MCC_F64) launch_pdl(k_prequant<double>, dim3(ppf, nf), dim3(256), 0, stream, A);
+    else launch_pdl(k_prequant<float>, dim3(ppf, nf), dim3(256), 0, stream, A);
+  }
+  const size_t hsm1 = 4 * (size_t)A.nsym1, hsm2 = 4 * (size_t)A.nsym2;
+  if (pv.dim == 2) {
+    PROF_SCOPE("k_grid2d", stream);
+    launch_pdl(k_grid2d<64, 16>, dim3(nf, (pv.nx + 63) / 64, (pv.ny + 15) / 16), dim3(256), hsm1,
+               stream, A);
+  } else {
+    PROF_SCOPE("k_grid3d", stream);
+    const unsigned int txy = (unsigned int)(((pv.nx + 31) / 32) * ((pv.ny + 7) / 8));
+    launch_pdl(k_grid3d<32, 8, 8>, dim3(nf, txy, (pv.nz + 7) / 8), dim3(256), hsm1, stream, A);
+  }
+  {
+    PROF_SCOPE("k_node", stream);
+    const unsigned int chunks = ppf < 65535 ? ppf : 65535;
+    if (pv.dim == 2) {
+      if (p->dtype == MCC_F64) launch_pdl(k_node<2, double>, dim3(nf, chunks), dim3(256), hsm2, stream, A);
+      else launch_pdl(k_node<2, float>, dim3(nf, chunks), dim3(256), hsm2, stream, A);
+    } else {
+      if (p->dtype == MCC_F64) launch_pdl(k_node<3, double>, dim3(nf, chunks), dim3(256), hsm2, stream, A);
+      else launch_pdl(k_node<3, float>, dim3(nf, chunks), dim3(256), hsm2, stream, A);
+    }
+  }
   {
     PROF_SCOPE("k_codebook", stream);
-    launch_pdl(k_codebook, dim3(2), dim3(256), cbsm, stream, a1, a2, p->lmax, st);
+    const size_t cbsm = codebook_smem(A.nsym1 > A.nsym2 ? A.nsym1 : A.nsym2);
+    launch_pdl(k_codebook, dim3(2, nf), dim3(1024), cbsm, stream, A);
   }
-  GroupArgs ga{sym1, sym2, ws + W.len1, ws + W.len2, n_g, n_v, ng1, ng2, p->C1, p->C2, nsym1, nsym2,
-               (unsigned short *)(out + F.ltab1), (unsigned short *)(out + F.ltab2),
-               (unsigned int *)(ws + W.gw), (unsigned int *)(ws + W.ge), (unsigned int *)(ws + W.gr),
-               (unsigned short *)(ws + W.pb), (unsigned int *)(ws + W.pe), (unsigned int *)(ws + W.pr)};
   {
     PROF_SCOPE("k_group_len", stream);
-    launch_pdl(k_group_len, dim3((unsigned int)(ng1 + ng2)), dim3(256), 0, stream, ga, st);
+    launch_pdl(k_group_len, dim3((unsigned int)ng, nf), dim3(256), 0, stream, A);
   }
-  ScanArgs sa{(const unsigned int *)(ws + W.gw), (const unsigned int *)(ws + W.ge),
-              (const unsigned int *)(ws + W.gr), ng1, ng2, out, capacity, F, p->dtype, pv.dim,
-              p->R1, p->R2, p->C1, p->C2, p->lmax, pv.nx, pv.ny, pv.nz, n_v, n_g};
   {
     PROF_SCOPE("k_scan", stream);
-    launch_pdl(k_scan, dim3(1), dim3(160), 0, stream, sa, st);
+    launch_pdl(k_scan, dim3(nf), dim3(160), 0, stream, A);
   }
-  const int cmax = p->C1 > p->C2 ? p->C1 : p->C2;
-  const size_t stage_bytes = 4 * (size_t)cmax * p->lmax;  // worst-case words of one group
-  PackArgs pa{sym1, sym2, (const unsigned int *)(ws + W.code1), (const unsigned int *)(ws + W.code2),
-              ws + W.len1, ws + W.len2, val1, val2, d_values, n_g, n_v, ng1, ng2, p->C1, p->C2,
-              nsym1, nsym2, p->dtype == MCC_F64 ? 8 : 4, out, (const unsigned short *)(ws + W.pb),
-              (const unsigned int *)(ws + W.pe), (const unsigned int *)(ws + W.pr)};
   {
     PROF_SCOPE("k_pack", stream);
-    launch_pdl(k_pack, dim3((unsigned int)(ng1 + ng2)), dim3(256), stage_bytes, stream, pa, st);
+    const int cmax = p->C1 > p->C2 ? p->C1 : p->C2;
+    const size_t stage_bytes = 4 * (size_t)cmax * p->lmax;  // worst-case words of one group
+    launch_pdl(k_pack, dim3((unsigned int)ng, nf), dim3(256), stage_bytes, stream, A);
   }
   if (cudaGetLastError() != cudaSuccess) return MCC_ERR_CUDA;
   return MCC_OK;
+}
+
+mcc_status launch_compress(const PlanView &pv, const void *d_values, const mcc_params *p,
+                           unsigned char *ws, unsigned char *out, size_t capacity,
+                           cudaStream_t stream) {
+  const void *xs[1] = {d_values};
+  return launch_compress_batch(pv, 1, xs, p, ws, (int64_t)compress_ws_layout(pv, p).total, out,
+                               (int64_t)capacity, capacity, stream);
 }

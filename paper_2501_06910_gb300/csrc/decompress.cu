@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "common.cuh"
 #include "workspace.cuh"
@@ -28,6 +29,46 @@ namespace {
 __device__ __forceinline__ uint32_t ld32(const unsigned char *p) { return *(const uint32_t *)p; }
 __device__ __forceinline__ uint64_t ld64(const unsigned char *p) {
   return (uint64_t)ld32(p) | ((uint64_t)ld32(p + 4) << 32);
+}
+
+// Arguments shared by every decompression kernel of one launch chain: the
+// plan, the workspace layout (one region of wss bytes per field), the input
+// streams (iss bytes apart, in_bytes each) and the output arrays.
+struct DecArgs {
+  PlanView pv;
+  DecompressWs W;
+  unsigned char *ws0;
+  int64_t wss;
+  const unsigned char *in0;
+  int64_t iss;
+  int nf, dtype;
+  uint64_t in_bytes[kMaxBatch];
+  void *xo[kMaxBatch];
+};
+
+struct DCtx {
+  Status *st;
+  DecInfo *info;
+  DecTab *tab1, *tab2;
+  int *q1, *q2;
+  const unsigned char *in;
+  uint64_t in_bytes;
+  void *xo;
+};
+
+__device__ __forceinline__ DCtx dctx_of(const DecArgs &A, int f) {
+  DCtx c;
+  unsigned char *ws = A.ws0 + (int64_t)f * A.wss;
+  c.st = (Status *)ws;
+  c.info = (DecInfo *)(ws + A.W.info);
+  c.tab1 = (DecTab *)(ws + A.W.tab1);
+  c.tab2 = (DecTab *)(ws + A.W.tab2);
+  c.q1 = (int *)(ws + A.W.q1);
+  c.q2 = (int *)(ws + A.W.q2);
+  c.in = A.in0 + (int64_t)f * A.iss;
+  c.in_bytes = A.in_bytes[f];
+  c.xo = A.xo[f];
+  return c;
 }
 
 __device__ __forceinline__ bool block_failed(const Status *st) {
@@ -99,9 +140,13 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
   return true;
 }
 
-__global__ void __launch_bounds__(256) k_dec_prep(PrepArgs a, Status *st) {
+__global__ void __launch_bounds__(256) k_dec_prep(const __grid_constant__ DecArgs A) {
   pdl_trigger();
   pdl_wait();
+  const DCtx c = dctx_of(A, blockIdx.y);
+  Status *st = c.st;
+  const PrepArgs a{c.in, c.in_bytes, A.dtype, A.pv.dim, A.pv.nx, A.pv.ny, A.pv.nz, A.pv.n_v,
+                   A.pv.n_g, c.info, c.tab1, c.tab2};
   __shared__ DecInfo I;
   __shared__ int ok;
   __shared__ unsigned char lens[2 * kMaxR];
@@ -260,15 +305,19 @@ __device__ __forceinline__ bool group_setup(const unsigned char *in, uint64_t gt
 constexpr int kDecRound = 64;  // steps decoded per shared-memory round
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_dec_syms(const unsigned char *__restrict__ in,
-                                                  const DecInfo *__restrict__ info,
-                                                  const DecTab *__restrict__ tab1,
-                                                  const DecTab *__restrict__ tab2, int nb1,
-                                                  int64_t n_g, int64_t n_v, int *__restrict__ delta,
-                                                  int *__restrict__ q2s, T *__restrict__ xo,
-                                                  Status *st) {
+__global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArgs A, int nb1) {
   pdl_trigger();
   pdl_wait();
+  const DCtx c = dctx_of(A, blockIdx.y);
+  const unsigned char *__restrict__ in = c.in;
+  const DecInfo *__restrict__ info = c.info;
+  const DecTab *__restrict__ tab1 = c.tab1;
+  const DecTab *__restrict__ tab2 = c.tab2;
+  const int64_t n_g = A.pv.n_g, n_v = A.pv.n_v;
+  int *__restrict__ delta = c.q1;
+  int *__restrict__ q2s = c.q2;
+  T *__restrict__ xo = (T *)c.xo;
+  Status *st = c.st;
   __shared__ DecTab Tb;
   extern __shared__ unsigned short sbuf[];  // [warps][kDecRound][32]
   if (block_failed(st)) return;
@@ -407,9 +456,14 @@ __global__ void __launch_bounds__(256) k_dec_syms(const unsigned char *__restric
 // ---------------------------------------------------------------------------
 // inverse Lorenzo: inclusive prefix sums (wrapping int32 arithmetic)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scan_rows(int *q, int nx, int64_t nrows, const Status *st) {
+__global__ void __launch_bounds__(256) k_scan_rows(const __grid_constant__ DecArgs A) {
   pdl_trigger();
   pdl_wait();
+  const DCtx c = dctx_of(A, blockIdx.y);
+  int *q = c.q1;
+  const int nx = A.pv.nx;
+  const int64_t nrows = (int64_t)A.pv.ny * A.pv.nz;
+  const Status *st = c.st;
   if (*(volatile const unsigned int *)&st->err) return;
   const int lane = threadIdx.x & 31;
   const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -432,10 +486,13 @@ __global__ void __launch_bounds__(256) k_scan_rows(int *q, int nx, int64_t nrows
 // Inclusive scan along an axis of length L and stride S, for columns
 // base = outer * plane + inner (inner < n_inner contiguous). Block: 32
 // consecutive columns x 8 warps, each warp scanning one segment of the axis.
-__global__ void __launch_bounds__(256) k_scan_axis(int *q, int64_t n_inner, int64_t n_outer,
-                                                   int64_t plane, int L, int64_t S, const Status *st) {
+__global__ void __launch_bounds__(256) k_scan_axis(const __grid_constant__ DecArgs A, int64_t n_inner,
+                                                   int64_t n_outer, int64_t plane, int L, int64_t S) {
   pdl_trigger();
   pdl_wait();
+  const DCtx c = dctx_of(A, blockIdx.y);
+  int *q = c.q1;
+  const Status *st = c.st;
   __shared__ unsigned int part[8][33];
   if (*(volatile const unsigned int *)&st->err) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -464,19 +521,23 @@ __global__ void __launch_bounds__(256) k_scan_axis(int *q, int64_t n_inner, int6
 // k_recon: x' = s2 (K + P + q2) at every vertex, P = round(rho12 g(x1'))
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
-__global__ void __launch_bounds__(256) k_recon(const DecInfo *__restrict__ info, PlanView pv,
-                                               const int *__restrict__ q1,
-                                               const int *__restrict__ q2s, T *__restrict__ xo,
-                                               const Status *st) {
+__global__ void __launch_bounds__(256) k_recon(const __grid_constant__ DecArgs A) {
   pdl_trigger();
   pdl_wait();
+  const DCtx c = dctx_of(A, blockIdx.x);
+  const DecInfo *__restrict__ info = c.info;
+  const PlanView &pv = A.pv;
+  const int *__restrict__ q1 = c.q1;
+  const int *__restrict__ q2s = c.q2;
+  T *__restrict__ xo = (T *)c.xo;
+  const Status *st = c.st;
   if (*(volatile const unsigned int *)&st->err) return;
   const DecInfo I = *info;
   const int64_t n = pv.n_v;
   const int nx = pv.nx;
   const int64_t sxy = (int64_t)pv.nx * pv.ny;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p0 < n; p0 += 2 * stride) {
+  const int64_t stride = (int64_t)gridDim.y * blockDim.x;
+  for (int64_t p0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; p0 < n; p0 += 2 * stride) {
 #pragma unroll
     for (int u = 0; u < 2; u++) {
       const int64_t p = p0 + u * stride;
@@ -513,70 +574,87 @@ DecompressWs decompress_ws_layout(const PlanView &pv) {
   return w;
 }
 
-mcc_status launch_decompress(const PlanView &pv, const unsigned char *in, size_t in_bytes,
-                             void *d_values, int dtype, unsigned char *ws, cudaStream_t stream) {
-  const DecompressWs W = decompress_ws_layout(pv);
-  Status *st = (Status *)ws;
-  DecInfo *info = (DecInfo *)(ws + W.info);
-  DecTab *tab1 = (DecTab *)(ws + W.tab1), *tab2 = (DecTab *)(ws + W.tab2);
-  int *q1 = (int *)(ws + W.q1);
-  if (cudaMemsetAsync(ws, 0, kStatusBytes, stream) != cudaSuccess) return MCC_ERR_CUDA;
-  PrepArgs pa{in, in_bytes, dtype, pv.dim, pv.nx, pv.ny, pv.nz, pv.n_v, pv.n_g, info, tab1, tab2};
-  {
-    PROF_SCOPE("k_dec_prep", stream);
-    k_dec_prep<<<2, 256, 0, stream>>>(pa, st);
+// Decompress nf fields (nf <= kMaxBatch): field f reads in_bytes[f] bytes at
+// in0 + f * iss, uses the workspace region ws0 + f * wss and writes n_v
+// values of dtype to xo[f].
+mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned char *in0, int64_t iss,
+                                   const uint64_t *in_bytes, void *const *xo, int dtype,
+                                   unsigned char *ws0, int64_t wss, cudaStream_t stream) {
+  if (nf < 1 || nf > kMaxBatch) return MCC_ERR_INVALID_ARG;
+  DecArgs A;
+  memset(&A, 0, sizeof(A));
+  A.pv = pv;
+  A.W = decompress_ws_layout(pv);
+  A.ws0 = ws0;
+  A.wss = wss;
+  A.in0 = in0;
+  A.iss = iss;
+  A.nf = nf;
+  A.dtype = dtype;
+  for (int f = 0; f < nf; f++) {
+    A.in_bytes[f] = in_bytes[f];
+    A.xo[f] = xo[f];
   }
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int *q2s = (int *)(ws + W.q2);
-  // group counts depend on the stream's chunk sizes: size the decoder for the
+  if (cudaMemset2DAsync(ws0, (size_t)wss, 0, kStatusBytes, (size_t)nf, stream) != cudaSuccess)
+    return MCC_ERR_CUDA;
+  {
+    PROF_SCOPE("k_dec_prep", stream);
+    k_dec_prep<<<dim3(2, nf), 256, 0, stream>>>(A);
+  }
+  // group counts depend on the streams' chunk sizes: size the decoder for the
   // smallest chunk and let warps stride over the groups that exist
   const int64_t max_g1 = ngroups(pv.n_g, 1), max_g2 = ngroups(pv.n_v, 1);
-  const unsigned int cap = (unsigned int)sms * 2;
+  const unsigned int cap = (unsigned int)((sms * 2 + nf - 1) / nf) + 1;
   const unsigned int nb1 = nblk(max_g1, 8) < cap ? nblk(max_g1, 8) : cap;
   const unsigned int nb2 = nblk(max_g2, 8) < cap ? nblk(max_g2, 8) : cap;
   {
     PROF_SCOPE("k_dec_syms", stream);
     const size_t sm = (size_t)8 * kDecRound * 32 * sizeof(unsigned short);  // [warps][round][32]
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_dec_syms<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      cudaFuncSetAttribute(k_dec_syms<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
-    }
     if (dtype == MCC_F64)
-      launch_pdl(k_dec_syms<double>, dim3(nb1 + nb2), dim3(256), sm, stream, in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (double *)d_values, st);
+      launch_pdl(k_dec_syms<double>, dim3(nb1 + nb2, nf), dim3(256), sm, stream, A, (int)nb1);
     else
-      launch_pdl(k_dec_syms<float>, dim3(nb1 + nb2), dim3(256), sm, stream, in, info, tab1, tab2, (int)nb1, pv.n_g, pv.n_v, q1, q2s, (float *)d_values, st);
+      launch_pdl(k_dec_syms<float>, dim3(nb1 + nb2, nf), dim3(256), sm, stream, A, (int)nb1);
   }
-  const int64_t nrows = (int64_t)pv.ny * pv.nz;
   {
     PROF_SCOPE("k_scan_rows", stream);
-    launch_pdl(k_scan_rows, dim3(nblk(nrows, 8)), dim3(256), 0, stream, q1, pv.nx, nrows, st);
+    const int64_t nrows = (int64_t)pv.ny * pv.nz;
+    launch_pdl(k_scan_rows, dim3(nblk(nrows, 8), nf), dim3(256), 0, stream, A);
   }
   {  // y: columns (x, z), stride nx
     PROF_SCOPE("k_scan_axis", stream);
     const int64_t blocks = (pv.nx + 31) / 32 * (int64_t)pv.nz;
-    launch_pdl(k_scan_axis, dim3((unsigned int)blocks), dim3(256), 0, stream, q1, pv.nx, pv.nz, (int64_t)pv.nx * pv.ny,
-                                                         pv.ny, pv.nx, st);
+    launch_pdl(k_scan_axis, dim3((unsigned int)blocks, nf), dim3(256), 0, stream, A, (int64_t)pv.nx,
+               (int64_t)pv.nz, (int64_t)pv.nx * pv.ny, pv.ny, (int64_t)pv.nx);
   }
   if (pv.dim == 3) {  // z: columns (x, y), stride nx ny
     PROF_SCOPE("k_scan_axis", stream);
     const int64_t ninner = (int64_t)pv.nx * pv.ny;
-    launch_pdl(k_scan_axis, dim3((unsigned int)((ninner + 31) / 32)), dim3(256), 0, stream, q1, ninner, 1, 0, pv.nz, ninner, st);
+    launch_pdl(k_scan_axis, dim3((unsigned int)((ninner + 31) / 32), nf), dim3(256), 0, stream, A,
+               ninner, (int64_t)1, (int64_t)0, pv.nz, ninner);
   }
   {
     PROF_SCOPE("k_recon", stream);
-    const unsigned int rb = (unsigned int)sms * 8;
+    unsigned int chunks = (unsigned int)((sms * 8 + nf - 1) / nf);
+    if (chunks > 65535) chunks = 65535;
     if (pv.dim == 2) {
-      if (dtype == MCC_F64) launch_pdl(k_recon<2, double>, dim3(rb), dim3(256), 0, stream, info, pv, q1, q2s, (double *)d_values, st);
-      else launch_pdl(k_recon<2, float>, dim3(rb), dim3(256), 0, stream, info, pv, q1, q2s, (float *)d_values, st);
+      if (dtype == MCC_F64) launch_pdl(k_recon<2, double>, dim3(nf, chunks), dim3(256), 0, stream, A);
+      else launch_pdl(k_recon<2, float>, dim3(nf, chunks), dim3(256), 0, stream, A);
     } else {
-      if (dtype == MCC_F64) launch_pdl(k_recon<3, double>, dim3(rb), dim3(256), 0, stream, info, pv, q1, q2s, (double *)d_values, st);
-      else launch_pdl(k_recon<3, float>, dim3(rb), dim3(256), 0, stream, info, pv, q1, q2s, (float *)d_values, st);
+      if (dtype == MCC_F64) launch_pdl(k_recon<3, double>, dim3(nf, chunks), dim3(256), 0, stream, A);
+      else launch_pdl(k_recon<3, float>, dim3(nf, chunks), dim3(256), 0, stream, A);
     }
   }
   if (cudaGetLastError() != cudaSuccess) return MCC_ERR_CUDA;
   return MCC_OK;
+}
+
+mcc_status launch_decompress(const PlanView &pv, const unsigned char *in, size_t in_bytes,
+                             void *d_values, int dtype, unsigned char *ws, cudaStream_t stream) {
+  const uint64_t nb[1] = {in_bytes};
+  void *xo[1] = {d_values};
+  return launch_decompress_batch(pv, 1, in, 0, nb, xo, dtype, ws,
+                                 (int64_t)decompress_ws_layout(pv).total, stream);
 }

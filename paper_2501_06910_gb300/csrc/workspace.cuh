@@ -46,3 +46,10 @@ mcc_status launch_compress(const mcc::PlanView &pv, const void *d_values, const 
                            cudaStream_t stream);
 mcc_status launch_decompress(const mcc::PlanView &pv, const unsigned char *in, size_t in_bytes,
                              void *d_values, int dtype, unsigned char *ws, cudaStream_t stream);
+mcc_status launch_compress_batch(const mcc::PlanView &pv, int nf, const void *const *xs,
+                                 const mcc_params *ps, unsigned char *ws0, int64_t wss,
+                                 unsigned char *out0, int64_t oss, size_t capacity,
+                                 cudaStream_t stream);
+mcc_status launch_decompress_batch(const mcc::PlanView &pv, int nf, const unsigned char *in0,
+                                   int64_t iss, const uint64_t *in_bytes, void *const *xo,
+                                   int dtype, unsigned char *ws0, int64_t wss, cudaStream_t stream);

@@ -220,3 +220,39 @@ def test_full_size_2d_graded_1024():
         y = G.decompress(gp, s_gpu, np.float64)
         assert np.array_equal(y, oracle.decompress(op, s_orc))
         assert np.abs(y - x).max() <= oracle.field_params(x, eb=eb)["tau2"]
+
+
+@pytest.mark.parametrize("n", [1, 5, 70])
+def test_batched_streams_equal_single_field_streams(n):
+    """Batched compression (many fields on one plan, per-field bounds) gives
+    each field exactly the stream of the oracle's single-field compression;
+    batched decompression gives the oracle's values."""
+    import torch
+    import gpu_helpers as G
+    import paper_2501_06910_gb300 as mcc
+    c, e, nn, x, op, gp = _setup("ragged2d")
+    rng = np.random.default_rng(n)
+    fields, kws = [], []
+    for f in range(n):
+        fields.append(synth.field_bumps_noise(c, seed=100 + f) * (1 + f % 3))
+        kws.append(dict(eb_mode="rel" if f % 2 else "abs", eb=float(10 ** rng.uniform(-5, -2)),
+                        grid_fraction=float(rng.uniform(0.2, 0.8))))
+    prms = [mcc.params_default(dtype=mcc.F64, **k) for k in kws]
+    slot = (mcc.compress_bound(gp, prms[0]) + 7) // 8 * 8
+    cws, dws = mcc.workspace_size(gp, prms[0])
+    chain = min(n, 7)  # force several launch chains for n = 70
+    ws = torch.empty(cws * chain, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(slot * n, dtype=torch.uint8, device="cuda")
+    xs = [torch.from_numpy(v).cuda() for v in fields]
+    sizes = mcc.compress_batch(gp, xs, prms, ws, out, slot)
+    host = out.cpu().numpy()
+    for f in range(n):
+        ref = oracle.compress(op, fields[f], **kws[f])
+        assert sizes[f] == ref.size
+        assert np.array_equal(host[f * slot:f * slot + sizes[f]], ref), f
+    ys = [torch.empty_like(t) for t in xs]
+    wsd = torch.empty(dws * chain, dtype=torch.uint8, device="cuda")
+    mcc.decompress_batch(gp, out, slot, sizes, ys, wsd)
+    for f in range(n):
+        want = oracle.decompress(op, host[f * slot:f * slot + sizes[f]])
+        assert np.array_equal(ys[f].cpu().numpy(), want), f
