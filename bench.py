@@ -199,6 +199,7 @@ def main():
     ap.add_argument("--no-kernel-times", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--preroll", type=float, default=0.5, help="seconds of untimed steps")
+    ap.add_argument("--batch", type=int, default=16, help="fields per step of the batched line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -316,6 +317,51 @@ def main():
         mcc.profile_reset()
     launches_per_step = (sum(n for _, n in prof.values()) / args.steps) if prof else None
 
+    # batched: B fields of the same workload per step through mcc_compress_batch
+    # and mcc_decompress_batch (one graph; plan shared; L2 flushed per step)
+    batched = None
+    if args.batch > 1:
+        B = args.batch
+        xs = [x.clone() for _ in range(B)]
+        ys = [torch.empty_like(x) for _ in range(B)]
+        prms = [mcc.params_default(dtype=mcc.F64, eb=args.eb, grid_fraction=0.5) for _ in range(B)]
+        slot = (cap + 7) // 8 * 8
+        bout = torch.zeros(slot * B, dtype=torch.uint8, device=dev)
+        cws, dws = mcc.workspace_size(plan, prm)
+        chain = min(B, 64)
+        bwsc = torch.empty(cws * chain, dtype=torch.uint8, device=dev)
+        bwsd = torch.empty(dws * chain, dtype=torch.uint8, device=dev)
+
+        def bstep():
+            mcc.compress_batch(plan, xs, prms, bwsc, bout, slot, sync=False)
+            mcc.decompress_batch(plan, bout, slot, [slot] * B, ys, bwsd, sync=False)
+
+        bstep()
+        sizes = mcc.compress_batch(plan, xs, prms, bwsc, bout, slot, sync=True)
+        mcc.decompress_batch(plan, bout, slot, sizes, ys, bwsd, sync=True)
+        if any(not torch.equal(ys[f], y) for f in range(B)):
+            raise SystemExit("batched result differs from the single-field result")
+        bgraph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(bgraph):
+            bstep()
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            bgraph.replay()
+        bs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        be = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            bs[k].record(stream)
+            bgraph.replay()
+            be[k].record(stream)
+        torch.cuda.synchronize()
+        bms = statistics.mean(s.elapsed_time(e) for s, e in zip(bs, be))
+        batched = {"fields_per_step": B, "ms_per_step": bms,
+                   "value": world * B * x_np.nbytes / (bms * 1e-3) / 1e9, "unit": "GB/s",
+                   "compression_ratio": x_np.nbytes / sizes[0]}
+        del bgraph, bout, bwsc, bwsd, xs, ys
+
     # end to end through the API with host buffers (pinned)
     e2e = None
     h2d = d2h = 0
@@ -403,6 +449,7 @@ def main():
             "value": world * nbytes / (e2e * 1e-3) / 1e9, "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": None if launches_per_step is None else int(round(launches_per_step * args.steps)),
+        "batched": batched,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
