@@ -613,6 +613,12 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
   {
     PROF_SCOPE("k_dec_syms", stream);
     const size_t sm = (size_t)8 * kDecRound * 32 * sizeof(unsigned short);  // [warps][round][32]
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_dec_syms<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_dec_syms<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
     if (dtype == MCC_F64)
       launch_pdl(k_dec_syms<double>, dim3(nb1 + nb2, nf), dim3(256), sm, stream, A, (int)nb1);
     else
