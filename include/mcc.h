@@ -179,6 +179,21 @@ mcc_status mcc_decompress_batch(mcc_plan plan, int n, const void *d_in, size_t s
                                 void *d_workspace, size_t workspace_bytes, int sync,
                                 mcc_stream stream);
 
+/* Decompression without any device allocation (the paper has no counterpart;
+ * this serves callers that cannot call cudaMalloc, e.g. code that must stay
+ * inside a memory budget owned by another allocator, or a plugin handed only
+ * its input and output buffers). Same result as mcc_decompress; the scratch
+ * memory is a fixed array inside this library's device image of
+ * mcc_static_scratch_bytes() bytes (32 MiB) per device, held by every GPU
+ * that loads the library until the process exits. Plans whose decompression
+ * workspace (mcc_workspace_size) exceeds it get MCC_ERR_CAPACITY. The first
+ * call on a device looks up the array's device address (make that first call
+ * before any stream capture). All calls on a device share the array and leave
+ * its contents behind: calls whose GPU work overlaps race. */
+mcc_status mcc_decompress_static(mcc_plan plan, const void *d_in, size_t in_bytes, void *d_values,
+                                 int dtype, int sync, mcc_stream stream);
+size_t mcc_static_scratch_bytes(void);
+
 /* Synchronise the stream and read the status (and, after a compression, the
  * stream size; may be NULL) that the last call recorded in the workspace. */
 mcc_status mcc_workspace_result(const void *d_workspace, mcc_stream stream, size_t *out_size);

@@ -94,6 +94,10 @@ def load():
             lib.mcc_decompress_batch.argtypes = [P, C.c_int, P, S, C.POINTER(S), C.POINTER(P),
                                                  C.c_int, P, S, C.c_int, P]
             lib.mcc_compress_batch.restype = C.c_int
+            lib.mcc_decompress_static.argtypes = [P, P, S, P, C.c_int, C.c_int, P]
+            lib.mcc_decompress_static.restype = C.c_int
+            lib.mcc_static_scratch_bytes.argtypes = []
+            lib.mcc_static_scratch_bytes.restype = S
             lib.mcc_decompress_batch.restype = C.c_int
             lib.mcc_profile_enable.argtypes = [C.c_int]
             lib.mcc_profile_enable.restype = None
@@ -294,3 +298,17 @@ def decompress_batch(plan: Plan, stream_bytes: torch.Tensor, slot_bytes: int, in
                                      dtype, _dptr(workspace), workspace.numel(), 1 if sync else 0,
                                      _stream(stream))
     _check(st, "decompress_batch")
+
+
+def decompress_static(plan: Plan, stream_bytes: torch.Tensor, nbytes: int, out: torch.Tensor,
+                      sync: bool = True, stream=None):
+    """mcc_decompress_static: decompression whose scratch memory is a fixed
+    array inside the library (no device allocation by the call)."""
+    dtype = F64 if out.dtype == torch.float64 else F32
+    st = load().mcc_decompress_static(plan.handle, _dptr(stream_bytes), int(nbytes), _dptr(out),
+                                      dtype, 1 if sync else 0, _stream(stream))
+    _check(st, "decompress_static")
+
+
+def static_scratch_bytes() -> int:
+    return int(load().mcc_static_scratch_bytes())
