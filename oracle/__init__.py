@@ -52,7 +52,8 @@ class _Grid(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("dtype", C.c_int), ("eb_mode", C.c_int), ("eb", C.c_double),
                 ("grid_fraction", C.c_double), ("R1", C.c_int), ("R2", C.c_int),
-                ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int)]
+                ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int),
+                ("model", C.c_void_p), ("model_bytes", C.c_size_t)]
 
 
 class _Field(C.Structure):
@@ -85,6 +86,9 @@ def _load():
             lib.orc_canonical_codes.argtypes = [P, C.c_int, P]
             lib.orc_lorenzo.argtypes = [C.c_int, P, P, P]
             lib.orc_lorenzo_inverse.argtypes = [C.c_int, P, P, P]
+            lib.orc_mlp_predict.argtypes = [C.c_int, P, C.c_size_t, P, P, C.c_float, C.c_int64, P, P]
+            lib.orc_mlp_quantize.argtypes = [C.c_int, C.c_int, P, C.c_float, C.c_float, P]
+            lib.orc_mlp_grad.argtypes = [P, P, P, P, P, P, P, P, C.c_int64, C.c_int, C.c_int, P, P]
             _lib = lib
     return _lib
 
@@ -181,10 +185,17 @@ DEFAULTS = dict(eb_mode="rel", eb=1e-4, grid_fraction=0.5, R1=512, R2=512, C1=12
                 lmax=24)
 
 
-def make_params(dtype, **kw):
+def make_params(dtype, model=None, **kw):
+    """Parameters; ``model`` is a learned-predictor blob (uint8 array) or None.
+    The returned structure keeps a reference to the blob."""
     p = dict(DEFAULTS)
     p.update(kw)
     out = _Params()
+    if model is not None:
+        blob = np.ascontiguousarray(model, dtype=np.uint8)
+        out._blob = blob
+        out.model = blob.ctypes.data
+        out.model_bytes = blob.size
     out.dtype = 0 if np.dtype(dtype) == np.float64 else 1
     out.eb_mode = 1 if p["eb_mode"] in ("rel", 1) else 0
     out.eb = float(p["eb"])
@@ -288,3 +299,88 @@ def lorenzo_inverse(d):
     q = np.empty_like(d)
     _load().orc_lorenzo_inverse(dim, _ptr(n), _ptr(d), _ptr(q))
     return q
+
+
+# --------------------------------------------------------------------------- #
+# learned predictor
+# --------------------------------------------------------------------------- #
+MODEL_BYTES = 5736
+MLP_PARAMS = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def pack_model(dim, sx, s1, s2, e3, W1, W2, W3, b1, b2, b3):
+    """Model blob from its integer fields (the byte format the stream embeds):
+    magic, version 1, dim, n_in, sx, s1, s2, e3, W1 int8 [64][16],
+    W2 int8 [64][64], W3 int8 [64], b1, b2 int32 [64], b3 int32."""
+    blob = np.zeros(MODEL_BYTES, np.uint8)
+    head = np.array([0x4D43434D, 1, dim, (1 << dim) - 1 + dim, sx, s1, s2, e3], np.int64)
+    blob[0:32] = head.astype(np.uint32).view(np.uint8)
+    blob[32:1056] = np.asarray(W1, np.int8).reshape(-1).view(np.uint8)
+    blob[1056:5152] = np.asarray(W2, np.int8).reshape(-1).view(np.uint8)
+    blob[5152:5216] = np.asarray(W3, np.int8).reshape(-1).view(np.uint8)
+    blob[5216:5472] = np.asarray(b1, np.int32).view(np.uint8)
+    blob[5472:5728] = np.asarray(b2, np.int32).view(np.uint8)
+    blob[5728:5732] = np.asarray([b3], np.int32).view(np.uint8)
+    return blob
+
+
+def unpack_model(blob):
+    """Inverse of pack_model: dict of the integer fields."""
+    blob = np.asarray(blob, np.uint8)
+    head = blob[0:32].view(np.int32)
+    return dict(magic=int(np.uint32(head[0])), version=int(head[1]), dim=int(head[2]),
+                n_in=int(head[3]), sx=int(head[4]), s1=int(head[5]), s2=int(head[6]),
+                e3=int(head[7]), W1=blob[32:1056].view(np.int8).reshape(64, 16).copy(),
+                W2=blob[1056:5152].view(np.int8).reshape(64, 64).copy(),
+                W3=blob[5152:5216].view(np.int8).copy(), b1=blob[5216:5472].view(np.int32).copy(),
+                b2=blob[5472:5728].view(np.int32).copy(), b3=int(blob[5728:5732].view(np.int32)[0]))
+
+
+def split_params(params):
+    """Float parameter vector (5313) -> W1 [64,16], b1, W2 [64,64], b2, W3, b3."""
+    params = np.asarray(params)
+    o = np.cumsum([0, 1024, 64, 4096, 64, 64, 1])
+    W1, b1, W2, b2, W3, b3 = (params[o[i]:o[i + 1]] for i in range(6))
+    return W1.reshape(64, 16), b1, W2.reshape(64, 64), b2, W3, b3
+
+
+def mlp_quantize(dim, sx, params, max_z1, max_z2):
+    """Post-training quantisation of the float network into a model blob."""
+    params = _c(params, np.float32)
+    assert params.size == MLP_PARAMS
+    blob = np.zeros(MODEL_BYTES, np.uint8)
+    st = _load().orc_mlp_quantize(dim, sx, _ptr(params), float(max_z1), float(max_z2), _ptr(blob))
+    if st:
+        raise OracleError(st, "mlp_quantize")
+    return blob
+
+
+def mlp_predict(dim, model, corners, fr, rho12_f):
+    """Integer-exact predictor: corners int32 [n, 8], fr float32 [n, 3] ->
+    (features int32 [n, 16], p float32 [n])."""
+    model = _c(model, np.uint8)
+    corners = _c(corners, np.int32)
+    fr = _c(fr, np.float32)
+    n = corners.shape[0]
+    feats = np.zeros((n, 16), np.int32)
+    p = np.zeros(n, np.float32)
+    st = _load().orc_mlp_predict(dim, _ptr(model), model.size, _ptr(corners), _ptr(fr),
+                                 float(rho12_f), n, _ptr(feats), _ptr(p))
+    if st:
+        raise OracleError(st, "mlp_predict")
+    return feats, p
+
+
+def mlp_grad(W1, b1, W2, b2, W3, b3, X, Y, loss="l1", rounding=True):
+    """FP64 loss and gradient of the training network. loss: "l1" (mean
+    absolute error) or "l2" (mean squared error); rounding: round the
+    tensor-core operands to bfloat16 as the GPU does."""
+    arrs = [_c(a, np.float32) for a in (W1, b1, W2, b2, W3, b3, X, Y)]
+    grad = np.zeros(MLP_PARAMS)
+    lossv = np.zeros(1)
+    st = _load().orc_mlp_grad(*[_ptr(a) for a in arrs], arrs[6].shape[0],
+                              {"l2": 0, "l1": 1}[loss], 1 if rounding else 0, _ptr(grad),
+                              _ptr(lossv))
+    if st:
+        raise ValueError(f"orc_mlp_grad: status {st}")
+    return float(lossv[0]), grad

@@ -398,6 +398,183 @@ static int64_t rescale(int64_t a, float acc, int64_t rq, float rf) {
   return hi + (int64_t)rintf(t);
 }
 
+/* g at a vertex: the corner codes of its cell (order 000, 100, 010, 110, 001,
+ * 101, 011, 111; x fastest) and the multilinear interpolation written on the
+ * integer differences from corner 000, in FP32 with the fused multiply-adds
+ * written out. Returns acc (the interpolation minus c000, in grid bins). */
+static float vertex_interp(int dim, const int32_t *q1, int64_t nx, int64_t ny, uint32_t c, float fx,
+                           float fy, float fz, int32_t cor[8]) {
+  cor[0] = q1[c];
+  cor[1] = q1[c + 1];
+  cor[2] = q1[c + nx];
+  cor[3] = q1[c + nx + 1];
+  int32_t c000 = cor[0], c100 = cor[1], c010 = cor[2], c110 = cor[3];
+  int32_t d100 = wrap_sub(c100, c000), d010 = wrap_sub(c010, c000);
+  int32_t d110 = wrap_add(wrap_sub(wrap_sub(c110, c100), c010), c000);
+  float acc;
+  if (dim == 2) {
+    acc = fx * (float)d100;
+    acc = fmaf(fy, (float)d010, acc);
+    float fxy = fx * fy;
+    acc = fmaf(fxy, (float)d110, acc);
+    return acc;
+  }
+  int64_t sxy = nx * ny;
+  cor[4] = q1[c + sxy];
+  cor[5] = q1[c + sxy + 1];
+  cor[6] = q1[c + sxy + nx];
+  cor[7] = q1[c + sxy + nx + 1];
+  int32_t c001 = cor[4], c101 = cor[5], c011 = cor[6], c111 = cor[7];
+  int32_t d001 = wrap_sub(c001, c000);
+  int32_t d101 = wrap_add(wrap_sub(wrap_sub(c101, c100), c001), c000);
+  int32_t d011 = wrap_add(wrap_sub(wrap_sub(c011, c010), c001), c000);
+  int32_t d111 = wrap_sub(c111, c110);
+  d111 = wrap_sub(d111, c101);
+  d111 = wrap_sub(d111, c011);
+  d111 = wrap_add(d111, c100);
+  d111 = wrap_add(d111, c010);
+  d111 = wrap_add(d111, c001);
+  d111 = wrap_sub(d111, c000);
+  acc = fx * (float)d100;
+  acc = fmaf(fy, (float)d010, acc);
+  acc = fmaf(fz, (float)d001, acc);
+  float fxy = fx * fy, fxz = fx * fz, fyz = fy * fz;
+  float fxyz = fxy * fz;
+  acc = fmaf(fxy, (float)d110, acc);
+  acc = fmaf(fxz, (float)d101, acc);
+  acc = fmaf(fyz, (float)d011, acc);
+  acc = fmaf(fxyz, (float)d111, acc);
+  return acc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* learned residual predictor: an integer-exact MLP                         */
+/* ------------------------------------------------------------------------ */
+/* Inputs: the corner codes' differences from corner 000 in vertex bins,
+ * e_k = (c_k - c_000) * (s1/s2), scaled by 2^-sx and rounded to [-127, 127],
+ * and the local coordinates rounded to 0..127. Two hidden layers of 64 ReLU
+ * units with 8-bit activations (right shifts s1, s2 with rounding, clamped to
+ * 0..255), int8 weights, int32 biases, output p = acc3 * 2^e3 in vertex bins.
+ * Every sum is an integer below 2^24 in magnitude, so it is exact in any
+ * order and in FP32 as well as in integers. */
+#define MLP_H 64
+#define MLP_K 16
+#define MODEL_MAGIC 0x4D43434Du /* 'M' 'C' 'C' 'M' */
+#define MODEL_BYTES 5736u
+
+typedef struct {
+  int dim, n_in, sx, s1, s2, e3;
+  int8_t W1[MLP_H][MLP_K], W2[MLP_H][MLP_H], W3[MLP_H];
+  int32_t b1[MLP_H], b2[MLP_H], b3;
+} mlp_t;
+
+static int model_parse(const uint8_t *b, size_t n, int dim, mlp_t *m) {
+  if (!b || n != MODEL_BYTES) return ORC_ERR_INVALID_ARG;
+  if (get_u32(b) != MODEL_MAGIC || get_u32(b + 4) != 1) return ORC_ERR_INVALID_ARG;
+  m->dim = (int)get_u32(b + 8);
+  m->n_in = (int)get_u32(b + 12);
+  memcpy(&m->sx, b + 16, 4);
+  memcpy(&m->s1, b + 20, 4);
+  memcpy(&m->s2, b + 24, 4);
+  memcpy(&m->e3, b + 28, 4);
+  if (m->dim != dim || m->n_in != (1 << dim) - 1 + dim) return ORC_ERR_INVALID_ARG;
+  if (m->sx < -60 || m->sx > 60 || m->s1 < 1 || m->s1 > 30 || m->s2 < 1 || m->s2 > 30 ||
+      m->e3 < -100 || m->e3 > 60)
+    return ORC_ERR_INVALID_ARG;
+  memcpy(m->W1, b + 32, sizeof(m->W1));
+  memcpy(m->W2, b + 1056, sizeof(m->W2));
+  memcpy(m->W3, b + 5152, sizeof(m->W3));
+  memcpy(m->b1, b + 5216, sizeof(m->b1));
+  memcpy(m->b2, b + 5472, sizeof(m->b2));
+  memcpy(&m->b3, b + 5728, 4);
+  for (int j = 0; j < MLP_H; j++) {
+    for (int i = 0; i < MLP_K; i++)
+      if (m->W1[j][i] < -127 || (i >= m->n_in && m->W1[j][i] != 0)) return ORC_ERR_INVALID_ARG;
+    for (int i = 0; i < MLP_H; i++)
+      if (m->W2[j][i] < -127) return ORC_ERR_INVALID_ARG;
+    if (m->W3[j] < -127) return ORC_ERR_INVALID_ARG;
+    if (m->b1[j] < -(1 << 22) || m->b1[j] > (1 << 22) || m->b2[j] < -(1 << 22) ||
+        m->b2[j] > (1 << 22))
+      return ORC_ERR_INVALID_ARG;
+  }
+  if (m->b3 < -(1 << 22) || m->b3 > (1 << 22)) return ORC_ERR_INVALID_ARG;
+  return ORC_OK;
+}
+
+static void mlp_features(int dim, int sx, const int32_t cor[8], float fx, float fy, float fz,
+                         float rho12_f, int32_t xq[MLP_K]) {
+  const int nc = 1 << dim;
+  const float scale = ldexpf(1.0f, -sx);
+  memset(xq, 0, sizeof(int32_t) * MLP_K);
+  for (int k = 1; k < nc; k++) {
+    float e = (float)wrap_sub(cor[k], cor[0]) * rho12_f;
+    e = e * scale;
+    float r = rintf(e);
+    if (r > 127.0f) r = 127.0f;
+    if (r < -127.0f) r = -127.0f;
+    xq[k - 1] = (int32_t)r;
+  }
+  const float f3[3] = {fx, fy, fz};
+  for (int d = 0; d < dim; d++) xq[nc - 1 + d] = (int32_t)rintf(f3[d] * 127.0f);
+}
+
+static int32_t act8(int32_t a, int s) {
+  /* round(a / 2^s) half up, clamped to 0..255 (negative sums give 0) */
+  int64_t t = (int64_t)a + ((int64_t)1 << (s - 1));
+  if (t < 0) return 0;
+  int64_t v = t >> s;
+  return v > 255 ? 255 : (int32_t)v;
+}
+
+static float mlp_forward(const mlp_t *m, const int32_t xq[MLP_K]) {
+  int32_t h1[MLP_H], h2[MLP_H];
+  for (int j = 0; j < MLP_H; j++) {
+    int32_t a = m->b1[j];
+    for (int i = 0; i < MLP_K; i++) a += (int32_t)m->W1[j][i] * xq[i];
+    h1[j] = act8(a, m->s1);
+  }
+  for (int j = 0; j < MLP_H; j++) {
+    int32_t a = m->b2[j];
+    for (int i = 0; i < MLP_H; i++) a += (int32_t)m->W2[j][i] * h1[i];
+    h2[j] = act8(a, m->s2);
+  }
+  int32_t a = m->b3;
+  for (int i = 0; i < MLP_H; i++) a += (int32_t)m->W3[i] * h2[i];
+  return ldexpf((float)a, m->e3);
+}
+
+/* P = round((s1/s2) g + p): the fixed-point rescale of the interpolation with
+ * the network's correction added in FP32 before rounding. */
+static int64_t rescale_p(int64_t a, float acc, int64_t rq, float rf, float p) {
+  const uint64_t mask = ((uint64_t)1 << RHO_BITS) - 1;
+  unsigned __int128 U = (unsigned __int128)(uint64_t)(a < 0 ? -a : a) * (uint64_t)rq;
+  uint64_t q = (uint64_t)(U >> RHO_BITS), r = (uint64_t)U & mask;
+  int64_t hi;
+  uint64_t lo;
+  if (a >= 0) { hi = (int64_t)q; lo = r; }
+  else if (r == 0) { hi = -(int64_t)q; lo = 0; }
+  else { hi = -(int64_t)q - 1; lo = ((uint64_t)1 << RHO_BITS) - r; }
+  float base = (float)lo * 0x1p-40f;
+  float t = fmaf(acc, rf, base);
+  t = t + p;
+  return hi + (int64_t)rintf(t);
+}
+
+int orc_mlp_predict(int dim, const uint8_t *model, size_t model_bytes, const int32_t *corners,
+                    const float *fr, float rho12_f, int64_t n, int32_t *features, float *p) {
+  mlp_t m;
+  int st = model_parse(model, model_bytes, dim, &m);
+  if (st) return st;
+  for (int64_t i = 0; i < n; i++) {
+    int32_t xq[MLP_K];
+    const int32_t *cor = corners + 8 * i;
+    mlp_features(dim, m.sx, cor, fr[3 * i], fr[3 * i + 1], fr[3 * i + 2], rho12_f, xq);
+    if (features) memcpy(features + MLP_K * i, xq, sizeof(xq));
+    p[i] = mlp_forward(&m, xq);
+  }
+  return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Lorenzo prediction on the grid codes (zero outside the grid)              */
 /* ------------------------------------------------------------------------ */
@@ -550,7 +727,7 @@ int orc_canonical_codes(const uint8_t *len, int nsym, uint32_t *code) {
 /* ------------------------------------------------------------------------ */
 typedef struct {
   size_t lens1, lens2, gtab1, gtab2, etab1, etab2, rtab2, ltab1, ltab2, out1, out2, raw, bits1,
-      bits2, total;
+      bits2, model, total;
 } layout_t;
 
 static int64_t ngroups(int64_t n, int C) { return n == 0 ? 0 : (n + 32 * (int64_t)C - 1) / (32 * (int64_t)C); }
@@ -558,9 +735,10 @@ static int64_t ngroups(int64_t n, int C) { return n == 0 ? 0 : (n + 32 * (int64_
 /* Section order: header | code lengths 1, 2 | group word offsets 1, 2 |
  * group escape-count prefixes 1, 2 | group raw-count prefix 2 | lane bit
  * lengths 1, 2 | escape values 1, 2 (int32) | raw values (dtype) |
- * bitstream 1, 2 (u32 words). */
+ * bitstream 1, 2 (u32 words) | predictor model (when used, 8-byte aligned). */
 static void make_layout(int R1, int R2, int64_t ng1, int64_t ng2, uint64_t nout1, uint64_t nout2,
-                        uint64_t nraw, size_t vsz, uint64_t words1, uint64_t words2, layout_t *L) {
+                        uint64_t nraw, size_t vsz, uint64_t words1, uint64_t words2,
+                        size_t model_bytes, layout_t *L) {
   size_t o = HEADER_BYTES;
   L->lens1 = o; o += 2 * (size_t)R1;
   L->lens2 = o; o += 2 * (size_t)R2;
@@ -579,6 +757,8 @@ static void make_layout(int R1, int R2, int64_t ng1, int64_t ng2, uint64_t nout1
   o = align_up(o, 4);
   L->bits1 = o; o += 4 * (size_t)words1;
   L->bits2 = o; o += 4 * (size_t)words2;
+  o = align_up(o, 8);
+  L->model = o; o += model_bytes;
   L->total = o;
 }
 
@@ -596,7 +776,7 @@ size_t orc_compress_bound(const orc_grid *g, int64_t n_v, const orc_params *p) {
   uint64_t w1 = (uint64_t)((ng * p->lmax + 31) / 32 + g1);
   uint64_t w2 = (uint64_t)((n_v * p->lmax + 31) / 32 + g2);
   layout_t L;
-  make_layout(p->R1, p->R2, g1, g2, (uint64_t)ng, 0, (uint64_t)n_v, vsz, w1, w2, &L);
+  make_layout(p->R1, p->R2, g1, g2, (uint64_t)ng, 0, (uint64_t)n_v, vsz, w1, w2, MODEL_BYTES, &L);
   return L.total + 16;
 }
 
@@ -662,6 +842,9 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   const int64_t ng = nx * ny * nz;
   const size_t vsz = p->dtype == 0 ? 8 : 4;
   const int R1 = p->R1, R2 = p->R2;
+  mlp_t model;
+  const int use_model = p->model != NULL;
+  if (use_model && (st = model_parse(p->model, p->model_bytes, dim, &model))) return st;
 
   int32_t *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_v);
   int32_t *q1 = (int32_t *)malloc(sizeof(int32_t) * (size_t)ng);
@@ -719,48 +902,23 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     h1[sym1[j]]++;
   }
 
-  /* 4. g(x1') at every vertex, residual code q2 = Q - P, bound guard */
+  /* 4. g(x1') at every vertex (plus the learned correction when a model is
+   *    given), residual code q2 = Q - P, bound guard */
   uint64_t nout2 = 0, nraw = 0;
   for (int64_t i = 0; i < n_v; i++) {
-    uint32_t c = cell[i];
     float fx = (float)frac[i] * 0x1p-15f;
     float fy = (float)frac[n_v + i] * 0x1p-15f;
-    int32_t c000 = q1[c], c100 = q1[c + 1], c010 = q1[c + nx], c110 = q1[c + nx + 1];
-    int32_t d100 = wrap_sub(c100, c000), d010 = wrap_sub(c010, c000);
-    float acc;
-    if (dim == 2) {
-      int32_t d110 = wrap_add(wrap_sub(wrap_sub(c110, c100), c010), c000);
-      acc = fx * (float)d100;
-      acc = fmaf(fy, (float)d010, acc);
-      float fxy = fx * fy;
-      acc = fmaf(fxy, (float)d110, acc);
+    float fz = dim == 3 ? (float)frac[2 * n_v + i] * 0x1p-15f : 0.0f;
+    int32_t cor[8];
+    float acc = vertex_interp(dim, q1, nx, ny, cell[i], fx, fy, fz, cor);
+    int64_t P;
+    if (use_model) {
+      int32_t xq[MLP_K];
+      mlp_features(dim, model.sx, cor, fx, fy, fz, f.rho12_f, xq);
+      P = rescale_p(cor[0], acc, f.rho12_q, f.rho12_f, mlp_forward(&model, xq));
     } else {
-      float fz = (float)frac[2 * n_v + i] * 0x1p-15f;
-      int64_t sxy = nx * ny;
-      int32_t c001 = q1[c + sxy], c101 = q1[c + sxy + 1], c011 = q1[c + sxy + nx],
-              c111 = q1[c + sxy + nx + 1];
-      int32_t d001 = wrap_sub(c001, c000);
-      int32_t d110 = wrap_add(wrap_sub(wrap_sub(c110, c100), c010), c000);
-      int32_t d101 = wrap_add(wrap_sub(wrap_sub(c101, c100), c001), c000);
-      int32_t d011 = wrap_add(wrap_sub(wrap_sub(c011, c010), c001), c000);
-      int32_t d111 = wrap_sub(c111, c110);
-      d111 = wrap_sub(d111, c101);
-      d111 = wrap_sub(d111, c011);
-      d111 = wrap_add(d111, c100);
-      d111 = wrap_add(d111, c010);
-      d111 = wrap_add(d111, c001);
-      d111 = wrap_sub(d111, c000);
-      acc = fx * (float)d100;
-      acc = fmaf(fy, (float)d010, acc);
-      acc = fmaf(fz, (float)d001, acc);
-      float fxy = fx * fy, fxz = fx * fz, fyz = fy * fz;
-      float fxyz = fxy * fz;
-      acc = fmaf(fxy, (float)d110, acc);
-      acc = fmaf(fxz, (float)d101, acc);
-      acc = fmaf(fyz, (float)d011, acc);
-      acc = fmaf(fxyz, (float)d111, acc);
+      P = rescale(cor[0], acc, f.rho12_q, f.rho12_f);
     }
-    int64_t P = rescale(c000, acc, f.rho12_q, f.rho12_f);
     int64_t q2 = (int64_t)Q[i] - P;
     /* guard: reconstruct exactly as the decompressor will, check |x - x'| */
     double v = load_value(x, p->dtype, i);
@@ -791,7 +949,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     uint64_t w1 = pack_component(sym1, ng, p->C1, len1, code1, NULL, NULL, NULL, NULL, 0xFFFF, NULL);
     uint64_t w2 = pack_component(sym2, n_v, p->C2, len2, code2, NULL, NULL, NULL, NULL, 0xFFFF, NULL);
     layout_t L;
-    make_layout(R1, R2, g1, g2, nout1, nout2, nraw, vsz, w1, w2, &L);
+    make_layout(R1, R2, g1, g2, nout1, nout2, nraw, vsz, w1, w2, use_model ? MODEL_BYTES : 0, &L);
     *out_size = L.total;
     if (L.total > capacity || !out) { st = ORC_ERR_CAPACITY; goto done; }
     memset(out, 0, L.total);
@@ -801,7 +959,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     put_u32(h + 8, HEADER_BYTES);
     put_u32(h + 12, (uint32_t)p->dtype);
     put_u32(h + 16, (uint32_t)dim);
-    put_u32(h + 20, (uint32_t)(f.guard ? 1 : 0));
+    put_u32(h + 20, (uint32_t)((f.guard ? 1 : 0) | (use_model ? 2 : 0)));
     put_u32(h + 24, (uint32_t)R1);
     put_u32(h + 28, (uint32_t)R2);
     put_u32(h + 32, (uint32_t)p->C1);
@@ -827,6 +985,8 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     put_u64(h + 168, w1);
     put_u64(h + 176, w2);
     put_u64(h + 184, (uint64_t)L.total);
+    put_u64(h + 192, (uint64_t)(use_model ? MODEL_BYTES : 0));
+    if (use_model) memcpy(out + L.model, p->model, MODEL_BYTES);
     memcpy(out + L.lens1, len1, (size_t)2 * R1);
     memcpy(out + L.lens2, len2, (size_t)2 * R2);
     pack_component(sym1, ng, p->C1, len1, code1, (uint32_t *)(out + L.gtab1),
@@ -983,7 +1143,7 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
   if (dim != g->dim || nx != g->n[0] || ny != g->n[1] || nz != g->n[2]) return ORC_ERR_CORRUPT;
   if ((int64_t)get_u64(in + 56) != n_v || (int64_t)get_u64(in + 64) != nx * ny * nz)
     return ORC_ERR_CORRUPT;
-  orc_params chk = {dtype, 0, 1.0, 0.5, R1, R2, C1, C2, lmax};
+  orc_params chk = {dtype, 0, 1.0, 0.5, R1, R2, C1, C2, lmax, NULL, 0};
   if (check_params(&chk)) return ORC_ERR_CORRUPT;
   const int64_t ng = nx * ny * nz;
   const double s2 = get_f64(in + 104);
@@ -996,9 +1156,17 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
   if (nout1 > (uint64_t)ng || nout2 > (uint64_t)n_v || nraw > (uint64_t)n_v) return ORC_ERR_CORRUPT;
   if (w1 > (uint64_t)ng * 24 + 64 || w2 > (uint64_t)n_v * 24 + 64) return ORC_ERR_CORRUPT;
   const size_t vsz = dtype == 0 ? 8 : 4;
+  const uint32_t flags = get_u32(in + 20);
+  const uint64_t mbytes = get_u64(in + 192);
+  const int use_model = (flags & 2) != 0;
+  if (flags & ~3u) return ORC_ERR_CORRUPT;
+  if (mbytes != (use_model ? MODEL_BYTES : 0)) return ORC_ERR_CORRUPT;
   layout_t L;
-  make_layout(R1, R2, ngroups(ng, C1), ngroups(n_v, C2), nout1, nout2, nraw, vsz, w1, w2, &L);
+  make_layout(R1, R2, ngroups(ng, C1), ngroups(n_v, C2), nout1, nout2, nraw, vsz, w1, w2,
+              (size_t)mbytes, &L);
   if (L.total != total || total > size) return ORC_ERR_CORRUPT;
+  mlp_t model;
+  if (use_model && model_parse(in + L.model, MODEL_BYTES, dim, &model)) return ORC_ERR_CORRUPT;
 
   int st = ORC_OK;
   uint16_t *sym1 = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)ng);
@@ -1040,45 +1208,19 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
       } else {
         q2 = (int64_t)s - R2;
       }
-      uint32_t c = cell[i];
       float fx = (float)frac[i] * 0x1p-15f;
       float fy = (float)frac[n_v + i] * 0x1p-15f;
-      int32_t c000 = q1[c], c100 = q1[c + 1], c010 = q1[c + nx], c110 = q1[c + nx + 1];
-      int32_t d100 = wrap_sub(c100, c000), d010 = wrap_sub(c010, c000);
-      float acc;
-      if (dim == 2) {
-        int32_t d110 = wrap_add(wrap_sub(wrap_sub(c110, c100), c010), c000);
-        acc = fx * (float)d100;
-        acc = fmaf(fy, (float)d010, acc);
-        float fxy = fx * fy;
-        acc = fmaf(fxy, (float)d110, acc);
+      float fz = dim == 3 ? (float)frac[2 * n_v + i] * 0x1p-15f : 0.0f;
+      int32_t cor[8];
+      float acc = vertex_interp(dim, q1, nx, ny, cell[i], fx, fy, fz, cor);
+      int64_t P;
+      if (use_model) {
+        int32_t xq[MLP_K];
+        mlp_features(dim, model.sx, cor, fx, fy, fz, rho12_f, xq);
+        P = rescale_p(cor[0], acc, rho12_q, rho12_f, mlp_forward(&model, xq));
       } else {
-        float fz = (float)frac[2 * n_v + i] * 0x1p-15f;
-        int64_t sxy = nx * ny;
-        int32_t c001 = q1[c + sxy], c101 = q1[c + sxy + 1], c011 = q1[c + sxy + nx],
-                c111 = q1[c + sxy + nx + 1];
-        int32_t d001 = wrap_sub(c001, c000);
-        int32_t d110 = wrap_add(wrap_sub(wrap_sub(c110, c100), c010), c000);
-        int32_t d101 = wrap_add(wrap_sub(wrap_sub(c101, c100), c001), c000);
-        int32_t d011 = wrap_add(wrap_sub(wrap_sub(c011, c010), c001), c000);
-        int32_t d111 = wrap_sub(c111, c110);
-        d111 = wrap_sub(d111, c101);
-        d111 = wrap_sub(d111, c011);
-        d111 = wrap_add(d111, c100);
-        d111 = wrap_add(d111, c010);
-        d111 = wrap_add(d111, c001);
-        d111 = wrap_sub(d111, c000);
-        acc = fx * (float)d100;
-        acc = fmaf(fy, (float)d010, acc);
-        acc = fmaf(fz, (float)d001, acc);
-        float fxy = fx * fy, fxz = fx * fz, fyz = fy * fz;
-        float fxyz = fxy * fz;
-        acc = fmaf(fxy, (float)d110, acc);
-        acc = fmaf(fxz, (float)d101, acc);
-        acc = fmaf(fyz, (float)d011, acc);
-        acc = fmaf(fxyz, (float)d111, acc);
+        P = rescale(cor[0], acc, rho12_q, rho12_f);
       }
-      int64_t P = rescale(c000, acc, rho12_q, rho12_f);
       double xr = s2 * (double)(K + P + q2);
       if (dtype == 0) ((double *)xout)[i] = xr;
       else ((float *)xout)[i] = (float)xr;
@@ -1089,4 +1231,182 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
 done:
   free(sym1); free(sym2); free(dl); free(q1);
   return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* training network (the float form the predictor is trained in)            */
+/* ------------------------------------------------------------------------ */
+/* Round a float to bfloat16 (nearest, ties to even) and back. */
+static double bf16(float v) {
+  uint32_t b;
+  memcpy(&b, &v, 4);
+  if ((b & 0x7F800000u) == 0x7F800000u) return (double)v; /* inf / nan unchanged */
+  uint32_t lsb = (b >> 16) & 1u;
+  b = (b + 0x7FFFu + lsb) & 0xFFFF0000u;
+  float r;
+  memcpy(&r, &b, 4);
+  return (double)r;
+}
+
+/* Loss and gradient of the float training network p = W3 a2 + b3,
+ * a2 = relu(W2 a1 + b2), a1 = relu(W1 x + b1), over a batch of B samples:
+ * mean absolute error (loss_kind 1) or mean squared error (loss_kind 0).
+ * Layout: W1 [64][16], b1 [64], W2 [64][64], b2 [64], W3 [64], b3 [1]; grad
+ * in the same layout (5313 values).
+ *
+ * rounding 0: the network in FP64 as written (the definition).
+ * rounding 1: every operand of a tensor-core product rounded to bfloat16 as
+ * the GPU rounds it: the weights, the inputs, a1 and a2 in the forward pass;
+ * da2 (the gradient at the second hidden layer) where it multiplies a1 (for
+ * dW2) and W2 (for da1), and da1 where it multiplies x (for dW1). The bias
+ * gradients, dW3 and everything else stay unrounded. Sums are in FP64. */
+int orc_mlp_grad(const float *W1, const float *b1, const float *W2, const float *b2,
+                 const float *W3, const float *b3, const float *X, const float *Y, int64_t B,
+                 int loss_kind, int rounding, double *grad, double *loss) {
+  if (B <= 0 || (loss_kind != 0 && loss_kind != 1) || (rounding != 0 && rounding != 1))
+    return ORC_ERR_INVALID_ARG;
+  double w1[MLP_H][MLP_K], w2[MLP_H][MLP_H], w3[MLP_H];
+#define RND(v) (rounding ? bf16((float)(v)) : (double)(v))
+  for (int j = 0; j < MLP_H; j++) {
+    for (int i = 0; i < MLP_K; i++) w1[j][i] = RND(W1[j * MLP_K + i]);
+    for (int i = 0; i < MLP_H; i++) w2[j][i] = RND(W2[j * MLP_H + i]);
+    w3[j] = RND(W3[j]);
+  }
+  const size_t ng = (size_t)MLP_H * MLP_K + MLP_H + (size_t)MLP_H * MLP_H + MLP_H + MLP_H + 1;
+  memset(grad, 0, sizeof(double) * ng);
+  double *gW1 = grad, *gb1 = gW1 + MLP_H * MLP_K, *gW2 = gb1 + MLP_H, *gb2 = gW2 + MLP_H * MLP_H,
+         *gW3 = gb2 + MLP_H, *gb3 = gW3 + MLP_H;
+  double L = 0.0;
+  for (int64_t n = 0; n < B; n++) {
+    double x[MLP_K], z1[MLP_H], a1[MLP_H], z2[MLP_H], a2[MLP_H];
+    for (int i = 0; i < MLP_K; i++) x[i] = RND(X[n * MLP_K + i]);
+    for (int j = 0; j < MLP_H; j++) {
+      double z = b1[j];
+      for (int i = 0; i < MLP_K; i++) z += w1[j][i] * x[i];
+      z1[j] = z;
+      a1[j] = RND(z > 0.0 ? z : 0.0);
+    }
+    for (int j = 0; j < MLP_H; j++) {
+      double z = b2[j];
+      for (int i = 0; i < MLP_H; i++) z += w2[j][i] * a1[i];
+      z2[j] = z;
+      a2[j] = RND(z > 0.0 ? z : 0.0);
+    }
+    double pr = b3[0];
+    for (int i = 0; i < MLP_H; i++) pr += w3[i] * a2[i];
+    const double e = pr - (double)Y[n];
+    double dp;
+    if (loss_kind == 0) {
+      L += e * e;
+      dp = 2.0 * e / (double)B;
+    } else {
+      L += fabs(e);
+      dp = (e > 0.0 ? 1.0 : e < 0.0 ? -1.0 : 0.0) / (double)B;
+    }
+    gb3[0] += dp;
+    double da2[MLP_H], da2r[MLP_H], da1[MLP_H];
+    for (int i = 0; i < MLP_H; i++) {
+      gW3[i] += dp * a2[i];
+      da2[i] = z2[i] > 0.0 ? dp * w3[i] : 0.0;
+      da2r[i] = RND(da2[i]);
+    }
+    for (int j = 0; j < MLP_H; j++) {
+      gb2[j] += da2[j];
+      for (int i = 0; i < MLP_H; i++) gW2[j * MLP_H + i] += da2r[j] * a1[i];
+    }
+    for (int i = 0; i < MLP_H; i++) {
+      double t = 0.0;
+      for (int j = 0; j < MLP_H; j++) t += w2[j][i] * da2r[j];
+      da1[i] = z1[i] > 0.0 ? t : 0.0;
+    }
+    for (int j = 0; j < MLP_H; j++) {
+      gb1[j] += da1[j];
+      const double d = RND(da1[j]);
+      for (int i = 0; i < MLP_K; i++) gW1[j * MLP_K + i] += d * x[i];
+    }
+  }
+#undef RND
+  *loss = L / (double)B;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* post-training quantisation of the float network                          */
+/* ------------------------------------------------------------------------ */
+/* Largest a in [-40, 40] with maxw 2^a <= 127 (0 for a zero matrix). */
+static int weight_exp(double maxw) {
+  if (maxw == 0.0) return 0;
+  int a = -40;
+  while (a < 40 && ldexp(maxw, a + 1) <= 127.0) a++;
+  return a;
+}
+
+/* Smallest t in [-60, 60] with maxz 2^-t <= 255. */
+static int act_exp(double maxz) {
+  int t = -60;
+  while (t < 60 && ldexp(maxz, -t) > 255.0) t++;
+  return t;
+}
+
+static int32_t qbias(float b, int k) {
+  double v = rint(ldexp((double)b, k));
+  if (v > (double)(1 << 22)) v = (double)(1 << 22);
+  if (v < -(double)(1 << 22)) v = -(double)(1 << 22);
+  return (int32_t)v;
+}
+
+/* The float network takes x = X 2^-7 (X the integer features). With weight
+ * exponents a_l (W_l 2^a_l rounded to int8) and activation exponents t_l
+ * (the hidden values are relu(z_l) 2^-t_l on 0..255, t_l the smallest that
+ * fits the calibration maximum max_z_l), the integer accumulators are
+ * 2^(a1+7) z1, 2^(a2-t1) z2 and 2^(a3-t2) p, so s1 = t1 + a1 + 7,
+ * s2 = t2 + a2 - t1 and e3 = t2 - a3. A shift above 30 lowers the weight
+ * exponent, one below 1 raises the activation exponent. */
+int orc_mlp_quantize(int dim, int sx, const float *params, float max_z1, float max_z2,
+                     uint8_t *model) {
+  if ((dim != 2 && dim != 3) || sx < -60 || sx > 60 || !params || !model) return ORC_ERR_INVALID_ARG;
+  if (!(max_z1 >= 0.0f) || !(max_z2 >= 0.0f) || isinf(max_z1) || isinf(max_z2))
+    return ORC_ERR_INVALID_ARG;
+  const int n_in = (1 << dim) - 1 + dim;
+  const float *W1 = params, *b1 = W1 + MLP_H * MLP_K, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H,
+              *W3 = b2 + MLP_H, *b3 = W3 + MLP_H;
+  double m1 = 0.0, m2 = 0.0, m3 = 0.0;
+  for (int j = 0; j < MLP_H; j++) {
+    for (int i = 0; i < n_in; i++) m1 = fmax(m1, fabs((double)W1[j * MLP_K + i]));
+    for (int i = 0; i < MLP_H; i++) m2 = fmax(m2, fabs((double)W2[j * MLP_H + i]));
+    m3 = fmax(m3, fabs((double)W3[j]));
+  }
+  if (!(m1 <= 1e30 && m2 <= 1e30 && m3 <= 1e30)) return ORC_ERR_INVALID_ARG;
+  int a1 = weight_exp(m1), t1 = act_exp(max_z1);
+  int s1 = t1 + a1 + 7;
+  if (s1 > 30) { a1 -= s1 - 30; s1 = 30; }
+  if (s1 < 1) { t1 += 1 - s1; s1 = 1; }
+  int a2 = weight_exp(m2), t2 = act_exp(max_z2);
+  int s2 = t2 + a2 - t1;
+  if (s2 > 30) { a2 -= s2 - 30; s2 = 30; }
+  if (s2 < 1) { t2 += 1 - s2; s2 = 1; }
+  const int a3 = weight_exp(m3);
+  const int e3 = t2 - a3;
+  if (e3 < -100 || e3 > 60) return ORC_ERR_RANGE;
+
+  memset(model, 0, MODEL_BYTES);
+  put_u32(model + 0, MODEL_MAGIC);
+  put_u32(model + 4, 1);
+  put_u32(model + 8, (uint32_t)dim);
+  put_u32(model + 12, (uint32_t)n_in);
+  put_u32(model + 16, (uint32_t)sx);
+  put_u32(model + 20, (uint32_t)s1);
+  put_u32(model + 24, (uint32_t)s2);
+  put_u32(model + 28, (uint32_t)e3);
+  for (int j = 0; j < MLP_H; j++) {
+    for (int i = 0; i < n_in; i++)
+      model[32 + j * MLP_K + i] = (uint8_t)(int8_t)rint(ldexp((double)W1[j * MLP_K + i], a1));
+    for (int i = 0; i < MLP_H; i++)
+      model[1056 + j * MLP_H + i] = (uint8_t)(int8_t)rint(ldexp((double)W2[j * MLP_H + i], a2));
+    model[5152 + j] = (uint8_t)(int8_t)rint(ldexp((double)W3[j], a3));
+    put_u32(model + 5216 + 4 * j, (uint32_t)qbias(b1[j], a1 + 7));
+    put_u32(model + 5472 + 4 * j, (uint32_t)qbias(b2[j], a2 - t1));
+  }
+  put_u32(model + 5728, (uint32_t)qbias(b3[0], a3 - t2));
+  return ORC_OK;
 }

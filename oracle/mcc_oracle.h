@@ -66,6 +66,8 @@ typedef struct {
   int R1, R2;         /* quantisation radii (alphabet 2R) */
   int C1, C2;         /* symbols per lane chunk */
   int lmax;           /* Huffman length limit */
+  const uint8_t *model; /* learned predictor (integer MLP blob) or NULL */
+  size_t model_bytes;
 } orc_params;
 
 /* Per-field scalars derived from the values (Sec. III bound split). */
@@ -98,6 +100,27 @@ int orc_huffman_lengths(const uint64_t *count, int nsym, int lmax, uint8_t *len)
 int orc_canonical_codes(const uint8_t *len, int nsym, uint32_t *code);
 void orc_lorenzo(int dim, const int32_t n[3], const int32_t *q, int32_t *delta);
 void orc_lorenzo_inverse(int dim, const int32_t n[3], const int32_t *delta, int32_t *q);
+
+/* Learned predictor: for n vertices given their 8 corner codes (corners,
+ * [n][8], order 000,100,010,110,001,101,011,111) and local coordinates (fr,
+ * [n][3]), the integer features ([n][16], may be NULL) and the correction p
+ * in vertex bins. */
+int orc_mlp_predict(int dim, const uint8_t *model, size_t model_bytes, const int32_t *corners,
+                    const float *fr, float rho12_f, int64_t n, int32_t *features, float *p);
+
+/* Loss (loss_kind 0: mean squared, 1: mean absolute error) and FP64
+ * gradient of the float training network on a batch; rounding 1 rounds the
+ * tensor-core operands to bfloat16 (see the definition in mcc_oracle.c). */
+int orc_mlp_grad(const float *W1, const float *b1, const float *W2, const float *b2,
+                 const float *W3, const float *b3, const float *X, const float *Y, int64_t B,
+                 int loss_kind, int rounding, double *grad, double *loss);
+
+/* Post-training quantisation of the float network (params in the gradient's
+ * layout, trained on the features times 2^-7) into a model blob of
+ * 5736 bytes, given the feature exponent sx and the calibration maxima of
+ * relu(z1) and relu(z2). */
+int orc_mlp_quantize(int dim, int sx, const float *params, float max_z1, float max_z2,
+                     uint8_t *model);
 
 #ifdef __cplusplus
 }
