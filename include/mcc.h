@@ -56,6 +56,9 @@ typedef enum {
 
 enum { MCC_F64 = 0, MCC_F32 = 1 };   /* value types */
 enum { MCC_ABS = 0, MCC_REL = 1 };   /* bound modes: absolute, or x (max - min) */
+enum { MCC_PRED_ZERO = 0, MCC_PRED_LEARNED = 1 };  /* residual predictor */
+#define MCC_MODEL_BYTES 5736   /* learned-predictor blob */
+#define MCC_MLP_PARAMS 5313    /* float parameters of the training network */
 
 /* Unstructured mesh (Sec. IV-C input: vertex coordinates {p_i} and
  * connectivity {c_j}). Triangles for dim 2, tetrahedra for dim 3. */
@@ -88,6 +91,15 @@ typedef struct {
   int R1, R2;            /* quantisation radii: alphabets of 2R symbols, 4..2048 */
   int C1, C2;            /* symbols per lane chunk (32 lanes per group), 1..256 */
   int lmax;              /* Huffman code length limit, 1..24 */
+  /* Residual predictor. MCC_PRED_ZERO: the method as published, the vertex
+   * prediction is the interpolation g(x1'). MCC_PRED_LEARNED: a learned
+   * correction p(corner codes, local coordinates) is added to g before the
+   * vertex rounding (P = round(rho12 g + p), so the bound holds as before);
+   * d_model is a device pointer (4-byte aligned) to an MCC_MODEL_BYTES blob
+   * (see mcc_model_train), copied into every stream that uses it. An invalid
+   * blob records MCC_ERR_INVALID_ARG on the device. */
+  int predictor;
+  const void *d_model;
 } mcc_params;
 
 typedef struct mcc_plan_s *mcc_plan;
@@ -101,7 +113,7 @@ typedef struct {
 } mcc_plan_info;
 
 /* Defaults: F64, REL, eb 1e-4, grid_fraction 0.5, R1 = R2 = 512,
- * C1 = C2 = 128, lmax 24. */
+ * C1 = C2 = 128, lmax 24, MCC_PRED_ZERO. */
 void mcc_params_default(mcc_params *p);
 
 /* Build the mesh -> grid mapping once per mesh (Sec. IV-B: reused across
@@ -199,6 +211,80 @@ size_t mcc_static_scratch_bytes(void);
 mcc_status mcc_workspace_result(const void *d_workspace, mcc_stream stream, size_t *out_size);
 
 const char *mcc_status_string(mcc_status s);
+
+/* ---- learned residual predictor: training ------------------------------
+ * No counterpart in the paper (its predictor for the residual component is
+ * the interpolation g alone). The correction network takes, per vertex, the
+ * corner codes of its grid cell (differences from corner 000 in vertex bins,
+ * scaled by 2^-sx and rounded to [-127, 127]; the level of corner 000 as a
+ * fraction of the value range, rounded to 0..127) and its local coordinates
+ * (rounded to 0..127), and runs two hidden layers of 64 ReLU units. The
+ * stored model is integer (int8 weights, 8-bit activations, power-of-two
+ * scales), so compressor and decompressor evaluate it bit for bit; it is
+ * trained in floating point on the residuals the method itself generates:
+ * target y = Q - rho12 g (the vertex code minus the interpolated prediction,
+ * in vertex bins), so that the corrected prediction round(rho12 g + p)
+ * leaves residual codes near zero. */
+enum { MCC_LOSS_L2 = 0, MCC_LOSS_L1 = 1 };
+
+typedef struct {
+  int steps;                 /* Adam steps, 1..1e6 (default 1500) */
+  int batch;                 /* samples per step, multiple of 128, <= 65536 (4096) */
+  float lr, beta1, beta2, eps; /* Adam (2e-3, 0.9, 0.999, 1e-8) */
+  int loss;                  /* MCC_LOSS_L1 (default) or MCC_LOSS_L2 */
+  int64_t samples_per_field; /* vertices drawn (with replacement) per field (65536) */
+  uint64_t seed;             /* sampling, minibatch and initialisation seed (1) */
+} mcc_train_cfg;
+
+void mcc_train_cfg_default(mcc_train_cfg *cfg);
+
+/* Device workspace bytes for mcc_model_train with n training fields. */
+mcc_status mcc_train_workspace_size(mcc_plan plan, const mcc_params *p, const mcc_train_cfg *cfg,
+                                    int n, size_t *bytes);
+
+/* Train a model on n fields of this plan (d_fields: a HOST array of n device
+ * pointers to n_vertices values of p->dtype; the bound parameters of p apply
+ * to every field, its predictor fields are ignored). Steps: for each field
+ * the front of the compression chain (bound split, vertex and grid codes),
+ * then cfg->samples_per_field vertices drawn by a counter-based hash with
+ * their features and targets; the feature exponent sx from the 99.9th
+ * percentile of the corner differences; cfg->steps Adam steps on minibatches
+ * of cfg->batch samples (tensor-core forward and backward passes, per-CTA
+ * partial gradients summed in a fixed order: the run is deterministic);
+ * calibration of the hidden-layer ranges over all samples; quantisation into
+ * the MCC_MODEL_BYTES blob at d_model_out (device, 4-byte aligned). The
+ * workspace (device, 256-byte aligned) must hold mcc_train_workspace_size
+ * bytes. h_loss (host, cfg->steps floats, may be NULL) receives the
+ * minibatch loss of every step. Synchronises the stream; returns the first
+ * field's device-side error (e.g. MCC_ERR_RANGE) if any. */
+mcc_status mcc_model_train(mcc_plan plan, int n, const void *const *d_fields, const mcc_params *p,
+                           const mcc_train_cfg *cfg, void *d_workspace, size_t workspace_bytes,
+                           void *d_model_out, float *h_loss, mcc_stream stream);
+
+/* One evaluation of the training network's loss and gradient, the kernels
+ * every training step runs (exposed for gradient checks). d_params: the
+ * MCC_MLP_PARAMS float parameters, layout W1 [64][16], b1 [64], W2 [64][64],
+ * b2 [64], W3 [64], b3 [1]; d_x: [B][16] inputs (16-byte aligned); d_y: [B]
+ * targets; loss MCC_LOSS_L1 (mean absolute) or MCC_LOSS_L2 (mean squared
+ * error). Writes d_grad (MCC_MLP_PARAMS floats, same layout) and *d_loss.
+ * Tensor-core operands are rounded to bf16 (weights, inputs, hidden
+ * activations, and the hidden-layer gradients where they multiply), sums are
+ * FP32. Workspace: mcc_mlp_grad_workspace_size(B) bytes (device). */
+size_t mcc_mlp_grad_workspace_size(int64_t B);
+mcc_status mcc_mlp_grad(const float *d_params, const float *d_x, const float *d_y, int64_t B,
+                        int loss, void *d_workspace, size_t workspace_bytes, float *d_grad,
+                        float *d_loss, mcc_stream stream);
+
+/* Post-training quantisation of the float parameters (the network trained on
+ * the features times 2^-7) into a model blob at d_model (device,
+ * MCC_MODEL_BYTES, 4-byte aligned): weight exponents a_l (largest with
+ * |W_l| 2^a_l <= 127), activation exponents t_l (smallest with
+ * max_z_l 2^-t_l <= 255), shifts s1 = t1 + a1 + 7, s2 = t2 + a2 - t1 (a shift
+ * above 30 lowers the weight exponent, one below 1 raises the activation
+ * exponent), e3 = t2 - a3; weights and biases rounded to nearest even. The
+ * outcome (an mcc_status) is written to *d_status (device int). */
+mcc_status mcc_mlp_quantize(int dim, int sx, const float *d_params, float max_z1, float max_z2,
+                            void *d_model, int *d_status, mcc_stream stream);
 
 /* Diagnostics (no counterpart in the paper): per-kernel device timing. While
  * enabled, every kernel that mcc_compress / mcc_decompress launches is

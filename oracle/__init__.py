@@ -86,7 +86,7 @@ def _load():
             lib.orc_canonical_codes.argtypes = [P, C.c_int, P]
             lib.orc_lorenzo.argtypes = [C.c_int, P, P, P]
             lib.orc_lorenzo_inverse.argtypes = [C.c_int, P, P, P]
-            lib.orc_mlp_predict.argtypes = [C.c_int, P, C.c_size_t, P, P, C.c_float, C.c_int64, P, P]
+            lib.orc_mlp_predict.argtypes = [C.c_int, P, C.c_size_t, P, P, C.c_float, C.c_int64, C.c_int64, P, P]
             lib.orc_mlp_quantize.argtypes = [C.c_int, C.c_int, P, C.c_float, C.c_float, P]
             lib.orc_mlp_grad.argtypes = [P, P, P, P, P, P, P, P, C.c_int64, C.c_int, C.c_int, P, P]
             _lib = lib
@@ -313,7 +313,7 @@ def pack_model(dim, sx, s1, s2, e3, W1, W2, W3, b1, b2, b3):
     magic, version 1, dim, n_in, sx, s1, s2, e3, W1 int8 [64][16],
     W2 int8 [64][64], W3 int8 [64], b1, b2 int32 [64], b3 int32."""
     blob = np.zeros(MODEL_BYTES, np.uint8)
-    head = np.array([0x4D43434D, 1, dim, (1 << dim) - 1 + dim, sx, s1, s2, e3], np.int64)
+    head = np.array([0x4D43434D, 1, dim, (1 << dim) + dim, sx, s1, s2, e3], np.int64)
     blob[0:32] = head.astype(np.uint32).view(np.uint8)
     blob[32:1056] = np.asarray(W1, np.int8).reshape(-1).view(np.uint8)
     blob[1056:5152] = np.asarray(W2, np.int8).reshape(-1).view(np.uint8)
@@ -355,9 +355,10 @@ def mlp_quantize(dim, sx, params, max_z1, max_z2):
     return blob
 
 
-def mlp_predict(dim, model, corners, fr, rho12_f):
-    """Integer-exact predictor: corners int32 [n, 8], fr float32 [n, 3] ->
-    (features int32 [n, 16], p float32 [n])."""
+def mlp_predict(dim, model, corners, fr, rho12_f, Qhi=0):
+    """Integer-exact predictor: corners int32 [n, 8], fr float32 [n, 3], s1/s2
+    in FP32 and the largest vertex code -> (features int32 [n, 16], p float32
+    [n])."""
     model = _c(model, np.uint8)
     corners = _c(corners, np.int32)
     fr = _c(fr, np.float32)
@@ -365,7 +366,7 @@ def mlp_predict(dim, model, corners, fr, rho12_f):
     feats = np.zeros((n, 16), np.int32)
     p = np.zeros(n, np.float32)
     st = _load().orc_mlp_predict(dim, _ptr(model), model.size, _ptr(corners), _ptr(fr),
-                                 float(rho12_f), n, _ptr(feats), _ptr(p))
+                                 float(rho12_f), int(Qhi), n, _ptr(feats), _ptr(p))
     if st:
         raise OracleError(st, "mlp_predict")
     return feats, p

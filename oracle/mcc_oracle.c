@@ -452,7 +452,10 @@ static float vertex_interp(int dim, const int32_t *q1, int64_t nx, int64_t ny, u
 /* ------------------------------------------------------------------------ */
 /* Inputs: the corner codes' differences from corner 000 in vertex bins,
  * e_k = (c_k - c_000) * (s1/s2), scaled by 2^-sx and rounded to [-127, 127],
- * and the local coordinates rounded to 0..127. Two hidden layers of 64 ReLU
+ * the local coordinates rounded to 0..127, and the level of corner 000 as a
+ * fraction of the value range, L = c_000 (s1/s2) / Qhi rounded to 0..127
+ * (Qhi the largest vertex code), so the network sees the corner values
+ * themselves, not only their differences. Two hidden layers of 64 ReLU
  * units with 8-bit activations (right shifts s1, s2 with rounding, clamped to
  * 0..255), int8 weights, int32 biases, output p = acc3 * 2^e3 in vertex bins.
  * Every sum is an integer below 2^24 in magnitude, so it is exact in any
@@ -477,7 +480,7 @@ static int model_parse(const uint8_t *b, size_t n, int dim, mlp_t *m) {
   memcpy(&m->s1, b + 20, 4);
   memcpy(&m->s2, b + 24, 4);
   memcpy(&m->e3, b + 28, 4);
-  if (m->dim != dim || m->n_in != (1 << dim) - 1 + dim) return ORC_ERR_INVALID_ARG;
+  if (m->dim != dim || m->n_in != (1 << dim) + dim) return ORC_ERR_INVALID_ARG;
   if (m->sx < -60 || m->sx > 60 || m->s1 < 1 || m->s1 > 30 || m->s2 < 1 || m->s2 > 30 ||
       m->e3 < -100 || m->e3 > 60)
     return ORC_ERR_INVALID_ARG;
@@ -502,7 +505,7 @@ static int model_parse(const uint8_t *b, size_t n, int dim, mlp_t *m) {
 }
 
 static void mlp_features(int dim, int sx, const int32_t cor[8], float fx, float fy, float fz,
-                         float rho12_f, int32_t xq[MLP_K]) {
+                         float rho12_f, int64_t Qhi, int32_t xq[MLP_K]) {
   const int nc = 1 << dim;
   const float scale = ldexpf(1.0f, -sx);
   memset(xq, 0, sizeof(int32_t) * MLP_K);
@@ -516,6 +519,14 @@ static void mlp_features(int dim, int sx, const int32_t cor[8], float fx, float 
   }
   const float f3[3] = {fx, fy, fz};
   for (int d = 0; d < dim; d++) xq[nc - 1 + d] = (int32_t)rintf(f3[d] * 127.0f);
+  float lv = 0.0f;
+  if (Qhi > 0) {
+    const float inv = 127.0f / (float)Qhi;
+    lv = rintf(((float)cor[0] * rho12_f) * inv);
+    if (lv > 127.0f) lv = 127.0f;
+    if (lv < 0.0f) lv = 0.0f;
+  }
+  xq[nc - 1 + dim] = (int32_t)lv;
 }
 
 static int32_t act8(int32_t a, int s) {
@@ -544,7 +555,9 @@ static float mlp_forward(const mlp_t *m, const int32_t xq[MLP_K]) {
 }
 
 /* P = round((s1/s2) g + p): the fixed-point rescale of the interpolation with
- * the network's correction added in FP32 before rounding. */
+ * the network's correction added in FP32 before rounding. The rounded
+ * fraction is clamped to +-2^50 (a larger correction makes the residual code
+ * leave the int32 range, so the vertex is stored raw either way). */
 static int64_t rescale_p(int64_t a, float acc, int64_t rq, float rf, float p) {
   const uint64_t mask = ((uint64_t)1 << RHO_BITS) - 1;
   unsigned __int128 U = (unsigned __int128)(uint64_t)(a < 0 ? -a : a) * (uint64_t)rq;
@@ -557,18 +570,21 @@ static int64_t rescale_p(int64_t a, float acc, int64_t rq, float rf, float p) {
   float base = (float)lo * 0x1p-40f;
   float t = fmaf(acc, rf, base);
   t = t + p;
+  if (t > 0x1p50f) t = 0x1p50f;
+  if (t < -0x1p50f) t = -0x1p50f;
   return hi + (int64_t)rintf(t);
 }
 
 int orc_mlp_predict(int dim, const uint8_t *model, size_t model_bytes, const int32_t *corners,
-                    const float *fr, float rho12_f, int64_t n, int32_t *features, float *p) {
+                    const float *fr, float rho12_f, int64_t Qhi, int64_t n, int32_t *features,
+                    float *p) {
   mlp_t m;
   int st = model_parse(model, model_bytes, dim, &m);
   if (st) return st;
   for (int64_t i = 0; i < n; i++) {
     int32_t xq[MLP_K];
     const int32_t *cor = corners + 8 * i;
-    mlp_features(dim, m.sx, cor, fr[3 * i], fr[3 * i + 1], fr[3 * i + 2], rho12_f, xq);
+    mlp_features(dim, m.sx, cor, fr[3 * i], fr[3 * i + 1], fr[3 * i + 2], rho12_f, Qhi, xq);
     if (features) memcpy(features + MLP_K * i, xq, sizeof(xq));
     p[i] = mlp_forward(&m, xq);
   }
@@ -914,7 +930,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     int64_t P;
     if (use_model) {
       int32_t xq[MLP_K];
-      mlp_features(dim, model.sx, cor, fx, fy, fz, f.rho12_f, xq);
+      mlp_features(dim, model.sx, cor, fx, fy, fz, f.rho12_f, f.Qhi, xq);
       P = rescale_p(cor[0], acc, f.rho12_q, f.rho12_f, mlp_forward(&model, xq));
     } else {
       P = rescale(cor[0], acc, f.rho12_q, f.rho12_f);
@@ -986,6 +1002,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     put_u64(h + 176, w2);
     put_u64(h + 184, (uint64_t)L.total);
     put_u64(h + 192, (uint64_t)(use_model ? MODEL_BYTES : 0));
+    put_u64(h + 200, (uint64_t)f.Qhi);
     if (use_model) memcpy(out + L.model, p->model, MODEL_BYTES);
     memcpy(out + L.lens1, len1, (size_t)2 * R1);
     memcpy(out + L.lens2, len2, (size_t)2 * R2);
@@ -1158,6 +1175,8 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
   const size_t vsz = dtype == 0 ? 8 : 4;
   const uint32_t flags = get_u32(in + 20);
   const uint64_t mbytes = get_u64(in + 192);
+  const int64_t Qhi = (int64_t)get_u64(in + 200);
+  if (Qhi < 0 || Qhi >= ((int64_t)1 << 29)) return ORC_ERR_CORRUPT;
   const int use_model = (flags & 2) != 0;
   if (flags & ~3u) return ORC_ERR_CORRUPT;
   if (mbytes != (use_model ? MODEL_BYTES : 0)) return ORC_ERR_CORRUPT;
@@ -1216,7 +1235,7 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
       int64_t P;
       if (use_model) {
         int32_t xq[MLP_K];
-        mlp_features(dim, model.sx, cor, fx, fy, fz, rho12_f, xq);
+        mlp_features(dim, model.sx, cor, fx, fy, fz, rho12_f, Qhi, xq);
         P = rescale_p(cor[0], acc, rho12_q, rho12_f, mlp_forward(&model, xq));
       } else {
         P = rescale(cor[0], acc, rho12_q, rho12_f);
@@ -1367,9 +1386,11 @@ int orc_mlp_quantize(int dim, int sx, const float *params, float max_z1, float m
   if ((dim != 2 && dim != 3) || sx < -60 || sx > 60 || !params || !model) return ORC_ERR_INVALID_ARG;
   if (!(max_z1 >= 0.0f) || !(max_z2 >= 0.0f) || isinf(max_z1) || isinf(max_z2))
     return ORC_ERR_INVALID_ARG;
-  const int n_in = (1 << dim) - 1 + dim;
+  const int n_in = (1 << dim) + dim;
   const float *W1 = params, *b1 = W1 + MLP_H * MLP_K, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H,
               *W3 = b2 + MLP_H, *b3 = W3 + MLP_H;
+  for (int k = 0; k < MLP_H * MLP_K + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1; k++)
+    if (!isfinite(params[k])) return ORC_ERR_INVALID_ARG;
   double m1 = 0.0, m2 = 0.0, m3 = 0.0;
   for (int j = 0; j < MLP_H; j++) {
     for (int i = 0; i < n_in; i++) m1 = fmax(m1, fabs((double)W1[j * MLP_K + i]));

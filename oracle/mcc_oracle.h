@@ -103,10 +103,12 @@ void orc_lorenzo_inverse(int dim, const int32_t n[3], const int32_t *delta, int3
 
 /* Learned predictor: for n vertices given their 8 corner codes (corners,
  * [n][8], order 000,100,010,110,001,101,011,111) and local coordinates (fr,
- * [n][3]), the integer features ([n][16], may be NULL) and the correction p
- * in vertex bins. */
+ * [n][3]), with s1/s2 (rho12_f) and the largest vertex code Qhi of the
+ * field, the integer features ([n][16], may be NULL) and the correction p in
+ * vertex bins. */
 int orc_mlp_predict(int dim, const uint8_t *model, size_t model_bytes, const int32_t *corners,
-                    const float *fr, float rho12_f, int64_t n, int32_t *features, float *p);
+                    const float *fr, float rho12_f, int64_t Qhi, int64_t n, int32_t *features,
+                    float *p);
 
 /* Loss (loss_kind 0: mean squared, 1: mean absolute error) and FP64
  * gradient of the float training network on a batch; rounding 1 rounds the

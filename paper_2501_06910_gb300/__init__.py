@@ -28,6 +28,10 @@ __all__ = [
 OK, INVALID_ARG, CUDA, OOM, RANGE, CORRUPT, CAPACITY, TIMEOUT, UNSUPPORTED = range(9)
 F64, F32 = 0, 1
 ABS, REL = 0, 1
+PRED_ZERO, PRED_LEARNED = 0, 1
+LOSS_L2, LOSS_L1 = 0, 1
+MODEL_BYTES = 5736
+MLP_PARAMS = 5313
 
 _lock = threading.Lock()
 _lib = None
@@ -50,13 +54,23 @@ class _GridSpec(C.Structure):
 
 
 class Params(C.Structure):
-    """mcc_params: dtype, eb_mode, eb, grid_fraction, R1, R2, C1, C2, lmax."""
+    """mcc_params: dtype, eb_mode, eb, grid_fraction, R1, R2, C1, C2, lmax,
+    predictor, d_model."""
     _fields_ = [("dtype", C.c_int), ("eb_mode", C.c_int), ("eb", C.c_double),
                 ("grid_fraction", C.c_double), ("R1", C.c_int), ("R2", C.c_int),
-                ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int)]
+                ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int),
+                ("predictor", C.c_int), ("d_model", C.c_void_p)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TrainCfg(C.Structure):
+    """mcc_train_cfg: steps, batch, lr, beta1, beta2, eps, loss,
+    samples_per_field, seed."""
+    _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("loss", C.c_int),
+                ("samples_per_field", C.c_int64), ("seed", C.c_uint64)]
 
 
 class _PlanInfo(C.Structure):
@@ -105,6 +119,19 @@ def load():
             lib.mcc_profile_reset.restype = None
             lib.mcc_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
             lib.mcc_profile_read.restype = C.c_int
+            lib.mcc_train_cfg_default.argtypes = [C.POINTER(TrainCfg)]
+            lib.mcc_train_cfg_default.restype = None
+            lib.mcc_train_workspace_size.argtypes = [P, C.POINTER(Params), C.POINTER(TrainCfg),
+                                                     C.c_int, C.POINTER(S)]
+            lib.mcc_model_train.argtypes = [P, C.c_int, C.POINTER(P), C.POINTER(Params),
+                                            C.POINTER(TrainCfg), P, S, P, P, P]
+            lib.mcc_mlp_grad_workspace_size.argtypes = [C.c_int64]
+            lib.mcc_mlp_grad_workspace_size.restype = S
+            lib.mcc_mlp_grad.argtypes = [P, P, P, C.c_int64, C.c_int, P, S, P, P, P]
+            lib.mcc_mlp_quantize.argtypes = [C.c_int, C.c_int, P, C.c_float, C.c_float, P, P, P]
+            for fn in ("mcc_train_workspace_size", "mcc_model_train", "mcc_mlp_grad",
+                       "mcc_mlp_quantize"):
+                getattr(lib, fn).restype = C.c_int
             for fn in ("mcc_plan_create", "mcc_plan_get_info", "mcc_plan_copy_tables",
                        "mcc_workspace_size", "mcc_compress_bound", "mcc_compress",
                        "mcc_decompress", "mcc_workspace_result"):
@@ -135,9 +162,17 @@ def _dptr(t: torch.Tensor):
     return C.c_void_p(t.data_ptr())
 
 
-def params_default(**overrides) -> Params:
+def params_default(model=None, **overrides) -> Params:
+    """Parameters; ``model`` (a CUDA uint8 tensor of MODEL_BYTES) selects the
+    learned predictor. The structure keeps a reference to the tensor."""
     p = Params()
     load().mcc_params_default(C.byref(p))
+    if model is not None:
+        if model.dtype != torch.uint8 or model.numel() != MODEL_BYTES:
+            raise ValueError("model must be a uint8 tensor of MODEL_BYTES bytes")
+        p._model = model
+        p.predictor = PRED_LEARNED
+        p.d_model = _dptr(model).value
     for k, v in overrides.items():
         if k == "dtype" and not isinstance(v, int):
             v = F64 if v in (torch.float64, "float64", "f64") else F32
@@ -312,3 +347,66 @@ def decompress_static(plan: Plan, stream_bytes: torch.Tensor, nbytes: int, out: 
 
 def static_scratch_bytes() -> int:
     return int(load().mcc_static_scratch_bytes())
+
+
+# --------------------------------------------------------------------------- #
+# learned predictor: training
+# --------------------------------------------------------------------------- #
+def train_cfg_default(**overrides) -> TrainCfg:
+    c = TrainCfg()
+    load().mcc_train_cfg_default(C.byref(c))
+    for k, v in overrides.items():
+        if k == "loss" and isinstance(v, str):
+            v = LOSS_L1 if v == "l1" else LOSS_L2
+        setattr(c, k, v)
+    return c
+
+
+def train_workspace_size(plan: "Plan", params: Params, cfg: TrainCfg, n: int) -> int:
+    size = C.c_size_t(0)
+    _check(load().mcc_train_workspace_size(plan.handle, C.byref(params), C.byref(cfg), int(n),
+                                           C.byref(size)), "train_workspace_size")
+    return int(size.value)
+
+
+def model_train(plan: "Plan", fields, params: Params, cfg: TrainCfg, workspace=None, stream=None):
+    """mcc_model_train: returns (model blob as a CUDA uint8 tensor, per-step
+    minibatch losses as a list). Synchronises."""
+    n = len(fields)
+    if workspace is None:
+        workspace = torch.empty(train_workspace_size(plan, params, cfg, n), dtype=torch.uint8,
+                                device="cuda")
+    model = torch.zeros(MODEL_BYTES, dtype=torch.uint8, device="cuda")
+    ptrs = (C.c_void_p * n)(*[_dptr(x).value for x in fields])
+    losses = (C.c_float * cfg.steps)()
+    st = load().mcc_model_train(plan.handle, n, ptrs, C.byref(params), C.byref(cfg),
+                                _dptr(workspace), workspace.numel(), _dptr(model), losses,
+                                _stream(stream))
+    _check(st, "model_train")
+    return model, [float(v) for v in losses]
+
+
+def mlp_grad(params: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, loss="l1", stream=None):
+    """mcc_mlp_grad: (gradient as a CUDA float tensor, loss) of the training
+    network on the batch (X [B, 16], Y [B], float32 CUDA tensors)."""
+    B = int(X.shape[0])
+    ws = torch.empty(max(4, int(load().mcc_mlp_grad_workspace_size(B))), dtype=torch.uint8,
+                     device="cuda")
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    lossv = torch.empty(1, dtype=torch.float32, device="cuda")
+    st = load().mcc_mlp_grad(_dptr(params), _dptr(X), _dptr(Y), B,
+                             LOSS_L1 if loss == "l1" else LOSS_L2, _dptr(ws), ws.numel(),
+                             _dptr(grad), _dptr(lossv), _stream(stream))
+    _check(st, "mlp_grad")
+    return grad, lossv
+
+
+def mlp_quantize(dim: int, sx: int, params: torch.Tensor, max_z1: float, max_z2: float,
+                 stream=None):
+    """mcc_mlp_quantize: (model blob as a CUDA uint8 tensor, device status)."""
+    model = torch.zeros(MODEL_BYTES, dtype=torch.uint8, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    st = load().mcc_mlp_quantize(int(dim), int(sx), _dptr(params), float(max_z1), float(max_z2),
+                                 _dptr(model), _dptr(status), _stream(stream))
+    _check(st, "mlp_quantize")
+    return model, status

@@ -21,6 +21,8 @@ extern "C" void mcc_params_default(mcc_params *p) {
   p->C1 = 128;
   p->C2 = 128;
   p->lmax = 24;
+  p->predictor = MCC_PRED_ZERO;
+  p->d_model = nullptr;
 }
 
 extern "C" const char *mcc_status_string(mcc_status s) {
@@ -60,7 +62,8 @@ extern "C" mcc_status mcc_compress_bound(mcc_plan plan, const mcc_params *p, siz
   const uint64_t vsz = p->dtype == MCC_F64 ? 8 : 4;
   const uint64_t w1 = (uint64_t)((pv.n_g * p->lmax + 31) / 32 + ng1);
   const uint64_t w2 = (uint64_t)((pv.n_v * p->lmax + 31) / 32 + ng2);
-  const Layout L = make_layout(p->R1, p->R2, ng1, ng2, (uint64_t)pv.n_g, 0, (uint64_t)pv.n_v, vsz, w1, w2);
+  const Layout L = make_layout(p->R1, p->R2, ng1, ng2, (uint64_t)pv.n_g, 0, (uint64_t)pv.n_v, vsz,
+                               w1, w2, kModelBytes);  // room for a learned-predictor blob
   *max_bytes = L.total + 16;
   return MCC_OK;
 }

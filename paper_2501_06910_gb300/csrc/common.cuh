@@ -31,6 +31,7 @@ constexpr int kMaxC = 256;
 constexpr int kMaxLen = 24;
 constexpr int kMaxBatch = 64;               // fields per kernel launch
 constexpr int kLutBits = 12;               // first-level decode table (two symbols per entry)
+constexpr uint32_t kModelBytes = 5736;     // learned-predictor blob
 
 // header byte offsets
 enum : uint32_t {
@@ -38,8 +39,10 @@ enum : uint32_t {
   H_R2 = 28, H_C1 = 32, H_C2 = 36, H_LMAX = 40, H_NX = 44, H_NY = 48, H_NZ = 52, H_NV = 56,
   H_NG = 64, H_TAU = 72, H_TAU1 = 80, H_TAU2 = 88, H_S1 = 96, H_S2 = 104, H_K = 112,
   H_RHO21 = 120, H_RHO12 = 128, H_FILL = 136, H_NOUT1 = 144, H_NOUT2 = 152, H_NRAW = 160,
-  H_W1 = 168, H_W2 = 176, H_TOTAL = 184
+  H_W1 = 168, H_W2 = 176, H_TOTAL = 184, H_MODEL = 192, H_QHI = 200
 };
+// header flags
+enum : uint32_t { F_GUARD = 1, F_MODEL = 2 };
 
 __host__ __device__ inline uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 __host__ __device__ inline int64_t ngroups(int64_t n, int C) {
@@ -48,15 +51,17 @@ __host__ __device__ inline int64_t ngroups(int64_t n, int C) {
 
 // Section offsets of a stream. Order: header | code lengths 1, 2 | group word
 // offsets 1, 2 | group escape prefixes 1, 2 | group raw prefix 2 | lane bit
-// lengths 1, 2 | escape values 1, 2 (int32) | raw values | bitstreams 1, 2.
+// lengths 1, 2 | escape values 1, 2 (int32) | raw values | bitstreams 1, 2 |
+// learned-predictor blob (8-byte aligned, absent in plain streams).
 struct Layout {
   uint64_t lens1, lens2, gtab1, gtab2, etab1, etab2, rtab2, ltab1, ltab2, out1, out2, raw, bits1,
-      bits2, total;
+      bits2, model, total;
 };
 
 __host__ __device__ inline Layout make_layout(int R1, int R2, int64_t ng1, int64_t ng2,
                                               uint64_t nout1, uint64_t nout2, uint64_t nraw,
-                                              uint64_t vsz, uint64_t w1, uint64_t w2) {
+                                              uint64_t vsz, uint64_t w1, uint64_t w2,
+                                              uint64_t model_bytes = 0) {
   Layout L;
   uint64_t o = kHeaderBytes;
   L.lens1 = o; o += 2 * (uint64_t)R1;
@@ -76,6 +81,8 @@ __host__ __device__ inline Layout make_layout(int R1, int R2, int64_t ng1, int64
   o = align_up(o, 4);
   L.bits1 = o; o += 4 * w1;
   L.bits2 = o; o += 4 * w2;
+  o = align_up(o, 8);
+  L.model = o; o += model_bytes;
   L.total = o;
   return L;
 }
@@ -147,8 +154,10 @@ __host__ __device__ inline double key_value(unsigned long long k) {
 // ---------------------------------------------------------------------------
 // round(rho * (a + acc)), rho = rq 2^-40: integer part of a*rho from the exact
 // 128-bit product, 40-bit fraction plus FP32 correction acc*rho, one fused
-// multiply-add, round to nearest even.
-__device__ __forceinline__ long long rescale(long long a, float acc, long long rq, float rf) {
+// multiply-add, round to nearest even. rescale_split returns the integer part
+// and the FP32 fraction before rounding.
+__device__ __forceinline__ void rescale_split(long long a, float acc, long long rq, float rf,
+                                              long long &hi, float &t) {
   const unsigned long long ua = (unsigned long long)(a < 0 ? -a : a);
   const unsigned long long ur = (unsigned long long)rq;
   const unsigned long long lo64 = ua * ur;
@@ -156,13 +165,25 @@ __device__ __forceinline__ long long rescale(long long a, float acc, long long r
   const unsigned long long mask = (1ull << kRhoBits) - 1;
   unsigned long long q = (hi64 << (64 - kRhoBits)) | (lo64 >> kRhoBits);
   unsigned long long r = lo64 & mask;
-  long long hi;
   unsigned long long lo;
   if (a >= 0) { hi = (long long)q; lo = r; }
   else if (r == 0) { hi = -(long long)q; lo = 0; }
   else { hi = -(long long)q - 1; lo = (1ull << kRhoBits) - r; }
   const float base = __fmul_rn(__ull2float_rn(lo), 0x1p-40f);
-  const float t = __fmaf_rn(acc, rf, base);
+  t = __fmaf_rn(acc, rf, base);
+}
+
+template <bool HAS_P = false>
+__device__ __forceinline__ long long rescale(long long a, float acc, long long rq, float rf,
+                                             float pc = 0.0f) {
+  long long hi;
+  float t;
+  rescale_split(a, acc, rq, rf, hi, t);
+  if (HAS_P) {  // the learned correction, in vertex bins; beyond +-2^50 the
+                // residual code leaves int32 and the vertex is stored raw
+    t = __fadd_rn(t, pc);
+    t = fminf(fmaxf(t, -0x1p50f), 0x1p50f);
+  }
   return hi + (long long)rintf(t);
 }
 
@@ -170,16 +191,14 @@ __device__ __forceinline__ int wsub(int a, int b) { return (int)((unsigned)a - (
 __device__ __forceinline__ int wadd(int a, int b) { return (int)((unsigned)a + (unsigned)b); }
 
 // Grid -> vertex interpolation g (bilinear / trilinear on the grid codes of
-// the vertex's cell), returned in node units P = round(rho12 * g).
+// the vertex's cell) as acc = g - c_000 in grid bins; returns c_000.
 template <int DIM>
-__device__ __forceinline__ long long predict_vertex(const int *__restrict__ q1, uint32_t c,
-                                                    float fx, float fy, float fz, int nx,
-                                                    int64_t sxy, long long rq, float rf) {
+__device__ __forceinline__ int interp_vertex(const int *__restrict__ q1, uint32_t c, float fx,
+                                             float fy, float fz, int nx, int64_t sxy, float &acc) {
   const int c000 = __ldg(q1 + c), c100 = __ldg(q1 + c + 1);
   const int c010 = __ldg(q1 + c + nx), c110 = __ldg(q1 + c + nx + 1);
   const int d100 = wsub(c100, c000), d010 = wsub(c010, c000);
   const int d110 = wadd(wsub(wsub(c110, c100), c010), c000);
-  float acc;
   if (DIM == 2) {
     acc = __fmul_rn(fx, __int2float_rn(d100));
     acc = __fmaf_rn(fy, __int2float_rn(d010), acc);
@@ -208,7 +227,19 @@ __device__ __forceinline__ long long predict_vertex(const int *__restrict__ q1, 
     acc = __fmaf_rn(fyz, __int2float_rn(d011), acc);
     acc = __fmaf_rn(fxyz, __int2float_rn(d111), acc);
   }
-  return rescale(c000, acc, rq, rf);
+  return c000;
+}
+
+// The vertex prediction in node units, P = round(rho12 * g + pc), pc the
+// learned correction when HAS_P.
+template <int DIM, bool HAS_P = false>
+__device__ __forceinline__ long long predict_vertex(const int *__restrict__ q1, uint32_t c,
+                                                    float fx, float fy, float fz, int nx,
+                                                    int64_t sxy, long long rq, float rf,
+                                                    float pc = 0.0f) {
+  float acc;
+  const int c000 = interp_vertex<DIM>(q1, c, fx, fy, fz, nx, sxy, acc);
+  return rescale<HAS_P>(c000, acc, rq, rf, pc);
 }
 
 // ---------------------------------------------------------------------------

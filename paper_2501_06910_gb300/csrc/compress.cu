@@ -7,6 +7,8 @@
 //   k_grid       x1 = f(x): barycentric interpolation of Q at every grid
 //                point (Sec. IV-D), grid codes q1, N-D Lorenzo difference,
 //                symbols + histogram (C(x1))
+//   k_predict    (learned predictor only) the network's correction p at
+//                every vertex, from the corner codes of its cell
 //   k_node       g(x1'): multilinear interpolation of q1 at every vertex,
 //                residual code q2 = Q - P, bound guard, symbols + histogram
 //                (C(x2), residuals serialised 1-D, Sec. IV-B)
@@ -21,6 +23,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "predictor.cuh"
 #include "workspace.cuh"
 #include "prof.cuh"
 
@@ -49,6 +52,7 @@ struct CompArgs {
   int64_t ng1, ng2;
   const void *x[kMaxBatch];
   RParams rp[kMaxBatch];
+  const unsigned char *model[kMaxBatch];  // learned-predictor blob or NULL
 };
 
 // Per-field pointers into the workspace and the output slot.
@@ -58,6 +62,7 @@ struct Ctx {
   unsigned char *len1, *len2, *out;
   int *Q, *q1, *val1, *val2;
   unsigned short *sym1, *sym2, *pb;
+  float *p;
   const void *x;
 };
 
@@ -83,6 +88,7 @@ __device__ __forceinline__ Ctx ctx_of(const CompArgs &A, int f) {
   c.pb = (unsigned short *)(ws + A.W.pb);
   c.pe = (unsigned int *)(ws + A.W.pe);
   c.pr = (unsigned int *)(ws + A.W.pr);
+  c.p = (float *)(ws + A.W.p);
   c.out = A.out0 + (int64_t)f * A.oss;
   c.x = A.x[f];
   return c;
@@ -420,7 +426,7 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
 // ---------------------------------------------------------------------------
 // k_node: residual codes at the vertices
 // ---------------------------------------------------------------------------
-template <int DIM, typename T>
+template <int DIM, typename T, bool HAS_P>
 __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
@@ -444,6 +450,8 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
   const int nx = pv.nx;
   const int64_t sxy = (int64_t)pv.nx * pv.ny;
   const int rawsym = 2 * R2 - 1;
+  const float *__restrict__ pcor = c.p;
+  const bool use_p = HAS_P && A.model[blockIdx.x] != nullptr;
   unsigned int nesc = 0, nraw = 0;
   const int64_t stride = (int64_t)gridDim.y * blockDim.x;
   const int64_t nloop = (n + stride - 1) / stride * stride;  // uniform trip count per warp
@@ -456,7 +464,8 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
       const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + i)), 0x1p-15f);
       const float fz = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + i)), 0x1p-15f) : 0.0f;
       const int Qi = __ldg(Q + i);
-      const long long P = predict_vertex<DIM>(q1, c, fx, fy, fz, nx, sxy, f.rho12_q, f.rho12_f);
+      const float pc = use_p ? __ldg(pcor + i) : 0.0f;
+      const long long P = predict_vertex<DIM, HAS_P>(q1, c, fx, fy, fz, nx, sxy, f.rho12_q, f.rho12_f, pc);
       const long long q2 = (long long)Qi - P;
       bool raw = q2 <= -2147483648ll || q2 > 2147483647ll;  // INT32_MIN is reserved
       if (f.guard) {
@@ -862,52 +871,70 @@ __global__ void __launch_bounds__(160) k_scan(const __grid_constant__ CompArgs A
   const unsigned long long t = warp_exclusive_scan(src[w], cnt[w], (unsigned int *)(o + dst[w]));
   if ((threadIdx.x & 31) == 0) tot[w] = t;
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  const unsigned long long w1 = tot[0], w2 = tot[1], e1 = tot[2], e2 = tot[3], r2 = tot[4];
-  const uint64_t vsz = a.dtype == MCC_F64 ? 8 : 4;
-  const Layout L = make_layout(a.R1, a.R2, a.ng1, a.ng2, e1, e2, r2, vsz, w1, w2);
-  st->L = L;
-  st->w1 = w1;
-  st->w2 = w2;
-  st->out_size = L.total;
-  if (L.total > a.capacity) { set_error(st, MCC_ERR_CAPACITY); return; }
-  const FieldParams &f = st->f;
-  for (int i = 0; i < (int)kHeaderBytes; i += 8) put64(o + i, 0);
-  put32(o + H_MAGIC, kMagic);
-  put32(o + H_VERSION, kVersion);
-  put32(o + H_HBYTES, kHeaderBytes);
-  put32(o + H_DTYPE, (uint32_t)a.dtype);
-  put32(o + H_DIM, (uint32_t)a.dim);
-  put32(o + H_FLAGS, f.guard ? 1u : 0u);
-  put32(o + H_R1, (uint32_t)a.R1);
-  put32(o + H_R2, (uint32_t)a.R2);
-  put32(o + H_C1, (uint32_t)a.C1);
-  put32(o + H_C2, (uint32_t)a.C2);
-  put32(o + H_LMAX, (uint32_t)a.lmax);
-  put32(o + H_NX, (uint32_t)a.nx);
-  put32(o + H_NY, (uint32_t)a.ny);
-  put32(o + H_NZ, (uint32_t)a.nz);
-  put64(o + H_NV, (uint64_t)a.n_v);
-  put64(o + H_NG, (uint64_t)a.n_g);
-  put64(o + H_TAU, (uint64_t)__double_as_longlong(f.tau));
-  put64(o + H_TAU1, (uint64_t)__double_as_longlong(f.tau1));
-  put64(o + H_TAU2, (uint64_t)__double_as_longlong(f.tau2));
-  put64(o + H_S1, (uint64_t)__double_as_longlong(f.s1));
-  put64(o + H_S2, (uint64_t)__double_as_longlong(f.s2));
-  put64(o + H_K, (uint64_t)f.K);
-  put64(o + H_RHO21, (uint64_t)f.rho21_q);
-  put64(o + H_RHO12, (uint64_t)f.rho12_q);
-  put64(o + H_FILL, (uint64_t)f.fill_u);
-  put64(o + H_NOUT1, e1);
-  put64(o + H_NOUT2, e2);
-  put64(o + H_NRAW, r2);
-  put64(o + H_W1, w1);
-  put64(o + H_W2, w2);
-  put64(o + H_TOTAL, L.total);
-  // zero the alignment padding between sections
-  for (uint64_t p = F.lens2 + 2 * (uint64_t)a.R2; p < F.gtab1; p++) o[p] = 0;
-  for (uint64_t p = L.out2 + 4 * e2; p < L.raw; p++) o[p] = 0;
-  for (uint64_t p = L.raw + vsz * r2; p < L.bits1; p++) o[p] = 0;
+  const unsigned char *model = A.model[blockIdx.x];
+  __shared__ unsigned long long model_at;  // stream offset of the model section, 0 = none
+  if (threadIdx.x == 0) {
+    model_at = 0;
+    const unsigned long long w1 = tot[0], w2 = tot[1], e1 = tot[2], e2 = tot[3], r2 = tot[4];
+    const uint64_t vsz = a.dtype == MCC_F64 ? 8 : 4;
+    const Layout L = make_layout(a.R1, a.R2, a.ng1, a.ng2, e1, e2, r2, vsz, w1, w2,
+                                 model ? kModelBytes : 0);
+    st->L = L;
+    st->w1 = w1;
+    st->w2 = w2;
+    st->out_size = L.total;
+    if (L.total > a.capacity) {
+      set_error(st, MCC_ERR_CAPACITY);
+    } else {
+      const FieldParams &f = st->f;
+      for (int i = 0; i < (int)kHeaderBytes; i += 8) put64(o + i, 0);
+      put32(o + H_MAGIC, kMagic);
+      put32(o + H_VERSION, kVersion);
+      put32(o + H_HBYTES, kHeaderBytes);
+      put32(o + H_DTYPE, (uint32_t)a.dtype);
+      put32(o + H_DIM, (uint32_t)a.dim);
+      put32(o + H_FLAGS, (f.guard ? F_GUARD : 0u) | (model ? F_MODEL : 0u));
+      put32(o + H_R1, (uint32_t)a.R1);
+      put32(o + H_R2, (uint32_t)a.R2);
+      put32(o + H_C1, (uint32_t)a.C1);
+      put32(o + H_C2, (uint32_t)a.C2);
+      put32(o + H_LMAX, (uint32_t)a.lmax);
+      put32(o + H_NX, (uint32_t)a.nx);
+      put32(o + H_NY, (uint32_t)a.ny);
+      put32(o + H_NZ, (uint32_t)a.nz);
+      put64(o + H_NV, (uint64_t)a.n_v);
+      put64(o + H_NG, (uint64_t)a.n_g);
+      put64(o + H_TAU, (uint64_t)__double_as_longlong(f.tau));
+      put64(o + H_TAU1, (uint64_t)__double_as_longlong(f.tau1));
+      put64(o + H_TAU2, (uint64_t)__double_as_longlong(f.tau2));
+      put64(o + H_S1, (uint64_t)__double_as_longlong(f.s1));
+      put64(o + H_S2, (uint64_t)__double_as_longlong(f.s2));
+      put64(o + H_K, (uint64_t)f.K);
+      put64(o + H_RHO21, (uint64_t)f.rho21_q);
+      put64(o + H_RHO12, (uint64_t)f.rho12_q);
+      put64(o + H_FILL, (uint64_t)f.fill_u);
+      put64(o + H_NOUT1, e1);
+      put64(o + H_NOUT2, e2);
+      put64(o + H_NRAW, r2);
+      put64(o + H_W1, w1);
+      put64(o + H_W2, w2);
+      put64(o + H_TOTAL, L.total);
+      put64(o + H_MODEL, model ? kModelBytes : 0);
+      put64(o + H_QHI, (uint64_t)f.Qhi);
+      // zero the alignment padding between sections
+      for (uint64_t p = F.lens2 + 2 * (uint64_t)a.R2; p < F.gtab1; p++) o[p] = 0;
+      for (uint64_t p = L.out2 + 4 * e2; p < L.raw; p++) o[p] = 0;
+      for (uint64_t p = L.raw + vsz * r2; p < L.bits1; p++) o[p] = 0;
+      for (uint64_t p = L.bits2 + 4 * w2; p < L.model; p++) o[p] = 0;
+      if (model) model_at = L.model;
+    }
+  }
+  __syncthreads();
+  if (model_at) {  // the blob travels with the stream
+    const unsigned int *src = (const unsigned int *)model;
+    unsigned int *dst = (unsigned int *)(o + model_at);
+    for (int i = threadIdx.x; i < (int)kModelBytes / 4; i += blockDim.x) dst[i] = src[i];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1044,6 +1071,9 @@ mcc_status check_params(const mcc_params *p) {
   if (p->R1 < 4 || p->R1 > kMaxR || p->R2 < 4 || p->R2 > kMaxR) return MCC_ERR_UNSUPPORTED;
   if (p->C1 < 1 || p->C1 > kMaxC || p->C2 < 1 || p->C2 > kMaxC) return MCC_ERR_UNSUPPORTED;
   if (p->lmax < 1 || p->lmax > kMaxLen) return MCC_ERR_UNSUPPORTED;
+  if (p->predictor != MCC_PRED_ZERO && p->predictor != MCC_PRED_LEARNED) return MCC_ERR_INVALID_ARG;
+  if (p->predictor == MCC_PRED_LEARNED && (!p->d_model || ((uintptr_t)p->d_model & 3)))
+    return MCC_ERR_INVALID_ARG;
   return MCC_OK;
 }
 
@@ -1070,6 +1100,7 @@ CompressWs compress_ws_layout(const PlanView &pv, const mcc_params *p) {
   w.pb = take(2 * kParts * 32 * (size_t)(ng1 + ng2));
   w.pe = take(4 * kParts * (size_t)(ng1 + ng2));
   w.pr = take(4 * kParts * (size_t)(ng1 + ng2));
+  w.p = take(4 * (size_t)pv.n_v);
   w.total = o;
   return w;
 }
@@ -1081,7 +1112,7 @@ CompressWs compress_ws_layout(const PlanView &pv, const mcc_params *p) {
 mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *xs,
                                  const mcc_params *ps, unsigned char *ws0, int64_t wss,
                                  unsigned char *out0, int64_t oss, size_t capacity,
-                                 cudaStream_t stream) {
+                                 cudaStream_t stream, bool front_only) {
   if (nf < 1 || nf > kMaxBatch) return MCC_ERR_INVALID_ARG;
   const mcc_params *p = ps;
   CompArgs A;  // launch arguments (passed by value as a grid constant)
@@ -1105,10 +1136,13 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   A.ng1 = ngroups(pv.n_g, p->C1);
   A.ng2 = ngroups(pv.n_v, p->C2);
   A.F = make_layout(p->R1, p->R2, A.ng1, A.ng2, 0, 0, 0, 8, 0, 0);
-  if (capacity < A.F.out1) return MCC_ERR_CAPACITY;
+  if (!front_only && capacity < A.F.out1) return MCC_ERR_CAPACITY;
+  bool any_model = false;
   for (int f = 0; f < nf; f++) {
     A.x[f] = xs[f];
     A.rp[f] = RParams{ps[f].dtype, ps[f].eb_mode, ps[f].eb, ps[f].grid_fraction};
+    A.model[f] = ps[f].predictor == MCC_PRED_LEARNED ? (const unsigned char *)ps[f].d_model : nullptr;
+    any_model = any_model || A.model[f];
   }
   const int64_t ng = A.ng1 + A.ng2;
   const int sms = num_sms();
@@ -1142,15 +1176,45 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     const unsigned int txy = (unsigned int)(((pv.nx + 31) / 32) * ((pv.ny + 7) / 8));
     launch_pdl(k_grid3d<32, 8, 8>, dim3(nf, txy, (pv.nz + 7) / 8), dim3(256), hsm1, stream, A);
   }
+  if (front_only) return cudaGetLastError() == cudaSuccess ? MCC_OK : MCC_ERR_CUDA;
+  if (any_model) {  // learned corrections p at every vertex of the fields with a model
+    PROF_SCOPE("k_predict", stream);
+    PredArgs P;
+    memset(&P, 0, sizeof(P));
+    P.pv = pv;
+    P.nf = nf;
+    P.bad_model_err = MCC_ERR_INVALID_ARG;
+    for (int f = 0; f < nf; f++) {
+      unsigned char *ws = ws0 + (int64_t)f * wss;
+      P.q1[f] = (const int *)(ws + A.W.q1);
+      P.p[f] = (float *)(ws + A.W.p);
+      P.model[f] = A.model[f];
+      P.rho12_f[f] = &((const Status *)ws)->f.rho12_f;
+      P.qhi[f] = &((const Status *)ws)->f.Qhi;
+      P.st[f] = (Status *)ws;
+    }
+    launch_predict(P, stream, true);
+  }
   {
     PROF_SCOPE("k_node", stream);
     const unsigned int chunks = ppf < 65535 ? ppf : 65535;
+    const dim3 grid(nf, chunks);
     if (pv.dim == 2) {
-      if (p->dtype == MCC_F64) launch_pdl(k_node<2, double>, dim3(nf, chunks), dim3(256), hsm2, stream, A);
-      else launch_pdl(k_node<2, float>, dim3(nf, chunks), dim3(256), hsm2, stream, A);
+      if (p->dtype == MCC_F64) {
+        if (any_model) launch_pdl(k_node<2, double, true>, grid, dim3(256), hsm2, stream, A);
+        else launch_pdl(k_node<2, double, false>, grid, dim3(256), hsm2, stream, A);
+      } else {
+        if (any_model) launch_pdl(k_node<2, float, true>, grid, dim3(256), hsm2, stream, A);
+        else launch_pdl(k_node<2, float, false>, grid, dim3(256), hsm2, stream, A);
+      }
     } else {
-      if (p->dtype == MCC_F64) launch_pdl(k_node<3, double>, dim3(nf, chunks), dim3(256), hsm2, stream, A);
-      else launch_pdl(k_node<3, float>, dim3(nf, chunks), dim3(256), hsm2, stream, A);
+      if (p->dtype == MCC_F64) {
+        if (any_model) launch_pdl(k_node<3, double, true>, grid, dim3(256), hsm2, stream, A);
+        else launch_pdl(k_node<3, double, false>, grid, dim3(256), hsm2, stream, A);
+      } else {
+        if (any_model) launch_pdl(k_node<3, float, true>, grid, dim3(256), hsm2, stream, A);
+        else launch_pdl(k_node<3, float, false>, grid, dim3(256), hsm2, stream, A);
+      }
     }
   }
   {

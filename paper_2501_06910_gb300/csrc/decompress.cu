@@ -8,8 +8,10 @@
 //                 escapes and raw values
 //   k_scan_rows / k_scan_axis
 //                 inverse Lorenzo: inclusive prefix sums along x, y (, z)
-//   k_recon       reconstruction x' = s2 (K + P + q2), P = round(rho12 g(q1)),
-//                 fully parallel over the vertices
+//   k_predict     learned correction p at every vertex (streams with a
+//                 model; returns at once for the others)
+//   k_recon       reconstruction x' = s2 (K + P + q2), P = round(rho12 g(q1)
+//                 + p), fully parallel over the vertices
 //
 // Every read of the stream is bounds-checked against the validated layout; a
 // corrupt stream records MCC_ERR_CORRUPT and the affected warp stops.
@@ -19,6 +21,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "predictor.cuh"
 #include "workspace.cuh"
 #include "prof.cuh"
 
@@ -51,6 +54,7 @@ struct DCtx {
   DecInfo *info;
   DecTab *tab1, *tab2;
   int *q1, *q2;
+  float *p;
   const unsigned char *in;
   uint64_t in_bytes;
   void *xo;
@@ -65,6 +69,7 @@ __device__ __forceinline__ DCtx dctx_of(const DecArgs &A, int f) {
   c.tab2 = (DecTab *)(ws + A.W.tab2);
   c.q1 = (int *)(ws + A.W.q1);
   c.q2 = (int *)(ws + A.W.q2);
+  c.p = (float *)(ws + A.W.p);
   c.in = A.in0 + (int64_t)f * A.iss;
   c.in_bytes = A.in_bytes[f];
   c.xo = A.xo[f];
@@ -97,6 +102,12 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
     return false;
   I.dtype = (int)ld32(h + H_DTYPE);
   I.dim = (int)ld32(h + H_DIM);
+  const uint32_t flags = ld32(h + H_FLAGS);
+  if (flags & ~(F_GUARD | F_MODEL)) return false;
+  I.use_model = (flags & F_MODEL) ? 1 : 0;
+  if (ld64(h + H_MODEL) != (I.use_model ? kModelBytes : 0)) return false;
+  I.Qhi = (long long)ld64(h + H_QHI);
+  if (I.Qhi < 0 || I.Qhi >= (1ll << 29)) return false;
   if (I.dtype != a.dtype) return false;
   if (I.dim != a.dim || (int)ld32(h + H_NX) != a.nx || (int)ld32(h + H_NY) != a.ny ||
       (int)ld32(h + H_NZ) != a.nz)
@@ -129,7 +140,8 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
       I.w2 > (uint64_t)a.n_v * kMaxLen / 32 + I.ng2 + 1)
     return false;
   const uint64_t vsz = I.dtype == MCC_F64 ? 8 : 4;
-  I.L = make_layout(I.R1, I.R2, I.ng1, I.ng2, I.nout1, I.nout2, I.nraw, vsz, I.w1, I.w2);
+  I.L = make_layout(I.R1, I.R2, I.ng1, I.ng2, I.nout1, I.nout2, I.nraw, vsz, I.w1, I.w2,
+                    I.use_model ? kModelBytes : 0);
   if (I.L.total != ld64(h + H_TOTAL) || I.L.total > a.in_bytes) return false;
   const unsigned char *in = a.in;
   if (ld32(in + I.L.gtab1) != 0 || ld32(in + I.L.gtab1 + 4 * I.ng1) != I.w1) return false;
@@ -521,7 +533,7 @@ __global__ void __launch_bounds__(256) k_scan_axis(const __grid_constant__ DecAr
 // k_recon: x' = s2 (K + P + q2) at every vertex, P = round(rho12 g(x1'))
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
-__global__ void __launch_bounds__(256) k_recon(const __grid_constant__ DecArgs A) {
+__global__ void __launch_bounds__(256, 6) k_recon(const __grid_constant__ DecArgs A) {
   pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.x);
@@ -529,6 +541,7 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ DecArgs A
   const PlanView &pv = A.pv;
   const int *__restrict__ q1 = c.q1;
   const int *__restrict__ q2s = c.q2;
+  const float *__restrict__ pcor = c.p;
   T *__restrict__ xo = (T *)c.xo;
   const Status *st = c.st;
   if (*(volatile const unsigned int *)&st->err) return;
@@ -548,7 +561,10 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ DecArgs A
       const float fx = __fmul_rn(__uint2float_rn(__ldg(pv.frac + p)), 0x1p-15f);
       const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + p)), 0x1p-15f);
       const float fz = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + p)), 0x1p-15f) : 0.0f;
-      const long long P = predict_vertex<DIM>(q1, c, fx, fy, fz, nx, sxy, I.rho12_q, I.rho12_f);
+      // one code path for both stream kinds: adding p = 0 leaves the plain
+      // prediction unchanged (t + 0 = t, and -0 + 0 = +0 rounds to the same 0)
+      const float pc = I.use_model ? __ldg(pcor + p) : 0.0f;
+      const long long P = predict_vertex<DIM, true>(q1, c, fx, fy, fz, nx, sxy, I.rho12_q, I.rho12_f, pc);
       xo[p] = (T)__dmul_rn(I.s2, (double)(I.K + P + (long long)q2));
     }
   }
@@ -570,6 +586,7 @@ DecompressWs decompress_ws_layout(const PlanView &pv) {
   w.tab2 = take(sizeof(DecTab));
   w.q1 = take(4 * (size_t)pv.n_g);
   w.q2 = take(4 * (size_t)pv.n_v);
+  w.p = take(4 * (size_t)pv.n_v);
   w.total = o;
   return w;
 }
@@ -640,6 +657,28 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
     const int64_t ninner = (int64_t)pv.nx * pv.ny;
     launch_pdl(k_scan_axis, dim3((unsigned int)((ninner + 31) / 32), nf), dim3(256), 0, stream, A,
                ninner, (int64_t)1, (int64_t)0, pv.nz, ninner);
+  }
+  {  // learned corrections (the kernel returns at once for plain streams)
+    PROF_SCOPE("k_predict", stream);
+    PredArgs P;
+    memset(&P, 0, sizeof(P));
+    P.pv = pv;
+    P.nf = nf;
+    P.bad_model_err = MCC_ERR_CORRUPT;
+    const DecompressWs W = A.W;
+    for (int f = 0; f < nf; f++) {
+      unsigned char *ws = ws0 + (int64_t)f * wss;
+      const DecInfo *info = (const DecInfo *)(ws + W.info);
+      P.q1[f] = (const int *)(ws + W.q1);
+      P.p[f] = (float *)(ws + W.p);
+      P.model[f] = in0 + (int64_t)f * iss;
+      P.model_off[f] = &info->L.model;
+      P.use[f] = &info->use_model;
+      P.rho12_f[f] = &info->rho12_f;
+      P.qhi[f] = &info->Qhi;
+      P.st[f] = (Status *)ws;
+    }
+    launch_predict(P, stream, true);
   }
   {
     PROF_SCOPE("k_recon", stream);

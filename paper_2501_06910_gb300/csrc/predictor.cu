@@ -1,0 +1,280 @@
+// predictor.cu -- inference of the learned residual predictor on the tensor
+// cores (bf16 mma.sync m16n8k16, FP32 accumulation).
+//
+// Each warp takes 32 consecutive vertices: lanes compute the integer features
+// of their vertex (corner-code differences in vertex bins, local coordinates
+// and the level of corner 000), then the warp runs two 16-row tiles through the network:
+// layer 1 (16 -> 64) is 8 MMAs, layer 2 (64 -> 64) 32 MMAs, layer 3 (64 -> 1,
+// padded to 8 columns) 4 MMAs. Accumulator fragments of one layer become the
+// A fragments of the next in registers (columns 16k .. 16k+15 of the output
+// are tiles 2k and 2k+1). Every product and partial sum is an integer below
+// 2^24 in magnitude, so the FP32 accumulation is exact and the result equals
+// the integer arithmetic of the definition.
+//
+// The activation round(a / 2^s) half up, clamped to 0..255, is taken in FP32
+// without conversions: a + 2^(s-1) is exact for s <= 23 (|a| < 2^23), the
+// scaling by 2^-s is exact, and adding 2^23 rounding down leaves floor() in
+// the low bits; for s >= 24 the result is 0. Integers of magnitude <= 256 are
+// exact in bf16 and their FP32 bit pattern ends in 16 zero bits, so a pair
+// packs into a bf16x2 register with one byte permutation.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "predictor.cuh"
+
+using namespace mcc;
+
+namespace {
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// two small integers held in FP32 -> bf16x2 (lo in the low half)
+__device__ __forceinline__ uint32_t pack_int2(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+__device__ __forceinline__ float act8(float a, float half, float inv) {
+  const float x = __fmul_rn(__fadd_rn(a, half), inv);
+  const float f = __fsub_rn(__fadd_rd(x, 0x1p23f), 0x1p23f);
+  return fminf(fmaxf(f, 0.0f), 255.0f);
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// Model in shared memory: bf16 weights with rows padded by 8 elements
+// (row strides of 12 and 36 words put the 8 rows of a fragment load on
+// distinct banks), biases as exact floats.
+struct SModel {
+  uint16_t W1[kH][kK + 8];
+  uint16_t W2[kH][kH + 8];
+  uint16_t W3[8][kH + 8];  // row 0 = W3, rows 1..7 = 0
+  float b1[kH], b2[kH];
+  float b3, half1, inv1, half2, inv2, out_scale, sxs;
+  int ok;
+};
+
+__device__ __forceinline__ uint16_t bf16_of_int8(int v) {
+  return (uint16_t)(__float_as_uint((float)v) >> 16);
+}
+
+// Parse and validate the blob (the same checks as the format's definition);
+// every thread returns the same verdict.
+__device__ bool load_model(const unsigned char *blob, int dim, SModel &m) {
+  const int tid = threadIdx.x;
+  const int nin = (1 << dim) + dim;
+  if (tid == 0) {
+    const int *w = (const int *)blob;
+    const int sx = w[M_SX / 4], s1 = w[M_S1 / 4], s2 = w[M_S2 / 4], e3 = w[M_E3 / 4];
+    const int b3 = w[M_B3 / 4];
+    int ok = (uint32_t)w[M_MAGIC / 4] == kModelMagic && w[M_VERSION / 4] == 1 &&
+             w[M_DIM / 4] == dim && w[M_NIN / 4] == nin;
+    ok = ok && sx >= -60 && sx <= 60 && s1 >= 1 && s1 <= 30 && s2 >= 1 && s2 <= 30 && e3 >= -100 &&
+         e3 <= 60 && b3 >= -(1 << 22) && b3 <= (1 << 22);
+    m.ok = ok;
+    if (ok) {
+      m.b3 = (float)b3;
+      // s >= 24: every activation is 0 (|a| < 2^23); half = inv = 0 gives that
+      m.half1 = s1 <= 23 ? pow2f(s1 - 1) : 0.0f;
+      m.inv1 = s1 <= 23 ? pow2f(-s1) : 0.0f;
+      m.half2 = s2 <= 23 ? pow2f(s2 - 1) : 0.0f;
+      m.inv2 = s2 <= 23 ? pow2f(-s2) : 0.0f;
+      m.out_scale = pow2f(e3);
+      m.sxs = pow2f(-sx);
+    }
+  }
+  __syncthreads();
+  int bad = 0;
+  const signed char *W1 = (const signed char *)(blob + M_W1);
+  const signed char *W2 = (const signed char *)(blob + M_W2);
+  const signed char *W3 = (const signed char *)(blob + M_W3);
+  for (int e = tid; e < kH * kK; e += blockDim.x) {
+    const int v = W1[e], i = e % kK;
+    bad |= v < -127 || (i >= nin && v != 0);
+    m.W1[e / kK][i] = bf16_of_int8(v);
+  }
+  for (int e = tid; e < kH * kH; e += blockDim.x) {
+    const int v = W2[e];
+    bad |= v < -127;
+    m.W2[e / kH][e % kH] = bf16_of_int8(v);
+  }
+  for (int e = tid; e < 8 * kH; e += blockDim.x) {
+    const int v = e < kH ? (int)W3[e] : 0;
+    bad |= v < -127;
+    m.W3[e / kH][e % kH] = bf16_of_int8(v);
+  }
+  for (int j = tid; j < kH; j += blockDim.x) {
+    const int c1 = ((const int *)(blob + M_B1))[j], c2 = ((const int *)(blob + M_B2))[j];
+    bad |= c1 < -(1 << 22) || c1 > (1 << 22) || c2 < -(1 << 22) || c2 > (1 << 22);
+    m.b1[j] = (float)c1;
+    m.b2[j] = (float)c2;
+  }
+  if (bad) atomicAnd(&m.ok, 0);
+  __syncthreads();
+  return m.ok != 0;
+}
+
+// Layer output fragments (8 n-tiles of 16x8, C layout) -> activations as the
+// A fragments of the next layer (4 k-tiles of 16x16).
+__device__ __forceinline__ void act_to_frag(const float (&h)[8][4], const float *bias, float half,
+                                            float inv, int tq, uint32_t (&a)[4][4]) {
+#pragma unroll
+  for (int nt = 0; nt < 8; nt++) {
+    const int c0 = 8 * nt + 2 * tq;
+    const float bl = bias[c0], bh = bias[c0 + 1];
+    const float v0 = act8(__fadd_rn(h[nt][0], bl), half, inv);
+    const float v1 = act8(__fadd_rn(h[nt][1], bh), half, inv);
+    const float v2 = act8(__fadd_rn(h[nt][2], bl), half, inv);
+    const float v3 = act8(__fadd_rn(h[nt][3], bh), half, inv);
+    a[nt >> 1][(nt & 1) ? 2 : 0] = pack_int2(v0, v1);
+    a[nt >> 1][(nt & 1) ? 3 : 1] = pack_int2(v2, v3);
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_predict(const __grid_constant__ PredArgs A) {
+  pdl_trigger();
+  pdl_wait();
+  __shared__ SModel m;
+  __shared__ __align__(16) uint16_t xs[8][32][kK + 8];
+  __shared__ float ps[8][32];
+  __shared__ int skip;
+  const int f = blockIdx.x;
+  Status *st = A.st[f];
+  if (threadIdx.x == 0)  // fields without a model (or a plain stream) have nothing to do
+    skip = A.model[f] == nullptr || *(volatile unsigned int *)&st->err != 0 ||
+           (A.use[f] && *A.use[f] == 0);
+  __syncthreads();
+  if (skip) return;
+  const unsigned char *blob = A.model[f] + (A.model_off[f] ? *A.model_off[f] : 0);
+  if (!load_model(blob, DIM, m)) {
+    if (threadIdx.x == 0) set_error(st, A.bad_model_err);
+    return;
+  }
+  const PlanView &pv = A.pv;
+  const int *__restrict__ q1 = A.q1[f];
+  float *__restrict__ pout = A.p[f];
+  const float rf = *A.rho12_f[f];
+  const long long Qhi = *A.qhi[f];
+  const float linv = Qhi > 0 ? __fdiv_rn(127.0f, __ll2float_rn(Qhi)) : 0.0f;
+  const float sxs = m.sxs;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, tq = lane & 3;
+  const int64_t n = pv.n_v;
+  const int nx = pv.nx;
+  const int64_t sxy = (int64_t)pv.nx * pv.ny;
+  const int64_t step = (int64_t)gridDim.y * 256;
+  for (int64_t base = ((int64_t)blockIdx.y * 8 + w) * 32; base < n; base += step) {
+    // ---- features of this lane's vertex
+    const int64_t i = base + lane;
+    float feat[kK];
+#pragma unroll
+    for (int k = 0; k < kK; k++) feat[k] = 0.0f;
+    if (i < n) {
+      const uint32_t c = __ldg(pv.cell + i);
+      int cor[8];
+      cor[0] = __ldg(q1 + c);
+      cor[1] = __ldg(q1 + c + 1);
+      cor[2] = __ldg(q1 + c + nx);
+      cor[3] = __ldg(q1 + c + nx + 1);
+      if (DIM == 3) {
+        cor[4] = __ldg(q1 + c + sxy);
+        cor[5] = __ldg(q1 + c + sxy + 1);
+        cor[6] = __ldg(q1 + c + sxy + nx);
+        cor[7] = __ldg(q1 + c + sxy + nx + 1);
+      }
+#pragma unroll
+      for (int k = 1; k < (1 << DIM); k++) {
+        float e = __fmul_rn(__int2float_rn(wsub(cor[k], cor[0])), rf);
+        e = __fmul_rn(e, sxs);
+        feat[k - 1] = fminf(fmaxf(rintf(e), -127.0f), 127.0f);
+      }
+#pragma unroll
+      for (int d = 0; d < DIM; d++) {
+        const float fr = __fmul_rn(__uint2float_rn(__ldg(pv.frac + (int64_t)d * n + i)), 0x1p-15f);
+        feat[(1 << DIM) - 1 + d] = rintf(__fmul_rn(fr, 127.0f));
+      }
+      const float lv = rintf(__fmul_rn(__fmul_rn(__int2float_rn(cor[0]), rf), linv));
+      feat[(1 << DIM) + DIM - 1] = fminf(fmaxf(lv, 0.0f), 127.0f);
+    }
+#pragma unroll
+    for (int k = 0; k < kK; k += 2)
+      *reinterpret_cast<uint32_t *>(&xs[w][lane][k]) = pack_int2(feat[k], feat[k + 1]);
+    __syncwarp();
+    // ---- two 16-row tiles through the network
+#pragma unroll
+    for (int t = 0; t < 2; t++) {
+      const int r0 = 16 * t + g, r1 = r0 + 8;
+      uint32_t a[4];
+      a[0] = *reinterpret_cast<const uint32_t *>(&xs[w][r0][2 * tq]);
+      a[1] = *reinterpret_cast<const uint32_t *>(&xs[w][r1][2 * tq]);
+      a[2] = *reinterpret_cast<const uint32_t *>(&xs[w][r0][2 * tq + 8]);
+      a[3] = *reinterpret_cast<const uint32_t *>(&xs[w][r1][2 * tq + 8]);
+      float h[8][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; nt++) {
+        h[nt][0] = h[nt][1] = h[nt][2] = h[nt][3] = 0.0f;
+        const int col = 8 * nt + g;
+        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&m.W1[col][2 * tq]);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&m.W1[col][2 * tq + 8]);
+        mma_bf16(h[nt], a, b0, b1);
+      }
+      uint32_t a2[4][4];
+      act_to_frag(h, m.b1, m.half1, m.inv1, tq, a2);
+#pragma unroll
+      for (int nt = 0; nt < 8; nt++) {
+        h[nt][0] = h[nt][1] = h[nt][2] = h[nt][3] = 0.0f;
+        const int col = 8 * nt + g;
+#pragma unroll
+        for (int kt = 0; kt < 4; kt++) {
+          const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&m.W2[col][16 * kt + 2 * tq]);
+          const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&m.W2[col][16 * kt + 2 * tq + 8]);
+          mma_bf16(h[nt], a2[kt], b0, b1);
+        }
+      }
+      uint32_t a3[4][4];
+      act_to_frag(h, m.b2, m.half2, m.inv2, tq, a3);
+      float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int kt = 0; kt < 4; kt++) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&m.W3[g][16 * kt + 2 * tq]);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&m.W3[g][16 * kt + 2 * tq + 8]);
+        mma_bf16(o, a3[kt], b0, b1);
+      }
+      if (tq == 0) {  // column 0 holds the outputs of rows g and g + 8
+        ps[w][r0] = __fmul_rn(__fadd_rn(o[0], m.b3), m.out_scale);
+        ps[w][r1] = __fmul_rn(__fadd_rn(o[2], m.b3), m.out_scale);
+      }
+    }
+    __syncwarp();
+    if (i < n) pout[i] = ps[w][lane];
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_predict(const PredArgs &A, cudaStream_t stream, bool pdl) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t warps = (A.pv.n_v + 31) / 32;
+  int64_t chunks = (sms * 4 + A.nf - 1) / A.nf;
+  if (chunks > (warps + 7) / 8) chunks = (warps + 7) / 8;
+  if (chunks < 1) chunks = 1;
+  if (chunks > 65535) chunks = 65535;
+  const dim3 grid(A.nf, (unsigned int)chunks);
+  if (A.pv.dim == 2) {
+    if (pdl) return launch_pdl(k_predict<2>, grid, dim3(256), 0, stream, A);
+    k_predict<2><<<grid, 256, 0, stream>>>(A);
+  } else {
+    if (pdl) return launch_pdl(k_predict<3>, grid, dim3(256), 0, stream, A);
+    k_predict<3><<<grid, 256, 0, stream>>>(A);
+  }
+  return cudaGetLastError();
+}

@@ -8,7 +8,7 @@ namespace mcc {
 // Compression workspace (byte offsets; the status block sits at 0).
 struct CompressWs {
   size_t hist1, hist2, code1, code2, len1, len2, Q, q1, sym1, sym2, val1, val2, gw, ge, gr, pb, pe,
-      pr, total;
+      pr, p, total;
 };
 
 // Decode tables of one component: first-level table on kLutBits bits
@@ -22,8 +22,8 @@ struct DecTab {
 
 // Parsed and validated stream header.
 struct DecInfo {
-  int dtype, dim, R1, R2, C1, C2, lmax, pad;
-  long long K, rho12_q;
+  int dtype, dim, R1, R2, C1, C2, lmax, use_model;
+  long long K, rho12_q, Qhi;
   float rho12_f;
   int pad2;
   double s2;
@@ -33,7 +33,7 @@ struct DecInfo {
 };
 
 struct DecompressWs {
-  size_t info, tab1, tab2, q1, q2, total;
+  size_t info, tab1, tab2, q1, q2, p, total;
 };
 
 }  // namespace mcc
@@ -46,10 +46,12 @@ mcc_status launch_compress(const mcc::PlanView &pv, const void *d_values, const 
                            cudaStream_t stream);
 mcc_status launch_decompress(const mcc::PlanView &pv, const unsigned char *in, size_t in_bytes,
                              void *d_values, int dtype, unsigned char *ws, cudaStream_t stream);
+// front_only: stop after the grid stage (field parameters, vertex codes Q and
+// grid codes q1 in the workspace; no output is written).
 mcc_status launch_compress_batch(const mcc::PlanView &pv, int nf, const void *const *xs,
                                  const mcc_params *ps, unsigned char *ws0, int64_t wss,
                                  unsigned char *out0, int64_t oss, size_t capacity,
-                                 cudaStream_t stream);
+                                 cudaStream_t stream, bool front_only = false);
 mcc_status launch_decompress_batch(const mcc::PlanView &pv, int nf, const unsigned char *in0,
                                    int64_t iss, const uint64_t *in_bytes, void *const *xo,
                                    int dtype, unsigned char *ws0, int64_t wss, cudaStream_t stream);

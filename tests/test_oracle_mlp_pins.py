@@ -24,28 +24,7 @@ def plan3d():
     return coords, oracle.Plan(coords, cells, (13, 12, 9))
 
 
-def _blank(dim, sx=0, s1=1, s2=1, e3=0):
-    return dict(dim=dim, sx=sx, s1=s1, s2=s2, e3=e3, W1=np.zeros((H, 16), np.int8),
-                W2=np.zeros((H, H), np.int8), W3=np.zeros(H, np.int8),
-                b1=np.zeros(H, np.int32), b2=np.zeros(H, np.int32), b3=0)
-
-
-def _pack(m):
-    return oracle.pack_model(**m)
-
-
-def _random_model(dim, seed, sx=0):
-    """A valid model with activations that use their 8-bit range."""
-    rng = np.random.default_rng(seed)
-    n_in = (1 << dim) - 1 + dim
-    m = _blank(dim, sx=sx, s1=9, s2=11, e3=-9)
-    m["W1"][:, :n_in] = rng.integers(-127, 128, (H, n_in))
-    m["W2"][:] = rng.integers(-127, 128, (H, H))
-    m["W3"][:] = rng.integers(-127, 128, H)
-    m["b1"][:] = rng.integers(-4000, 4000, H)
-    m["b2"][:] = rng.integers(-20000, 20000, H)
-    m["b3"] = int(rng.integers(-1000, 1000))
-    return m
+from mlp_models import blank as _blank, pack as _pack, random_model as _random_model  # noqa: E402
 
 
 # --------------------------------------------------------------------------- #
@@ -111,6 +90,21 @@ def test_identity_network_returns_corner_differences(dim):
         want = np.round(fr[:, d].astype(np.float64) * 127.0)
         assert np.array_equal(p, want.astype(np.float32))
     assert np.all(feats[:, nc - 1 + dim:] == 0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_level_feature(dim):
+    """The last feature is the level of corner 000 as a fraction of the value
+    range: rint(127 c_000 (s1/s2) / Qhi), clamped to 0..127; 0 when Qhi = 0."""
+    nc = 1 << dim
+    corners = np.zeros((6, 8), np.int32)
+    corners[:, 0] = [0, 50, 100, 199, 400, 1000]
+    m = _pack(_identity_model(dim, nc - 1 + dim))
+    _, p = oracle.mlp_predict(dim, m, corners, np.zeros((6, 3), np.float32), 2.0, Qhi=400)
+    # 127 * 2 c / 400: 0, 31.75, 63.5 (ties to even: 64), 126.365, 254 -> 127, 635 -> 127
+    assert list(p) == [0.0, 32.0, 64.0, 126.0, 127.0, 127.0]
+    _, p = oracle.mlp_predict(dim, m, corners, np.zeros((6, 3), np.float32), 2.0, Qhi=0)
+    assert np.all(p == 0.0)
 
 
 def test_feature_scale_by_bin_ratio():
@@ -197,7 +191,8 @@ def test_learned_prediction_is_interpolation_plus_network(plan2d):
     corners[:, 2], corners[:, 3] = q1[c + nx], q1[c + nx + 1]
     fr32 = np.zeros((plan.n_v, 3), np.float32)
     fr32[:, :2] = (plan.frac.astype(np.float32) * np.float32(2.0 ** -15)).T
-    _, p = oracle.mlp_predict(2, blob, corners, fr32, f["rho12_f"])
+    _, p = oracle.mlp_predict(2, blob, corners, fr32, f["rho12_f"], Qhi=f["Qhi"])
+    assert int(s[200:208].view(np.int64)[0]) == f["Qhi"]
     fr = plan.frac.astype(np.float64) / 32768.0
     g = ((1 - fr[0]) * (1 - fr[1]) * corners[:, 0] + fr[0] * (1 - fr[1]) * corners[:, 1]
          + (1 - fr[0]) * fr[1] * corners[:, 2] + fr[0] * fr[1] * corners[:, 3])
@@ -324,14 +319,14 @@ def test_quantize_dyadic_weights_exactly():
     rng = np.random.default_rng(7)
     params = _float_params(7)
     W1, b1, W2, b2, W3, b3 = oracle.split_params(params)
-    I1 = rng.integers(-127, 128, (H, 16)); I1[:, 10:] = 0; I1[0, 0] = 127
+    I1 = rng.integers(-127, 128, (H, 16)); I1[:, 11:] = 0; I1[0, 0] = 127
     W1[:] = I1 * 2.0 ** -9
     b1[:] = rng.integers(-500, 500, H) * 2.0 ** -16
     blob = oracle.mlp_quantize(3, 2, params, 3.0, 5.0)
     m = oracle.unpack_model(blob)
     assert np.array_equal(m["W1"], I1)
     assert np.array_equal(m["b1"], np.rint(b1.astype(np.float64) * 2.0 ** 16).astype(np.int32))
-    assert m["sx"] == 2 and m["dim"] == 3 and m["n_in"] == 7 + 3
+    assert m["sx"] == 2 and m["dim"] == 3 and m["n_in"] == 7 + 3 + 1
 
 
 def test_quantize_scale_invariances():
@@ -389,3 +384,20 @@ def test_quantize_degenerate_and_errors():
         oracle.mlp_quantize(2, 61, params, 1.0, 1.0)
     with pytest.raises(oracle.OracleError):
         oracle.mlp_quantize(2, 0, params, -1.0, 1.0)
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_edge_models_hold_bound(plan2d, plan3d, which):
+    """Saturated or zeroed activations, extreme exponents and biases: the
+    bound holds whatever the network says (a correction too large for the
+    residual codes turns the vertex into a raw value)."""
+    from mlp_models import edge_models
+    coords, plan = plan2d if which == "2d" else plan3d
+    x = synth.field_vortex(coords, seed=9) if which == "3d" else synth.field_bumps_noise(coords, seed=9)
+    f = oracle.field_params(x, eb=1e-4)
+    for name, m in edge_models(plan.dim):
+        s, dbg = oracle.compress(plan, x, debug=True, eb=1e-4, model=_pack(m))
+        y = oracle.decompress(plan, s)
+        assert np.abs(y - x).max() <= f["tau2"], name
+        if name == "e3_max":  # p = 0 only where the output sum is exactly 0
+            assert np.mean(dbg["sym2"] == 2 * 512 - 1) > 0.99
