@@ -859,8 +859,10 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   const size_t vsz = p->dtype == 0 ? 8 : 4;
   const int R1 = p->R1, R2 = p->R2;
   mlp_t model;
-  const int use_model = p->model != NULL;
+  int use_model = p->model != NULL;
   if (use_model && (st = model_parse(p->model, p->model_bytes, dim, &model))) return st;
+  /* with auto_select both predictors run and the smaller encoding is kept */
+  const int passes = use_model && p->auto_select ? 2 : 1;
 
   int32_t *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_v);
   int32_t *q1 = (int32_t *)malloc(sizeof(int32_t) * (size_t)ng);
@@ -868,13 +870,17 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   uint16_t *sym1 = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)ng);
   uint16_t *sym2 = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n_v);
   int32_t *val2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_v);
+  uint16_t *sym2b = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n_v);
+  int32_t *val2b = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_v);
   uint64_t *h1 = (uint64_t *)calloc((size_t)2 * R1, sizeof(uint64_t));
   uint64_t *h2 = (uint64_t *)calloc((size_t)2 * R2, sizeof(uint64_t));
+  uint64_t *h2b = (uint64_t *)calloc((size_t)2 * R2, sizeof(uint64_t));
+  uint8_t *len2b = (uint8_t *)calloc((size_t)2 * R2, 1);
   uint8_t *len1 = (uint8_t *)calloc((size_t)2 * R1, 1), *len2 = (uint8_t *)calloc((size_t)2 * R2, 1);
   uint32_t *code1 = (uint32_t *)calloc((size_t)2 * R1, 4), *code2 = (uint32_t *)calloc((size_t)2 * R2, 4);
   st = ORC_OK;
   if (!Q || !q1 || !dl || !sym1 || !sym2 || !val2 || !h1 || !h2 || !len1 || !len2 || !code1 ||
-      !code2) {
+      !code2 || !sym2b || !val2b || !h2b || !len2b) {
     st = ORC_ERR_OOM;
     goto done;
   }
@@ -919,38 +925,68 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   }
 
   /* 4. g(x1') at every vertex (plus the learned correction when a model is
-   *    given), residual code q2 = Q - P, bound guard */
-  uint64_t nout2 = 0, nraw = 0;
-  for (int64_t i = 0; i < n_v; i++) {
-    float fx = (float)frac[i] * 0x1p-15f;
-    float fy = (float)frac[n_v + i] * 0x1p-15f;
-    float fz = dim == 3 ? (float)frac[2 * n_v + i] * 0x1p-15f : 0.0f;
-    int32_t cor[8];
-    float acc = vertex_interp(dim, q1, nx, ny, cell[i], fx, fy, fz, cor);
-    int64_t P;
-    if (use_model) {
-      int32_t xq[MLP_K];
-      mlp_features(dim, model.sx, cor, fx, fy, fz, f.rho12_f, f.Qhi, xq);
-      P = rescale_p(cor[0], acc, f.rho12_q, f.rho12_f, mlp_forward(&model, xq));
-    } else {
-      P = rescale(cor[0], acc, f.rho12_q, f.rho12_f);
+   *    given), residual code q2 = Q - P, bound guard. With auto_select, pass
+   *    0 is the plain predictor and pass 1 the learned one. */
+  uint64_t nout2 = 0, nraw = 0, nout2b = 0, nrawb = 0;
+  for (int pass = 0; pass < passes; pass++) {
+    const int um = passes == 2 ? pass : use_model;
+    uint16_t *s2 = pass ? sym2b : sym2;
+    int32_t *v2 = pass ? val2b : val2;
+    uint64_t *hh = pass ? h2b : h2;
+    uint64_t *no = pass ? &nout2b : &nout2, *nr = pass ? &nrawb : &nraw;
+    for (int64_t i = 0; i < n_v; i++) {
+      float fx = (float)frac[i] * 0x1p-15f;
+      float fy = (float)frac[n_v + i] * 0x1p-15f;
+      float fz = dim == 3 ? (float)frac[2 * n_v + i] * 0x1p-15f : 0.0f;
+      int32_t cor[8];
+      float acc = vertex_interp(dim, q1, nx, ny, cell[i], fx, fy, fz, cor);
+      int64_t P;
+      if (um) {
+        int32_t xq[MLP_K];
+        mlp_features(dim, model.sx, cor, fx, fy, fz, f.rho12_f, f.Qhi, xq);
+        P = rescale_p(cor[0], acc, f.rho12_q, f.rho12_f, mlp_forward(&model, xq));
+      } else {
+        P = rescale(cor[0], acc, f.rho12_q, f.rho12_f);
+      }
+      int64_t q2 = (int64_t)Q[i] - P;
+      /* guard: reconstruct exactly as the decompressor will, check |x - x'| */
+      double v = load_value(x, p->dtype, i);
+      double xr = f.s2 * (double)((int64_t)Q[i] + f.K);
+      double xo = p->dtype == 0 ? xr : (double)(float)xr;
+      if (fabs(v - xo) > f.tau2 || q2 <= INT32_MIN || q2 > INT32_MAX) {
+        s2[i] = (uint16_t)(2 * R2 - 1);
+        (*nr)++;
+      } else if (q2 >= -(R2 - 1) && q2 <= R2 - 2) {
+        s2[i] = (uint16_t)(q2 + R2);
+      } else {
+        s2[i] = 0;
+        v2[i] = (int32_t)q2;
+        (*no)++;
+      }
+      hh[s2[i]]++;
     }
-    int64_t q2 = (int64_t)Q[i] - P;
-    /* guard: reconstruct exactly as the decompressor will, check |x - x'| */
-    double v = load_value(x, p->dtype, i);
-    double xr = f.s2 * (double)((int64_t)Q[i] + f.K);
-    double xo = p->dtype == 0 ? xr : (double)(float)xr;
-    if (fabs(v - xo) > f.tau2 || q2 <= INT32_MIN || q2 > INT32_MAX) {
-      sym2[i] = (uint16_t)(2 * R2 - 1);
-      nraw++;
-    } else if (q2 >= -(R2 - 1) && q2 <= R2 - 2) {
-      sym2[i] = (uint16_t)(q2 + R2);
-    } else {
-      sym2[i] = 0;
-      val2[i] = (int32_t)q2;
-      nout2++;
+  }
+  if (passes == 2) {
+    /* the exact encoded size of each choice: code bits plus escape and raw
+     * values, plus the model for the learned one; a tie keeps the plain */
+    if ((st = orc_huffman_lengths(h2, 2 * R2, p->lmax, len2))) goto done;
+    if ((st = orc_huffman_lengths(h2b, 2 * R2, p->lmax, len2b))) goto done;
+    uint64_t bz = 0, bl = 0;
+    for (int k = 0; k < 2 * R2; k++) {
+      bz += h2[k] * len2[k];
+      bl += h2b[k] * len2b[k];
     }
-    h2[sym2[i]]++;
+    bz += 32 * h2[0] + 8 * vsz * h2[2 * R2 - 1];
+    bl += 32 * h2b[0] + 8 * vsz * h2b[2 * R2 - 1] + 8 * (uint64_t)MODEL_BYTES;
+    if (bl < bz) {
+      uint16_t *ts = sym2; sym2 = sym2b; sym2b = ts;
+      int32_t *tv = val2; val2 = val2b; val2b = tv;
+      uint64_t *th = h2; h2 = h2b; h2b = th;
+      nout2 = nout2b;
+      nraw = nrawb;
+    } else {
+      use_model = 0;
+    }
   }
 
   /* 5. canonical Huffman code books */
@@ -1028,6 +1064,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   if (sym2_dbg) memcpy(sym2_dbg, sym2, sizeof(uint16_t) * (size_t)n_v);
 done:
   free(Q); free(q1); free(dl); free(sym1); free(sym2); free(val2); free(h1); free(h2);
+  free(sym2b); free(val2b); free(h2b); free(len2b);
   free(len1); free(len2); free(code1); free(code2);
   return st;
 }

@@ -68,6 +68,7 @@ typedef struct {
   int lmax;           /* Huffman length limit */
   const uint8_t *model; /* learned predictor (integer MLP blob) or NULL */
   size_t model_bytes;
+  int auto_select;    /* with a model: keep the predictor whose encoding is smaller */
 } orc_params;
 
 /* Per-field scalars derived from the values (Sec. III bound split). */

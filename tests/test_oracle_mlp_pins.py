@@ -401,3 +401,69 @@ def test_edge_models_hold_bound(plan2d, plan3d, which):
         assert np.abs(y - x).max() <= f["tau2"], name
         if name == "e3_max":  # p = 0 only where the output sum is exactly 0
             assert np.mean(dbg["sym2"] == 2 * 512 - 1) > 0.99
+
+
+def _auto_cost(sym2, R2, vsz, model):
+    cnt = np.bincount(sym2, minlength=2 * R2).astype(np.uint64)
+    ln = oracle.huffman_lengths(cnt).astype(np.uint64)
+    bits = int((cnt * ln).sum()) + 32 * int(cnt[0]) + 8 * vsz * int(cnt[2 * R2 - 1])
+    return bits + (8 * oracle.MODEL_BYTES if model else 0)
+
+
+def _convex_model(B):
+    """p ~ -(B[0] f(X) + B[1] f(Y)), f(t) = t (127 - t) / 127^2: the bilinear
+    interpolation error of a paraboloid, in vertex bins, as a piecewise-linear
+    function of the coordinate features X, Y (knots 0, 32, 64, 96: ReLU units
+    relu(X - t) carried exactly through both layers), output scale 2^-4."""
+    knots = np.array([0, 32, 64, 96, 127], np.float64)
+    f = knots * (127 - knots) / 127.0 ** 2
+    slope = np.diff(f) / np.diff(knots)
+    c = np.concatenate([[slope[0]], np.diff(slope)])
+    m = _blank(2, s1=1, s2=1, e3=-4)
+    for a in range(2):
+        for k in range(4):
+            u = 4 * a + k
+            m["W1"][u, 3 + a] = 2
+            m["b1"][u] = -2 * int(knots[k])
+            m["W2"][u, u] = 2
+            m["W3"][u] = int(np.rint(-B[a] * c[k] * 16))
+    return m
+
+
+@pytest.fixture(scope="module")
+def plan2d_big():
+    coords, cells = synth.mesh2d_jittered(nside=200, seed=33)
+    return coords, oracle.Plan(coords, cells, (33, 29))
+
+
+@pytest.mark.parametrize("which", ["zero", "random", "convex"])
+def test_auto_selection_keeps_the_smaller_encoding(plan2d_big, which):
+    """Auto selection: both predictors run; the learned one is kept when its
+    code bits plus escape and raw values plus the model are fewer than the
+    plain predictor's (a tie keeps the plain). Costs recomputed here from the
+    two single-predictor runs. For a paraboloid the bilinear interpolation
+    error is a known function of the local coordinates, which a hand-built
+    network predicts, so there the learned predictor wins."""
+    coords, plan = plan2d_big
+    eb = 2e-6
+    s2 = 2 * (0.5 * eb) * (1 - 2.0 ** -20)
+    if which == "convex":
+        x = coords[:, 0] ** 2 + coords[:, 1] ** 2
+        h = plan.grid.h
+        m = _convex_model((h[0] ** 2 / s2, h[1] ** 2 / s2))
+    else:
+        x = 1e-3 * synth.field_bumps_noise(coords, seed=14)
+        m = _blank(2) if which == "zero" else _random_model(2, 15)
+    blob = _pack(m)
+    kw = dict(eb=eb, eb_mode="abs")
+    s0, d0 = oracle.compress(plan, x, debug=True, **kw)
+    s1, d1 = oracle.compress(plan, x, debug=True, model=blob, **kw)
+    sa = oracle.compress(plan, x, model=blob, auto=True, **kw)
+    c0 = _auto_cost(d0["sym2"], 512, 8, False)
+    c1 = _auto_cost(d1["sym2"], 512, 8, True)
+    want = s1 if c1 < c0 else s0
+    assert np.array_equal(sa, want)
+    if which == "convex":
+        assert c1 < c0
+    else:
+        assert c1 >= c0
