@@ -56,7 +56,7 @@ typedef enum {
 
 enum { MCC_F64 = 0, MCC_F32 = 1 };   /* value types */
 enum { MCC_ABS = 0, MCC_REL = 1 };   /* bound modes: absolute, or x (max - min) */
-enum { MCC_PRED_ZERO = 0, MCC_PRED_LEARNED = 1 };  /* residual predictor */
+enum { MCC_PRED_ZERO = 0, MCC_PRED_LEARNED = 1, MCC_PRED_AUTO = 2 };  /* residual predictor */
 #define MCC_MODEL_BYTES 5736   /* learned-predictor blob */
 #define MCC_MLP_PARAMS 5313    /* float parameters of the training network */
 
@@ -97,7 +97,11 @@ typedef struct {
    * vertex rounding (P = round(rho12 g + p), so the bound holds as before);
    * d_model is a device pointer (4-byte aligned) to an MCC_MODEL_BYTES blob
    * (see mcc_model_train), copied into every stream that uses it. An invalid
-   * blob records MCC_ERR_INVALID_ARG on the device. */
+   * blob records MCC_ERR_INVALID_ARG on the device. MCC_PRED_AUTO: both
+   * predictors run and the field keeps the one whose encoding is smaller:
+   * code bits (sum over symbols of count x code length, each predictor with
+   * the code book of its own histogram) plus 32 bits per escape, the raw
+   * values and, for the learned one, the model; a tie keeps the plain one. */
   int predictor;
   const void *d_model;
 } mcc_params;

@@ -28,7 +28,7 @@ __all__ = [
 OK, INVALID_ARG, CUDA, OOM, RANGE, CORRUPT, CAPACITY, TIMEOUT, UNSUPPORTED = range(9)
 F64, F32 = 0, 1
 ABS, REL = 0, 1
-PRED_ZERO, PRED_LEARNED = 0, 1
+PRED_ZERO, PRED_LEARNED, PRED_AUTO = 0, 1, 2
 LOSS_L2, LOSS_L1 = 0, 1
 MODEL_BYTES = 5736
 MLP_PARAMS = 5313
@@ -162,16 +162,17 @@ def _dptr(t: torch.Tensor):
     return C.c_void_p(t.data_ptr())
 
 
-def params_default(model=None, **overrides) -> Params:
+def params_default(model=None, auto=False, **overrides) -> Params:
     """Parameters; ``model`` (a CUDA uint8 tensor of MODEL_BYTES) selects the
-    learned predictor. The structure keeps a reference to the tensor."""
+    learned predictor, or with ``auto`` the smaller of learned and plain. The
+    structure keeps a reference to the tensor."""
     p = Params()
     load().mcc_params_default(C.byref(p))
     if model is not None:
         if model.dtype != torch.uint8 or model.numel() != MODEL_BYTES:
             raise ValueError("model must be a uint8 tensor of MODEL_BYTES bytes")
         p._model = model
-        p.predictor = PRED_LEARNED
+        p.predictor = PRED_AUTO if auto else PRED_LEARNED
         p.d_model = _dptr(model).value
     for k, v in overrides.items():
         if k == "dtype" and not isinstance(v, int):

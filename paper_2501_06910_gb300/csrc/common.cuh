@@ -122,6 +122,7 @@ struct Status {
   unsigned long long w1, w2;          // bitstream words per component
   Layout L;                            // stream layout of the current call
   FieldParams f;
+  unsigned int pick;                   // auto predictor: 1 = learned kept
 };
 static_assert(sizeof(Status) <= 1024, "status block");
 constexpr size_t kStatusBytes = 1024;

@@ -53,6 +53,8 @@ struct CompArgs {
   const void *x[kMaxBatch];
   RParams rp[kMaxBatch];
   const unsigned char *model[kMaxBatch];  // learned-predictor blob or NULL
+  unsigned char mode[kMaxBatch];          // MCC_PRED_* per field
+  int any_auto;
 };
 
 // Per-field pointers into the workspace and the output slot.
@@ -66,22 +68,26 @@ struct Ctx {
   const void *x;
 };
 
-__device__ __forceinline__ Ctx ctx_of(const CompArgs &A, int f) {
+// The residual component's arrays of field f: the learned side when the
+// field's auto choice kept the learned predictor (read from its status block).
+__device__ __forceinline__ Ctx ctx_of(const CompArgs &A, int f, bool chosen = false) {
   Ctx c;
   unsigned char *ws = A.ws0 + (int64_t)f * A.wss;
+  const bool b = chosen && A.any_auto && A.mode[f] == MCC_PRED_AUTO &&
+                 *(volatile const unsigned int *)&((const Status *)ws)->pick;
   c.st = (Status *)ws;
   c.hist1 = (unsigned int *)(ws + A.W.hist1);
-  c.hist2 = (unsigned int *)(ws + A.W.hist2);
+  c.hist2 = (unsigned int *)(ws + (b ? A.W.hist2b : A.W.hist2));
   c.code1 = (unsigned int *)(ws + A.W.code1);
-  c.code2 = (unsigned int *)(ws + A.W.code2);
+  c.code2 = (unsigned int *)(ws + (b ? A.W.code2b : A.W.code2));
   c.len1 = ws + A.W.len1;
-  c.len2 = ws + A.W.len2;
+  c.len2 = ws + (b ? A.W.len2b : A.W.len2);
   c.Q = (int *)(ws + A.W.Q);
   c.q1 = (int *)(ws + A.W.q1);
   c.sym1 = (unsigned short *)(ws + A.W.sym1);
-  c.sym2 = (unsigned short *)(ws + A.W.sym2);
+  c.sym2 = (unsigned short *)(ws + (b ? A.W.sym2b : A.W.sym2));
   c.val1 = (int *)(ws + A.W.val1);
-  c.val2 = (int *)(ws + A.W.val2);
+  c.val2 = (int *)(ws + (b ? A.W.val2b : A.W.val2));
   c.gw = (unsigned int *)(ws + A.W.gw);
   c.ge = (unsigned int *)(ws + A.W.ge);
   c.gr = (unsigned int *)(ws + A.W.gr);
@@ -169,6 +175,11 @@ __global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ CompArgs
   const int nhist = (int)((A.W.hist2 - A.W.hist1) / 4 + A.nsym2);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nhist; i += gridDim.x * blockDim.x)
     hist[i] = 0;
+  if (A.mode[blockIdx.y] == MCC_PRED_AUTO) {
+    unsigned int *hb = (unsigned int *)(A.ws0 + (int64_t)blockIdx.y * A.wss + A.W.hist2b);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nsym2; i += gridDim.x * blockDim.x)
+      hb[i] = 0;
+  }
   unsigned long long mn = 0, mx = 0;  // mn holds ~key (max of ~key = min key)
   bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -426,11 +437,26 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
 // ---------------------------------------------------------------------------
 // k_node: residual codes at the vertices
 // ---------------------------------------------------------------------------
+// Residual symbol of one vertex: raw (guard failed or the code leaves int32),
+// a code within the alphabet, or an escape whose value goes to val2.
+__device__ __forceinline__ int residual_symbol(long long q2, bool guard_fail, int R2, int64_t i,
+                                               int *__restrict__ val2) {
+  if (guard_fail || q2 <= -2147483648ll || q2 > 2147483647ll) return 2 * R2 - 1;  // INT32_MIN reserved
+  if (q2 >= -(R2 - 1) && q2 <= R2 - 2) return (int)q2 + R2;
+  val2[i] = (int)q2;
+  return 0;
+}
+
+// HAS_P: some field of the launch uses the learned predictor (mode 1) or
+// chooses between both (mode 2: the plain side goes to sym2 / hist2, the
+// learned side to sym2b / hist2b; the histograms share the dynamic shared
+// memory, the learned one at offset 2 R2).
 template <int DIM, typename T, bool HAS_P>
 __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
-  const Ctx c = ctx_of(A, blockIdx.x);
+  const int fi = blockIdx.x;
+  const Ctx c = ctx_of(A, fi);
   const PlanView &pv = A.pv;
   const T *__restrict__ x = (const T *)c.x;
   const int *__restrict__ Q = c.Q;
@@ -439,60 +465,63 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
   const int R2 = A.R2;
   unsigned short *__restrict__ sym2 = c.sym2;
   int *__restrict__ val2 = c.val2;
-  unsigned int *hist2 = c.hist2;
+  unsigned char *ws = A.ws0 + (int64_t)fi * A.wss;
+  unsigned short *__restrict__ sym2b = (unsigned short *)(ws + A.W.sym2b);
+  int *__restrict__ val2b = (int *)(ws + A.W.val2b);
   extern __shared__ unsigned int shist[];
   if (block_failed(st)) return;
+  const int mode = HAS_P ? A.mode[fi] : MCC_PRED_ZERO;
+  const bool both = mode == MCC_PRED_AUTO;
   const int nsym = 2 * R2;
-  for (int i = threadIdx.x; i < nsym; i += blockDim.x) shist[i] = 0;
+  for (int i = threadIdx.x; i < (both ? 2 : 1) * nsym; i += blockDim.x) shist[i] = 0;
   __syncthreads();
   const FieldParams f = st->f;
   const int64_t n = pv.n_v;
   const int nx = pv.nx;
   const int64_t sxy = (int64_t)pv.nx * pv.ny;
-  const int rawsym = 2 * R2 - 1;
   const float *__restrict__ pcor = c.p;
-  const bool use_p = HAS_P && A.model[blockIdx.x] != nullptr;
-  unsigned int nesc = 0, nraw = 0;
   const int64_t stride = (int64_t)gridDim.y * blockDim.x;
   const int64_t nloop = (n + stride - 1) / stride * stride;  // uniform trip count per warp
   for (int64_t i = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i < nloop; i += stride) {
     const bool valid = i < n;
-    int sym = 0;
+    int sym = 0, symb = 0;
     if (valid) {
-      const uint32_t c = __ldg(pv.cell + i);
+      const uint32_t cl = __ldg(pv.cell + i);
       const float fx = __fmul_rn(__uint2float_rn(__ldg(pv.frac + i)), 0x1p-15f);
       const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + i)), 0x1p-15f);
       const float fz = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + i)), 0x1p-15f) : 0.0f;
       const int Qi = __ldg(Q + i);
-      const float pc = use_p ? __ldg(pcor + i) : 0.0f;
-      const long long P = predict_vertex<DIM, HAS_P>(q1, c, fx, fy, fz, nx, sxy, f.rho12_q, f.rho12_f, pc);
-      const long long q2 = (long long)Qi - P;
-      bool raw = q2 <= -2147483648ll || q2 > 2147483647ll;  // INT32_MIN is reserved
-      if (f.guard) {
+      float acc;
+      const int c000 = interp_vertex<DIM>(q1, cl, fx, fy, fz, nx, sxy, acc);
+      bool gfail = false;
+      if (f.guard) {  // reconstruct as the decompressor will and check |x - x'|
         const double v = (double)__ldg(x + i);
         const double xr = __dmul_rn(f.s2, (double)((long long)Qi + f.K));
         const double xo = sizeof(T) == 8 ? xr : (double)__double2float_rn(xr);
-        if (fabs(__dsub_rn(v, xo)) > f.tau2) raw = true;
+        gfail = fabs(__dsub_rn(v, xo)) > f.tau2;
       }
-      if (raw) {
-        sym = rawsym;
-        nraw++;
-      } else if (q2 >= -(R2 - 1) && q2 <= R2 - 2) {
-        sym = (int)q2 + R2;
+      const float pc = mode != MCC_PRED_ZERO ? __ldg(pcor + i) : 0.0f;
+      if (both) {
+        const long long P0 = rescale<false>(c000, acc, f.rho12_q, f.rho12_f);
+        const long long P1 = rescale<true>(c000, acc, f.rho12_q, f.rho12_f, pc);
+        sym = residual_symbol((long long)Qi - P0, gfail, R2, i, val2);
+        symb = residual_symbol((long long)Qi - P1, gfail, R2, i, val2b);
+        sym2b[i] = (unsigned short)symb;
       } else {
-        sym = 0;
-        val2[i] = (int)q2;
-        nesc++;
+        const long long P = rescale<HAS_P>(c000, acc, f.rho12_q, f.rho12_f, pc);
+        sym = residual_symbol((long long)Qi - P, gfail, R2, i, val2);
       }
       sym2[i] = (unsigned short)sym;
     }
     hist_add(shist, sym, valid);
+    if (both) hist_add(shist + nsym, symb, valid);
   }
-  if (nesc) atomicAdd(&st->nout2, nesc);
-  if (nraw) atomicAdd(&st->nraw, nraw);
   __syncthreads();
-  for (int i = threadIdx.x; i < nsym; i += blockDim.x)
-    if (shist[i]) atomicAdd(hist2 + i, shist[i]);
+  unsigned int *hist2b = (unsigned int *)(ws + A.W.hist2b);
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x) {
+    if (shist[i]) atomicAdd(c.hist2 + i, shist[i]);
+    if (both && shist[nsym + i]) atomicAdd(hist2b + i, shist[nsym + i]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -534,8 +563,17 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
   const int lmax = AA.lmax;
   if (block_failed(st)) return;
   const bool c1 = blockIdx.x == 0;
-  const CodebookArgs A{c1 ? c.hist1 : c.hist2, c1 ? AA.nsym1 : AA.nsym2, c1 ? c.code1 : c.code2,
-                       c1 ? c.len1 : c.len2, c.out + (c1 ? AA.F.lens1 : AA.F.lens2)};
+  // block 2: the learned side of an auto field; with auto, k_choose writes
+  // the residual code lengths into the stream
+  const bool side_b = blockIdx.x == 2;
+  const bool autof = AA.mode[blockIdx.y] == MCC_PRED_AUTO;
+  if (side_b && !autof) return;
+  unsigned char *ws = AA.ws0 + (int64_t)blockIdx.y * AA.wss;
+  const CodebookArgs A{c1 ? c.hist1 : (side_b ? (const unsigned int *)(ws + AA.W.hist2b) : c.hist2),
+                       c1 ? AA.nsym1 : AA.nsym2,
+                       c1 ? c.code1 : (side_b ? (unsigned int *)(ws + AA.W.code2b) : c.code2),
+                       c1 ? c.len1 : (side_b ? ws + AA.W.len2b : c.len2),
+                       c1 ? c.out + AA.F.lens1 : (autof ? nullptr : c.out + AA.F.lens2)};
   const int nsym = A.nsym;
   int npn = 1;  // power of two >= nsym: room for the sort's padding
   while (npn < nsym) npn <<= 1;
@@ -707,9 +745,57 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
   for (int s = tid; s < nsym; s += blockDim.x) {
     const int L = lens[s];
     A.len[s] = (unsigned char)L;
-    A.stream_lens[s] = (unsigned char)L;
+    if (A.stream_lens) A.stream_lens[s] = (unsigned char)L;
     A.code[s] = L ? ct.first[L] + rank[s] : 0u;
   }
+}
+
+// ---------------------------------------------------------------------------
+// k_choose: the auto predictor's choice per field, from the exact encoded
+// size of both sides: code bits (count x length), 32 bits per escape, the raw
+// values and, for the learned side, the model; a tie keeps the plain side.
+// Writes the chosen code lengths into the stream.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_choose(const __grid_constant__ CompArgs A) {
+  pdl_trigger();
+  pdl_wait();
+  const int fi = blockIdx.x;
+  if (A.mode[fi] != MCC_PRED_AUTO) return;
+  const Ctx c = ctx_of(A, fi);
+  Status *st = c.st;
+  __shared__ unsigned long long part[2][8];
+  __shared__ unsigned int pick;
+  if (block_failed(st)) return;
+  unsigned char *ws = A.ws0 + (int64_t)fi * A.wss;
+  const unsigned int *h0 = c.hist2, *h1 = (const unsigned int *)(ws + A.W.hist2b);
+  const unsigned char *l0 = c.len2, *l1 = ws + A.W.len2b;
+  const int nsym = A.nsym2;
+  unsigned long long b0 = 0, b1 = 0;
+  for (int s = threadIdx.x; s < nsym; s += blockDim.x) {
+    b0 += (unsigned long long)h0[s] * l0[s];
+    b1 += (unsigned long long)h1[s] * l1[s];
+  }
+  for (int o = 16; o; o >>= 1) {
+    b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+    b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    part[0][threadIdx.x >> 5] = b0;
+    part[1][threadIdx.x >> 5] = b1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long z = 0, l = 0;
+    for (int w = 0; w < 8; w++) { z += part[0][w]; l += part[1][w]; }
+    const unsigned long long vbits = A.dtype == MCC_F64 ? 64 : 32;
+    z += 32ull * h0[0] + vbits * h0[nsym - 1];
+    l += 32ull * h1[0] + vbits * h1[nsym - 1] + 8ull * kModelBytes;
+    pick = l < z ? 1u : 0u;
+    st->pick = pick;
+  }
+  __syncthreads();
+  const unsigned char *ls = pick ? l1 : l0;
+  for (int s = threadIdx.x; s < nsym; s += blockDim.x) c.out[A.F.lens2 + s] = ls[s];
 }
 
 size_t codebook_smem(int nsym) {
@@ -741,7 +827,7 @@ struct GroupArgs {
 __global__ void __launch_bounds__(256) k_group_len(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
-  const Ctx c = ctx_of(A, blockIdx.y);
+  const Ctx c = ctx_of(A, blockIdx.y, true);
   const Status *st = c.st;
   const GroupArgs a{c.sym1, c.sym2, c.len1, c.len2, A.pv.n_g, A.pv.n_v, A.ng1, A.ng2, A.C1, A.C2,
                     A.nsym1, A.nsym2, (unsigned short *)(c.out + A.F.ltab1),
@@ -871,7 +957,9 @@ __global__ void __launch_bounds__(160) k_scan(const __grid_constant__ CompArgs A
   const unsigned long long t = warp_exclusive_scan(src[w], cnt[w], (unsigned int *)(o + dst[w]));
   if ((threadIdx.x & 31) == 0) tot[w] = t;
   __syncthreads();
-  const unsigned char *model = A.model[blockIdx.x];
+  const int mode = A.mode[blockIdx.x];
+  const unsigned char *model =
+      mode == MCC_PRED_LEARNED || (mode == MCC_PRED_AUTO && st->pick) ? A.model[blockIdx.x] : nullptr;
   __shared__ unsigned long long model_at;  // stream offset of the model section, 0 = none
   if (threadIdx.x == 0) {
     model_at = 0;
@@ -958,7 +1046,7 @@ struct PackArgs {
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
-  const Ctx c = ctx_of(A, blockIdx.y);
+  const Ctx c = ctx_of(A, blockIdx.y, true);
   const Status *st = c.st;
   const PackArgs a{c.sym1, c.sym2, c.code1, c.code2, c.len1, c.len2, c.val1, c.val2, c.x,
                    A.pv.n_g, A.pv.n_v, A.ng1, A.ng2, A.C1, A.C2, A.nsym1, A.nsym2,
@@ -1071,8 +1159,10 @@ mcc_status check_params(const mcc_params *p) {
   if (p->R1 < 4 || p->R1 > kMaxR || p->R2 < 4 || p->R2 > kMaxR) return MCC_ERR_UNSUPPORTED;
   if (p->C1 < 1 || p->C1 > kMaxC || p->C2 < 1 || p->C2 > kMaxC) return MCC_ERR_UNSUPPORTED;
   if (p->lmax < 1 || p->lmax > kMaxLen) return MCC_ERR_UNSUPPORTED;
-  if (p->predictor != MCC_PRED_ZERO && p->predictor != MCC_PRED_LEARNED) return MCC_ERR_INVALID_ARG;
-  if (p->predictor == MCC_PRED_LEARNED && (!p->d_model || ((uintptr_t)p->d_model & 3)))
+  if (p->predictor != MCC_PRED_ZERO && p->predictor != MCC_PRED_LEARNED &&
+      p->predictor != MCC_PRED_AUTO)
+    return MCC_ERR_INVALID_ARG;
+  if (p->predictor != MCC_PRED_ZERO && (!p->d_model || ((uintptr_t)p->d_model & 3)))
     return MCC_ERR_INVALID_ARG;
   return MCC_OK;
 }
@@ -1101,6 +1191,11 @@ CompressWs compress_ws_layout(const PlanView &pv, const mcc_params *p) {
   w.pe = take(4 * kParts * (size_t)(ng1 + ng2));
   w.pr = take(4 * kParts * (size_t)(ng1 + ng2));
   w.p = take(4 * (size_t)pv.n_v);
+  w.hist2b = take(4 * 2 * (size_t)p->R2);
+  w.code2b = take(4 * 2 * (size_t)p->R2);
+  w.len2b = take(2 * (size_t)p->R2);
+  w.sym2b = take(2 * (size_t)pv.n_v);
+  w.val2b = take(4 * (size_t)pv.n_v);
   w.total = o;
   return w;
 }
@@ -1141,8 +1236,10 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   for (int f = 0; f < nf; f++) {
     A.x[f] = xs[f];
     A.rp[f] = RParams{ps[f].dtype, ps[f].eb_mode, ps[f].eb, ps[f].grid_fraction};
-    A.model[f] = ps[f].predictor == MCC_PRED_LEARNED ? (const unsigned char *)ps[f].d_model : nullptr;
+    A.mode[f] = (unsigned char)ps[f].predictor;
+    A.model[f] = ps[f].predictor != MCC_PRED_ZERO ? (const unsigned char *)ps[f].d_model : nullptr;
     any_model = any_model || A.model[f];
+    A.any_auto = A.any_auto || ps[f].predictor == MCC_PRED_AUTO;
   }
   const int64_t ng = A.ng1 + A.ng2;
   const int sms = num_sms();
@@ -1166,7 +1263,7 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     if (p->dtype == MCC_F64) launch_pdl(k_prequant<double>, dim3(ppf, nf), dim3(256), 0, stream, A);
     else launch_pdl(k_prequant<float>, dim3(ppf, nf), dim3(256), 0, stream, A);
   }
-  const size_t hsm1 = 4 * (size_t)A.nsym1, hsm2 = 4 * (size_t)A.nsym2;
+  const size_t hsm1 = 4 * (size_t)A.nsym1, hsm2 = 4 * (size_t)A.nsym2 * (A.any_auto ? 2 : 1);
   if (pv.dim == 2) {
     PROF_SCOPE("k_grid2d", stream);
     launch_pdl(k_grid2d<64, 16>, dim3(nf, (pv.nx + 63) / 64, (pv.ny + 15) / 16), dim3(256), hsm1,
@@ -1220,7 +1317,11 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   {
     PROF_SCOPE("k_codebook", stream);
     const size_t cbsm = codebook_smem(A.nsym1 > A.nsym2 ? A.nsym1 : A.nsym2);
-    launch_pdl(k_codebook, dim3(2, nf), dim3(1024), cbsm, stream, A);
+    launch_pdl(k_codebook, dim3(A.any_auto ? 3 : 2, nf), dim3(1024), cbsm, stream, A);
+  }
+  if (A.any_auto) {
+    PROF_SCOPE("k_choose", stream);
+    launch_pdl(k_choose, dim3(nf), dim3(256), 0, stream, A);
   }
   {
     PROF_SCOPE("k_group_len", stream);

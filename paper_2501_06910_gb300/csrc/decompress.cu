@@ -241,6 +241,7 @@ struct BitReader {
   int nb;                  // valid bits in buf
   unsigned long long wi;   // next word
   unsigned long long consumed;
+  unsigned int nxt;        // word wi, loaded one refill ahead (hides the load latency)
 
   __device__ __forceinline__ unsigned int word(unsigned long long i) const {
     return i < nwords ? __ldg(w + i) : 0u;
@@ -252,6 +253,7 @@ struct BitReader {
     wi = bit >> 5;
     buf = ((unsigned long long)word(wi) << 32) | word(wi + 1);
     wi += 2;
+    nxt = word(wi);
     const int sk = (int)(bit & 31);
     buf <<= sk;
     nb = 64 - sk;
@@ -259,9 +261,10 @@ struct BitReader {
   }
   __device__ __forceinline__ void refill() {
     if (nb < 32) {
-      buf |= (unsigned long long)word(wi) << (32 - nb);
+      buf |= (unsigned long long)nxt << (32 - nb);
       wi++;
       nb += 32;
+      nxt = word(wi);
     }
   }
 };
@@ -378,11 +381,21 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
     bool lane_bad = false;
     unsigned int used = 0, e_run = e0, r_run = r0;
     int k = 0;
+    // a group without escapes or raw values takes the vectorised emit path
+    const bool simple = e0 == e1 && (c1 || r0 == r1);
     for (int kb = 0; kb < C; kb += kDecRound) {
       const int kend = min(cnt, kb + kDecRound);
+      const int steps = min(kDecRound, C - kb);
+      const int64_t p0 = gbase + 32 * (int64_t)kb;  // first position of the round
+      if (p0 >= n) break;
       // ---- phase 1: decode this round of the lane's chunk into shared memory
-      if (fast)
-        for (int j = kb; j < kend; j++) buf[(j - kb) * 32 + lane] = s0;
+      // (buf holds the round's positions in order: p0 + 32 (k - kb) + lane)
+      if (fast) {
+        const unsigned int f2 = (unsigned int)s0 | ((unsigned int)s0 << 16);
+        const uint4 f4 = make_uint4(f2, f2, f2, f2);
+        for (int q = lane; q < steps * 4; q += 32) reinterpret_cast<uint4 *>(buf)[q] = f4;
+        __syncwarp();
+      }
       while (k < kend && !lane_bad) {
         r.refill();
         const unsigned int win = (unsigned int)(r.buf >> 32);
@@ -425,6 +438,30 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
         k++;
       }
       __syncwarp();
+      if (simple) {
+        // ---- phase 2, no escapes or raw values: values in position order,
+        // four per 16-byte store; an escape or raw symbol here is corrupt
+        const int64_t nvalid = min((int64_t)32 * steps, n - p0);
+        const int bad_lo = -R, bad_hi = R - 1;
+        for (int q = lane; 4 * q < nvalid; q += 32) {
+          const uint2 s4 = reinterpret_cast<const uint2 *>(buf)[q];
+          const int v0 = (int)(s4.x & 0xFFFFu) - R, v1 = (int)(s4.x >> 16) - R;
+          const int v2 = (int)(s4.y & 0xFFFFu) - R, v3 = (int)(s4.y >> 16) - R;
+          if (4 * q + 3 < nvalid) {
+            lane_bad |= v0 == bad_lo || v0 == bad_hi || v1 == bad_lo || v1 == bad_hi ||
+                        v2 == bad_lo || v2 == bad_hi || v3 == bad_lo || v3 == bad_hi;
+            *reinterpret_cast<int4 *>(dst + p0 + 4 * q) = make_int4(v0, v1, v2, v3);
+          } else {
+            const int vv[4] = {v0, v1, v2, v3};
+            for (int e = 0; e < 4 && 4 * q + e < nvalid; e++) {
+              lane_bad |= vv[e] == bad_lo || vv[e] == bad_hi;
+              dst[p0 + 4 * q + e] = vv[e];
+            }
+          }
+        }
+        __syncwarp();
+        continue;
+      }
       // ---- phase 2: emit 32 consecutive positions per step
       for (int kk = kb; kk < kb + kDecRound && kk < C; kk++) {
         const int64_t p0 = gbase + 32 * (int64_t)kk;

@@ -8,7 +8,7 @@ namespace mcc {
 // Compression workspace (byte offsets; the status block sits at 0).
 struct CompressWs {
   size_t hist1, hist2, code1, code2, len1, len2, Q, q1, sym1, sym2, val1, val2, gw, ge, gr, pb, pe,
-      pr, p, total;
+      pr, p, hist2b, code2b, len2b, sym2b, val2b, total;  // *b: the learned side of auto
 };
 
 // Decode tables of one component: first-level table on kLutBits bits

@@ -154,3 +154,66 @@ def test_static_decompress_of_learned_stream():
     out = torch.empty(op.n_v, dtype=torch.float64, device="cuda")
     mcc.decompress_static(gp, st, s.size, out)
     assert np.array_equal(out.cpu().numpy(), oracle.decompress(op, s))
+
+
+# --------------------------------------------------------------------------- #
+# automatic choice between the plain and the learned predictor
+# --------------------------------------------------------------------------- #
+def _convex_case():
+    if "convex" not in _cache:
+        import gpu_helpers as G
+        c, e = synth.mesh2d_jittered(nside=200, seed=33)
+        _cache["convex"] = (c, e, oracle.Plan(c, e, (33, 29)), G.plan(c, e, (33, 29)))
+    return _cache["convex"]
+
+
+@pytest.mark.parametrize("which", ["zero", "random", "convex"])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_auto_choice_bit_exact(which, dtype):
+    import gpu_helpers as G
+    from test_oracle_mlp_pins import _convex_model
+    from mlp_models import blank
+    c, e, op, gp = _convex_case()
+    eb = 2e-6
+    s2 = 2 * (0.5 * eb) * (1 - 2.0 ** -20)
+    if which == "convex":
+        x = c[:, 0] ** 2 + c[:, 1] ** 2
+        m = _convex_model((op.grid.h[0] ** 2 / s2, op.grid.h[1] ** 2 / s2))
+    else:
+        x = 1e-3 * synth.field_bumps_noise(c, seed=14)
+        m = blank(2) if which == "zero" else random_model(2, 15)
+    x = x.astype(dtype)
+    blob = pack(m)
+    kw = dict(eb=eb, eb_mode="abs")
+    want = oracle.compress(op, x, model=blob, auto=True, **kw)
+    got = G.compress(gp, x, model=_dev(blob), auto=True, **kw)
+    assert np.array_equal(got, want)
+    learned = bool(int(want[20:24].view(np.uint32)[0]) & 2)
+    assert learned == (which == "convex")
+    assert np.array_equal(G.decompress(gp, got, dtype), oracle.decompress(op, want))
+
+
+def test_auto_in_a_mixed_batch():
+    import gpu_helpers as G
+    import paper_2501_06910_gb300 as mcc
+    from test_oracle_mlp_pins import _convex_model
+    c, e, op, gp = _convex_case()
+    eb = 2e-6
+    s2 = 2 * (0.5 * eb) * (1 - 2.0 ** -20)
+    blob = pack(_convex_model((op.grid.h[0] ** 2 / s2, op.grid.h[1] ** 2 / s2)))
+    fields = [c[:, 0] ** 2 + c[:, 1] ** 2, 1e-3 * synth.field_bumps_noise(c, seed=3),
+              c[:, 0] ** 2 + 0.5 * c[:, 1] ** 2, 1e-3 * synth.field_bumps_noise(c, seed=4)]
+    modes = [dict(model=_dev(blob), auto=True), dict(model=_dev(blob), auto=True), {},
+             dict(model=_dev(blob))]
+    okw = [dict(model=blob, auto=True), dict(model=blob, auto=True), {}, dict(model=blob)]
+    prms = [G.params(np.float64, eb=eb, eb_mode="abs", **m) for m in modes]
+    xs = [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in fields]
+    slot = (max(mcc.compress_bound(gp, p) for p in prms) + 7) // 8 * 8
+    ws1 = gp.workspace(prms[0])
+    wsb = torch.zeros(ws1.numel() * 4, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(slot * 4, dtype=torch.uint8, device="cuda")
+    sizes = mcc.compress_batch(gp, xs, prms, wsb, out, slot)
+    for i in range(4):
+        got = out[i * slot: i * slot + sizes[i]].cpu().numpy()
+        want = oracle.compress(op, fields[i], eb=eb, eb_mode="abs", **okw[i])
+        assert np.array_equal(got, want), i
