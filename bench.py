@@ -21,6 +21,7 @@ the sum over ranks of the input bytes divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -417,8 +418,13 @@ def main():
         achieved = alg.get(dom, 0) / (per_kernel[dom]["ms_per_launch"] * 1e-3) / 1e9
         traffic = None
         tfile = os.path.join(ROOT, "profiles", "dram_traffic.json")
-        if os.path.exists(tfile):
-            traffic = json.load(open(tfile)).get(dom)
+        if os.path.exists(tfile):  # counters count only while the kernel is unchanged
+            ent = json.load(open(tfile)).get(dom)
+            if isinstance(ent, dict):
+                src = os.path.join(ROOT, "paper_2501_06910_gb300", "csrc", ent["source"])
+                if os.path.exists(src) and \
+                        hashlib.sha1(open(src, "rb").read()).hexdigest() == ent["sha1"]:
+                    traffic = ent["bytes"]
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
                     "peak_source": "measured" if peaks else "fallback"}
