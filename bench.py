@@ -187,6 +187,180 @@ def cpu_baseline(wl, eb, budget_s=12.0):
                       f"{t_total:.1f} s, plan excluded"}
 
 
+def time_replays(fn, flush, steps, warmup, stream):
+    """fn captured in one CUDA graph; mean ms of `steps` replays, each after an
+    L2 flush and bracketed by events on the launch stream."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    for _ in range(warmup):
+        flush.fill_(1)
+        g.replay()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k, (a, b) in enumerate(ev):
+        flush.fill_(k & 0xFF)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    del g
+    return ms
+
+
+def learned_line(args, dev, flush, stream):
+    """The learned residual predictor on the 3D annulus (8M vertices, 256^3
+    grid): trained on the GPU on 16 seeds of vortex + noise fields, evaluated
+    on 2 unseen seeds at rel 1e-4 against the plain predictor (auto choice
+    per field)."""
+    import torch
+    import paper_2501_06910_gb300 as mcc
+    from synth import torchgen
+    t0 = time.perf_counter()
+    coords, cells = synth.mesh3d_annulus()
+    cd = torch.from_numpy(coords).to(dev)
+    plan = mcc.plan_create(cd, torch.from_numpy(cells).to(dev), (256, 256, 256))
+    del cells
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    eb = 1e-4
+    base = dict(dtype=mcc.F64, eb=eb, grid_fraction=0.5)
+    train = [torchgen.field_vortex(cd, seed=1000 + i) for i in range(16)]
+    cfg = mcc.train_cfg_default()
+    t0 = time.perf_counter()
+    model, losses = mcc.model_train(plan, train, mcc.params_default(**base), cfg)
+    t_train = time.perf_counter() - t0
+    del train
+    res = {"workload": "3d-annulus-8M-tets39M-grid256^3, vortex + 4-octave noise, FP64, "
+                       "train seeds 1000-1015, eval seeds 2000-2001, rel 1e-4",
+           "train_s": t_train, "train_steps": cfg.steps, "train_batch": cfg.batch,
+           "samples_per_field": int(cfg.samples_per_field),
+           "loss_first_100": float(np.mean(losses[:100])),
+           "loss_last_100": float(np.mean(losses[-100:])), "setup_s": t_setup}
+    n = coords.shape[0]
+    out = {}
+    for label, prm in (("plain", mcc.params_default(**base)),
+                       ("learned", mcc.params_default(model=model, auto=True, **base))):
+        cws, dws = mcc.workspace_size(plan, prm)
+        wsc = torch.empty(cws, dtype=torch.uint8, device=dev)
+        wsd = torch.empty(dws, dtype=torch.uint8, device=dev)
+        cap = mcc.compress_bound(plan, prm)
+        buf = torch.empty(cap, dtype=torch.uint8, device=dev)
+        sizes, mss, chosen = [], [], []
+        for seed in (2000, 2001):
+            x = torchgen.field_vortex(cd, seed=seed)
+            y = torch.empty_like(x)
+            size = mcc.compress(plan, x, prm, wsc, buf)
+            mcc.decompress(plan, buf, size, y, wsd)
+            tau = eb * float(x.max() - x.min())
+            if not float((y - x).abs().max()) <= tau:
+                raise SystemExit(f"learned line: bound violated ({label})")
+            chosen.append("learned" if int(buf[20].item()) & 2 else "plain")
+            sizes.append(size)
+
+            def step():
+                mcc.compress(plan, x, prm, wsc, buf, sync=False)
+                mcc.decompress(plan, buf, cap, y, wsd, sync=False)
+
+            mss.append(time_replays(step, flush, max(5, args.steps // 4), args.warmup, stream))
+        out[label] = {"compression_ratio": 2 * n * 8 / sum(sizes), "stream_bytes": sizes,
+                      "ms_per_field": statistics.mean(mss),
+                      "GBps": n * 8 / (statistics.mean(mss) * 1e-3) / 1e9,
+                      "chosen": chosen}
+        del wsc, wsd, buf
+    res.update(out)
+    res["ratio_gain"] = out["learned"]["compression_ratio"] / out["plain"]["compression_ratio"]
+    plan.close()
+    return res
+
+
+def batched_c4_line(args, dev, flush, stream):
+    """Many variables x timesteps on one mesh: 1M-vertex 2D mesh, 4 variables
+    x 64 timesteps of advected Gaussian bumps (FP64), per-variable rel bounds
+    1e-6, 1e-4, 1e-3, 1e-2; R and C per variable from the autotuner; every
+    variable's 64 fields in one batched compress + decompress chain, all four
+    in one CUDA graph; against the same fields one call at a time."""
+    import torch
+    import paper_2501_06910_gb300 as mcc
+    from paper_2501_06910_gb300 import autotune
+    from synth import torchgen
+    coords, cells = synth.mesh2d_jittered(nside=1000, seed=41)
+    cd = torch.from_numpy(coords).to(dev)
+    plan = mcc.plan_create(cd, torch.from_numpy(cells).to(dev), (1024, 1024))
+    del cells
+    nvars, nsteps = 4, 64
+    ebs = [1e-6, 1e-4, 1e-3, 1e-2]
+    fields = [[None] * nsteps for _ in range(nvars)]
+    for v, t, f in torchgen.fields_advected(cd, nvars=nvars, nsteps=nsteps, seed=8):
+        fields[v][t] = f
+    n = coords.shape[0]
+    tuned, tables, prms = [], [], []
+    for v in range(nvars):
+        best, table = autotune.tune(plan, fields[v][0], dict(dtype=mcc.F64, eb=ebs[v]))
+        tuned.append(best)
+        tables.append(table)
+        prms.append(mcc.params_default(**best))
+    slots, outs, wscs, wsds, ys = [], [], [], [], []
+    for v in range(nvars):
+        cws, dws = mcc.workspace_size(plan, prms[v])
+        slot = (mcc.compress_bound(plan, prms[v]) + 7) // 8 * 8
+        slots.append(slot)
+        outs.append(torch.empty(slot * nsteps, dtype=torch.uint8, device=dev))
+        wscs.append(torch.empty(cws * nsteps, dtype=torch.uint8, device=dev))
+        wsds.append(torch.empty(dws * nsteps, dtype=torch.uint8, device=dev))
+        ys.append([torch.empty_like(fields[v][0]) for _ in range(nsteps)])
+    sizes = []
+    for v in range(nvars):
+        sz = mcc.compress_batch(plan, fields[v], [prms[v]] * nsteps, wscs[v], outs[v], slots[v])
+        mcc.decompress_batch(plan, outs[v], slots[v], sz, ys[v], wsds[v])
+        for t in (0, nsteps - 1):
+            x = fields[v][t]
+            if not float((ys[v][t] - x).abs().max()) <= ebs[v] * float(x.max() - x.min()):
+                raise SystemExit("batched c4 line: bound violated")
+        sizes.append(sz)
+
+    def bstep():
+        for v in range(nvars):
+            mcc.compress_batch(plan, fields[v], [prms[v]] * nsteps, wscs[v], outs[v], slots[v],
+                               sync=False)
+            mcc.decompress_batch(plan, outs[v], slots[v], [slots[v]] * nsteps, ys[v], wsds[v],
+                                 sync=False)
+
+    reps = max(3, args.steps // 10)
+    bms = time_replays(bstep, flush, reps, args.warmup, stream)
+    # the same 256 fields one call at a time (the plain form), one graph
+    cws1, dws1 = mcc.workspace_size(plan, prms[0])
+    ws1c = torch.empty(max(mcc.workspace_size(plan, p)[0] for p in prms), dtype=torch.uint8,
+                       device=dev)
+    ws1d = torch.empty(max(mcc.workspace_size(plan, p)[1] for p in prms), dtype=torch.uint8,
+                       device=dev)
+
+    def sstep():
+        for v in range(nvars):
+            for t in range(nsteps):
+                o = outs[v][t * slots[v]:(t + 1) * slots[v]]
+                mcc.compress(plan, fields[v][t], prms[v], ws1c, o, sync=False)
+                mcc.decompress(plan, o, slots[v], ys[v][t], ws1d, sync=False)
+
+    sms = time_replays(sstep, flush, reps, args.warmup, stream)
+    total = nvars * nsteps * n * 8
+    res = {"workload": "2d-jittered-1M-grid1024^2, 4 vars x 64 steps advected bumps FP64, "
+                       "rel bounds 1e-6/1e-4/1e-3/1e-2",
+           "fields": nvars * nsteps, "input_bytes": total,
+           "ms_per_step": bms, "GBps": total / (bms * 1e-3) / 1e9,
+           "one_call_per_field": {"ms_per_step": sms, "GBps": total / (sms * 1e-3) / 1e9},
+           "per_var": [{"eb_rel": ebs[v], "R": tuned[v]["R1"], "C": tuned[v]["C1"],
+                        "compression_ratio": nsteps * n * 8 / sum(sizes[v]),
+                        "autotune": [list(r) for r in tables[v]]} for v in range(nvars)]}
+    plan.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,6 +375,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--preroll", type=float, default=0.5, help="seconds of untimed steps")
     ap.add_argument("--batch", type=int, default=16, help="fields per step of the batched line")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-predictor line")
+    ap.add_argument("--no-c4", action="store_true", help="skip the variables x timesteps line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -391,6 +567,12 @@ def main():
             raise SystemExit("e2e mismatch")
         e2e = statistics.mean(e2e_ms)
 
+    learned = batched_c4 = None
+    if not args.no_learned:
+        learned = learned_line(args, dev, flush, stream)
+    if not args.no_c4:
+        batched_c4 = batched_c4_line(args, dev, flush, stream)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -456,6 +638,8 @@ def main():
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": None if launches_per_step is None else int(round(launches_per_step * args.steps)),
         "batched": batched,
+        "learned": learned,
+        "batched_c4": batched_c4,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -152,7 +152,7 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
   return true;
 }
 
-__global__ void __launch_bounds__(256) k_dec_prep(const __grid_constant__ DecArgs A) {
+__global__ void __launch_bounds__(1024) k_dec_prep(const __grid_constant__ DecArgs A) {
   pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.y);
@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(256) k_dec_prep(const __grid_constant__ DecArg
   __shared__ CanonTables ct;
   __shared__ int bad;
   __shared__ __align__(16) unsigned char hdr[kHeaderBytes];
+  __shared__ unsigned int single[1 << kLutBits];
   // the header in one round trip (the stream must be at least a header long)
   const bool has_header = a.in_bytes >= kHeaderBytes;
   if (has_header && threadIdx.x < kHeaderBytes / 4)
@@ -206,27 +207,37 @@ __global__ void __launch_bounds__(256) k_dec_prep(const __grid_constant__ DecArg
     T->offset[threadIdx.x] = ct.offset[threadIdx.x];
   }
   __syncthreads();
-  // first-level table: entry = l1 | l2 << 4 | sym1 << 8 | sym2 << 20 for the
-  // one or two complete codes at the front of a kLutBits-bit window (l1 = 0:
-  // the first code is longer than the window; l2 = 0: no second code fits)
+  // first-level table: for the complete codes at the front of a kLutBits-bit
+  // window (at most four), entry = l1 | total << 4 | count << 8 |
+  // sym_j << (11 + 12 j): l1 the first code's length (0: longer than the
+  // window), total the length of all `count` codes. Built in two passes: the
+  // first code of every window (single), then chains of lookups in it.
   const int lb = I.lmax < kLutBits ? I.lmax : kLutBits;
   for (int e = threadIdx.x; e < (1 << kLutBits); e += blockDim.x) {
     unsigned int v = 0;
     for (int l = 1; l <= lb; l++) {
-      const unsigned int c = (unsigned int)e >> (kLutBits - l);
-      if (c - ct.first[l] < ct.count[l]) {
-        v = ((unsigned int)T->sorted[ct.offset[l] + c - ct.first[l]] << 8) | (unsigned int)l;
-        const unsigned int rest = ((unsigned int)e << l) & ((1u << kLutBits) - 1);
-        for (int l2 = 1; l2 <= lb && l + l2 <= kLutBits; l2++) {
-          const unsigned int c2 = rest >> (kLutBits - l2);
-          if (c2 - ct.first[l2] < ct.count[l2]) {
-            v |= ((unsigned int)T->sorted[ct.offset[l2] + c2 - ct.first[l2]] << 20) | ((unsigned int)l2 << 4);
-            break;
-          }
-        }
+      const unsigned int cw = (unsigned int)e >> (kLutBits - l);
+      if (cw - ct.first[l] < ct.count[l]) {
+        v = (unsigned int)l | ((unsigned int)T->sorted[ct.offset[l] + cw - ct.first[l]] << 8);
         break;
       }
     }
+    single[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < (1 << kLutBits); e += blockDim.x) {
+    unsigned long long v = 0;
+    int used = 0, cnt = 0;
+    while (cnt < 4) {
+      const unsigned int sv = single[((unsigned int)e << used) & ((1u << kLutBits) - 1)];
+      const int l = (int)(sv & 15);
+      if (!l || used + l > kLutBits) break;  // the window's zero padding is not code
+      v |= (unsigned long long)(sv >> 8) << (11 + 12 * cnt);
+      if (cnt == 0) v |= (unsigned long long)l;
+      used += l;
+      cnt++;
+    }
+    if (cnt) v |= ((unsigned long long)used << 4) | ((unsigned long long)cnt << 8);
     T->lut[e] = v;
   }
 }
@@ -408,16 +419,20 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
           k += z;
           continue;
         }
-        const unsigned int e = Tb.lut[win >> (32 - kLutBits)];
+        const unsigned long long e = Tb.lut[win >> (32 - kLutBits)];
         int len = (int)(e & 15), sym;
         if (len) {
-          sym = (int)((e >> 8) & 0xFFF);
-          const int l2 = (int)((e >> 4) & 15);
-          if (l2 && k + 1 < kend) {  // a second complete code in the window
-            buf[(k - kb) * 32 + lane] = (unsigned short)sym;
-            k++;
-            sym = (int)(e >> 20);
-            len += l2;
+          const int cnt = (int)((e >> 8) & 7);
+          if (cnt > 1 && k + cnt <= kend) {  // every complete code in the window
+            len = (int)((e >> 4) & 15);
+            unsigned short *bp = buf + (k - kb) * 32 + lane;
+            bp[0] = (unsigned short)((e >> 11) & 0xFFF);
+            if (cnt > 2) bp[32] = (unsigned short)((e >> 23) & 0xFFF);
+            if (cnt > 3) bp[64] = (unsigned short)((e >> 35) & 0xFFF);
+            k += cnt - 1;  // the last code is written below
+            sym = (int)((e >> (11 + 12 * (cnt - 1))) & 0xFFF);
+          } else {
+            sym = (int)((e >> 11) & 0xFFF);
           }
         } else {
           sym = -1;
@@ -656,7 +671,7 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
     return MCC_ERR_CUDA;
   {
     PROF_SCOPE("k_dec_prep", stream);
-    k_dec_prep<<<dim3(2, nf), 256, 0, stream>>>(A);
+    k_dec_prep<<<dim3(2, nf), 1024, 0, stream>>>(A);
   }
   // group counts depend on the streams' chunk sizes: size the decoder for the
   // smallest chunk and let warps stride over the groups that exist

@@ -11,11 +11,12 @@ struct CompressWs {
       pr, p, hist2b, code2b, len2b, sym2b, val2b, total;  // *b: the learned side of auto
 };
 
-// Decode tables of one component: first-level table on kLutBits bits
-// (entry = symbol << 8 | length, length 0 = longer code) and the canonical
-// (first code, count, offset) per length with the symbols in canonical order.
+// Decode tables of one component: first-level table on kLutBits bits (up to
+// four complete codes at the front of the window per entry, see k_dec_prep)
+// and the canonical (first code, count, offset) per length with the symbols
+// in canonical order.
 struct DecTab {
-  unsigned int lut[1 << kLutBits];
+  unsigned long long lut[1 << kLutBits];
   unsigned int first[kMaxLen + 2], count[kMaxLen + 2], offset[kMaxLen + 2];
   unsigned short sorted[2 * kMaxR];
 };
