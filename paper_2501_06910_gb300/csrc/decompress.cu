@@ -363,7 +363,6 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
   const int *outv = (const int *)(in + (c1 ? I.L.out1 : I.L.out2));
   const T *rawv = (const T *)(in + I.L.raw);
   int *dst = c1 ? delta : q2s;
-  const unsigned lt = (1u << lane) - 1;
   const bool fast = Tb.count[1] == 1;          // a symbol owns the code "0"
   const unsigned short s0 = Tb.sorted[0];      // (the first canonical symbol)
   unsigned short *buf = sbuf + (size_t)wid * kDecRound * 32;
@@ -453,60 +452,73 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
         k++;
       }
       __syncwarp();
-      if (simple) {
-        // ---- phase 2, no escapes or raw values: values in position order,
-        // four per 16-byte store; an escape or raw symbol here is corrupt
+      // ---- phase 2: the round's values in position order, four per lane and
+      // 16-byte store per iteration (128 positions per warp iteration);
+      // escapes and raw values take their slots from the group's prefixes
+      // plus a warp scan of the per-lane counts (skipped when the iteration
+      // has none, and for the whole round when the group has none)
+      {
         const int64_t nvalid = min((int64_t)32 * steps, n - p0);
-        const int bad_lo = -R, bad_hi = R - 1;
-        for (int q = lane; 4 * q < nvalid; q += 32) {
-          const uint2 s4 = reinterpret_cast<const uint2 *>(buf)[q];
-          const int v0 = (int)(s4.x & 0xFFFFu) - R, v1 = (int)(s4.x >> 16) - R;
-          const int v2 = (int)(s4.y & 0xFFFFu) - R, v3 = (int)(s4.y >> 16) - R;
-          if (4 * q + 3 < nvalid) {
-            lane_bad |= v0 == bad_lo || v0 == bad_hi || v1 == bad_lo || v1 == bad_hi ||
-                        v2 == bad_lo || v2 == bad_hi || v3 == bad_lo || v3 == bad_hi;
-            *reinterpret_cast<int4 *>(dst + p0 + 4 * q) = make_int4(v0, v1, v2, v3);
-          } else {
-            const int vv[4] = {v0, v1, v2, v3};
-            for (int e = 0; e < 4 && 4 * q + e < nvalid; e++) {
-              lane_bad |= vv[e] == bad_lo || vv[e] == bad_hi;
-              dst[p0 + 4 * q + e] = vv[e];
+        for (int it = 0; (int64_t)it * 128 < nvalid; it++) {
+          const int q = it * 32 + lane;
+          const int64_t t0 = 4 * (int64_t)q;
+          const int nv = t0 >= nvalid ? 0 : (int)min((int64_t)4, nvalid - t0);
+          int sy[4] = {-1, -1, -1, -1};
+          if (nv) {
+            const uint2 s4 = reinterpret_cast<const uint2 *>(buf)[q];
+            sy[0] = (int)(s4.x & 0xFFFFu);
+            sy[1] = (int)(s4.x >> 16);
+            sy[2] = (int)(s4.y & 0xFFFFu);
+            sy[3] = (int)(s4.y >> 16);
+            for (int e = nv; e < 4; e++) sy[e] = -1;
+          }
+          int v[4];
+          unsigned em = 0, rm = 0;  // this lane's escapes / raw values (bit e)
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            v[e] = sy[e] - R;
+            if (sy[e] == 0) em |= 1u << e;
+            else if (sy[e] == rawsym) {
+              if (c1) lane_bad = true;
+              else rm |= 1u << e;
             }
+          }
+          if (!simple && __any_sync(0xffffffffu, em | rm)) {
+            unsigned int ce = __popc(em), cr = __popc(rm), xe = ce, xr = cr;
+            for (int o = 1; o < 32; o <<= 1) {  // inclusive scans over the lanes
+              const unsigned int te = __shfl_up_sync(0xffffffffu, xe, o);
+              const unsigned int tr = __shfl_up_sync(0xffffffffu, xr, o);
+              if (lane >= o) { xe += te; xr += tr; }
+            }
+            unsigned int ie = e_run + xe - ce, ir = r_run + xr - cr;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              if ((em >> e) & 1) {
+                v[e] = 0;
+                if (ie < e1) v[e] = __ldg(outv + ie);
+                else lane_bad = true;
+                if (!c1 && v[e] == INT_MIN) lane_bad = true;  // never an escape value
+                ie++;
+              } else if ((rm >> e) & 1) {
+                if (ir < r1) xo[p0 + t0 + e] = rawv[ir];
+                else lane_bad = true;
+                v[e] = INT_MIN;
+                ir++;
+              }
+            }
+            e_run += __shfl_sync(0xffffffffu, xe, 31);
+            r_run += __shfl_sync(0xffffffffu, xr, 31);
+          } else if (em | rm) {
+            lane_bad = true;  // the group's tables say it has none
+          }
+          if (nv == 4) {
+            *reinterpret_cast<int4 *>(dst + p0 + t0) = make_int4(v[0], v[1], v[2], v[3]);
+          } else {
+            for (int e = 0; e < nv; e++) dst[p0 + t0 + e] = v[e];
           }
         }
         __syncwarp();
-        continue;
       }
-      // ---- phase 2: emit 32 consecutive positions per step
-      for (int kk = kb; kk < kb + kDecRound && kk < C; kk++) {
-        const int64_t p0 = gbase + 32 * (int64_t)kk;
-        if (p0 >= n) break;
-        const bool valid = kk < cnt;
-        const int sym = valid ? buf[(kk - kb) * 32 + lane] : -1;
-        const bool esc = sym == 0;
-        const bool raw = !c1 && sym == rawsym;
-        const unsigned em = __ballot_sync(0xffffffffu, esc);
-        const unsigned rm = __ballot_sync(0xffffffffu, raw);
-        int v = sym - R;
-        if (esc) {
-          const unsigned int idx = e_run + __popc(em & lt);
-          v = 0;
-          if (idx < e1) v = __ldg(outv + idx);
-          else lane_bad = true;
-          if (!c1 && v == INT_MIN) lane_bad = true;  // never an escape value
-        } else if (raw) {
-          const unsigned int idx = r_run + __popc(rm & lt);
-          if (idx < r1) xo[p0 + lane] = rawv[idx];
-          else lane_bad = true;
-          v = INT_MIN;
-        } else if (c1 && sym == rawsym) {
-          lane_bad = true;
-        }
-        e_run += __popc(em);
-        r_run += __popc(rm);
-        if (valid) dst[p0 + lane] = v;
-      }
-      __syncwarp();
     }
     if (used != lane_bits) lane_bad = true;
     if (__any_sync(0xffffffffu, lane_bad) || e_run != e1 || r_run != r1) {
