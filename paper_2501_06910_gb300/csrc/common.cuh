@@ -192,22 +192,37 @@ __device__ __forceinline__ int wsub(int a, int b) { return (int)((unsigned)a - (
 __device__ __forceinline__ int wadd(int a, int b) { return (int)((unsigned)a + (unsigned)b); }
 
 // Grid -> vertex interpolation g (bilinear / trilinear on the grid codes of
-// the vertex's cell) as acc = g - c_000 in grid bins; returns c_000.
+// the vertex's cell) as acc = g - c_000 in grid bins. corner_codes gathers the
+// cell's codes (order 000, 100, 010, 110, 001, 101, 011, 111), interp_acc
+// evaluates the interpolation on their integer differences.
 template <int DIM>
-__device__ __forceinline__ int interp_vertex(const int *__restrict__ q1, uint32_t c, float fx,
-                                             float fy, float fz, int nx, int64_t sxy, float &acc) {
-  const int c000 = __ldg(q1 + c), c100 = __ldg(q1 + c + 1);
-  const int c010 = __ldg(q1 + c + nx), c110 = __ldg(q1 + c + nx + 1);
+__device__ __forceinline__ void corner_codes(const int *__restrict__ q1, uint32_t c, int nx,
+                                             int64_t sxy, int (&k)[8]) {
+  k[0] = __ldg(q1 + c);
+  k[1] = __ldg(q1 + c + 1);
+  k[2] = __ldg(q1 + c + nx);
+  k[3] = __ldg(q1 + c + nx + 1);
+  if (DIM == 3) {
+    k[4] = __ldg(q1 + c + sxy);
+    k[5] = __ldg(q1 + c + sxy + 1);
+    k[6] = __ldg(q1 + c + sxy + nx);
+    k[7] = __ldg(q1 + c + sxy + nx + 1);
+  }
+}
+
+template <int DIM>
+__device__ __forceinline__ float interp_acc(const int (&k)[8], float fx, float fy, float fz) {
+  const int c000 = k[0], c100 = k[1], c010 = k[2], c110 = k[3];
   const int d100 = wsub(c100, c000), d010 = wsub(c010, c000);
   const int d110 = wadd(wsub(wsub(c110, c100), c010), c000);
+  float acc;
   if (DIM == 2) {
     acc = __fmul_rn(fx, __int2float_rn(d100));
     acc = __fmaf_rn(fy, __int2float_rn(d010), acc);
     const float fxy = __fmul_rn(fx, fy);
     acc = __fmaf_rn(fxy, __int2float_rn(d110), acc);
   } else {
-    const int c001 = __ldg(q1 + c + sxy), c101 = __ldg(q1 + c + sxy + 1);
-    const int c011 = __ldg(q1 + c + sxy + nx), c111 = __ldg(q1 + c + sxy + nx + 1);
+    const int c001 = k[4], c101 = k[5], c011 = k[6], c111 = k[7];
     const int d001 = wsub(c001, c000);
     const int d101 = wadd(wsub(wsub(c101, c100), c001), c000);
     const int d011 = wadd(wsub(wsub(c011, c010), c001), c000);
@@ -228,7 +243,17 @@ __device__ __forceinline__ int interp_vertex(const int *__restrict__ q1, uint32_
     acc = __fmaf_rn(fyz, __int2float_rn(d011), acc);
     acc = __fmaf_rn(fxyz, __int2float_rn(d111), acc);
   }
-  return c000;
+  return acc;
+}
+
+// returns c_000, acc = g - c_000
+template <int DIM>
+__device__ __forceinline__ int interp_vertex(const int *__restrict__ q1, uint32_t c, float fx,
+                                             float fy, float fz, int nx, int64_t sxy, float &acc) {
+  int k[8];
+  corner_codes<DIM>(q1, c, nx, sxy, k);
+  acc = interp_acc<DIM>(k, fx, fy, fz);
+  return k[0];
 }
 
 // The vertex prediction in node units, P = round(rho12 * g + pc), pc the

@@ -184,12 +184,12 @@ __global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ CompArgs
   bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (; i + 3 * stride < n; i += 4 * stride) {
-    double v[4];
+  for (; i + 7 * stride < n; i += 8 * stride) {
+    double v[8];
 #pragma unroll
-    for (int u = 0; u < 4; u++) v[u] = (double)__ldcs(x + i + u * stride);
+    for (int u = 0; u < 8; u++) v[u] = (double)__ldcs(x + i + u * stride);
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
+    for (int u = 0; u < 8; u++) {
       const unsigned long long b = value_bits(v[u]);
       bad |= ((b >> 52) & 0x7FF) == 0x7FF;
       const unsigned long long k = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
@@ -481,40 +481,59 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
   const int64_t sxy = (int64_t)pv.nx * pv.ny;
   const float *__restrict__ pcor = c.p;
   const int64_t stride = (int64_t)gridDim.y * blockDim.x;
-  const int64_t nloop = (n + stride - 1) / stride * stride;  // uniform trip count per warp
-  for (int64_t i = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i < nloop; i += stride) {
-    const bool valid = i < n;
-    int sym = 0, symb = 0;
-    if (valid) {
-      const uint32_t cl = __ldg(pv.cell + i);
-      const float fx = __fmul_rn(__uint2float_rn(__ldg(pv.frac + i)), 0x1p-15f);
-      const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + i)), 0x1p-15f);
-      const float fz = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + i)), 0x1p-15f) : 0.0f;
-      const int Qi = __ldg(Q + i);
-      float acc;
-      const int c000 = interp_vertex<DIM>(q1, cl, fx, fy, fz, nx, sxy, acc);
-      bool gfail = false;
-      if (f.guard) {  // reconstruct as the decompressor will and check |x - x'|
-        const double v = (double)__ldg(x + i);
-        const double xr = __dmul_rn(f.s2, (double)((long long)Qi + f.K));
-        const double xo = sizeof(T) == 8 ? xr : (double)__double2float_rn(xr);
-        gfail = fabs(__dsub_rn(v, xo)) > f.tau2;
-      }
-      const float pc = mode != MCC_PRED_ZERO ? __ldg(pcor + i) : 0.0f;
-      if (both) {
-        const long long P0 = rescale<false>(c000, acc, f.rho12_q, f.rho12_f);
-        const long long P1 = rescale<true>(c000, acc, f.rho12_q, f.rho12_f, pc);
-        sym = residual_symbol((long long)Qi - P0, gfail, R2, i, val2);
-        symb = residual_symbol((long long)Qi - P1, gfail, R2, i, val2b);
-        sym2b[i] = (unsigned short)symb;
-      } else {
-        const long long P = rescale<HAS_P>(c000, acc, f.rho12_q, f.rho12_f, pc);
-        sym = residual_symbol((long long)Qi - P, gfail, R2, i, val2);
-      }
-      sym2[i] = (unsigned short)sym;
+  // two vertices per thread and iteration, their gathers issued together;
+  // uniform trip count per warp
+  const int64_t nloop = (n + 2 * stride - 1) / (2 * stride) * (2 * stride);
+  for (int64_t i0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i0 < nloop; i0 += 2 * stride) {
+    int64_t iv[2] = {i0, i0 + stride};
+    bool valid[2];
+    uint32_t cl[2];
+    float fr[2][3];
+    int Qv[2];
+    int cor[2][8];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      valid[u] = iv[u] < n;
+      const int64_t i = valid[u] ? iv[u] : 0;
+      cl[u] = __ldg(pv.cell + i);
+      fr[u][0] = __fmul_rn(__uint2float_rn(__ldg(pv.frac + i)), 0x1p-15f);
+      fr[u][1] = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + i)), 0x1p-15f);
+      fr[u][2] = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + i)), 0x1p-15f) : 0.0f;
+      Qv[u] = __ldg(Q + i);
     }
-    hist_add(shist, sym, valid);
-    if (both) hist_add(shist + nsym, symb, valid);
+#pragma unroll
+    for (int u = 0; u < 2; u++) corner_codes<DIM>(q1, cl[u], nx, sxy, cor[u]);
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const int64_t i = iv[u];
+      int sym = 0, symb = 0;
+      if (valid[u]) {
+        const int Qi = Qv[u];
+        const float acc = interp_acc<DIM>(cor[u], fr[u][0], fr[u][1], fr[u][2]);
+        const int c000 = cor[u][0];
+        bool gfail = false;
+        if (f.guard) {  // reconstruct as the decompressor will and check |x - x'|
+          const double v = (double)__ldg(x + i);
+          const double xr = __dmul_rn(f.s2, (double)((long long)Qi + f.K));
+          const double xo = sizeof(T) == 8 ? xr : (double)__double2float_rn(xr);
+          gfail = fabs(__dsub_rn(v, xo)) > f.tau2;
+        }
+        const float pc = mode != MCC_PRED_ZERO ? __ldg(pcor + i) : 0.0f;
+        if (both) {
+          const long long P0 = rescale<false>(c000, acc, f.rho12_q, f.rho12_f);
+          const long long P1 = rescale<true>(c000, acc, f.rho12_q, f.rho12_f, pc);
+          sym = residual_symbol((long long)Qi - P0, gfail, R2, i, val2);
+          symb = residual_symbol((long long)Qi - P1, gfail, R2, i, val2b);
+          sym2b[i] = (unsigned short)symb;
+        } else {
+          const long long P = rescale<HAS_P>(c000, acc, f.rho12_q, f.rho12_f, pc);
+          sym = residual_symbol((long long)Qi - P, gfail, R2, i, val2);
+        }
+        sym2[i] = (unsigned short)sym;
+      }
+      hist_add(shist, sym, valid[u]);
+      if (both) hist_add(shist + nsym, symb, valid[u]);
+    }
   }
   __syncthreads();
   unsigned int *hist2b = (unsigned int *)(ws + A.W.hist2b);
@@ -1251,7 +1270,7 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   }
   if (cudaMemset2DAsync(ws0, (size_t)wss, 0, kStatusBytes, (size_t)nf, stream) != cudaSuccess)
     return MCC_ERR_CUDA;
-  const unsigned int bpf = (unsigned int)((sms * 4 + nf - 1) / nf);  // reduce blocks per field
+  const unsigned int bpf = (unsigned int)((sms * 2 + nf - 1) / nf);  // reduce blocks per field
   const unsigned int ppf = (unsigned int)((sms * 8 + nf - 1) / nf);  // prequant / node blocks per field
   {
     PROF_SCOPE("k_reduce", stream);

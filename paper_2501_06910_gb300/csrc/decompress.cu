@@ -561,15 +561,15 @@ __global__ void __launch_bounds__(256) k_scan_rows(const __grid_constant__ DecAr
 
 // Inclusive scan along an axis of length L and stride S, for columns
 // base = outer * plane + inner (inner < n_inner contiguous). Block: 32
-// consecutive columns x 8 warps, each warp scanning one segment of the axis.
-__global__ void __launch_bounds__(256) k_scan_axis(const __grid_constant__ DecArgs A, int64_t n_inner,
-                                                   int64_t n_outer, int64_t plane, int L, int64_t S) {
+// consecutive columns x 32 warps, each warp scanning one segment of the axis.
+__global__ void __launch_bounds__(1024) k_scan_axis(const __grid_constant__ DecArgs A, int64_t n_inner,
+                                                    int64_t n_outer, int64_t plane, int L, int64_t S) {
   pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.y);
   int *q = c.q1;
   const Status *st = c.st;
-  __shared__ unsigned int part[8][33];
+  __shared__ unsigned int part[32][33];
   if (*(volatile const unsigned int *)&st->err) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nblk_inner = (n_inner + 31) / 32;
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(256) k_scan_axis(const __grid_constant__ DecAr
   const int64_t inner = (blockIdx.x % nblk_inner) * 32 + lane;
   const bool valid = inner < n_inner && outer < n_outer;
   int *col = q + outer * plane + inner;
-  const int seg = (L + 7) / 8;
+  const int seg = (L + 31) / 32;
   const int t0 = w * seg, t1 = min(L, t0 + seg);
   unsigned int sum = 0;
   if (valid)
@@ -615,21 +615,35 @@ __global__ void __launch_bounds__(256, 6) k_recon(const __grid_constant__ DecArg
   const int64_t sxy = (int64_t)pv.nx * pv.ny;
   const int64_t stride = (int64_t)gridDim.y * blockDim.x;
   for (int64_t p0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; p0 < n; p0 += 2 * stride) {
+    // two vertices per iteration, their gathers issued together
+    int64_t pv2[2] = {p0, p0 + stride};
+    bool go[2];
+    int q2v[2];
+    uint32_t cl[2];
+    float fr[2][3];
+    int cor[2][8];
 #pragma unroll
     for (int u = 0; u < 2; u++) {
-      const int64_t p = p0 + u * stride;
-      if (p >= n) break;
-      const int q2 = __ldg(q2s + p);
-      if (q2 == INT_MIN) continue;  // raw value already in place
-      const uint32_t c = __ldg(pv.cell + p);
-      const float fx = __fmul_rn(__uint2float_rn(__ldg(pv.frac + p)), 0x1p-15f);
-      const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + p)), 0x1p-15f);
-      const float fz = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + p)), 0x1p-15f) : 0.0f;
+      const int64_t p = pv2[u] < n ? pv2[u] : p0;
+      q2v[u] = __ldg(q2s + p);
+      go[u] = pv2[u] < n && q2v[u] != INT_MIN;  // INT_MIN: raw value already in place
+      cl[u] = __ldg(pv.cell + p);
+      fr[u][0] = __fmul_rn(__uint2float_rn(__ldg(pv.frac + p)), 0x1p-15f);
+      fr[u][1] = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + p)), 0x1p-15f);
+      fr[u][2] = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + p)), 0x1p-15f) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; u++) corner_codes<DIM>(q1, cl[u], nx, sxy, cor[u]);
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      if (!go[u]) continue;
+      const int64_t p = pv2[u];
+      const float acc = interp_acc<DIM>(cor[u], fr[u][0], fr[u][1], fr[u][2]);
       // one code path for both stream kinds: adding p = 0 leaves the plain
       // prediction unchanged (t + 0 = t, and -0 + 0 = +0 rounds to the same 0)
       const float pc = I.use_model ? __ldg(pcor + p) : 0.0f;
-      const long long P = predict_vertex<DIM, true>(q1, c, fx, fy, fz, nx, sxy, I.rho12_q, I.rho12_f, pc);
-      xo[p] = (T)__dmul_rn(I.s2, (double)(I.K + P + (long long)q2));
+      const long long P = rescale<true>(cor[u][0], acc, I.rho12_q, I.rho12_f, pc);
+      xo[p] = (T)__dmul_rn(I.s2, (double)(I.K + P + (long long)q2v[u]));
     }
   }
 }
@@ -713,13 +727,13 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
   {  // y: columns (x, z), stride nx
     PROF_SCOPE("k_scan_axis", stream);
     const int64_t blocks = (pv.nx + 31) / 32 * (int64_t)pv.nz;
-    launch_pdl(k_scan_axis, dim3((unsigned int)blocks, nf), dim3(256), 0, stream, A, (int64_t)pv.nx,
+    launch_pdl(k_scan_axis, dim3((unsigned int)blocks, nf), dim3(1024), 0, stream, A, (int64_t)pv.nx,
                (int64_t)pv.nz, (int64_t)pv.nx * pv.ny, pv.ny, (int64_t)pv.nx);
   }
   if (pv.dim == 3) {  // z: columns (x, y), stride nx ny
     PROF_SCOPE("k_scan_axis", stream);
     const int64_t ninner = (int64_t)pv.nx * pv.ny;
-    launch_pdl(k_scan_axis, dim3((unsigned int)((ninner + 31) / 32), nf), dim3(256), 0, stream, A,
+    launch_pdl(k_scan_axis, dim3((unsigned int)((ninner + 31) / 32), nf), dim3(1024), 0, stream, A,
                ninner, (int64_t)1, (int64_t)0, pv.nz, ninner);
   }
   {  // learned corrections (the kernel returns at once for plain streams)
