@@ -118,7 +118,7 @@ struct Status {
   unsigned long long out_size;
   unsigned long long key_lo, key_hi;  // ordered keys of min / max
   unsigned int nout1, nout2, nraw;    // escape counts (atomics)
-  unsigned int pad0;
+  unsigned int groups_done;           // k_group_len completion counter
   unsigned long long w1, w2;          // bitstream words per component
   Layout L;                            // stream layout of the current call
   FieldParams f;

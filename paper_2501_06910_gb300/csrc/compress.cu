@@ -14,7 +14,8 @@
 //                (C(x2), residuals serialised 1-D, Sec. IV-B)
 //   k_codebook   canonical Huffman code books (one CTA per component)
 //   k_group_len  bit length of every lane chunk, escapes per group
-//   k_scan       group offsets, section layout, header
+//                (its last block per field: group offsets, section
+//                layout, header)
 //   k_pack       bit packing through shared memory, escape / raw values
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -843,6 +844,8 @@ struct GroupArgs {
   unsigned int *pe, *pr;          // workspace [ng1 + ng2][kParts]
 };
 
+__device__ void scan_field(const CompArgs &A, int fi);
+
 __global__ void __launch_bounds__(256) k_group_len(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
@@ -907,6 +910,17 @@ __global__ void __launch_bounds__(256) k_group_len(const __grid_constant__ CompA
       a.gr[gi] = r;
     }
   }
+  // the last block of the field to finish scans the group totals and writes
+  // the layout and header (the former k_scan)
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    last = atomicAdd(&c.st->groups_done, 1u) == (unsigned int)(a.ng1 + a.ng2) - 1u;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  scan_field(A, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -922,7 +936,7 @@ __device__ unsigned long long warp_exclusive_scan(const unsigned int *in, int64_
     unsigned int v[8];
     const int64_t i0 = base + 8 * lane;
 #pragma unroll
-    for (int j = 0; j < 8; j++) v[j] = i0 + j < n ? __ldg(in + i0 + j) : 0u;
+    for (int j = 0; j < 8; j++) v[j] = i0 + j < n ? __ldcg(in + i0 + j) : 0u;  // other blocks' writes
     unsigned int tot = 0;
 #pragma unroll
     for (int j = 0; j < 8; j++) tot += v[j];
@@ -957,10 +971,10 @@ struct ScanArgs {
 __device__ __forceinline__ void put32(unsigned char *p, uint32_t v) { *(uint32_t *)p = v; }
 __device__ __forceinline__ void put64(unsigned char *p, uint64_t v) { *(uint64_t *)p = v; }
 
-__global__ void __launch_bounds__(160) k_scan(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
-  pdl_wait();
-  const Ctx c = ctx_of(A, blockIdx.x);
+// Layout and header of field fi from the group totals; run by the last
+// k_group_len block of the field (every thread of the block calls it).
+__device__ void scan_field(const CompArgs &A, int fi) {
+  const Ctx c = ctx_of(A, fi);
   Status *st = c.st;
   const ScanArgs a{c.gw, c.ge, c.gr, A.ng1, A.ng2, c.out, A.capacity, A.F, A.dtype, A.pv.dim,
                    A.R1, A.R2, A.C1, A.C2, A.lmax, A.pv.nx, A.pv.ny, A.pv.nz, A.pv.n_v, A.pv.n_g};
@@ -969,16 +983,18 @@ __global__ void __launch_bounds__(160) k_scan(const __grid_constant__ CompArgs A
   const Layout F = a.fixed;
   unsigned char *o = a.out;
   // five independent prefixes, one warp each
-  const int w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5;  // warps 0..4 scan, the others wait
   const unsigned int *src[5] = {a.gw, a.gw + a.ng1, a.ge, a.ge + a.ng1, a.gr + a.ng1};
   const uint64_t dst[5] = {F.gtab1, F.gtab2, F.etab1, F.etab2, F.rtab2};
   const int64_t cnt[5] = {a.ng1, a.ng2, a.ng1, a.ng2, a.ng2};
-  const unsigned long long t = warp_exclusive_scan(src[w], cnt[w], (unsigned int *)(o + dst[w]));
-  if ((threadIdx.x & 31) == 0) tot[w] = t;
+  if (w < 5) {
+    const unsigned long long t = warp_exclusive_scan(src[w], cnt[w], (unsigned int *)(o + dst[w]));
+    if ((threadIdx.x & 31) == 0) tot[w] = t;
+  }
   __syncthreads();
-  const int mode = A.mode[blockIdx.x];
+  const int mode = A.mode[fi];
   const unsigned char *model =
-      mode == MCC_PRED_LEARNED || (mode == MCC_PRED_AUTO && st->pick) ? A.model[blockIdx.x] : nullptr;
+      mode == MCC_PRED_LEARNED || (mode == MCC_PRED_AUTO && st->pick) ? A.model[fi] : nullptr;
   __shared__ unsigned long long model_at;  // stream offset of the model section, 0 = none
   if (threadIdx.x == 0) {
     model_at = 0;
@@ -1345,10 +1361,6 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   {
     PROF_SCOPE("k_group_len", stream);
     launch_pdl(k_group_len, dim3((unsigned int)ng, nf), dim3(256), 0, stream, A);
-  }
-  {
-    PROF_SCOPE("k_scan", stream);
-    launch_pdl(k_scan, dim3(nf), dim3(160), 0, stream, A);
   }
   {
     PROF_SCOPE("k_pack", stream);
