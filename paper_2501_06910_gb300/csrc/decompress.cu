@@ -561,15 +561,17 @@ __global__ void __launch_bounds__(256) k_scan_rows(const __grid_constant__ DecAr
 
 // Inclusive scan along an axis of length L and stride S, for columns
 // base = outer * plane + inner (inner < n_inner contiguous). Block: 32
-// consecutive columns x 32 warps, each warp scanning one segment of the axis.
-__global__ void __launch_bounds__(1024) k_scan_axis(const __grid_constant__ DecArgs A, int64_t n_inner,
-                                                    int64_t n_outer, int64_t plane, int L, int64_t S) {
+// consecutive columns x W warps, each warp scanning one segment of the axis
+// (W = 32 when there are few column blocks, 8 otherwise).
+template <int W>
+__global__ void __launch_bounds__(32 * W) k_scan_axis(const __grid_constant__ DecArgs A, int64_t n_inner,
+                                                      int64_t n_outer, int64_t plane, int L, int64_t S) {
   pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.y);
   int *q = c.q1;
   const Status *st = c.st;
-  __shared__ unsigned int part[32][33];
+  __shared__ unsigned int part[W][33];
   if (*(volatile const unsigned int *)&st->err) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nblk_inner = (n_inner + 31) / 32;
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(1024) k_scan_axis(const __grid_constant__ DecA
   const int64_t inner = (blockIdx.x % nblk_inner) * 32 + lane;
   const bool valid = inner < n_inner && outer < n_outer;
   int *col = q + outer * plane + inner;
-  const int seg = (L + 31) / 32;
+  const int seg = (L + W - 1) / W;
   const int t0 = w * seg, t1 = min(L, t0 + seg);
   unsigned int sum = 0;
   if (valid)
@@ -724,17 +726,22 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
     const int64_t nrows = (int64_t)pv.ny * pv.nz;
     launch_pdl(k_scan_rows, dim3(nblk(nrows, 8), nf), dim3(256), 0, stream, A);
   }
-  {  // y: columns (x, z), stride nx
+  // scans along y (columns (x, z), stride nx) and, in 3D, z (columns (x, y),
+  // stride nx ny); 32 warps per column block when the blocks are few
+  auto scan_axis = [&](int64_t n_inner, int64_t n_outer, int64_t plane, int L, int64_t S) {
     PROF_SCOPE("k_scan_axis", stream);
-    const int64_t blocks = (pv.nx + 31) / 32 * (int64_t)pv.nz;
-    launch_pdl(k_scan_axis, dim3((unsigned int)blocks, nf), dim3(1024), 0, stream, A, (int64_t)pv.nx,
-               (int64_t)pv.nz, (int64_t)pv.nx * pv.ny, pv.ny, (int64_t)pv.nx);
-  }
-  if (pv.dim == 3) {  // z: columns (x, y), stride nx ny
-    PROF_SCOPE("k_scan_axis", stream);
+    const int64_t blocks = (n_inner + 31) / 32 * n_outer;
+    if (blocks < 4 * (int64_t)sms)
+      launch_pdl(k_scan_axis<32>, dim3((unsigned int)blocks, nf), dim3(1024), 0, stream, A, n_inner,
+                 n_outer, plane, L, S);
+    else
+      launch_pdl(k_scan_axis<8>, dim3((unsigned int)blocks, nf), dim3(256), 0, stream, A, n_inner,
+                 n_outer, plane, L, S);
+  };
+  scan_axis((int64_t)pv.nx, (int64_t)pv.nz, (int64_t)pv.nx * pv.ny, pv.ny, (int64_t)pv.nx);
+  if (pv.dim == 3) {
     const int64_t ninner = (int64_t)pv.nx * pv.ny;
-    launch_pdl(k_scan_axis, dim3((unsigned int)((ninner + 31) / 32), nf), dim3(1024), 0, stream, A,
-               ninner, (int64_t)1, (int64_t)0, pv.nz, ninner);
+    scan_axis(ninner, 1, 0, pv.nz, ninner);
   }
   {  // learned corrections (the kernel returns at once for plain streams)
     PROF_SCOPE("k_predict", stream);

@@ -12,9 +12,9 @@
 // the integer arithmetic of the definition.
 //
 // The activation round(a / 2^s) half up, clamped to 0..255, is taken in FP32
-// without conversions: a + 2^(s-1) is exact for s <= 23 (|a| < 2^23), the
-// scaling by 2^-s is exact, and adding 2^23 rounding down leaves floor() in
-// the low bits; for s >= 24 the result is 0. Integers of magnitude <= 256 are
+// without conversions: (a + 2^(s-1)) 2^-s is one exact fused multiply-add for
+// s <= 23 (|a| < 2^23), and adding 2^23 rounding down leaves floor() in the
+// low bits; for s >= 24 the result is 0. Integers of magnitude <= 256 are
 // exact in bf16 and their FP32 bit pattern ends in 16 zero bits, so a pair
 // packs into a bf16x2 register with one byte permutation.
 #include <cuda_runtime.h>
@@ -40,8 +40,11 @@ __device__ __forceinline__ uint32_t pack_int2(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
-__device__ __forceinline__ float act8(float a, float half, float inv) {
-  const float x = __fmul_rn(__fadd_rn(a, half), inv);
+// act(h + b, s) with bb = (b + 2^(s-1)) 2^-s precomputed: one fused
+// multiply-add gives (h + b + 2^(s-1)) 2^-s exactly (an integer below 2^24
+// times a power of two), then floor and clamp.
+__device__ __forceinline__ float act8(float h, float inv, float bb) {
+  const float x = __fmaf_rn(h, inv, bb);
   const float f = __fsub_rn(__fadd_rd(x, 0x1p23f), 0x1p23f);
   return fminf(fmaxf(f, 0.0f), 255.0f);
 }
@@ -55,7 +58,7 @@ struct SModel {
   uint16_t W1[kH][kK + 8];
   uint16_t W2[kH][kH + 8];
   uint16_t W3[8][kH + 8];  // row 0 = W3, rows 1..7 = 0
-  float b1[kH], b2[kH];
+  float bb1[kH], bb2[kH];  // (b + 2^(s-1)) 2^-s per unit
   float b3, half1, inv1, half2, inv2, out_scale, sxs;
   int ok;
 };
@@ -112,8 +115,9 @@ __device__ bool load_model(const unsigned char *blob, int dim, SModel &m) {
   for (int j = tid; j < kH; j += blockDim.x) {
     const int c1 = ((const int *)(blob + M_B1))[j], c2 = ((const int *)(blob + M_B2))[j];
     bad |= c1 < -(1 << 22) || c1 > (1 << 22) || c2 < -(1 << 22) || c2 > (1 << 22);
-    m.b1[j] = (float)c1;
-    m.b2[j] = (float)c2;
+    // |b| <= 2^22 and 2^(s-1) <= 2^22: the sums and their scaling are exact
+    m.bb1[j] = __fmul_rn(__fadd_rn((float)c1, m.half1), m.inv1);
+    m.bb2[j] = __fmul_rn(__fadd_rn((float)c2, m.half2), m.inv2);
   }
   if (bad) atomicAnd(&m.ok, 0);
   __syncthreads();
@@ -122,16 +126,16 @@ __device__ bool load_model(const unsigned char *blob, int dim, SModel &m) {
 
 // Layer output fragments (8 n-tiles of 16x8, C layout) -> activations as the
 // A fragments of the next layer (4 k-tiles of 16x16).
-__device__ __forceinline__ void act_to_frag(const float (&h)[8][4], const float *bias, float half,
-                                            float inv, int tq, uint32_t (&a)[4][4]) {
+__device__ __forceinline__ void act_to_frag(const float (&h)[8][4], const float *bb, float inv,
+                                            int tq, uint32_t (&a)[4][4]) {
 #pragma unroll
   for (int nt = 0; nt < 8; nt++) {
     const int c0 = 8 * nt + 2 * tq;
-    const float bl = bias[c0], bh = bias[c0 + 1];
-    const float v0 = act8(__fadd_rn(h[nt][0], bl), half, inv);
-    const float v1 = act8(__fadd_rn(h[nt][1], bh), half, inv);
-    const float v2 = act8(__fadd_rn(h[nt][2], bl), half, inv);
-    const float v3 = act8(__fadd_rn(h[nt][3], bh), half, inv);
+    const float bl = bb[c0], bh = bb[c0 + 1];
+    const float v0 = act8(h[nt][0], inv, bl);
+    const float v1 = act8(h[nt][1], inv, bh);
+    const float v2 = act8(h[nt][2], inv, bl);
+    const float v3 = act8(h[nt][3], inv, bh);
     a[nt >> 1][(nt & 1) ? 2 : 0] = pack_int2(v0, v1);
     a[nt >> 1][(nt & 1) ? 3 : 1] = pack_int2(v2, v3);
   }
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(256) k_predict(const __grid_constant__ PredArg
         mma_bf16(h[nt], a, b0, b1);
       }
       uint32_t a2[4][4];
-      act_to_frag(h, m.b1, m.half1, m.inv1, tq, a2);
+      act_to_frag(h, m.bb1, m.inv1, tq, a2);
 #pragma unroll
       for (int nt = 0; nt < 8; nt++) {
         h[nt][0] = h[nt][1] = h[nt][2] = h[nt][3] = 0.0f;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(256) k_predict(const __grid_constant__ PredArg
         }
       }
       uint32_t a3[4][4];
-      act_to_frag(h, m.b2, m.half2, m.inv2, tq, a3);
+      act_to_frag(h, m.bb2, m.inv2, tq, a3);
       float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int kt = 0; kt < 4; kt++) {
