@@ -263,30 +263,51 @@ __global__ void __launch_bounds__(256) k_prequant(const __grid_constant__ CompAr
 // ---------------------------------------------------------------------------
 // grid codes: x1 = f(x) on the vertex codes, rescaled to grid bins
 // ---------------------------------------------------------------------------
-template <int DIM>
-__device__ __forceinline__ int grid_code(int64_t j, const PlanView &pv, const int *__restrict__ Q,
-                                         const FieldParams &f, Status *st) {
-  const int v0 = __ldg(pv.vid + j);
-  long long a;
-  float acc = 0.0f;
-  if (v0 < 0) {
-    a = f.fill_u;
-  } else {
-    const int qa = __ldg(Q + v0);
-    a = qa;
+// Grid codes of U points at once: every point's plan entries, then every
+// vertex code, are loaded before any is used (the gathers overlap).
+template <int DIM, int U>
+__device__ __forceinline__ void grid_codes(const int64_t (&j)[U], const bool (&ok)[U],
+                                           const PlanView &pv, const int *__restrict__ Q,
+                                           const FieldParams &f, Status *st, int (&out)[U]) {
+  int v[U][DIM + 1];
+  float lf[U][DIM];
 #pragma unroll
-    for (int k = 1; k <= DIM; k++) {
-      const int dk = wsub(__ldg(Q + __ldg(pv.vid + k * pv.n_g + j)), qa);
-      const float lf = __fmul_rn(__uint2float_rn(__ldg(pv.lam + (k - 1) * pv.n_g + j)), 0x1p-15f);
-      acc = k == 1 ? __fmul_rn(__int2float_rn(dk), lf) : __fmaf_rn(__int2float_rn(dk), lf, acc);
+  for (int u = 0; u < U; u++) {
+    const int64_t jj = ok[u] ? j[u] : 0;
+#pragma unroll
+    for (int k = 0; k <= DIM; k++) v[u][k] = __ldg(pv.vid + k * pv.n_g + jj);
+#pragma unroll
+    for (int k = 0; k < DIM; k++)
+      lf[u][k] = __fmul_rn(__uint2float_rn(__ldg(pv.lam + k * pv.n_g + jj)), 0x1p-15f);
+    if (!ok[u]) v[u][0] = -1;
+  }
+  int qv[U][DIM + 1];
+#pragma unroll
+  for (int u = 0; u < U; u++)
+#pragma unroll
+    for (int k = 0; k <= DIM; k++) qv[u][k] = v[u][0] >= 0 ? __ldg(Q + v[u][k]) : 0;
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    long long a;
+    float acc = 0.0f;
+    if (v[u][0] < 0) {
+      a = f.fill_u;
+    } else {
+      const int qa = qv[u][0];
+      a = qa;
+#pragma unroll
+      for (int k = 1; k <= DIM; k++) {
+        const int dk = wsub(qv[u][k], qa);
+        acc = k == 1 ? __fmul_rn(__int2float_rn(dk), lf[u][0])
+                     : __fmaf_rn(__int2float_rn(dk), lf[u][k - 1], acc);
+      }
     }
+    const long long q = rescale(a, acc, f.rho21_q, f.rho21_f);
+    out[u] = 0;
+    if (!ok[u]) continue;
+    if (q <= -(1ll << 27) || q >= (1ll << 27)) set_error(st, MCC_ERR_RANGE);
+    else out[u] = (int)q;
   }
-  const long long q = rescale(a, acc, f.rho21_q, f.rho21_f);
-  if (q <= -(1ll << 27) || q >= (1ll << 27)) {
-    set_error(st, MCC_ERR_RANGE);
-    return 0;
-  }
-  return (int)q;
 }
 
 // Shared-memory histogram add, aggregated over lanes holding the same symbol.
@@ -319,16 +340,28 @@ __global__ void __launch_bounds__(256) k_grid2d(const __grid_constant__ CompArgs
   const FieldParams f = st->f;
   const int nx = pv.nx, ny = pv.ny;
   const int x0 = blockIdx.y * TX, y0 = blockIdx.z * TY;
-  for (int idx = threadIdx.x; idx < (TY + 1) * (TX + 1); idx += blockDim.x) {
-    const int ly = idx / (TX + 1), lx = idx - ly * (TX + 1);
-    const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-    int q = 0;
-    if (gx >= 0 && gy >= 0 && gx < nx && gy < ny) {
-      const int64_t j = gx + (int64_t)nx * gy;
-      q = grid_code<2>(j, pv, Q, f, st);
-      if (lx > 0 && ly > 0) q1[j] = q;
+  {  // the tile with its halo row and column: every thread's points at once
+    constexpr int NP = (TY + 1) * (TX + 1), U = (NP + 255) / 256;
+    int64_t j[U];
+    bool ok[U];
+    int q[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int idx = threadIdx.x + 256 * u;
+      const int ly = idx / (TX + 1), lx = idx - ly * (TX + 1);
+      const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+      ok[u] = idx < NP && gx >= 0 && gy >= 0 && gx < nx && gy < ny;
+      j[u] = gx + (int64_t)nx * gy;
     }
-    s[ly][lx] = q;
+    grid_codes<2, U>(j, ok, pv, Q, f, st, q);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int idx = threadIdx.x + 256 * u;
+      if (idx >= NP) continue;
+      const int ly = idx / (TX + 1), lx = idx - ly * (TX + 1);
+      if (ok[u] && lx > 0 && ly > 0) q1[j[u]] = q[u];
+      s[ly][lx] = q[u];
+    }
   }
   __syncthreads();
   unsigned int nesc = 0;
@@ -374,7 +407,8 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
   unsigned int *hist1 = c.hist1;
   const int txs = (A.pv.nx + TX - 1) / TX;
   extern __shared__ unsigned int shist[];
-  __shared__ int s[2][TY + 1][TX + 1];
+  // the tile with its halo plane, row and column
+  __shared__ int s[SZ + 1][TY + 1][TX + 1];
   if (block_failed(st)) return;
   const int nsym = 2 * R1;
   for (int i = threadIdx.x; i < nsym; i += blockDim.x) shist[i] = 0;
@@ -382,52 +416,61 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
   const int nx = pv.nx, ny = pv.ny, nz = pv.nz;
   const int x0 = (blockIdx.y % txs) * TX, y0 = (blockIdx.y / txs) * TY, z0 = blockIdx.z * SZ;
   const int64_t sxy = (int64_t)nx * ny;
+  constexpr int NP = (SZ + 1) * (TY + 1) * (TX + 1), U = 4;
+  constexpr int NT = TX * TY;
+  for (int base = 0; base < NP; base += U * NT) {  // U points per thread at once
+    int64_t j[U];
+    bool ok[U];
+    int q[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int idx = base + threadIdx.x + NT * u;
+      const int lz = idx / ((TY + 1) * (TX + 1)), rem = idx - lz * ((TY + 1) * (TX + 1));
+      const int ly = rem / (TX + 1), lx = rem - ly * (TX + 1);
+      const int gx = x0 - 1 + lx, gy = y0 - 1 + ly, gz = z0 - 1 + lz;
+      ok[u] = idx < NP && gx >= 0 && gy >= 0 && gz >= 0 && gx < nx && gy < ny && gz < nz;
+      j[u] = gx + (int64_t)nx * gy + sxy * gz;
+    }
+    grid_codes<3, U>(j, ok, pv, Q, f, st, q);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int idx = base + threadIdx.x + NT * u;
+      if (idx >= NP) continue;
+      const int lz = idx / ((TY + 1) * (TX + 1)), rem = idx - lz * ((TY + 1) * (TX + 1));
+      const int ly = rem / (TX + 1), lx = rem - ly * (TX + 1);
+      if (ok[u] && lx > 0 && ly > 0 && lz > 0) q1[j[u]] = q[u];
+      s[lz][ly][lx] = q[u];
+    }
+  }
+  __syncthreads();
   unsigned int nesc = 0;
-  int cur = 0;
-  for (int z = z0 - 1; z < min(z0 + SZ, nz); z++) {
-    for (int idx = threadIdx.x; idx < (TY + 1) * (TX + 1); idx += blockDim.x) {
-      const int ly = idx / (TX + 1), lx = idx - ly * (TX + 1);
-      const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-      int q = 0;
-      if (z >= 0 && gx >= 0 && gy >= 0 && gx < nx && gy < ny) {
-        const int64_t j = gx + (int64_t)nx * gy + sxy * z;
-        q = grid_code<3>(j, pv, Q, f, st);
-        if (lx > 0 && ly > 0 && z >= z0) q1[j] = q;
+  for (int idx = threadIdx.x; idx < SZ * NT; idx += NT) {
+    const int lz = idx / NT, rem = idx - lz * NT;
+    const int ly = rem / TX, lx = rem - ly * TX;
+    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+    const bool valid = gx < nx && gy < ny && gz < nz;
+    int sym = 0;
+    if (valid) {
+      const int zc = lz + 1, zp = lz;
+      int d = s[zc][ly + 1][lx + 1];
+      d = wsub(d, s[zc][ly + 1][lx]);
+      d = wsub(d, s[zc][ly][lx + 1]);
+      d = wsub(d, s[zp][ly + 1][lx + 1]);
+      d = wadd(d, s[zc][ly][lx]);
+      d = wadd(d, s[zp][ly + 1][lx]);
+      d = wadd(d, s[zp][ly][lx + 1]);
+      d = wsub(d, s[zp][ly][lx]);
+      const int64_t j = gx + (int64_t)nx * gy + sxy * gz;
+      if (d >= -(R1 - 1) && d <= R1 - 2) {
+        sym = d + R1;
+      } else {
+        sym = 0;
+        val1[j] = d;
+        nesc++;
       }
-      s[cur][ly][lx] = q;
+      sym1[j] = (unsigned short)sym;
     }
-    __syncthreads();
-    if (z >= z0) {
-      const int prv = cur ^ 1;
-      for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
-        const int ly = idx / TX, lx = idx - ly * TX;
-        const int gx = x0 + lx, gy = y0 + ly;
-        const bool valid = gx < nx && gy < ny;
-        int sym = 0;
-        if (valid) {
-          int d = s[cur][ly + 1][lx + 1];
-          d = wsub(d, s[cur][ly + 1][lx]);
-          d = wsub(d, s[cur][ly][lx + 1]);
-          d = wsub(d, s[prv][ly + 1][lx + 1]);
-          d = wadd(d, s[cur][ly][lx]);
-          d = wadd(d, s[prv][ly + 1][lx]);
-          d = wadd(d, s[prv][ly][lx + 1]);
-          d = wsub(d, s[prv][ly][lx]);
-          const int64_t j = gx + (int64_t)nx * gy + sxy * z;
-          if (d >= -(R1 - 1) && d <= R1 - 2) {
-            sym = d + R1;
-          } else {
-            sym = 0;
-            val1[j] = d;
-            nesc++;
-          }
-          sym1[j] = (unsigned short)sym;
-        }
-        hist_add(shist, sym, valid);
-      }
-    }
-    __syncthreads();
-    cur ^= 1;
+    hist_add(shist, sym, valid);
   }
   if (nesc) atomicAdd(&st->nout1, nesc);
   __syncthreads();
