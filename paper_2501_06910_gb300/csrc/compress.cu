@@ -658,10 +658,15 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
   const int tid = threadIdx.x;
   if (tid == 0) m_sh = 0;
   __syncthreads();
-  for (int s = tid; s < nsym; s += blockDim.x) {
-    cnt[s] = A.hist[s];
-    lens[s] = 0;
-    if (cnt[s]) atomicAdd(&m_sh, 1);
+  {
+    int mloc = 0;
+    for (int s = tid; s < nsym; s += blockDim.x) {
+      cnt[s] = A.hist[s];
+      lens[s] = 0;
+      mloc += cnt[s] != 0;
+    }
+    for (int o = 16; o; o >>= 1) mloc += __shfl_xor_sync(0xffffffffu, mloc, o);
+    if ((tid & 31) == 0 && mloc) atomicAdd(&m_sh, mloc);
   }
   __syncthreads();
   const int m = m_sh;
@@ -671,26 +676,45 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
   }
   while (m >= 2) {
     if (tid == 0) { kpos = 0; maxlen = 0; sa = 0; sb = 0; sc = 0; }
-    __syncthreads();
-    for (int s = tid; s < nsym; s += blockDim.x)
-      if (cnt[s]) keyA[atomicAdd(&kpos, 1)] = ((unsigned long long)cnt[s] << 32) | (unsigned)s;
-    __syncthreads();
-    // bitonic sort of the (count, symbol) keys into sk (padding sorts last)
-    int npow = 1;
-    while (npow < m) npow <<= 1;
-    for (int i = tid; i < npow; i += blockDim.x) sk[i] = i < m ? keyA[i] : ~0ull;
-    __syncthreads();
-    for (int kk = 2; kk <= npow; kk <<= 1)
-      for (int j = kk >> 1; j > 0; j >>= 1) {
-        for (int i = tid; i < npow; i += blockDim.x) {
-          const int q = i ^ j;
-          if (q > i) {
-            const unsigned long long x0 = sk[i], x1 = sk[q];
-            if ((x0 > x1) == ((i & kk) == 0)) { sk[i] = x1; sk[q] = x0; }
+    // bitonic sort of the (count, symbol) keys of all npn slots into sk:
+    // unused symbols and padding carry ~0 and sort last, so sk[0 .. m) are
+    // the used symbols in (count, symbol) order
+    if ((int)blockDim.x >= npn) {
+      // one key per thread; partners closer than 32 by warp shuffles
+      unsigned long long x = tid < nsym && cnt[tid] ? ((unsigned long long)cnt[tid] << 32) | (unsigned)tid
+                                                   : ~0ull;
+      for (int kk = 2; kk <= npn; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+          unsigned long long y;
+          if (j >= 32) {
+            if (tid < npn) sk[tid] = x;
+            __syncthreads();
+            y = tid < npn ? sk[tid ^ j] : x;
+            __syncthreads();
+          } else {
+            y = __shfl_xor_sync(0xffffffffu, x, j);
           }
+          const bool up = (tid & kk) == 0, lower = (tid & j) == 0;
+          x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
         }
-        __syncthreads();
-      }
+      if (tid < npn) sk[tid] = x;
+      __syncthreads();
+    } else {
+      for (int i = tid; i < npn; i += blockDim.x)
+        sk[i] = i < nsym && cnt[i] ? ((unsigned long long)cnt[i] << 32) | (unsigned)i : ~0ull;
+      __syncthreads();
+      for (int kk = 2; kk <= npn; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+          for (int i = tid; i < npn; i += blockDim.x) {
+            const int q = i ^ j;
+            if (q > i) {
+              const unsigned long long x0 = sk[i], x1 = sk[q];
+              if ((x0 > x1) == ((i & kk) == 0)) { sk[i] = x1; sk[q] = x0; }
+            }
+          }
+          __syncthreads();
+        }
+    }
     for (;;) {
       if (tid == 0) {
         const int a = sa, b = sb, c = sc;
@@ -709,22 +733,32 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
             // batch of leaves becomes available (a heuristic: any stopping
             // point gives the same tree)
             int aa = a, bb = b, cc = c;
+            // queue heads kept in registers: the next leaf's weight and the
+            // next internal node's (internal nodes are appended at cc)
+            unsigned long long wl = aa < m ? sk[aa] >> 32 : ~0ull;
+            unsigned long long wi = bb < cc ? Iw[bb] : ~0ull;
             for (int s = 0; s < 512 && cc < m - 1; s++) {
               int id[2];
               unsigned long long w[2];
 #pragma unroll
               for (int r = 0; r < 2; r++) {
-                const bool lf = aa < m && (bb >= cc || (sk[aa] >> 32) <= Iw[bb]);
-                if (lf) { id[r] = aa; w[r] = sk[aa] >> 32; aa++; }
-                else { id[r] = m + bb; w[r] = Iw[bb]; bb++; }
+                const bool lf = aa < m && (bb >= cc || wl <= wi);
+                if (lf) {
+                  id[r] = aa; w[r] = wl; aa++;
+                  wl = aa < m ? sk[aa] >> 32 : ~0ull;
+                } else {
+                  id[r] = m + bb; w[r] = wi; bb++;
+                  wi = bb < cc ? Iw[bb] : ~0ull;
+                }
               }
-              Iw[cc] = w[0] + w[1];
+              const unsigned long long wn = w[0] + w[1];
+              Iw[cc] = wn;
               parent[id[0]] = (unsigned short)(m + cc);
               parent[id[1]] = (unsigned short)(m + cc);
+              if (bb == cc) wi = wn;  // the new node heads an empty queue
               cc++;
               if (cc >= m - 1 || aa + kBatchMin >= m) continue;
-              const unsigned long long tn =
-                  (bb >= cc || (sk[aa] >> 32) <= Iw[bb]) ? (sk[aa] >> 32) : Iw[bb];
+              const unsigned long long tn = (bb >= cc || wl <= wi) ? wl : wi;
               if ((sk[aa + kBatchMin] >> 32) <= 2 * tn) break;
             }
             sa = aa; sb = bb; sc = cc;
@@ -763,13 +797,13 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
         Iw[c + i] = node_w(e0, m, sk, Iw) + node_w(e1, m, sk, Iw);
         parent[e0] = (unsigned short)(m + c + i);
         parent[e1] = (unsigned short)(m + c + i);
-        const int nlf = (e0 < m) + (e1 < m);
-        if (nlf) atomicAdd(&snleaf, nlf);
       }
       __syncthreads();
       if (tid == 0) {
-        sa = a + snleaf;
-        sb = b + (be - snleaf);
+        // picks 0 .. be-1 hold every leaf of the batch except an odd last one
+        const int nleaf = nl - ((nl + ni) > be && mid[be] < m ? 1 : 0);
+        sa = a + nleaf;
+        sb = b + (be - nleaf);
         sc = c + be / 2;
       }
       __syncthreads();
