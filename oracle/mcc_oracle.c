@@ -665,6 +665,10 @@ int orc_huffman_lengths(const uint64_t *count, int nsym, int lmax, uint8_t *len)
   int m = 0;
   for (int s = 0; s < nsym; s++) m += count[s] != 0;
   if (m == 0) return ORC_OK;
+  /* m codes fit in lmax bits only if m <= 2^lmax; then halving the counts
+   * ends (at worst with all counts 1, a tree of depth ceil(log2 m)) */
+  if (lmax < 1 || lmax > 32 || (lmax < 31 && (uint64_t)m > ((uint64_t)1 << lmax)))
+    return ORC_ERR_INVALID_ARG;
   if (m == 1) {
     for (int s = 0; s < nsym; s++)
       if (count[s]) len[s] = 1;
@@ -782,6 +786,8 @@ static int check_params(const orc_params *p) {
   if (p->R1 < 4 || p->R1 > 32768 || p->R2 < 4 || p->R2 > 32768) return ORC_ERR_INVALID_ARG;
   if (p->C1 < 1 || p->C1 > 2048 || p->C2 < 1 || p->C2 > 2048) return ORC_ERR_INVALID_ARG;
   if (p->lmax < 1 || p->lmax > 24) return ORC_ERR_INVALID_ARG;
+  /* every symbol of an alphabet must fit in lmax bits */
+  if (2 * p->R1 > (1 << p->lmax) || 2 * p->R2 > (1 << p->lmax)) return ORC_ERR_INVALID_ARG;
   return ORC_OK;
 }
 

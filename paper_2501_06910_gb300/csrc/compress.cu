@@ -674,7 +674,11 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
     for (int s = tid; s < nsym; s += blockDim.x)
       if (cnt[s]) lens[s] = 1;
   }
-  while (m >= 2) {
+  for (int round = 0; m >= 2; round++) {
+    if (round > 64) {  // cannot happen with 2R <= 2^lmax (checked on the host)
+      if (tid == 0) set_error(st, MCC_ERR_INVALID_ARG);
+      return;
+    }
     if (tid == 0) { kpos = 0; maxlen = 0; sa = 0; sb = 0; sc = 0; }
     // bitonic sort of the (count, symbol) keys of all npn slots into sk:
     // unused symbols and padding carry ~0 and sort last, so sk[0 .. m) are
@@ -1271,6 +1275,9 @@ mcc_status check_params(const mcc_params *p) {
   if (p->R1 < 4 || p->R1 > kMaxR || p->R2 < 4 || p->R2 > kMaxR) return MCC_ERR_UNSUPPORTED;
   if (p->C1 < 1 || p->C1 > kMaxC || p->C2 < 1 || p->C2 > kMaxC) return MCC_ERR_UNSUPPORTED;
   if (p->lmax < 1 || p->lmax > kMaxLen) return MCC_ERR_UNSUPPORTED;
+  // every symbol of an alphabet must fit in lmax bits (this also bounds the
+  // code book's count halving: all counts 1 give a tree of depth log2(2R))
+  if (2 * p->R1 > (1 << p->lmax) || 2 * p->R2 > (1 << p->lmax)) return MCC_ERR_INVALID_ARG;
   if (p->predictor != MCC_PRED_ZERO && p->predictor != MCC_PRED_LEARNED &&
       p->predictor != MCC_PRED_AUTO)
     return MCC_ERR_INVALID_ARG;

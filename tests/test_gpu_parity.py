@@ -71,6 +71,8 @@ PARAMS = [
     dict(eb_mode="abs", eb=1e-3, grid_fraction=0.5),
     dict(eb=1e-3, R1=37, R2=6, C1=7, C2=13, lmax=12),
     dict(eb=1e-5, grid_fraction=0.3, C1=256, C2=1),
+    dict(eb=1e-7, R1=2048, R2=2048, C1=256, C2=256, lmax=24),  # largest alphabet and chunks
+    dict(eb=1e-2, R1=4, R2=4, C1=1, C2=2, lmax=3),            # smallest alphabet, 3-bit limit
 ]
 
 
@@ -132,6 +134,13 @@ def test_device_errors():
     with pytest.raises(mcc.MCCError) as err:
         G.compress(gp, x, eb=-1.0)
     assert err.value.status == mcc.INVALID_ARG
+    # an alphabet of 2R symbols cannot be coded within lmax bits when
+    # 2R > 2^lmax: rejected on the host, as by the oracle
+    with pytest.raises(mcc.MCCError) as err:
+        G.compress(gp, x, R1=512, R2=512, lmax=9)
+    assert err.value.status == mcc.INVALID_ARG
+    with pytest.raises(oracle.OracleError):
+        oracle.compress(op, x, R1=512, R2=512, lmax=9)
     # the context stays usable
     s = G.compress(gp, x)
     assert np.array_equal(s, oracle.compress(op, x))

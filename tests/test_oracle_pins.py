@@ -70,6 +70,14 @@ def test_huffman_optimal_cost_random(seed):
     assert kraft == pytest.approx(1.0, abs=0)
 
 
+def test_huffman_infeasible_limit_rejected():
+    """m used symbols need m <= 2^lmax; the halving loop would never end."""
+    with pytest.raises(oracle.OracleError):
+        oracle.huffman_lengths(np.ones(9, dtype=np.uint64), lmax=3)
+    ln = oracle.huffman_lengths(np.ones(8, dtype=np.uint64), lmax=3)
+    assert list(ln) == [3] * 8
+
+
 def test_huffman_length_limit_fibonacci():
     fib = [1, 1]
     while len(fib) < 26:
@@ -363,6 +371,10 @@ def test_errors_and_corruption(plan2d):
     with pytest.raises(oracle.OracleError) as e:
         oracle.compress(plan, x, eb=1e-12)
     assert e.value.status == oracle.RANGE
+    # 2R symbols need 2R <= 2^lmax; otherwise no length-limited code exists
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.compress(plan, x, R1=512, R2=512, lmax=9)
+    assert e.value.status == oracle.INVALID_ARG
     s = oracle.compress(plan, x)
     for cut in (0, 100, s.size - 1):
         with pytest.raises(oracle.OracleError) as e:
