@@ -36,7 +36,12 @@
 
 #define HEADER_BYTES 384u
 #define MAGIC 0x3143434Du /* bytes 'M' 'C' 'C' '1' */
-#define VERSION 1u
+#define VERSION 2u
+/* Lane table of a group (LTAB_BYTES): u16 base, then one u8 per lane; lane l
+ * occupies base + delta_l bits. base = max(min lane bits, max lane bits -
+ * 255): a lane shorter than base is padded with zero bits to base (delta 0),
+ * so every delta fits a byte. */
+#define LTAB_BYTES 34
 #define LAM_ONE 32768.0   /* u16 fixed point: value * 2^15 */
 #define TOL64 1e-12       /* barycentric tolerance of the FP64 inside test */
 #define TOL32 0.05f       /* FP32 pre-filter rejects lambda < -0.05 */
@@ -768,8 +773,9 @@ static void make_layout(int R1, int R2, int64_t ng1, int64_t ng2, uint64_t nout1
   L->etab1 = o; o += 4 * (size_t)(ng1 + 1);
   L->etab2 = o; o += 4 * (size_t)(ng2 + 1);
   L->rtab2 = o; o += 4 * (size_t)(ng2 + 1);
-  L->ltab1 = o; o += 64 * (size_t)ng1;
-  L->ltab2 = o; o += 64 * (size_t)ng2;
+  L->ltab1 = o; o += LTAB_BYTES * (size_t)ng1;
+  L->ltab2 = o; o += LTAB_BYTES * (size_t)ng2;
+  o = align_up(o, 4);
   L->out1 = o; o += 4 * (size_t)nout1;
   L->out2 = o; o += 4 * (size_t)nout2;
   o = align_up(o, 8);
@@ -804,11 +810,12 @@ size_t orc_compress_bound(const orc_grid *g, int64_t n_v, const orc_params *p) {
 
 /* Pack one component: symbols in lane-chunk order. Lane l of group g owns the
  * symbols g*32C + 32k + l (k = 0..C-1); each lane's codes are concatenated
- * MSB-first, the 32 lanes of a group follow each other without gaps, and
- * each group starts on a 32-bit word. Bit b of a group is bit 31 - b%32 of
- * its word b/32. Writes gtab (word offsets) and ltab (lane bit lengths). */
+ * MSB-first (then its padding), the 32 lanes of a group follow each other
+ * without gaps, and each group starts on a 32-bit word. Bit b of a group is
+ * bit 31 - b%32 of its word b/32. Writes gtab (word offsets) and ltab (lane
+ * table). */
 static uint64_t pack_component(const uint16_t *sym, int64_t n, int C, const uint8_t *len,
-                               const uint32_t *code, uint32_t *gtab, uint16_t *ltab,
+                               const uint32_t *code, uint32_t *gtab, uint8_t *ltab,
                                uint32_t *etab, uint32_t *rtab, uint16_t raw_sym,
                                uint32_t *words /* may be NULL: count only */) {
   int64_t G = 32 * (int64_t)C, ng = ngroups(n, C);
@@ -821,9 +828,26 @@ static uint64_t pack_component(const uint16_t *sym, int64_t n, int C, const uint
       ne += sym[p] == 0;
       nr += sym[p] == raw_sym;
     }
+    uint64_t lane_bits[32], mn = ~(uint64_t)0, mx = 0;
+    for (int l = 0; l < 32; l++) {
+      lane_bits[l] = 0;
+      for (int64_t k = 0; k < C; k++) {
+        int64_t p = g * G + 32 * k + l;
+        if (p >= n) break;
+        lane_bits[l] += len[sym[p]];
+      }
+      if (lane_bits[l] < mn) mn = lane_bits[l];
+      if (lane_bits[l] > mx) mx = lane_bits[l];
+    }
+    const uint64_t base = mx > 255 && mx - 255 > mn ? mx - 255 : mn;
+    if (ltab) {
+      ltab[(size_t)g * LTAB_BYTES] = (uint8_t)(base & 0xFF);
+      ltab[(size_t)g * LTAB_BYTES + 1] = (uint8_t)(base >> 8);
+    }
     uint64_t bit = 0;
     for (int l = 0; l < 32; l++) {
-      uint64_t lane_bits = 0;
+      const uint64_t padded = lane_bits[l] < base ? base : lane_bits[l];
+      uint64_t b0 = bit;
       for (int64_t k = 0; k < C; k++) {
         int64_t p = g * G + 32 * k + l;
         if (p >= n) break;
@@ -835,9 +859,9 @@ static uint64_t pack_component(const uint16_t *sym, int64_t n, int C, const uint
           }
           bit++;
         }
-        lane_bits += len[s];
       }
-      if (ltab) ltab[g * 32 + l] = (uint16_t)lane_bits;
+      bit = b0 + padded;  /* padding bits stay zero */
+      if (ltab) ltab[(size_t)g * LTAB_BYTES + 2 + l] = (uint8_t)(padded - base);
     }
     w += (bit + 31) / 32;
   }
@@ -1049,10 +1073,10 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     memcpy(out + L.lens1, len1, (size_t)2 * R1);
     memcpy(out + L.lens2, len2, (size_t)2 * R2);
     pack_component(sym1, ng, p->C1, len1, code1, (uint32_t *)(out + L.gtab1),
-                   (uint16_t *)(out + L.ltab1), (uint32_t *)(out + L.etab1), NULL, 0xFFFF,
+                   out + L.ltab1, (uint32_t *)(out + L.etab1), NULL, 0xFFFF,
                    (uint32_t *)(out + L.bits1));
     pack_component(sym2, n_v, p->C2, len2, code2, (uint32_t *)(out + L.gtab2),
-                   (uint16_t *)(out + L.ltab2), (uint32_t *)(out + L.etab2),
+                   out + L.ltab2, (uint32_t *)(out + L.etab2),
                    (uint32_t *)(out + L.rtab2), (uint16_t)(2 * R2 - 1), (uint32_t *)(out + L.bits2));
     /* escape values and raw values in increasing index order */
     uint64_t k1 = 0, k2 = 0, kr = 0;
@@ -1159,18 +1183,22 @@ static int unpack_component(const uint8_t *in, size_t size, const layout_t *L, i
     r.w = (const uint32_t *)(in + off_b);
     r.nwords = w1; /* a group may not read past its own words */
     uint64_t start = w0 * 32;
+    const uint8_t *lt = in + off_l + (size_t)g * LTAB_BYTES;
+    const uint64_t base = (uint64_t)lt[0] | ((uint64_t)lt[1] << 8);
     for (int l = 0; l < 32; l++) {
-      uint16_t lb;
-      memcpy(&lb, in + off_l + 2 * (size_t)(g * 32 + l), 2);
+      const uint64_t lb = base + lt[2 + l];
       r.bit = start;
       for (int64_t k = 0; k < C; k++) {
         int64_t p = g * G + 32 * k + l;
         if (p >= n) break;
         if (decode_symbol(&D, lmax, &r, &sym[p])) { free(D.sorted); return ORC_ERR_CORRUPT; }
       }
-      if (r.bit - start != lb) { free(D.sorted); return ORC_ERR_CORRUPT; }
+      /* the codes fill the lane, or a padded lane (delta 0) ends early */
+      const uint64_t used = r.bit - start;
+      if (used > lb || (used < lb && lt[2 + l] != 0)) { free(D.sorted); return ORC_ERR_CORRUPT; }
       start += lb;
     }
+    if (start > w1 * 32) { free(D.sorted); return ORC_ERR_CORRUPT; }
   }
   free(D.sorted);
   return ORC_OK;

@@ -22,7 +22,7 @@ namespace mcc {
 // stream format
 // ---------------------------------------------------------------------------
 constexpr uint32_t kMagic = 0x3143434Du;  // bytes 'M' 'C' 'C' '1'
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr uint32_t kHeaderBytes = 384;
 constexpr int kRhoBits = 40;               // bin-width ratios in 2^-40 fixed point
 constexpr double kBinShrink = 1.0 - 1.0 / 1048576.0;  // bins are 2 tau (1 - 2^-20)
@@ -32,6 +32,10 @@ constexpr int kMaxLen = 24;
 constexpr int kMaxBatch = 64;               // fields per kernel launch
 constexpr int kLutBits = 12;               // first-level decode table (two symbols per entry)
 constexpr uint32_t kModelBytes = 5736;     // learned-predictor blob
+// Lane table of a group: u16 base, then one u8 per lane; lane l occupies
+// base + delta_l bits, base = max(min lane bits, max lane bits - 255) (lanes
+// shorter than base are padded with zero bits, so every delta fits a byte).
+constexpr uint32_t kLtabBytes = 34;
 
 // header byte offsets
 enum : uint32_t {
@@ -72,8 +76,9 @@ __host__ __device__ inline Layout make_layout(int R1, int R2, int64_t ng1, int64
   L.etab1 = o; o += 4 * (uint64_t)(ng1 + 1);
   L.etab2 = o; o += 4 * (uint64_t)(ng2 + 1);
   L.rtab2 = o; o += 4 * (uint64_t)(ng2 + 1);
-  L.ltab1 = o; o += 64 * (uint64_t)ng1;
-  L.ltab2 = o; o += 64 * (uint64_t)ng2;
+  L.ltab1 = o; o += kLtabBytes * (uint64_t)ng1;
+  L.ltab2 = o; o += kLtabBytes * (uint64_t)ng2;
+  o = align_up(o, 4);
   L.out1 = o; o += 4 * nout1;
   L.out2 = o; o += 4 * nout2;
   o = align_up(o, 8);

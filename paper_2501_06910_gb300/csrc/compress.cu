@@ -919,7 +919,7 @@ struct GroupArgs {
   const unsigned char *len1, *len2;
   int64_t n1, n2, ng1, ng2;
   int C1, C2, nsym1, nsym2;
-  unsigned short *ltab1, *ltab2;  // in the output stream
+  unsigned char *ltab1, *ltab2;   // in the output stream
   unsigned int *gw, *ge, *gr;     // workspace [ng1 + ng2]
   unsigned short *pb;             // workspace [ng1 + ng2][kParts][32]
   unsigned int *pe, *pr;          // workspace [ng1 + ng2][kParts]
@@ -933,8 +933,8 @@ __global__ void __launch_bounds__(256) k_group_len(const __grid_constant__ CompA
   const Ctx c = ctx_of(A, blockIdx.y, true);
   const Status *st = c.st;
   const GroupArgs a{c.sym1, c.sym2, c.len1, c.len2, A.pv.n_g, A.pv.n_v, A.ng1, A.ng2, A.C1, A.C2,
-                    A.nsym1, A.nsym2, (unsigned short *)(c.out + A.F.ltab1),
-                    (unsigned short *)(c.out + A.F.ltab2), c.gw, c.ge, c.gr, c.pb, c.pe, c.pr};
+                    A.nsym1, A.nsym2, c.out + A.F.ltab1, c.out + A.F.ltab2, c.gw, c.ge, c.gr,
+                    c.pb, c.pe, c.pr};
   __shared__ unsigned char L[2 * kMaxR];
   __shared__ unsigned int sbits[kParts][32];
   __shared__ unsigned int sesc[kParts], sraw[kParts];
@@ -981,7 +981,21 @@ __global__ void __launch_bounds__(256) k_group_len(const __grid_constant__ CompA
     unsigned int tot = 0;
 #pragma unroll
     for (int q = 0; q < kParts; q++) tot += sbits[q][lane];
-    (c1 ? a.ltab1 : a.ltab2)[g * 32 + lane] = (unsigned short)tot;
+    // lane table: base and one-byte deltas; lanes shorter than base are
+    // padded (their padding closes their last part)
+    unsigned int mn = tot, mx = tot;
+    for (int o = 16; o; o >>= 1) {
+      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const unsigned int base = mx > 255u && mx - 255u > mn ? mx - 255u : mn;
+    const unsigned int padded = tot < base ? base : tot;
+    unsigned char *lt = (c1 ? a.ltab1 : a.ltab2) + (int64_t)g * kLtabBytes;
+    if (lane == 0) { lt[0] = (unsigned char)(base & 0xFF); lt[1] = (unsigned char)(base >> 8); }
+    lt[2 + lane] = (unsigned char)(padded - base);
+    if (padded != tot)
+      a.pb[(gi * kParts + kParts - 1) * 32 + lane] = (unsigned short)(sbits[kParts - 1][lane] + padded - tot);
+    tot = padded;
     for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if (lane == 0) {
       unsigned int e = 0, r = 0;
@@ -1187,7 +1201,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A
   const unsigned int *gtab = (const unsigned int *)(o + (c1 ? L.gtab1 : L.gtab2));
   const unsigned int *etab = (const unsigned int *)(o + (c1 ? L.etab1 : L.etab2));
   const unsigned int *rtab = (const unsigned int *)(o + L.rtab2);
-  const unsigned short *ltab = (const unsigned short *)(o + (c1 ? L.ltab1 : L.ltab2));
+  const unsigned char *ltg = o + (c1 ? L.ltab1 : L.ltab2) + (int64_t)g * kLtabBytes;
   int *outv = (int *)(o + (c1 ? L.out1 : L.out2));
   unsigned int *bits = (unsigned int *)(o + (c1 ? L.bits1 : L.bits2));
 
@@ -1199,7 +1213,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // bit offset of (part w, lane): lanes before this one, then earlier parts
-  const unsigned int lb = ltab[g * 32 + lane];
+  const unsigned int lb = ((unsigned int)ltg[0] | ((unsigned int)ltg[1] << 8)) + ltg[2 + lane];
   unsigned int incl = lb;
   for (int sft = 1; sft < 32; sft <<= 1) {
     const unsigned int t = __shfl_up_sync(0xffffffffu, incl, sft);

@@ -296,12 +296,15 @@ __device__ __forceinline__ bool group_setup(const unsigned char *in, uint64_t gt
                                            uint64_t etab_off, uint64_t ltab_off, uint64_t bits_off,
                                            unsigned long long words, unsigned long long nesc,
                                            int64_t g, BitReader &r, unsigned int &lane_bits,
-                                           unsigned int &e0, unsigned int &e1) {
+                                           unsigned int &lane_delta, unsigned int &e0,
+                                           unsigned int &e1) {
   const int lane = threadIdx.x & 31;
   const unsigned int w0 = ld32(in + gtab_off + 4 * g), w1 = ld32(in + gtab_off + 4 * (g + 1));
   e0 = ld32(in + etab_off + 4 * g);
   e1 = ld32(in + etab_off + 4 * (g + 1));
-  lane_bits = *(const unsigned short *)(in + ltab_off + 2 * (g * 32 + lane));
+  const unsigned char *lt = in + ltab_off + (uint64_t)g * kLtabBytes;
+  lane_delta = lt[2 + lane];
+  lane_bits = ((unsigned int)lt[0] | ((unsigned int)lt[1] << 8)) + lane_delta;
   unsigned int incl = lane_bits;
   for (int s = 1; s < 32; s <<= 1) {
     const unsigned int t = __shfl_up_sync(0xffffffffu, incl, s);
@@ -371,11 +374,11 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
   const int64_t wstride = nblocks * (blockDim.x >> 5);
   for (int64_t g = b0 * (blockDim.x >> 5) + wid; g < ng; g += wstride) {
     BitReader r;
-    unsigned int lane_bits, e0, e1, r0 = 0, r1 = 0;
+    unsigned int lane_bits, lane_delta, e0, e1, r0 = 0, r1 = 0;
     bool ok = c1 ? group_setup(in, I.L.gtab1, I.L.etab1, I.L.ltab1, I.L.bits1, I.w1, I.nout1, g, r,
-                               lane_bits, e0, e1)
+                               lane_bits, lane_delta, e0, e1)
                  : group_setup(in, I.L.gtab2, I.L.etab2, I.L.ltab2, I.L.bits2, I.w2, I.nout2, g, r,
-                               lane_bits, e0, e1);
+                               lane_bits, lane_delta, e0, e1);
     if (!c1) {
       r0 = ld32(in + I.L.rtab2 + 4 * g);
       r1 = ld32(in + I.L.rtab2 + 4 * (g + 1));
@@ -520,7 +523,8 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
         __syncwarp();
       }
     }
-    if (used != lane_bits) lane_bad = true;
+    // the codes fill the lane, or a padded lane (delta 0) ends early
+    if (used > lane_bits || (used < lane_bits && lane_delta != 0)) lane_bad = true;
     if (__any_sync(0xffffffffu, lane_bad) || e_run != e1 || r_run != r1) {
       if (lane == 0) set_error(st, MCC_ERR_CORRUPT);
       return;

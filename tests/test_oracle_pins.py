@@ -432,3 +432,30 @@ def test_vertex_predictor_is_multilinear_interpolation(plan2d, plan3d, which):
     P = dbg["Q"].astype(np.int64) - (sym - 512)
     assert ok.mean() > 0.9
     assert np.abs(P - rho12 * g)[ok].max() <= 0.5 + 1e-3
+
+
+def test_lane_table_padding(plan2d):
+    """Lane tables store u16 base + u8 deltas; a group whose lane lengths
+    spread over more than 255 bits pads its short lanes up to max - 255 (zero
+    bits after their codes). Half the vertices of every 32 noisy, half
+    constant, so lane lengths differ widely: the stream still decodes within
+    the bound and the table shows the clamped spread."""
+    coords, plan = plan2d
+    rng = np.random.default_rng(17)
+    i = np.arange(plan.n_v)
+    x = np.where(i % 32 < 16, rng.normal(0, 1, plan.n_v), 0.25)
+    kw = dict(eb=1e-4, eb_mode="abs", C2=64, R2=2048, lmax=24)
+    s = oracle.compress(plan, x, **kw)
+    y = oracle.decompress(plan, s)
+    assert np.abs(y - x).max() <= 0.5e-4
+    # residual lane table: after the grid's, header fields give the sizes
+    hdr32 = s[:64].view(np.uint32)
+    R1, R2, C1, C2 = (int(v) for v in hdr32[6:10])
+    ng1 = -(-plan.n_g // (32 * C1))
+    ng2 = -(-plan.n_v // (32 * C2))
+    o = 384 + 2 * R1 + 2 * R2
+    o = (o + 3) // 4 * 4 + 4 * (ng1 + 1) * 2 + 4 * (ng2 + 1) * 3
+    lt2 = s[o + 34 * ng1: o + 34 * ng1 + 34 * ng2].reshape(ng2, 34)
+    deltas = lt2[0, 2:]
+    # the longest lane sits at base + 255; the lanes padded up to base have 0
+    assert deltas.max() == 255 and (deltas == 0).sum() >= 8
