@@ -275,6 +275,38 @@ def learned_line(args, dev, flush, stream):
         del wsc, wsd, buf
     res.update(out)
     res["ratio_gain"] = out["learned"]["compression_ratio"] / out["plain"]["compression_ratio"]
+    # the 3D configuration itself: grid / residual split swept 0.2 .. 0.8,
+    # FP64 and FP32 fields (seed 6), plain predictor, rel 1e-4
+    sweep = []
+    x64 = torchgen.field_vortex(cd, seed=6)
+    for dt, xx in (("f64", x64), ("f32", x64.float())):
+        yy = torch.empty_like(xx)
+        for frac in (0.2, 0.35, 0.5, 0.65, 0.8):
+            prm = mcc.params_default(dtype=mcc.F64 if dt == "f64" else mcc.F32, eb=eb,
+                                     grid_fraction=frac)
+            cws, dws = mcc.workspace_size(plan, prm)
+            wsc = torch.empty(cws, dtype=torch.uint8, device=dev)
+            wsd = torch.empty(dws, dtype=torch.uint8, device=dev)
+            cap = mcc.compress_bound(plan, prm)
+            buf = torch.empty(cap, dtype=torch.uint8, device=dev)
+            size = mcc.compress(plan, xx, prm, wsc, buf)
+            mcc.decompress(plan, buf, size, yy, wsd)
+            tau = eb * float(xx.max() - xx.min())
+            err = float((yy.double() - xx.double()).abs().max())
+            if not err <= tau:
+                raise SystemExit(f"split sweep: bound violated ({dt}, {frac})")
+
+            def sstep(prm=prm, xx=xx, yy=yy, wsc=wsc, wsd=wsd, buf=buf, cap=cap):
+                mcc.compress(plan, xx, prm, wsc, buf, sync=False)
+                mcc.decompress(plan, buf, cap, yy, wsd, sync=False)
+
+            ms = time_replays(sstep, flush, 5, args.warmup, stream)
+            nb = xx.numel() * xx.element_size()
+            sweep.append({"dtype": dt, "grid_fraction": frac, "compression_ratio": nb / size,
+                          "ms_per_field": ms, "GBps": nb / (ms * 1e-3) / 1e9,
+                          "max_abs_err_over_tau": err / tau})
+            del wsc, wsd, buf
+    res["c3_split_sweep"] = sweep
     plan.close()
     return res
 
@@ -567,6 +599,25 @@ def main():
             raise SystemExit("e2e mismatch")
         e2e = statistics.mean(e2e_ms)
 
+    # the other bounds of the 2D graded configuration (1e-6, 1e-2): ratio and
+    # compress+decompress time of the same field
+    bounds = {}
+    for eb in (1e-6, 1e-2):
+        prm_b = mcc.params_default(dtype=mcc.F64, eb=eb, grid_fraction=0.5)
+        size_b = mcc.compress(plan, x, prm_b, wsc, out)
+        mcc.decompress(plan, out, size_b, y, wsd)
+        tau_b = eb * (float(x.max()) - float(x.min()))
+        if not float((y - x).abs().max()) <= tau_b:
+            raise SystemExit(f"bound violated at eb {eb}")
+
+        def bstep_b(prm_b=prm_b):
+            mcc.compress(plan, x, prm_b, wsc, out, sync=False)
+            mcc.decompress(plan, out, cap, y, wsd, sync=False)
+
+        ms_b = time_replays(bstep_b, flush, max(5, args.steps // 4), args.warmup, stream)
+        bounds[str(eb)] = {"compression_ratio": x_np.nbytes / size_b, "ms_per_step": ms_b,
+                           "GBps": x_np.nbytes / (ms_b * 1e-3) / 1e9}
+
     learned = batched_c4 = None
     if not args.no_learned:
         learned = learned_line(args, dev, flush, stream)
@@ -637,6 +688,7 @@ def main():
             "value": world * nbytes / (e2e * 1e-3) / 1e9, "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": None if launches_per_step is None else int(round(launches_per_step * args.steps)),
+        "other_bounds": bounds,
         "batched": batched,
         "learned": learned,
         "batched_c4": batched_c4,
