@@ -53,7 +53,8 @@ class _Params(C.Structure):
     _fields_ = [("dtype", C.c_int), ("eb_mode", C.c_int), ("eb", C.c_double),
                 ("grid_fraction", C.c_double), ("R1", C.c_int), ("R2", C.c_int),
                 ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int),
-                ("model", C.c_void_p), ("model_bytes", C.c_size_t), ("auto_select", C.c_int)]
+                ("model", C.c_void_p), ("model_bytes", C.c_size_t), ("auto_select", C.c_int),
+                ("open_loop", C.c_int)]
 
 
 class _Field(C.Structure):
@@ -185,7 +186,7 @@ DEFAULTS = dict(eb_mode="rel", eb=1e-4, grid_fraction=0.5, R1=512, R2=512, C1=12
                 lmax=24)
 
 
-def make_params(dtype, model=None, auto=False, **kw):
+def make_params(dtype, model=None, auto=False, open_loop=False, **kw):
     """Parameters; ``model`` is a learned-predictor blob (uint8 array) or None;
     ``auto`` keeps whichever predictor encodes smaller. The returned structure
     keeps a reference to the blob."""
@@ -193,6 +194,7 @@ def make_params(dtype, model=None, auto=False, **kw):
     p.update(kw)
     out = _Params()
     out.auto_select = 1 if auto else 0
+    out.open_loop = 1 if open_loop else 0
     if model is not None:
         blob = np.ascontiguousarray(model, dtype=np.uint8)
         out._blob = blob

@@ -452,6 +452,48 @@ static float vertex_interp(int dim, const int32_t *q1, int64_t nx, int64_t ny, u
   return acc;
 }
 
+/* Open loop: g on real corner values (vertex bins) in FP64, the same
+ * difference form and order as vertex_interp, products and sums rounded one
+ * at a time. */
+static double vertex_interp64(int dim, const double c[8], float fx, float fy, float fz) {
+  const double x = fx, y = fy, z = fz;
+  const double d100 = c[1] - c[0], d010 = c[2] - c[0];
+  const double d110 = ((c[3] - c[1]) - c[2]) + c[0];
+  double acc = x * d100;
+  acc = acc + y * d010;
+  if (dim == 2) {
+    const double xy = x * y;
+    acc = acc + xy * d110;
+    return c[0] + acc;
+  }
+  const double d001 = c[4] - c[0];
+  const double d101 = ((c[5] - c[1]) - c[4]) + c[0];
+  const double d011 = ((c[6] - c[2]) - c[4]) + c[0];
+  const double d111 = ((((((c[7] - c[3]) - c[5]) - c[6]) + c[1]) + c[2]) + c[4]) - c[0];
+  acc = acc + z * d001;
+  const double xy = x * y, xz = x * z, yz = y * z, xyz = xy * z;
+  acc = acc + xy * d110;
+  acc = acc + xz * d101;
+  acc = acc + yz * d011;
+  acc = acc + xyz * d111;
+  return c[0] + acc;
+}
+
+static void corner_values(int dim, const double *arr, int64_t nx, int64_t ny, uint32_t c,
+                          double out[8]) {
+  out[0] = arr[c];
+  out[1] = arr[c + 1];
+  out[2] = arr[c + nx];
+  out[3] = arr[c + nx + 1];
+  if (dim == 3) {
+    const int64_t sxy = nx * ny;
+    out[4] = arr[c + sxy];
+    out[5] = arr[c + sxy + 1];
+    out[6] = arr[c + sxy + nx];
+    out[7] = arr[c + sxy + nx + 1];
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* learned residual predictor: an integer-exact MLP                         */
 /* ------------------------------------------------------------------------ */
@@ -794,6 +836,8 @@ static int check_params(const orc_params *p) {
   if (p->lmax < 1 || p->lmax > 24) return ORC_ERR_INVALID_ARG;
   /* every symbol of an alphabet must fit in lmax bits */
   if (2 * p->R1 > (1 << p->lmax) || 2 * p->R2 > (1 << p->lmax)) return ORC_ERR_INVALID_ARG;
+  if (p->open_loop != 0 && p->open_loop != 1) return ORC_ERR_INVALID_ARG;
+  if (p->open_loop && p->model) return ORC_ERR_INVALID_ARG;  /* the predictor is closed loop */
   return ORC_OK;
 }
 
@@ -897,6 +941,8 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   int32_t *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_v);
   int32_t *q1 = (int32_t *)malloc(sizeof(int32_t) * (size_t)ng);
   int32_t *dl = (int32_t *)malloc(sizeof(int32_t) * (size_t)ng);
+  const int open = p->open_loop;
+  double *x1v = open ? (double *)malloc(sizeof(double) * (size_t)ng) : NULL;
   uint16_t *sym1 = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)ng);
   uint16_t *sym2 = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n_v);
   int32_t *val2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_v);
@@ -910,7 +956,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   uint32_t *code1 = (uint32_t *)calloc((size_t)2 * R1, 4), *code2 = (uint32_t *)calloc((size_t)2 * R2, 4);
   st = ORC_OK;
   if (!Q || !q1 || !dl || !sym1 || !sym2 || !val2 || !h1 || !h2 || !len1 || !len2 || !code1 ||
-      !code2 || !sym2b || !val2b || !h2b || !len2b) {
+      !code2 || !sym2b || !val2b || !h2b || !len2b || (open && !x1v)) {
     st = ORC_ERR_OOM;
     goto done;
   }
@@ -941,6 +987,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     int64_t q = rescale(a, acc, f.rho21_q, f.rho21_f);
     if (q <= -((int64_t)1 << 27) || q >= ((int64_t)1 << 27)) { st = ORC_ERR_RANGE; goto done; }
     q1[j] = (int32_t)q;
+    if (open) x1v[j] = (double)a + (double)acc;  /* x1 itself, in vertex bins */
   }
 
   /* 3. C(x1): Lorenzo difference and symbols */
@@ -970,6 +1017,41 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
       float fz = dim == 3 ? (float)frac[2 * n_v + i] * 0x1p-15f : 0.0f;
       int32_t cor[8];
       float acc = vertex_interp(dim, q1, nx, ny, cell[i], fx, fy, fz, cor);
+      if (open) {
+        /* Algorithm 3 as printed: x2 = x - g(x1) with the unquantised x1, its
+         * code q2 = round(x2 / s2) (vertex bins: u - K - g(x1), u = x / s2,
+         * taken as (Q - g) + (u - rint(u))); reconstruction s2 (K + q2 +
+         * g(x1')), bound tau1 + tau2, every vertex checked */
+        double c[8], cq[8];
+        corner_values(dim, x1v, nx, ny, cell[i], c);
+        const double gv = vertex_interp64(dim, c, fx, fy, fz);
+        const double rho12 = (double)f.rho12_q * 0x1p-40;
+        for (int k = 0; k < (1 << dim); k++) cq[k] = (double)cor[k] * rho12;
+        const double gq = vertex_interp64(dim, cq, fx, fy, fz);
+        double v = load_value(x, p->dtype, i);
+        const double u = v * f.inv2;
+        const double r = ((double)Q[i] - gv) + (u - rint(u));
+        const double q2d = rint(r);
+        int raw = !(fabs(q2d) < 2147483647.0);
+        const int64_t q2 = raw ? 0 : (int64_t)q2d;
+        if (!raw) {
+          const double xr = f.s2 * ((double)(f.K + q2) + gq);
+          const double xo = p->dtype == 0 ? xr : (double)(float)xr;
+          raw = !(fabs(v - xo) <= f.tau1 + f.tau2);
+        }
+        if (raw) {
+          s2[i] = (uint16_t)(2 * R2 - 1);
+          (*nr)++;
+        } else if (q2 >= -(R2 - 1) && q2 <= R2 - 2) {
+          s2[i] = (uint16_t)(q2 + R2);
+        } else {
+          s2[i] = 0;
+          v2[i] = (int32_t)q2;
+          (*no)++;
+        }
+        hh[s2[i]]++;
+        continue;
+      }
       int64_t P;
       if (um) {
         int32_t xq[MLP_K];
@@ -1041,7 +1123,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     put_u32(h + 8, HEADER_BYTES);
     put_u32(h + 12, (uint32_t)p->dtype);
     put_u32(h + 16, (uint32_t)dim);
-    put_u32(h + 20, (uint32_t)((f.guard ? 1 : 0) | (use_model ? 2 : 0)));
+    put_u32(h + 20, (uint32_t)((f.guard || open ? 1 : 0) | (use_model ? 2 : 0) | (open ? 4 : 0)));
     put_u32(h + 24, (uint32_t)R1);
     put_u32(h + 28, (uint32_t)R2);
     put_u32(h + 32, (uint32_t)p->C1);
@@ -1094,7 +1176,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   if (sym2_dbg) memcpy(sym2_dbg, sym2, sizeof(uint16_t) * (size_t)n_v);
 done:
   free(Q); free(q1); free(dl); free(sym1); free(sym2); free(val2); free(h1); free(h2);
-  free(sym2b); free(val2b); free(h2b); free(len2b);
+  free(sym2b); free(val2b); free(h2b); free(len2b); free(x1v);
   free(len1); free(len2); free(code1); free(code2);
   return st;
 }
@@ -1249,7 +1331,9 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
   const int64_t Qhi = (int64_t)get_u64(in + 200);
   if (Qhi < 0 || Qhi >= ((int64_t)1 << 29)) return ORC_ERR_CORRUPT;
   const int use_model = (flags & 2) != 0;
-  if (flags & ~3u) return ORC_ERR_CORRUPT;
+  const int open = (flags & 4) != 0;
+  if (flags & ~7u) return ORC_ERR_CORRUPT;
+  if (open && use_model) return ORC_ERR_CORRUPT;
   if (mbytes != (use_model ? MODEL_BYTES : 0)) return ORC_ERR_CORRUPT;
   layout_t L;
   make_layout(R1, R2, ngroups(ng, C1), ngroups(n_v, C2), nout1, nout2, nraw, vsz, w1, w2,
@@ -1303,6 +1387,16 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
       float fz = dim == 3 ? (float)frac[2 * n_v + i] * 0x1p-15f : 0.0f;
       int32_t cor[8];
       float acc = vertex_interp(dim, q1, nx, ny, cell[i], fx, fy, fz, cor);
+      if (open) {
+        double cq[8];
+        const double rho12 = (double)rho12_q * 0x1p-40;
+        for (int k = 0; k < (1 << dim); k++) cq[k] = (double)cor[k] * rho12;
+        const double gq = vertex_interp64(dim, cq, fx, fy, fz);
+        const double xr = s2 * ((double)(K + q2) + gq);
+        if (dtype == 0) ((double *)xout)[i] = xr;
+        else ((float *)xout)[i] = (float)xr;
+        continue;
+      }
       int64_t P;
       if (use_model) {
         int32_t xq[MLP_K];

@@ -69,6 +69,8 @@ typedef struct {
   const uint8_t *model; /* learned predictor (integer MLP blob) or NULL */
   size_t model_bytes;
   int auto_select;    /* with a model: keep the predictor whose encoding is smaller */
+  int open_loop;      /* 1: residual against g(x1) with the unquantised x1 (Algorithm 3
+                         as printed), bound tau1 + tau2; 0: against g(x1'), bound tau2 */
 } orc_params;
 
 /* Per-field scalars derived from the values (Sec. III bound split). */
