@@ -276,36 +276,40 @@ def learned_line(args, dev, flush, stream):
     res.update(out)
     res["ratio_gain"] = out["learned"]["compression_ratio"] / out["plain"]["compression_ratio"]
     # the 3D configuration itself: grid / residual split swept 0.2 .. 0.8,
-    # FP64 and FP32 fields (seed 6), plain predictor, rel 1e-4
+    # FP64 and FP32 fields (seed 6), plain predictor, rel 1e-4, closed loop
+    # (residual against the decompressed grid) and open loop (against the
+    # grid before quantisation, Algorithm 3 as printed)
     sweep = []
     x64 = torchgen.field_vortex(cd, seed=6)
-    for dt, xx in (("f64", x64), ("f32", x64.float())):
+    cases = [(dt, xx, loop, frac) for dt, xx in (("f64", x64), ("f32", x64.float()))
+             for loop in ("closed", "open") for frac in (0.2, 0.35, 0.5, 0.65, 0.8)]
+    for dt, xx, loop, frac in cases:
         yy = torch.empty_like(xx)
-        for frac in (0.2, 0.35, 0.5, 0.65, 0.8):
-            prm = mcc.params_default(dtype=mcc.F64 if dt == "f64" else mcc.F32, eb=eb,
-                                     grid_fraction=frac)
-            cws, dws = mcc.workspace_size(plan, prm)
-            wsc = torch.empty(cws, dtype=torch.uint8, device=dev)
-            wsd = torch.empty(dws, dtype=torch.uint8, device=dev)
-            cap = mcc.compress_bound(plan, prm)
-            buf = torch.empty(cap, dtype=torch.uint8, device=dev)
-            size = mcc.compress(plan, xx, prm, wsc, buf)
-            mcc.decompress(plan, buf, size, yy, wsd)
-            tau = eb * float(xx.max() - xx.min())
-            err = float((yy.double() - xx.double()).abs().max())
-            if not err <= tau:
-                raise SystemExit(f"split sweep: bound violated ({dt}, {frac})")
+        prm = mcc.params_default(dtype=mcc.F64 if dt == "f64" else mcc.F32, eb=eb,
+                                 grid_fraction=frac, open_loop=loop == "open")
+        cws, dws = mcc.workspace_size(plan, prm)
+        wsc = torch.empty(cws, dtype=torch.uint8, device=dev)
+        wsd = torch.empty(dws, dtype=torch.uint8, device=dev)
+        cap = mcc.compress_bound(plan, prm)
+        buf = torch.empty(cap, dtype=torch.uint8, device=dev)
+        size = mcc.compress(plan, xx, prm, wsc, buf)
+        mcc.decompress(plan, buf, size, yy, wsd)
+        tau = eb * float(xx.max() - xx.min())
+        err = float((yy.double() - xx.double()).abs().max())
+        if not err <= tau:
+            raise SystemExit(f"split sweep: bound violated ({dt}, {frac})")
 
-            def sstep(prm=prm, xx=xx, yy=yy, wsc=wsc, wsd=wsd, buf=buf, cap=cap):
-                mcc.compress(plan, xx, prm, wsc, buf, sync=False)
-                mcc.decompress(plan, buf, cap, yy, wsd, sync=False)
+        def sstep(prm=prm, xx=xx, yy=yy, wsc=wsc, wsd=wsd, buf=buf, cap=cap):
+            mcc.compress(plan, xx, prm, wsc, buf, sync=False)
+            mcc.decompress(plan, buf, cap, yy, wsd, sync=False)
 
-            ms = time_replays(sstep, flush, 5, args.warmup, stream)
-            nb = xx.numel() * xx.element_size()
-            sweep.append({"dtype": dt, "grid_fraction": frac, "compression_ratio": nb / size,
-                          "ms_per_field": ms, "GBps": nb / (ms * 1e-3) / 1e9,
-                          "max_abs_err_over_tau": err / tau})
-            del wsc, wsd, buf
+        ms = time_replays(sstep, flush, 5, args.warmup, stream)
+        nb = xx.numel() * xx.element_size()
+        sweep.append({"dtype": dt, "loop": loop, "grid_fraction": frac,
+                      "compression_ratio": nb / size,
+                      "ms_per_field": ms, "GBps": nb / (ms * 1e-3) / 1e9,
+                      "max_abs_err_over_tau": err / tau})
+        del wsc, wsd, buf
     res["c3_split_sweep"] = sweep
     plan.close()
     return res

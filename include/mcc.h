@@ -57,6 +57,7 @@ typedef enum {
 enum { MCC_F64 = 0, MCC_F32 = 1 };   /* value types */
 enum { MCC_ABS = 0, MCC_REL = 1 };   /* bound modes: absolute, or x (max - min) */
 enum { MCC_PRED_ZERO = 0, MCC_PRED_LEARNED = 1, MCC_PRED_AUTO = 2 };  /* residual predictor */
+enum { MCC_LOOP_CLOSED = 0, MCC_LOOP_OPEN = 1 };  /* residual against g(x1') or g(x1) */
 #define MCC_MODEL_BYTES 5736   /* learned-predictor blob */
 #define MCC_MLP_PARAMS 5313    /* float parameters of the training network */
 
@@ -104,6 +105,16 @@ typedef struct {
    * values and, for the learned one, the model; a tie keeps the plain one. */
   int predictor;
   const void *d_model;
+  /* Residual reference (Algorithm 3). MCC_LOOP_CLOSED: x2 = x - g(x1'), the
+   * interpolation of the decompressed grid, so the vertex error is the
+   * residual's alone, |x - x'| <= tau2, and tau1 only trades rate between the
+   * components. MCC_LOOP_OPEN: x2 = x - g(x1) with the grid component before
+   * quantisation, as Algorithm 3 prints it; the grid's error reaches the
+   * vertices and the bound is |x - x'| <= tau1 + tau2 <= tau (Sec. III),
+   * checked at every vertex (violators are stored raw). The vertex code is
+   * q2 = round(x / s2 - g(x1)) in FP64 and the reconstruction s2 (q2 +
+   * g(x1')). Open loop takes MCC_PRED_ZERO only. */
+  int loop;
 } mcc_params;
 
 typedef struct mcc_plan_s *mcc_plan;
@@ -117,7 +128,7 @@ typedef struct {
 } mcc_plan_info;
 
 /* Defaults: F64, REL, eb 1e-4, grid_fraction 0.5, R1 = R2 = 512,
- * C1 = C2 = 128, lmax 24, MCC_PRED_ZERO. */
+ * C1 = C2 = 128, lmax 24, MCC_PRED_ZERO, MCC_LOOP_CLOSED. */
 void mcc_params_default(mcc_params *p);
 
 /* Build the mesh -> grid mapping once per mesh (Sec. IV-B: reused across

@@ -29,6 +29,7 @@ OK, INVALID_ARG, CUDA, OOM, RANGE, CORRUPT, CAPACITY, TIMEOUT, UNSUPPORTED = ran
 F64, F32 = 0, 1
 ABS, REL = 0, 1
 PRED_ZERO, PRED_LEARNED, PRED_AUTO = 0, 1, 2
+LOOP_CLOSED, LOOP_OPEN = 0, 1
 LOSS_L2, LOSS_L1 = 0, 1
 MODEL_BYTES = 5736
 MLP_PARAMS = 5313
@@ -55,11 +56,11 @@ class _GridSpec(C.Structure):
 
 class Params(C.Structure):
     """mcc_params: dtype, eb_mode, eb, grid_fraction, R1, R2, C1, C2, lmax,
-    predictor, d_model."""
+    predictor, d_model, loop."""
     _fields_ = [("dtype", C.c_int), ("eb_mode", C.c_int), ("eb", C.c_double),
                 ("grid_fraction", C.c_double), ("R1", C.c_int), ("R2", C.c_int),
                 ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int),
-                ("predictor", C.c_int), ("d_model", C.c_void_p)]
+                ("predictor", C.c_int), ("d_model", C.c_void_p), ("loop", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -162,12 +163,15 @@ def _dptr(t: torch.Tensor):
     return C.c_void_p(t.data_ptr())
 
 
-def params_default(model=None, auto=False, **overrides) -> Params:
+def params_default(model=None, auto=False, open_loop=False, **overrides) -> Params:
     """Parameters; ``model`` (a CUDA uint8 tensor of MODEL_BYTES) selects the
-    learned predictor, or with ``auto`` the smaller of learned and plain. The
-    structure keeps a reference to the tensor."""
+    learned predictor, or with ``auto`` the smaller of learned and plain;
+    ``open_loop`` takes the residual against the unquantised grid component
+    (bound tau1 + tau2). The structure keeps a reference to the tensor."""
     p = Params()
     load().mcc_params_default(C.byref(p))
+    if open_loop:
+        p.loop = LOOP_OPEN
     if model is not None:
         if model.dtype != torch.uint8 or model.numel() != MODEL_BYTES:
             raise ValueError("model must be a uint8 tensor of MODEL_BYTES bytes")

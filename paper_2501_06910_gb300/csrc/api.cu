@@ -23,6 +23,7 @@ extern "C" void mcc_params_default(mcc_params *p) {
   p->lmax = 24;
   p->predictor = MCC_PRED_ZERO;
   p->d_model = nullptr;
+  p->loop = MCC_LOOP_CLOSED;
 }
 
 extern "C" const char *mcc_status_string(mcc_status s) {

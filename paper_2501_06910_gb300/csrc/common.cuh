@@ -46,7 +46,7 @@ enum : uint32_t {
   H_W1 = 168, H_W2 = 176, H_TOTAL = 184, H_MODEL = 192, H_QHI = 200
 };
 // header flags
-enum : uint32_t { F_GUARD = 1, F_MODEL = 2 };
+enum : uint32_t { F_GUARD = 1, F_MODEL = 2, F_OPEN = 4 };
 
 __host__ __device__ inline uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 __host__ __device__ inline int64_t ngroups(int64_t n, int C) {
@@ -249,6 +249,53 @@ __device__ __forceinline__ float interp_acc(const int (&k)[8], float fx, float f
     acc = __fmaf_rn(fxyz, __int2float_rn(d111), acc);
   }
   return acc;
+}
+
+// Open loop: g on real corner values (vertex bins) in FP64, the same
+// difference form and term order as interp_acc, every operation rounded on
+// its own (no contraction): g = c_000 + sum of weight x difference.
+template <int DIM>
+__device__ __forceinline__ double interp64(const double (&c)[8], float fx, float fy, float fz) {
+  const double x = fx, y = fy;
+  const double d100 = __dsub_rn(c[1], c[0]), d010 = __dsub_rn(c[2], c[0]);
+  const double d110 = __dadd_rn(__dsub_rn(__dsub_rn(c[3], c[1]), c[2]), c[0]);
+  double acc = __dmul_rn(x, d100);
+  acc = __dadd_rn(acc, __dmul_rn(y, d010));
+  if (DIM == 2) {
+    acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(x, y), d110));
+    return __dadd_rn(c[0], acc);
+  }
+  const double z = fz;
+  const double d001 = __dsub_rn(c[4], c[0]);
+  const double d101 = __dadd_rn(__dsub_rn(__dsub_rn(c[5], c[1]), c[4]), c[0]);
+  const double d011 = __dadd_rn(__dsub_rn(__dsub_rn(c[6], c[2]), c[4]), c[0]);
+  double d111 = __dsub_rn(c[7], c[3]);
+  d111 = __dsub_rn(d111, c[5]);
+  d111 = __dsub_rn(d111, c[6]);
+  d111 = __dadd_rn(d111, c[1]);
+  d111 = __dadd_rn(d111, c[2]);
+  d111 = __dadd_rn(d111, c[4]);
+  d111 = __dsub_rn(d111, c[0]);
+  acc = __dadd_rn(acc, __dmul_rn(z, d001));
+  const double xy = __dmul_rn(x, y), xz = __dmul_rn(x, z), yz = __dmul_rn(y, z);
+  const double xyz = __dmul_rn(xy, z);
+  acc = __dadd_rn(acc, __dmul_rn(xy, d110));
+  acc = __dadd_rn(acc, __dmul_rn(xz, d101));
+  acc = __dadd_rn(acc, __dmul_rn(yz, d011));
+  acc = __dadd_rn(acc, __dmul_rn(xyz, d111));
+  return __dadd_rn(c[0], acc);
+}
+
+// g(x1') for the open loop: the grid codes in vertex bins, q1 rho12 (rho12 =
+// rho12_q 2^-40, exact in FP64), interpolated by interp64.
+template <int DIM>
+__device__ __forceinline__ double interp64_codes(const int (&k)[8], long long rho12_q, float fx,
+                                                 float fy, float fz) {
+  const double r = __dmul_rn((double)rho12_q, 0x1p-40);
+  double c[8];
+#pragma unroll
+  for (int t = 0; t < (1 << DIM); t++) c[t] = __dmul_rn((double)k[t], r);
+  return interp64<DIM>(c, fx, fy, fz);
 }
 
 // returns c_000, acc = g - c_000

@@ -55,6 +55,7 @@ struct CompArgs {
   RParams rp[kMaxBatch];
   const unsigned char *model[kMaxBatch];  // learned-predictor blob or NULL
   unsigned char mode[kMaxBatch];          // MCC_PRED_* per field
+  unsigned char open[kMaxBatch];          // MCC_LOOP_OPEN per field
   int any_auto;
 };
 
@@ -265,10 +266,13 @@ __global__ void __launch_bounds__(256) k_prequant(const __grid_constant__ CompAr
 // ---------------------------------------------------------------------------
 // Grid codes of U points at once: every point's plan entries, then every
 // vertex code, are loaded before any is used (the gathers overlap).
+// x1 receives the grid value before quantisation (vertex bins, a + acc) for
+// the open loop.
 template <int DIM, int U>
 __device__ __forceinline__ void grid_codes(const int64_t (&j)[U], const bool (&ok)[U],
                                            const PlanView &pv, const int *__restrict__ Q,
-                                           const FieldParams &f, Status *st, int (&out)[U]) {
+                                           const FieldParams &f, Status *st, int (&out)[U],
+                                           double (&x1)[U]) {
   int v[U][DIM + 1];
   float lf[U][DIM];
 #pragma unroll
@@ -303,6 +307,7 @@ __device__ __forceinline__ void grid_codes(const int64_t (&j)[U], const bool (&o
       }
     }
     const long long q = rescale(a, acc, f.rho21_q, f.rho21_f);
+    x1[u] = __dadd_rn((double)a, (double)acc);
     out[u] = 0;
     if (!ok[u]) continue;
     if (q <= -(1ll << 27) || q >= (1ll << 27)) set_error(st, MCC_ERR_RANGE);
@@ -329,6 +334,8 @@ __global__ void __launch_bounds__(256) k_grid2d(const __grid_constant__ CompArgs
   Status *st = c.st;
   const int R1 = A.R1;
   int *__restrict__ q1 = c.q1;
+  double *__restrict__ x1v =
+      A.open[blockIdx.x] ? (double *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.x1v) : nullptr;
   unsigned short *__restrict__ sym1 = c.sym1;
   int *__restrict__ val1 = c.val1;
   unsigned int *hist1 = c.hist1;
@@ -345,6 +352,7 @@ __global__ void __launch_bounds__(256) k_grid2d(const __grid_constant__ CompArgs
     int64_t j[U];
     bool ok[U];
     int q[U];
+    double x1[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = threadIdx.x + 256 * u;
@@ -353,13 +361,16 @@ __global__ void __launch_bounds__(256) k_grid2d(const __grid_constant__ CompArgs
       ok[u] = idx < NP && gx >= 0 && gy >= 0 && gx < nx && gy < ny;
       j[u] = gx + (int64_t)nx * gy;
     }
-    grid_codes<2, U>(j, ok, pv, Q, f, st, q);
+    grid_codes<2, U>(j, ok, pv, Q, f, st, q, x1);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = threadIdx.x + 256 * u;
       if (idx >= NP) continue;
       const int ly = idx / (TX + 1), lx = idx - ly * (TX + 1);
-      if (ok[u] && lx > 0 && ly > 0) q1[j[u]] = q[u];
+      if (ok[u] && lx > 0 && ly > 0) {
+        q1[j[u]] = q[u];
+        if (x1v) x1v[j[u]] = x1[u];
+      }
       s[ly][lx] = q[u];
     }
   }
@@ -402,6 +413,8 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
   Status *st = c.st;
   const int R1 = A.R1;
   int *__restrict__ q1 = c.q1;
+  double *__restrict__ x1v =
+      A.open[blockIdx.x] ? (double *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.x1v) : nullptr;
   unsigned short *__restrict__ sym1 = c.sym1;
   int *__restrict__ val1 = c.val1;
   unsigned int *hist1 = c.hist1;
@@ -422,6 +435,7 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
     int64_t j[U];
     bool ok[U];
     int q[U];
+    double x1[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = base + threadIdx.x + NT * u;
@@ -431,14 +445,17 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
       ok[u] = idx < NP && gx >= 0 && gy >= 0 && gz >= 0 && gx < nx && gy < ny && gz < nz;
       j[u] = gx + (int64_t)nx * gy + sxy * gz;
     }
-    grid_codes<3, U>(j, ok, pv, Q, f, st, q);
+    grid_codes<3, U>(j, ok, pv, Q, f, st, q, x1);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = base + threadIdx.x + NT * u;
       if (idx >= NP) continue;
       const int lz = idx / ((TY + 1) * (TX + 1)), rem = idx - lz * ((TY + 1) * (TX + 1));
       const int ly = rem / (TX + 1), lx = rem - ly * (TX + 1);
-      if (ok[u] && lx > 0 && ly > 0 && lz > 0) q1[j[u]] = q[u];
+      if (ok[u] && lx > 0 && ly > 0 && lz > 0) {
+        q1[j[u]] = q[u];
+        if (x1v) x1v[j[u]] = x1[u];
+      }
       s[lz][ly][lx] = q[u];
     }
   }
@@ -491,11 +508,78 @@ __device__ __forceinline__ int residual_symbol(long long q2, bool guard_fail, in
   return 0;
 }
 
+// Open loop (Algorithm 3 as printed): q2 = round(x / s2 - K - g(x1)) with
+// x1 the grid values before quantisation, evaluated as (Q - g) + (u - rint(u))
+// (u = x / s2) so that both terms stay small; every vertex is reconstructed
+// as the decompressor will, s2 (K + q2 + g(x1')), and checked against
+// tau1 + tau2 after the cast to T (Sec. III); violators are stored raw.
+template <int DIM, typename T>
+__device__ __forceinline__ void node_open(const CompArgs &A, const Ctx &c, const FieldParams &f,
+                                          unsigned int *shist) {
+  const PlanView &pv = A.pv;
+  const T *__restrict__ x = (const T *)c.x;
+  const int *__restrict__ Q = c.Q;
+  const int *__restrict__ q1 = c.q1;
+  const double *__restrict__ x1v =
+      (const double *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.x1v);
+  unsigned short *__restrict__ sym2 = c.sym2;
+  const int R2 = A.R2;
+  const int64_t n = pv.n_v;
+  const int nx = pv.nx;
+  const int64_t sxy = (int64_t)pv.nx * pv.ny;
+  const double tau = __dadd_rn(f.tau1, f.tau2);
+  const int64_t stride = (int64_t)gridDim.y * blockDim.x;
+  const int64_t nloop = (n + stride - 1) / stride * stride;  // uniform trip count per warp
+  for (int64_t i0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i0 < nloop; i0 += stride) {
+    const bool valid = i0 < n;
+    int sym = 0;
+    if (valid) {
+      const int64_t i = i0;
+      const uint32_t cl = __ldg(pv.cell + i);
+      const float fx = __fmul_rn(__uint2float_rn(__ldg(pv.frac + i)), 0x1p-15f);
+      const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + i)), 0x1p-15f);
+      const float fz =
+          DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + i)), 0x1p-15f) : 0.0f;
+      double cv[8];
+      cv[0] = __ldg(x1v + cl);
+      cv[1] = __ldg(x1v + cl + 1);
+      cv[2] = __ldg(x1v + cl + nx);
+      cv[3] = __ldg(x1v + cl + nx + 1);
+      if (DIM == 3) {
+        cv[4] = __ldg(x1v + cl + sxy);
+        cv[5] = __ldg(x1v + cl + sxy + 1);
+        cv[6] = __ldg(x1v + cl + sxy + nx);
+        cv[7] = __ldg(x1v + cl + sxy + nx + 1);
+      }
+      int cor[8];
+      corner_codes<DIM>(q1, cl, nx, sxy, cor);
+      const double v = (double)__ldg(x + i);
+      const int Qi = __ldg(Q + i);
+      const double gv = interp64<DIM>(cv, fx, fy, fz);
+      const double gq = interp64_codes<DIM>(cor, f.rho12_q, fx, fy, fz);
+      const double u = __dmul_rn(v, f.inv2);
+      const double r = __dadd_rn(__dsub_rn((double)Qi, gv), __dsub_rn(u, rint(u)));
+      const double q2d = rint(r);
+      bool raw = !(fabs(q2d) < 2147483647.0);
+      const long long q2 = raw ? 0 : (long long)q2d;
+      if (!raw) {
+        const double xr = __dmul_rn(f.s2, __dadd_rn((double)(f.K + q2), gq));
+        const double xo = sizeof(T) == 8 ? xr : (double)__double2float_rn(xr);
+        raw = !(fabs(__dsub_rn(v, xo)) <= tau);
+      }
+      sym = residual_symbol(q2, raw, R2, i, c.val2);
+      sym2[i] = (unsigned short)sym;
+    }
+    hist_add(shist, sym, valid);
+  }
+}
+
 // HAS_P: some field of the launch uses the learned predictor (mode 1) or
 // chooses between both (mode 2: the plain side goes to sym2 / hist2, the
 // learned side to sym2b / hist2b; the histograms share the dynamic shared
-// memory, the learned one at offset 2 R2).
-template <int DIM, typename T, bool HAS_P>
+// memory, the learned one at offset 2 R2). OPEN: some field of the launch
+// takes the open loop (node_open; such a field has no model).
+template <int DIM, typename T, bool HAS_P, bool OPEN>
 __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
@@ -528,6 +612,8 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
   // two vertices per thread and iteration, their gathers issued together;
   // uniform trip count per warp
   const int64_t nloop = (n + 2 * stride - 1) / (2 * stride) * (2 * stride);
+  if (OPEN && A.open[fi]) node_open<DIM, T>(A, c, f, shist);
+  else
   for (int64_t i0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i0 < nloop; i0 += 2 * stride) {
     int64_t iv[2] = {i0, i0 + stride};
     bool valid[2];
@@ -1111,7 +1197,9 @@ __device__ void scan_field(const CompArgs &A, int fi) {
       put32(o + H_HBYTES, kHeaderBytes);
       put32(o + H_DTYPE, (uint32_t)a.dtype);
       put32(o + H_DIM, (uint32_t)a.dim);
-      put32(o + H_FLAGS, (f.guard ? F_GUARD : 0u) | (model ? F_MODEL : 0u));
+      const bool open = A.open[fi] != 0;
+      put32(o + H_FLAGS, (f.guard || open ? F_GUARD : 0u) | (model ? F_MODEL : 0u) |
+                             (open ? F_OPEN : 0u));
       put32(o + H_R1, (uint32_t)a.R1);
       put32(o + H_R2, (uint32_t)a.R2);
       put32(o + H_C1, (uint32_t)a.C1);
@@ -1297,6 +1385,8 @@ mcc_status check_params(const mcc_params *p) {
     return MCC_ERR_INVALID_ARG;
   if (p->predictor != MCC_PRED_ZERO && (!p->d_model || ((uintptr_t)p->d_model & 3)))
     return MCC_ERR_INVALID_ARG;
+  if (p->loop != MCC_LOOP_CLOSED && p->loop != MCC_LOOP_OPEN) return MCC_ERR_INVALID_ARG;
+  if (p->loop == MCC_LOOP_OPEN && p->predictor != MCC_PRED_ZERO) return MCC_ERR_INVALID_ARG;
   return MCC_OK;
 }
 
@@ -1329,6 +1419,7 @@ CompressWs compress_ws_layout(const PlanView &pv, const mcc_params *p) {
   w.len2b = take(2 * (size_t)p->R2);
   w.sym2b = take(2 * (size_t)pv.n_v);
   w.val2b = take(4 * (size_t)pv.n_v);
+  w.x1v = take(8 * (size_t)pv.n_g);
   w.total = o;
   return w;
 }
@@ -1365,8 +1456,10 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   A.ng2 = ngroups(pv.n_v, p->C2);
   A.F = make_layout(p->R1, p->R2, A.ng1, A.ng2, 0, 0, 0, 8, 0, 0);
   if (!front_only && capacity < A.F.out1) return MCC_ERR_CAPACITY;
-  bool any_model = false;
+  bool any_model = false, any_open = false;
   for (int f = 0; f < nf; f++) {
+    A.open[f] = ps[f].loop == MCC_LOOP_OPEN ? 1 : 0;
+    any_open = any_open || A.open[f];
     A.x[f] = xs[f];
     A.rp[f] = RParams{ps[f].dtype, ps[f].eb_mode, ps[f].eb, ps[f].grid_fraction};
     A.mode[f] = (unsigned char)ps[f].predictor;
@@ -1429,23 +1522,23 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     PROF_SCOPE("k_node", stream);
     const unsigned int chunks = ppf < 65535 ? ppf : 65535;
     const dim3 grid(nf, chunks);
+    // variants: plain, with the learned predictor, with open-loop fields
+    // (which also serves learned fields of the same batch)
+#define MCC_NODE(D, T)                                                                  \
+  do {                                                                                  \
+    if (any_open) launch_pdl(k_node<D, T, true, true>, grid, dim3(256), hsm2, stream, A); \
+    else if (any_model)                                                                 \
+      launch_pdl(k_node<D, T, true, false>, grid, dim3(256), hsm2, stream, A);          \
+    else launch_pdl(k_node<D, T, false, false>, grid, dim3(256), hsm2, stream, A);      \
+  } while (0)
     if (pv.dim == 2) {
-      if (p->dtype == MCC_F64) {
-        if (any_model) launch_pdl(k_node<2, double, true>, grid, dim3(256), hsm2, stream, A);
-        else launch_pdl(k_node<2, double, false>, grid, dim3(256), hsm2, stream, A);
-      } else {
-        if (any_model) launch_pdl(k_node<2, float, true>, grid, dim3(256), hsm2, stream, A);
-        else launch_pdl(k_node<2, float, false>, grid, dim3(256), hsm2, stream, A);
-      }
+      if (p->dtype == MCC_F64) MCC_NODE(2, double);
+      else MCC_NODE(2, float);
     } else {
-      if (p->dtype == MCC_F64) {
-        if (any_model) launch_pdl(k_node<3, double, true>, grid, dim3(256), hsm2, stream, A);
-        else launch_pdl(k_node<3, double, false>, grid, dim3(256), hsm2, stream, A);
-      } else {
-        if (any_model) launch_pdl(k_node<3, float, true>, grid, dim3(256), hsm2, stream, A);
-        else launch_pdl(k_node<3, float, false>, grid, dim3(256), hsm2, stream, A);
-      }
+      if (p->dtype == MCC_F64) MCC_NODE(3, double);
+      else MCC_NODE(3, float);
     }
+#undef MCC_NODE
   }
   {
     PROF_SCOPE("k_codebook", stream);

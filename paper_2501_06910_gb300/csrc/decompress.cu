@@ -103,8 +103,10 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
   I.dtype = (int)ld32(h + H_DTYPE);
   I.dim = (int)ld32(h + H_DIM);
   const uint32_t flags = ld32(h + H_FLAGS);
-  if (flags & ~(F_GUARD | F_MODEL)) return false;
+  if (flags & ~(F_GUARD | F_MODEL | F_OPEN)) return false;
   I.use_model = (flags & F_MODEL) ? 1 : 0;
+  I.open = (flags & F_OPEN) ? 1 : 0;
+  if (I.open && I.use_model) return false;
   if (ld64(h + H_MODEL) != (I.use_model ? kModelBytes : 0)) return false;
   I.Qhi = (long long)ld64(h + H_QHI);
   if (I.Qhi < 0 || I.Qhi >= (1ll << 29)) return false;
@@ -600,8 +602,33 @@ __global__ void __launch_bounds__(32 * W) k_scan_axis(const __grid_constant__ De
 }
 
 // ---------------------------------------------------------------------------
-// k_recon: x' = s2 (K + P + q2) at every vertex, P = round(rho12 g(x1'))
+// k_recon: x' = s2 (K + P + q2) at every vertex, P = round(rho12 g(x1'));
+// open-loop streams: x' = s2 ((K + q2) + g(x1')) in FP64 (recon_open)
 // ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__device__ __forceinline__ void recon_open(const DecArgs &A, double s2, long long K,
+                                           long long rho12_q, const int *q1, const int *q2s,
+                                           T *xo) {
+  const PlanView &pv = A.pv;
+  const int64_t n = pv.n_v;
+  const int nx = pv.nx;
+  const int64_t sxy = (int64_t)pv.nx * pv.ny;
+  const int64_t stride = (int64_t)gridDim.y * blockDim.x;
+  for (int64_t p = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; p < n; p += stride) {
+    const int q2 = __ldg(q2s + p);
+    if (q2 == INT_MIN) continue;  // raw value already in place
+    const uint32_t cl = __ldg(pv.cell + p);
+    const float fx = __fmul_rn(__uint2float_rn(__ldg(pv.frac + p)), 0x1p-15f);
+    const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + p)), 0x1p-15f);
+    const float fz =
+        DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + p)), 0x1p-15f) : 0.0f;
+    int cor[8];
+    corner_codes<DIM>(q1, cl, nx, sxy, cor);
+    const double gq = interp64_codes<DIM>(cor, rho12_q, fx, fy, fz);
+    xo[p] = (T)__dmul_rn(s2, __dadd_rn((double)(K + (long long)q2), gq));
+  }
+}
+
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256, 6) k_recon(const __grid_constant__ DecArgs A) {
   pdl_trigger();
@@ -616,6 +643,10 @@ __global__ void __launch_bounds__(256, 6) k_recon(const __grid_constant__ DecArg
   const Status *st = c.st;
   if (*(volatile const unsigned int *)&st->err) return;
   const DecInfo I = *info;
+  if (I.open) {
+    recon_open<DIM, T>(A, I.s2, I.K, I.rho12_q, q1, q2s, xo);
+    return;
+  }
   const int64_t n = pv.n_v;
   const int nx = pv.nx;
   const int64_t sxy = (int64_t)pv.nx * pv.ny;

@@ -749,6 +749,7 @@ extern "C" mcc_status mcc_model_train(mcc_plan plan, int n, const void *const *d
   mcc_params pz = *p;  // the residuals of the method without a predictor
   pz.predictor = MCC_PRED_ZERO;
   pz.d_model = nullptr;
+  pz.loop = MCC_LOOP_CLOSED;  // the predictor serves the closed loop only
   const PlanView pv = mcc_plan_view(plan);
   const TrainWs T = train_ws_layout(pv, &pz, cfg, n);
   if (workspace_bytes < T.total) return MCC_ERR_CAPACITY;

@@ -8,7 +8,8 @@ namespace mcc {
 // Compression workspace (byte offsets; the status block sits at 0).
 struct CompressWs {
   size_t hist1, hist2, code1, code2, len1, len2, Q, q1, sym1, sym2, val1, val2, gw, ge, gr, pb, pe,
-      pr, p, hist2b, code2b, len2b, sym2b, val2b, total;  // *b: the learned side of auto
+      pr, p, hist2b, code2b, len2b, sym2b, val2b, x1v, total;  // *b: the learned side of auto;
+                                                               // x1v: open-loop x1 (FP64)
 };
 
 // Decode tables of one component: first-level table on kLutBits bits (up to
@@ -26,7 +27,7 @@ struct DecInfo {
   int dtype, dim, R1, R2, C1, C2, lmax, use_model;
   long long K, rho12_q, Qhi;
   float rho12_f;
-  int pad2;
+  int open;  // open-loop stream: x' = s2 (K + q2 + g(x1')) in FP64
   double s2;
   unsigned long long nout1, nout2, nraw, w1, w2;
   long long ng1, ng2;
