@@ -158,29 +158,60 @@ __host__ __device__ inline double key_value(unsigned long long k) {
 // ---------------------------------------------------------------------------
 // predictor arithmetic (must match between compression and decompression)
 // ---------------------------------------------------------------------------
+// GB300 runs 64-bit integer <-> float conversions on its FP64 unit (a few
+// operations per clock per SM), so the two below take 32-bit conversions and
+// integer operations only, with the same results as __ull2float_rn and
+// (long long)rintf.
+//
+// Nearest float of 0 <= v < 2^40: above 2^32 the bits below the 32 kept are
+// folded into a sticky bit, which sits below the rounding position of the
+// 24-bit significand (at least two bits below it), then an exact scaling.
+__device__ __forceinline__ float u40_to_float(unsigned long long v) {
+  if (v < (1ull << 32)) return __uint2float_rn((unsigned)v);
+  const int s = v >= (1ull << 39) ? 8 : 7;
+  const unsigned h = (unsigned)(v >> s) | ((v & ((1ull << s) - 1)) != 0 ? 1u : 0u);
+  return __fmul_rn(__uint2float_rn(h), s == 8 ? 256.0f : 128.0f);
+}
+
+// rint(t) as a 64-bit integer for |t| < 2^62: below 2^30 the 32-bit
+// conversion (ties to even); above, t is an integer (24-bit significand)
+// rebuilt from its exponent and significand.
+__device__ __forceinline__ long long rint_ll(float t) {
+  if (fabsf(t) < 0x1p30f) return (long long)__float2int_rn(t);
+  const unsigned b = __float_as_uint(t);
+  const int e = (int)((b >> 23) & 0xFF) - 150;  // t = m 2^e, e >= 7 here
+  const long long r = (long long)((b & 0x7FFFFFu) | 0x800000u) << e;
+  return (b >> 31) ? -r : r;
+}
+
 // round(rho * (a + acc)), rho = rq 2^-40: integer part of a*rho from the exact
 // 128-bit product, 40-bit fraction plus FP32 correction acc*rho, one fused
 // multiply-add, round to nearest even. rescale_split returns the integer part
-// and the FP32 fraction before rounding.
-__device__ __forceinline__ void rescale_split(long long a, float acc, long long rq, float rf,
+// and the FP32 fraction before rounding. |t| stays far below 2^62: |acc| <
+// 2^34 (int32 code differences), rho < 2^10, and the learned correction is
+// clamped to 2^50.
+__device__ __forceinline__ void rescale_split(int a, float acc, long long rq, float rf,
                                               long long &hi, float &t) {
-  const unsigned long long ua = (unsigned long long)(a < 0 ? -a : a);
+  // |a| rq < 2^82 from two 32 x 32 -> 64-bit products (rq < 2^50): a rq =
+  // (p1 + (p0 >> 32)) 2^32 + (p0 mod 2^32); 64-bit products and their high
+  // halves are slow on this GPU
+  const unsigned ua = a < 0 ? 0u - (unsigned)a : (unsigned)a;
   const unsigned long long ur = (unsigned long long)rq;
-  const unsigned long long lo64 = ua * ur;
-  const unsigned long long hi64 = __umul64hi(ua, ur);
-  const unsigned long long mask = (1ull << kRhoBits) - 1;
-  unsigned long long q = (hi64 << (64 - kRhoBits)) | (lo64 >> kRhoBits);
-  unsigned long long r = lo64 & mask;
+  const unsigned long long p0 = (unsigned long long)ua * (unsigned)ur;
+  const unsigned long long p1 = (unsigned long long)ua * (unsigned)(ur >> 32);
+  const unsigned long long mid = p1 + (p0 >> 32);
+  const unsigned long long q = mid >> (kRhoBits - 32);
+  const unsigned long long r = ((mid & ((1ull << (kRhoBits - 32)) - 1)) << 32) | (p0 & 0xFFFFFFFFull);
   unsigned long long lo;
   if (a >= 0) { hi = (long long)q; lo = r; }
   else if (r == 0) { hi = -(long long)q; lo = 0; }
   else { hi = -(long long)q - 1; lo = (1ull << kRhoBits) - r; }
-  const float base = __fmul_rn(__ull2float_rn(lo), 0x1p-40f);
+  const float base = __fmul_rn(u40_to_float(lo), 0x1p-40f);
   t = __fmaf_rn(acc, rf, base);
 }
 
 template <bool HAS_P = false>
-__device__ __forceinline__ long long rescale(long long a, float acc, long long rq, float rf,
+__device__ __forceinline__ long long rescale(int a, float acc, long long rq, float rf,
                                              float pc = 0.0f) {
   long long hi;
   float t;
@@ -190,7 +221,7 @@ __device__ __forceinline__ long long rescale(long long a, float acc, long long r
     t = __fadd_rn(t, pc);
     t = fminf(fmaxf(t, -0x1p50f), 0x1p50f);
   }
-  return hi + (long long)rintf(t);
+  return hi + rint_ll(t);
 }
 
 __device__ __forceinline__ int wsub(int a, int b) { return (int)((unsigned)a - (unsigned)b); }

@@ -266,13 +266,13 @@ __global__ void __launch_bounds__(256) k_prequant(const __grid_constant__ CompAr
 // ---------------------------------------------------------------------------
 // Grid codes of U points at once: every point's plan entries, then every
 // vertex code, are loaded before any is used (the gathers overlap).
-// x1 receives the grid value before quantisation (vertex bins, a + acc) for
-// the open loop.
+// Open loop: x1v (or NULL) receives, at the points flagged in own, the grid
+// value before quantisation (vertex bins, a + acc; FP64 work, done only then).
 template <int DIM, int U>
 __device__ __forceinline__ void grid_codes(const int64_t (&j)[U], const bool (&ok)[U],
                                            const PlanView &pv, const int *__restrict__ Q,
                                            const FieldParams &f, Status *st, int (&out)[U],
-                                           double (&x1)[U]) {
+                                           double *__restrict__ x1v, const bool (&own)[U]) {
   int v[U][DIM + 1];
   float lf[U][DIM];
 #pragma unroll
@@ -292,10 +292,10 @@ __device__ __forceinline__ void grid_codes(const int64_t (&j)[U], const bool (&o
     for (int k = 0; k <= DIM; k++) qv[u][k] = v[u][0] >= 0 ? __ldg(Q + v[u][k]) : 0;
 #pragma unroll
   for (int u = 0; u < U; u++) {
-    long long a;
+    int a;  // a vertex code or the fill value: both in [0, Qhi], Qhi < 2^29
     float acc = 0.0f;
     if (v[u][0] < 0) {
-      a = f.fill_u;
+      a = (int)f.fill_u;
     } else {
       const int qa = qv[u][0];
       a = qa;
@@ -307,7 +307,7 @@ __device__ __forceinline__ void grid_codes(const int64_t (&j)[U], const bool (&o
       }
     }
     const long long q = rescale(a, acc, f.rho21_q, f.rho21_f);
-    x1[u] = __dadd_rn((double)a, (double)acc);
+    if (x1v && own[u]) x1v[j[u]] = __dadd_rn((double)a, (double)acc);
     out[u] = 0;
     if (!ok[u]) continue;
     if (q <= -(1ll << 27) || q >= (1ll << 27)) set_error(st, MCC_ERR_RANGE);
@@ -352,25 +352,23 @@ __global__ void __launch_bounds__(256) k_grid2d(const __grid_constant__ CompArgs
     int64_t j[U];
     bool ok[U];
     int q[U];
-    double x1[U];
+    bool own[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = threadIdx.x + 256 * u;
       const int ly = idx / (TX + 1), lx = idx - ly * (TX + 1);
       const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
       ok[u] = idx < NP && gx >= 0 && gy >= 0 && gx < nx && gy < ny;
+      own[u] = ok[u] && lx > 0 && ly > 0;
       j[u] = gx + (int64_t)nx * gy;
     }
-    grid_codes<2, U>(j, ok, pv, Q, f, st, q, x1);
+    grid_codes<2, U>(j, ok, pv, Q, f, st, q, x1v, own);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = threadIdx.x + 256 * u;
       if (idx >= NP) continue;
       const int ly = idx / (TX + 1), lx = idx - ly * (TX + 1);
-      if (ok[u] && lx > 0 && ly > 0) {
-        q1[j[u]] = q[u];
-        if (x1v) x1v[j[u]] = x1[u];
-      }
+      if (own[u]) q1[j[u]] = q[u];
       s[ly][lx] = q[u];
     }
   }
@@ -435,7 +433,7 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
     int64_t j[U];
     bool ok[U];
     int q[U];
-    double x1[U];
+    bool own[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = base + threadIdx.x + NT * u;
@@ -443,19 +441,17 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
       const int ly = rem / (TX + 1), lx = rem - ly * (TX + 1);
       const int gx = x0 - 1 + lx, gy = y0 - 1 + ly, gz = z0 - 1 + lz;
       ok[u] = idx < NP && gx >= 0 && gy >= 0 && gz >= 0 && gx < nx && gy < ny && gz < nz;
+      own[u] = ok[u] && lx > 0 && ly > 0 && lz > 0;
       j[u] = gx + (int64_t)nx * gy + sxy * gz;
     }
-    grid_codes<3, U>(j, ok, pv, Q, f, st, q, x1);
+    grid_codes<3, U>(j, ok, pv, Q, f, st, q, x1v, own);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = base + threadIdx.x + NT * u;
       if (idx >= NP) continue;
       const int lz = idx / ((TY + 1) * (TX + 1)), rem = idx - lz * ((TY + 1) * (TX + 1));
       const int ly = rem / (TX + 1), lx = rem - ly * (TX + 1);
-      if (ok[u] && lx > 0 && ly > 0 && lz > 0) {
-        q1[j[u]] = q[u];
-        if (x1v) x1v[j[u]] = x1[u];
-      }
+      if (own[u]) q1[j[u]] = q[u];
       s[lz][ly][lx] = q[u];
     }
   }
