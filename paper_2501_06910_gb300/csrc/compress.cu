@@ -186,25 +186,49 @@ __global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ CompArgs
   bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (; i + 7 * stride < n; i += 8 * stride) {
-    double v[8];
+  // x is read with the default caching: k_prequant reads it again from L2
+  if (sizeof(T) == 8) {
+    for (; i + 7 * stride < n; i += 8 * stride) {
+      double v[8];
 #pragma unroll
-    for (int u = 0; u < 8; u++) v[u] = (double)__ldcs(x + i + u * stride);
+      for (int u = 0; u < 8; u++) v[u] = (double)__ldg(x + i + u * stride);
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const unsigned long long b = value_bits(v[u]);
+      for (int u = 0; u < 8; u++) {
+        const unsigned long long b = value_bits(v[u]);
+        bad |= ((b >> 52) & 0x7FF) == 0x7FF;
+        const unsigned long long k = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+        mn = max(mn, ~k);
+        mx = max(mx, k);
+      }
+    }
+    for (; i < n; i += stride) {
+      const unsigned long long b = value_bits((double)__ldg(x + i));
       bad |= ((b >> 52) & 0x7FF) == 0x7FF;
       const unsigned long long k = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
       mn = max(mn, ~k);
       mx = max(mx, k);
     }
-  }
-  for (; i < n; i += stride) {
-    const unsigned long long b = value_bits((double)__ldcs(x + i));
-    bad |= ((b >> 52) & 0x7FF) == 0x7FF;
-    const unsigned long long k = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-    mn = max(mn, ~k);
-    mx = max(mx, k);
+  } else {
+    // FP32: ordered 32-bit keys (no float -> double conversion per value,
+    // a slow operation on this GPU); the extremes are widened once below
+    unsigned int mn32 = 0, mx32 = 0;
+    for (; i < n; i += stride) {
+      const unsigned int b = __float_as_uint((float)__ldg(x + i));
+      bad |= ((b >> 23) & 0xFF) == 0xFF;
+      const unsigned int k = (b >> 31) ? ~b : (b | 0x80000000u);
+      mn32 = max(mn32, ~k);
+      mx32 = max(mx32, k);
+    }
+    if (mx32 != 0) {  // this thread saw a value: keys of the same values as doubles
+      const unsigned int klo = ~mn32, khi = mx32;
+      const float flo = __uint_as_float((klo >> 31) ? (klo & 0x7FFFFFFFu) : ~klo);
+      const float fhi = __uint_as_float((khi >> 31) ? (khi & 0x7FFFFFFFu) : ~khi);
+      const unsigned long long blo = value_bits((double)flo), bhi = value_bits((double)fhi);
+      const unsigned long long kl = (blo >> 63) ? ~blo : (blo | 0x8000000000000000ull);
+      const unsigned long long kh = (bhi >> 63) ? ~bhi : (bhi | 0x8000000000000000ull);
+      mn = ~kl;
+      mx = kh;
+    }
   }
   for (int o = 16; o; o >>= 1) {
     mn = max(mn, __shfl_xor_sync(0xffffffffu, mn, o));

@@ -145,13 +145,19 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
   I.L = make_layout(I.R1, I.R2, I.ng1, I.ng2, I.nout1, I.nout2, I.nraw, vsz, I.w1, I.w2,
                     I.use_model ? kModelBytes : 0);
   if (I.L.total != ld64(h + H_TOTAL) || I.L.total > a.in_bytes) return false;
+  // the ends of the group tables: ten independent loads issued together
   const unsigned char *in = a.in;
-  if (ld32(in + I.L.gtab1) != 0 || ld32(in + I.L.gtab1 + 4 * I.ng1) != I.w1) return false;
-  if (ld32(in + I.L.gtab2) != 0 || ld32(in + I.L.gtab2 + 4 * I.ng2) != I.w2) return false;
-  if (ld32(in + I.L.etab1) != 0 || ld32(in + I.L.etab1 + 4 * I.ng1) != I.nout1) return false;
-  if (ld32(in + I.L.etab2) != 0 || ld32(in + I.L.etab2 + 4 * I.ng2) != I.nout2) return false;
-  if (ld32(in + I.L.rtab2) != 0 || ld32(in + I.L.rtab2 + 4 * I.ng2) != I.nraw) return false;
-  return true;
+  const uint64_t off[10] = {I.L.gtab1, I.L.gtab1 + 4 * I.ng1, I.L.gtab2, I.L.gtab2 + 4 * I.ng2,
+                            I.L.etab1, I.L.etab1 + 4 * I.ng1, I.L.etab2, I.L.etab2 + 4 * I.ng2,
+                            I.L.rtab2, I.L.rtab2 + 4 * I.ng2};
+  const uint64_t want[10] = {0, I.w1, 0, I.w2, 0, I.nout1, 0, I.nout2, 0, I.nraw};
+  unsigned int v[10];
+#pragma unroll
+  for (int k = 0; k < 10; k++) v[k] = ld32(in + off[k]);
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 10; k++) ok = ok && v[k] == want[k];
+  return ok;
 }
 
 __global__ void __launch_bounds__(1024) k_dec_prep(const __grid_constant__ DecArgs A) {
