@@ -210,9 +210,12 @@ __global__ void __launch_bounds__(1024) k_dec_prep(const __grid_constant__ DecAr
   for (int s = threadIdx.x; s < nsym; s += blockDim.x)
     if (lens[s]) T->sorted[ct.offset[lens[s]] + rank[s]] = (unsigned short)s;
   if (threadIdx.x <= kMaxLen + 1) {
-    T->first[threadIdx.x] = ct.first[threadIdx.x];
-    T->count[threadIdx.x] = ct.count[threadIdx.x];
-    T->offset[threadIdx.x] = ct.offset[threadIdx.x];
+    const int l = threadIdx.x;
+    T->first[l] = ct.first[l];
+    T->count[l] = ct.count[l];
+    T->offset[l] = ct.offset[l];
+    T->lim[l] = l >= 1 && l <= kMaxLen
+                    ? (unsigned long long)(ct.first[l] + ct.count[l]) << (32 - l) : 0ull;
   }
   __syncthreads();
   // first-level table: for the complete codes at the front of a kLutBits-bit
@@ -294,6 +297,7 @@ __device__ __forceinline__ void load_tab(DecTab *dst, const DecTab *src, int nsy
     dst->first[i] = src->first[i];
     dst->count[i] = src->count[i];
     dst->offset[i] = src->offset[i];
+    dst->lim[i] = src->lim[i];
   }
   for (int i = threadIdx.x; i < nsym; i += blockDim.x) dst->sorted[i] = src->sorted[i];
 }
@@ -445,16 +449,16 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
             sym = (int)((e >> 11) & 0xFFF);
           }
         } else {
-          sym = -1;
-          for (int l = kLutBits + 1; l <= lmax; l++) {
-            const unsigned int c = win >> (32 - l);
-            if (c - Tb.first[l] < Tb.count[l]) {
-              sym = Tb.sorted[Tb.offset[l] + c - Tb.first[l]];
-              len = l;
-              break;
-            }
-          }
-          if (sym < 0) { lane_bad = true; break; }
+          // a code longer than the table: its length from the limits (one
+          // independent comparison per length instead of a serial search;
+          // the window is at or above lim[kLutBits] here)
+          int nl = 0;
+#pragma unroll
+          for (int l = kLutBits + 1; l <= kMaxLen; l++)
+            nl += (l <= lmax && (unsigned long long)win >= Tb.lim[l]) ? 1 : 0;
+          len = kLutBits + 1 + nl;
+          if (len > lmax) { lane_bad = true; break; }
+          sym = Tb.sorted[Tb.offset[len] + (win >> (32 - len)) - Tb.first[len]];
         }
         r.buf <<= len;
         r.nb -= len;

@@ -18,6 +18,10 @@ struct CompressWs {
 // in canonical order.
 struct DecTab {
   unsigned long long lut[1 << kLutBits];
+  // lim[l]: (first[l] + count[l]) 2^(32-l), the left-aligned end of the codes
+  // of length l (nondecreasing in l): a 32-bit window's code length is the
+  // smallest l with window < lim[l]
+  unsigned long long lim[kMaxLen + 2];
   unsigned int first[kMaxLen + 2], count[kMaxLen + 2], offset[kMaxLen + 2];
   unsigned short sorted[2 * kMaxR];
 };
