@@ -629,20 +629,24 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
   const int64_t sxy = (int64_t)pv.nx * pv.ny;
   const float *__restrict__ pcor = c.p;
   const int64_t stride = (int64_t)gridDim.y * blockDim.x;
-  // two vertices per thread and iteration, their gathers issued together;
-  // uniform trip count per warp
-  const int64_t nloop = (n + 2 * stride - 1) / (2 * stride) * (2 * stride);
+  // U vertices per thread and iteration (4 in 2D, 2 in 3D), their gathers
+  // issued together; uniform trip count per warp
+  constexpr int U = DIM == 2 ? 4 : 2;
+  const int64_t nloop = (n + U * stride - 1) / (U * stride) * (U * stride);
   if (OPEN && A.open[fi]) node_open<DIM, T>(A, c, f, shist);
   else
-  for (int64_t i0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i0 < nloop; i0 += 2 * stride) {
-    int64_t iv[2] = {i0, i0 + stride};
-    bool valid[2];
-    uint32_t cl[2];
-    float fr[2][3];
-    int Qv[2];
-    int cor[2][8];
+  for (int64_t i0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i0 < nloop; i0 += U * stride) {
+    int64_t iv[U];
+    iv[0] = i0;
 #pragma unroll
-    for (int u = 0; u < 2; u++) {
+    for (int u = 1; u < U; u++) iv[u] = iv[u - 1] + stride;
+    bool valid[U];
+    uint32_t cl[U];
+    float fr[U][3];
+    int Qv[U];
+    int cor[U][8];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
       valid[u] = iv[u] < n;
       const int64_t i = valid[u] ? iv[u] : 0;
       cl[u] = __ldg(pv.cell + i);
@@ -652,9 +656,9 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
       Qv[u] = __ldg(Q + i);
     }
 #pragma unroll
-    for (int u = 0; u < 2; u++) corner_codes<DIM>(q1, cl[u], nx, sxy, cor[u]);
+    for (int u = 0; u < U; u++) corner_codes<DIM>(q1, cl[u], nx, sxy, cor[u]);
 #pragma unroll
-    for (int u = 0; u < 2; u++) {
+    for (int u = 0; u < U; u++) {
       const int64_t i = iv[u];
       int sym = 0, symb = 0;
       if (valid[u]) {

@@ -639,8 +639,8 @@ __device__ __forceinline__ void recon_open(const DecArgs &A, double s2, long lon
   }
 }
 
-template <int DIM, typename T>
-__global__ void __launch_bounds__(256, 6) k_recon(const __grid_constant__ DecArgs A) {
+template <int DIM, typename T, int U>
+__global__ void __launch_bounds__(256, U == 2 ? 6 : 4) k_recon(const __grid_constant__ DecArgs A) {
   pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.x);
@@ -661,16 +661,19 @@ __global__ void __launch_bounds__(256, 6) k_recon(const __grid_constant__ DecArg
   const int nx = pv.nx;
   const int64_t sxy = (int64_t)pv.nx * pv.ny;
   const int64_t stride = (int64_t)gridDim.y * blockDim.x;
-  for (int64_t p0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; p0 < n; p0 += 2 * stride) {
-    // two vertices per iteration, their gathers issued together
-    int64_t pv2[2] = {p0, p0 + stride};
-    bool go[2];
-    int q2v[2];
-    uint32_t cl[2];
-    float fr[2][3];
-    int cor[2][8];
+  for (int64_t p0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; p0 < n; p0 += U * stride) {
+    // U vertices per iteration, their gathers issued together
+    int64_t pv2[U];
+    pv2[0] = p0;
 #pragma unroll
-    for (int u = 0; u < 2; u++) {
+    for (int u = 1; u < U; u++) pv2[u] = pv2[u - 1] + stride;
+    bool go[U];
+    int q2v[U];
+    uint32_t cl[U];
+    float fr[U][3];
+    int cor[U][8];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
       const int64_t p = pv2[u] < n ? pv2[u] : p0;
       q2v[u] = __ldg(q2s + p);
       go[u] = pv2[u] < n && q2v[u] != INT_MIN;  // INT_MIN: raw value already in place
@@ -680,9 +683,9 @@ __global__ void __launch_bounds__(256, 6) k_recon(const __grid_constant__ DecArg
       fr[u][2] = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + p)), 0x1p-15f) : 0.0f;
     }
 #pragma unroll
-    for (int u = 0; u < 2; u++) corner_codes<DIM>(q1, cl[u], nx, sxy, cor[u]);
+    for (int u = 0; u < U; u++) corner_codes<DIM>(q1, cl[u], nx, sxy, cor[u]);
 #pragma unroll
-    for (int u = 0; u < 2; u++) {
+    for (int u = 0; u < U; u++) {
       if (!go[u]) continue;
       const int64_t p = pv2[u];
       const float acc = interp_acc<DIM>(cor[u], fr[u][0], fr[u][1], fr[u][2]);
@@ -815,11 +818,11 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
     unsigned int chunks = (unsigned int)((sms * 8 + nf - 1) / nf);
     if (chunks > 65535) chunks = 65535;
     if (pv.dim == 2) {
-      if (dtype == MCC_F64) launch_pdl(k_recon<2, double>, dim3(nf, chunks), dim3(256), 0, stream, A);
-      else launch_pdl(k_recon<2, float>, dim3(nf, chunks), dim3(256), 0, stream, A);
+      if (dtype == MCC_F64) launch_pdl(k_recon<2, double, 4>, dim3(nf, chunks), dim3(256), 0, stream, A);
+      else launch_pdl(k_recon<2, float, 4>, dim3(nf, chunks), dim3(256), 0, stream, A);
     } else {
-      if (dtype == MCC_F64) launch_pdl(k_recon<3, double>, dim3(nf, chunks), dim3(256), 0, stream, A);
-      else launch_pdl(k_recon<3, float>, dim3(nf, chunks), dim3(256), 0, stream, A);
+      if (dtype == MCC_F64) launch_pdl(k_recon<3, double, 2>, dim3(nf, chunks), dim3(256), 0, stream, A);
+      else launch_pdl(k_recon<3, float, 2>, dim3(nf, chunks), dim3(256), 0, stream, A);
     }
   }
   if (cudaGetLastError() != cudaSuccess) return MCC_ERR_CUDA;
