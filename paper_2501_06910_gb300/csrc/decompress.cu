@@ -548,6 +548,22 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
 // ---------------------------------------------------------------------------
 // inverse Lorenzo: inclusive prefix sums (wrapping int32 arithmetic)
 // ---------------------------------------------------------------------------
+// One warp per row; every lane holds 8 consecutive values of a 256-value
+// chunk (two 16-byte loads when the rows are 16-byte aligned), scans them
+// locally, and a warp scan of the lane totals offsets them. The next chunk is
+// loaded before the current one is stored, so the loads of a row overlap.
+__device__ __forceinline__ void load8(const int *r, int i0, int nx, bool vec, unsigned int (&v)[8]) {
+  if (vec && i0 + 8 <= nx) {
+    const int4 a = *reinterpret_cast<const int4 *>(r + i0);
+    const int4 b = *reinterpret_cast<const int4 *>(r + i0 + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; e++) v[e] = i0 + e < nx ? (unsigned int)r[i0 + e] : 0u;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_scan_rows(const __grid_constant__ DecArgs A) {
   pdl_trigger();
   pdl_wait();
@@ -561,17 +577,35 @@ __global__ void __launch_bounds__(256) k_scan_rows(const __grid_constant__ DecAr
   const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= nrows) return;
   int *r = q + row * nx;
+  const bool vec = (nx & 3) == 0;  // rows start on 16-byte boundaries (q is 256-aligned)
   unsigned int carry = 0;
-  for (int base = 0; base < nx; base += 32) {
-    const int i = base + lane;
-    unsigned int v = i < nx ? (unsigned int)r[i] : 0u;
-    for (int s = 1; s < 32; s <<= 1) {
-      const unsigned int t = __shfl_up_sync(0xffffffffu, v, s);
-      if (lane >= s) v += t;
+  unsigned int v[8];
+  load8(r, 8 * lane, nx, vec, v);
+  for (int base = 0; base < nx; base += 256) {
+    unsigned int nv[8];
+    if (base + 256 < nx) load8(r, base + 256 + 8 * lane, nx, vec, nv);
+#pragma unroll
+    for (int e = 1; e < 8; e++) v[e] += v[e - 1];
+    unsigned int incl = v[7];
+    for (int sft = 1; sft < 32; sft <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, sft);
+      if (lane >= sft) incl += t;
     }
-    v += carry;
-    if (i < nx) r[i] = (int)v;
-    carry = __shfl_sync(0xffffffffu, v, 31);
+    const unsigned int off = carry + incl - v[7];
+    const int i0 = base + 8 * lane;
+    if (vec && i0 + 8 <= nx) {
+      *reinterpret_cast<int4 *>(r + i0) =
+          make_int4((int)(v[0] + off), (int)(v[1] + off), (int)(v[2] + off), (int)(v[3] + off));
+      *reinterpret_cast<int4 *>(r + i0 + 4) =
+          make_int4((int)(v[4] + off), (int)(v[5] + off), (int)(v[6] + off), (int)(v[7] + off));
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; e++)
+        if (i0 + e < nx) r[i0 + e] = (int)(v[e] + off);
+    }
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll
+    for (int e = 0; e < 8; e++) v[e] = nv[e];
   }
 }
 
@@ -604,10 +638,16 @@ __global__ void __launch_bounds__(32 * W) k_scan_axis(const __grid_constant__ De
   __syncthreads();
   unsigned int pre = 0;
   for (int k = 0; k < w; k++) pre += part[k][lane];
-  if (valid)
-    for (int t = t0; t < t1; t++) {
-      pre += (unsigned int)col[(int64_t)t * S];
-      col[(int64_t)t * S] = (int)pre;
+  if (valid)  // eight loads in flight before their stores
+    for (int t = t0; t < t1; t += 8) {
+      unsigned int v[8];
+#pragma unroll
+      for (int e = 0; e < 8; e++) v[e] = t + e < t1 ? (unsigned int)col[(int64_t)(t + e) * S] : 0u;
+#pragma unroll
+      for (int e = 0; e < 8; e++) {
+        pre += v[e];
+        if (t + e < t1) col[(int64_t)(t + e) * S] = (int)pre;
+      }
     }
 }
 
