@@ -180,13 +180,14 @@ mcc_status mcc_decompress(mcc_plan plan, const void *d_in, size_t in_bytes, void
 /* Batched form of Algorithms 3 and 4 for many variables / timesteps on one
  * mesh (Sec. IV-B: the mapping is computed once and reused across variables
  * and timesteps). Field f is compressed from d_values[f] (a HOST array of n
- * device pointers) with per_field[f] (a host array; eb_mode, eb and
- * grid_fraction may differ per field, dtype, R1, R2, C1, C2 and lmax must
- * equal per_field[0]'s) into the slot d_out + f * slot_bytes (slot_bytes a
- * multiple of 8 and >= mcc_compress_bound). Fields run in launch chains of up
- * to 64 whose kernels carry a field dimension, so latency-bound stages (code
- * books, decode tables, Huffman decoding) of different fields overlap and the
- * fields share plan tiles in L2. The workspace holds one compression
+ * device pointers) with per_field[f] (a host array; eb_mode, eb,
+ * grid_fraction, predictor, d_model and loop may differ per field; dtype, R1,
+ * R2, C1, C2 and lmax must equal per_field[0]'s) into the slot d_out + f *
+ * slot_bytes (slot_bytes a multiple of 8 and >= mcc_compress_bound). Fields
+ * run in launch chains of up to 64 whose kernels carry a field dimension, so
+ * latency-bound stages (code books, decode tables, Huffman decoding) of
+ * different fields overlap and the fields share plan tiles in L2. The
+ * workspace holds one compression
  * workspace (mcc_workspace_size) per field of a chain: workspace_bytes /
  * that size fields per chain, at least one. If out_sizes (host, n entries) is
  * non-NULL the call synchronises and fills it; device-side errors are then
@@ -259,7 +260,8 @@ mcc_status mcc_train_workspace_size(mcc_plan plan, const mcc_params *p, const mc
 
 /* Train a model on n fields of this plan (d_fields: a HOST array of n device
  * pointers to n_vertices values of p->dtype; the bound parameters of p apply
- * to every field, its predictor fields are ignored). Steps: for each field
+ * to every field, its predictor and loop fields are ignored: the model serves
+ * the closed loop). Steps: for each field
  * the front of the compression chain (bound split, vertex and grid codes),
  * then cfg->samples_per_field vertices drawn by a counter-based hash with
  * their features and targets; the feature exponent sx from the 99.9th
