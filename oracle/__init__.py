@@ -54,7 +54,7 @@ class _Params(C.Structure):
                 ("grid_fraction", C.c_double), ("R1", C.c_int), ("R2", C.c_int),
                 ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int),
                 ("model", C.c_void_p), ("model_bytes", C.c_size_t), ("auto_select", C.c_int),
-                ("open_loop", C.c_int)]
+                ("open_loop", C.c_int), ("f_op", C.c_int), ("g_op", C.c_int)]
 
 
 class _Field(C.Structure):
@@ -186,7 +186,8 @@ DEFAULTS = dict(eb_mode="rel", eb=1e-4, grid_fraction=0.5, R1=512, R2=512, C1=12
                 lmax=24)
 
 
-def make_params(dtype, model=None, auto=False, open_loop=False, **kw):
+def make_params(dtype, model=None, auto=False, open_loop=False, f_op="barycentric",
+                g_op="multilinear", **kw):
     """Parameters; ``model`` is a learned-predictor blob (uint8 array) or None;
     ``auto`` keeps whichever predictor encodes smaller. The returned structure
     keeps a reference to the blob."""
@@ -195,6 +196,8 @@ def make_params(dtype, model=None, auto=False, open_loop=False, **kw):
     out = _Params()
     out.auto_select = 1 if auto else 0
     out.open_loop = 1 if open_loop else 0
+    out.f_op = {"barycentric": 0, "cluster": 1}[f_op] if isinstance(f_op, str) else int(f_op)
+    out.g_op = {"multilinear": 0, "nearest": 1}[g_op] if isinstance(g_op, str) else int(g_op)
     if model is not None:
         blob = np.ascontiguousarray(model, dtype=np.uint8)
         out._blob = blob

@@ -452,6 +452,18 @@ static float vertex_interp(int dim, const int32_t *q1, int64_t nx, int64_t ny, u
   return acc;
 }
 
+/* Nearest grid node m_k of vertex k (Sec. III-B): the corner of its cell on
+ * the near side of the midpoint along every axis, read from the local
+ * coordinates (2^-15 units; exactly half goes to the upper node). */
+static int64_t nearest_node(int dim, int64_t nx, int64_t ny, uint32_t c, const uint16_t *frac,
+                            int64_t n_v, int64_t i) {
+  int64_t m = c;
+  if (frac[i] >= 16384) m += 1;
+  if (frac[n_v + i] >= 16384) m += nx;
+  if (dim == 3 && frac[2 * n_v + i] >= 16384) m += nx * ny;
+  return m;
+}
+
 /* Open loop: g on real corner values (vertex bins) in FP64, the same
  * difference form and order as vertex_interp, products and sums rounded one
  * at a time. */
@@ -838,6 +850,9 @@ static int check_params(const orc_params *p) {
   if (2 * p->R1 > (1 << p->lmax) || 2 * p->R2 > (1 << p->lmax)) return ORC_ERR_INVALID_ARG;
   if (p->open_loop != 0 && p->open_loop != 1) return ORC_ERR_INVALID_ARG;
   if (p->open_loop && p->model) return ORC_ERR_INVALID_ARG;  /* the predictor is closed loop */
+  if (p->f_op != 0 && p->f_op != 1) return ORC_ERR_INVALID_ARG;
+  if (p->g_op != 0 && p->g_op != 1) return ORC_ERR_INVALID_ARG;
+  if (p->g_op && p->model) return ORC_ERR_INVALID_ARG;  /* it corrects the interpolation */
   return ORC_OK;
 }
 
@@ -943,6 +958,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   int32_t *dl = (int32_t *)malloc(sizeof(int32_t) * (size_t)ng);
   const int open = p->open_loop;
   double *x1v = open ? (double *)malloc(sizeof(double) * (size_t)ng) : NULL;
+  int64_t *csum = NULL, *ccnt = NULL;  /* cluster sums and sizes (cluster-mean f) */
   uint16_t *sym1 = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)ng);
   uint16_t *sym2 = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n_v);
   int32_t *val2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_v);
@@ -968,12 +984,32 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     Q[i] = (int32_t)((int64_t)rint(u) - f.K);
   }
 
-  /* 2. f: barycentric interpolation of the vertex codes onto the grid, then
-   *    rescaled to grid bins: q1 = round((s2 / s1) * x1) */
+  /* 2. f: barycentric interpolation of the vertex codes onto the grid, or
+   *    the cluster mean (the mean of the codes of the vertices whose nearest
+   *    node is j: integer part S / n, fraction (S mod n) / n in FP32; a node
+   *    no vertex is nearest to keeps the fill value, the paper's x1 = 0),
+   *    then rescaled to grid bins: q1 = round((s2 / s1) * x1) */
+  if (p->f_op) {
+    csum = (int64_t *)calloc((size_t)ng, sizeof(int64_t));
+    ccnt = (int64_t *)calloc((size_t)ng, sizeof(int64_t));
+    if (!csum || !ccnt) { st = ORC_ERR_OOM; goto done; }
+    for (int64_t i = 0; i < n_v; i++) {
+      const int64_t m = nearest_node(dim, nx, ny, cell[i], frac, n_v, i);
+      csum[m] += Q[i];
+      ccnt[m] += 1;
+    }
+  }
   for (int64_t j = 0; j < ng; j++) {
     int64_t a;
     float acc = 0.0f;
-    if (vid[j] < 0) {
+    if (p->f_op) {
+      if (ccnt[j] == 0) {
+        a = f.fill_u;
+      } else {
+        a = csum[j] / ccnt[j];
+        acc = (float)(csum[j] - a * ccnt[j]) / (float)ccnt[j];
+      }
+    } else if (vid[j] < 0) {
       a = f.fill_u;
     } else {
       a = Q[vid[j]];
@@ -1022,12 +1058,19 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
          * code q2 = round(x2 / s2) (vertex bins: u - K - g(x1), u = x / s2,
          * taken as (Q - g) + (u - rint(u))); reconstruction s2 (K + q2 +
          * g(x1')), bound tau1 + tau2, every vertex checked */
-        double c[8], cq[8];
-        corner_values(dim, x1v, nx, ny, cell[i], c);
-        const double gv = vertex_interp64(dim, c, fx, fy, fz);
+        double gv, gq;
         const double rho12 = (double)f.rho12_q * 0x1p-40;
-        for (int k = 0; k < (1 << dim); k++) cq[k] = (double)cor[k] * rho12;
-        const double gq = vertex_interp64(dim, cq, fx, fy, fz);
+        if (p->g_op) {  /* nearest node */
+          const int64_t m = nearest_node(dim, nx, ny, cell[i], frac, n_v, i);
+          gv = x1v[m];
+          gq = (double)q1[m] * rho12;
+        } else {
+          double c[8], cq[8];
+          corner_values(dim, x1v, nx, ny, cell[i], c);
+          gv = vertex_interp64(dim, c, fx, fy, fz);
+          for (int k = 0; k < (1 << dim); k++) cq[k] = (double)cor[k] * rho12;
+          gq = vertex_interp64(dim, cq, fx, fy, fz);
+        }
         double v = load_value(x, p->dtype, i);
         const double u = v * f.inv2;
         const double r = ((double)Q[i] - gv) + (u - rint(u));
@@ -1053,7 +1096,10 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
         continue;
       }
       int64_t P;
-      if (um) {
+      if (p->g_op) {  /* nearest node: P = round((s1/s2) q1[m]) */
+        P = rescale(q1[nearest_node(dim, nx, ny, cell[i], frac, n_v, i)], 0.0f, f.rho12_q,
+                    f.rho12_f);
+      } else if (um) {
         int32_t xq[MLP_K];
         mlp_features(dim, model.sx, cor, fx, fy, fz, f.rho12_f, f.Qhi, xq);
         P = rescale_p(cor[0], acc, f.rho12_q, f.rho12_f, mlp_forward(&model, xq));
@@ -1123,7 +1169,8 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     put_u32(h + 8, HEADER_BYTES);
     put_u32(h + 12, (uint32_t)p->dtype);
     put_u32(h + 16, (uint32_t)dim);
-    put_u32(h + 20, (uint32_t)((f.guard || open ? 1 : 0) | (use_model ? 2 : 0) | (open ? 4 : 0)));
+    put_u32(h + 20, (uint32_t)((f.guard || open ? 1 : 0) | (use_model ? 2 : 0) | (open ? 4 : 0) |
+                               (p->g_op ? 8 : 0) | (p->f_op ? 16 : 0)));
     put_u32(h + 24, (uint32_t)R1);
     put_u32(h + 28, (uint32_t)R2);
     put_u32(h + 32, (uint32_t)p->C1);
@@ -1176,7 +1223,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   if (sym2_dbg) memcpy(sym2_dbg, sym2, sizeof(uint16_t) * (size_t)n_v);
 done:
   free(Q); free(q1); free(dl); free(sym1); free(sym2); free(val2); free(h1); free(h2);
-  free(sym2b); free(val2b); free(h2b); free(len2b); free(x1v);
+  free(sym2b); free(val2b); free(h2b); free(len2b); free(x1v); free(csum); free(ccnt);
   free(len1); free(len2); free(code1); free(code2);
   return st;
 }
@@ -1332,8 +1379,9 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
   if (Qhi < 0 || Qhi >= ((int64_t)1 << 29)) return ORC_ERR_CORRUPT;
   const int use_model = (flags & 2) != 0;
   const int open = (flags & 4) != 0;
-  if (flags & ~7u) return ORC_ERR_CORRUPT;
-  if (open && use_model) return ORC_ERR_CORRUPT;
+  const int g_near = (flags & 8) != 0;  /* bit 4: cluster-mean f (compression only) */
+  if (flags & ~31u) return ORC_ERR_CORRUPT;
+  if ((open || g_near) && use_model) return ORC_ERR_CORRUPT;
   if (mbytes != (use_model ? MODEL_BYTES : 0)) return ORC_ERR_CORRUPT;
   layout_t L;
   make_layout(R1, R2, ngroups(ng, C1), ngroups(n_v, C2), nout1, nout2, nraw, vsz, w1, w2,
@@ -1387,18 +1435,26 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
       float fz = dim == 3 ? (float)frac[2 * n_v + i] * 0x1p-15f : 0.0f;
       int32_t cor[8];
       float acc = vertex_interp(dim, q1, nx, ny, cell[i], fx, fy, fz, cor);
+      const int64_t m = g_near ? nearest_node(dim, nx, ny, cell[i], frac, n_v, i) : 0;
       if (open) {
-        double cq[8];
         const double rho12 = (double)rho12_q * 0x1p-40;
-        for (int k = 0; k < (1 << dim); k++) cq[k] = (double)cor[k] * rho12;
-        const double gq = vertex_interp64(dim, cq, fx, fy, fz);
+        double gq;
+        if (g_near) {
+          gq = (double)q1[m] * rho12;
+        } else {
+          double cq[8];
+          for (int k = 0; k < (1 << dim); k++) cq[k] = (double)cor[k] * rho12;
+          gq = vertex_interp64(dim, cq, fx, fy, fz);
+        }
         const double xr = s2 * ((double)(K + q2) + gq);
         if (dtype == 0) ((double *)xout)[i] = xr;
         else ((float *)xout)[i] = (float)xr;
         continue;
       }
       int64_t P;
-      if (use_model) {
+      if (g_near) {
+        P = rescale(q1[m], 0.0f, rho12_q, rho12_f);
+      } else if (use_model) {
         int32_t xq[MLP_K];
         mlp_features(dim, model.sx, cor, fx, fy, fz, rho12_f, Qhi, xq);
         P = rescale_p(cor[0], acc, rho12_q, rho12_f, mlp_forward(&model, xq));

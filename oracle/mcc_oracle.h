@@ -71,6 +71,10 @@ typedef struct {
   int auto_select;    /* with a model: keep the predictor whose encoding is smaller */
   int open_loop;      /* 1: residual against g(x1) with the unquantised x1 (Algorithm 3
                          as printed), bound tau1 + tau2; 0: against g(x1'), bound tau2 */
+  int f_op;           /* mesh -> grid: 0 barycentric interpolation, 1 cluster mean
+                         (mean of the vertices whose nearest node is j, Sec. III-C) */
+  int g_op;           /* grid -> mesh: 0 bi/trilinear interpolation, 1 nearest node
+                         (x2[k] = x[k] - x1[m_k], Sec. III-B) */
 } orc_params;
 
 /* Per-field scalars derived from the values (Sec. III bound split). */

@@ -165,7 +165,7 @@ def test_open_loop_errors():
             G.compress(gp, x, eb=1e-3, **bad)
         assert err.value.status == mcc.INVALID_ARG
     s = G.compress(gp, x, eb=1e-3, open_loop=True)
-    for flip in (2, 8):
+    for flip in (2, 32):
         t = s.copy()
         t[20] |= flip
         with pytest.raises(mcc.MCCError) as err:

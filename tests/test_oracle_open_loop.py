@@ -131,7 +131,7 @@ def test_open_loop_errors(plans):
         oracle.compress(plan, x, eb=1e-3, open_loop=True, model=pack(random_model(2, 1)))
     assert err.value.status == 1  # invalid argument
     s = oracle.compress(plan, x, eb=1e-3, open_loop=True)
-    for bad in (s[20] | 2, s[20] | 8):
+    for bad in (s[20] | 2, s[20] | 32):
         t = s.copy()
         t[20] = bad
         with pytest.raises(oracle.OracleError) as err:
