@@ -58,6 +58,8 @@ enum { MCC_F64 = 0, MCC_F32 = 1 };   /* value types */
 enum { MCC_ABS = 0, MCC_REL = 1 };   /* bound modes: absolute, or x (max - min) */
 enum { MCC_PRED_ZERO = 0, MCC_PRED_LEARNED = 1, MCC_PRED_AUTO = 2 };  /* residual predictor */
 enum { MCC_LOOP_CLOSED = 0, MCC_LOOP_OPEN = 1 };  /* residual against g(x1') or g(x1) */
+enum { MCC_F_BARYCENTRIC = 0, MCC_F_CLUSTER = 1 };   /* mesh -> grid operator f */
+enum { MCC_G_MULTILINEAR = 0, MCC_G_NEAREST = 1 };   /* grid -> mesh operator g */
 #define MCC_MODEL_BYTES 5736   /* learned-predictor blob */
 #define MCC_MLP_PARAMS 5313    /* float parameters of the training network */
 
@@ -115,6 +117,20 @@ typedef struct {
    * q2 = round(x / s2 - g(x1)) in FP64 and the reconstruction s2 (q2 +
    * g(x1')). Open loop takes MCC_PRED_ZERO only. */
   int loop;
+  /* Operators (Sec. III-B, III-C). f, mesh -> grid: MCC_F_BARYCENTRIC, the
+   * barycentric interpolation of the vertex codes in the simplex holding the
+   * node; MCC_F_CLUSTER, the paper's cluster mean: the mean of the codes of
+   * the vertices whose nearest node is the node (integer part, then the
+   * remainder / count in FP32), a node no vertex is nearest to keeping the
+   * fill value (the paper initialises x1 to 0). g, grid -> mesh:
+   * MCC_G_MULTILINEAR, bilinear / trilinear interpolation over the vertex's
+   * cell; MCC_G_NEAREST, the paper's nearest node m_k (the cell corner on the
+   * near side of every midplane of the cell, half going up), P =
+   * round((s1/s2) q1[m_k]). Both gs are linear with weights summing to 1, so
+   * the bound holds for every combination. The nearest-node g takes
+   * MCC_PRED_ZERO only (the learned predictor corrects the interpolation). */
+  int f_op;
+  int g_op;
 } mcc_params;
 
 typedef struct mcc_plan_s *mcc_plan;
@@ -128,7 +144,8 @@ typedef struct {
 } mcc_plan_info;
 
 /* Defaults: F64, REL, eb 1e-4, grid_fraction 0.5, R1 = R2 = 512,
- * C1 = C2 = 128, lmax 24, MCC_PRED_ZERO, MCC_LOOP_CLOSED. */
+ * C1 = C2 = 128, lmax 24, MCC_PRED_ZERO, MCC_LOOP_CLOSED, MCC_F_BARYCENTRIC,
+ * MCC_G_MULTILINEAR. */
 void mcc_params_default(mcc_params *p);
 
 /* Build the mesh -> grid mapping once per mesh (Sec. IV-B: reused across
@@ -181,15 +198,15 @@ mcc_status mcc_decompress(mcc_plan plan, const void *d_in, size_t in_bytes, void
  * mesh (Sec. IV-B: the mapping is computed once and reused across variables
  * and timesteps). Field f is compressed from d_values[f] (a HOST array of n
  * device pointers) with per_field[f] (a host array; eb_mode, eb,
- * grid_fraction, predictor, d_model and loop may differ per field; dtype, R1,
- * R2, C1, C2 and lmax must equal per_field[0]'s) into the slot d_out + f *
- * slot_bytes (slot_bytes a multiple of 8 and >= mcc_compress_bound). Fields
- * run in launch chains of up to 64 whose kernels carry a field dimension, so
- * latency-bound stages (code books, decode tables, Huffman decoding) of
- * different fields overlap and the fields share plan tiles in L2. The
- * workspace holds one compression
- * workspace (mcc_workspace_size) per field of a chain: workspace_bytes /
- * that size fields per chain, at least one. If out_sizes (host, n entries) is
+ * grid_fraction, predictor, d_model, loop, f_op and g_op may differ per
+ * field; dtype, R1, R2, C1, C2 and lmax must equal per_field[0]'s) into the
+ * slot d_out + f * slot_bytes (slot_bytes a multiple of 8 and >=
+ * mcc_compress_bound). Fields run in launch chains of up to 64 whose kernels
+ * carry a field dimension, so latency-bound stages (code books, decode
+ * tables, Huffman decoding) of different fields overlap and the fields share
+ * plan tiles in L2. The workspace holds one compression workspace
+ * (mcc_workspace_size) per field of a chain: workspace_bytes / that size
+ * fields per chain, at least one. If out_sizes (host, n entries) is
  * non-NULL the call synchronises and fills it; device-side errors are then
  * returned (the first one found). */
 mcc_status mcc_compress_batch(mcc_plan plan, int n, const void *const *d_values,

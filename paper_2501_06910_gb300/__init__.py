@@ -30,6 +30,8 @@ F64, F32 = 0, 1
 ABS, REL = 0, 1
 PRED_ZERO, PRED_LEARNED, PRED_AUTO = 0, 1, 2
 LOOP_CLOSED, LOOP_OPEN = 0, 1
+F_BARYCENTRIC, F_CLUSTER = 0, 1
+G_MULTILINEAR, G_NEAREST = 0, 1
 LOSS_L2, LOSS_L1 = 0, 1
 MODEL_BYTES = 5736
 MLP_PARAMS = 5313
@@ -56,11 +58,12 @@ class _GridSpec(C.Structure):
 
 class Params(C.Structure):
     """mcc_params: dtype, eb_mode, eb, grid_fraction, R1, R2, C1, C2, lmax,
-    predictor, d_model, loop."""
+    predictor, d_model, loop, f_op, g_op."""
     _fields_ = [("dtype", C.c_int), ("eb_mode", C.c_int), ("eb", C.c_double),
                 ("grid_fraction", C.c_double), ("R1", C.c_int), ("R2", C.c_int),
                 ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int),
-                ("predictor", C.c_int), ("d_model", C.c_void_p), ("loop", C.c_int)]
+                ("predictor", C.c_int), ("d_model", C.c_void_p), ("loop", C.c_int),
+                ("f_op", C.c_int), ("g_op", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -167,11 +170,17 @@ def params_default(model=None, auto=False, open_loop=False, **overrides) -> Para
     """Parameters; ``model`` (a CUDA uint8 tensor of MODEL_BYTES) selects the
     learned predictor, or with ``auto`` the smaller of learned and plain;
     ``open_loop`` takes the residual against the unquantised grid component
-    (bound tau1 + tau2). The structure keeps a reference to the tensor."""
+    (bound tau1 + tau2); ``f_op`` ("barycentric" / "cluster") and ``g_op``
+    ("multilinear" / "nearest") pick the operators. The structure keeps a
+    reference to the tensor."""
     p = Params()
     load().mcc_params_default(C.byref(p))
     if open_loop:
         p.loop = LOOP_OPEN
+    for k, table in (("f_op", {"barycentric": F_BARYCENTRIC, "cluster": F_CLUSTER}),
+                     ("g_op", {"multilinear": G_MULTILINEAR, "nearest": G_NEAREST})):
+        if isinstance(overrides.get(k), str):
+            overrides[k] = table[overrides[k]]
     if model is not None:
         if model.dtype != torch.uint8 or model.numel() != MODEL_BYTES:
             raise ValueError("model must be a uint8 tensor of MODEL_BYTES bytes")

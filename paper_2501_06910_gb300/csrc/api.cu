@@ -24,6 +24,8 @@ extern "C" void mcc_params_default(mcc_params *p) {
   p->predictor = MCC_PRED_ZERO;
   p->d_model = nullptr;
   p->loop = MCC_LOOP_CLOSED;
+  p->f_op = MCC_F_BARYCENTRIC;
+  p->g_op = MCC_G_MULTILINEAR;
 }
 
 extern "C" const char *mcc_status_string(mcc_status s) {

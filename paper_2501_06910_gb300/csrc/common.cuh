@@ -46,7 +46,7 @@ enum : uint32_t {
   H_W1 = 168, H_W2 = 176, H_TOTAL = 184, H_MODEL = 192, H_QHI = 200
 };
 // header flags
-enum : uint32_t { F_GUARD = 1, F_MODEL = 2, F_OPEN = 4 };
+enum : uint32_t { F_GUARD = 1, F_MODEL = 2, F_OPEN = 4, F_GNEAR = 8, F_FCLUSTER = 16 };
 
 __host__ __device__ inline uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 __host__ __device__ inline int64_t ngroups(int64_t n, int C) {
@@ -327,6 +327,16 @@ __device__ __forceinline__ double interp64_codes(const int (&k)[8], long long rh
 #pragma unroll
   for (int t = 0; t < (1 << DIM); t++) c[t] = __dmul_rn((double)k[t], r);
   return interp64<DIM>(c, fx, fy, fz);
+}
+
+// Nearest grid node of a vertex (Sec. III-B): the corner of its cell on the
+// near side of every midplane, from the local coordinates in 2^-15 units
+// (exactly half goes to the upper node).
+template <int DIM>
+__device__ __forceinline__ uint32_t nearest_node(uint32_t c, unsigned fx, unsigned fy, unsigned fz,
+                                                 int nx, int64_t sxy) {
+  return c + (fx >= 16384u ? 1u : 0u) + (fy >= 16384u ? (uint32_t)nx : 0u) +
+         (DIM == 3 && fz >= 16384u ? (uint32_t)sxy : 0u);
 }
 
 // returns c_000, acc = g - c_000

@@ -56,6 +56,7 @@ struct CompArgs {
   const unsigned char *model[kMaxBatch];  // learned-predictor blob or NULL
   unsigned char mode[kMaxBatch];          // MCC_PRED_* per field
   unsigned char open[kMaxBatch];          // MCC_LOOP_OPEN per field
+  unsigned char fop[kMaxBatch], gop[kMaxBatch];  // MCC_F_* / MCC_G_* per field
   int any_auto;
 };
 
@@ -279,6 +280,27 @@ __global__ void __launch_bounds__(256) k_prequant(const __grid_constant__ CompAr
   const double inv2 = st->f.inv2;
   const long long K = st->f.K;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (A.fop[blockIdx.y] == MCC_F_CLUSTER) {
+    // cluster-mean f: every vertex adds its code to the sum and count of its
+    // nearest node (integer atomics: the totals do not depend on the order)
+    unsigned char *ws = A.ws0 + (int64_t)blockIdx.y * A.wss;
+    unsigned long long *csum = (unsigned long long *)(ws + A.W.csum);
+    unsigned int *ccnt = (unsigned int *)(ws + A.W.ccnt);
+    const PlanView &pv = A.pv;
+    const int64_t sxy = (int64_t)pv.nx * pv.ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+      const double v = (double)__ldg(x + i);
+      const int q = (int)(__double2ll_rn(__dmul_rn(v, inv2)) - K);
+      Q[i] = q;
+      const uint32_t c = __ldg(pv.cell + i);
+      const unsigned fx = __ldg(pv.frac + i), fy = __ldg(pv.frac + n + i);
+      const uint32_t m = pv.dim == 3 ? nearest_node<3>(c, fx, fy, __ldg(pv.frac + 2 * n + i), pv.nx, sxy)
+                                     : nearest_node<2>(c, fx, fy, 0u, pv.nx, sxy);
+      atomicAdd(csum + m, (unsigned long long)q);  // q >= 0: the codes start at the minimum
+      atomicAdd(ccnt + m, 1u);
+    }
+    return;
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
     const double v = (double)__ldg(x + i);
     Q[i] = (int)(__double2ll_rn(__dmul_rn(v, inv2)) - K);
@@ -339,6 +361,44 @@ __device__ __forceinline__ void grid_codes(const int64_t (&j)[U], const bool (&o
   }
 }
 
+// Cluster-mean f (Sec. III-C) at U grid points: the mean of the codes of the
+// vertices whose nearest node is the point, as integer part a = S / n and
+// fraction (S - a n) / n in FP32, rescaled to grid bins; a point no vertex is
+// nearest to takes the fill value.
+template <int U>
+__device__ __forceinline__ void grid_codes_cluster(const int64_t (&j)[U], const bool (&ok)[U],
+                                                   const unsigned long long *__restrict__ csum,
+                                                   const unsigned int *__restrict__ ccnt,
+                                                   const FieldParams &f, Status *st, int (&out)[U],
+                                                   double *__restrict__ x1v,
+                                                   const bool (&own)[U]) {
+  unsigned long long S[U];
+  unsigned int cnt[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    S[u] = ok[u] ? __ldg(csum + j[u]) : 0ull;
+    cnt[u] = ok[u] ? __ldg(ccnt + j[u]) : 0u;
+  }
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    int a;
+    float acc = 0.0f;
+    if (cnt[u] == 0) {
+      a = (int)f.fill_u;
+    } else {
+      const unsigned long long a64 = S[u] / cnt[u];
+      a = (int)a64;
+      acc = __fdiv_rn(__uint2float_rn((unsigned int)(S[u] - a64 * cnt[u])), __uint2float_rn(cnt[u]));
+    }
+    const long long q = rescale(a, acc, f.rho21_q, f.rho21_f);
+    if (x1v && own[u]) x1v[j[u]] = __dadd_rn((double)a, (double)acc);
+    out[u] = 0;
+    if (!ok[u]) continue;
+    if (q <= -(1ll << 27) || q >= (1ll << 27)) set_error(st, MCC_ERR_RANGE);
+    else out[u] = (int)q;
+  }
+}
+
 // Shared-memory histogram add, aggregated over lanes holding the same symbol.
 __device__ __forceinline__ void hist_add(unsigned int *sh, int sym, bool valid) {
   const int key = valid ? sym : -1;
@@ -360,6 +420,10 @@ __global__ void __launch_bounds__(256) k_grid2d(const __grid_constant__ CompArgs
   int *__restrict__ q1 = c.q1;
   double *__restrict__ x1v =
       A.open[blockIdx.x] ? (double *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.x1v) : nullptr;
+  const bool cluster = A.fop[blockIdx.x] == MCC_F_CLUSTER;
+  const unsigned long long *csum =
+      (const unsigned long long *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.csum);
+  const unsigned int *ccnt = (const unsigned int *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.ccnt);
   unsigned short *__restrict__ sym1 = c.sym1;
   int *__restrict__ val1 = c.val1;
   unsigned int *hist1 = c.hist1;
@@ -386,7 +450,8 @@ __global__ void __launch_bounds__(256) k_grid2d(const __grid_constant__ CompArgs
       own[u] = ok[u] && lx > 0 && ly > 0;
       j[u] = gx + (int64_t)nx * gy;
     }
-    grid_codes<2, U>(j, ok, pv, Q, f, st, q, x1v, own);
+    if (cluster) grid_codes_cluster<U>(j, ok, csum, ccnt, f, st, q, x1v, own);
+    else grid_codes<2, U>(j, ok, pv, Q, f, st, q, x1v, own);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = threadIdx.x + 256 * u;
@@ -437,6 +502,10 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
   int *__restrict__ q1 = c.q1;
   double *__restrict__ x1v =
       A.open[blockIdx.x] ? (double *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.x1v) : nullptr;
+  const bool cluster = A.fop[blockIdx.x] == MCC_F_CLUSTER;
+  const unsigned long long *csum =
+      (const unsigned long long *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.csum);
+  const unsigned int *ccnt = (const unsigned int *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.ccnt);
   unsigned short *__restrict__ sym1 = c.sym1;
   int *__restrict__ val1 = c.val1;
   unsigned int *hist1 = c.hist1;
@@ -468,7 +537,8 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
       own[u] = ok[u] && lx > 0 && ly > 0 && lz > 0;
       j[u] = gx + (int64_t)nx * gy + sxy * gz;
     }
-    grid_codes<3, U>(j, ok, pv, Q, f, st, q, x1v, own);
+    if (cluster) grid_codes_cluster<U>(j, ok, csum, ccnt, f, st, q, x1v, own);
+    else grid_codes<3, U>(j, ok, pv, Q, f, st, q, x1v, own);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = base + threadIdx.x + NT * u;
@@ -548,6 +618,7 @@ __device__ __forceinline__ void node_open(const CompArgs &A, const Ctx &c, const
   const int nx = pv.nx;
   const int64_t sxy = (int64_t)pv.nx * pv.ny;
   const double tau = __dadd_rn(f.tau1, f.tau2);
+  const bool near = A.gop[blockIdx.x] == MCC_G_NEAREST;
   const int64_t stride = (int64_t)gridDim.y * blockDim.x;
   const int64_t nloop = (n + stride - 1) / stride * stride;  // uniform trip count per warp
   for (int64_t i0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i0 < nloop; i0 += stride) {
@@ -560,23 +631,31 @@ __device__ __forceinline__ void node_open(const CompArgs &A, const Ctx &c, const
       const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + i)), 0x1p-15f);
       const float fz =
           DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + i)), 0x1p-15f) : 0.0f;
-      double cv[8];
-      cv[0] = __ldg(x1v + cl);
-      cv[1] = __ldg(x1v + cl + 1);
-      cv[2] = __ldg(x1v + cl + nx);
-      cv[3] = __ldg(x1v + cl + nx + 1);
-      if (DIM == 3) {
-        cv[4] = __ldg(x1v + cl + sxy);
-        cv[5] = __ldg(x1v + cl + sxy + 1);
-        cv[6] = __ldg(x1v + cl + sxy + nx);
-        cv[7] = __ldg(x1v + cl + sxy + nx + 1);
+      double gv, gq;
+      if (near) {  // nearest-node g: the node's values themselves
+        const uint32_t m = nearest_node<DIM>(cl, __ldg(pv.frac + i), __ldg(pv.frac + n + i),
+                                             DIM == 3 ? __ldg(pv.frac + 2 * n + i) : 0u, nx, sxy);
+        gv = __ldg(x1v + m);
+        gq = __dmul_rn((double)__ldg(q1 + m), __dmul_rn((double)f.rho12_q, 0x1p-40));
+      } else {
+        double cv[8];
+        cv[0] = __ldg(x1v + cl);
+        cv[1] = __ldg(x1v + cl + 1);
+        cv[2] = __ldg(x1v + cl + nx);
+        cv[3] = __ldg(x1v + cl + nx + 1);
+        if (DIM == 3) {
+          cv[4] = __ldg(x1v + cl + sxy);
+          cv[5] = __ldg(x1v + cl + sxy + 1);
+          cv[6] = __ldg(x1v + cl + sxy + nx);
+          cv[7] = __ldg(x1v + cl + sxy + nx + 1);
+        }
+        int cor[8];
+        corner_codes<DIM>(q1, cl, nx, sxy, cor);
+        gv = interp64<DIM>(cv, fx, fy, fz);
+        gq = interp64_codes<DIM>(cor, f.rho12_q, fx, fy, fz);
       }
-      int cor[8];
-      corner_codes<DIM>(q1, cl, nx, sxy, cor);
       const double v = (double)__ldg(x + i);
       const int Qi = __ldg(Q + i);
-      const double gv = interp64<DIM>(cv, fx, fy, fz);
-      const double gq = interp64_codes<DIM>(cor, f.rho12_q, fx, fy, fz);
       const double u = __dmul_rn(v, f.inv2);
       const double r = __dadd_rn(__dsub_rn((double)Qi, gv), __dsub_rn(u, rint(u)));
       const double q2d = rint(r);
@@ -591,6 +670,62 @@ __device__ __forceinline__ void node_open(const CompArgs &A, const Ctx &c, const
       sym2[i] = (unsigned short)sym;
     }
     hist_add(shist, sym, valid);
+  }
+}
+
+// Closed loop with the nearest-node g (Sec. III-B): P = round((s1/s2) q1[m])
+// with m the vertex's nearest node, one gather per vertex (four vertices per
+// thread and iteration); the guard as in the interpolating path.
+template <int DIM, typename T>
+__device__ __forceinline__ void node_nearest(const CompArgs &A, const Ctx &c, const FieldParams &f,
+                                             unsigned int *shist) {
+  const PlanView &pv = A.pv;
+  const T *__restrict__ x = (const T *)c.x;
+  const int *__restrict__ Q = c.Q;
+  const int *__restrict__ q1 = c.q1;
+  unsigned short *__restrict__ sym2 = c.sym2;
+  const int R2 = A.R2;
+  const int64_t n = pv.n_v;
+  const int nx = pv.nx;
+  const int64_t sxy = (int64_t)pv.nx * pv.ny;
+  const int64_t stride = (int64_t)gridDim.y * blockDim.x;
+  constexpr int U = 4;
+  const int64_t nloop = (n + U * stride - 1) / (U * stride) * (U * stride);
+  for (int64_t i0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i0 < nloop; i0 += U * stride) {
+    int64_t iv[U];
+    iv[0] = i0;
+#pragma unroll
+    for (int u = 1; u < U; u++) iv[u] = iv[u - 1] + stride;
+    uint32_t m[U];
+    int Qv[U], qm[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t i = iv[u] < n ? iv[u] : 0;
+      m[u] = nearest_node<DIM>(__ldg(pv.cell + i), __ldg(pv.frac + i), __ldg(pv.frac + n + i),
+                               DIM == 3 ? __ldg(pv.frac + 2 * n + i) : 0u, nx, sxy);
+      Qv[u] = __ldg(Q + i);
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) qm[u] = __ldg(q1 + m[u]);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t i = iv[u];
+      const bool valid = i < n;
+      int sym = 0;
+      if (valid) {
+        bool gfail = false;
+        if (f.guard) {
+          const double v = (double)__ldg(x + i);
+          const double xr = __dmul_rn(f.s2, (double)((long long)Qv[u] + f.K));
+          const double xo = sizeof(T) == 8 ? xr : (double)__double2float_rn(xr);
+          gfail = fabs(__dsub_rn(v, xo)) > f.tau2;
+        }
+        const long long P = rescale(qm[u], 0.0f, f.rho12_q, f.rho12_f);
+        sym = residual_symbol((long long)Qv[u] - P, gfail, R2, i, c.val2);
+        sym2[i] = (unsigned short)sym;
+      }
+      hist_add(shist, sym, valid);
+    }
   }
 }
 
@@ -634,6 +769,7 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
   constexpr int U = DIM == 2 ? 4 : 2;
   const int64_t nloop = (n + U * stride - 1) / (U * stride) * (U * stride);
   if (OPEN && A.open[fi]) node_open<DIM, T>(A, c, f, shist);
+  else if (OPEN && A.gop[fi] == MCC_G_NEAREST) node_nearest<DIM, T>(A, c, f, shist);
   else
   for (int64_t i0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i0 < nloop; i0 += U * stride) {
     int64_t iv[U];
@@ -1223,7 +1359,9 @@ __device__ void scan_field(const CompArgs &A, int fi) {
       put32(o + H_DIM, (uint32_t)a.dim);
       const bool open = A.open[fi] != 0;
       put32(o + H_FLAGS, (f.guard || open ? F_GUARD : 0u) | (model ? F_MODEL : 0u) |
-                             (open ? F_OPEN : 0u));
+                             (open ? F_OPEN : 0u) |
+                             (A.gop[fi] == MCC_G_NEAREST ? F_GNEAR : 0u) |
+                             (A.fop[fi] == MCC_F_CLUSTER ? F_FCLUSTER : 0u));
       put32(o + H_R1, (uint32_t)a.R1);
       put32(o + H_R2, (uint32_t)a.R2);
       put32(o + H_C1, (uint32_t)a.C1);
@@ -1411,6 +1549,9 @@ mcc_status check_params(const mcc_params *p) {
     return MCC_ERR_INVALID_ARG;
   if (p->loop != MCC_LOOP_CLOSED && p->loop != MCC_LOOP_OPEN) return MCC_ERR_INVALID_ARG;
   if (p->loop == MCC_LOOP_OPEN && p->predictor != MCC_PRED_ZERO) return MCC_ERR_INVALID_ARG;
+  if (p->f_op != MCC_F_BARYCENTRIC && p->f_op != MCC_F_CLUSTER) return MCC_ERR_INVALID_ARG;
+  if (p->g_op != MCC_G_MULTILINEAR && p->g_op != MCC_G_NEAREST) return MCC_ERR_INVALID_ARG;
+  if (p->g_op == MCC_G_NEAREST && p->predictor != MCC_PRED_ZERO) return MCC_ERR_INVALID_ARG;
   return MCC_OK;
 }
 
@@ -1444,6 +1585,8 @@ CompressWs compress_ws_layout(const PlanView &pv, const mcc_params *p) {
   w.sym2b = take(2 * (size_t)pv.n_v);
   w.val2b = take(4 * (size_t)pv.n_v);
   w.x1v = take(8 * (size_t)pv.n_g);
+  w.csum = take(8 * (size_t)pv.n_g);
+  w.ccnt = take(4 * (size_t)pv.n_g);
   w.total = o;
   return w;
 }
@@ -1480,10 +1623,15 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   A.ng2 = ngroups(pv.n_v, p->C2);
   A.F = make_layout(p->R1, p->R2, A.ng1, A.ng2, 0, 0, 0, 8, 0, 0);
   if (!front_only && capacity < A.F.out1) return MCC_ERR_CAPACITY;
-  bool any_model = false, any_open = false;
+  bool any_model = false, any_open = false, any_cluster = false;
   for (int f = 0; f < nf; f++) {
     A.open[f] = ps[f].loop == MCC_LOOP_OPEN ? 1 : 0;
-    any_open = any_open || A.open[f];
+    A.fop[f] = (unsigned char)ps[f].f_op;
+    A.gop[f] = (unsigned char)ps[f].g_op;
+    // the open-loop and nearest-node paths share the kernel variant with the
+    // runtime branches
+    any_open = any_open || A.open[f] || ps[f].g_op == MCC_G_NEAREST;
+    any_cluster = any_cluster || ps[f].f_op == MCC_F_CLUSTER;
     A.x[f] = xs[f];
     A.rp[f] = RParams{ps[f].dtype, ps[f].eb_mode, ps[f].eb, ps[f].grid_fraction};
     A.mode[f] = (unsigned char)ps[f].predictor;
@@ -1500,6 +1648,10 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     attr_set = true;
   }
   if (cudaMemset2DAsync(ws0, (size_t)wss, 0, kStatusBytes, (size_t)nf, stream) != cudaSuccess)
+    return MCC_ERR_CUDA;
+  if (any_cluster &&  // cluster sums and sizes (contiguous, one region per field)
+      cudaMemset2DAsync(ws0 + A.W.csum, (size_t)wss, 0, A.W.total - A.W.csum, (size_t)nf,
+                        stream) != cudaSuccess)
     return MCC_ERR_CUDA;
   const unsigned int bpf = (unsigned int)((sms * 2 + nf - 1) / nf);  // reduce blocks per field
   const unsigned int ppf = (unsigned int)((sms * 8 + nf - 1) / nf);  // prequant / node blocks per field

@@ -103,10 +103,11 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
   I.dtype = (int)ld32(h + H_DTYPE);
   I.dim = (int)ld32(h + H_DIM);
   const uint32_t flags = ld32(h + H_FLAGS);
-  if (flags & ~(F_GUARD | F_MODEL | F_OPEN)) return false;
+  if (flags & ~(F_GUARD | F_MODEL | F_OPEN | F_GNEAR | F_FCLUSTER)) return false;
   I.use_model = (flags & F_MODEL) ? 1 : 0;
   I.open = (flags & F_OPEN) ? 1 : 0;
-  if (I.open && I.use_model) return false;
+  I.gnear = (flags & F_GNEAR) ? 1 : 0;  // (F_FCLUSTER concerns compression only)
+  if ((I.open || I.gnear) && I.use_model) return false;
   if (ld64(h + H_MODEL) != (I.use_model ? kModelBytes : 0)) return false;
   I.Qhi = (long long)ld64(h + H_QHI);
   if (I.Qhi < 0 || I.Qhi >= (1ll << 29)) return false;
@@ -657,8 +658,8 @@ __global__ void __launch_bounds__(32 * W) k_scan_axis(const __grid_constant__ De
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
 __device__ __forceinline__ void recon_open(const DecArgs &A, double s2, long long K,
-                                           long long rho12_q, const int *q1, const int *q2s,
-                                           T *xo) {
+                                           long long rho12_q, bool near, const int *q1,
+                                           const int *q2s, T *xo) {
   const PlanView &pv = A.pv;
   const int64_t n = pv.n_v;
   const int nx = pv.nx;
@@ -672,15 +673,43 @@ __device__ __forceinline__ void recon_open(const DecArgs &A, double s2, long lon
     const float fy = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + p)), 0x1p-15f);
     const float fz =
         DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + p)), 0x1p-15f) : 0.0f;
-    int cor[8];
-    corner_codes<DIM>(q1, cl, nx, sxy, cor);
-    const double gq = interp64_codes<DIM>(cor, rho12_q, fx, fy, fz);
+    double gq;
+    if (near) {  // nearest-node g
+      const uint32_t m = nearest_node<DIM>(cl, __ldg(pv.frac + p), __ldg(pv.frac + n + p),
+                                           DIM == 3 ? __ldg(pv.frac + 2 * n + p) : 0u, nx, sxy);
+      gq = __dmul_rn((double)__ldg(q1 + m), __dmul_rn((double)rho12_q, 0x1p-40));
+    } else {
+      int cor[8];
+      corner_codes<DIM>(q1, cl, nx, sxy, cor);
+      gq = interp64_codes<DIM>(cor, rho12_q, fx, fy, fz);
+    }
     xo[p] = (T)__dmul_rn(s2, __dadd_rn((double)(K + (long long)q2), gq));
   }
 }
 
+// Closed loop with the nearest-node g: x' = s2 (K + P + q2), P =
+// round((s1/s2) q1[m]), one gather per vertex.
+template <int DIM, typename T>
+__device__ __forceinline__ void recon_nearest(const DecArgs &A, const DecInfo &I, const int *q1,
+                                              const int *q2s, T *xo) {
+  const PlanView &pv = A.pv;
+  const int64_t n = pv.n_v;
+  const int nx = pv.nx;
+  const int64_t sxy = (int64_t)pv.nx * pv.ny;
+  const int64_t stride = (int64_t)gridDim.y * blockDim.x;
+  for (int64_t p = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; p < n; p += stride) {
+    const int q2 = __ldg(q2s + p);
+    if (q2 == INT_MIN) continue;  // raw value already in place
+    const uint32_t m = nearest_node<DIM>(__ldg(pv.cell + p), __ldg(pv.frac + p),
+                                         __ldg(pv.frac + n + p),
+                                         DIM == 3 ? __ldg(pv.frac + 2 * n + p) : 0u, nx, sxy);
+    const long long P = rescale(__ldg(q1 + m), 0.0f, I.rho12_q, I.rho12_f);
+    xo[p] = (T)__dmul_rn(I.s2, (double)(I.K + P + (long long)q2));
+  }
+}
+
 template <int DIM, typename T, int U>
-__global__ void __launch_bounds__(256, U == 2 ? 6 : 4) k_recon(const __grid_constant__ DecArgs A) {
+__global__ void __launch_bounds__(256, U == 2 ? (DIM == 3 ? 5 : 6) : 4) k_recon(const __grid_constant__ DecArgs A) {
   pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.x);
@@ -694,7 +723,11 @@ __global__ void __launch_bounds__(256, U == 2 ? 6 : 4) k_recon(const __grid_cons
   if (*(volatile const unsigned int *)&st->err) return;
   const DecInfo I = *info;
   if (I.open) {
-    recon_open<DIM, T>(A, I.s2, I.K, I.rho12_q, q1, q2s, xo);
+    recon_open<DIM, T>(A, I.s2, I.K, I.rho12_q, I.gnear != 0, q1, q2s, xo);
+    return;
+  }
+  if (I.gnear) {
+    recon_nearest<DIM, T>(A, I, q1, q2s, xo);
     return;
   }
   const int64_t n = pv.n_v;
