@@ -622,6 +622,31 @@ def main():
         bounds[str(eb)] = {"compression_ratio": x_np.nbytes / size_b, "ms_per_step": ms_b,
                            "GBps": x_np.nbytes / (ms_b * 1e-3) / 1e9}
 
+    # the operators (Sec. III-B, III-C) on the same field: barycentric or
+    # cluster-mean f, bi/trilinear or nearest-node g, at the three bounds
+    operators = []
+    for eb in (1e-6, 1e-4, 1e-2):
+        for fop, gop in (("barycentric", "multilinear"), ("barycentric", "nearest"),
+                         ("cluster", "multilinear"), ("cluster", "nearest")):
+            prm_o = mcc.params_default(dtype=mcc.F64, eb=eb, grid_fraction=0.5, f_op=fop,
+                                       g_op=gop)
+            size_o = mcc.compress(plan, x, prm_o, wsc, out)
+            mcc.decompress(plan, out, size_o, y, wsd)
+            tau_o = eb * (float(x.max()) - float(x.min()))
+            err_o = float((y - x).abs().max())
+            if not err_o <= tau_o:
+                raise SystemExit(f"bound violated ({fop}, {gop}, {eb})")
+
+            def ostep(prm_o=prm_o):
+                mcc.compress(plan, x, prm_o, wsc, out, sync=False)
+                mcc.decompress(plan, out, cap, y, wsd, sync=False)
+
+            ms_o = time_replays(ostep, flush, max(5, args.steps // 4), args.warmup, stream)
+            operators.append({"eb_rel": eb, "f": fop, "g": gop,
+                              "compression_ratio": x_np.nbytes / size_o, "ms_per_step": ms_o,
+                              "GBps": x_np.nbytes / (ms_o * 1e-3) / 1e9,
+                              "max_abs_err_over_tau": err_o / tau_o})
+
     learned = batched_c4 = None
     if not args.no_learned:
         learned = learned_line(args, dev, flush, stream)
@@ -693,6 +718,7 @@ def main():
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": None if launches_per_step is None else int(round(launches_per_step * args.steps)),
         "other_bounds": bounds,
+        "operators": operators,
         "batched": batched,
         "learned": learned,
         "batched_c4": batched_c4,
