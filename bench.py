@@ -315,6 +315,48 @@ def learned_line(args, dev, flush, stream):
     return res
 
 
+def grid_init_line(args, dev, flush, stream, wl, x):
+    """Grid_Init (Algorithm 1) on the benchmark mesh: the grid from the
+    bottom k-th percentile of the edge extents (gmax 4096, delta 1), for
+    several k; ratio and compress+decompress rate at rel 1e-4 with the
+    default operators and with the paper's (cluster-mean f, nearest-node g).
+    The plan is built outside the timed region."""
+    import torch
+    import paper_2501_06910_gb300 as mcc
+    cd = torch.from_numpy(wl["coords"]).to(dev)
+    ed = torch.from_numpy(wl["cells"]).to(dev)
+    rows = []
+    for k in (30.0, 50.0, 70.0, 90.0, 99.0):
+        t0 = time.perf_counter()
+        n, lo, hi = mcc.grid_init(cd, ed, k, 1.0, 4096)
+        t_init = time.perf_counter() - t0
+        plan = mcc.plan_create(cd, ed, n, lo, hi)
+        for fop, gop in (("barycentric", "multilinear"), ("cluster", "nearest")):
+            prm = mcc.params_default(dtype=mcc.F64, eb=1e-4, grid_fraction=0.5, f_op=fop, g_op=gop)
+            wsc = plan.workspace(prm, "compress")
+            wsd = plan.workspace(prm, "decompress")
+            cap = mcc.compress_bound(plan, prm)
+            out = torch.empty(cap, dtype=torch.uint8, device=dev)
+            y = torch.empty_like(x)
+            size = mcc.compress(plan, x, prm, wsc, out)
+            mcc.decompress(plan, out, size, y, wsd)
+            tau = 1e-4 * (float(x.max()) - float(x.min()))
+            if not float((y - x).abs().max()) <= tau:
+                raise SystemExit(f"grid_init line: bound violated (k {k}, {fop}, {gop})")
+
+            def gstep(prm=prm, wsc=wsc, wsd=wsd, out=out, y=y, cap=cap):
+                mcc.compress(plan, x, prm, wsc, out, sync=False)
+                mcc.decompress(plan, out, cap, y, wsd, sync=False)
+
+            ms = time_replays(gstep, flush, 5, args.warmup, stream)
+            rows.append({"k_pct": k, "grid": list(n), "grid_init_s": t_init, "f": fop, "g": gop,
+                         "compression_ratio": x.numel() * 8 / size, "ms_per_step": ms,
+                         "GBps": x.numel() * 8 / (ms * 1e-3) / 1e9})
+            del wsc, wsd, out, y
+        plan.close()
+    return {"workload": wl["name"] + ", grid from Grid_Init (gmax 4096, delta 1)", "rows": rows}
+
+
 def batched_c4_line(args, dev, flush, stream):
     """Many variables x timesteps on one mesh: 1M-vertex 2D mesh, 4 variables
     x 64 timesteps of advected Gaussian bumps (FP64), per-variable rel bounds
@@ -413,6 +455,7 @@ def main():
     ap.add_argument("--batch", type=int, default=16, help="fields per step of the batched line")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-predictor line")
     ap.add_argument("--no-c4", action="store_true", help="skip the variables x timesteps line")
+    ap.add_argument("--no-grid-init", action="store_true", help="skip the Grid_Init line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -647,6 +690,10 @@ def main():
                               "GBps": x_np.nbytes / (ms_o * 1e-3) / 1e9,
                               "max_abs_err_over_tau": err_o / tau_o})
 
+    grid_init = None
+    if not args.no_grid_init and len(wl["n"]) == 2:
+        grid_init = grid_init_line(args, dev, flush, stream, wl, x)
+
     learned = batched_c4 = None
     if not args.no_learned:
         learned = learned_line(args, dev, flush, stream)
@@ -719,6 +766,7 @@ def main():
         "gpu_launches": None if launches_per_step is None else int(round(launches_per_step * args.steps)),
         "other_bounds": bounds,
         "operators": operators,
+        "grid_init": grid_init,
         "batched": batched,
         "learned": learned,
         "batched_c4": batched_c4,

@@ -156,6 +156,21 @@ void mcc_params_default(mcc_params *p);
  * the stream. The plan allocates and owns its device tables. */
 mcc_status mcc_plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, mcc_stream stream,
                            mcc_plan *out);
+
+/* Grid_Init (Algorithm 1): a grid layout for the mesh. For each axis d the
+ * spacing gs_d is the bottom k-th percentile, nearest rank (the
+ * ceil(k/100 N)-th smallest), of |p_a,d - p_b,d| over every edge of every
+ * cell (N = 3 n_cells edges in 2D, 6 n_cells in 3D; an edge shared by cells
+ * counts once per cell); while (max_d - min_d) / gs_d >= gmax, k grows by
+ * delta_pct (k carries over to the next axis, as the algorithm prints it).
+ * Writes n[d] = ceil((max_d - min_d) / gs_d) + 1 points and the corners
+ * lo = min, hi = max of the vertex coordinates to *out, ready for
+ * mcc_plan_create. k_pct in (0, 100], delta_pct > 0, gmax in [2, 32767].
+ * Synchronises the stream (the selection is host-driven, 8 passes per axis
+ * over the edges). MCC_ERR_RANGE when even k = 100 leaves gmax or more
+ * intervals; MCC_ERR_INVALID_ARG for invalid cells or a flat axis. */
+mcc_status mcc_grid_init(const mcc_mesh *mesh, double k_pct, double delta_pct, int32_t gmax,
+                         mcc_grid_spec *out, mcc_stream stream);
 void mcc_plan_destroy(mcc_plan plan);
 mcc_status mcc_plan_get_info(mcc_plan plan, mcc_plan_info *info);
 

@@ -73,6 +73,8 @@ def _load():
             lib = C.CDLL(build())
             P = C.c_void_p
             lib.orc_grid_resolve.argtypes = [C.c_int, C.c_int64, P, P, P, P, C.POINTER(_Grid)]
+            lib.orc_grid_init.argtypes = [C.c_int, C.c_int64, P, C.c_int64, P, C.c_double,
+                                          C.c_double, C.c_int32, P, P, P, P]
             lib.orc_point_in_simplex.argtypes = [C.POINTER(_Grid), P, P, P, P]
             lib.orc_locate.argtypes = [C.POINTER(_Grid), C.c_int64, P, C.c_int64, P, C.c_int, P]
             lib.orc_plan_tables.argtypes = [C.POINTER(_Grid), C.c_int64, P, P, P, P, P, P, P, P]
@@ -150,6 +152,20 @@ def locate(grid: Grid, coords, cells, brute=False):
     if st:
         raise OracleError(st, "locate")
     return owner
+
+
+def grid_init(coords, cells, k_pct, delta_pct=1.0, gmax=4096):
+    """Grid_Init (Algorithm 1): returns (n, lo, hi, gs) per axis."""
+    coords = _c(coords, np.float64)
+    cells = _c(cells, np.int32)
+    dim = coords.shape[1]
+    n = (C.c_int32 * 3)()
+    lo, hi, gs = (C.c_double * 3)(), (C.c_double * 3)(), (C.c_double * 3)()
+    st = _load().orc_grid_init(dim, coords.shape[0], _ptr(coords), cells.shape[0], _ptr(cells),
+                               C.c_double(k_pct), C.c_double(delta_pct), int(gmax), n, lo, hi, gs)
+    if st:
+        raise OracleError(st, "grid_init")
+    return tuple(n[:dim]), tuple(lo[:dim]), tuple(hi[:dim]), tuple(gs[:dim])
 
 
 class Plan:

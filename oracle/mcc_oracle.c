@@ -67,6 +67,73 @@ static double load_value(const void *x, int dtype, int64_t i) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Grid_Init (Algorithm 1): spacing per axis from the mesh                   */
+/* ------------------------------------------------------------------------ */
+static int cmp_f64(const void *a, const void *b) {
+  const double x = *(const double *)a, y = *(const double *)b;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Traverse the cells, take |p_a,d - p_b,d| for every edge of every cell (an
+ * edge shared by several cells counts once per cell, as the traversal meets
+ * it); gs_d is the bottom k-th percentile of these extents (nearest rank:
+ * the ceil(k/100 N)-th smallest); while (max_d - min_d) / gs_d reaches gmax,
+ * k grows by delta (k is not reset between axes, as Algorithm 1 prints it).
+ * Output: n_d = ceil((max_d - min_d) / gs_d) + 1 points per axis (spacing at
+ * most gs_d) and the corners min_d, max_d. ORC_ERR_RANGE when even k = 100
+ * leaves gmax or more nodes. */
+int orc_grid_init(int dim, int64_t n_v, const double *coords, int64_t n_c, const int32_t *cells,
+                  double k_pct, double delta_pct, int32_t gmax, int32_t n_out[3], double lo[3],
+                  double hi[3], double gs_out[3]) {
+  if (dim != 2 && dim != 3) return ORC_ERR_INVALID_ARG;
+  if (n_v < 1 || n_c < 1 || !coords || !cells) return ORC_ERR_INVALID_ARG;
+  if (!(k_pct > 0.0 && k_pct <= 100.0) || !(delta_pct > 0.0) || gmax < 2 || gmax > 32767)
+    return ORC_ERR_INVALID_ARG;
+  const int nvc = dim + 1, npair = dim == 2 ? 3 : 6;
+  for (int64_t i = 0; i < n_c * nvc; i++)
+    if (cells[i] < 0 || cells[i] >= n_v) return ORC_ERR_INVALID_ARG;
+  const int64_t N = n_c * npair;
+  double *ext = (double *)malloc(sizeof(double) * (size_t)N);
+  if (!ext) return ORC_ERR_OOM;
+  double k = k_pct;
+  for (int d = 0; d < 3; d++) { n_out[d] = 1; lo[d] = hi[d] = gs_out[d] = 0.0; }
+  for (int d = 0; d < dim; d++) {
+    double mn = coords[d], mx = coords[d];
+    for (int64_t i = 1; i < n_v; i++) {
+      const double c = coords[i * dim + d];
+      if (c < mn) mn = c;
+      if (c > mx) mx = c;
+    }
+    if (!(mn < mx)) { free(ext); return ORC_ERR_INVALID_ARG; }
+    int64_t e = 0;
+    for (int64_t c = 0; c < n_c; c++)
+      for (int a = 0; a < nvc; a++)
+        for (int b = a + 1; b < nvc; b++)
+          ext[e++] = fabs(coords[(int64_t)cells[c * nvc + a] * dim + d] -
+                          coords[(int64_t)cells[c * nvc + b] * dim + d]);
+    qsort(ext, (size_t)N, sizeof(double), cmp_f64);
+    double gs, gn;
+    for (;;) {
+      int64_t r = (int64_t)ceil(k / 100.0 * (double)N);
+      if (r < 1) r = 1;
+      if (r > N) r = N;
+      gs = ext[r - 1];
+      gn = gs > 0.0 ? (mx - mn) / gs : INFINITY;
+      if (gn < (double)gmax) break;
+      if (k >= 100.0) { free(ext); return ORC_ERR_RANGE; }
+      k = k + delta_pct;
+      if (k > 100.0) k = 100.0;
+    }
+    n_out[d] = (int32_t)ceil(gn) + 1;
+    lo[d] = mn;
+    hi[d] = mx;
+    gs_out[d] = gs;
+  }
+  free(ext);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* grid (Sec. IV-C: corners from the vertices' min / max per axis)           */
 /* ------------------------------------------------------------------------ */
 int orc_grid_resolve(int dim, int64_t n_v, const double *coords, const int32_t n[3],

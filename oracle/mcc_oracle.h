@@ -30,6 +30,14 @@ typedef struct {
   double lo[3], h[3], inv_h[3];
 } orc_grid;
 
+/* Grid_Init (Algorithm 1): points per axis from the bottom k-th percentile
+ * of the cells' edge extents along the axis, k raised by delta while the
+ * axis would have gmax or more intervals; corners from the vertices'
+ * min / max (see the definition in mcc_oracle.c). */
+int orc_grid_init(int dim, int64_t n_v, const double *coords, int64_t n_c, const int32_t *cells,
+                  double k_pct, double delta_pct, int32_t gmax, int32_t n_out[3], double lo[3],
+                  double hi[3], double gs_out[3]);
+
 /* Resolve the grid: lo/hi given, or the mesh bounding box when lo >= hi on
  * any axis (Sec. IV-C: corners from the vertex min / max). */
 int orc_grid_resolve(int dim, int64_t n_v, const double *coords,

@@ -98,6 +98,8 @@ def load():
             lib.mcc_status_string.argtypes = [C.c_int]
             lib.mcc_status_string.restype = C.c_char_p
             lib.mcc_plan_create.argtypes = [C.POINTER(_Mesh), C.POINTER(_GridSpec), P, C.POINTER(P)]
+            lib.mcc_grid_init.argtypes = [C.POINTER(_Mesh), C.c_double, C.c_double, C.c_int32,
+                                          C.POINTER(_GridSpec), P]
             lib.mcc_plan_destroy.argtypes = [P]
             lib.mcc_plan_destroy.restype = None
             lib.mcc_plan_get_info.argtypes = [P, C.POINTER(_PlanInfo)]
@@ -259,6 +261,18 @@ def plan_create(coords: torch.Tensor, cells: torch.Tensor, n, lo=None, hi=None,
     info = _PlanInfo()
     _check(load().mcc_plan_get_info(h, C.byref(info)), "plan_get_info")
     return Plan(h, info)
+
+
+def grid_init(coords: torch.Tensor, cells: torch.Tensor, k_pct: float, delta_pct: float = 1.0,
+              gmax: int = 4096, stream=None):
+    """mcc_grid_init (Algorithm 1): (n, lo, hi) per axis for plan_create from
+    the bottom k-th percentile of the cells' edge extents."""
+    dim = coords.shape[1]
+    m = _Mesh(dim, coords.shape[0], _dptr(coords).value, cells.shape[0], _dptr(cells).value)
+    g = _GridSpec()
+    _check(load().mcc_grid_init(C.byref(m), C.c_double(k_pct), C.c_double(delta_pct),
+                                C.c_int32(gmax), C.byref(g), _stream(stream)), "grid_init")
+    return tuple(g.n[:dim]), tuple(g.lo[:dim]), tuple(g.hi[:dim])
 
 
 def workspace_size(plan: Plan, params: Params):
