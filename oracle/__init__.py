@@ -73,6 +73,11 @@ def _load():
             lib = C.CDLL(build())
             P = C.c_void_p
             lib.orc_grid_resolve.argtypes = [C.c_int, C.c_int64, P, P, P, P, C.POINTER(_Grid)]
+            lib.orc_compress_bound_1d.argtypes = [C.c_int64, C.POINTER(_Params)]
+            lib.orc_compress_bound_1d.restype = C.c_size_t
+            lib.orc_compress_1d.argtypes = [C.c_int64, P, C.POINTER(_Params), P, C.c_size_t,
+                                            C.POINTER(C.c_size_t), P]
+            lib.orc_decompress_1d.argtypes = [C.c_int64, P, C.c_size_t, P]
             lib.orc_grid_init.argtypes = [C.c_int, C.c_int64, P, C.c_int64, P, C.c_double,
                                           C.c_double, C.c_int32, P, P, P, P]
             lib.orc_point_in_simplex.argtypes = [C.POINTER(_Grid), P, P, P, P]
@@ -283,6 +288,36 @@ def decompress(plan: Plan, stream, debug=False):
     if st:
         raise OracleError(st, "decompress")
     return (x, q1) if debug else x
+
+
+def compress_1d(x, debug=False, **kw):
+    """The paper's default: the vertex array in storage order through the
+    same coder in 1D. Returns the stream (and the codes Q when ``debug``)."""
+    x = np.ascontiguousarray(x)
+    if x.dtype not in (np.float64, np.float32):
+        raise TypeError("values must be float64 or float32")
+    p = make_params(x.dtype, **kw)
+    cap = int(_load().orc_compress_bound_1d(x.size, C.byref(p)))
+    out = np.zeros(cap, dtype=np.uint8)
+    size = C.c_size_t(0)
+    Q = np.empty(x.size, np.int32) if debug else None
+    st = _load().orc_compress_1d(x.size, _ptr(x), C.byref(p), _ptr(out), cap, C.byref(size),
+                                 _ptr(Q) if debug else None)
+    if st:
+        raise OracleError(st, "compress_1d")
+    out = out[: size.value].copy()
+    return (out, Q) if debug else out
+
+
+def decompress_1d(stream, n):
+    stream = np.ascontiguousarray(stream, dtype=np.uint8)
+    dtype = np.float32 if stream.size >= 16 and int(stream[12:16].view(np.uint32)[0]) == 1 \
+        else np.float64
+    x = np.empty(n, dtype=dtype)
+    st = _load().orc_decompress_1d(n, _ptr(stream), stream.size, _ptr(x))
+    if st:
+        raise OracleError(st, "decompress_1d")
+    return x
 
 
 # --------------------------------------------------------------------------- #

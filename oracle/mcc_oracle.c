@@ -1719,3 +1719,225 @@ int orc_mlp_quantize(int dim, int sx, const float *params, float max_z1, float m
   put_u32(model + 5728, (uint32_t)qbias(b3[0], a3 - t2));
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* the paper's "default": the same coder on the vertex array (Sec. V)        */
+/* ------------------------------------------------------------------------ */
+/* Spacing of the value type at magnitude M (at least the smallest
+ * subnormal): 2^(e - p) with M in [2^e, 2^(e+1)), p = 52 (FP64) or 23. */
+static double spacing_at(double M, int dtype) {
+  const int p = dtype == 0 ? 52 : 23;
+  const double tiny = dtype == 0 ? 0x1p-1074 : 0x1p-149;
+  if (!(M > 0.0)) return tiny;
+  int e;
+  frexp(M, &e); /* M = f 2^e, f in [0.5, 1): leading exponent e - 1 */
+  double u = ldexp(1.0, e - 1 - p);
+  return u > tiny ? u : tiny;
+}
+
+/* Per-field parameters of the 1D coder: tau as for the method, the bin
+ * s = 2 (tau - m) (1 - 2^-20) with the margin m = 4 u64(M) (+ 2 u32(M) for
+ * FP32 values), u the spacings at M = max |x|. The FP64 rounding of x / s
+ * and of s (K + Q) moves x' by at most about 3 u64(M) and the cast to FP32
+ * by at most u32(M), so |x - x'| <= tau at every value without a check and
+ * no value is stored raw (which would break the chain of differences). */
+static int field_params_1d(const orc_params *p, int64_t n, const void *x, orc_field *f) {
+  memset(f, 0, sizeof(*f));
+  if (n <= 0 || !x) return ORC_ERR_INVALID_ARG;
+  if (p->dtype != 0 && p->dtype != 1) return ORC_ERR_INVALID_ARG;
+  if (!(p->eb > 0.0) || !isfinite(p->eb)) return ORC_ERR_INVALID_ARG;
+  double lo = load_value(x, p->dtype, 0), hi = lo;
+  for (int64_t i = 0; i < n; i++) {
+    double v = load_value(x, p->dtype, i);
+    if (!isfinite(v)) return ORC_ERR_INVALID_ARG;
+    if (v < lo) lo = v;
+    if (v > hi) hi = v;
+  }
+  f->lo = lo;
+  f->hi = hi;
+  f->M = fabs(lo) > fabs(hi) ? fabs(lo) : fabs(hi);
+  double tau = p->eb;
+  if (p->eb_mode == 1 && hi > lo) tau = p->eb * (hi - lo);
+  f->tau = tau;
+  double m = 4.0 * spacing_at(f->M, 0);
+  if (p->dtype == 1) m = m + 2.0 * spacing_at(f->M, 1);
+  const double t = tau - m;
+  if (!isfinite(tau) || !(t >= 1e-290)) return ORC_ERR_RANGE;
+  f->tau1 = t;
+  f->tau2 = t;
+  f->s1 = (2.0 * t) * BIN_SHRINK;
+  f->s2 = f->s1;
+  if (!isfinite(f->s2)) return ORC_ERR_RANGE;
+  f->inv2 = 1.0 / f->s2;
+  double kd = rint(lo * f->inv2);
+  double hd = rint(hi * f->inv2);
+  if (!(fabs(kd) < 4611686018427387904.0) || !(fabs(hd) < 4611686018427387904.0))
+    return ORC_ERR_RANGE;
+  f->K = (int64_t)kd;
+  f->Qhi = (int64_t)hd - f->K;
+  if (f->Qhi >= ((int64_t)1 << 29)) return ORC_ERR_RANGE;
+  f->rho21_q = f->rho12_q = (int64_t)1 << 40; /* one bin: ratio 1 */
+  f->rho21_f = f->rho12_f = 1.0f;
+  return ORC_OK;
+}
+
+size_t orc_compress_bound_1d(int64_t n, const orc_params *p) {
+  size_t vsz = p->dtype == 0 ? 8 : 4;
+  int64_t g1 = ngroups(n, p->C1);
+  uint64_t w1 = (uint64_t)((n * p->lmax + 31) / 32 + g1);
+  layout_t L;
+  make_layout(p->R1, p->R2, g1, 0, (uint64_t)n, 0, 0, vsz, w1, 0, 0, &L);
+  (void)vsz;
+  return L.total + 16;
+}
+
+/* Q = round(x / s) - K; delta_i = Q_i - Q_(i-1) (delta_0 = Q_0); symbols
+ * delta + R1 or an escape; canonical Huffman; the grid component's
+ * lane-group stream with the residual component empty. Header: dim 1,
+ * n_x = n, flags bit 5. */
+int orc_compress_1d(int64_t n, const void *x, const orc_params *p, uint8_t *out, size_t capacity,
+                    size_t *out_size, int32_t *Q_dbg) {
+  if (!out_size) return ORC_ERR_INVALID_ARG;
+  *out_size = 0;
+  int st = check_params(p);
+  if (st) return st;
+  if (p->model || p->open_loop || p->f_op || p->g_op) return ORC_ERR_INVALID_ARG;
+  if (n >= ((int64_t)1 << 31)) return ORC_ERR_INVALID_ARG;
+  orc_field f;
+  if ((st = field_params_1d(p, n, x, &f))) return st;
+  const int R1 = p->R1, R2 = p->R2;
+  const size_t vsz = p->dtype == 0 ? 8 : 4;
+  int32_t *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t *dl = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  uint16_t *sym = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
+  uint64_t *h1 = (uint64_t *)calloc((size_t)2 * R1, sizeof(uint64_t));
+  uint8_t *len1 = (uint8_t *)calloc((size_t)2 * R1, 1), *len2 = (uint8_t *)calloc((size_t)2 * R2, 1);
+  uint32_t *code1 = (uint32_t *)calloc((size_t)2 * R1, 4);
+  if (!Q || !dl || !sym || !h1 || !len1 || !len2 || !code1) { st = ORC_ERR_OOM; goto done; }
+  for (int64_t i = 0; i < n; i++)
+    Q[i] = (int32_t)((int64_t)rint(load_value(x, p->dtype, i) * f.inv2) - f.K);
+  uint64_t nout1 = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const int32_t d = wrap_sub(Q[i], i ? Q[i - 1] : 0);
+    dl[i] = d;
+    if (d >= -(R1 - 1) && d <= R1 - 2) sym[i] = (uint16_t)(d + R1);
+    else { sym[i] = 0; nout1++; }
+    h1[sym[i]]++;
+  }
+  if ((st = orc_huffman_lengths(h1, 2 * R1, p->lmax, len1))) goto done;
+  orc_canonical_codes(len1, 2 * R1, code1);
+  {
+    const int64_t g1 = ngroups(n, p->C1);
+    const uint64_t w1 = pack_component(sym, n, p->C1, len1, code1, NULL, NULL, NULL, NULL, 0xFFFF, NULL);
+    layout_t L;
+    make_layout(R1, R2, g1, 0, nout1, 0, 0, vsz, w1, 0, 0, &L);
+    *out_size = L.total;
+    if (L.total > capacity || !out) { st = ORC_ERR_CAPACITY; goto done; }
+    memset(out, 0, L.total);
+    uint8_t *h = out;
+    put_u32(h + 0, MAGIC);
+    put_u32(h + 4, VERSION);
+    put_u32(h + 8, HEADER_BYTES);
+    put_u32(h + 12, (uint32_t)p->dtype);
+    put_u32(h + 16, 1u);
+    put_u32(h + 20, 32u);
+    put_u32(h + 24, (uint32_t)R1);
+    put_u32(h + 28, (uint32_t)R2);
+    put_u32(h + 32, (uint32_t)p->C1);
+    put_u32(h + 36, (uint32_t)p->C2);
+    put_u32(h + 40, (uint32_t)p->lmax);
+    put_u32(h + 44, (uint32_t)n);
+    put_u32(h + 48, 1u);
+    put_u32(h + 52, 1u);
+    put_u64(h + 56, (uint64_t)n);
+    put_u64(h + 64, (uint64_t)n);
+    put_f64(h + 72, f.tau);
+    put_f64(h + 80, f.tau1);
+    put_f64(h + 88, f.tau2);
+    put_f64(h + 96, f.s1);
+    put_f64(h + 104, f.s2);
+    put_u64(h + 112, (uint64_t)f.K);
+    put_u64(h + 120, (uint64_t)f.rho21_q);
+    put_u64(h + 128, (uint64_t)f.rho12_q);
+    put_u64(h + 136, 0);
+    put_u64(h + 144, nout1);
+    put_u64(h + 152, 0);
+    put_u64(h + 160, 0);
+    put_u64(h + 168, w1);
+    put_u64(h + 176, 0);
+    put_u64(h + 184, (uint64_t)L.total);
+    put_u64(h + 192, 0);
+    put_u64(h + 200, (uint64_t)f.Qhi);
+    memcpy(out + L.lens1, len1, (size_t)2 * R1);
+    memcpy(out + L.lens2, len2, (size_t)2 * R2);
+    pack_component(sym, n, p->C1, len1, code1, (uint32_t *)(out + L.gtab1), out + L.ltab1,
+                   (uint32_t *)(out + L.etab1), NULL, 0xFFFF, (uint32_t *)(out + L.bits1));
+    put_u32(out + L.gtab2, 0);  /* the empty residual component: one zero entry per table */
+    put_u32(out + L.etab2, 0);
+    put_u32(out + L.rtab2, 0);
+    uint64_t k1 = 0;
+    for (int64_t i = 0; i < n; i++)
+      if (sym[i] == 0) put_u32(out + L.out1 + 4 * k1++, (uint32_t)dl[i]);
+  }
+  if (Q_dbg) memcpy(Q_dbg, Q, sizeof(int32_t) * (size_t)n);
+done:
+  free(Q); free(dl); free(sym); free(h1); free(len1); free(len2); free(code1);
+  return st;
+}
+
+/* Inverse: decode the differences, prefix sums (wrapping int32) give Q,
+ * x' = cast(s (K + Q)). */
+int orc_decompress_1d(int64_t n, const uint8_t *in, size_t size, void *xout) {
+  if (!in || size < HEADER_BYTES) return ORC_ERR_CORRUPT;
+  if (get_u32(in) != MAGIC || get_u32(in + 4) != VERSION || get_u32(in + 8) != HEADER_BYTES)
+    return ORC_ERR_CORRUPT;
+  const int dtype = (int)get_u32(in + 12);
+  const int R1 = (int)get_u32(in + 24), R2 = (int)get_u32(in + 28);
+  const int C1 = (int)get_u32(in + 32), C2 = (int)get_u32(in + 36), lmax = (int)get_u32(in + 40);
+  if (dtype != 0 && dtype != 1) return ORC_ERR_CORRUPT;
+  if (get_u32(in + 16) != 1u || get_u32(in + 20) != 32u) return ORC_ERR_CORRUPT;
+  if (get_u32(in + 44) != (uint32_t)n || get_u32(in + 48) != 1u || get_u32(in + 52) != 1u ||
+      (int64_t)get_u64(in + 56) != n || (int64_t)get_u64(in + 64) != n)
+    return ORC_ERR_CORRUPT;
+  orc_params chk = {dtype, 0, 1.0, 0.5, R1, R2, C1, C2, lmax, NULL, 0};
+  if (check_params(&chk)) return ORC_ERR_CORRUPT;
+  const double s = get_f64(in + 104);
+  const int64_t K = (int64_t)get_u64(in + 112);
+  const uint64_t nout1 = get_u64(in + 144), w1 = get_u64(in + 168), total = get_u64(in + 184);
+  if (get_u64(in + 152) || get_u64(in + 160) || get_u64(in + 176) || get_u64(in + 192))
+    return ORC_ERR_CORRUPT;
+  if (nout1 > (uint64_t)n || w1 > (uint64_t)n * 24 + 64) return ORC_ERR_CORRUPT;
+  if (!(s > 0.0) || !isfinite(s)) return ORC_ERR_CORRUPT;
+  const size_t vsz = dtype == 0 ? 8 : 4;
+  layout_t L;
+  make_layout(R1, R2, ngroups(n, C1), 0, nout1, 0, 0, vsz, w1, 0, 0, &L);
+  if (L.total != total || total > size) return ORC_ERR_CORRUPT;
+  uint16_t *sym = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
+  int st = ORC_OK;
+  if (!sym) return ORC_ERR_OOM;
+  if ((st = unpack_component(in, size, &L, 1, n, C1, 2 * R1, lmax, w1, sym))) goto done;
+  {
+    uint64_t k = 0;
+    uint32_t q = 0;
+    for (int64_t i = 0; i < n; i++) {
+      int32_t d;
+      if (sym[i] == 0) {
+        if (k >= nout1) { st = ORC_ERR_CORRUPT; goto done; }
+        d = (int32_t)get_u32(in + L.out1 + 4 * k++);
+      } else if (sym[i] == 2 * R1 - 1) {
+        st = ORC_ERR_CORRUPT;
+        goto done;
+      } else {
+        d = (int32_t)sym[i] - R1;
+      }
+      q += (uint32_t)d;
+      const double xr = s * (double)(K + (int64_t)(int32_t)q);
+      if (dtype == 0) ((double *)xout)[i] = xr;
+      else ((float *)xout)[i] = (float)xr;
+    }
+    if (k != nout1) st = ORC_ERR_CORRUPT;
+  }
+done:
+  free(sym);
+  return st;
+}

@@ -139,6 +139,16 @@ int orc_mlp_grad(const float *W1, const float *b1, const float *W2, const float 
 int orc_mlp_quantize(int dim, int sx, const float *params, float max_z1, float max_z2,
                      uint8_t *model);
 
+/* ---- the paper's default: the same coder on the vertex array ----------- */
+/* The vertex values in storage order as one 1D array (the paper's "default"
+ * serialisation, Sec. V): Q = round(x / s) - K, 1D Lorenzo differences,
+ * the grid component's coder; the bin keeps a margin for the rounding so
+ * that no value is stored raw (see mcc_oracle.c). Header dim 1, flag bit 5. */
+size_t orc_compress_bound_1d(int64_t n, const orc_params *p);
+int orc_compress_1d(int64_t n, const void *x, const orc_params *p, uint8_t *out, size_t capacity,
+                    size_t *out_size, int32_t *Q_dbg);
+int orc_decompress_1d(int64_t n, const uint8_t *in, size_t size, void *xout);
+
 #ifdef __cplusplus
 }
 #endif
