@@ -690,6 +690,45 @@ def main():
                               "GBps": x_np.nbytes / (ms_o * 1e-3) / 1e9,
                               "max_abs_err_over_tau": err_o / tau_o})
 
+    # the paper's default baseline (Sec. V): the same coder on the vertex
+    # array in 1D, in storage order (shuffled ids) and in Morton order of the
+    # vertex positions (a file with spatial locality); the improvement is the
+    # method's ratio over it at the same bound
+    default_1d = []
+    orders = [("storage", None)]
+    if len(wl["n"]) == 2:
+        cxy = wl["coords"]
+        lo_c, span_c = cxy.min(axis=0), np.maximum(np.ptp(cxy, axis=0), 1e-300)
+        kk = np.minimum(((cxy - lo_c) / span_c * 65535.0).astype(np.int64), 65535)
+        orders.append(("morton", np.argsort(synth._morton2(kk[:, 0], kk[:, 1]), kind="stable")))
+    mc_ratio = {1e-6: bounds["1e-06"]["compression_ratio"], 1e-4: x_np.nbytes / size,
+                1e-2: bounds["0.01"]["compression_ratio"]}
+    for oname, perm in orders:
+        xo_d = x if perm is None else torch.from_numpy(np.ascontiguousarray(x_np[perm])).to(dev)
+        for eb in (1e-6, 1e-4, 1e-2):
+            prm_1 = mcc.params_default(dtype=mcc.F64, eb=eb)
+            s1 = mcc.compress_1d(xo_d, prm_1)
+            y1 = torch.empty_like(xo_d)
+            mcc.decompress_1d(s1, y1)
+            tau_1 = eb * (float(xo_d.max()) - float(xo_d.min()))
+            if not float((y1 - xo_d).abs().max()) <= tau_1:
+                raise SystemExit(f"1D coder: bound violated ({oname}, {eb})")
+            ws1c, ws1d = mcc.workspace_size_1d(xo_d.numel(), prm_1)
+            w1c = torch.empty(ws1c, dtype=torch.uint8, device=dev)
+            w1d = torch.empty(ws1d, dtype=torch.uint8, device=dev)
+            o1 = torch.empty(mcc.compress_bound_1d(xo_d.numel(), prm_1), dtype=torch.uint8, device=dev)
+
+            def step1(prm_1=prm_1, xo_d=xo_d, y1=y1, w1c=w1c, w1d=w1d, o1=o1):
+                mcc.compress_1d_into(xo_d, prm_1, w1c, o1, sync=False)
+                mcc.decompress_1d_into(o1, o1.numel(), y1, w1d, sync=False)
+
+            ms_1 = time_replays(step1, flush, max(5, args.steps // 4), args.warmup, stream)
+            r1 = x_np.nbytes / s1.numel()
+            default_1d.append({"order": oname, "eb_rel": eb, "compression_ratio": r1,
+                               "ms_per_step": ms_1, "GBps": x_np.nbytes / (ms_1 * 1e-3) / 1e9,
+                               "method_ratio": mc_ratio[eb], "improvement": mc_ratio[eb] / r1})
+            del w1c, w1d, o1
+
     grid_init = None
     if not args.no_grid_init and len(wl["n"]) == 2:
         grid_init = grid_init_line(args, dev, flush, stream, wl, x)
@@ -766,6 +805,7 @@ def main():
         "gpu_launches": None if launches_per_step is None else int(round(launches_per_step * args.steps)),
         "other_bounds": bounds,
         "operators": operators,
+        "default_1d": default_1d,
         "grid_init": grid_init,
         "batched": batched,
         "learned": learned,

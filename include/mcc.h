@@ -239,6 +239,31 @@ mcc_status mcc_decompress_batch(mcc_plan plan, int n, const void *d_in, size_t s
                                 void *d_workspace, size_t workspace_bytes, int sync,
                                 mcc_stream stream);
 
+/* ---- the paper's default baseline: the 1D coder on the vertex array ------
+ * The paper compares the multi-component method with its "default": the
+ * vertex values serialised in storage order into a 1D array and compressed
+ * by the same compressor (Sec. V). Here: the grid component's coder in one
+ * dimension, with no plan and no residual component: Q = round(x / s) - K,
+ * differences delta_i = Q_i - Q_(i-1) (delta_0 = Q_0) coded as symbols
+ * delta + R1 or escapes, canonical Huffman, the same lane-group stream
+ * (header dim 1, n_x = n, flags = 32). The bin is s = 2 (tau - m)(1 - 2^-20)
+ * with the margin m = 4 u64(M) (+ 2 u32(M) for FP32 values), u the value
+ * type's spacing at M = max |x|: the roundings of x / s, of s (K + Q) and of
+ * the cast stay inside it, so |x - x'| <= tau at every value and no value is
+ * stored raw. MCC_ERR_RANGE when tau <= m or the codes exceed 2^29 bins.
+ * Parameters as for the method (R1, C1, lmax, dtype, eb_mode, eb; R2 and C2
+ * are recorded); predictor, loop and operators must be the defaults. The
+ * buffers follow the rules of mcc_compress / mcc_decompress. */
+mcc_status mcc_workspace_size_1d(int64_t n, const mcc_params *p, size_t *compress_bytes,
+                                 size_t *decompress_bytes);
+mcc_status mcc_compress_bound_1d(int64_t n, const mcc_params *p, size_t *max_bytes);
+mcc_status mcc_compress_1d(const void *d_values, int64_t n, const mcc_params *p,
+                           void *d_workspace, size_t workspace_bytes, void *d_out,
+                           size_t capacity, size_t *out_size, mcc_stream stream);
+mcc_status mcc_decompress_1d(const void *d_in, size_t in_bytes, void *d_values, int64_t n,
+                             int dtype, void *d_workspace, size_t workspace_bytes, int sync,
+                             mcc_stream stream);
+
 /* Decompression without any device allocation (the paper has no counterpart;
  * this serves callers that cannot call cudaMalloc, e.g. code that must stay
  * inside a memory budget owned by another allocator, or a plugin handed only

@@ -98,6 +98,12 @@ def load():
             lib.mcc_status_string.argtypes = [C.c_int]
             lib.mcc_status_string.restype = C.c_char_p
             lib.mcc_plan_create.argtypes = [C.POINTER(_Mesh), C.POINTER(_GridSpec), P, C.POINTER(P)]
+            lib.mcc_workspace_size_1d.argtypes = [C.c_int64, C.POINTER(Params), C.POINTER(S),
+                                                  C.POINTER(S)]
+            lib.mcc_compress_bound_1d.argtypes = [C.c_int64, C.POINTER(Params), C.POINTER(S)]
+            lib.mcc_compress_1d.argtypes = [P, C.c_int64, C.POINTER(Params), P, S, P, S,
+                                            C.POINTER(S), P]
+            lib.mcc_decompress_1d.argtypes = [P, S, P, C.c_int64, C.c_int, P, S, C.c_int, P]
             lib.mcc_grid_init.argtypes = [C.POINTER(_Mesh), C.c_double, C.c_double, C.c_int32,
                                           C.POINTER(_GridSpec), P]
             lib.mcc_plan_destroy.argtypes = [P]
@@ -273,6 +279,60 @@ def grid_init(coords: torch.Tensor, cells: torch.Tensor, k_pct: float, delta_pct
     _check(load().mcc_grid_init(C.byref(m), C.c_double(k_pct), C.c_double(delta_pct),
                                 C.c_int32(gmax), C.byref(g), _stream(stream)), "grid_init")
     return tuple(g.n[:dim]), tuple(g.lo[:dim]), tuple(g.hi[:dim])
+
+
+def workspace_size_1d(n: int, params: Params):
+    """(compress, decompress) workspace bytes of the 1D coder for n values."""
+    cb, db = C.c_size_t(), C.c_size_t()
+    _check(load().mcc_workspace_size_1d(n, C.byref(params), C.byref(cb), C.byref(db)),
+           "workspace_size_1d")
+    return cb.value, db.value
+
+
+def compress_bound_1d(n: int, params: Params) -> int:
+    b = C.c_size_t()
+    _check(load().mcc_compress_bound_1d(n, C.byref(params), C.byref(b)), "compress_bound_1d")
+    return b.value
+
+
+def compress_1d_into(x: torch.Tensor, params: Params, workspace: torch.Tensor, out: torch.Tensor,
+                     sync: bool = True, stream=None):
+    """mcc_compress_1d (the paper's default baseline): the values in storage
+    order through the 1D coder into ``out``; returns the size when ``sync``
+    (without it the call only enqueues, so it can be graph-captured)."""
+    size = C.c_size_t()
+    _check(load().mcc_compress_1d(_dptr(x), x.numel(), C.byref(params), _dptr(workspace),
+                                  workspace.numel(), _dptr(out), out.numel(),
+                                  C.byref(size) if sync else None, _stream(stream)), "compress_1d")
+    return size.value if sync else None
+
+
+def decompress_1d_into(stream_bytes: torch.Tensor, nbytes: int, out: torch.Tensor,
+                       workspace: torch.Tensor, sync: bool = True, stream=None):
+    """mcc_decompress_1d into ``out`` (n values of the stream's type)."""
+    dtype = F64 if out.dtype == torch.float64 else F32
+    _check(load().mcc_decompress_1d(_dptr(stream_bytes), int(nbytes), _dptr(out), out.numel(), dtype,
+                                    _dptr(workspace), workspace.numel(), 1 if sync else 0,
+                                    _stream(stream)), "decompress_1d")
+    return out
+
+
+def compress_1d(x: torch.Tensor, params: Params, stream=None):
+    """compress_1d_into with its own workspace and output; returns the stream
+    as a uint8 CUDA tensor."""
+    cb, _ = workspace_size_1d(x.numel(), params)
+    ws = torch.empty(cb, dtype=torch.uint8, device=x.device)
+    out = torch.empty(compress_bound_1d(x.numel(), params), dtype=torch.uint8, device=x.device)
+    size = compress_1d_into(x, params, ws, out, True, stream)
+    return out[:size]
+
+
+def decompress_1d(stream_bytes: torch.Tensor, out: torch.Tensor, stream=None):
+    """decompress_1d_into with its own workspace."""
+    prm = params_default(dtype=F64 if out.dtype == torch.float64 else F32)
+    _, db = workspace_size_1d(out.numel(), prm)
+    ws = torch.empty(db, dtype=torch.uint8, device=out.device)
+    return decompress_1d_into(stream_bytes, stream_bytes.numel(), out, ws, True, stream)
 
 
 def workspace_size(plan: Plan, params: Params):

@@ -211,3 +211,84 @@ extern "C" mcc_status mcc_decompress_batch(mcc_plan plan, int n, const void *d_i
   }
   return MCC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// the paper's default baseline: the 1D coder on the vertex array
+// ---------------------------------------------------------------------------
+static PlanView plan_view_1d(int64_t n) {
+  PlanView pv;
+  memset(&pv, 0, sizeof(pv));
+  pv.dim = 1;
+  pv.nx = (int32_t)n;
+  pv.ny = pv.nz = 1;
+  pv.n_v = pv.n_g = n;
+  return pv;
+}
+
+static mcc_status check_1d(int64_t n, const mcc_params *p) {
+  if (n < 1 || n >= ((int64_t)1 << 31)) return MCC_ERR_INVALID_ARG;
+  const mcc_status s = check_params(p);
+  if (s) return s;
+  if (p->predictor != MCC_PRED_ZERO || p->loop != MCC_LOOP_CLOSED ||
+      p->f_op != MCC_F_BARYCENTRIC || p->g_op != MCC_G_MULTILINEAR)
+    return MCC_ERR_INVALID_ARG;
+  return MCC_OK;
+}
+
+extern "C" mcc_status mcc_workspace_size_1d(int64_t n, const mcc_params *p, size_t *cbytes,
+                                            size_t *dbytes) {
+  const mcc_status s = check_1d(n, p);
+  if (s) return s;
+  const PlanView pv = plan_view_1d(n);
+  if (cbytes) *cbytes = compress_ws_layout(pv, p).total;
+  if (dbytes) *dbytes = decompress_ws_layout(pv).total;
+  return MCC_OK;
+}
+
+extern "C" mcc_status mcc_compress_bound_1d(int64_t n, const mcc_params *p, size_t *max_bytes) {
+  if (!max_bytes) return MCC_ERR_INVALID_ARG;
+  const mcc_status s = check_1d(n, p);
+  if (s) return s;
+  const int64_t ng1 = ngroups(n, p->C1);
+  const uint64_t w1 = (uint64_t)((n * p->lmax + 31) / 32 + ng1);
+  const Layout L = make_layout(p->R1, p->R2, ng1, 0, (uint64_t)n, 0, 0, 8, w1, 0, 0);
+  *max_bytes = L.total + 16;
+  return MCC_OK;
+}
+
+extern "C" mcc_status mcc_compress_1d(const void *d_values, int64_t n, const mcc_params *p,
+                                      void *d_ws, size_t ws_bytes, void *d_out, size_t capacity,
+                                      size_t *out_size, mcc_stream s) {
+  if (!d_values || !d_ws || !d_out) return MCC_ERR_INVALID_ARG;
+  mcc_status st = check_1d(n, p);
+  if (st) return st;
+  if (((uintptr_t)d_out & 7) || ((uintptr_t)d_ws & 255) ||
+      ((uintptr_t)d_values & (p->dtype == MCC_F64 ? 7 : 3)))
+    return MCC_ERR_INVALID_ARG;
+  const PlanView pv = plan_view_1d(n);
+  if (ws_bytes < compress_ws_layout(pv, p).total) return MCC_ERR_CAPACITY;
+  cudaStream_t stream = (cudaStream_t)s;
+  st = launch_compress(pv, d_values, p, (unsigned char *)d_ws, (unsigned char *)d_out, capacity, stream);
+  if (st) return st;
+  if (out_size) return read_status(d_ws, stream, out_size);
+  return MCC_OK;
+}
+
+extern "C" mcc_status mcc_decompress_1d(const void *d_in, size_t in_bytes, void *d_values, int64_t n,
+                                        int dtype, void *d_ws, size_t ws_bytes, int sync,
+                                        mcc_stream s) {
+  if (!d_in || !d_values || !d_ws) return MCC_ERR_INVALID_ARG;
+  if (n < 1 || n >= ((int64_t)1 << 31)) return MCC_ERR_INVALID_ARG;
+  if (dtype != MCC_F64 && dtype != MCC_F32) return MCC_ERR_INVALID_ARG;
+  if (((uintptr_t)d_in & 3) || ((uintptr_t)d_ws & 255) ||
+      ((uintptr_t)d_values & (dtype == MCC_F64 ? 7 : 3)))
+    return MCC_ERR_INVALID_ARG;
+  const PlanView pv = plan_view_1d(n);
+  if (ws_bytes < decompress_ws_layout(pv).total) return MCC_ERR_CAPACITY;
+  cudaStream_t stream = (cudaStream_t)s;
+  const mcc_status st = launch_decompress(pv, (const unsigned char *)d_in, in_bytes, d_values, dtype,
+                                          (unsigned char *)d_ws, stream);
+  if (st) return st;
+  if (sync) return read_status(d_ws, stream, nullptr);
+  return MCC_OK;
+}

@@ -46,7 +46,7 @@ enum : uint32_t {
   H_W1 = 168, H_W2 = 176, H_TOTAL = 184, H_MODEL = 192, H_QHI = 200
 };
 // header flags
-enum : uint32_t { F_GUARD = 1, F_MODEL = 2, F_OPEN = 4, F_GNEAR = 8, F_FCLUSTER = 16 };
+enum : uint32_t { F_GUARD = 1, F_MODEL = 2, F_OPEN = 4, F_GNEAR = 8, F_FCLUSTER = 16, F_ONED = 32 };
 
 __host__ __device__ inline uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 __host__ __device__ inline int64_t ngroups(int64_t n, int C) {

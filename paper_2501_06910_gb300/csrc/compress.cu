@@ -37,6 +37,7 @@ constexpr int kRawNone = 0xFFFF;
 struct RParams {
   int dtype, eb_mode;
   double eb, frac;
+  int one_d;  // the 1D coder (the paper's default baseline)
 };
 
 // Arguments shared by every compression kernel of one launch chain: the plan,
@@ -58,6 +59,7 @@ struct CompArgs {
   unsigned char open[kMaxBatch];          // MCC_LOOP_OPEN per field
   unsigned char fop[kMaxBatch], gop[kMaxBatch];  // MCC_F_* / MCC_G_* per field
   int any_auto;
+  int one_d;  // the 1D coder: component 1 holds the vertex codes' differences
 };
 
 // Per-field pointers into the workspace and the output slot.
@@ -120,6 +122,49 @@ __device__ __forceinline__ unsigned long long value_bits(double v) {
 // k_reduce: min / max of x (ordered integer keys, no FP64 compares), finite
 // check, and -- in the last block to finish -- the per-field parameters.
 // ---------------------------------------------------------------------------
+// Spacing of the value type at magnitude M (at least the smallest
+// subnormal): 2^(e - p) with M in [2^e, 2^(e+1)), p = 52 (FP64) or 23.
+__device__ double spacing_at(double M, int dtype) {
+  const int p = dtype == MCC_F64 ? 52 : 23;
+  const double tiny = dtype == MCC_F64 ? 0x1p-1074 : 0x1p-149;
+  if (!(M > 0.0)) return tiny;
+  int e;
+  frexp(M, &e);  // M = f 2^e, f in [0.5, 1)
+  const double u = ldexp(1.0, e - 1 - p);
+  return u > tiny ? u : tiny;
+}
+
+// The 1D coder's parameters: bin s = 2 (tau - m) (1 - 2^-20), m = 4 u64(M)
+// (+ 2 u32(M) for FP32 values): the FP64 roundings of x / s and s (K + Q)
+// and the cast stay inside the margin, so every value holds the bound and
+// none is stored raw.
+__device__ void field_params_1d(Status *st, FieldParams &f, double tau, int dtype) {
+  double m = __dmul_rn(4.0, spacing_at(f.M, MCC_F64));
+  if (dtype == MCC_F32) m = __dadd_rn(m, __dmul_rn(2.0, spacing_at(f.M, MCC_F32)));
+  const double t = __dsub_rn(tau, m);
+  if (!isfinite(tau) || !(t >= 1e-290)) { set_error(st, MCC_ERR_RANGE); return; }
+  f.tau1 = t;
+  f.tau2 = t;
+  f.s1 = __dmul_rn(__dmul_rn(2.0, t), kBinShrink);
+  f.s2 = f.s1;
+  if (!isfinite(f.s2)) { set_error(st, MCC_ERR_RANGE); return; }
+  f.inv2 = __ddiv_rn(1.0, f.s2);
+  const double kd = rint(__dmul_rn(f.lo, f.inv2));
+  const double hd = rint(__dmul_rn(f.hi, f.inv2));
+  if (!(fabs(kd) < 4611686018427387904.0) || !(fabs(hd) < 4611686018427387904.0)) {
+    set_error(st, MCC_ERR_RANGE);
+    return;
+  }
+  f.K = (long long)kd;
+  f.Qhi = (long long)hd - f.K;
+  if (f.Qhi >= (1ll << 29)) { set_error(st, MCC_ERR_RANGE); return; }
+  f.fill_u = 0;
+  f.rho21_q = f.rho12_q = 1ll << kRhoBits;  // one bin: ratio 1
+  f.rho21_f = f.rho12_f = 1.0f;
+  f.guard = 0;
+  st->f = f;
+}
+
 __device__ void field_params(Status *st, RParams rp) {
   FieldParams f;
   memset(&f, 0, sizeof(f));
@@ -132,6 +177,10 @@ __device__ void field_params(Status *st, RParams rp) {
   double tau = rp.eb;
   if (rp.eb_mode == 1 && hi > lo) tau = __dmul_rn(rp.eb, __dsub_rn(hi, lo));
   f.tau = tau;
+  if (rp.one_d) {
+    field_params_1d(st, f, tau, rp.dtype);
+    return;
+  }
   f.tau1 = __dmul_rn(rp.frac, tau);
   f.tau2 = __dmul_rn(__dsub_rn(1.0, rp.frac), tau);
   if (!isfinite(tau) || !(f.tau1 >= 1e-290) || !(f.tau2 >= 1e-290)) { set_error(st, MCC_ERR_RANGE); return; }
@@ -305,6 +354,48 @@ __global__ void __launch_bounds__(256) k_prequant(const __grid_constant__ CompAr
     const double v = (double)__ldg(x + i);
     Q[i] = (int)(__double2ll_rn(__dmul_rn(v, inv2)) - K);
   }
+}
+
+// ---------------------------------------------------------------------------
+// k_delta1d: the 1D coder's symbols, delta_i = Q_i - Q_(i-1) (delta_0 = Q_0),
+// in component 1 (symbol delta + R1 or an escape), with its histogram
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void hist_add(unsigned int *sh, int sym, bool valid);
+
+__global__ void __launch_bounds__(256) k_delta1d(const __grid_constant__ CompArgs A) {
+  pdl_trigger();
+  pdl_wait();
+  const Ctx c = ctx_of(A, blockIdx.y);
+  Status *st = c.st;
+  extern __shared__ unsigned int shist[];
+  if (block_failed(st)) return;
+  const int R1 = A.R1, nsym = 2 * R1;
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x) shist[i] = 0;
+  __syncthreads();
+  const int64_t n = A.pv.n_g;
+  const int *__restrict__ Q = c.Q;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nloop = (n + stride - 1) / stride * stride;  // uniform trip count per warp
+  unsigned int nesc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nloop; i += stride) {
+    const bool valid = i < n;
+    int sym = 0;
+    if (valid) {
+      const int d = wsub(__ldg(Q + i), i ? __ldg(Q + i - 1) : 0);
+      if (d >= -(R1 - 1) && d <= R1 - 2) {
+        sym = d + R1;
+      } else {
+        c.val1[i] = d;
+        nesc++;
+      }
+      c.sym1[i] = (unsigned short)sym;
+    }
+    hist_add(shist, sym, valid);
+  }
+  if (nesc) atomicAdd(&st->nout1, nesc);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x)
+    if (shist[i]) atomicAdd(c.hist1 + i, shist[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1352,13 +1443,24 @@ __device__ void scan_field(const CompArgs &A, int fi) {
     } else {
       const FieldParams &f = st->f;
       for (int i = 0; i < (int)kHeaderBytes; i += 8) put64(o + i, 0);
+      // the alignment gaps between sections are zero (no stale bytes of the
+      // caller's buffer in the stream, which is then a function of the input)
+      const uint64_t gap[5][2] = {{L.lens2 + 2 * (uint64_t)a.R2, L.gtab1},
+                                  {L.ltab2 + kLtabBytes * (uint64_t)a.ng2, L.out1},
+                                  {L.out2 + 4 * e2, L.raw},
+                                  {L.raw + vsz * r2, L.bits1},
+                                  {L.bits2 + 4 * w2, L.model}};
+#pragma unroll
+      for (int k = 0; k < 5; k++)
+        for (uint64_t b = gap[k][0]; b < gap[k][1]; b++) o[b] = 0;
       put32(o + H_MAGIC, kMagic);
       put32(o + H_VERSION, kVersion);
       put32(o + H_HBYTES, kHeaderBytes);
       put32(o + H_DTYPE, (uint32_t)a.dtype);
       put32(o + H_DIM, (uint32_t)a.dim);
       const bool open = A.open[fi] != 0;
-      put32(o + H_FLAGS, (f.guard || open ? F_GUARD : 0u) | (model ? F_MODEL : 0u) |
+      if (A.one_d) put32(o + H_FLAGS, F_ONED);
+      else put32(o + H_FLAGS, (f.guard || open ? F_GUARD : 0u) | (model ? F_MODEL : 0u) |
                              (open ? F_OPEN : 0u) |
                              (A.gop[fi] == MCC_G_NEAREST ? F_GNEAR : 0u) |
                              (A.fop[fi] == MCC_F_CLUSTER ? F_FCLUSTER : 0u));
@@ -1619,8 +1721,9 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   A.lmax = p->lmax;
   A.nsym1 = 2 * p->R1;
   A.nsym2 = 2 * p->R2;
+  A.one_d = pv.dim == 1;  // the 1D coder: no residual component
   A.ng1 = ngroups(pv.n_g, p->C1);
-  A.ng2 = ngroups(pv.n_v, p->C2);
+  A.ng2 = A.one_d ? 0 : ngroups(pv.n_v, p->C2);
   A.F = make_layout(p->R1, p->R2, A.ng1, A.ng2, 0, 0, 0, 8, 0, 0);
   if (!front_only && capacity < A.F.out1) return MCC_ERR_CAPACITY;
   bool any_model = false, any_open = false, any_cluster = false;
@@ -1633,7 +1736,7 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     any_open = any_open || A.open[f] || ps[f].g_op == MCC_G_NEAREST;
     any_cluster = any_cluster || ps[f].f_op == MCC_F_CLUSTER;
     A.x[f] = xs[f];
-    A.rp[f] = RParams{ps[f].dtype, ps[f].eb_mode, ps[f].eb, ps[f].grid_fraction};
+    A.rp[f] = RParams{ps[f].dtype, ps[f].eb_mode, ps[f].eb, ps[f].grid_fraction, A.one_d};
     A.mode[f] = (unsigned char)ps[f].predictor;
     A.model[f] = ps[f].predictor != MCC_PRED_ZERO ? (const unsigned char *)ps[f].d_model : nullptr;
     any_model = any_model || A.model[f];
@@ -1666,7 +1769,10 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     else launch_pdl(k_prequant<float>, dim3(ppf, nf), dim3(256), 0, stream, A);
   }
   const size_t hsm1 = 4 * (size_t)A.nsym1, hsm2 = 4 * (size_t)A.nsym2 * (A.any_auto ? 2 : 1);
-  if (pv.dim == 2) {
+  if (A.one_d) {
+    PROF_SCOPE("k_delta1d", stream);
+    launch_pdl(k_delta1d, dim3(ppf, nf), dim3(256), hsm1, stream, A);
+  } else if (pv.dim == 2) {
     PROF_SCOPE("k_grid2d", stream);
     launch_pdl(k_grid2d<64, 16>, dim3(nf, (pv.nx + 63) / 64, (pv.ny + 15) / 16), dim3(256), hsm1,
                stream, A);
@@ -1676,7 +1782,7 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     launch_pdl(k_grid3d<32, 8, 8>, dim3(nf, txy, (pv.nz + 7) / 8), dim3(256), hsm1, stream, A);
   }
   if (front_only) return cudaGetLastError() == cudaSuccess ? MCC_OK : MCC_ERR_CUDA;
-  if (any_model) {  // learned corrections p at every vertex of the fields with a model
+  if (!A.one_d && any_model) {  // learned corrections p at every vertex of the fields with a model
     PROF_SCOPE("k_predict", stream);
     PredArgs P;
     memset(&P, 0, sizeof(P));
@@ -1694,7 +1800,7 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     }
     launch_predict(P, stream, true);
   }
-  {
+  if (!A.one_d) {
     PROF_SCOPE("k_node", stream);
     const unsigned int chunks = ppf < 65535 ? ppf : 65535;
     const dim3 grid(nf, chunks);

@@ -103,7 +103,9 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
   I.dtype = (int)ld32(h + H_DTYPE);
   I.dim = (int)ld32(h + H_DIM);
   const uint32_t flags = ld32(h + H_FLAGS);
-  if (flags & ~(F_GUARD | F_MODEL | F_OPEN | F_GNEAR | F_FCLUSTER)) return false;
+  if (flags & ~(F_GUARD | F_MODEL | F_OPEN | F_GNEAR | F_FCLUSTER | F_ONED)) return false;
+  // a 1D stream has this flag alone, and only 1D streams have it
+  if (a.dim == 1 ? flags != F_ONED : (flags & F_ONED) != 0) return false;
   I.use_model = (flags & F_MODEL) ? 1 : 0;
   I.open = (flags & F_OPEN) ? 1 : 0;
   I.gnear = (flags & F_GNEAR) ? 1 : 0;  // (F_FCLUSTER concerns compression only)
@@ -138,7 +140,7 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
   I.w2 = ld64(h + H_W2);
   if (I.nout1 > (uint64_t)a.n_g || I.nout2 > (uint64_t)a.n_v || I.nraw > (uint64_t)a.n_v) return false;
   I.ng1 = ngroups(a.n_g, I.C1);
-  I.ng2 = ngroups(a.n_v, I.C2);
+  I.ng2 = a.dim == 1 ? 0 : ngroups(a.n_v, I.C2);  // the 1D coder has no residual component
   if (I.w1 > (uint64_t)a.n_g * kMaxLen / 32 + I.ng1 + 1 ||
       I.w2 > (uint64_t)a.n_v * kMaxLen / 32 + I.ng2 + 1)
     return false;
@@ -653,6 +655,127 @@ __global__ void __launch_bounds__(32 * W) k_scan_axis(const __grid_constant__ De
 }
 
 // ---------------------------------------------------------------------------
+// the 1D coder: Q = inclusive prefix sums of the differences (wrapping int32)
+// in three launches (chunk sums, their exclusive scan in one block, the
+// chunks scanned from their offsets), then x' = s (K + Q)
+// ---------------------------------------------------------------------------
+constexpr int kScan1dChunk = 256 * 16;  // values per chunk (one block)
+
+__global__ void __launch_bounds__(256) k_scan1d_sums(const __grid_constant__ DecArgs A) {
+  pdl_trigger();
+  pdl_wait();
+  const DCtx c = dctx_of(A, blockIdx.y);
+  if (*(volatile const unsigned int *)&c.st->err) return;
+  const int64_t n = A.pv.n_g;
+  const int *__restrict__ d = c.q1;
+  unsigned int *part = (unsigned int *)c.q2;
+  const int64_t nchunk = (n + kScan1dChunk - 1) / kScan1dChunk;
+  __shared__ unsigned int ws[8];
+  for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    const int64_t base = ch * kScan1dChunk;
+    unsigned int v[16], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const int64_t i = base + threadIdx.x + 256 * k;
+      v[k] = i < n ? (unsigned int)__ldg(d + i) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) sum += v[k];
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int t = 0;
+      for (int w = 0; w < 8; w++) t += ws[w];
+      part[ch] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// exclusive scan of the chunk sums, in place (one block per field)
+__global__ void __launch_bounds__(1024) k_scan1d_top(const __grid_constant__ DecArgs A) {
+  pdl_trigger();
+  pdl_wait();
+  const DCtx c = dctx_of(A, blockIdx.y);
+  if (*(volatile const unsigned int *)&c.st->err) return;
+  const int64_t nchunk = (A.pv.n_g + kScan1dChunk - 1) / kScan1dChunk;
+  unsigned int *part = (unsigned int *)c.q2;
+  __shared__ unsigned int ws[32];
+  __shared__ unsigned int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t base = 0; base < nchunk; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    const unsigned int v = i < nchunk ? part[i] : 0u;
+    unsigned int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      unsigned int s = ws[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int t = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += t;
+      }
+      ws[lane] = s;  // inclusive over the warps
+    }
+    __syncthreads();
+    const unsigned int excl = carry + (w ? ws[w - 1] : 0u) + incl - v;
+    if (i < nchunk) part[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += ws[31];
+    __syncthreads();
+  }
+}
+
+// each chunk scanned from its offset: Q, then x' = s (K + Q)
+template <typename T>
+__global__ void __launch_bounds__(256) k_recon1d(const __grid_constant__ DecArgs A) {
+  pdl_trigger();
+  pdl_wait();
+  const DCtx c = dctx_of(A, blockIdx.y);
+  if (*(volatile const unsigned int *)&c.st->err) return;
+  const DecInfo I = *c.info;
+  const int64_t n = A.pv.n_g;
+  const int *__restrict__ d = c.q1;
+  const unsigned int *part = (const unsigned int *)c.q2;
+  T *__restrict__ xo = (T *)c.xo;
+  const int64_t nchunk = (n + kScan1dChunk - 1) / kScan1dChunk;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ unsigned int ws[8];
+  for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    // 16 consecutive values per thread: a local scan, then the scan of the
+    // thread totals across the block
+    const int64_t base = ch * kScan1dChunk + 16 * (int64_t)threadIdx.x;
+    unsigned int v[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = base + k < n ? (unsigned int)__ldg(d + base + k) : 0u;
+#pragma unroll
+    for (int k = 1; k < 16; k++) v[k] += v[k - 1];
+    unsigned int incl = v[15];
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    unsigned int before = 0;
+    for (int k = 0; k < w; k++) before += ws[k];
+    const unsigned int off = __ldg(part + ch) + before + incl - v[15];
+#pragma unroll
+    for (int k = 0; k < 16; k++)
+      if (base + k < n)
+        xo[base + k] = (T)__dmul_rn(I.s2, (double)(I.K + (long long)(int)(v[k] + off)));
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // k_recon: x' = s2 (K + P + q2) at every vertex, P = round(rho12 g(x1'));
 // open-loop streams: x' = s2 ((K + q2) + g(x1')) in FP64 (recon_open)
 // ---------------------------------------------------------------------------
@@ -841,6 +964,24 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
       launch_pdl(k_dec_syms<double>, dim3(nb1 + nb2, nf), dim3(256), sm, stream, A, (int)nb1);
     else
       launch_pdl(k_dec_syms<float>, dim3(nb1 + nb2, nf), dim3(256), sm, stream, A, (int)nb1);
+  }
+  if (pv.dim == 1) {  // the 1D coder
+    const int64_t nchunk = (pv.n_g + kScan1dChunk - 1) / kScan1dChunk;
+    const unsigned int cb = (unsigned int)(nchunk < 65535 ? nchunk : 65535);
+    {
+      PROF_SCOPE("k_scan1d_sums", stream);
+      launch_pdl(k_scan1d_sums, dim3(cb, nf), dim3(256), 0, stream, A);
+    }
+    {
+      PROF_SCOPE("k_scan1d_top", stream);
+      launch_pdl(k_scan1d_top, dim3(1, nf), dim3(1024), 0, stream, A);
+    }
+    {
+      PROF_SCOPE("k_recon1d", stream);
+      if (dtype == MCC_F64) launch_pdl(k_recon1d<double>, dim3(cb, nf), dim3(256), 0, stream, A);
+      else launch_pdl(k_recon1d<float>, dim3(cb, nf), dim3(256), 0, stream, A);
+    }
+    return cudaGetLastError() == cudaSuccess ? MCC_OK : MCC_ERR_CUDA;
   }
   {
     PROF_SCOPE("k_scan_rows", stream);

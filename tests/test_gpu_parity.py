@@ -209,6 +209,25 @@ def test_deterministic_repeat():
     assert np.array_equal(a, b)
 
 
+def test_stream_independent_of_output_buffer():
+    """The stream is a function of the input: output buffers filled with
+    garbage give the same bytes as zeroed ones (the alignment gaps between
+    sections are written)."""
+    import torch
+    import paper_2501_06910_gb300 as mcc
+    c, e, n, x, op, gp = _setup("annulus_small")
+    want = oracle.compress(op, x, eb=1e-3)
+    prm = mcc.params_default(eb=1e-3)
+    for R in (511, 512, 7):  # odd and even alphabets move the gaps
+        prm.R1 = prm.R2 = R
+        want = oracle.compress(op, x, eb=1e-3, R1=R, R2=R)
+        ws = gp.workspace(prm)
+        ws.fill_(0xA5)
+        out = torch.full((mcc.compress_bound(gp, prm),), 0xA5, dtype=torch.uint8, device="cuda")
+        size = mcc.compress(gp, torch.from_numpy(x).cuda(), prm, ws, out)
+        assert np.array_equal(out[:size].cpu().numpy(), want), R
+
+
 @pytest.mark.slow
 def test_full_size_2d_graded_1024():
     """The 2M-vertex graded Delaunay mesh on the 1024^2 grid (the benchmark
