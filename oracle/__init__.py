@@ -54,7 +54,8 @@ class _Params(C.Structure):
                 ("grid_fraction", C.c_double), ("R1", C.c_int), ("R2", C.c_int),
                 ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int),
                 ("model", C.c_void_p), ("model_bytes", C.c_size_t), ("auto_select", C.c_int),
-                ("open_loop", C.c_int), ("f_op", C.c_int), ("g_op", C.c_int)]
+                ("open_loop", C.c_int), ("f_op", C.c_int), ("g_op", C.c_int),
+                ("zero_run", C.c_int)]
 
 
 class _Field(C.Structure):
@@ -208,15 +209,17 @@ DEFAULTS = dict(eb_mode="rel", eb=1e-4, grid_fraction=0.5, R1=512, R2=512, C1=12
 
 
 def make_params(dtype, model=None, auto=False, open_loop=False, f_op="barycentric",
-                g_op="multilinear", **kw):
+                g_op="multilinear", zero_run=False, **kw):
     """Parameters; ``model`` is a learned-predictor blob (uint8 array) or None;
-    ``auto`` keeps whichever predictor encodes smaller. The returned structure
-    keeps a reference to the blob."""
+    ``auto`` keeps whichever predictor encodes smaller; ``zero_run`` turns on
+    the zero-run stage before the Huffman coder. The returned structure keeps
+    a reference to the blob."""
     p = dict(DEFAULTS)
     p.update(kw)
     out = _Params()
     out.auto_select = 1 if auto else 0
     out.open_loop = 1 if open_loop else 0
+    out.zero_run = int(zero_run) if not isinstance(zero_run, bool) else (1 if zero_run else 0)
     out.f_op = {"barycentric": 0, "cluster": 1}[f_op] if isinstance(f_op, str) else int(f_op)
     out.g_op = {"multilinear": 0, "nearest": 1}[g_op] if isinstance(g_op, str) else int(g_op)
     if model is not None:

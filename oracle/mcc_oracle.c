@@ -920,6 +920,11 @@ static int check_params(const orc_params *p) {
   if (p->f_op != 0 && p->f_op != 1) return ORC_ERR_INVALID_ARG;
   if (p->g_op != 0 && p->g_op != 1) return ORC_ERR_INVALID_ARG;
   if (p->g_op && p->model) return ORC_ERR_INVALID_ARG;  /* it corrects the interpolation */
+  if (p->zero_run != 0 && p->zero_run != 1) return ORC_ERR_INVALID_ARG;
+  /* the two run tokens extend each alphabet to 2R + 2 symbols */
+  if (p->zero_run && (p->R1 > 32767 || p->R2 > 32767 || 2 * p->R1 + 2 > (1 << p->lmax) ||
+                      2 * p->R2 + 2 > (1 << p->lmax)))
+    return ORC_ERR_INVALID_ARG;
   return ORC_OK;
 }
 
@@ -934,18 +939,64 @@ size_t orc_compress_bound(const orc_grid *g, int64_t n_v, const orc_params *p) {
   return L.total + 16;
 }
 
-/* Pack one component: symbols in lane-chunk order. Lane l of group g owns the
- * symbols g*32C + 32k + l (k = 0..C-1); each lane's codes are concatenated
- * MSB-first (then its padding), the 32 lanes of a group follow each other
- * without gaps, and each group starts on a 32-bit word. Bit b of a group is
- * bit 31 - b%32 of its word b/32. Writes gtab (word offsets) and ltab (lane
- * table). */
-static uint64_t pack_component(const uint16_t *sym, int64_t n, int C, const uint8_t *len,
-                               const uint32_t *code, uint32_t *gtab, uint8_t *ltab,
-                               uint32_t *etab, uint32_t *rtab, uint16_t raw_sym,
+/* Zero-run stage (an option; not in the paper). The symbols of one lane, in
+ * lane order, become tokens: with zr, every maximal run of r >= 1 zero
+ * symbols z = R (a Lorenzo difference or residual of 0) becomes the digits
+ * d_i in {1, 2} of r = sum_i d_i 2^i (bijective base 2), least significant
+ * digit first, as token 2R for a digit 1 and token 2R + 1 for a digit 2;
+ * every other symbol is its own token. Without zr the tokens are the
+ * symbols. A lane of c symbols gives at most c tokens. */
+static int put_run(int64_t r, int R, uint16_t *tok, int nt) {
+  while (r > 0) {
+    const int64_t d = r % 2 == 1 ? 1 : 2;
+    tok[nt++] = (uint16_t)(2 * R + d - 1);
+    r = (r - d) / 2;
+  }
+  return nt;
+}
+
+static int lane_tokens(const uint16_t *sym, int64_t n, int C, int64_t g, int l, int R, int zr,
+                       uint16_t *tok) {
+  int nt = 0;
+  int64_t run = 0;
+  for (int64_t k = 0; k < C; k++) {
+    const int64_t p = g * 32 * (int64_t)C + 32 * k + l;
+    if (p >= n) break;
+    if (zr && sym[p] == R) {
+      run++;
+      continue;
+    }
+    nt = put_run(run, R, tok, nt);
+    run = 0;
+    tok[nt++] = sym[p];
+  }
+  return put_run(run, R, tok, nt);
+}
+
+/* Token counts of one component over all its lanes (h has 2R + 2 entries,
+ * zeroed by the caller). */
+static void token_hist(const uint16_t *sym, int64_t n, int C, int R, int zr, uint64_t *h) {
+  uint16_t tok[2048];
+  for (int64_t g = 0; g < ngroups(n, C); g++)
+    for (int l = 0; l < 32; l++) {
+      const int nt = lane_tokens(sym, n, C, g, l, R, zr, tok);
+      for (int t = 0; t < nt; t++) h[tok[t]]++;
+    }
+}
+
+/* Pack one component: tokens in lane-chunk order. Lane l of group g owns the
+ * symbols g*32C + 32k + l (k = 0..C-1); each lane's token codes are
+ * concatenated MSB-first (then its padding), the 32 lanes of a group follow
+ * each other without gaps, and each group starts on a 32-bit word. Bit b of a
+ * group is bit 31 - b%32 of its word b/32. Writes gtab (word offsets) and
+ * ltab (lane table); escape and raw counts are taken over the symbols. */
+static uint64_t pack_component(const uint16_t *sym, int64_t n, int C, int R, int zr,
+                               const uint8_t *len, const uint32_t *code, uint32_t *gtab,
+                               uint8_t *ltab, uint32_t *etab, uint32_t *rtab, uint16_t raw_sym,
                                uint32_t *words /* may be NULL: count only */) {
   int64_t G = 32 * (int64_t)C, ng = ngroups(n, C);
   uint64_t w = 0, ne = 0, nr = 0;
+  uint16_t tok[2048];
   for (int64_t g = 0; g < ng; g++) {
     if (gtab) gtab[g] = (uint32_t)w;
     if (etab) etab[g] = (uint32_t)ne;
@@ -957,11 +1008,8 @@ static uint64_t pack_component(const uint16_t *sym, int64_t n, int C, const uint
     uint64_t lane_bits[32], mn = ~(uint64_t)0, mx = 0;
     for (int l = 0; l < 32; l++) {
       lane_bits[l] = 0;
-      for (int64_t k = 0; k < C; k++) {
-        int64_t p = g * G + 32 * k + l;
-        if (p >= n) break;
-        lane_bits[l] += len[sym[p]];
-      }
+      const int nt = lane_tokens(sym, n, C, g, l, R, zr, tok);
+      for (int t = 0; t < nt; t++) lane_bits[l] += len[tok[t]];
       if (lane_bits[l] < mn) mn = lane_bits[l];
       if (lane_bits[l] > mx) mx = lane_bits[l];
     }
@@ -974,10 +1022,9 @@ static uint64_t pack_component(const uint16_t *sym, int64_t n, int C, const uint
     for (int l = 0; l < 32; l++) {
       const uint64_t padded = lane_bits[l] < base ? base : lane_bits[l];
       uint64_t b0 = bit;
-      for (int64_t k = 0; k < C; k++) {
-        int64_t p = g * G + 32 * k + l;
-        if (p >= n) break;
-        uint16_t s = sym[p];
+      const int nt = lane_tokens(sym, n, C, g, l, R, zr, tok);
+      for (int t = 0; t < nt; t++) {
+        const uint16_t s = tok[t];
         for (int b = len[s] - 1; b >= 0; b--) {
           if (words && ((code[s] >> b) & 1u)) {
             uint64_t pos = bit;
@@ -1031,12 +1078,15 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   int32_t *val2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_v);
   uint16_t *sym2b = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n_v);
   int32_t *val2b = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_v);
-  uint64_t *h1 = (uint64_t *)calloc((size_t)2 * R1, sizeof(uint64_t));
-  uint64_t *h2 = (uint64_t *)calloc((size_t)2 * R2, sizeof(uint64_t));
-  uint64_t *h2b = (uint64_t *)calloc((size_t)2 * R2, sizeof(uint64_t));
-  uint8_t *len2b = (uint8_t *)calloc((size_t)2 * R2, 1);
-  uint8_t *len1 = (uint8_t *)calloc((size_t)2 * R1, 1), *len2 = (uint8_t *)calloc((size_t)2 * R2, 1);
-  uint32_t *code1 = (uint32_t *)calloc((size_t)2 * R1, 4), *code2 = (uint32_t *)calloc((size_t)2 * R2, 4);
+  /* code books over 2R symbols plus the zero-run stage's two run tokens
+   * (which keep count 0, hence no code, without the stage) */
+  const int nsym1 = 2 * R1 + 2, nsym2 = 2 * R2 + 2;
+  uint64_t *h1 = (uint64_t *)calloc((size_t)nsym1, sizeof(uint64_t));
+  uint64_t *h2 = (uint64_t *)calloc((size_t)nsym2, sizeof(uint64_t));
+  uint64_t *h2b = (uint64_t *)calloc((size_t)nsym2, sizeof(uint64_t));
+  uint8_t *len2b = (uint8_t *)calloc((size_t)nsym2, 1);
+  uint8_t *len1 = (uint8_t *)calloc((size_t)nsym1, 1), *len2 = (uint8_t *)calloc((size_t)nsym2, 1);
+  uint32_t *code1 = (uint32_t *)calloc((size_t)nsym1, 4), *code2 = (uint32_t *)calloc((size_t)nsym2, 4);
   st = ORC_OK;
   if (!Q || !q1 || !dl || !sym1 || !sym2 || !val2 || !h1 || !h2 || !len1 || !len2 || !code1 ||
       !code2 || !sym2b || !val2b || !h2b || !len2b || (open && !x1v)) {
@@ -1191,13 +1241,25 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
       hh[s2[i]]++;
     }
   }
+  /* 4b. zero-run stage: the code books count tokens (runs of zero symbols
+   *     as their digits) instead of symbols; escape and raw counts stay */
+  if (p->zero_run) {
+    memset(h1, 0, sizeof(uint64_t) * (size_t)nsym1);
+    memset(h2, 0, sizeof(uint64_t) * (size_t)nsym2);
+    token_hist(sym1, ng, p->C1, R1, 1, h1);
+    token_hist(sym2, n_v, p->C2, R2, 1, h2);
+    if (passes == 2) {
+      memset(h2b, 0, sizeof(uint64_t) * (size_t)nsym2);
+      token_hist(sym2b, n_v, p->C2, R2, 1, h2b);
+    }
+  }
   if (passes == 2) {
     /* the exact encoded size of each choice: code bits plus escape and raw
      * values, plus the model for the learned one; a tie keeps the plain */
-    if ((st = orc_huffman_lengths(h2, 2 * R2, p->lmax, len2))) goto done;
-    if ((st = orc_huffman_lengths(h2b, 2 * R2, p->lmax, len2b))) goto done;
+    if ((st = orc_huffman_lengths(h2, nsym2, p->lmax, len2))) goto done;
+    if ((st = orc_huffman_lengths(h2b, nsym2, p->lmax, len2b))) goto done;
     uint64_t bz = 0, bl = 0;
-    for (int k = 0; k < 2 * R2; k++) {
+    for (int k = 0; k < nsym2; k++) {
       bz += h2[k] * len2[k];
       bl += h2b[k] * len2b[k];
     }
@@ -1215,16 +1277,19 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
   }
 
   /* 5. canonical Huffman code books */
-  if ((st = orc_huffman_lengths(h1, 2 * R1, p->lmax, len1))) goto done;
-  if ((st = orc_huffman_lengths(h2, 2 * R2, p->lmax, len2))) goto done;
-  orc_canonical_codes(len1, 2 * R1, code1);
-  orc_canonical_codes(len2, 2 * R2, code2);
+  if ((st = orc_huffman_lengths(h1, nsym1, p->lmax, len1))) goto done;
+  if ((st = orc_huffman_lengths(h2, nsym2, p->lmax, len2))) goto done;
+  orc_canonical_codes(len1, nsym1, code1);
+  orc_canonical_codes(len2, nsym2, code2);
 
   /* 6. layout, then write */
   {
     int64_t g1 = ngroups(ng, p->C1), g2 = ngroups(n_v, p->C2);
-    uint64_t w1 = pack_component(sym1, ng, p->C1, len1, code1, NULL, NULL, NULL, NULL, 0xFFFF, NULL);
-    uint64_t w2 = pack_component(sym2, n_v, p->C2, len2, code2, NULL, NULL, NULL, NULL, 0xFFFF, NULL);
+    const int zr = p->zero_run;
+    uint64_t w1 = pack_component(sym1, ng, p->C1, R1, zr, len1, code1, NULL, NULL, NULL, NULL,
+                                 0xFFFF, NULL);
+    uint64_t w2 = pack_component(sym2, n_v, p->C2, R2, zr, len2, code2, NULL, NULL, NULL, NULL,
+                                 0xFFFF, NULL);
     layout_t L;
     make_layout(R1, R2, g1, g2, nout1, nout2, nraw, vsz, w1, w2, use_model ? MODEL_BYTES : 0, &L);
     *out_size = L.total;
@@ -1237,7 +1302,7 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     put_u32(h + 12, (uint32_t)p->dtype);
     put_u32(h + 16, (uint32_t)dim);
     put_u32(h + 20, (uint32_t)((f.guard || open ? 1 : 0) | (use_model ? 2 : 0) | (open ? 4 : 0) |
-                               (p->g_op ? 8 : 0) | (p->f_op ? 16 : 0)));
+                               (p->g_op ? 8 : 0) | (p->f_op ? 16 : 0) | (zr ? 64 : 0)));
     put_u32(h + 24, (uint32_t)R1);
     put_u32(h + 28, (uint32_t)R2);
     put_u32(h + 32, (uint32_t)p->C1);
@@ -1268,10 +1333,15 @@ int orc_compress(const orc_grid *g, int64_t n_v, const int32_t *vid, const uint1
     if (use_model) memcpy(out + L.model, p->model, MODEL_BYTES);
     memcpy(out + L.lens1, len1, (size_t)2 * R1);
     memcpy(out + L.lens2, len2, (size_t)2 * R2);
-    pack_component(sym1, ng, p->C1, len1, code1, (uint32_t *)(out + L.gtab1),
+    /* the run tokens' code lengths (zero without the stage) */
+    out[208] = len1[2 * R1];
+    out[209] = len1[2 * R1 + 1];
+    out[210] = len2[2 * R2];
+    out[211] = len2[2 * R2 + 1];
+    pack_component(sym1, ng, p->C1, R1, zr, len1, code1, (uint32_t *)(out + L.gtab1),
                    out + L.ltab1, (uint32_t *)(out + L.etab1), NULL, 0xFFFF,
                    (uint32_t *)(out + L.bits1));
-    pack_component(sym2, n_v, p->C2, len2, code2, (uint32_t *)(out + L.gtab2),
+    pack_component(sym2, n_v, p->C2, R2, zr, len2, code2, (uint32_t *)(out + L.gtab2),
                    out + L.ltab2, (uint32_t *)(out + L.etab2),
                    (uint32_t *)(out + L.rtab2), (uint16_t)(2 * R2 - 1), (uint32_t *)(out + L.bits2));
     /* escape values and raw values in increasing index order */
@@ -1357,15 +1427,29 @@ static int decode_symbol(const decoder_t *D, int lmax, bitreader_t *r, uint16_t 
   return ORC_ERR_CORRUPT;
 }
 
+/* Decode one component into symbols. With zr the code book also holds the
+ * two run tokens (lengths from header bytes 208 + 2 (which - 1) and the next)
+ * and each lane's tokens expand back: a digit d at digit position i (counted
+ * from the last symbol that was not a digit) stands for d 2^i zero symbols. */
 static int unpack_component(const uint8_t *in, size_t size, const layout_t *L, int which,
-                            int64_t n, int C, int nsym, int lmax, uint64_t words, uint16_t *sym) {
+                            int64_t n, int C, int R, int zr, int lmax, uint64_t words,
+                            uint16_t *sym) {
   size_t off_len = which == 1 ? L->lens1 : L->lens2;
   size_t off_g = which == 1 ? L->gtab1 : L->gtab2;
   size_t off_l = which == 1 ? L->ltab1 : L->ltab2;
   size_t off_b = which == 1 ? L->bits1 : L->bits2;
   (void)size;
+  const int nsym = 2 * R + 2;
+  uint8_t *len = (uint8_t *)calloc((size_t)nsym, 1);
+  if (!len) return ORC_ERR_OOM;
+  memcpy(len, in + off_len, (size_t)2 * R);
+  if (zr) {
+    len[2 * R] = in[208 + 2 * (which - 1)];
+    len[2 * R + 1] = in[209 + 2 * (which - 1)];
+  }
   decoder_t D;
-  int st = decoder_init(in + off_len, nsym, lmax, &D);
+  int st = decoder_init(len, nsym, lmax, &D);
+  free(len);
   if (st) { free(D.sorted); return st; }
   int64_t G = 32 * (int64_t)C, ng = ngroups(n, C);
   if (get_u32(in + off_g) != 0 || get_u32(in + off_g + 4 * (size_t)ng) != words) {
@@ -1384,10 +1468,24 @@ static int unpack_component(const uint8_t *in, size_t size, const layout_t *L, i
     for (int l = 0; l < 32; l++) {
       const uint64_t lb = base + lt[2 + l];
       r.bit = start;
-      for (int64_t k = 0; k < C; k++) {
-        int64_t p = g * G + 32 * k + l;
-        if (p >= n) break;
-        if (decode_symbol(&D, lmax, &r, &sym[p])) { free(D.sorted); return ORC_ERR_CORRUPT; }
+      int64_t cnt = 0;  /* the lane's symbols: positions g G + 32 k + l < n */
+      while (cnt < C && g * G + 32 * cnt + l < n) cnt++;
+      int64_t k = 0;
+      int digit = 0;
+      while (k < cnt) {
+        uint16_t t;
+        if (decode_symbol(&D, lmax, &r, &t)) { free(D.sorted); return ORC_ERR_CORRUPT; }
+        if (t >= 2 * R) {  /* a run digit (only in the zero-run stage's code book) */
+          const int64_t z = (int64_t)(t - 2 * R + 1) << digit;
+          if (digit > 40 || z > cnt - k) { free(D.sorted); return ORC_ERR_CORRUPT; }
+          for (int64_t e = 0; e < z; e++) sym[g * G + 32 * (k + e) + l] = (uint16_t)R;
+          k += z;
+          digit++;
+        } else {
+          sym[g * G + 32 * k + l] = t;
+          k++;
+          digit = 0;
+        }
       }
       /* the codes fill the lane, or a padded lane (delta 0) ends early */
       const uint64_t used = r.bit - start;
@@ -1427,7 +1525,10 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
   if (dim != g->dim || nx != g->n[0] || ny != g->n[1] || nz != g->n[2]) return ORC_ERR_CORRUPT;
   if ((int64_t)get_u64(in + 56) != n_v || (int64_t)get_u64(in + 64) != nx * ny * nz)
     return ORC_ERR_CORRUPT;
+  const uint32_t flags = get_u32(in + 20);
+  const int zr = (flags & 64) != 0;  /* bit 6: zero-run stage */
   orc_params chk = {dtype, 0, 1.0, 0.5, R1, R2, C1, C2, lmax, NULL, 0};
+  chk.zero_run = zr;
   if (check_params(&chk)) return ORC_ERR_CORRUPT;
   const int64_t ng = nx * ny * nz;
   const double s2 = get_f64(in + 104);
@@ -1440,14 +1541,13 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
   if (nout1 > (uint64_t)ng || nout2 > (uint64_t)n_v || nraw > (uint64_t)n_v) return ORC_ERR_CORRUPT;
   if (w1 > (uint64_t)ng * 24 + 64 || w2 > (uint64_t)n_v * 24 + 64) return ORC_ERR_CORRUPT;
   const size_t vsz = dtype == 0 ? 8 : 4;
-  const uint32_t flags = get_u32(in + 20);
   const uint64_t mbytes = get_u64(in + 192);
   const int64_t Qhi = (int64_t)get_u64(in + 200);
   if (Qhi < 0 || Qhi >= ((int64_t)1 << 29)) return ORC_ERR_CORRUPT;
   const int use_model = (flags & 2) != 0;
   const int open = (flags & 4) != 0;
   const int g_near = (flags & 8) != 0;  /* bit 4: cluster-mean f (compression only) */
-  if (flags & ~31u) return ORC_ERR_CORRUPT;
+  if (flags & ~(31u | 64u)) return ORC_ERR_CORRUPT;
   if ((open || g_near) && use_model) return ORC_ERR_CORRUPT;
   if (mbytes != (use_model ? MODEL_BYTES : 0)) return ORC_ERR_CORRUPT;
   layout_t L;
@@ -1463,8 +1563,8 @@ int orc_decompress(const orc_grid *g, int64_t n_v, const uint32_t *cell, const u
   int32_t *dl = (int32_t *)malloc(sizeof(int32_t) * (size_t)ng);
   int32_t *q1 = (int32_t *)malloc(sizeof(int32_t) * (size_t)ng);
   if (!sym1 || !sym2 || !dl || !q1) { st = ORC_ERR_OOM; goto done; }
-  if ((st = unpack_component(in, size, &L, 1, ng, C1, 2 * R1, lmax, w1, sym1))) goto done;
-  if ((st = unpack_component(in, size, &L, 2, n_v, C2, 2 * R2, lmax, w2, sym2))) goto done;
+  if ((st = unpack_component(in, size, &L, 1, ng, C1, R1, zr, lmax, w1, sym1))) goto done;
+  if ((st = unpack_component(in, size, &L, 2, n_v, C2, R2, zr, lmax, w2, sym2))) goto done;
 
   /* grid: symbols -> Lorenzo differences; escapes take the next value */
   if ((st = check_prefix(in + L.etab1, ngroups(ng, C1), nout1, sym1, ng, C1, 0))) goto done;
@@ -1792,9 +1892,10 @@ size_t orc_compress_bound_1d(int64_t n, const orc_params *p) {
 }
 
 /* Q = round(x / s) - K; delta_i = Q_i - Q_(i-1) (delta_0 = Q_0); symbols
- * delta + R1 or an escape; canonical Huffman; the grid component's
- * lane-group stream with the residual component empty. Header: dim 1,
- * n_x = n, flags bit 5. */
+ * delta + R1 or an escape; canonical Huffman (of tokens with the zero-run
+ * stage); the grid component's lane-group stream with the residual
+ * component empty. Header: dim 1, n_x = n, flags bit 5 (and bit 6 with the
+ * zero-run stage). */
 int orc_compress_1d(int64_t n, const void *x, const orc_params *p, uint8_t *out, size_t capacity,
                     size_t *out_size, int32_t *Q_dbg) {
   if (!out_size) return ORC_ERR_INVALID_ARG;
@@ -1810,9 +1911,10 @@ int orc_compress_1d(int64_t n, const void *x, const orc_params *p, uint8_t *out,
   int32_t *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
   int32_t *dl = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
   uint16_t *sym = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
-  uint64_t *h1 = (uint64_t *)calloc((size_t)2 * R1, sizeof(uint64_t));
-  uint8_t *len1 = (uint8_t *)calloc((size_t)2 * R1, 1), *len2 = (uint8_t *)calloc((size_t)2 * R2, 1);
-  uint32_t *code1 = (uint32_t *)calloc((size_t)2 * R1, 4);
+  const int nsym1 = 2 * R1 + 2, zr = p->zero_run;  /* 2R symbols and the two run tokens */
+  uint64_t *h1 = (uint64_t *)calloc((size_t)nsym1, sizeof(uint64_t));
+  uint8_t *len1 = (uint8_t *)calloc((size_t)nsym1, 1), *len2 = (uint8_t *)calloc((size_t)2 * R2, 1);
+  uint32_t *code1 = (uint32_t *)calloc((size_t)nsym1, 4);
   if (!Q || !dl || !sym || !h1 || !len1 || !len2 || !code1) { st = ORC_ERR_OOM; goto done; }
   for (int64_t i = 0; i < n; i++)
     Q[i] = (int32_t)((int64_t)rint(load_value(x, p->dtype, i) * f.inv2) - f.K);
@@ -1824,11 +1926,16 @@ int orc_compress_1d(int64_t n, const void *x, const orc_params *p, uint8_t *out,
     else { sym[i] = 0; nout1++; }
     h1[sym[i]]++;
   }
-  if ((st = orc_huffman_lengths(h1, 2 * R1, p->lmax, len1))) goto done;
-  orc_canonical_codes(len1, 2 * R1, code1);
+  if (zr) {  /* the zero-run stage: count tokens */
+    memset(h1, 0, sizeof(uint64_t) * (size_t)nsym1);
+    token_hist(sym, n, p->C1, R1, 1, h1);
+  }
+  if ((st = orc_huffman_lengths(h1, nsym1, p->lmax, len1))) goto done;
+  orc_canonical_codes(len1, nsym1, code1);
   {
     const int64_t g1 = ngroups(n, p->C1);
-    const uint64_t w1 = pack_component(sym, n, p->C1, len1, code1, NULL, NULL, NULL, NULL, 0xFFFF, NULL);
+    const uint64_t w1 = pack_component(sym, n, p->C1, R1, zr, len1, code1, NULL, NULL, NULL, NULL,
+                                       0xFFFF, NULL);
     layout_t L;
     make_layout(R1, R2, g1, 0, nout1, 0, 0, vsz, w1, 0, 0, &L);
     *out_size = L.total;
@@ -1840,7 +1947,7 @@ int orc_compress_1d(int64_t n, const void *x, const orc_params *p, uint8_t *out,
     put_u32(h + 8, HEADER_BYTES);
     put_u32(h + 12, (uint32_t)p->dtype);
     put_u32(h + 16, 1u);
-    put_u32(h + 20, 32u);
+    put_u32(h + 20, zr ? 32u | 64u : 32u);
     put_u32(h + 24, (uint32_t)R1);
     put_u32(h + 28, (uint32_t)R2);
     put_u32(h + 32, (uint32_t)p->C1);
@@ -1870,7 +1977,9 @@ int orc_compress_1d(int64_t n, const void *x, const orc_params *p, uint8_t *out,
     put_u64(h + 200, (uint64_t)f.Qhi);
     memcpy(out + L.lens1, len1, (size_t)2 * R1);
     memcpy(out + L.lens2, len2, (size_t)2 * R2);
-    pack_component(sym, n, p->C1, len1, code1, (uint32_t *)(out + L.gtab1), out + L.ltab1,
+    out[208] = len1[2 * R1];  /* the run tokens' code lengths */
+    out[209] = len1[2 * R1 + 1];
+    pack_component(sym, n, p->C1, R1, zr, len1, code1, (uint32_t *)(out + L.gtab1), out + L.ltab1,
                    (uint32_t *)(out + L.etab1), NULL, 0xFFFF, (uint32_t *)(out + L.bits1));
     put_u32(out + L.gtab2, 0);  /* the empty residual component: one zero entry per table */
     put_u32(out + L.etab2, 0);
@@ -1895,11 +2004,14 @@ int orc_decompress_1d(int64_t n, const uint8_t *in, size_t size, void *xout) {
   const int R1 = (int)get_u32(in + 24), R2 = (int)get_u32(in + 28);
   const int C1 = (int)get_u32(in + 32), C2 = (int)get_u32(in + 36), lmax = (int)get_u32(in + 40);
   if (dtype != 0 && dtype != 1) return ORC_ERR_CORRUPT;
-  if (get_u32(in + 16) != 1u || get_u32(in + 20) != 32u) return ORC_ERR_CORRUPT;
+  const uint32_t flags = get_u32(in + 20);  /* bit 5 alone, or with bit 6 (zero-run stage) */
+  if (get_u32(in + 16) != 1u || (flags != 32u && flags != (32u | 64u))) return ORC_ERR_CORRUPT;
+  const int zr = flags == (32u | 64u);
   if (get_u32(in + 44) != (uint32_t)n || get_u32(in + 48) != 1u || get_u32(in + 52) != 1u ||
       (int64_t)get_u64(in + 56) != n || (int64_t)get_u64(in + 64) != n)
     return ORC_ERR_CORRUPT;
   orc_params chk = {dtype, 0, 1.0, 0.5, R1, R2, C1, C2, lmax, NULL, 0};
+  chk.zero_run = zr;
   if (check_params(&chk)) return ORC_ERR_CORRUPT;
   const double s = get_f64(in + 104);
   const int64_t K = (int64_t)get_u64(in + 112);
@@ -1915,7 +2027,7 @@ int orc_decompress_1d(int64_t n, const uint8_t *in, size_t size, void *xout) {
   uint16_t *sym = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
   int st = ORC_OK;
   if (!sym) return ORC_ERR_OOM;
-  if ((st = unpack_component(in, size, &L, 1, n, C1, 2 * R1, lmax, w1, sym))) goto done;
+  if ((st = unpack_component(in, size, &L, 1, n, C1, R1, zr, lmax, w1, sym))) goto done;
   {
     uint64_t k = 0;
     uint32_t q = 0;

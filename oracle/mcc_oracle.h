@@ -83,6 +83,9 @@ typedef struct {
                          (mean of the vertices whose nearest node is j, Sec. III-C) */
   int g_op;           /* grid -> mesh: 0 bi/trilinear interpolation, 1 nearest node
                          (x2[k] = x[k] - x1[m_k], Sec. III-B) */
+  int zero_run;       /* 1: lossless zero-run stage before the Huffman coder (not in
+                         the paper): within each lane chunk a run of r zero symbols
+                         becomes the digits of r in bijective base 2 */
 } orc_params;
 
 /* Per-field scalars derived from the values (Sec. III bound split). */
