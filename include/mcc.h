@@ -131,6 +131,17 @@ typedef struct {
    * MCC_PRED_ZERO only (the learned predictor corrects the interpolation). */
   int f_op;
   int g_op;
+  /* Zero-run stage (not in the paper; 0 off, 1 on): before the Huffman
+   * coder, every maximal run of r zero symbols in a lane chunk (a Lorenzo
+   * difference or residual of 0, symbol R) becomes the digits of r in
+   * bijective base 2, least significant first (r = sum d_i 2^i, d_i in
+   * {1, 2}; token 2R for a digit 1, 2R + 1 for a digit 2), and each code
+   * book covers these 2R + 2 tokens. Lossless; it lifts the one bit per
+   * symbol floor of a Huffman code where zeros dominate (loose bounds).
+   * Stream flags bit 6; the two run tokens' code lengths sit at header
+   * bytes 208..209 (grid component) and 210..211 (residual component).
+   * Requires R <= 2047 (MCC_ERR_UNSUPPORTED) and 2R + 2 <= 2^lmax. */
+  int zero_run;
 } mcc_params;
 
 typedef struct mcc_plan_s *mcc_plan;
@@ -145,7 +156,7 @@ typedef struct {
 
 /* Defaults: F64, REL, eb 1e-4, grid_fraction 0.5, R1 = R2 = 512,
  * C1 = C2 = 128, lmax 24, MCC_PRED_ZERO, MCC_LOOP_CLOSED, MCC_F_BARYCENTRIC,
- * MCC_G_MULTILINEAR. */
+ * MCC_G_MULTILINEAR, zero_run 0. */
 void mcc_params_default(mcc_params *p);
 
 /* Build the mesh -> grid mapping once per mesh (Sec. IV-B: reused across
@@ -213,7 +224,7 @@ mcc_status mcc_decompress(mcc_plan plan, const void *d_in, size_t in_bytes, void
  * mesh (Sec. IV-B: the mapping is computed once and reused across variables
  * and timesteps). Field f is compressed from d_values[f] (a HOST array of n
  * device pointers) with per_field[f] (a host array; eb_mode, eb,
- * grid_fraction, predictor, d_model, loop, f_op and g_op may differ per
+ * grid_fraction, predictor, d_model, loop, f_op, g_op and zero_run may differ per
  * field; dtype, R1, R2, C1, C2 and lmax must equal per_field[0]'s) into the
  * slot d_out + f * slot_bytes (slot_bytes a multiple of 8 and >=
  * mcc_compress_bound). Fields run in launch chains of up to 64 whose kernels
@@ -246,13 +257,14 @@ mcc_status mcc_decompress_batch(mcc_plan plan, int n, const void *d_in, size_t s
  * dimension, with no plan and no residual component: Q = round(x / s) - K,
  * differences delta_i = Q_i - Q_(i-1) (delta_0 = Q_0) coded as symbols
  * delta + R1 or escapes, canonical Huffman, the same lane-group stream
- * (header dim 1, n_x = n, flags = 32). The bin is s = 2 (tau - m)(1 - 2^-20)
+ * (header dim 1, n_x = n, flags = 32, or 32 | 64 with the zero-run stage).
+ * The bin is s = 2 (tau - m)(1 - 2^-20)
  * with the margin m = 4 u64(M) (+ 2 u32(M) for FP32 values), u the value
  * type's spacing at M = max |x|: the roundings of x / s, of s (K + Q) and of
  * the cast stay inside it, so |x - x'| <= tau at every value and no value is
  * stored raw. MCC_ERR_RANGE when tau <= m or the codes exceed 2^29 bins.
  * Parameters as for the method (R1, C1, lmax, dtype, eb_mode, eb; R2 and C2
- * are recorded); predictor, loop and operators must be the defaults. The
+ * are recorded; zero_run applies); predictor, loop and operators must be the defaults. The
  * buffers follow the rules of mcc_compress / mcc_decompress. */
 mcc_status mcc_workspace_size_1d(int64_t n, const mcc_params *p, size_t *compress_bytes,
                                  size_t *decompress_bytes);

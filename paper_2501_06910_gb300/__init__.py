@@ -58,12 +58,12 @@ class _GridSpec(C.Structure):
 
 class Params(C.Structure):
     """mcc_params: dtype, eb_mode, eb, grid_fraction, R1, R2, C1, C2, lmax,
-    predictor, d_model, loop, f_op, g_op."""
+    predictor, d_model, loop, f_op, g_op, zero_run."""
     _fields_ = [("dtype", C.c_int), ("eb_mode", C.c_int), ("eb", C.c_double),
                 ("grid_fraction", C.c_double), ("R1", C.c_int), ("R2", C.c_int),
                 ("C1", C.c_int), ("C2", C.c_int), ("lmax", C.c_int),
                 ("predictor", C.c_int), ("d_model", C.c_void_p), ("loop", C.c_int),
-                ("f_op", C.c_int), ("g_op", C.c_int)]
+                ("f_op", C.c_int), ("g_op", C.c_int), ("zero_run", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -179,7 +179,8 @@ def params_default(model=None, auto=False, open_loop=False, **overrides) -> Para
     learned predictor, or with ``auto`` the smaller of learned and plain;
     ``open_loop`` takes the residual against the unquantised grid component
     (bound tau1 + tau2); ``f_op`` ("barycentric" / "cluster") and ``g_op``
-    ("multilinear" / "nearest") pick the operators. The structure keeps a
+    ("multilinear" / "nearest") pick the operators; ``zero_run=True`` turns
+    on the zero-run stage before the Huffman coder. The structure keeps a
     reference to the tensor."""
     p = Params()
     load().mcc_params_default(C.byref(p))
@@ -200,6 +201,8 @@ def params_default(model=None, auto=False, open_loop=False, **overrides) -> Para
             v = F64 if v in (torch.float64, "float64", "f64") else F32
         if k == "eb_mode" and isinstance(v, str):
             v = REL if v == "rel" else ABS
+        if k == "zero_run" and isinstance(v, bool):
+            v = int(v)
         setattr(p, k, v)
     return p
 

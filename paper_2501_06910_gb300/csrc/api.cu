@@ -26,6 +26,7 @@ extern "C" void mcc_params_default(mcc_params *p) {
   p->loop = MCC_LOOP_CLOSED;
   p->f_op = MCC_F_BARYCENTRIC;
   p->g_op = MCC_G_MULTILINEAR;
+  p->zero_run = 0;
 }
 
 extern "C" const char *mcc_status_string(mcc_status s) {

@@ -43,10 +43,19 @@ enum : uint32_t {
   H_R2 = 28, H_C1 = 32, H_C2 = 36, H_LMAX = 40, H_NX = 44, H_NY = 48, H_NZ = 52, H_NV = 56,
   H_NG = 64, H_TAU = 72, H_TAU1 = 80, H_TAU2 = 88, H_S1 = 96, H_S2 = 104, H_K = 112,
   H_RHO21 = 120, H_RHO12 = 128, H_FILL = 136, H_NOUT1 = 144, H_NOUT2 = 152, H_NRAW = 160,
-  H_W1 = 168, H_W2 = 176, H_TOTAL = 184, H_MODEL = 192, H_QHI = 200
+  H_W1 = 168, H_W2 = 176, H_TOTAL = 184, H_MODEL = 192, H_QHI = 200,
+  H_RUNLEN = 208  // zero-run stage: code lengths of the run tokens 2R, 2R + 1 of
+                  // component 1 (bytes 208, 209) and component 2 (210, 211)
 };
 // header flags
-enum : uint32_t { F_GUARD = 1, F_MODEL = 2, F_OPEN = 4, F_GNEAR = 8, F_FCLUSTER = 16, F_ONED = 32 };
+enum : uint32_t {
+  F_GUARD = 1, F_MODEL = 2, F_OPEN = 4, F_GNEAR = 8, F_FCLUSTER = 16, F_ONED = 32, F_ZRUN = 64
+};
+// Zero-run stage: a maximal run of r zero symbols (symbol R) in a lane chunk
+// is coded as the digits d_i in {1, 2} of r = sum d_i 2^i (bijective base 2),
+// least significant first, token 2R + d_i - 1; a code book covers 2R + 2
+// tokens (the run tokens keep count 0, hence no code, without the stage).
+constexpr int kRunTokens = 2;
 
 __host__ __device__ inline uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 __host__ __device__ inline int64_t ngroups(int64_t n, int C) {

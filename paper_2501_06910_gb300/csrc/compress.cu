@@ -58,7 +58,8 @@ struct CompArgs {
   unsigned char mode[kMaxBatch];          // MCC_PRED_* per field
   unsigned char open[kMaxBatch];          // MCC_LOOP_OPEN per field
   unsigned char fop[kMaxBatch], gop[kMaxBatch];  // MCC_F_* / MCC_G_* per field
-  int any_auto;
+  unsigned char zr[kMaxBatch];            // zero-run stage per field
+  int any_auto, any_zr;
   int one_d;  // the 1D coder: component 1 holds the vertex codes' differences
 };
 
@@ -68,7 +69,7 @@ struct Ctx {
   unsigned int *hist1, *hist2, *code1, *code2, *gw, *ge, *gr, *pe, *pr;
   unsigned char *len1, *len2, *out;
   int *Q, *q1, *val1, *val2;
-  unsigned short *sym1, *sym2, *pb;
+  unsigned short *sym1, *sym2, *pb, *rs;
   float *p;
   const void *x;
 };
@@ -97,6 +98,7 @@ __device__ __forceinline__ Ctx ctx_of(const CompArgs &A, int f, bool chosen = fa
   c.ge = (unsigned int *)(ws + A.W.ge);
   c.gr = (unsigned int *)(ws + A.W.gr);
   c.pb = (unsigned short *)(ws + A.W.pb);
+  c.rs = (unsigned short *)(ws + (b ? A.W.rsb : A.W.rs));
   c.pe = (unsigned int *)(ws + A.W.pe);
   c.pr = (unsigned int *)(ws + A.W.pr);
   c.p = (float *)(ws + A.W.p);
@@ -944,7 +946,8 @@ struct CodebookArgs {
   int nsym;
   unsigned int *code;
   unsigned char *len;
-  unsigned char *stream_lens;
+  unsigned char *stream_lens;  // the 2R symbols' lengths in the stream (or NULL)
+  int zsym;                    // the zero-run stage's zero symbol R (no token), or -1
 };
 
 constexpr int kBatchMin = 24;
@@ -973,9 +976,11 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
                        c1 ? AA.nsym1 : AA.nsym2,
                        c1 ? c.code1 : (side_b ? (unsigned int *)(ws + AA.W.code2b) : c.code2),
                        c1 ? c.len1 : (side_b ? ws + AA.W.len2b : c.len2),
-                       c1 ? c.out + AA.F.lens1 : (autof ? nullptr : c.out + AA.F.lens2)};
+                       c1 ? c.out + AA.F.lens1 : (autof ? nullptr : c.out + AA.F.lens2),
+                       AA.zr[blockIdx.y] ? (c1 ? AA.R1 : AA.R2) : -1};
   const int nsym = A.nsym;
-  int npn = 1;  // power of two >= nsym: room for the sort's padding
+  const int nstream = c1 ? 2 * AA.R1 : 2 * AA.R2;  // lengths stored in the lens section
+  int npn = 1;  // power of two >= nsym: the shared-memory size of the sort
   while (npn < nsym) npn <<= 1;
   unsigned int *cnt = (unsigned int *)smem;                                // [nsym]
   unsigned long long *keyA = (unsigned long long *)(cnt + nsym);           // [nsym] (nsym even)
@@ -998,7 +1003,8 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
   {
     int mloc = 0;
     for (int s = tid; s < nsym; s += blockDim.x) {
-      cnt[s] = A.hist[s];
+      // with the zero-run stage the zero symbol is coded as run digits only
+      cnt[s] = s == A.zsym ? 0u : A.hist[s];
       lens[s] = 0;
       mloc += cnt[s] != 0;
     }
@@ -1017,20 +1023,26 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
       return;
     }
     if (tid == 0) { kpos = 0; maxlen = 0; sa = 0; sb = 0; sc = 0; }
-    // bitonic sort of the (count, symbol) keys of all npn slots into sk:
-    // unused symbols and padding carry ~0 and sort last, so sk[0 .. m) are
-    // the used symbols in (count, symbol) order
-    if ((int)blockDim.x >= npn) {
+    __syncthreads();
+    // the m used symbols' (count, symbol) keys, compacted into keyA in any
+    // order (the sort fixes it)
+    for (int s = tid; s < nsym; s += blockDim.x)
+      if (cnt[s]) keyA[atomicAdd(&kpos, 1)] = ((unsigned long long)cnt[s] << 32) | (unsigned)s;
+    __syncthreads();
+    int mp = 1;  // power of two >= m: the sort's width (padding carries ~0)
+    while (mp < m) mp <<= 1;
+    // bitonic sort of the keys into sk: sk[0 .. m) are the used symbols in
+    // (count, symbol) order
+    if ((int)blockDim.x >= mp) {
       // one key per thread; partners closer than 32 by warp shuffles
-      unsigned long long x = tid < nsym && cnt[tid] ? ((unsigned long long)cnt[tid] << 32) | (unsigned)tid
-                                                   : ~0ull;
-      for (int kk = 2; kk <= npn; kk <<= 1)
+      unsigned long long x = tid < m ? keyA[tid] : ~0ull;
+      for (int kk = 2; kk <= mp; kk <<= 1)
         for (int j = kk >> 1; j > 0; j >>= 1) {
           unsigned long long y;
           if (j >= 32) {
-            if (tid < npn) sk[tid] = x;
+            if (tid < mp) sk[tid] = x;
             __syncthreads();
-            y = tid < npn ? sk[tid ^ j] : x;
+            y = tid < mp ? sk[tid ^ j] : x;
             __syncthreads();
           } else {
             y = __shfl_xor_sync(0xffffffffu, x, j);
@@ -1038,15 +1050,14 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
           const bool up = (tid & kk) == 0, lower = (tid & j) == 0;
           x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
         }
-      if (tid < npn) sk[tid] = x;
+      if (tid < mp) sk[tid] = x;
       __syncthreads();
     } else {
-      for (int i = tid; i < npn; i += blockDim.x)
-        sk[i] = i < nsym && cnt[i] ? ((unsigned long long)cnt[i] << 32) | (unsigned)i : ~0ull;
+      for (int i = tid; i < mp; i += blockDim.x) sk[i] = i < m ? keyA[i] : ~0ull;
       __syncthreads();
-      for (int kk = 2; kk <= npn; kk <<= 1)
+      for (int kk = 2; kk <= mp; kk <<= 1)
         for (int j = kk >> 1; j > 0; j >>= 1) {
-          for (int i = tid; i < npn; i += blockDim.x) {
+          for (int i = tid; i < mp; i += blockDim.x) {
             const int q = i ^ j;
             if (q > i) {
               const unsigned long long x0 = sk[i], x1 = sk[q];
@@ -1183,7 +1194,7 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
   for (int s = tid; s < nsym; s += blockDim.x) {
     const int L = lens[s];
     A.len[s] = (unsigned char)L;
-    if (A.stream_lens) A.stream_lens[s] = (unsigned char)L;
+    if (A.stream_lens && s < nstream) A.stream_lens[s] = (unsigned char)L;
     A.code[s] = L ? ct.first[L] + rank[s] : 0u;
   }
 }
@@ -1226,14 +1237,15 @@ __global__ void __launch_bounds__(256) k_choose(const __grid_constant__ CompArgs
     unsigned long long z = 0, l = 0;
     for (int w = 0; w < 8; w++) { z += part[0][w]; l += part[1][w]; }
     const unsigned long long vbits = A.dtype == MCC_F64 ? 64 : 32;
-    z += 32ull * h0[0] + vbits * h0[nsym - 1];
-    l += 32ull * h1[0] + vbits * h1[nsym - 1] + 8ull * kModelBytes;
+    const int raw = 2 * A.R2 - 1;  // the raw-value symbol
+    z += 32ull * h0[0] + vbits * h0[raw];
+    l += 32ull * h1[0] + vbits * h1[raw] + 8ull * kModelBytes;
     pick = l < z ? 1u : 0u;
     st->pick = pick;
   }
   __syncthreads();
   const unsigned char *ls = pick ? l1 : l0;
-  for (int s = threadIdx.x; s < nsym; s += blockDim.x) c.out[A.F.lens2 + s] = ls[s];
+  for (int s = threadIdx.x; s < 2 * A.R2; s += blockDim.x) c.out[A.F.lens2 + s] = ls[s];
 }
 
 size_t codebook_smem(int nsym) {
@@ -1250,6 +1262,120 @@ size_t codebook_smem(int nsym) {
 // totals to the stream's lane table, group totals to gw / ge / gr.
 // ---------------------------------------------------------------------------
 constexpr int kParts = 8;
+
+// ---------------------------------------------------------------------------
+// Zero-run stage. A run of r zero symbols is coded as the digits d_i in
+// {1, 2} of r = sum d_i 2^i (bijective base 2), least significant first.
+// These digits are the bits of r + 1 below its leading one, each plus one
+// (r + 1 = 2^n + sum (d_i - 1) 2^i), so a run has n = floor(log2(r + 1))
+// digits, popc(r + 1) - 1 of them 2s.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int run_bits(unsigned int r, unsigned int l1, unsigned int l2) {
+  if (!r) return 0;
+  const unsigned int v = r + 1, nd = 31 - __clz(v), n2 = __popc(v) - 1;
+  return (nd - n2) * l1 + n2 * l2;
+}
+
+// ---------------------------------------------------------------------------
+// k_runs (zero-run stage): one CTA per group of 32 lane chunks, warp w over
+// steps [w C / 8, (w+1) C / 8) of every lane as in k_group_len. Each (part,
+// lane) finds the zero symbols before its first other symbol and after its
+// last one, and counts the digits of the runs between; warp 0 then chains the
+// parts of each lane: the run that ends at the first other symbol of part w
+// began in an earlier part when the parts between hold zeros only. These runs
+// go to rs[group][kParts + 1][32] (entry w: the run ending in part w, entry
+// kParts: the run ending the lane), and every digit to the component's
+// histogram (tokens 2R, 2R + 1). Blocks past the groups of both components
+// take the learned side of an auto field.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_runs(const __grid_constant__ CompArgs A) {
+  pdl_trigger();
+  pdl_wait();
+  const int fi = blockIdx.y;
+  const int64_t ng = A.ng1 + A.ng2;
+  const bool side_b = (int64_t)blockIdx.x >= ng;
+  if (!A.zr[fi] || (side_b && A.mode[fi] != MCC_PRED_AUTO)) return;  // uniform per block
+  const Ctx c = ctx_of(A, fi);
+  if (block_failed(c.st)) return;
+  unsigned char *ws = A.ws0 + (int64_t)fi * A.wss;
+  const int64_t gi = side_b ? (int64_t)blockIdx.x - A.ng2 : blockIdx.x;  // side b: ng1 + g
+  const bool c1 = gi < A.ng1;
+  const int64_t g = c1 ? gi : gi - A.ng1;
+  const int C = c1 ? A.C1 : A.C2, R = c1 ? A.R1 : A.R2;
+  const int64_t n = c1 ? A.pv.n_g : A.pv.n_v;
+  const unsigned short *sym =
+      c1 ? c.sym1 : (side_b ? (const unsigned short *)(ws + A.W.sym2b) : c.sym2);
+  unsigned int *hist = c1 ? c.hist1 : (side_b ? (unsigned int *)(ws + A.W.hist2b) : c.hist2);
+  unsigned short *rs = (unsigned short *)(ws + (side_b ? A.W.rsb : A.W.rs)) +
+                       gi * (kParts + 1) * 32;
+  __shared__ unsigned short lead[kParts][32], trail[kParts][32];
+  __shared__ unsigned char seen_s[kParts][32];
+  __shared__ unsigned int dig[2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x < 2) dig[threadIdx.x] = 0;
+  const int k0 = (w * C) / kParts, k1 = ((w + 1) * C) / kParts;
+  const int64_t base = g * 32 * (int64_t)C + lane;
+  unsigned int run = 0, first = 0, n1 = 0, n2 = 0;
+  bool seen = false;
+#pragma unroll 4
+  for (int k = k0; k < k1; k++) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (p < n) {
+      if (__ldg(sym + p) == R) {
+        run++;
+      } else {
+        if (!seen) {
+          first = run;
+          seen = true;
+        } else if (run) {
+          const unsigned int v = run + 1, nd = 31 - __clz(v), b2 = __popc(v) - 1;
+          n1 += nd - b2;
+          n2 += b2;
+        }
+        run = 0;
+      }
+    }
+  }
+  lead[w][lane] = (unsigned short)(seen ? first : run);  // a part of zeros only: all of them
+  trail[w][lane] = (unsigned short)(seen ? run : 0);
+  seen_s[w][lane] = seen ? 1 : 0;
+  __syncthreads();
+  if (w == 0) {
+    unsigned int carry = 0;
+#pragma unroll
+    for (int q = 0; q < kParts; q++) {
+      unsigned int r = 0;
+      if (seen_s[q][lane]) {
+        r = carry + lead[q][lane];
+        carry = trail[q][lane];
+      } else {
+        carry += lead[q][lane];
+      }
+      rs[q * 32 + lane] = (unsigned short)r;
+      if (r) {
+        const unsigned int v = r + 1, nd = 31 - __clz(v), b2 = __popc(v) - 1;
+        n1 += nd - b2;
+        n2 += b2;
+      }
+    }
+    rs[kParts * 32 + lane] = (unsigned short)carry;
+    if (carry) {
+      const unsigned int v = carry + 1, nd = 31 - __clz(v), b2 = __popc(v) - 1;
+      n1 += nd - b2;
+      n2 += b2;
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+    n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  }
+  if (lane == 0 && (n1 | n2)) {
+    atomicAdd(&dig[0], n1);
+    atomicAdd(&dig[1], n2);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 && dig[threadIdx.x]) atomicAdd(hist + 2 * R + threadIdx.x, dig[threadIdx.x]);
+}
 
 struct GroupArgs {
   const unsigned short *sym1, *sym2;
@@ -1286,20 +1412,49 @@ __global__ void __launch_bounds__(256) k_group_len(const __grid_constant__ CompA
   const unsigned char *lsrc = c1 ? a.len1 : a.len2;
   for (int i = threadIdx.x; i < nsym; i += blockDim.x) L[i] = lsrc[i];
   __syncthreads();
-  const int rawsym = c1 ? kRawNone : a.nsym2 - 1;
+  const int R = c1 ? A.R1 : A.R2;
+  const int rawsym = c1 ? kRawNone : 2 * A.R2 - 1;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int k0 = (w * C) / kParts, k1 = ((w + 1) * C) / kParts;
   const int64_t base = g * 32 * (int64_t)C + lane;
   unsigned int bits = 0, esc = 0, raw = 0;
+  if (!A.zr[blockIdx.y]) {
 #pragma unroll 4
-  for (int k = k0; k < k1; k++) {
-    const int64_t p = base + 32 * (int64_t)k;
-    if (p < n) {
-      const int sy = __ldg(sym + p);
-      bits += L[sy];
-      esc += sy == 0;
-      raw += sy == rawsym;
+    for (int k = k0; k < k1; k++) {
+      const int64_t p = base + 32 * (int64_t)k;
+      if (p < n) {
+        const int sy = __ldg(sym + p);
+        bits += L[sy];
+        esc += sy == 0;
+        raw += sy == rawsym;
+      }
     }
+  } else {
+    // zero-run stage: a run is costed where it ends, the runs that reach
+    // back into earlier parts (and the lane's last run) from k_runs
+    const unsigned int l1 = L[2 * R], l2 = L[2 * R + 1];
+    unsigned int run = 0;
+    bool seen = false;
+#pragma unroll 4
+    for (int k = k0; k < k1; k++) {
+      const int64_t p = base + 32 * (int64_t)k;
+      if (p < n) {
+        const int sy = __ldg(sym + p);
+        if (sy == R) {
+          run++;
+        } else {
+          if (seen) bits += run_bits(run, l1, l2);
+          seen = true;
+          run = 0;
+          bits += L[sy];
+          esc += sy == 0;
+          raw += sy == rawsym;
+        }
+      }
+    }
+    const unsigned short *rs = c.rs + gi * (kParts + 1) * 32;
+    bits += run_bits(rs[w * 32 + lane], l1, l2);
+    if (w == kParts - 1) bits += run_bits(rs[kParts * 32 + lane], l1, l2);
   }
   a.pb[(gi * kParts + w) * 32 + lane] = (unsigned short)bits;
   sbits[w][lane] = bits;
@@ -1459,11 +1614,12 @@ __device__ void scan_field(const CompArgs &A, int fi) {
       put32(o + H_DTYPE, (uint32_t)a.dtype);
       put32(o + H_DIM, (uint32_t)a.dim);
       const bool open = A.open[fi] != 0;
-      if (A.one_d) put32(o + H_FLAGS, F_ONED);
+      const uint32_t zflag = A.zr[fi] ? F_ZRUN : 0u;
+      if (A.one_d) put32(o + H_FLAGS, F_ONED | zflag);
       else put32(o + H_FLAGS, (f.guard || open ? F_GUARD : 0u) | (model ? F_MODEL : 0u) |
                              (open ? F_OPEN : 0u) |
                              (A.gop[fi] == MCC_G_NEAREST ? F_GNEAR : 0u) |
-                             (A.fop[fi] == MCC_F_CLUSTER ? F_FCLUSTER : 0u));
+                             (A.fop[fi] == MCC_F_CLUSTER ? F_FCLUSTER : 0u) | zflag);
       put32(o + H_R1, (uint32_t)a.R1);
       put32(o + H_R2, (uint32_t)a.R2);
       put32(o + H_C1, (uint32_t)a.C1);
@@ -1491,6 +1647,15 @@ __device__ void scan_field(const CompArgs &A, int fi) {
       put64(o + H_TOTAL, L.total);
       put64(o + H_MODEL, model ? kModelBytes : 0);
       put64(o + H_QHI, (uint64_t)f.Qhi);
+      if (zflag) {  // the run tokens' code lengths (of the chosen residual side)
+        const Ctx cc = ctx_of(A, fi, true);
+        o[H_RUNLEN] = cc.len1[2 * a.R1];
+        o[H_RUNLEN + 1] = cc.len1[2 * a.R1 + 1];
+        if (!A.one_d) {
+          o[H_RUNLEN + 2] = cc.len2[2 * a.R2];
+          o[H_RUNLEN + 3] = cc.len2[2 * a.R2 + 1];
+        }
+      }
       // zero the alignment padding between sections
       for (uint64_t p = F.lens2 + 2 * (uint64_t)a.R2; p < F.gtab1; p++) o[p] = 0;
       for (uint64_t p = L.out2 + 4 * e2; p < L.raw; p++) o[p] = 0;
@@ -1525,6 +1690,9 @@ struct PackArgs {
   const unsigned int *pe, *pr;
 };
 
+// ZR: the batch has a field with the zero-run stage (a separate variant keeps
+// the plain one's register count)
+template <bool ZR>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
@@ -1548,7 +1716,9 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A
   const unsigned int *csrc = c1 ? a.code1 : a.code2;
   const unsigned char *lsrc = c1 ? a.len1 : a.len2;
   const int *val = c1 ? a.val1 : a.val2;
-  const int rawsym = c1 ? kRawNone : a.nsym2 - 1;
+  const int R = c1 ? A.R1 : A.R2;
+  const int rawsym = c1 ? kRawNone : 2 * A.R2 - 1;
+  const bool zr = ZR && A.zr[blockIdx.y] != 0;
   unsigned char *o = a.out;
   const unsigned int *gtab = (const unsigned int *)(o + (c1 ? L.gtab1 : L.gtab2));
   const unsigned int *etab = (const unsigned int *)(o + (c1 ? L.etab1 : L.etab2));
@@ -1582,17 +1752,42 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A
   const int k0 = (w * C) / kParts, k1 = ((w + 1) * C) / kParts;
   const int64_t base = g * 32 * (int64_t)C + lane;
   const unsigned lt = (1u << lane) - 1;
+  // a code of cl >= 1 bits at the lane's bit position
+  auto put = [&](unsigned int code, unsigned int cl) {
+    const unsigned long long v = ((unsigned long long)code << (64 - cl)) >> (pos & 31);
+    atomicOr(stage + (pos >> 5), (unsigned int)(v >> 32));
+    if ((pos & 31) + cl > 32) atomicOr(stage + (pos >> 5) + 1, (unsigned int)v);
+    pos += cl;
+  };
+  // zero-run stage: the digits of a run, least significant first (bit i of
+  // r + 1 below its leading one selects token 2R + bit)
+  auto put_run = [&](unsigned int r) {
+    if (!r) return;
+    const unsigned int v = r + 1, nd = 31 - __clz(v);
+    for (unsigned int i = 0; i < nd; i++) {
+      const int t = 2 * R + (int)((v >> i) & 1u);
+      put(scode[t], slen[t]);
+    }
+  };
+  const unsigned short *rs = c.rs + gi * (kParts + 1) * 32;
+  unsigned int run = 0;
+  bool seen = false;
 #pragma unroll 4
   for (int k = k0; k < k1; k++) {
     const int64_t p = base + 32 * (int64_t)k;
     const bool valid = p < n;
     const int sy = valid ? (int)__ldg(sym + p) : -1;
     if (valid) {
-      const unsigned int cl = slen[sy];
-      const unsigned long long v = ((unsigned long long)scode[sy] << (64 - cl)) >> (pos & 31);
-      atomicOr(stage + (pos >> 5), (unsigned int)(v >> 32));
-      if ((pos & 31) + cl > 32) atomicOr(stage + (pos >> 5) + 1, (unsigned int)v);
-      pos += cl;
+      if (zr && sy == R) {
+        run++;
+      } else {
+        if (zr) {  // the run that ends here (the first one may reach back)
+          put_run(seen ? run : rs[w * 32 + lane]);
+          seen = true;
+          run = 0;
+        }
+        put(scode[sy], slen[sy]);
+      }
     }
     const unsigned em = __ballot_sync(0xffffffffu, sy == 0);
     if (sy == 0) outv[e_run + __popc(em & lt)] = __ldg(val + p);
@@ -1607,6 +1802,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A
       r_run += __popc(rm);
     }
   }
+  if (zr && w == kParts - 1) put_run(rs[kParts * 32 + lane]);  // the lane's last run
   __syncthreads();
   for (unsigned int i = threadIdx.x; i < nw; i += blockDim.x) bits[w0 + i] = stage[i];
 }
@@ -1654,6 +1850,12 @@ mcc_status check_params(const mcc_params *p) {
   if (p->f_op != MCC_F_BARYCENTRIC && p->f_op != MCC_F_CLUSTER) return MCC_ERR_INVALID_ARG;
   if (p->g_op != MCC_G_MULTILINEAR && p->g_op != MCC_G_NEAREST) return MCC_ERR_INVALID_ARG;
   if (p->g_op == MCC_G_NEAREST && p->predictor != MCC_PRED_ZERO) return MCC_ERR_INVALID_ARG;
+  if (p->zero_run != 0 && p->zero_run != 1) return MCC_ERR_INVALID_ARG;
+  if (p->zero_run) {  // 2R + 2 tokens: the decode tables hold 2 kMaxR symbols
+    if (p->R1 > kMaxR - 1 || p->R2 > kMaxR - 1) return MCC_ERR_UNSUPPORTED;
+    if (2 * p->R1 + kRunTokens > (1 << p->lmax) || 2 * p->R2 + kRunTokens > (1 << p->lmax))
+      return MCC_ERR_INVALID_ARG;
+  }
   return MCC_OK;
 }
 
@@ -1662,12 +1864,14 @@ CompressWs compress_ws_layout(const PlanView &pv, const mcc_params *p) {
   size_t o = kStatusBytes;
   auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
   const int64_t ng1 = ngroups(pv.n_g, p->C1), ng2 = ngroups(pv.n_v, p->C2);
-  w.hist1 = take(4 * 2 * (size_t)p->R1);
-  w.hist2 = take(4 * 2 * (size_t)p->R2);
-  w.code1 = take(4 * 2 * (size_t)p->R1);
-  w.code2 = take(4 * 2 * (size_t)p->R2);
-  w.len1 = take(2 * (size_t)p->R1);
-  w.len2 = take(2 * (size_t)p->R2);
+  // code books: 2R symbols and the zero-run stage's run tokens
+  const size_t ns1 = 2 * (size_t)p->R1 + kRunTokens, ns2 = 2 * (size_t)p->R2 + kRunTokens;
+  w.hist1 = take(4 * ns1);
+  w.hist2 = take(4 * ns2);
+  w.code1 = take(4 * ns1);
+  w.code2 = take(4 * ns2);
+  w.len1 = take(ns1);
+  w.len2 = take(ns2);
   w.Q = take(4 * (size_t)pv.n_v);
   w.q1 = take(4 * (size_t)pv.n_g);
   w.sym1 = take(2 * (size_t)pv.n_g);
@@ -1681,12 +1885,14 @@ CompressWs compress_ws_layout(const PlanView &pv, const mcc_params *p) {
   w.pe = take(4 * kParts * (size_t)(ng1 + ng2));
   w.pr = take(4 * kParts * (size_t)(ng1 + ng2));
   w.p = take(4 * (size_t)pv.n_v);
-  w.hist2b = take(4 * 2 * (size_t)p->R2);
-  w.code2b = take(4 * 2 * (size_t)p->R2);
-  w.len2b = take(2 * (size_t)p->R2);
+  w.hist2b = take(4 * ns2);
+  w.code2b = take(4 * ns2);
+  w.len2b = take(ns2);
   w.sym2b = take(2 * (size_t)pv.n_v);
   w.val2b = take(4 * (size_t)pv.n_v);
   w.x1v = take(8 * (size_t)pv.n_g);
+  w.rs = take(2 * (kParts + 1) * 32 * (size_t)(ng1 + ng2));
+  w.rsb = take(2 * (kParts + 1) * 32 * (size_t)(ng1 + ng2));
   w.csum = take(8 * (size_t)pv.n_g);
   w.ccnt = take(4 * (size_t)pv.n_g);
   w.total = o;
@@ -1719,8 +1925,14 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   A.C1 = p->C1;
   A.C2 = p->C2;
   A.lmax = p->lmax;
-  A.nsym1 = 2 * p->R1;
-  A.nsym2 = 2 * p->R2;
+  for (int f = 0; f < nf; f++) {
+    A.zr[f] = ps[f].zero_run ? 1 : 0;
+    A.any_zr = A.any_zr || A.zr[f];
+  }
+  // code books over the 2R symbols, plus the run tokens when a field of the
+  // batch takes the zero-run stage
+  A.nsym1 = 2 * p->R1 + (A.any_zr ? kRunTokens : 0);
+  A.nsym2 = 2 * p->R2 + (A.any_zr ? kRunTokens : 0);
   A.one_d = pv.dim == 1;  // the 1D coder: no residual component
   A.ng1 = ngroups(pv.n_g, p->C1);
   A.ng2 = A.one_d ? 0 : ngroups(pv.n_v, p->C2);
@@ -1747,7 +1959,8 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_pack<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_pack<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   if (cudaMemset2DAsync(ws0, (size_t)wss, 0, kStatusBytes, (size_t)nf, stream) != cudaSuccess)
@@ -1822,6 +2035,11 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     }
 #undef MCC_NODE
   }
+  if (A.any_zr) {
+    PROF_SCOPE("k_runs", stream);
+    launch_pdl(k_runs, dim3((unsigned int)(ng + (A.any_auto ? A.ng2 : 0)), nf), dim3(256), 0,
+               stream, A);
+  }
   {
     PROF_SCOPE("k_codebook", stream);
     const size_t cbsm = codebook_smem(A.nsym1 > A.nsym2 ? A.nsym1 : A.nsym2);
@@ -1839,7 +2057,8 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     PROF_SCOPE("k_pack", stream);
     const int cmax = p->C1 > p->C2 ? p->C1 : p->C2;
     const size_t stage_bytes = 4 * (size_t)cmax * p->lmax;  // worst-case words of one group
-    launch_pdl(k_pack, dim3((unsigned int)ng, nf), dim3(256), stage_bytes, stream, A);
+    if (A.any_zr) launch_pdl(k_pack<true>, dim3((unsigned int)ng, nf), dim3(256), stage_bytes, stream, A);
+    else launch_pdl(k_pack<false>, dim3((unsigned int)ng, nf), dim3(256), stage_bytes, stream, A);
   }
   if (cudaGetLastError() != cudaSuccess) return MCC_ERR_CUDA;
   return MCC_OK;

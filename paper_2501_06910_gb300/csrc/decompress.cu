@@ -103,9 +103,11 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
   I.dtype = (int)ld32(h + H_DTYPE);
   I.dim = (int)ld32(h + H_DIM);
   const uint32_t flags = ld32(h + H_FLAGS);
-  if (flags & ~(F_GUARD | F_MODEL | F_OPEN | F_GNEAR | F_FCLUSTER | F_ONED)) return false;
-  // a 1D stream has this flag alone, and only 1D streams have it
-  if (a.dim == 1 ? flags != F_ONED : (flags & F_ONED) != 0) return false;
+  if (flags & ~(F_GUARD | F_MODEL | F_OPEN | F_GNEAR | F_FCLUSTER | F_ONED | F_ZRUN)) return false;
+  // a 1D stream has this flag alone (or with the zero-run stage's), and only
+  // 1D streams have it
+  if (a.dim == 1 ? (flags & ~F_ZRUN) != F_ONED : (flags & F_ONED) != 0) return false;
+  I.zr = (flags & F_ZRUN) ? 1 : 0;
   I.use_model = (flags & F_MODEL) ? 1 : 0;
   I.open = (flags & F_OPEN) ? 1 : 0;
   I.gnear = (flags & F_GNEAR) ? 1 : 0;  // (F_FCLUSTER concerns compression only)
@@ -124,6 +126,7 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
   I.C2 = (int)ld32(h + H_C2);
   I.lmax = (int)ld32(h + H_LMAX);
   if (I.R1 < 4 || I.R1 > kMaxR || I.R2 < 4 || I.R2 > kMaxR) return false;
+  if (I.zr && (I.R1 > kMaxR - 1 || I.R2 > kMaxR - 1)) return false;  // 2R + 2 tokens fit the tables
   if (I.C1 < 1 || I.C1 > kMaxC || I.C2 < 1 || I.C2 > kMaxC) return false;
   if (I.lmax < 1 || I.lmax > kMaxLen) return false;
   I.s2 = __longlong_as_double((long long)ld64(h + H_S2));
@@ -192,11 +195,12 @@ __global__ void __launch_bounds__(1024) k_dec_prep(const __grid_constant__ DecAr
   }
   __syncthreads();
   if (!ok) return;
-  const int nsym = blockIdx.x == 0 ? 2 * I.R1 : 2 * I.R2;
+  const int ns = blockIdx.x == 0 ? 2 * I.R1 : 2 * I.R2;  // lengths in the lens section
+  const int nsym = ns + (I.zr ? kRunTokens : 0);           // the zero-run stage's run tokens
   const unsigned char *src = a.in + (blockIdx.x == 0 ? I.L.lens1 : I.L.lens2);
   DecTab *T = blockIdx.x == 0 ? a.tab1 : a.tab2;
   for (int s = threadIdx.x; s < nsym; s += blockDim.x) {
-    lens[s] = src[s];
+    lens[s] = s < ns ? src[s] : hdr[H_RUNLEN + 2 * blockIdx.x + (s - ns)];
     if (lens[s] > I.lmax) bad = 1;
   }
   __syncthreads();
@@ -225,7 +229,9 @@ __global__ void __launch_bounds__(1024) k_dec_prep(const __grid_constant__ DecAr
   // window (at most four), entry = l1 | total << 4 | count << 8 |
   // sym_j << (11 + 12 j): l1 the first code's length (0: longer than the
   // window), total the length of all `count` codes. Built in two passes: the
-  // first code of every window (single), then chains of lookups in it.
+  // first code of every window (single), then chains of lookups in it. A
+  // run token (zero-run stage) is never chained: it stands alone in its
+  // entry, and a chain stops before one.
   const int lb = I.lmax < kLutBits ? I.lmax : kLutBits;
   for (int e = threadIdx.x; e < (1 << kLutBits); e += blockDim.x) {
     unsigned int v = 0;
@@ -246,10 +252,12 @@ __global__ void __launch_bounds__(1024) k_dec_prep(const __grid_constant__ DecAr
       const unsigned int sv = single[((unsigned int)e << used) & ((1u << kLutBits) - 1)];
       const int l = (int)(sv & 15);
       if (!l || used + l > kLutBits) break;  // the window's zero padding is not code
+      if ((int)(sv >> 8) >= ns && cnt) break;  // a run token after a symbol
       v |= (unsigned long long)(sv >> 8) << (11 + 12 * cnt);
       if (cnt == 0) v |= (unsigned long long)l;
       used += l;
       cnt++;
+      if ((int)(sv >> 8) >= ns) break;  // a run token stands alone
     }
     if (cnt) v |= ((unsigned long long)used << 4) | ((unsigned long long)cnt << 8);
     T->lut[e] = v;
@@ -381,8 +389,13 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
   const int *outv = (const int *)(in + (c1 ? I.L.out1 : I.L.out2));
   const T *rawv = (const T *)(in + I.L.raw);
   int *dst = c1 ? delta : q2s;
-  const bool fast = Tb.count[1] == 1;          // a symbol owns the code "0"
-  const unsigned short s0 = Tb.sorted[0];      // (the first canonical symbol)
+  // zero-run stage: run tokens 2R (digit 1) and 2R + 1 (digit 2); the
+  // chunk is pre-filled with the zero symbol R and a digit d at digit
+  // position i skips d 2^i steps
+  const bool zr = I.zr != 0;
+  const int tok0 = 2 * R;
+  const bool fast = !zr && Tb.count[1] == 1;   // a symbol owns the code "0"
+  const unsigned short s0 = zr ? (unsigned short)R : Tb.sorted[0];  // the pre-fill symbol
   unsigned short *buf = sbuf + (size_t)wid * kDecRound * 32;
   const int64_t b0 = c1 ? blockIdx.x : blockIdx.x - nb1;
   const int64_t nblocks = c1 ? nb1 : gridDim.x - nb1;
@@ -408,7 +421,7 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
     const int cnt = left <= 0 ? 0 : (int)min((int64_t)C, (left + 31) / 32);
     bool lane_bad = false;
     unsigned int used = 0, e_run = e0, r_run = r0;
-    int k = 0;
+    int k = 0, digit = 0;
     // a group without escapes or raw values takes the vectorised emit path
     const bool simple = e0 == e1 && (c1 || r0 == r1);
     for (int kb = 0; kb < C; kb += kDecRound) {
@@ -418,7 +431,7 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
       if (p0 >= n) break;
       // ---- phase 1: decode this round of the lane's chunk into shared memory
       // (buf holds the round's positions in order: p0 + 32 (k - kb) + lane)
-      if (fast) {
+      if (fast || zr) {
         const unsigned int f2 = (unsigned int)s0 | ((unsigned int)s0 << 16);
         const uint4 f4 = make_uint4(f2, f2, f2, f2);
         for (int q = lane; q < steps * 4; q += 32) reinterpret_cast<uint4 *>(buf)[q] = f4;
@@ -441,7 +454,7 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
         if (len) {
           const int cnt = (int)((e >> 8) & 7);
           if (cnt > 1 && k + cnt <= kend) {  // every complete code in the window
-            len = (int)((e >> 4) & 15);
+            len = (int)((e >> 4) & 15);      // (symbols only: run tokens stand alone)
             unsigned short *bp = buf + (k - kb) * 32 + lane;
             bp[0] = (unsigned short)((e >> 11) & 0xFFF);
             if (cnt > 2) bp[32] = (unsigned short)((e >> 23) & 0xFFF);
@@ -466,6 +479,14 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
         r.buf <<= len;
         r.nb -= len;
         used += len;
+        if (zr && sym >= tok0) {  // a run digit: its zeros are pre-filled
+          const int z = (sym - tok0 + 1) << digit;
+          if (z > cnt - k) { lane_bad = true; break; }
+          k += z;
+          digit++;
+          continue;
+        }
+        digit = 0;
         buf[(k - kb) * 32 + lane] = (unsigned short)sym;
         k++;
       }

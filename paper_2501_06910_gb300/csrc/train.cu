@@ -750,6 +750,7 @@ extern "C" mcc_status mcc_model_train(mcc_plan plan, int n, const void *const *d
   pz.predictor = MCC_PRED_ZERO;
   pz.d_model = nullptr;
   pz.loop = MCC_LOOP_CLOSED;  // the predictor serves the closed loop only
+  pz.zero_run = 0;            // (the coder does not run in training)
   const PlanView pv = mcc_plan_view(plan);
   const TrainWs T = train_ws_layout(pv, &pz, cfg, n);
   if (workspace_bytes < T.total) return MCC_ERR_CAPACITY;

@@ -8,9 +8,11 @@ namespace mcc {
 // Compression workspace (byte offsets; the status block sits at 0).
 struct CompressWs {
   size_t hist1, hist2, code1, code2, len1, len2, Q, q1, sym1, sym2, val1, val2, gw, ge, gr, pb, pe,
-      pr, p, hist2b, code2b, len2b, sym2b, val2b, x1v, csum, ccnt, total;
-  // *b: the learned side of auto; x1v: open-loop x1 (FP64); csum / ccnt:
-  // cluster sums (u64) and sizes (u32) per grid node for the cluster-mean f
+      pr, p, hist2b, code2b, len2b, sym2b, val2b, x1v, rs, rsb, csum, ccnt, total;
+  // *b: the learned side of auto; x1v: open-loop x1 (FP64); rs / rsb: the
+  // zero-run stage's runs that end in each part of each lane (u16, per group
+  // [parts + 1][32]); csum / ccnt: cluster sums (u64) and sizes (u32) per
+  // grid node for the cluster-mean f
 };
 
 // Decode tables of one component: first-level table on kLutBits bits (up to
@@ -34,6 +36,7 @@ struct DecInfo {
   float rho12_f;
   int open;  // open-loop stream: x' = s2 (K + q2 + g(x1')) in FP64
   int gnear;  // nearest-node g
+  int zr;     // zero-run stage: code books of 2R + 2 tokens
   double s2;
   unsigned long long nout1, nout2, nraw, w1, w2;
   long long ng1, ng2;
