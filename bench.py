@@ -498,6 +498,11 @@ def main():
     st2, _ = mcc.workspace_result(wsd)
     if st != 0 or st2 != 0:
         raise SystemExit(f"device status {st}/{st2}")
+    # the main line's bitstream sizes (words) for the algorithmic bytes; the
+    # other lines below reuse `out`
+    hdr = out[:192].cpu().numpy()
+    W1 = int(hdr[168:176].view(np.uint64)[0])
+    W2 = int(hdr[176:184].view(np.uint64)[0])
     tau = args.eb * (float(x.max()) - float(x.min()))
     err = float((y - x).abs().max())
     if not err <= tau:
@@ -690,6 +695,30 @@ def main():
                               "GBps": x_np.nbytes / (ms_o * 1e-3) / 1e9,
                               "max_abs_err_over_tau": err_o / tau_o})
 
+    # the zero-run stage (runs of zero symbols as digit tokens before the
+    # Huffman coder) against the plain coder on the same field, from tight
+    # bounds (short runs) to loose ones (long runs)
+    zero_run = []
+    for eb in (1e-6, 1e-4, 1e-3, 1e-2, 1e-1):
+        row = {"eb_rel": eb}
+        for zr in (0, 1):
+            prm_z = mcc.params_default(dtype=mcc.F64, eb=eb, grid_fraction=0.5, zero_run=zr)
+            size_z = mcc.compress(plan, x, prm_z, wsc, out)
+            mcc.decompress(plan, out, size_z, y, wsd)
+            tau_z = eb * (float(x.max()) - float(x.min()))
+            if not float((y - x).abs().max()) <= tau_z:
+                raise SystemExit(f"bound violated (zero_run {zr}, {eb})")
+
+            def zstep(prm_z=prm_z):
+                mcc.compress(plan, x, prm_z, wsc, out, sync=False)
+                mcc.decompress(plan, out, cap, y, wsd, sync=False)
+
+            ms_z = time_replays(zstep, flush, max(5, args.steps // 4), args.warmup, stream)
+            key = "zero_run" if zr else "plain"
+            row[key] = {"compression_ratio": x_np.nbytes / size_z, "ms_per_step": ms_z,
+                        "GBps": x_np.nbytes / (ms_z * 1e-3) / 1e9}
+        zero_run.append(row)
+
     # the paper's default baseline (Sec. V): the same coder on the vertex
     # array in 1D, in storage order (shuffled ids) and in Morton order of the
     # vertex positions (a file with spatial locality); the improvement is the
@@ -745,9 +774,6 @@ def main():
         return
 
     nbytes = x_np.nbytes
-    hdr = out[:192].cpu().numpy()
-    W1 = int(hdr[168:176].view(np.uint64)[0])
-    W2 = int(hdr[176:184].view(np.uint64)[0])
     alg = algorithmic_bytes(len(wl["n"]), x_np.size, int(np.prod(wl["n"])), 8, W1, W2, size)
     per_kernel = {}
     if prof:
@@ -805,6 +831,7 @@ def main():
         "gpu_launches": None if launches_per_step is None else int(round(launches_per_step * args.steps)),
         "other_bounds": bounds,
         "operators": operators,
+        "zero_run": zero_run,
         "default_1d": default_1d,
         "grid_init": grid_init,
         "batched": batched,

@@ -1,6 +1,6 @@
 """GPU against the oracle over the seeded random configurations of
 test_oracle_properties (meshes, fields, value types, bounds, splits, radii,
-chunk sizes, length limits, operators, loops): the same stream byte for
+chunk sizes, length limits, operators, loops, the zero-run stage): the same stream byte for
 byte and the same decoded values, or the same error; the 1D coder likewise."""
 import numpy as np
 import pytest

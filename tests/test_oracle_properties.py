@@ -1,5 +1,5 @@
-"""Property tests of the oracle over random meshes, fields and parameters:
-the bound at every vertex (closed loop tau2, open loop tau1 + tau2), a
+"""Property tests of the oracle over random meshes, fields and parameters
+(with and without the zero-run stage): the bound at every vertex (closed loop tau2, open loop tau1 + tau2), a
 deterministic stream, decoding equal to the debug codes' reconstruction,
 and the 1D coder's bound. Seeded draws (numpy), so the CPU suite stays
 reproducible without extra packages."""
@@ -39,6 +39,11 @@ def _draw(seed):
               f_op=str(rng.choice(["barycentric", "cluster"])),
               g_op=str(rng.choice(["multilinear", "nearest"])), open_loop=bool(rng.random() < 0.3))
     kw["lmax"] = max(kw["lmax"], int(np.ceil(np.log2(2 * max(kw["R1"], kw["R2"])))))
+    # the zero-run stage on half of the draws (its alphabets of 2R + 2 tokens
+    # take R < 2048 and one more bit of length limit where 2R fills lmax)
+    kw["zero_run"] = bool(rng.random() < 0.5) and max(kw["R1"], kw["R2"]) < 2048
+    if kw["zero_run"]:
+        kw["lmax"] = max(kw["lmax"], int(np.ceil(np.log2(2 * max(kw["R1"], kw["R2"]) + 2))))
     return c, e, n, x.astype(dtype), kw
 
 
