@@ -55,6 +55,7 @@ def algorithmic_bytes(dim, n_v, n_g, vsz, w1, w2, cbytes):
         "k_group_len": 2 * (n_g + n_v),
         "k_scan": 0,
         "k_pack": 2 * (n_g + n_v) + cbytes,
+        "k_runs": 2 * (n_g + n_v),
         "k_dec_prep": 0,
         "k_dec_syms": 4 * (w1 + w2) + 4 * (n_g + n_v),
         "k_scan_rows": 8 * n_g,
@@ -447,6 +448,8 @@ def main():
     ap.add_argument("--impl", default="mcc", choices=["mcc", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--eb", type=float, default=1e-4)
+    ap.add_argument("--zero-run", action="store_true",
+                    help="main line with the zero-run stage (the other lines as they are)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernel-times", action="store_true")
@@ -478,7 +481,8 @@ def main():
                            torch.from_numpy(wl["cells"]).to(dev), wl["n"])
     x_np = wl["x"]
     x = torch.from_numpy(x_np).to(dev)
-    prm = mcc.params_default(dtype=mcc.F64, eb=args.eb, grid_fraction=0.5)
+    prm = mcc.params_default(dtype=mcc.F64, eb=args.eb, grid_fraction=0.5,
+                             zero_run=1 if args.zero_run else 0)
     wsc = plan.workspace(prm, "compress")
     wsd = plan.workspace(prm, "decompress")
     cap = mcc.compress_bound(plan, prm)
@@ -818,6 +822,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": wl["name"], "n_vertices": int(x_np.size),
                    "grid": list(wl["n"]), "eb_rel": args.eb, "grid_fraction": 0.5,
+                   "zero_run": bool(args.zero_run),
                    "compression_ratio": nbytes / size, "stream_bytes": int(size),
                    "max_abs_err_over_tau": err / tau,
                    "l2": "flushed before every step (256 MiB write, untimed)",

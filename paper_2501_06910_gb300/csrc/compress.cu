@@ -1693,7 +1693,7 @@ struct PackArgs {
 // ZR: the batch has a field with the zero-run stage (a separate variant keeps
 // the plain one's register count)
 template <bool ZR>
-__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A) {
+__global__ void __launch_bounds__(256, ZR ? 5 : 6) k_pack(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
   const Ctx c = ctx_of(A, blockIdx.y, true);
@@ -1748,6 +1748,14 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A
     e_run += a.pe[gi * kParts + q];
     r_run += a.pr[gi * kParts + q];
   }
+  // zero-run stage: the runs that end at this part's first other symbol and
+  // at the lane's end (from k_runs)
+  unsigned int rs_first = 0, rs_end = 0;
+  if (zr) {
+    const unsigned short *rs = c.rs + gi * (kParts + 1) * 32;
+    rs_first = rs[w * 32 + lane];
+    rs_end = rs[kParts * 32 + lane];
+  }
   __syncthreads();
   const int k0 = (w * C) / kParts, k1 = ((w + 1) * C) / kParts;
   const int64_t base = g * 32 * (int64_t)C + lane;
@@ -1769,7 +1777,6 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A
       put(scode[t], slen[t]);
     }
   };
-  const unsigned short *rs = c.rs + gi * (kParts + 1) * 32;
   unsigned int run = 0;
   bool seen = false;
 #pragma unroll 4
@@ -1782,7 +1789,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A
         run++;
       } else {
         if (zr) {  // the run that ends here (the first one may reach back)
-          put_run(seen ? run : rs[w * 32 + lane]);
+          put_run(seen ? run : rs_first);
           seen = true;
           run = 0;
         }
@@ -1802,7 +1809,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CompArgs A
       r_run += __popc(rm);
     }
   }
-  if (zr && w == kParts - 1) put_run(rs[kParts * 32 + lane]);  // the lane's last run
+  if (zr && w == kParts - 1) put_run(rs_end);  // the lane's last run
   __syncthreads();
   for (unsigned int i = threadIdx.x; i < nw; i += blockDim.x) bits[w0 + i] = stage[i];
 }
