@@ -20,6 +20,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "predictor.cuh"
 #include "workspace.cuh"
@@ -380,7 +382,8 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
     const int64_t first = (c1 ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - nb1) * (blockDim.x >> 5);
     if (first >= ng) return;
   }
-  load_tab(&Tb, c1 ? tab1 : tab2, c1 ? 2 * I.R1 : 2 * I.R2);
+  // (with the zero-run stage the code book also holds the two run tokens)
+  load_tab(&Tb, c1 ? tab1 : tab2, (c1 ? 2 * I.R1 : 2 * I.R2) + (I.zr ? kRunTokens : 0));
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t n = c1 ? n_g : n_v;
@@ -389,17 +392,19 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
   const int *outv = (const int *)(in + (c1 ? I.L.out1 : I.L.out2));
   const T *rawv = (const T *)(in + I.L.raw);
   int *dst = c1 ? delta : q2s;
-  // zero-run stage: run tokens 2R (digit 1) and 2R + 1 (digit 2); the
-  // chunk is pre-filled with the zero symbol R and a digit d at digit
-  // position i skips d 2^i steps
-  const bool zr = I.zr != 0;
   const int tok0 = 2 * R;
-  const bool fast = !zr && Tb.count[1] == 1;   // a symbol owns the code "0"
-  const unsigned short s0 = zr ? (unsigned short)R : Tb.sorted[0];  // the pre-fill symbol
   unsigned short *buf = sbuf + (size_t)wid * kDecRound * 32;
   const int64_t b0 = c1 ? blockIdx.x : blockIdx.x - nb1;
   const int64_t nblocks = c1 ? nb1 : gridDim.x - nb1;
   const int64_t wstride = nblocks * (blockDim.x >> 5);
+  // The group loop, compiled once per stream kind (the branch is uniform):
+  // with the zero-run stage (run tokens 2R for a digit 1 and 2R + 1 for a
+  // digit 2; the chunk is pre-filled with the zero symbol R and a digit d at
+  // digit position i skips d 2^i steps), and without it.
+  auto groups = [&](auto zr_kind) {
+  constexpr bool zr = decltype(zr_kind)::value;
+  const bool fast = !zr && Tb.count[1] == 1;   // a symbol owns the code "0"
+  const unsigned short s0 = zr ? (unsigned short)R : Tb.sorted[0];  // the pre-fill symbol
   for (int64_t g = b0 * (blockDim.x >> 5) + wid; g < ng; g += wstride) {
     BitReader r;
     unsigned int lane_bits, lane_delta, e0, e1, r0 = 0, r1 = 0;
@@ -567,6 +572,9 @@ __global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArg
     }
     __syncwarp();
   }
+  };
+  if (I.zr) groups(std::true_type{});
+  else groups(std::false_type{});
 }
 
 // ---------------------------------------------------------------------------

@@ -98,6 +98,18 @@ def test_zero_run_constant_field_closed_form():
     assert int(got[176:184].view(np.uint64)[0]) == 7
 
 
+def test_zero_run_full_alphabet_with_raw_values():
+    """R = 4 with every residual symbol but zero in use, raw values and both
+    run tokens: 2R + 1 codes, one more than the 2R symbols."""
+    rng = np.random.default_rng(3)
+    c, e, n, x, op, gp = _setup("ragged2d")
+    xx = (synth.field_bumps_noise(c, seed=82) * 0.05 + rng.standard_normal(c.shape[0]) * 0.01
+          + 1e5).astype(np.float32)
+    got, _ = _check("ragged2d", xx, eb=0.012, eb_mode="abs", R1=4, R2=4)
+    lens2 = [int(v) for v in got[392:400]] + [int(got[210]), int(got[211])]
+    assert sum(1 for v in lens2 if v) == 9 and int(got[160:168].view(np.uint64)[0]) > 0
+
+
 def test_zero_run_learned_and_auto():
     import gpu_helpers as G
     c, e, n, x, op, gp = _setup("annulus_small")
