@@ -46,7 +46,7 @@ def build(force: bool = False) -> str:
 
 class _Grid(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int32 * 3), ("lo", C.c_double * 3),
-                ("h", C.c_double * 3), ("inv_h", C.c_double * 3)]
+                ("h", C.c_double * 3), ("inv_h", C.c_double * 3), ("keep", C.c_void_p * 3)]
 
 
 class _Params(C.Structure):
@@ -114,9 +114,11 @@ def _c(a, dtype):
 # grid and plan
 # --------------------------------------------------------------------------- #
 class Grid:
-    """Resolved rectilinear grid (corners, spacing) -- Sec. IV-C."""
+    """Resolved rectilinear grid (corners, spacing) -- Sec. IV-C. ``keep``
+    (one increasing index array per axis) keeps only those planes of the
+    uniform grid (Grid_Coarsen, Algorithm 2)."""
 
-    def __init__(self, coords, n, lo=None, hi=None):
+    def __init__(self, coords, n, lo=None, hi=None, keep=None):
         coords = _c(coords, np.float64)
         dim = coords.shape[1]
         nn = np.ones(3, dtype=np.int32)
@@ -130,12 +132,28 @@ class Grid:
                                       _ptr(lo3), _ptr(hi3), C.byref(g))
         if st:
             raise OracleError(st, "grid_resolve")
+        self.base_n = tuple(int(v) for v in g.n)
+        self._keep = None
+        if keep is not None:
+            self._keep = []
+            for d in range(dim):
+                k = np.ascontiguousarray(keep[d], dtype=np.int32)
+                if k.size < 2 or np.any(np.diff(k) <= 0) or k[0] < 0 or k[-1] >= g.n[d]:
+                    raise ValueError("keep: increasing base indices, at least two per axis")
+                self._keep.append(k)
+                g.keep[d] = k.ctypes.data
+                g.n[d] = k.size
         self._g = g
         self.dim = dim
         self.n = tuple(int(v) for v in g.n)
         self.lo = np.array(g.lo[:])
         self.h = np.array(g.h[:])
         self.n_g = int(np.prod(self.n))
+
+    def coords_of_axis(self, d):
+        """Coordinates of the grid's points along axis d."""
+        idx = self._keep[d] if self._keep is not None else np.arange(self.n[d])
+        return self.lo[d] + idx.astype(np.float64) * self.h[d]
 
 
 def point_in_simplex(grid: Grid, coords, cell, idx):
@@ -174,16 +192,37 @@ def grid_init(coords, cells, k_pct, delta_pct=1.0, gmax=4096):
     return tuple(n[:dim]), tuple(lo[:dim]), tuple(hi[:dim]), tuple(gs[:dim])
 
 
+def grid_coarsen(plan, g_op="multilinear"):
+    """Grid_Coarsen (Algorithm 2) on a plan of a uniform grid: the kept
+    plane indices per axis (a list of int32 arrays) for ``Plan(..., n,
+    keep=...)`` with the same n, lo, hi."""
+    g = plan.grid
+    if g._keep is not None:
+        raise ValueError("grid_coarsen takes a uniform grid")
+    gop = {"multilinear": 0, "nearest": 1}[g_op] if isinstance(g_op, str) else int(g_op)
+    outs = [np.empty(max(g.n[d], 1), dtype=np.int32) for d in range(3)]
+    keep_p = (C.c_void_p * 3)(*[o.ctypes.data for o in outs])
+    n_out = (C.c_int32 * 3)()
+    lib = _load()
+    lib.orc_grid_coarsen.argtypes = [C.POINTER(_Grid), C.c_int64, C.c_void_p, C.c_void_p, C.c_int,
+                                     C.c_void_p * 3, C.c_int32 * 3]
+    st = lib.orc_grid_coarsen(C.byref(g._g), plan.n_v, _ptr(plan.cell), _ptr(plan.frac), gop,
+                              keep_p, n_out)
+    if st:
+        raise OracleError(st, "grid_coarsen")
+    return [outs[d][: n_out[d]].copy() for d in range(g.dim)]
+
+
 class Plan:
     """Mesh -> grid mapping tables: per grid point vertex ids ``vid``
     [(dim+1), n_g] (vid[0] = -1 outside the mesh) and u16 weights ``lam``
     [dim, n_g]; per vertex the cell index ``cell`` [n_v] and u16 local
     coordinates ``frac`` [dim, n_v]."""
 
-    def __init__(self, coords, cells, n, lo=None, hi=None, brute=False):
+    def __init__(self, coords, cells, n, lo=None, hi=None, brute=False, keep=None):
         coords = _c(coords, np.float64)
         cells = _c(cells, np.int32)
-        self.grid = Grid(coords, n, lo, hi)
+        self.grid = Grid(coords, n, lo, hi, keep)
         g = self.grid
         self.dim = g.dim
         self.n_v = coords.shape[0]

@@ -246,11 +246,15 @@ static void rel32(const orc_grid *g, const double *coords, int32_t v, float out[
 int orc_point_in_simplex(const orc_grid *g, const double *coords, const int32_t *cell,
                          const int32_t idx[3], double lam[4]) {
   const int dim = g->dim;
+  /* the point's index on the base grid (Grid_Coarsen keeps a subset of its
+   * planes; the point lies where it lies on the base grid) */
+  int32_t bi[3];
+  for (int d = 0; d < 3; d++) bi[d] = d < dim && g->keep[d] ? g->keep[d][idx[d]] : idx[d];
   /* FP32 pre-filter: reject points that are clearly outside. */
   float hf[3], pf[3], vf[4][3], l32[4], den32;
   for (int d = 0; d < 3; d++) {
     hf[d] = (float)g->h[d];
-    pf[d] = (float)idx[d] * hf[d];
+    pf[d] = (float)bi[d] * hf[d];
   }
   for (int k = 0; k <= dim; k++) rel32(g, coords, cell[k], vf[k]);
   if (dim == 2) {
@@ -266,7 +270,7 @@ int orc_point_in_simplex(const orc_grid *g, const double *coords, const int32_t 
   /* FP64 barycentric test on the grid point lo + i h. */
   double P[3], V[4][3], den;
   for (int d = 0; d < 3; d++) {
-    double ih = (double)idx[d] * g->h[d];
+    double ih = (double)bi[d] * g->h[d];
     P[d] = g->lo[d] + ih;
   }
   for (int k = 0; k <= dim; k++)
@@ -283,7 +287,8 @@ int orc_point_in_simplex(const orc_grid *g, const double *coords, const int32_t 
 }
 
 /* Grid-index range of a simplex's bounding box, from FP32 relative
- * coordinates with a margin of MARGIN32 cells. Returns 0 if empty. */
+ * coordinates with a margin of MARGIN32 cells (base-grid cells; with kept
+ * planes, the kept indices inside that base range). Returns 0 if empty. */
 static int candidate_range(const orc_grid *g, const double *coords, const int32_t *cell,
                            int32_t ilo[3], int32_t ihi[3]) {
   float vf[4][3];
@@ -295,18 +300,42 @@ static int candidate_range(const orc_grid *g, const double *coords, const int32_
       if (vf[k][d] < mn) mn = vf[k][d];
       if (vf[k][d] > mx) mx = vf[k][d];
     }
+    const int32_t *kp = g->keep[d];
     float hf = (float)g->h[d];
     float a = mn / hf - MARGIN32;
     float b = mx / hf + MARGIN32;
-    float top = (float)(g->n[d] - 1);
+    float top = (float)(kp ? kp[g->n[d] - 1] : g->n[d] - 1);
     if (!(a <= top) || !(b >= 0.0f)) return 0; /* also rejects NaN */
     a = ceilf(a);
     b = floorf(b);
     if (a < 0.0f) a = 0.0f;
     if (b > top) b = top;
     if (a > b) return 0;
-    ilo[d] = (int32_t)a;
-    ihi[d] = (int32_t)b;
+    if (!kp) {
+      ilo[d] = (int32_t)a;
+      ihi[d] = (int32_t)b;
+      continue;
+    }
+    /* the kept planes with base index in [a, b]: the first at or above a,
+     * the last at or below b (binary searches over the increasing list) */
+    int32_t lo_k = 0, hi_k = g->n[d];
+    while (lo_k < hi_k) {
+      const int32_t md = (lo_k + hi_k) / 2;
+      if ((float)kp[md] < a) lo_k = md + 1;
+      else hi_k = md;
+    }
+    const int32_t i0 = lo_k;
+    lo_k = 0;
+    hi_k = g->n[d];
+    while (lo_k < hi_k) {
+      const int32_t md = (lo_k + hi_k) / 2;
+      if ((float)kp[md] <= b) lo_k = md + 1;
+      else hi_k = md;
+    }
+    const int32_t i1 = lo_k - 1;
+    if (i0 > i1) return 0;
+    ilo[d] = i0;
+    ihi[d] = i1;
   }
   return 1;
 }
@@ -383,13 +412,32 @@ int orc_plan_tables(const orc_grid *g, int64_t n_v, const double *coords, const 
     int64_t ci[3] = {0, 0, 0};
     for (int d = 0; d < dim; d++) {
       double dd = coords[i * dim + d] - g->lo[d];
-      double t = dd * g->inv_h[d];
-      double fl = floor(t);
+      double t = dd * g->inv_h[d];  /* in base-grid spacings */
       int64_t c;
-      if (!(fl >= 0.0)) c = 0;
-      else if (fl > (double)(g->n[d] - 2)) c = g->n[d] - 2;
-      else c = (int64_t)fl;
-      double f = t - (double)c;
+      double f;
+      const int32_t *kp = g->keep[d];
+      if (!kp) {
+        double fl = floor(t);
+        if (!(fl >= 0.0)) c = 0;
+        else if (fl > (double)(g->n[d] - 2)) c = g->n[d] - 2;
+        else c = (int64_t)fl;
+        f = t - (double)c;
+      } else {
+        /* kept planes: the last interval [kp[c], kp[c + 1]] starting at or
+         * below t (the first one below kp[0]); f in that interval */
+        c = 0;
+        int64_t lo_k = 0, hi_k = g->n[d] - 2;  /* binary search in [0, n - 2] */
+        while (lo_k <= hi_k) {
+          const int64_t md = (lo_k + hi_k) / 2;
+          if ((double)kp[md] <= t) {
+            c = md;
+            lo_k = md + 1;
+          } else {
+            hi_k = md - 1;
+          }
+        }
+        f = (t - (double)kp[c]) / (double)(kp[c + 1] - kp[c]);
+      }
       ci[d] = c;
       frac[(int64_t)d * n_v + i] = to_u16_unit(f);
     }
@@ -397,6 +445,56 @@ int orc_plan_tables(const orc_grid *g, int64_t n_v, const double *coords, const 
   }
   (void)nz;
   return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid_Coarsen (Algorithm 2)                                                */
+/* ------------------------------------------------------------------------ */
+/* Every vertex marks the nodes its g uses: the nearest node (the corner of
+ * its cell on the near side of every midplane, from the u16 local
+ * coordinates, half going up) or all corners of its cell. A node marks the
+ * planes through it, one per axis; the unmarked planes go (every node on
+ * them is unvisited), and the grid keeps the others in order. Removing a
+ * plane leaves the other planes' marks as they were, so the axes and
+ * planes may be taken in any order. */
+int orc_grid_coarsen(const orc_grid *g, int64_t n_v, const uint32_t *cell, const uint16_t *frac,
+                     int g_op, int32_t *keep_out[3], int32_t n_out[3]) {
+  const int dim = g->dim;
+  if (g_op != 0 && g_op != 1) return ORC_ERR_INVALID_ARG;
+  if (n_v < 1 || !cell || !frac) return ORC_ERR_INVALID_ARG;
+  for (int d = 0; d < dim; d++)
+    if (g->keep[d] || !keep_out[d]) return ORC_ERR_INVALID_ARG;  /* a uniform grid */
+  const int64_t nx = g->n[0], ny = g->n[1];
+  uint8_t *mark[3] = {NULL, NULL, NULL};
+  int st = ORC_OK;
+  for (int d = 0; d < dim; d++)
+    if (!(mark[d] = (uint8_t *)calloc((size_t)g->n[d], 1))) { st = ORC_ERR_OOM; goto done; }
+  for (int64_t i = 0; i < n_v; i++) {
+    const int64_t c = cell[i];
+    const int64_t ci[3] = {c % nx, (c / nx) % ny, c / (nx * ny)};
+    for (int d = 0; d < dim; d++) {
+      if (ci[d] < 0 || ci[d] + 1 >= g->n[d]) { st = ORC_ERR_INVALID_ARG; goto done; }
+      if (g_op == 1) {
+        mark[d][ci[d] + (frac[(int64_t)d * n_v + i] >= 16384 ? 1 : 0)] = 1;
+      } else {
+        mark[d][ci[d]] = 1;
+        mark[d][ci[d] + 1] = 1;
+      }
+    }
+  }
+  for (int d = 0; d < 3; d++) {
+    if (d >= dim) { n_out[d] = 1; continue; }
+    int32_t m = 0;
+    for (int32_t k = 0; k < g->n[d]; k++) m += mark[d][k];
+    const int all = m < 2;  /* fewer than two planes cannot make a grid */
+    m = 0;
+    for (int32_t k = 0; k < g->n[d]; k++)
+      if (all || mark[d][k]) keep_out[d][m++] = k;
+    n_out[d] = m;
+  }
+done:
+  for (int d = 0; d < 3; d++) free(mark[d]);
+  return st;
 }
 
 /* ------------------------------------------------------------------------ */

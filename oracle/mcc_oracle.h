@@ -28,6 +28,11 @@ typedef struct {
   int dim;                 /* 2 or 3 */
   int32_t n[3];            /* grid points per axis (n[2] = 1 in 2D) */
   double lo[3], h[3], inv_h[3];
+  /* Grid_Coarsen (Algorithm 2): the kept planes of a uniform base grid with
+   * corner lo and spacing h, as increasing base indices keep[d][0 .. n[d]);
+   * NULL keeps every plane (the uniform grid itself). Point i along axis d
+   * lies at lo[d] + keep[d][i] * h[d]. */
+  const int32_t *keep[3];
 } orc_grid;
 
 /* Grid_Init (Algorithm 1): points per axis from the bottom k-th percentile
@@ -37,6 +42,17 @@ typedef struct {
 int orc_grid_init(int dim, int64_t n_v, const double *coords, int64_t n_c, const int32_t *cells,
                   double k_pct, double delta_pct, int32_t gmax, int32_t n_out[3], double lo[3],
                   double hi[3], double gs_out[3]);
+
+/* Grid_Coarsen (Algorithm 2) on a uniform grid g and its vertex tables
+ * (cell, frac from orc_plan_tables): every vertex marks the grid nodes its
+ * g uses (g_op 1, nearest node: the cell corner on the near side of every
+ * midplane; g_op 0, multilinear: all 2^dim corners of its cell); a plane
+ * (line in 2D) of the grid normal to axis d at index k is kept when one of
+ * its nodes is marked. keep_out[d] (n[d] entries each) receives the kept
+ * indices, n_out[d] their count. An axis that would keep fewer than two
+ * planes keeps them all. */
+int orc_grid_coarsen(const orc_grid *g, int64_t n_v, const uint32_t *cell, const uint16_t *frac,
+                     int g_op, int32_t *keep_out[3], int32_t n_out[3]);
 
 /* Resolve the grid: lo/hi given, or the mesh bounding box when lo >= hi on
  * any axis (Sec. IV-C: corners from the vertex min / max). */
