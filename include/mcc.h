@@ -168,6 +168,34 @@ void mcc_params_default(mcc_params *p);
 mcc_status mcc_plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, mcc_stream stream,
                            mcc_plan *out);
 
+/* Grid_Coarsen (Algorithm 2) on a plan of a uniform grid: every vertex
+ * marks the grid nodes its g uses (g_op MCC_G_NEAREST: the nearest node, the
+ * cell corner on the near side of every midplane from the plan's local
+ * coordinates, half going up; MCC_G_MULTILINEAR: all 2^dim corners of its
+ * cell), and a plane of the grid normal to axis d (a line in 2D) stays when
+ * one of its nodes is marked. keep_out (HOST, n[0] + n[1] (+ n[2]) entries)
+ * receives the kept indices of axis 0, then axis 1 (then axis 2), n_out[d]
+ * their counts (n_out[2] = 1 in 2D). An axis that would keep fewer than two
+ * planes keeps all of them. Synchronises the stream. MCC_ERR_INVALID_ARG
+ * for a plan made with mcc_plan_create_kept or an unknown g_op. */
+mcc_status mcc_grid_coarsen(mcc_plan plan, int g_op, int32_t *keep_out, int32_t n_out[3],
+                            mcc_stream stream);
+
+/* The plan of the kept planes of a uniform grid (Algorithm 2's updated
+ * layout S): grid as for mcc_plan_create (the uniform base grid), keep a
+ * HOST array of n_keep[0] + n_keep[1] (+ n_keep[2]) increasing base indices,
+ * at least two per axis (mcc_grid_coarsen's output). Point i of axis d
+ * lies at lo[d] + keep_d[i] h[d]: every grid point is a base grid point,
+ * located and weighted as there; a vertex's cell lies between the kept
+ * planes around it and its local coordinate is (t - k_c) / (k_(c+1) - k_c),
+ * t = (p - lo) / h in base spacings. The compressor takes the plan like
+ * any other (n_keep[d] points per axis); the stream records those counts,
+ * so decompression takes the same plan. mcc_plan_get_info reports the kept
+ * counts with the base corner and spacing. */
+mcc_status mcc_plan_create_kept(const mcc_mesh *mesh, const mcc_grid_spec *grid,
+                                const int32_t *keep, const int32_t n_keep[3], mcc_stream stream,
+                                mcc_plan *out);
+
 /* Grid_Init (Algorithm 1): a grid layout for the mesh. For each axis d the
  * spacing gs_d is the bottom k-th percentile, nearest rank (the
  * ceil(k/100 N)-th smallest), of |p_a,d - p_b,d| over every edge of every

@@ -14,6 +14,8 @@ import ctypes as C
 import os
 import threading
 
+import numpy as np
+
 import torch
 
 from .native_build import LIB, build
@@ -98,6 +100,9 @@ def load():
             lib.mcc_status_string.argtypes = [C.c_int]
             lib.mcc_status_string.restype = C.c_char_p
             lib.mcc_plan_create.argtypes = [C.POINTER(_Mesh), C.POINTER(_GridSpec), P, C.POINTER(P)]
+            lib.mcc_plan_create_kept.argtypes = [C.POINTER(_Mesh), C.POINTER(_GridSpec), P, P, P,
+                                                 C.POINTER(P)]
+            lib.mcc_grid_coarsen.argtypes = [P, C.c_int, P, P, P]
             lib.mcc_workspace_size_1d.argtypes = [C.c_int64, C.POINTER(Params), C.POINTER(S),
                                                   C.POINTER(S)]
             lib.mcc_compress_bound_1d.argtypes = [C.c_int64, C.POINTER(Params), C.POINTER(S)]
@@ -144,7 +149,8 @@ def load():
             for fn in ("mcc_train_workspace_size", "mcc_model_train", "mcc_mlp_grad",
                        "mcc_mlp_quantize"):
                 getattr(lib, fn).restype = C.c_int
-            for fn in ("mcc_plan_create", "mcc_plan_get_info", "mcc_plan_copy_tables",
+            for fn in ("mcc_plan_create", "mcc_plan_create_kept", "mcc_grid_coarsen",
+                       "mcc_plan_get_info", "mcc_plan_copy_tables",
                        "mcc_workspace_size", "mcc_compress_bound", "mcc_compress",
                        "mcc_decompress", "mcc_workspace_result"):
                 getattr(lib, fn).restype = C.c_int
@@ -253,10 +259,12 @@ class Plan:
 
 
 def plan_create(coords: torch.Tensor, cells: torch.Tensor, n, lo=None, hi=None,
-                stream=None) -> Plan:
+                stream=None, keep=None) -> Plan:
     """mcc_plan_create: coords float64 [n_v, dim], cells int32 [n_c, dim+1],
     both on the device; n grid points per axis; lo/hi corners (None: the mesh
-    bounding box)."""
+    bounding box). ``keep`` (one increasing index array per axis, e.g. from
+    ``grid_coarsen``) builds the plan on those planes of that grid
+    (mcc_plan_create_kept)."""
     dim = coords.shape[1]
     m = _Mesh(dim, coords.shape[0], _dptr(coords).value, cells.shape[0], _dptr(cells).value)
     g = _GridSpec()
@@ -265,11 +273,36 @@ def plan_create(coords: torch.Tensor, cells: torch.Tensor, n, lo=None, hi=None,
         g.lo[d] = lo[d] if lo is not None and d < dim else 0.0
         g.hi[d] = hi[d] if hi is not None and d < dim else 0.0
     h = C.c_void_p()
-    _check(load().mcc_plan_create(C.byref(m), C.byref(g), _stream(stream), C.byref(h)),
-           "plan_create")
+    if keep is None:
+        _check(load().mcc_plan_create(C.byref(m), C.byref(g), _stream(stream), C.byref(h)),
+               "plan_create")
+    else:
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(keep[d], dtype=np.int32)
+                                                    for d in range(dim)]), dtype=np.int32)
+        nk = (C.c_int32 * 3)(*[len(keep[d]) if d < dim else 1 for d in range(3)])
+        _check(load().mcc_plan_create_kept(C.byref(m), C.byref(g), flat.ctypes.data,
+                                           C.cast(nk, C.c_void_p), _stream(stream), C.byref(h)),
+               "plan_create_kept")
     info = _PlanInfo()
     _check(load().mcc_plan_get_info(h, C.byref(info)), "plan_get_info")
     return Plan(h, info)
+
+
+def grid_coarsen(plan: Plan, g_op="multilinear", stream=None):
+    """mcc_grid_coarsen (Algorithm 2): the kept plane indices per axis (a list
+    of int32 numpy arrays) of a plan's uniform grid, for plan_create(...,
+    keep=...) with the same n, lo and hi."""
+    gop = {"multilinear": G_MULTILINEAR, "nearest": G_NEAREST}[g_op] if isinstance(g_op, str) \
+        else int(g_op)
+    out = np.empty(int(sum(plan.n)), dtype=np.int32)
+    n_out = (C.c_int32 * 3)()
+    _check(load().mcc_grid_coarsen(plan.handle, gop, out.ctypes.data, C.cast(n_out, C.c_void_p),
+                                   _stream(stream)), "grid_coarsen")
+    res, o = [], 0
+    for d in range(plan.dim):
+        res.append(out[o: o + n_out[d]].copy())
+        o += n_out[d]
+    return res
 
 
 def grid_init(coords: torch.Tensor, cells: torch.Tensor, k_pct: float, delta_pct: float = 1.0,

@@ -16,6 +16,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 
@@ -25,6 +26,7 @@ using namespace mcc;
 
 struct mcc_plan_s {
   int dim;
+  int kept;  // on kept planes of a uniform grid (Grid_Coarsen)
   int32_t n[3];
   double lo[3], h[3], inv_h[3];
   int64_t n_v, n_g, n_outside;
@@ -40,12 +42,22 @@ constexpr double kTol64 = 1e-12;
 constexpr float kTol32 = 0.05f;
 constexpr float kMargin32 = 0.01f;
 
+// The grid of a plan: n[d] points per axis at lo + i h, or, with kept planes
+// (Grid_Coarsen), at lo + keep[d][i] h on the uniform base grid (device
+// arrays, increasing); top[d] is the largest base index.
 struct GridDev {
   int dim;
   int32_t n[3];
   double lo[3], h[3], inv_h[3];
   float hf[3];
+  const int32_t *keep[3];
+  int32_t top[3];
 };
+
+// base-grid index of point i along axis d
+__device__ __forceinline__ int32_t base_index(const GridDev &g, int d, int32_t i) {
+  return g.keep[d] ? __ldg(g.keep[d] + i) : i;
+}
 
 // ---- barycentric coordinates (same operation order as the definition) ----
 __device__ __forceinline__ void bary2_f(const float *a, const float *b, const float *c,
@@ -231,15 +243,38 @@ __global__ void k_raster(const double *__restrict__ coords, const int32_t *__res
     }
     float a = __fsub_rn(__fdiv_rn(mn, g.hf[d]), kMargin32);
     float b = __fadd_rn(__fdiv_rn(mx, g.hf[d]), kMargin32);
-    const float top = (float)(g.n[d] - 1);
+    const float top = (float)g.top[d];
     if (!(a <= top) || !(b >= 0.0f)) return;
     a = ceilf(a);
     b = floorf(b);
     if (a < 0.0f) a = 0.0f;
     if (b > top) b = top;
     if (a > b) return;
-    ilo[d] = (int32_t)a;
-    ihi[d] = (int32_t)b;
+    if (!g.keep[d]) {
+      ilo[d] = (int32_t)a;
+      ihi[d] = (int32_t)b;
+      continue;
+    }
+    // kept planes with base index in [a, b]: the first at or above a, the
+    // last at or below b
+    const int32_t *kp = g.keep[d];
+    int32_t lo_k = 0, hi_k = g.n[d];
+    while (lo_k < hi_k) {
+      const int32_t md = (lo_k + hi_k) >> 1;
+      if (__int2float_rn(__ldg(kp + md)) < a) lo_k = md + 1;
+      else hi_k = md;
+    }
+    const int32_t i0 = lo_k;
+    lo_k = 0;
+    hi_k = g.n[d];
+    while (lo_k < hi_k) {
+      const int32_t md = (lo_k + hi_k) >> 1;
+      if (__int2float_rn(__ldg(kp + md)) <= b) lo_k = md + 1;
+      else hi_k = md;
+    }
+    if (i0 > lo_k - 1) return;
+    ilo[d] = i0;
+    ihi[d] = lo_k - 1;
   }
   bool have64 = false;
   double V[4][3];
@@ -250,8 +285,10 @@ __global__ void k_raster(const double *__restrict__ coords, const int32_t *__res
         const int64_t j = x + nx * (y + ny * (int64_t)z);
         if (owner[j] <= (unsigned int)t) continue;  // a smaller id already owns it
         const int32_t idx[3] = {x, y, z};
+        int32_t bi[3] = {0, 0, 0};  // the point's index on the base grid
+        for (int d = 0; d < DIM; d++) bi[d] = base_index(g, d, idx[d]);
         float pf[3] = {0.f, 0.f, 0.f};
-        for (int d = 0; d < DIM; d++) pf[d] = __fmul_rn(__int2float_rn(idx[d]), g.hf[d]);
+        for (int d = 0; d < DIM; d++) pf[d] = __fmul_rn(__int2float_rn(bi[d]), g.hf[d]);
         if (!prefilter<DIM>(vf, pf)) continue;
         if (!have64) {
           for (int k = 0; k <= DIM; k++)
@@ -259,7 +296,7 @@ __global__ void k_raster(const double *__restrict__ coords, const int32_t *__res
           have64 = true;
         }
         double P[3] = {0.0, 0.0, 0.0}, lam[4];
-        for (int d = 0; d < DIM; d++) P[d] = __dadd_rn(g.lo[d], __dmul_rn((double)idx[d], g.h[d]));
+        for (int d = 0; d < DIM; d++) P[d] = __dadd_rn(g.lo[d], __dmul_rn((double)bi[d], g.h[d]));
         if (inside64<DIM>(V, P, lam)) atomicMin(owner + j, (unsigned int)t);
       }
 }
@@ -286,7 +323,8 @@ __global__ void k_grid_tables(const double *__restrict__ coords, const int32_t *
     vid[k * n_g + j] = v;
     for (int d = 0; d < 3; d++) V[k][d] = d < DIM ? coords[(int64_t)v * DIM + d] : 0.0;
   }
-  for (int d = 0; d < DIM; d++) P[d] = __dadd_rn(g.lo[d], __dmul_rn((double)idx[d], g.h[d]));
+  for (int d = 0; d < DIM; d++)
+    P[d] = __dadd_rn(g.lo[d], __dmul_rn((double)base_index(g, d, idx[d]), g.h[d]));
   inside64<DIM>(V, P, l);
   for (int k = 0; k < DIM; k++) lam[k * n_g + j] = to_u16_unit(l[k + 1]);
 }
@@ -299,16 +337,61 @@ __global__ void k_node_tables(const double *__restrict__ coords, int64_t n_v, Gr
   int64_t ci[3] = {0, 0, 0};
   for (int d = 0; d < DIM; d++) {
     const double dd = __dsub_rn(coords[i * DIM + d], g.lo[d]);
-    const double t = __dmul_rn(dd, g.inv_h[d]);
-    const double fl = floor(t);
+    const double t = __dmul_rn(dd, g.inv_h[d]);  // in base-grid spacings
     int64_t c;
-    if (!(fl >= 0.0)) c = 0;
-    else if (fl > (double)(g.n[d] - 2)) c = g.n[d] - 2;
-    else c = (int64_t)fl;
+    double f;
+    if (!g.keep[d]) {
+      const double fl = floor(t);
+      if (!(fl >= 0.0)) c = 0;
+      else if (fl > (double)(g.n[d] - 2)) c = g.n[d] - 2;
+      else c = (int64_t)fl;
+      f = __dsub_rn(t, (double)c);
+    } else {
+      // kept planes: the last interval [k_c, k_(c+1)] starting at or below t
+      // (the first one below k_0), f in that interval
+      const int32_t *kp = g.keep[d];
+      c = 0;
+      int32_t lo_k = 0, hi_k = g.n[d] - 2;
+      while (lo_k <= hi_k) {
+        const int32_t md = (lo_k + hi_k) >> 1;
+        if ((double)__ldg(kp + md) <= t) {
+          c = md;
+          lo_k = md + 1;
+        } else {
+          hi_k = md - 1;
+        }
+      }
+      const int32_t k0 = __ldg(kp + c), k1 = __ldg(kp + c + 1);
+      f = __ddiv_rn(__dsub_rn(t, (double)k0), (double)(k1 - k0));
+    }
     ci[d] = c;
-    frac[(int64_t)d * n_v + i] = to_u16_unit(__dsub_rn(t, (double)c));
+    frac[(int64_t)d * n_v + i] = to_u16_unit(f);
   }
   cell[i] = (uint32_t)(ci[0] + (int64_t)g.n[0] * (ci[1] + (int64_t)g.n[1] * ci[2]));
+}
+
+// Grid_Coarsen (Algorithm 2): every vertex marks, per axis, the planes of
+// the nodes its g uses (the nearest node, half going up; or both corners of
+// its cell). mark holds n[0] + n[1] + n[2] bytes, axis by axis.
+template <int DIM>
+__global__ void k_coarsen_mark(const uint32_t *__restrict__ cell, const uint16_t *__restrict__ frac,
+                               int64_t n_v, int32_t nx, int32_t ny, int32_t nz, int nearest,
+                               unsigned char *mark) {
+  const int64_t off[3] = {0, nx, (int64_t)nx + ny};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_v;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = cell[i];
+    const int64_t ci[3] = {c % nx, (c / nx) % ny, c / ((int64_t)nx * ny)};
+    for (int d = 0; d < DIM; d++) {
+      if (nearest) {
+        mark[off[d] + ci[d] + (frac[(int64_t)d * n_v + i] >= 16384 ? 1 : 0)] = 1;
+      } else {
+        mark[off[d] + ci[d]] = 1;
+        mark[off[d] + ci[d] + 1] = 1;
+      }
+    }
+  }
+  (void)nz;
 }
 
 inline unsigned int nblocks(int64_t n, int bs) {
@@ -319,9 +402,10 @@ inline unsigned int nblocks(int64_t n, int bs) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-extern "C" mcc_status mcc_plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid,
-                                      mcc_stream stream_, mcc_plan *out) {
-  cudaStream_t stream = (cudaStream_t)stream_;
+// The plan of a uniform grid (keep == nullptr) or of kept planes of it
+// (keep: host array of n_keep[0] + n_keep[1] (+ n_keep[2]) base indices).
+static mcc_status plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, const int32_t *keep,
+                              const int32_t *n_keep, cudaStream_t stream, mcc_plan *out) {
   if (!out) return MCC_ERR_INVALID_ARG;
   *out = nullptr;
   if (!mesh || !grid) return MCC_ERR_INVALID_ARG;
@@ -330,11 +414,19 @@ extern "C" mcc_status mcc_plan_create(const mcc_mesh *mesh, const mcc_grid_spec 
   if (mesh->n_vertices < 1 || mesh->n_vertices >= (int64_t)1 << 31 || mesh->n_cells < 1 ||
       mesh->n_cells >= (int64_t)1 << 31 || !mesh->coords || !mesh->cells)
     return MCC_ERR_INVALID_ARG;
-  int64_t n_g = 1;
+  int64_t n_g = 1, n_keep_all = 0;
   bool use_bbox = false;
   for (int d = 0; d < dim; d++) {
     if (grid->n[d] < 2 || grid->n[d] > 32768) return MCC_ERR_INVALID_ARG;
-    n_g *= grid->n[d];
+    if (keep) {  // increasing base indices, at least two per axis
+      if (!n_keep || n_keep[d] < 2 || n_keep[d] > grid->n[d]) return MCC_ERR_INVALID_ARG;
+      const int32_t *k = keep + n_keep_all;
+      if (k[0] < 0 || k[n_keep[d] - 1] >= grid->n[d]) return MCC_ERR_INVALID_ARG;
+      for (int32_t i = 1; i < n_keep[d]; i++)
+        if (k[i] <= k[i - 1]) return MCC_ERR_INVALID_ARG;
+      n_keep_all += n_keep[d];
+    }
+    n_g *= keep ? n_keep[d] : grid->n[d];
     if (!(grid->lo[d] < grid->hi[d])) use_bbox = true;
   }
   if (n_g > ((int64_t)1 << 31)) return MCC_ERR_INVALID_ARG;
@@ -346,14 +438,19 @@ extern "C" mcc_status mcc_plan_create(const mcc_mesh *mesh, const mcc_grid_spec 
   unsigned long long *d_keys = nullptr;
   unsigned int *d_owner = nullptr;
   float4 *d_rel = nullptr;
+  int32_t *d_keep = nullptr;
   mcc_status st = MCC_OK;
   auto fail = [&](mcc_status s) {
-    cudaFree(d_flag); cudaFree(d_keys); cudaFree(d_owner); cudaFree(d_rel);
+    cudaFree(d_flag); cudaFree(d_keys); cudaFree(d_owner); cudaFree(d_rel); cudaFree(d_keep);
     if (P) { cudaFree(P->vid); cudaFree(P->lam); cudaFree(P->cell); cudaFree(P->frac); delete P; }
     return s;
   };
   if (cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&d_keys, 6 * sizeof(unsigned long long)) != cudaSuccess)
+    return fail(MCC_ERR_OOM);
+  if (keep && (cudaMalloc(&d_keep, sizeof(int32_t) * n_keep_all) != cudaSuccess ||
+               cudaMemcpyAsync(d_keep, keep, sizeof(int32_t) * n_keep_all, cudaMemcpyHostToDevice,
+                               stream) != cudaSuccess))
     return fail(MCC_ERR_OOM);
   cudaMemsetAsync(d_flag, 0, sizeof(int), stream);
   cudaMemsetAsync(d_keys, 0, 6 * sizeof(unsigned long long), stream);
@@ -380,13 +477,24 @@ extern "C" mcc_status mcc_plan_create(const mcc_mesh *mesh, const mcc_grid_spec 
       g.lo[d] = lo;
       g.h[d] = (hi - lo) / (double)(grid->n[d] - 1);
       g.inv_h[d] = 1.0 / g.h[d];
+      g.top[d] = grid->n[d] - 1;
     } else {
       g.n[d] = 1; g.lo[d] = 0.0; g.h[d] = 1.0; g.inv_h[d] = 1.0;
     }
     g.hf[d] = (float)g.h[d];
   }
+  if (keep) {  // the kept planes of the base grid just resolved
+    int64_t o = 0;
+    for (int d = 0; d < dim; d++) {
+      g.keep[d] = d_keep + o;
+      g.n[d] = n_keep[d];
+      g.top[d] = keep[o + n_keep[d] - 1];
+      o += n_keep[d];
+    }
+  }
 
   P->dim = dim;
+  P->kept = keep ? 1 : 0;
   for (int d = 0; d < 3; d++) {
     P->n[d] = g.n[d]; P->lo[d] = g.lo[d]; P->h[d] = g.h[d]; P->inv_h[d] = g.inv_h[d];
   }
@@ -419,10 +527,73 @@ extern "C" mcc_status mcc_plan_create(const mcc_mesh *mesh, const mcc_grid_spec 
       cudaStreamSynchronize(stream) != cudaSuccess)
     return fail(MCC_ERR_CUDA);
   P->n_outside = (int64_t)n_out;
-  cudaFree(d_flag); cudaFree(d_keys); cudaFree(d_owner); cudaFree(d_rel);
+  cudaFree(d_flag); cudaFree(d_keys); cudaFree(d_owner); cudaFree(d_rel); cudaFree(d_keep);
   *out = P;
   (void)st;
   return MCC_OK;
+}
+
+extern "C" mcc_status mcc_plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid,
+                                      mcc_stream stream, mcc_plan *out) {
+  return plan_create(mesh, grid, nullptr, nullptr, (cudaStream_t)stream, out);
+}
+
+extern "C" mcc_status mcc_plan_create_kept(const mcc_mesh *mesh, const mcc_grid_spec *grid,
+                                           const int32_t *keep, const int32_t n_keep[3],
+                                           mcc_stream stream, mcc_plan *out) {
+  if (!keep) {
+    if (out) *out = nullptr;
+    return MCC_ERR_INVALID_ARG;
+  }
+  return plan_create(mesh, grid, keep, n_keep, (cudaStream_t)stream, out);
+}
+
+extern "C" mcc_status mcc_grid_coarsen(mcc_plan P, int g_op, int32_t *keep_out, int32_t n_out[3],
+                                       mcc_stream stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (!P || !keep_out || !n_out || P->kept) return MCC_ERR_INVALID_ARG;
+  if (g_op != MCC_G_MULTILINEAR && g_op != MCC_G_NEAREST) return MCC_ERR_INVALID_ARG;
+  const int dim = P->dim;
+  const int64_t nm = (int64_t)P->n[0] + P->n[1] + (dim == 3 ? P->n[2] : 0);
+  unsigned char *d_mark = nullptr;
+  unsigned char *h_mark = new (std::nothrow) unsigned char[nm];
+  if (!h_mark) return MCC_ERR_OOM;
+  if (cudaMalloc(&d_mark, nm) != cudaSuccess) {
+    delete[] h_mark;
+    return MCC_ERR_OOM;
+  }
+  cudaMemsetAsync(d_mark, 0, nm, stream);
+  const unsigned int nb = (unsigned int)std::min<int64_t>((P->n_v + 255) / 256, 152 * 8);
+  const int nearest = g_op == MCC_G_NEAREST ? 1 : 0;
+  if (dim == 2)
+    k_coarsen_mark<2><<<nb, 256, 0, stream>>>(P->cell, P->frac, P->n_v, P->n[0], P->n[1], P->n[2],
+                                             nearest, d_mark);
+  else
+    k_coarsen_mark<3><<<nb, 256, 0, stream>>>(P->cell, P->frac, P->n_v, P->n[0], P->n[1], P->n[2],
+                                             nearest, d_mark);
+  mcc_status st = MCC_OK;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(h_mark, d_mark, nm, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    st = MCC_ERR_CUDA;
+  if (st == MCC_OK) {
+    int64_t o = 0, w = 0;
+    for (int d = 0; d < 3; d++) {
+      if (d >= dim) { n_out[d] = 1; continue; }
+      int32_t m = 0;
+      for (int32_t k = 0; k < P->n[d]; k++) m += h_mark[o + k];
+      const bool all = m < 2;  // fewer than two planes cannot make a grid
+      m = 0;
+      for (int32_t k = 0; k < P->n[d]; k++)
+        if (all || h_mark[o + k]) keep_out[w + m++] = k;
+      n_out[d] = m;
+      o += P->n[d];
+      w += m;
+    }
+  }
+  cudaFree(d_mark);
+  delete[] h_mark;
+  return st;
 }
 
 extern "C" void mcc_plan_destroy(mcc_plan P) {

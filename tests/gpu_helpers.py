@@ -6,10 +6,10 @@ import torch
 import paper_2501_06910_gb300 as mcc
 
 
-def plan(coords, cells, n, lo=None, hi=None):
+def plan(coords, cells, n, lo=None, hi=None, keep=None):
     c = torch.from_numpy(np.ascontiguousarray(coords, dtype=np.float64)).cuda()
     e = torch.from_numpy(np.ascontiguousarray(cells, dtype=np.int32)).cuda()
-    p = mcc.plan_create(c, e, n, lo, hi)
+    p = mcc.plan_create(c, e, n, lo, hi, keep=keep)
     torch.cuda.synchronize()
     return p
 
