@@ -320,8 +320,9 @@ def grid_init_line(args, dev, flush, stream, wl, x):
     """Grid_Init (Algorithm 1) on the benchmark mesh: the grid from the
     bottom k-th percentile of the edge extents (gmax 4096, delta 1), for
     several k; ratio and compress+decompress rate at rel 1e-4 with the
-    default operators and with the paper's (cluster-mean f, nearest-node g).
-    The plan is built outside the timed region."""
+    default operators and with the paper's (cluster-mean f, nearest-node g),
+    on the uniform grid and on its planes kept by Grid_Coarsen (Algorithm 2,
+    for the same g). The plans are built outside the timed region."""
     import torch
     import paper_2501_06910_gb300 as mcc
     cd = torch.from_numpy(wl["coords"]).to(dev)
@@ -332,28 +333,43 @@ def grid_init_line(args, dev, flush, stream, wl, x):
         n, lo, hi = mcc.grid_init(cd, ed, k, 1.0, 4096)
         t_init = time.perf_counter() - t0
         plan = mcc.plan_create(cd, ed, n, lo, hi)
-        for fop, gop in (("barycentric", "multilinear"), ("cluster", "nearest")):
-            prm = mcc.params_default(dtype=mcc.F64, eb=1e-4, grid_fraction=0.5, f_op=fop, g_op=gop)
-            wsc = plan.workspace(prm, "compress")
-            wsd = plan.workspace(prm, "decompress")
-            cap = mcc.compress_bound(plan, prm)
+
+        def measure(pl, prm, what):
+            wsc = pl.workspace(prm, "compress")
+            wsd = pl.workspace(prm, "decompress")
+            cap = mcc.compress_bound(pl, prm)
             out = torch.empty(cap, dtype=torch.uint8, device=dev)
             y = torch.empty_like(x)
-            size = mcc.compress(plan, x, prm, wsc, out)
-            mcc.decompress(plan, out, size, y, wsd)
+            size = mcc.compress(pl, x, prm, wsc, out)
+            mcc.decompress(pl, out, size, y, wsd)
             tau = 1e-4 * (float(x.max()) - float(x.min()))
             if not float((y - x).abs().max()) <= tau:
-                raise SystemExit(f"grid_init line: bound violated (k {k}, {fop}, {gop})")
+                raise SystemExit(f"grid_init line: bound violated (k {k}, {what})")
 
-            def gstep(prm=prm, wsc=wsc, wsd=wsd, out=out, y=y, cap=cap):
-                mcc.compress(plan, x, prm, wsc, out, sync=False)
-                mcc.decompress(plan, out, cap, y, wsd, sync=False)
+            def gstep():
+                mcc.compress(pl, x, prm, wsc, out, sync=False)
+                mcc.decompress(pl, out, cap, y, wsd, sync=False)
 
             ms = time_replays(gstep, flush, 5, args.warmup, stream)
-            rows.append({"k_pct": k, "grid": list(n), "grid_init_s": t_init, "f": fop, "g": gop,
-                         "compression_ratio": x.numel() * 8 / size, "ms_per_step": ms,
-                         "GBps": x.numel() * 8 / (ms * 1e-3) / 1e9})
-            del wsc, wsd, out, y
+            return x.numel() * 8 / size, ms
+
+        for fop, gop in (("barycentric", "multilinear"), ("cluster", "nearest")):
+            prm = mcc.params_default(dtype=mcc.F64, eb=1e-4, grid_fraction=0.5, f_op=fop, g_op=gop)
+            ratio, ms = measure(plan, prm, f"{fop}, {gop}")
+            row = {"k_pct": k, "grid": list(n), "grid_init_s": t_init, "f": fop, "g": gop,
+                   "compression_ratio": ratio, "ms_per_step": ms,
+                   "GBps": x.numel() * 8 / (ms * 1e-3) / 1e9}
+            try:  # the same on the planes Grid_Coarsen keeps (recorded, never fatal here)
+                keep = mcc.grid_coarsen(plan, gop)
+                kplan = mcc.plan_create(cd, ed, n, lo, hi, keep=keep)
+                ratio_k, ms_k = measure(kplan, prm, f"{fop}, {gop}, coarsened")
+                kplan.close()
+                row.update({"coarsened_grid": [int(v.size) for v in keep],
+                            "coarsened_compression_ratio": ratio_k, "coarsened_ms_per_step": ms_k,
+                            "coarsened_GBps": x.numel() * 8 / (ms_k * 1e-3) / 1e9})
+            except (Exception, SystemExit) as err:
+                row["coarsened_error"] = str(err)
+            rows.append(row)
         plan.close()
     return {"workload": wl["name"] + ", grid from Grid_Init (gmax 4096, delta 1)", "rows": rows}
 
