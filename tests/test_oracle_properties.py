@@ -77,3 +77,33 @@ def test_random_1d_coder_holds_the_bound(seed):
     xd = x.astype(np.float64)
     tau = kw1["eb"] * (xd.max() - xd.min()) if kw1["eb_mode"] == "rel" and xd.max() > xd.min() else kw1["eb"]
     assert np.abs(y.astype(np.float64) - xd).max() <= tau
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_coarsened_plans_hold_the_bound(seed):
+    """Grid_Coarsen on random meshes and grids finer than them: the plan on
+    the kept planes holds the bound and decodes deterministically, for the
+    g the planes were kept for."""
+    c, e, n, x, kw = _draw(2000 + seed)
+    rng = np.random.default_rng(seed)
+    n = tuple(int(v) * int(rng.integers(1, 4)) for v in n)  # up to 3x finer
+    op = oracle.Plan(c, e, n)
+    g_op = str(rng.choice(["multilinear", "nearest"]))
+    keep = oracle.grid_coarsen(op, g_op)
+    for d in range(op.dim):
+        assert keep[d].size >= 2 and np.all(np.diff(keep[d]) > 0)
+    kp = oracle.Plan(c, e, n, keep=keep)
+    kw = dict(kw, g_op=g_op, f_op=kw["f_op"])
+    if g_op == "nearest":
+        kw.pop("model", None)
+    try:
+        s = oracle.compress(kp, x, **kw)
+    except oracle.OracleError as err:
+        assert err.status == 4
+        return
+    assert np.array_equal(s, oracle.compress(kp, x, **kw))
+    y = oracle.decompress(kp, s)
+    f = oracle.field_params(x, **{k: v for k, v in kw.items()
+                                 if k not in ("f_op", "g_op", "open_loop")})
+    bound = f["tau1"] + f["tau2"] if kw["open_loop"] else f["tau2"]
+    assert np.abs(y.astype(np.float64) - x.astype(np.float64)).max() <= bound
