@@ -929,8 +929,11 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
 // ---------------------------------------------------------------------------
 // k_codebook: canonical Huffman code book of one component per CTA.
 //
-// Code lengths follow the two-queue construction over the leaves sorted by
-// (count, symbol): each step takes the two lightest nodes, a leaf before an
+// The used symbols' (count, symbol) keys are gathered by a shared counter and
+// bitonic-sorted at the next power of two of their number (with the
+// zero-run stage the symbol R takes no count: its zeros are coded as run
+// tokens 2R, 2R + 1). Code lengths follow the two-queue construction over
+// the leaves sorted by (count, symbol): each step takes the two lightest nodes, a leaf before an
 // internal node of equal weight, internal nodes in creation order. The pick
 // sequence is the sorted merge of the leaves and the internal nodes, and
 // internal node k is the sum of picks 2k and 2k+1; nodes created from picks
