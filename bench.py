@@ -40,6 +40,21 @@ import synth  # noqa: E402
 METRIC = "compress+decompress GB/s at eb=1e-4 rel"
 
 
+def component_bytes(header):
+    """Bytes of each component in a stream, from its header (uint8 array of
+    at least 208 bytes): the grid component's bitstream and escape values,
+    and the residual component's bitstream, escape values and raw values
+    (the shared header, code lengths and group tables are left out). The
+    paper's Fig. 5a/c compression ratios of the grid data and of the
+    residuals divide the components' raw bytes by these."""
+    u32 = lambda o: int(header[o:o + 4].view(np.uint32)[0])
+    u64 = lambda o: int(header[o:o + 8].view(np.uint64)[0])
+    vsz = 8 if u32(12) == 0 else 4
+    grid = 4 * (u64(168) + u64(144))
+    residual = 4 * (u64(176) + u64(152)) + vsz * u64(160)
+    return grid, residual
+
+
 def algorithmic_bytes(dim, n_v, n_g, vsz, w1, w2, cbytes):
     """HBM bytes each kernel must move at least once per launch (inputs read,
     outputs written). Gathers of the vertex codes and of the grid codes are
@@ -351,18 +366,21 @@ def grid_init_line(args, dev, flush, stream, wl, x):
                 mcc.decompress(pl, out, cap, y, wsd, sync=False)
 
             ms = time_replays(gstep, flush, 5, args.warmup, stream)
-            return x.numel() * 8 / size, ms
+            g_bytes, r_bytes = component_bytes(out[:208].cpu().numpy())
+            comp = {"grid_component_ratio": pl.n_grid * 8 / max(g_bytes, 1),
+                    "residual_component_ratio": x.numel() * 8 / max(r_bytes, 1)}
+            return x.numel() * 8 / size, ms, comp
 
         for fop, gop in (("barycentric", "multilinear"), ("cluster", "nearest")):
             prm = mcc.params_default(dtype=mcc.F64, eb=1e-4, grid_fraction=0.5, f_op=fop, g_op=gop)
-            ratio, ms = measure(plan, prm, f"{fop}, {gop}")
+            ratio, ms, comp = measure(plan, prm, f"{fop}, {gop}")
             row = {"k_pct": k, "grid": list(n), "grid_init_s": t_init, "f": fop, "g": gop,
                    "compression_ratio": ratio, "ms_per_step": ms,
-                   "GBps": x.numel() * 8 / (ms * 1e-3) / 1e9}
+                   "GBps": x.numel() * 8 / (ms * 1e-3) / 1e9, **comp}
             try:  # the same on the planes Grid_Coarsen keeps (recorded, never fatal here)
                 keep = mcc.grid_coarsen(plan, gop)
                 kplan = mcc.plan_create(cd, ed, n, lo, hi, keep=keep)
-                ratio_k, ms_k = measure(kplan, prm, f"{fop}, {gop}, coarsened")
+                ratio_k, ms_k, _ = measure(kplan, prm, f"{fop}, {gop}, coarsened")
                 kplan.close()
                 row.update({"coarsened_grid": [int(v.size) for v in keep],
                             "coarsened_compression_ratio": ratio_k, "coarsened_ms_per_step": ms_k,
