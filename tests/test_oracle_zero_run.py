@@ -179,6 +179,22 @@ def test_stream_decodes_independently(plan2d, eb, C):
         assert np.array_equal(np.array(lens), oracle.huffman_lengths(cnt, 24))
 
 
+@pytest.mark.parametrize("eb", [1e-1, 1e-3])
+def test_stream_decodes_independently_3d(eb):
+    """The same reader on a 3D annulus (tetrahedra, trilinear g) and on a
+    plan of kept planes (Grid_Coarsen): the stage sees only symbols."""
+    c, e = synth.mesh3d_annulus(nr=5, nth=20, nz=6, seed=4)
+    x = synth.field_vortex(c, seed=5)
+    base = oracle.Plan(c, e, (21, 19, 15))
+    for plan in (base, oracle.Plan(c, e, (21, 19, 15), keep=oracle.grid_coarsen(base, "nearest"))):
+        s, dbg = oracle.compress(plan, x, debug=True, eb=eb, C1=17, C2=64, zero_run=True)
+        for which, key in ((1, "sym1"), (2, "sym2")):
+            sym, toks, lens = _decode_component(s, which, True)
+            assert np.array_equal(sym, dbg[key].astype(np.int64))
+            C = 17 if which == 1 else 64
+            assert np.array_equal(toks, _tokens(dbg[key].astype(np.int64), sym.size, C, 512))
+
+
 def test_stage_off_decodes_independently(plan2d):
     """The same reader without the stage (tokens are the symbols)."""
     coords, plan = plan2d
