@@ -161,6 +161,21 @@ def test_bijective_digits_closed_form():
         assert sum(x << i for i, x in enumerate(d)) == r
 
 
+def test_digits_are_the_bits_of_r_plus_one():
+    """The identity the GPU coder uses to cost and write a run: the bijective
+    base-2 digits of r, least significant first, are the bits of r + 1
+    below its leading one, each plus one."""
+    for r in range(1, 20000):
+        d, t = [], r
+        while t:
+            x = 1 if t % 2 else 2
+            d.append(x)
+            t = (t - x) // 2
+        v = r + 1
+        bits = [(v >> i) & 1 for i in range(v.bit_length() - 1)]
+        assert d == [b + 1 for b in bits]
+
+
 @pytest.mark.parametrize("eb", [1e-1, 1e-2, 1e-4])
 @pytest.mark.parametrize("C", [1, 5, 128])
 def test_stream_decodes_independently(plan2d, eb, C):
