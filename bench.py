@@ -2,12 +2,14 @@
 """Throughput benchmark of the GB300 multi-component compressor.
 
 Metric: compress + decompress GB/s of input values (n_v x sizeof(value) bytes
-per field) at relative bound 1e-4 (grid / residual split 0.5), together with
-the compression ratio, on the 2D graded workload: 2,000,000 vertices with
-density ~ exp(-4 |p - c|) around c = (0.3, 0.6), Delaunay triangulated, a
-float64 field of 20 Gaussian bumps plus 6-octave value noise, on a 1024^2
-grid (the stand-in for the paper's OpenFOAM airfoil-large, Table I). The
-plan (mesh -> grid mapping) is built once and excluded, as in Sec. IV-A.
+per field) at relative bound 1e-4 (grid / residual split 0.5), with the
+compression ratio. Headline workload (default ``--config c3``): the 3D
+tetrahedral annulus, a cylinder of radius 1 and height 2 with a coaxial hole
+of radius 0.3, (64, 512, 244) jittered structured nodes (7,995,392 vertices)
+split into 39,191,040 tetrahedra, vertex and cell order shuffled; a float64
+swirling vortex plus 4-octave value noise; a 256^3 grid (the stand-in for
+the paper's Nek5000 pipe / VKI blade meshes, Table I). The plan (mesh -> grid
+mapping) is built once and excluded, as in Sec. IV-A.
 
 One step = mcc_compress + mcc_decompress of one device-resident field,
 enqueued without host synchronisation and replayed as one CUDA graph. The L2
@@ -16,13 +18,23 @@ timed with CUDA events on the launch stream. Under torchrun every rank runs an
 independent replica on its own GPU (the method has no exchange step); value is
 the sum over ranks of the input bytes divided by the slowest rank's time.
 
-``--impl reference`` times the CPU oracle (single core) on the same workload.
+Output: one compact JSON object per side measurement ({"side": name, ...};
+other bounds, operators, the zero-run stage, the 1D default, Grid_Init, the
+2D graded mesh, batches, the learned predictor, the split sweep, many
+variables x timesteps), then, as the LAST line, the headline (metric, value,
+roofline, cpu_baseline, e2e, clocks). ``--side-out PATH`` also writes the
+side objects to a file.
+
+``--impl reference`` times the CPU oracle on the machine's host cores (one
+process per core, each compressing and decompressing a bounded sample of the
+same workload) and prints the same headline keys with "impl": "reference".
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -38,6 +50,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "compress+decompress GB/s at eb=1e-4 rel"
+HEADLINE_MAX_BYTES = 2048
 
 
 def max_over_ranks(ms, world, device):
@@ -58,6 +71,25 @@ def job_value(world, nbytes, ms):
     return world * nbytes / (ms * 1e-3) / 1e9
 
 
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def rnd(v, digits=4):
+    """Round floats to `digits` significant digits (compact side lines)."""
+    if isinstance(v, float):
+        if not math.isfinite(v) or v == 0.0:
+            return v if math.isfinite(v) else None
+        return float(f"{v:.{digits}g}")
+    if isinstance(v, dict):
+        return {k: rnd(x, digits) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [rnd(x, digits) for x in v]
+    return v
+
+
 def component_bytes(header):
     """Bytes of each component in a stream, from its header (uint8 array of
     at least 208 bytes): the grid component's bitstream and escape values,
@@ -73,44 +105,36 @@ def component_bytes(header):
     return grid, residual
 
 
-def algorithmic_bytes(dim, n_v, n_g, vsz, w1, w2, cbytes):
-    """HBM bytes each kernel must move at least once per launch (inputs read,
-    outputs written). Gathers of the vertex codes and of the grid codes are
-    counted as cache hits: both arrays fit in L2."""
+def algorithmic_bytes(dim, n_v, n_g, vsz, cbytes):
+    """HBM bytes each kernel must move at least once per LAUNCH (inputs read,
+    outputs written), for a plain-predictor field. Gathers of the vertex
+    codes Q (4 n_v bytes) and of the grid codes q1 (4 n_g bytes) are counted
+    as cache hits (each array is read from HBM once by its streaming
+    producer or consumer). cbytes = the compressed stream."""
     k1 = dim + 1
     return {
-        "k_reduce": vsz * n_v,
-        "k_prequant": (vsz + 4) * n_v,
-        "k_grid2d": (4 * k1 + 2 * dim + 4 + 2) * n_g,
+        "k_reduce": vsz * n_v,                                 # x
+        "k_prequant": (vsz + 4) * n_v,                         # x in, Q out
+        "k_grid2d": (4 * k1 + 2 * dim + 4 + 2) * n_g,          # ids, weights in; q1, symbols out
         "k_grid3d": (4 * k1 + 2 * dim + 4 + 2) * n_g,
-        "k_node": (4 + 2 * dim + 4 + 2) * n_v,
+        "k_node": (4 + 2 * dim + 4 + 2) * n_v,                 # cell, local coords, Q in; symbols out
         "k_codebook": 0,
-        "k_group_len": 2 * (n_g + n_v),
-        "k_scan": 0,
-        "k_pack": 2 * (n_g + n_v) + cbytes,
+        "k_group_len": 2 * (n_g + n_v),                        # symbols in
+        "k_pack": 2 * (n_g + n_v) + cbytes,                    # symbols in, stream out
         "k_runs": 2 * (n_g + n_v),
         "k_dec_prep": 0,
-        "k_dec_syms": 4 * (w1 + w2) + 4 * (n_g + n_v),
-        "k_scan_rows": 8 * n_g,
-        "k_scan_axis": 12 * n_g,
-        "k_recon": 4 * n_v + (4 + 2 * dim) * n_v + vsz * n_v,
+        "k_dec_syms": cbytes + 4 * (n_g + n_v),                # stream in; deltas, q2 out
+        "k_scan_rows": 8 * n_g,                                # one read + one write per pass
+        "k_scan_axis": 8 * n_g,
+        "k_predict": 0,                                        # plain streams: returns at once
+        "k_recon": (4 + 2 * dim + 4 + vsz) * n_v,              # cell, local coords, q2 in; x' out
     }
 
 
-def load_workload(config):
-    if config == "c2":
-        coords, cells = synth.mesh2d_graded()
-        return dict(name="2d-graded-2M-delaunay-grid1024^2", coords=coords, cells=cells,
-                    x=synth.field_bumps_noise(coords), n=(1024, 1024))
-    if config == "c1":
-        coords, cells = synth.mesh2d_jittered()
-        return dict(name="2d-jittered-20k-grid128^2", coords=coords, cells=cells,
-                    x=synth.field_sincos(coords), n=(128, 128))
-    if config == "c3":
-        coords, cells = synth.mesh3d_annulus()
-        return dict(name="3d-annulus-8M-tets39M-grid256^3", coords=coords, cells=cells,
-                    x=synth.field_vortex(coords), n=(256, 256, 256))
-    raise SystemExit(f"unknown config {config}")
+def step_bytes(alg, per_kernel):
+    """Algorithmic bytes of one whole step: every kernel's per-launch bytes
+    times its launches per step."""
+    return sum(alg.get(k, 0) * v["launches_per_step"] for k, v in per_kernel.items())
 
 
 class ClockSampler:
@@ -167,63 +191,172 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
-                "window": "0.5 s pre-roll of the same step plus the timed region"}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def run_reference(args, wl):
-    """The CPU oracle (single-threaded C) timed on the same workload."""
+# --------------------------------------------------------------------------- #
+# workloads
+# --------------------------------------------------------------------------- #
+WORKLOADS = {
+    "c3": "3d-annulus-8M-tets39M-grid256^3-f64",
+    "c2": "2d-graded-2M-delaunay-grid1024^2-f64",
+    "c1": "2d-jittered-20k-grid128^2-f64",
+}
+
+
+def load_mesh(config):
+    """(coords, cells, grid) of a workload (the field is made separately)."""
+    if config == "c3":
+        coords, cells = synth.mesh3d_annulus()
+        return coords, cells, (256, 256, 256)
+    if config == "c2":
+        coords, cells = synth.mesh2d_graded()
+        return coords, cells, (1024, 1024)
+    if config == "c1":
+        coords, cells = synth.mesh2d_jittered()
+        return coords, cells, (128, 128)
+    raise SystemExit(f"unknown config {config}")
+
+
+def field_on_device(config, coords, cd):
+    """The workload's FP64 field, on the device (numpy for the 2D ones)."""
+    import torch
+    if config == "c3":
+        from synth import torchgen
+        return torchgen.field_vortex(cd, seed=6)
+    x = synth.field_bumps_noise(coords) if config == "c2" else synth.field_sincos(coords)
+    return torch.from_numpy(x).to(cd.device)
+
+
+# --------------------------------------------------------------------------- #
+# CPU baseline: the oracle on the host cores (one process per core)
+# --------------------------------------------------------------------------- #
+SLAB_LAYERS = 17
+
+
+def cpu_sample(config):
+    """A bounded sample of the workload for the CPU oracle: (coords, cells,
+    grid, x, description). The 3D annulus: its bottom 17 node layers (same
+    radial / angular resolution and z spacing) with an 18-plane grid of the
+    full grid's spacing; the 2D workloads: the full mesh."""
+    if config == "c3":
+        coords, cells = synth.mesh3d_annulus_slab(SLAB_LAYERS)
+        h = 2.0 / 255.0
+        nz = int(round(float(coords[:, 2].max() - coords[:, 2].min()) / h)) + 1
+        x = synth.field_vortex(coords)
+        return coords, cells, (256, 256, nz), x, (
+            f"z-slab of the annulus: {SLAB_LAYERS} of 244 node layers, {x.size} vertices, "
+            f"{cells.shape[0]} tets, grid 256x256x{nz} (same spacings), FP64 vortex, "
+            "rel 1e-4, plan excluded")
+    coords, cells, n = load_mesh(config)
+    x = synth.field_bumps_noise(coords) if config == "c2" else synth.field_sincos(coords)
+    return coords, cells, n, x, f"full workload ({x.size} vertices), plan excluded"
+
+
+_W = {}
+
+
+def _oracle_init(config, eb):
     import oracle
-    if int(os.environ.get("RANK", "0")) != 0:
-        return
-    plan = oracle.Plan(wl["coords"], wl["cells"], wl["n"])
-    x = wl["x"]
-    kw = dict(eb=args.eb, grid_fraction=0.5)
-    for _ in range(args.warmup):
-        oracle.decompress(plan, oracle.compress(plan, x, **kw))
-    times, size = [], 0
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        s = oracle.compress(plan, x, **kw)
-        oracle.decompress(plan, s)
-        times.append(time.perf_counter() - t0)
-        size = s.size
-    t = statistics.mean(times)
-    gbs = x.nbytes / t / 1e9
-    print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": wl["name"], "eb_rel": args.eb, "grid_fraction": 0.5,
-                   "compression_ratio": x.nbytes / size},
-        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"full workload, {args.steps} steps, plan excluded"},
-        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }), flush=True)
+    coords, cells, n, x, _ = cpu_sample(config)
+    _W.update(plan=oracle.Plan(coords, cells, n), x=x, eb=eb)
 
 
-def cpu_baseline(wl, eb, budget_s=12.0):
-    """The oracle's compress + decompress, repeated over a bounded time budget."""
+def _oracle_task(_):
     import oracle
-    plan = oracle.Plan(wl["coords"], wl["cells"], wl["n"])
-    x = wl["x"]
-    reps, t_total = 0, 0.0
-    while t_total < budget_s and reps < 200:
+    t0 = time.perf_counter()
+    s = oracle.compress(_W["plan"], _W["x"], eb=_W["eb"])
+    oracle.decompress(_W["plan"], s)
+    return time.perf_counter() - t0, int(s.size)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def oracle_all_cores(config, eb, steps, warmup, procs=None):
+    """One process per host core (spawned: none inherits a CUDA context);
+    a step = every process compresses and decompresses the sample once.
+    Returns (GB/s over all processes, per-step seconds, processes, nbytes,
+    stream bytes, description)."""
+    import multiprocessing as mp
+    procs = procs or host_cores()
+    _, _, _, x, desc = cpu_sample(config)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs, initializer=_oracle_init, initargs=(config, eb)) as pool:
+        for _ in range(warmup):
+            pool.map(_oracle_task, range(procs), chunksize=1)
+        walls, size = [], 0
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_task, range(procs), chunksize=1)
+            walls.append(time.perf_counter() - t0)
+            size = res[0][1]
+    t = statistics.mean(walls)
+    return procs * x.nbytes / t / 1e9, walls, procs, x.nbytes, size, desc
+
+
+def oracle_one_core(config, eb, steps, warmup):
+    """The oracle in this process (one thread): GB/s and seconds per step."""
+    import oracle
+    coords, cells, n, x, desc = cpu_sample(config)
+    plan = oracle.Plan(coords, cells, n)
+    for _ in range(warmup):
+        oracle.decompress(plan, oracle.compress(plan, x, eb=eb))
+    ts = []
+    for _ in range(steps):
         t0 = time.perf_counter()
         s = oracle.compress(plan, x, eb=eb)
         oracle.decompress(plan, s)
-        t_total += time.perf_counter() - t0
-        reps += 1
-    return {"value": x.nbytes * reps / t_total / 1e9, "unit": "GB/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{reps} x compress+decompress of the full {x.size}-vertex field, "
-                      f"{t_total:.1f} s, plan excluded"}
+        ts.append(time.perf_counter() - t0)
+    t = statistics.mean(ts)
+    return x.nbytes / t / 1e9, t, x.nbytes, int(s.size), desc
 
 
-def time_replays(fn, flush, steps, warmup, stream):
+def cpu_baseline(config, eb, steps=6, warmup=1):
+    """The oracle as it stands on the host cores: all cores (one process
+    each) and one core, on the bounded sample (10-30 s of CPU work)."""
+    v1, t1, nbytes, size, desc = oracle_one_core(config, eb, steps, warmup)
+    vn, walls, procs, _, _, _ = oracle_all_cores(config, eb, steps, warmup)
+    return {"value": vn, "unit": "GB/s", "cores": procs, "kind": "oracle",
+            "sample": f"{desc}; {steps} steps of one compress+decompress per process",
+            "single_core": {"value": v1, "cores": 1, "ms_per_step": t1 * 1e3},
+            "nproc": host_cores(), "compression_ratio": nbytes / size}
+
+
+def run_reference(args):
+    """The CPU oracle timed on the host cores: every step, one process per
+    core compresses and decompresses the bounded sample once (rank 0 only;
+    other ranks exit without work)."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    vn, walls, procs, nbytes, size, desc = oracle_all_cores(args.config, args.eb, args.steps,
+                                                            args.warmup)
+    v1, t1, _, _, _ = oracle_one_core(args.config, args.eb, max(3, min(args.steps, 10)), 1)
+    ms = statistics.mean(walls) * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": vn, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.config], "eb_rel": args.eb, "grid_fraction": 0.5,
+                   "compression_ratio": nbytes / size, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": vn, "unit": "GB/s", "cores": procs, "kind": "oracle",
+                         "sample": f"{desc}; a step = one compress+decompress per process",
+                         "single_core": {"value": v1, "cores": 1, "ms_per_step": t1 * 1e3},
+                         "nproc": host_cores()},
+        "e2e": {"value": vn, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(rnd(line, 6), allow_nan=False), flush=True)
+
+
+def time_replays(fn, flush, steps, warmup, stream, world=1):
     """fn captured in one CUDA graph; mean ms of `steps` replays, each after an
-    L2 flush and bracketed by events on the launch stream."""
+    L2 flush and bracketed by events on the launch stream (a barrier on both
+    sides of the timed loop when there are several ranks)."""
     import torch
     fn()
     torch.cuda.synchronize()
@@ -236,32 +369,257 @@ def time_replays(fn, flush, steps, warmup, stream):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     torch.cuda.synchronize()
+    barrier(world)
     for k, (a, b) in enumerate(ev):
         flush.fill_(k & 0xFF)
         a.record(stream)
         g.replay()
         b.record(stream)
     torch.cuda.synchronize()
+    barrier(world)
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     del g
     return ms
 
 
-def learned_line(args, dev, flush, stream):
-    """The learned residual predictor on the 3D annulus (8M vertices, 256^3
-    grid): trained on the GPU on 16 seeds of vortex + noise fields, evaluated
-    on 2 unseen seeds at rel 1e-4 against the plain predictor (auto choice
-    per field)."""
+class Field:
+    """One field on one plan with its workspaces and buffers."""
+
+    def __init__(self, mcc, plan, x, prm):
+        import torch
+        self.mcc, self.plan, self.x, self.prm = mcc, plan, x, prm
+        self.wsc = plan.workspace(prm, "compress")
+        self.wsd = plan.workspace(prm, "decompress")
+        self.cap = mcc.compress_bound(plan, prm)
+        self.out = torch.zeros(self.cap, dtype=torch.uint8, device=x.device)
+        self.y = torch.empty_like(x)
+
+    def step(self):
+        self.mcc.compress(self.plan, self.x, self.prm, self.wsc, self.out, sync=False)
+        self.mcc.decompress(self.plan, self.out, self.cap, self.y, self.wsd, sync=False)
+
+    def check(self, eb, what):
+        """One synchronous round trip; the bound at every vertex. Returns
+        (stream bytes, max |x - x'| / tau)."""
+        size = self.mcc.compress(self.plan, self.x, self.prm, self.wsc, self.out)
+        self.mcc.decompress(self.plan, self.out, size, self.y, self.wsd)
+        x = self.x.double()
+        tau = eb * (float(x.max()) - float(x.min()))
+        err = float((self.y.double() - x).abs().max())
+        if not err <= tau:
+            raise RuntimeError(f"{what}: bound violated ({err} > {tau})")
+        return size, err / tau
+
+
+def kernel_times(mcc, step, flush, steps):
+    """Per-kernel device times: the step captured with an event pair around
+    every kernel, replayed `steps` times (L2 flushed before each). Returns
+    {name: [total ms, launches]}."""
     import torch
-    import paper_2501_06910_gb300 as mcc
+    prof = {}
+    mcc.profile_reset()
+    mcc.profile_enable(True)
+    pgraph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(pgraph):
+        step()
+    mcc.profile_enable(False)
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        pgraph.replay()
+        torch.cuda.synchronize()
+        for name, (t, n) in mcc.profile_read().items():
+            a = prof.setdefault(name, [0.0, 0])
+            a[0] += t
+            a[1] += n
+    mcc.profile_reset()
+    del pgraph
+    return prof
+
+
+def dram_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, only
+    while the kernel's source file is the one the counters were taken on."""
+    tfile = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(tfile):
+        return None
+    ent = json.load(open(tfile)).get(kernel)
+    if not isinstance(ent, dict):
+        return None
+    src = os.path.join(ROOT, "paper_2501_06910_gb300", "csrc", ent["source"])
+    if os.path.exists(src) and hashlib.sha1(open(src, "rb").read()).hexdigest() == ent["sha1"]:
+        return ent["bytes"]
+    return None
+
+
+def build_headline(*, world, steps, warmup, ms, nbytes, config, prof, alg, peaks, cpu, e2e,
+                   clocks, traffic=None):
+    """The headline JSON object (the last stdout line, under 2 KB): metric and
+    value, the dominant kernel's roofline and the whole step's, the CPU
+    oracle baseline, the end-to-end figure and the clocks."""
+    per_kernel = {}
+    if prof:
+        tot = sum(t for t, _ in prof.values()) or 1.0
+        per_kernel = {k: {"ms_per_launch": t / n, "launches_per_step": n / steps, "share": t / tot}
+                      for k, (t, n) in prof.items() if n}
+    hbm = peaks.get("hbm_gbs")
+    peak_source = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    roofline = None
+    if per_kernel:
+        dom = max(per_kernel, key=lambda k: per_kernel[k]["share"])
+        achieved = alg.get(dom, 0) / (per_kernel[dom]["ms_per_launch"] * 1e-3) / 1e9
+        sb = step_bytes(alg, per_kernel)
+        step_gbs = sb / (ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": traffic(dom) if traffic else None,
+                    "kernel": dom, "alg_bytes_per_launch": alg.get(dom, 0),
+                    "step_alg_bytes": sb, "step_achieved": step_gbs, "step_frac": step_gbs / hbm,
+                    "peak_source": f"{peak_source} (hbm_gbs, copy)"}
+    launches = sum(n for _, n in prof.values()) if prof else None
+    line = {
+        "metric": METRIC,
+        "value": job_value(world, nbytes, ms),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": config,
+        "roofline": roofline,
+        "kernels_us": {k: [v["ms_per_launch"] * 1e3, v["launches_per_step"]]
+                       for k, v in sorted(per_kernel.items(), key=lambda kv: -kv[1]["share"])},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": None if launches is None else int(launches),
+        "clocks": clocks,
+    }
+    return rnd(line, 5)
+
+
+def headline_json(line):
+    s = json.dumps(line, allow_nan=False, separators=(",", ":"))
+    if len(s) > HEADLINE_MAX_BYTES:  # drop the per-kernel table before anything else
+        line = dict(line)
+        line.pop("kernels_us", None)
+        s = json.dumps(line, allow_nan=False, separators=(",", ":"))
+    return s
+
+
+class Sides:
+    """Side measurements: each printed as one compact JSON line as it
+    completes (and collected for --side-out); a failing one records its
+    error and the run goes on."""
+
+    def __init__(self, path):
+        self.path = path
+        self.rows = []
+
+    def run(self, name, fn, *a, **kw):
+        t0 = time.perf_counter()
+        try:
+            res = fn(*a, **kw)
+        except Exception as err:  # noqa: BLE001 -- recorded, never fatal
+            res = {"error": f"{type(err).__name__}: {err}"}
+        row = {"side": name, "wall_s": time.perf_counter() - t0, **(res or {})}
+        row = rnd(row, 4)
+        self.rows.append(row)
+        print(json.dumps(row, allow_nan=False, separators=(",", ":")), flush=True)
+        import torch
+        torch.cuda.empty_cache()
+
+    def write(self):
+        if self.path:
+            with open(self.path, "w") as f:
+                for r in self.rows:
+                    f.write(json.dumps(r, allow_nan=False) + "\n")
+
+
+# --------------------------------------------------------------------------- #
+# side measurements
+# --------------------------------------------------------------------------- #
+def rate(nbytes, ms):
+    return nbytes / (ms * 1e-3) / 1e9
+
+
+def side_bounds(mcc, plan, x, flush, stream, args, ebs=(1e-6, 1e-2)):
+    """Other bounds on the headline field: ratio and compress+decompress rate."""
+    rows = []
+    for eb in ebs:
+        f = Field(mcc, plan, x, mcc.params_default(dtype=mcc.F64, eb=eb, grid_fraction=0.5))
+        size, e = f.check(eb, f"eb {eb}")
+        ms = time_replays(f.step, flush, max(5, args.steps // 4), args.warmup, stream)
+        rows.append({"eb_rel": eb, "ratio": x.numel() * 8 / size, "ms": ms,
+                     "GBps": rate(x.numel() * 8, ms), "err_over_tau": e})
+    return {"rows": rows}
+
+
+def side_batched(mcc, plan, x, flush, stream, args, world):
+    """B copies of the headline field per step through mcc_compress_batch /
+    mcc_decompress_batch (one graph; plan shared; L2 flushed per step)."""
+    import torch
+    B = args.batch
+    xs = [x.clone() for _ in range(B)]
+    ys = [torch.empty_like(x) for _ in range(B)]
+    prm = mcc.params_default(dtype=mcc.F64, eb=args.eb, grid_fraction=0.5)
+    prms = [prm] * B
+    cap = mcc.compress_bound(plan, prm)
+    slot = (cap + 7) // 8 * 8
+    bout = torch.zeros(slot * B, dtype=torch.uint8, device=x.device)
+    cws, dws = mcc.workspace_size(plan, prm)
+    chain = min(B, 64)
+    bwsc = torch.empty(cws * chain, dtype=torch.uint8, device=x.device)
+    bwsd = torch.empty(dws * chain, dtype=torch.uint8, device=x.device)
+
+    def bstep():
+        mcc.compress_batch(plan, xs, prms, bwsc, bout, slot, sync=False)
+        mcc.decompress_batch(plan, bout, slot, [slot] * B, ys, bwsd, sync=False)
+
+    sizes = mcc.compress_batch(plan, xs, prms, bwsc, bout, slot, sync=True)
+    mcc.decompress_batch(plan, bout, slot, sizes, ys, bwsd, sync=True)
+    ref = Field(mcc, plan, x, prm)
+    ref.check(args.eb, "batched reference")
+    if any(not torch.equal(ys[f], ref.y) for f in range(B)):
+        raise RuntimeError("batched result differs from the single-field result")
+    ms = time_replays(bstep, flush, max(5, args.steps // 2), args.warmup, stream, world)
+    ms = max_over_ranks(ms, world, x.device)
+    return {"fields_per_step": B, "ms_per_step": ms,
+            "GBps": job_value(world, B * x.numel() * 8, ms),
+            "ratio": x.numel() * 8 / sizes[0]}
+
+
+def side_split(mcc, plan, cd, flush, stream, args):
+    """The 3D configuration's grid / residual split swept 0.2 .. 0.8, FP64
+    and FP32 fields (seed 6), rel 1e-4, closed loop (residual against the
+    decompressed grid) and open loop (against the grid before quantisation,
+    Algorithm 3 as printed): ratio / GB/s / max error over tau."""
     from synth import torchgen
-    t0 = time.perf_counter()
-    coords, cells = synth.mesh3d_annulus()
-    cd = torch.from_numpy(coords).to(dev)
-    plan = mcc.plan_create(cd, torch.from_numpy(cells).to(dev), (256, 256, 256))
-    del cells
-    torch.cuda.synchronize()
-    t_setup = time.perf_counter() - t0
+    x64 = torchgen.field_vortex(cd, seed=6)
+    rows = []
+    for dt, xx in (("f64", x64), ("f32", x64.float())):
+        for loop in ("closed", "open"):
+            for frac in (0.2, 0.35, 0.5, 0.65, 0.8):
+                prm = mcc.params_default(dtype=mcc.F64 if dt == "f64" else mcc.F32, eb=1e-4,
+                                         grid_fraction=frac, open_loop=loop == "open")
+                f = Field(mcc, plan, xx, prm)
+                size, e = f.check(1e-4, f"split {dt} {loop} {frac}")
+                ms = time_replays(f.step, flush, 5, args.warmup, stream)
+                nb = xx.numel() * xx.element_size()
+                rows.append([dt, loop, frac, nb / size, rate(nb, ms), e])
+                del f
+    return {"cols": ["dtype", "loop", "grid_fraction", "ratio", "GBps", "err_over_tau"],
+            "rows": rows}
+
+
+def side_learned(mcc, plan, cd, flush, stream, args):
+    """The learned residual predictor on the 3D annulus: trained on the GPU on
+    16 seeds of vortex + noise fields, evaluated on 2 unseen seeds at rel
+    1e-4 against the plain predictor (auto choice per field)."""
+    from synth import torchgen
     eb = 1e-4
     base = dict(dtype=mcc.F64, eb=eb, grid_fraction=0.5)
     train = [torchgen.field_vortex(cd, seed=1000 + i) for i in range(16)]
@@ -270,154 +628,159 @@ def learned_line(args, dev, flush, stream):
     model, losses = mcc.model_train(plan, train, mcc.params_default(**base), cfg)
     t_train = time.perf_counter() - t0
     del train
-    res = {"workload": "3d-annulus-8M-tets39M-grid256^3, vortex + 4-octave noise, FP64, "
-                       "train seeds 1000-1015, eval seeds 2000-2001, rel 1e-4",
-           "train_s": t_train, "train_steps": cfg.steps, "train_batch": cfg.batch,
-           "samples_per_field": int(cfg.samples_per_field),
+    res = {"train_s": t_train, "train_steps": cfg.steps, "train_batch": cfg.batch,
            "loss_first_100": float(np.mean(losses[:100])),
-           "loss_last_100": float(np.mean(losses[-100:])), "setup_s": t_setup}
-    n = coords.shape[0]
-    out = {}
+           "loss_last_100": float(np.mean(losses[-100:]))}
+    n = cd.shape[0]
     for label, prm in (("plain", mcc.params_default(**base)),
                        ("learned", mcc.params_default(model=model, auto=True, **base))):
-        cws, dws = mcc.workspace_size(plan, prm)
-        wsc = torch.empty(cws, dtype=torch.uint8, device=dev)
-        wsd = torch.empty(dws, dtype=torch.uint8, device=dev)
-        cap = mcc.compress_bound(plan, prm)
-        buf = torch.empty(cap, dtype=torch.uint8, device=dev)
         sizes, mss, chosen = [], [], []
         for seed in (2000, 2001):
-            x = torchgen.field_vortex(cd, seed=seed)
-            y = torch.empty_like(x)
-            size = mcc.compress(plan, x, prm, wsc, buf)
-            mcc.decompress(plan, buf, size, y, wsd)
-            tau = eb * float(x.max() - x.min())
-            if not float((y - x).abs().max()) <= tau:
-                raise SystemExit(f"learned line: bound violated ({label})")
-            chosen.append("learned" if int(buf[20].item()) & 2 else "plain")
+            f = Field(mcc, plan, torchgen.field_vortex(cd, seed=seed), prm)
+            size, _ = f.check(eb, f"learned line ({label})")
+            chosen.append("learned" if int(f.out[20].item()) & 2 else "plain")
             sizes.append(size)
-
-            def step():
-                mcc.compress(plan, x, prm, wsc, buf, sync=False)
-                mcc.decompress(plan, buf, cap, y, wsd, sync=False)
-
-            mss.append(time_replays(step, flush, max(5, args.steps // 4), args.warmup, stream))
-        out[label] = {"compression_ratio": 2 * n * 8 / sum(sizes), "stream_bytes": sizes,
-                      "ms_per_field": statistics.mean(mss),
-                      "GBps": n * 8 / (statistics.mean(mss) * 1e-3) / 1e9,
-                      "chosen": chosen}
-        del wsc, wsd, buf
-    res.update(out)
-    res["ratio_gain"] = out["learned"]["compression_ratio"] / out["plain"]["compression_ratio"]
-    # the 3D configuration itself: grid / residual split swept 0.2 .. 0.8,
-    # FP64 and FP32 fields (seed 6), plain predictor, rel 1e-4, closed loop
-    # (residual against the decompressed grid) and open loop (against the
-    # grid before quantisation, Algorithm 3 as printed)
-    sweep = []
-    x64 = torchgen.field_vortex(cd, seed=6)
-    cases = [(dt, xx, loop, frac) for dt, xx in (("f64", x64), ("f32", x64.float()))
-             for loop in ("closed", "open") for frac in (0.2, 0.35, 0.5, 0.65, 0.8)]
-    for dt, xx, loop, frac in cases:
-        yy = torch.empty_like(xx)
-        prm = mcc.params_default(dtype=mcc.F64 if dt == "f64" else mcc.F32, eb=eb,
-                                 grid_fraction=frac, open_loop=loop == "open")
-        cws, dws = mcc.workspace_size(plan, prm)
-        wsc = torch.empty(cws, dtype=torch.uint8, device=dev)
-        wsd = torch.empty(dws, dtype=torch.uint8, device=dev)
-        cap = mcc.compress_bound(plan, prm)
-        buf = torch.empty(cap, dtype=torch.uint8, device=dev)
-        size = mcc.compress(plan, xx, prm, wsc, buf)
-        mcc.decompress(plan, buf, size, yy, wsd)
-        tau = eb * float(xx.max() - xx.min())
-        err = float((yy.double() - xx.double()).abs().max())
-        if not err <= tau:
-            raise SystemExit(f"split sweep: bound violated ({dt}, {frac})")
-
-        def sstep(prm=prm, xx=xx, yy=yy, wsc=wsc, wsd=wsd, buf=buf, cap=cap):
-            mcc.compress(plan, xx, prm, wsc, buf, sync=False)
-            mcc.decompress(plan, buf, cap, yy, wsd, sync=False)
-
-        ms = time_replays(sstep, flush, 5, args.warmup, stream)
-        nb = xx.numel() * xx.element_size()
-        sweep.append({"dtype": dt, "loop": loop, "grid_fraction": frac,
-                      "compression_ratio": nb / size,
-                      "ms_per_field": ms, "GBps": nb / (ms * 1e-3) / 1e9,
-                      "max_abs_err_over_tau": err / tau})
-        del wsc, wsd, buf
-    res["c3_split_sweep"] = sweep
-    plan.close()
+            mss.append(time_replays(f.step, flush, max(5, args.steps // 4), args.warmup, stream))
+            del f
+        res[label] = {"ratio": 2 * n * 8 / sum(sizes), "ms_per_field": statistics.mean(mss),
+                      "GBps": rate(n * 8, statistics.mean(mss)), "chosen": chosen}
+    res["ratio_gain"] = res["learned"]["ratio"] / res["plain"]["ratio"]
     return res
 
 
-def grid_init_line(args, dev, flush, stream, wl, x):
-    """Grid_Init (Algorithm 1) on the benchmark mesh: the grid from the
-    bottom k-th percentile of the edge extents (gmax 4096, delta 1), for
-    several k; ratio and compress+decompress rate at rel 1e-4 with the
-    default operators and with the paper's (cluster-mean f, nearest-node g),
-    on the uniform grid and on its planes kept by Grid_Coarsen (Algorithm 2,
-    for the same g). The plans are built outside the timed region."""
+def side_c2(mcc, dev, flush, stream, args, sides):
+    """The 2D graded workload (2M vertices, 1024^2 grid, FP64): the main
+    figures at rel 1e-6 / 1e-4 / 1e-2, the operators (Sec. III-B, III-C),
+    the zero-run stage, the paper's 1D default (Sec. V) and Grid_Init
+    (Algorithm 1) with Grid_Coarsen (Algorithm 2); one side line each."""
     import torch
-    import paper_2501_06910_gb300 as mcc
-    cd = torch.from_numpy(wl["coords"]).to(dev)
-    ed = torch.from_numpy(wl["cells"]).to(dev)
-    rows = []
-    for k in (30.0, 50.0, 70.0, 90.0, 99.0):
-        t0 = time.perf_counter()
-        n, lo, hi = mcc.grid_init(cd, ed, k, 1.0, 4096)
-        t_init = time.perf_counter() - t0
-        plan = mcc.plan_create(cd, ed, n, lo, hi)
+    coords, cells, n = load_mesh("c2")
+    cd = torch.from_numpy(coords).to(dev)
+    ed = torch.from_numpy(cells).to(dev)
+    plan = mcc.plan_create(cd, ed, n)
+    x = field_on_device("c2", coords, cd)
+    nb = x.numel() * 8
+    ratios = {}
 
-        def measure(pl, prm, what):
-            wsc = pl.workspace(prm, "compress")
-            wsd = pl.workspace(prm, "decompress")
-            cap = mcc.compress_bound(pl, prm)
-            out = torch.empty(cap, dtype=torch.uint8, device=dev)
-            y = torch.empty_like(x)
-            size = mcc.compress(pl, x, prm, wsc, out)
-            mcc.decompress(pl, out, size, y, wsd)
-            tau = 1e-4 * (float(x.max()) - float(x.min()))
-            if not float((y - x).abs().max()) <= tau:
-                raise SystemExit(f"grid_init line: bound violated (k {k}, {what})")
+    def main_rows():
+        rows = []
+        for eb in (1e-6, 1e-4, 1e-2):
+            f = Field(mcc, plan, x, mcc.params_default(dtype=mcc.F64, eb=eb, grid_fraction=0.5))
+            size, e = f.check(eb, f"c2 eb {eb}")
+            ms = time_replays(f.step, flush, max(5, args.steps // 2), args.warmup, stream)
+            ratios[eb] = nb / size
+            rows.append({"eb_rel": eb, "ratio": nb / size, "ms": ms, "GBps": rate(nb, ms),
+                         "err_over_tau": e})
+        return {"workload": WORKLOADS["c2"], "rows": rows}
 
-            def gstep():
-                mcc.compress(pl, x, prm, wsc, out, sync=False)
-                mcc.decompress(pl, out, cap, y, wsd, sync=False)
+    def operators():
+        rows = []
+        for eb in (1e-6, 1e-4, 1e-2):
+            for fop, gop in (("barycentric", "multilinear"), ("barycentric", "nearest"),
+                             ("cluster", "multilinear"), ("cluster", "nearest")):
+                prm = mcc.params_default(dtype=mcc.F64, eb=eb, grid_fraction=0.5, f_op=fop,
+                                         g_op=gop)
+                f = Field(mcc, plan, x, prm)
+                size, e = f.check(eb, f"operators {fop} {gop} {eb}")
+                ms = time_replays(f.step, flush, 5, args.warmup, stream)
+                rows.append([eb, fop, gop, nb / size, rate(nb, ms), e])
+        return {"cols": ["eb_rel", "f", "g", "ratio", "GBps", "err_over_tau"], "rows": rows}
 
-            ms = time_replays(gstep, flush, 5, args.warmup, stream)
-            g_bytes, r_bytes = component_bytes(out[:208].cpu().numpy())
-            comp = {"grid_component_ratio": pl.n_grid * 8 / max(g_bytes, 1),
-                    "residual_component_ratio": x.numel() * 8 / max(r_bytes, 1)}
-            return x.numel() * 8 / size, ms, comp
-
-        for fop, gop in (("barycentric", "multilinear"), ("cluster", "nearest")):
-            prm = mcc.params_default(dtype=mcc.F64, eb=1e-4, grid_fraction=0.5, f_op=fop, g_op=gop)
-            ratio, ms, comp = measure(plan, prm, f"{fop}, {gop}")
-            row = {"k_pct": k, "grid": list(n), "grid_init_s": t_init, "f": fop, "g": gop,
-                   "compression_ratio": ratio, "ms_per_step": ms,
-                   "GBps": x.numel() * 8 / (ms * 1e-3) / 1e9, **comp}
-            try:  # the same on the planes Grid_Coarsen keeps (recorded, never fatal here)
-                keep = mcc.grid_coarsen(plan, gop)
-                kplan = mcc.plan_create(cd, ed, n, lo, hi, keep=keep)
-                ratio_k, ms_k, _ = measure(kplan, prm, f"{fop}, {gop}, coarsened")
-                kplan.close()
-                row.update({"coarsened_grid": [int(v.size) for v in keep],
-                            "coarsened_compression_ratio": ratio_k, "coarsened_ms_per_step": ms_k,
-                            "coarsened_GBps": x.numel() * 8 / (ms_k * 1e-3) / 1e9})
-            except (Exception, SystemExit) as err:
-                row["coarsened_error"] = str(err)
+    def zero_run():
+        rows = []
+        for eb in (1e-6, 1e-4, 1e-3, 1e-2, 1e-1):
+            row = [eb]
+            for zr in (0, 1):
+                f = Field(mcc, plan, x, mcc.params_default(dtype=mcc.F64, eb=eb,
+                                                           grid_fraction=0.5, zero_run=zr))
+                size, _ = f.check(eb, f"zero_run {zr} {eb}")
+                ms = time_replays(f.step, flush, 5, args.warmup, stream)
+                row += [nb / size, rate(nb, ms)]
             rows.append(row)
-        plan.close()
-    return {"workload": wl["name"] + ", grid from Grid_Init (gmax 4096, delta 1)", "rows": rows}
+        return {"cols": ["eb_rel", "plain_ratio", "plain_GBps", "zr_ratio", "zr_GBps"],
+                "rows": rows}
+
+    def default_1d():
+        rows = []
+        lo_c, span_c = coords.min(axis=0), np.maximum(np.ptp(coords, axis=0), 1e-300)
+        kk = np.minimum(((coords - lo_c) / span_c * 65535.0).astype(np.int64), 65535)
+        morton = np.argsort(synth._morton2(kk[:, 0], kk[:, 1]), kind="stable")
+        for oname, perm in (("storage", None), ("morton", morton)):
+            xo = x if perm is None else x[torch.from_numpy(morton).to(dev)].contiguous()
+            for eb in (1e-6, 1e-4, 1e-2):
+                prm = mcc.params_default(dtype=mcc.F64, eb=eb)
+                s1 = mcc.compress_1d(xo, prm)
+                y1 = torch.empty_like(xo)
+                mcc.decompress_1d(s1, y1)
+                tau = eb * float(xo.max() - xo.min())
+                if not float((y1 - xo).abs().max()) <= tau:
+                    raise RuntimeError(f"1D coder: bound violated ({oname}, {eb})")
+                ws1c, ws1d = mcc.workspace_size_1d(xo.numel(), prm)
+                w1c = torch.empty(ws1c, dtype=torch.uint8, device=dev)
+                w1d = torch.empty(ws1d, dtype=torch.uint8, device=dev)
+                o1 = torch.empty(mcc.compress_bound_1d(xo.numel(), prm), dtype=torch.uint8,
+                                 device=dev)
+
+                def step1(prm=prm, xo=xo, y1=y1, w1c=w1c, w1d=w1d, o1=o1):
+                    mcc.compress_1d_into(xo, prm, w1c, o1, sync=False)
+                    mcc.decompress_1d_into(o1, o1.numel(), y1, w1d, sync=False)
+
+                ms = time_replays(step1, flush, 5, args.warmup, stream)
+                r1 = nb / s1.numel()
+                rows.append([oname, eb, r1, rate(nb, ms), ratios.get(eb), ratios.get(eb, 0) / r1])
+        return {"cols": ["order", "eb_rel", "ratio", "GBps", "method_ratio", "improvement"],
+                "rows": rows}
+
+    def grid_init():
+        rows = []
+        for k in (30.0, 50.0, 70.0, 90.0, 99.0):
+            t0 = time.perf_counter()
+            gn, lo, hi = mcc.grid_init(cd, ed, k, 1.0, 4096)
+            t_init = time.perf_counter() - t0
+            gplan = mcc.plan_create(cd, ed, gn, lo, hi)
+            for fop, gop in (("barycentric", "multilinear"), ("cluster", "nearest")):
+                prm = mcc.params_default(dtype=mcc.F64, eb=1e-4, grid_fraction=0.5, f_op=fop,
+                                         g_op=gop)
+                f = Field(mcc, gplan, x, prm)
+                size, _ = f.check(1e-4, f"grid_init {k} {fop}")
+                ms = time_replays(f.step, flush, 5, args.warmup, stream)
+                g_bytes, r_bytes = component_bytes(f.out[:208].cpu().numpy())
+                row = [k, list(gn), t_init, fop, gop, nb / size, rate(nb, ms),
+                       gplan.n_grid * 8 / max(g_bytes, 1), nb / max(r_bytes, 1)]
+                try:  # the same on the planes Grid_Coarsen keeps
+                    keep = mcc.grid_coarsen(gplan, gop)
+                    kplan = mcc.plan_create(cd, ed, gn, lo, hi, keep=keep)
+                    fk = Field(mcc, kplan, x, prm)
+                    size_k, _ = fk.check(1e-4, f"grid_init {k} {fop} coarsened")
+                    ms_k = time_replays(fk.step, flush, 5, args.warmup, stream)
+                    row += [[int(v.size) for v in keep], nb / size_k, rate(nb, ms_k)]
+                    del fk
+                    kplan.close()
+                except Exception as err:  # noqa: BLE001
+                    row += [str(err), None, None]
+                rows.append(row)
+                del f
+            gplan.close()
+        return {"cols": ["k_pct", "grid", "grid_init_s", "f", "g", "ratio", "GBps",
+                         "grid_component_ratio", "residual_component_ratio", "coarsened_grid",
+                         "coarsened_ratio", "coarsened_GBps"], "rows": rows}
+
+    sides.run("c2_main", main_rows)
+    sides.run("c2_operators", operators)
+    sides.run("c2_zero_run", zero_run)
+    sides.run("c2_default_1d", default_1d)
+    if not args.no_grid_init:
+        sides.run("c2_grid_init", grid_init)
+    plan.close()
 
 
-def batched_c4_line(args, dev, flush, stream):
+def side_c4(mcc, dev, flush, stream, args):
     """Many variables x timesteps on one mesh: 1M-vertex 2D mesh, 4 variables
     x 64 timesteps of advected Gaussian bumps (FP64), per-variable rel bounds
     1e-6, 1e-4, 1e-3, 1e-2; R and C per variable from the autotuner; every
     variable's 64 fields in one batched compress + decompress chain, all four
     in one CUDA graph; against the same fields one call at a time."""
     import torch
-    import paper_2501_06910_gb300 as mcc
     from paper_2501_06910_gb300 import autotune
     from synth import torchgen
     coords, cells = synth.mesh2d_jittered(nside=1000, seed=41)
@@ -430,11 +793,10 @@ def batched_c4_line(args, dev, flush, stream):
     for v, t, f in torchgen.fields_advected(cd, nvars=nvars, nsteps=nsteps, seed=8):
         fields[v][t] = f
     n = coords.shape[0]
-    tuned, tables, prms = [], [], []
+    tuned, prms = [], []
     for v in range(nvars):
-        best, table = autotune.tune(plan, fields[v][0], dict(dtype=mcc.F64, eb=ebs[v]))
+        best, _ = autotune.tune(plan, fields[v][0], dict(dtype=mcc.F64, eb=ebs[v]))
         tuned.append(best)
-        tables.append(table)
         prms.append(mcc.params_default(**best))
     slots, outs, wscs, wsds, ys = [], [], [], [], []
     for v in range(nvars):
@@ -452,7 +814,7 @@ def batched_c4_line(args, dev, flush, stream):
         for t in (0, nsteps - 1):
             x = fields[v][t]
             if not float((ys[v][t] - x).abs().max()) <= ebs[v] * float(x.max() - x.min()):
-                raise SystemExit("batched c4 line: bound violated")
+                raise RuntimeError("batched c4 line: bound violated")
         sizes.append(sz)
 
     def bstep():
@@ -464,8 +826,6 @@ def batched_c4_line(args, dev, flush, stream):
 
     reps = max(3, args.steps // 10)
     bms = time_replays(bstep, flush, reps, args.warmup, stream)
-    # the same 256 fields one call at a time (the plain form), one graph
-    cws1, dws1 = mcc.workspace_size(plan, prms[0])
     ws1c = torch.empty(max(mcc.workspace_size(plan, p)[0] for p in prms), dtype=torch.uint8,
                        device=dev)
     ws1d = torch.empty(max(mcc.workspace_size(plan, p)[1] for p in prms), dtype=torch.uint8,
@@ -481,45 +841,77 @@ def batched_c4_line(args, dev, flush, stream):
     sms = time_replays(sstep, flush, reps, args.warmup, stream)
     total = nvars * nsteps * n * 8
     res = {"workload": "2d-jittered-1M-grid1024^2, 4 vars x 64 steps advected bumps FP64, "
-                       "rel bounds 1e-6/1e-4/1e-3/1e-2",
-           "fields": nvars * nsteps, "input_bytes": total,
-           "ms_per_step": bms, "GBps": total / (bms * 1e-3) / 1e9,
-           "one_call_per_field": {"ms_per_step": sms, "GBps": total / (sms * 1e-3) / 1e9},
-           "per_var": [{"eb_rel": ebs[v], "R": tuned[v]["R1"], "C": tuned[v]["C1"],
-                        "compression_ratio": nsteps * n * 8 / sum(sizes[v]),
-                        "autotune": [list(r) for r in tables[v]]} for v in range(nvars)]}
+                       "rel 1e-6/1e-4/1e-3/1e-2",
+           "fields": nvars * nsteps, "ms_per_step": bms, "GBps": rate(total, bms),
+           "one_call_per_field_GBps": rate(total, sms),
+           "per_var": [[ebs[v], tuned[v]["R1"], tuned[v]["C1"], nsteps * n * 8 / sum(sizes[v])]
+                       for v in range(nvars)], "per_var_cols": ["eb_rel", "R", "C", "ratio"]}
     plan.close()
     return res
+
+
+def measure_e2e(mcc, F, x_host, flush, steps, warmup, world):
+    """End to end through the API with host buffers (pinned): every step
+    copies the field in, compresses (the call returns the stream size to the
+    host), copies the stream out and back in, decompresses and copies the
+    values out. Returns (ms per step, h2d bytes, d2h bytes)."""
+    import torch
+    out_host = torch.empty(F.cap, dtype=torch.uint8).pin_memory()
+    y_host = torch.empty_like(x_host).pin_memory()
+    x_dev = torch.empty_like(F.x)
+    in_dev = torch.empty_like(F.out)
+    ms, h2d, d2h = [], 0, 0
+    for k in range(warmup + steps):
+        if k == warmup:
+            torch.cuda.synchronize()
+            barrier(world)
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x_dev.copy_(x_host, non_blocking=True)
+        n_out = mcc.compress(F.plan, x_dev, F.prm, F.wsc, F.out, sync=True)
+        out_host[:n_out].copy_(F.out[:n_out])
+        in_dev[:n_out].copy_(out_host[:n_out], non_blocking=True)
+        mcc.decompress(F.plan, in_dev, n_out, F.y, F.wsd, sync=False)
+        y_host.copy_(F.y)
+        torch.cuda.synchronize()
+        if k >= warmup:
+            ms.append((time.perf_counter() - t0) * 1e3)
+        h2d = x_host.numel() * x_host.element_size() + n_out
+        d2h = n_out + y_host.numel() * y_host.element_size()
+    barrier(world)
+    if not torch.equal(y_host, F.y.cpu()):
+        raise SystemExit("e2e mismatch")
+    return statistics.mean(ms), h2d, d2h
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mcc", choices=["mcc", "reference"])
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--eb", type=float, default=1e-4)
-    ap.add_argument("--zero-run", action="store_true",
-                    help="main line with the zero-run stage (the other lines as they are)")
+    ap.add_argument("--zero-run", action="store_true", help="headline with the zero-run stage")
+    ap.add_argument("--side", default="all",
+                    help="comma list of side lines (bounds,batched,split,learned,c2,c4), "
+                         "'all' or 'none'")
+    ap.add_argument("--side-out", default=None, help="also write the side lines to this file")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernel-times", action="store_true")
-    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-grid-init", action="store_true")
     ap.add_argument("--preroll", type=float, default=0.5, help="seconds of untimed steps")
     ap.add_argument("--batch", type=int, default=16, help="fields per step of the batched line")
-    ap.add_argument("--no-learned", action="store_true", help="skip the learned-predictor line")
-    ap.add_argument("--no-c4", action="store_true", help="skip the variables x timesteps line")
-    ap.add_argument("--no-grid-init", action="store_true", help="skip the Grid_Init line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    wl = load_workload(args.config)
     if args.impl == "reference":
-        return run_reference(args, wl)
+        return run_reference(args)
 
     import torch
     import torch.distributed as dist
@@ -529,61 +921,44 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    plan = mcc.plan_create(torch.from_numpy(wl["coords"]).to(dev),
-                           torch.from_numpy(wl["cells"]).to(dev), wl["n"])
-    x_np = wl["x"]
-    x = torch.from_numpy(x_np).to(dev)
+    coords, cells, n = load_mesh(args.config)
+    n_cells = int(cells.shape[0])
+    cd = torch.from_numpy(coords).to(dev)
+    ed = torch.from_numpy(cells).to(dev)
+    del cells
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = mcc.plan_create(cd, ed, n)
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t0
+    del ed
+    x = field_on_device(args.config, coords, cd)
     prm = mcc.params_default(dtype=mcc.F64, eb=args.eb, grid_fraction=0.5,
                              zero_run=1 if args.zero_run else 0)
-    wsc = plan.workspace(prm, "compress")
-    wsd = plan.workspace(prm, "decompress")
-    cap = mcc.compress_bound(plan, prm)
-    out = torch.zeros(cap, dtype=torch.uint8, device=dev)
-    y = torch.empty_like(x)
+    F = Field(mcc, plan, x, prm)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-
-    def step():
-        mcc.compress(plan, x, prm, wsc, out, sync=False)
-        mcc.decompress(plan, out, cap, y, wsd, sync=False)
-
     for _ in range(args.warmup):
         flush.fill_(1)
-        step()
-    st, size = mcc.workspace_result(wsc)
-    st2, _ = mcc.workspace_result(wsd)
+        F.step()
+    st, _ = mcc.workspace_result(F.wsc)
+    st2, _ = mcc.workspace_result(F.wsd)
     if st != 0 or st2 != 0:
         raise SystemExit(f"device status {st}/{st2}")
-    # the main line's bitstream sizes (words) for the algorithmic bytes; the
-    # other lines below reuse `out`
-    hdr = out[:192].cpu().numpy()
-    W1 = int(hdr[168:176].view(np.uint64)[0])
-    W2 = int(hdr[176:184].view(np.uint64)[0])
-    tau = args.eb * (float(x.max()) - float(x.min()))
-    err = float((y - x).abs().max())
-    if not err <= tau:
-        raise SystemExit(f"bound violated: {err} > {tau}")
+    size, err_over_tau = F.check(args.eb, "headline")
+    y_ref = F.y.clone()
 
-    graph = None
-    if not args.no_graph:
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            step()
-        torch.cuda.synchronize()
-
-    def run_step():
-        if graph is not None:
-            graph.replay()
-        else:
-            step()
-
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        F.step()
+    torch.cuda.synchronize()
     for _ in range(args.warmup):
         flush.fill_(1)
-        run_step()
-    y.zero_()
-    run_step()
+        graph.replay()
+    F.y.zero_()
+    graph.replay()
     torch.cuda.synchronize()
-    if float((y - x).abs().max()) != err:
+    if not torch.equal(F.y, y_ref):
         raise SystemExit("graph replay differs from the eager step")
 
     # timed region: K steps, each bracketed by events, L2 flushed before each
@@ -593,306 +968,73 @@ def main():
         t_end = time.perf_counter() + args.preroll
         while time.perf_counter() < t_end:  # pre-roll under the same load
             flush.fill_(3)
-            run_step()
+            graph.replay()
             torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        barrier(world)
         torch.cuda.synchronize()
         for k in range(args.steps):
             flush.fill_(k & 0xFF)
             starts[k].record(stream)
-            run_step()
+            graph.replay()
             ends[k].record(stream)
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        barrier(world)
     ms = max_over_ranks(statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends)), world, dev)
     clocks = clk.summary()
+    del graph
 
-    # per-kernel device times: the same step captured with an event pair
-    # around every kernel, replayed K times (L2 flushed before each)
-    prof = {}
-    if not args.no_kernel_times:
-        mcc.profile_reset()
-        mcc.profile_enable(True)
-        pgraph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(pgraph):
-            step()
-        mcc.profile_enable(False)
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            pgraph.replay()
-            torch.cuda.synchronize()
-            for name, (t, n) in mcc.profile_read().items():
-                a = prof.setdefault(name, [0.0, 0])
-                a[0] += t
-                a[1] += n
-        mcc.profile_reset()
-    launches_per_step = (sum(n for _, n in prof.values()) / args.steps) if prof else None
+    prof = {} if args.no_kernel_times else kernel_times(mcc, F.step, flush, args.steps)
 
-    # batched: B fields of the same workload per step through mcc_compress_batch
-    # and mcc_decompress_batch (one graph; plan shared; L2 flushed per step)
-    batched = None
-    if args.batch > 1:
-        B = args.batch
-        xs = [x.clone() for _ in range(B)]
-        ys = [torch.empty_like(x) for _ in range(B)]
-        prms = [mcc.params_default(dtype=mcc.F64, eb=args.eb, grid_fraction=0.5) for _ in range(B)]
-        slot = (cap + 7) // 8 * 8
-        bout = torch.zeros(slot * B, dtype=torch.uint8, device=dev)
-        cws, dws = mcc.workspace_size(plan, prm)
-        chain = min(B, 64)
-        bwsc = torch.empty(cws * chain, dtype=torch.uint8, device=dev)
-        bwsd = torch.empty(dws * chain, dtype=torch.uint8, device=dev)
-
-        def bstep():
-            mcc.compress_batch(plan, xs, prms, bwsc, bout, slot, sync=False)
-            mcc.decompress_batch(plan, bout, slot, [slot] * B, ys, bwsd, sync=False)
-
-        bstep()
-        sizes = mcc.compress_batch(plan, xs, prms, bwsc, bout, slot, sync=True)
-        mcc.decompress_batch(plan, bout, slot, sizes, ys, bwsd, sync=True)
-        if any(not torch.equal(ys[f], y) for f in range(B)):
-            raise SystemExit("batched result differs from the single-field result")
-        bgraph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(bgraph):
-            bstep()
-        for _ in range(args.warmup):
-            flush.fill_(1)
-            bgraph.replay()
-        bs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        be = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            bs[k].record(stream)
-            bgraph.replay()
-            be[k].record(stream)
-        torch.cuda.synchronize()
-        bms = max_over_ranks(statistics.mean(s.elapsed_time(e) for s, e in zip(bs, be)), world, dev)
-        batched = {"fields_per_step": B, "ms_per_step": bms,
-                   "value": job_value(world, B * x_np.nbytes, bms), "unit": "GB/s",
-                   "compression_ratio": x_np.nbytes / sizes[0]}
-        del bgraph, bout, bwsc, bwsd, xs, ys
-
-    # end to end through the API with host buffers (pinned)
     e2e = None
-    h2d = d2h = 0
     if not args.no_e2e:
-        x_host = torch.from_numpy(x_np).pin_memory()
-        out_host = torch.empty(cap, dtype=torch.uint8).pin_memory()
-        y_host = torch.empty_like(x_host).pin_memory()
-        x_dev = torch.empty_like(x)
-        in_dev = torch.empty_like(out)
-        e2e_ms = []
-        for k in range(args.warmup + args.steps):
-            flush.fill_(k & 0xFF)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            x_dev.copy_(x_host, non_blocking=True)
-            n_out = mcc.compress(plan, x_dev, prm, wsc, out, sync=True)
-            out_host[:n_out].copy_(out[:n_out])
-            in_dev[:n_out].copy_(out_host[:n_out], non_blocking=True)
-            mcc.decompress(plan, in_dev, n_out, y, wsd, sync=False)
-            y_host.copy_(y)
-            torch.cuda.synchronize()
-            if k >= args.warmup:
-                e2e_ms.append((time.perf_counter() - t0) * 1e3)
-            h2d, d2h = x_np.nbytes + n_out, n_out + x_np.nbytes
-        if not torch.equal(y_host, y.cpu()):
-            raise SystemExit("e2e mismatch")
-        e2e = max_over_ranks(statistics.mean(e2e_ms), world, dev)
+        x_host = x.cpu().pin_memory()
+        e_ms, h2d, d2h = measure_e2e(mcc, F, x_host, flush, args.steps, args.warmup, world)
+        e_ms = max_over_ranks(e_ms, world, dev)
+        e2e = {"value": job_value(world, x.numel() * 8, e_ms), "unit": "GB/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e_ms,
+               "how": "pinned host field in, stream out and back, values out; C-ABI calls"}
 
-    # the other bounds of the 2D graded configuration (1e-6, 1e-2): ratio and
-    # compress+decompress time of the same field
-    bounds = {}
-    for eb in (1e-6, 1e-2):
-        prm_b = mcc.params_default(dtype=mcc.F64, eb=eb, grid_fraction=0.5)
-        size_b = mcc.compress(plan, x, prm_b, wsc, out)
-        mcc.decompress(plan, out, size_b, y, wsd)
-        tau_b = eb * (float(x.max()) - float(x.min()))
-        if not float((y - x).abs().max()) <= tau_b:
-            raise SystemExit(f"bound violated at eb {eb}")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.config, args.eb)
 
-        def bstep_b(prm_b=prm_b):
-            mcc.compress(plan, x, prm_b, wsc, out, sync=False)
-            mcc.decompress(plan, out, cap, y, wsd, sync=False)
+    sides = Sides(args.side_out)
+    want = set() if args.side == "none" or world > 1 else (
+        {"bounds", "batched", "split", "learned", "c2", "c4"} if args.side == "all"
+        else set(args.side.split(",")))
+    if "bounds" in want:
+        sides.run("bounds", side_bounds, mcc, plan, x, flush, stream, args)
+    if "batched" in want and args.batch > 1:
+        sides.run("batched", side_batched, mcc, plan, x, flush, stream, args, world)
+    if args.config == "c3":
+        if "split" in want:
+            sides.run("split_sweep_c3", side_split, mcc, plan, cd, flush, stream, args)
+        if "learned" in want:
+            sides.run("learned_c5", side_learned, mcc, plan, cd, flush, stream, args)
+    del F
+    plan.close()
+    torch.cuda.empty_cache()
+    if "c2" in want and args.config != "c2":
+        side_c2(mcc, dev, flush, stream, args, sides)
+    if "c4" in want:
+        sides.run("c4_vars_x_steps", side_c4, mcc, dev, flush, stream, args)
+    sides.write()
 
-        ms_b = time_replays(bstep_b, flush, max(5, args.steps // 4), args.warmup, stream)
-        bounds[str(eb)] = {"compression_ratio": x_np.nbytes / size_b, "ms_per_step": ms_b,
-                           "GBps": x_np.nbytes / (ms_b * 1e-3) / 1e9}
-
-    # the operators (Sec. III-B, III-C) on the same field: barycentric or
-    # cluster-mean f, bi/trilinear or nearest-node g, at the three bounds
-    operators = []
-    for eb in (1e-6, 1e-4, 1e-2):
-        for fop, gop in (("barycentric", "multilinear"), ("barycentric", "nearest"),
-                         ("cluster", "multilinear"), ("cluster", "nearest")):
-            prm_o = mcc.params_default(dtype=mcc.F64, eb=eb, grid_fraction=0.5, f_op=fop,
-                                       g_op=gop)
-            size_o = mcc.compress(plan, x, prm_o, wsc, out)
-            mcc.decompress(plan, out, size_o, y, wsd)
-            tau_o = eb * (float(x.max()) - float(x.min()))
-            err_o = float((y - x).abs().max())
-            if not err_o <= tau_o:
-                raise SystemExit(f"bound violated ({fop}, {gop}, {eb})")
-
-            def ostep(prm_o=prm_o):
-                mcc.compress(plan, x, prm_o, wsc, out, sync=False)
-                mcc.decompress(plan, out, cap, y, wsd, sync=False)
-
-            ms_o = time_replays(ostep, flush, max(5, args.steps // 4), args.warmup, stream)
-            operators.append({"eb_rel": eb, "f": fop, "g": gop,
-                              "compression_ratio": x_np.nbytes / size_o, "ms_per_step": ms_o,
-                              "GBps": x_np.nbytes / (ms_o * 1e-3) / 1e9,
-                              "max_abs_err_over_tau": err_o / tau_o})
-
-    # the zero-run stage (runs of zero symbols as digit tokens before the
-    # Huffman coder) against the plain coder on the same field, from tight
-    # bounds (short runs) to loose ones (long runs)
-    zero_run = []
-    for eb in (1e-6, 1e-4, 1e-3, 1e-2, 1e-1):
-        row = {"eb_rel": eb}
-        for zr in (0, 1):
-            prm_z = mcc.params_default(dtype=mcc.F64, eb=eb, grid_fraction=0.5, zero_run=zr)
-            size_z = mcc.compress(plan, x, prm_z, wsc, out)
-            mcc.decompress(plan, out, size_z, y, wsd)
-            tau_z = eb * (float(x.max()) - float(x.min()))
-            if not float((y - x).abs().max()) <= tau_z:
-                raise SystemExit(f"bound violated (zero_run {zr}, {eb})")
-
-            def zstep(prm_z=prm_z):
-                mcc.compress(plan, x, prm_z, wsc, out, sync=False)
-                mcc.decompress(plan, out, cap, y, wsd, sync=False)
-
-            ms_z = time_replays(zstep, flush, max(5, args.steps // 4), args.warmup, stream)
-            key = "zero_run" if zr else "plain"
-            row[key] = {"compression_ratio": x_np.nbytes / size_z, "ms_per_step": ms_z,
-                        "GBps": x_np.nbytes / (ms_z * 1e-3) / 1e9}
-        zero_run.append(row)
-
-    # the paper's default baseline (Sec. V): the same coder on the vertex
-    # array in 1D, in storage order (shuffled ids) and in Morton order of the
-    # vertex positions (a file with spatial locality); the improvement is the
-    # method's ratio over it at the same bound
-    default_1d = []
-    orders = [("storage", None)]
-    if len(wl["n"]) == 2:
-        cxy = wl["coords"]
-        lo_c, span_c = cxy.min(axis=0), np.maximum(np.ptp(cxy, axis=0), 1e-300)
-        kk = np.minimum(((cxy - lo_c) / span_c * 65535.0).astype(np.int64), 65535)
-        orders.append(("morton", np.argsort(synth._morton2(kk[:, 0], kk[:, 1]), kind="stable")))
-    mc_ratio = {1e-6: bounds["1e-06"]["compression_ratio"], 1e-4: x_np.nbytes / size,
-                1e-2: bounds["0.01"]["compression_ratio"]}
-    for oname, perm in orders:
-        xo_d = x if perm is None else torch.from_numpy(np.ascontiguousarray(x_np[perm])).to(dev)
-        for eb in (1e-6, 1e-4, 1e-2):
-            prm_1 = mcc.params_default(dtype=mcc.F64, eb=eb)
-            s1 = mcc.compress_1d(xo_d, prm_1)
-            y1 = torch.empty_like(xo_d)
-            mcc.decompress_1d(s1, y1)
-            tau_1 = eb * (float(xo_d.max()) - float(xo_d.min()))
-            if not float((y1 - xo_d).abs().max()) <= tau_1:
-                raise SystemExit(f"1D coder: bound violated ({oname}, {eb})")
-            ws1c, ws1d = mcc.workspace_size_1d(xo_d.numel(), prm_1)
-            w1c = torch.empty(ws1c, dtype=torch.uint8, device=dev)
-            w1d = torch.empty(ws1d, dtype=torch.uint8, device=dev)
-            o1 = torch.empty(mcc.compress_bound_1d(xo_d.numel(), prm_1), dtype=torch.uint8, device=dev)
-
-            def step1(prm_1=prm_1, xo_d=xo_d, y1=y1, w1c=w1c, w1d=w1d, o1=o1):
-                mcc.compress_1d_into(xo_d, prm_1, w1c, o1, sync=False)
-                mcc.decompress_1d_into(o1, o1.numel(), y1, w1d, sync=False)
-
-            ms_1 = time_replays(step1, flush, max(5, args.steps // 4), args.warmup, stream)
-            r1 = x_np.nbytes / s1.numel()
-            default_1d.append({"order": oname, "eb_rel": eb, "compression_ratio": r1,
-                               "ms_per_step": ms_1, "GBps": x_np.nbytes / (ms_1 * 1e-3) / 1e9,
-                               "method_ratio": mc_ratio[eb], "improvement": mc_ratio[eb] / r1})
-            del w1c, w1d, o1
-
-    grid_init = None
-    if not args.no_grid_init and len(wl["n"]) == 2:
-        grid_init = grid_init_line(args, dev, flush, stream, wl, x)
-
-    learned = batched_c4 = None
-    if not args.no_learned:
-        learned = learned_line(args, dev, flush, stream)
-    if not args.no_c4:
-        batched_c4 = batched_c4_line(args, dev, flush, stream)
-
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
-
-    nbytes = x_np.nbytes
-    alg = algorithmic_bytes(len(wl["n"]), x_np.size, int(np.prod(wl["n"])), 8, W1, W2, size)
-    per_kernel = {}
-    if prof:
-        tot = sum(t for t, _ in prof.values())
-        per_kernel = {k: {"ms_per_launch": v[0] / v[1], "launches_per_step": v[1] / args.steps,
-                          "share": v[0] / tot,
-                          "alg_GBps": alg.get(k, 0) / (v[0] / v[1] * 1e-3) / 1e9}
-                      for k, v in prof.items() if v[1]}
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    roofline = None
-    if per_kernel:
-        dom = max(per_kernel,
-                  key=lambda k: per_kernel[k]["ms_per_launch"] * per_kernel[k]["launches_per_step"])
-        achieved = alg.get(dom, 0) / (per_kernel[dom]["ms_per_launch"] * 1e-3) / 1e9
-        traffic = None
-        tfile = os.path.join(ROOT, "profiles", "dram_traffic.json")
-        if os.path.exists(tfile):  # counters count only while the kernel is unchanged
-            ent = json.load(open(tfile)).get(dom)
-            if isinstance(ent, dict):
-                src = os.path.join(ROOT, "paper_2501_06910_gb300", "csrc", ent["source"])
-                if os.path.exists(src) and \
-                        hashlib.sha1(open(src, "rb").read()).hexdigest() == ent["sha1"]:
-                    traffic = ent["bytes"]
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
-                    "peak_source": "measured" if peaks else "fallback"}
-    cpu = None if args.no_cpu_baseline else cpu_baseline(wl, args.eb)
-    line = {
-        "metric": METRIC,
-        "value": job_value(world, nbytes, ms),
-        "unit": "GB/s",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": ms,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": wl["name"], "n_vertices": int(x_np.size),
-                   "grid": list(wl["n"]), "eb_rel": args.eb, "grid_fraction": 0.5,
-                   "zero_run": bool(args.zero_run),
-                   "compression_ratio": nbytes / size, "stream_bytes": int(size),
-                   "max_abs_err_over_tau": err / tau,
-                   "l2": "flushed before every step (256 MiB write, untimed)",
-                   "cuda_graph": graph is not None, "parallelism": f"replicas x{world}"},
-        "roofline": roofline,
-        "kernels": per_kernel,
-        "cpu_baseline": cpu,
-        "e2e": None if e2e is None else {
-            "value": world * nbytes / (e2e * 1e-3) / 1e9, "unit": "GB/s",
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": None if launches_per_step is None else int(round(launches_per_step * args.steps)),
-        "other_bounds": bounds,
-        "operators": operators,
-        "zero_run": zero_run,
-        "default_1d": default_1d,
-        "grid_init": grid_init,
-        "batched": batched,
-        "learned": learned,
-        "batched_c4": batched_c4,
-        "clocks": clocks,
-    }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+        nbytes = x.numel() * 8
+        alg = algorithmic_bytes(len(n), x.numel(), int(np.prod(n)), 8, size)
+        config = {"workload": WORKLOADS[args.config], "n_vertices": int(x.numel()),
+                  "n_cells": n_cells, "grid": list(n), "eb_rel": args.eb, "grid_fraction": 0.5,
+                  "zero_run": bool(args.zero_run), "compression_ratio": nbytes / size,
+                  "stream_bytes": int(size), "max_abs_err_over_tau": err_over_tau,
+                  "plan_s": t_plan, "l2": "flushed before every step (256 MiB write, untimed)",
+                  "cuda_graph": True, "parallelism": f"replicas x{world}"}
+        line = build_headline(world=world, steps=args.steps, warmup=args.warmup, ms=ms,
+                              nbytes=nbytes, config=config, prof=prof, alg=alg, peaks=peaks,
+                              cpu=cpu, e2e=e2e, clocks=clocks, traffic=dram_traffic)
+        print(headline_json(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

@@ -28,6 +28,7 @@ __all__ = [
     "mesh2d_jittered",
     "mesh2d_graded",
     "mesh3d_annulus",
+    "mesh3d_annulus_slab",
     "mesh2d_two_triangles",
     "field_sincos",
     "field_linear",
@@ -185,6 +186,17 @@ def mesh3d_annulus(nr: int = 64, nth: int = 512, nz: int = 244, R: float = 1.0,
         tets.append(np.where(even[:, None], te, to))
     cells = np.concatenate(tets).astype(np.int32)
     return _relabel(coords, cells, rng)
+
+
+def mesh3d_annulus_slab(layers: int = 17, nz_full: int = 244, H_full: float = 2.0,
+                        seed: int = 5):
+    """The bottom ``layers`` node layers of ``mesh3d_annulus(nz=nz_full,
+    H=H_full)``: the same radial / angular resolution and the same z spacing,
+    jitter and tetrahedral split, over a height of H_full (layers - 1) /
+    (nz_full - 1). A bounded sample of the 3D workload with its structure
+    (a CPU-sized piece of the same mesh shape). Returns (coords, cells)."""
+    H = H_full * (layers - 1) / (nz_full - 1)
+    return mesh3d_annulus(nz=layers, H=H, seed=seed)
 
 
 # --------------------------------------------------------------------------- #
