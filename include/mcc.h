@@ -311,10 +311,12 @@ mcc_status mcc_decompress_1d(const void *d_in, size_t in_bytes, void *d_values, 
  * memory is a fixed array inside this library's device image of
  * mcc_static_scratch_bytes() bytes (32 MiB) per device, held by every GPU
  * that loads the library until the process exits. Plans whose decompression
- * workspace (mcc_workspace_size) exceeds it get MCC_ERR_CAPACITY. The first
- * call on a device looks up the array's device address (make that first call
- * before any stream capture). All calls on a device share the array and leave
- * its contents behind: calls whose GPU work overlaps race. */
+ * workspace (mcc_workspace_size) exceeds it get MCC_ERR_CAPACITY. Every call
+ * looks up the array's device address in the current context (so a reset
+ * device never sees a stale one); the first call on a device may load the
+ * library's device code: make it before any stream capture. All calls on a
+ * device share the array and leave its contents behind: calls whose GPU work
+ * overlaps race. */
 mcc_status mcc_decompress_static(mcc_plan plan, const void *d_in, size_t in_bytes, void *d_values,
                                  int dtype, int sync, mcc_stream stream);
 size_t mcc_static_scratch_bytes(void);

@@ -15,8 +15,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "common.cuh"
 #include "workspace.cuh"
 
@@ -25,26 +23,20 @@ using namespace mcc;
 namespace {
 
 constexpr size_t kStaticScratchBytes = (size_t)32 << 20;  // 32 MiB per device
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 
-// Device address of g_scratch per device, looked up once with that device
-// current (in host code g_scratch names a host-side stand-in, not memory the
-// GPU can use).
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
-
+// Device address of g_scratch in the current context. In host code g_scratch
+// names a host-side stand-in, not memory the GPU can use, so the address is
+// looked up with the caller's device current -- on every call, not cached: a
+// context torn down and created again (cudaDeviceReset, another primary
+// context) maps the array at a new address, and a cached one would be stale.
+// The lookup allocates nothing; the first one on a device may load the
+// library's device code.
 mcc_status scratch_address(void **out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MCC_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return MCC_ERR_CUDA;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return MCC_ERR_CUDA;
+  *out = p;
   return MCC_OK;
 }
 
