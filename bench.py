@@ -105,18 +105,39 @@ def component_bytes(header):
     return grid, residual
 
 
-def algorithmic_bytes(dim, n_v, n_g, vsz, cbytes):
+def algorithmic_bytes(dim, n_v, n_g, vsz, cbytes, c1bytes=None, launched=()):
     """HBM bytes each kernel must move at least once per LAUNCH (inputs read,
     outputs written), for a plain-predictor field. Gathers of the vertex
     codes Q (4 n_v bytes) and of the grid codes q1 (4 n_g bytes) are counted
     as cache hits (each array is read from HBM once by its streaming
-    producer or consumer). cbytes = the compressed stream."""
-    k1 = dim + 1
+    producer or consumer). cbytes = the compressed stream, c1bytes = its grid
+    component's share. Names ending in _grid / _res are the launches of one
+    component on the plan's second stream; the plain name then covers the
+    other component."""
+    c1 = cbytes // 2 if c1bytes is None else c1bytes
+    alg = {
+        "k_group_len_grid": 2 * n_g,
+        "k_runs_grid": 2 * n_g,
+        "k_codebook_grid": 0,
+        "k_dec_syms_res": (cbytes - c1) + 4 * n_v,
+        **_alg_both(dim, n_v, n_g, vsz, cbytes),
+    }
+    if "k_group_len_grid" in launched:  # the caller's stream kept the residual groups
+        alg["k_group_len"] = 2 * n_v
+        alg["k_runs"] = 2 * n_v
+        alg["k_pack"] = 2 * (n_g + n_v) + cbytes
+    if "k_dec_syms_res" in launched:  # ... and the grid component's decoding
+        alg["k_dec_syms"] = c1 + 4 * n_g
+    return alg
+
+
+def _alg_both(dim, n_v, n_g, vsz, cbytes):
     return {
         "k_reduce": vsz * n_v,                                 # x
         "k_prequant": (vsz + 4) * n_v,                         # x in, Q out
-        "k_grid2d": (4 * k1 + 2 * dim + 4 + 2) * n_g,          # ids, weights in; q1, symbols out
-        "k_grid3d": (4 * k1 + 2 * dim + 4 + 2) * n_g,
+        "k_grid2d": (16 + 4 + 2) * n_g,                        # 16-byte plan record in; q1, symbols out
+        "k_grid_codes": (16 + 8 + 4) * n_g,                    # 3D: ids, weights in; q1 out
+        "k_grid3d": (4 + 2) * n_g,                             # 3D: q1 in; symbols out
         "k_node": (4 + 2 * dim + 4 + 2) * n_v,                 # cell, local coords, Q in; symbols out
         "k_codebook": 0,
         "k_group_len": 2 * (n_g + n_v),                        # symbols in
@@ -794,8 +815,14 @@ def side_c4(mcc, dev, flush, stream, args):
         fields[v][t] = f
     n = coords.shape[0]
     tuned, prms = [], []
+    launch_table = []
     for v in range(nvars):
-        best, _ = autotune.tune(plan, fields[v][0], dict(dtype=mcc.F64, eb=ebs[v]))
+        # R and C per variable; the plan's launch configuration (shared by
+        # the variables) from the 1e-4 variable's first timestep
+        best, _ = autotune.tune(plan, fields[v][0], dict(dtype=mcc.F64, eb=ebs[v]),
+                                launch=v == 1)
+        if v == 1:
+            launch_table = autotune.tune.launch_table
         tuned.append(best)
         prms.append(mcc.params_default(**best))
     slots, outs, wscs, wsds, ys = [], [], [], [], []
@@ -824,8 +851,37 @@ def side_c4(mcc, dev, flush, stream, args):
             mcc.decompress_batch(plan, outs[v], slots[v], [slots[v]] * nsteps, ys[v], wsds[v],
                                  sync=False)
 
+    # fields per launch chain: timed on the 1e-4 variable's 64 timesteps
+    chain_table = autotune.tune_batch(plan, fields[1], [prms[1]] * nsteps, chains=(0, 8, 16, 64))
     reps = max(3, args.steps // 10)
     bms = time_replays(bstep, flush, reps, args.warmup, stream)
+    # the same step recorded by the library's own graph API (mcc_graph_*) on a
+    # second stream and replayed through mcc_graph_launch
+    gs = torch.cuda.Stream()
+    gs.wait_stream(stream)
+
+    def bstep_on(s_):
+        for v in range(nvars):
+            mcc.compress_batch(plan, fields[v], [prms[v]] * nsteps, wscs[v], outs[v], slots[v],
+                               sync=False, stream=s_)
+            mcc.decompress_batch(plan, outs[v], slots[v], [slots[v]] * nsteps, ys[v], wsds[v],
+                                 sync=False, stream=s_)
+
+    graph = mcc.graph_capture(lambda: bstep_on(gs), gs)
+    for _ in range(args.warmup):
+        graph.launch(gs)
+    gms = []
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        gs.wait_stream(stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(gs)
+        graph.launch(gs)
+        b.record(gs)
+        b.synchronize()
+        gms.append(a.elapsed_time(b))
+    graph.close()
+    lms = statistics.mean(gms)
     ws1c = torch.empty(max(mcc.workspace_size(plan, p)[0] for p in prms), dtype=torch.uint8,
                        device=dev)
     ws1d = torch.empty(max(mcc.workspace_size(plan, p)[1] for p in prms), dtype=torch.uint8,
@@ -843,6 +899,10 @@ def side_c4(mcc, dev, flush, stream, args):
     res = {"workload": "2d-jittered-1M-grid1024^2, 4 vars x 64 steps advected bumps FP64, "
                        "rel 1e-6/1e-4/1e-3/1e-2",
            "fields": nvars * nsteps, "ms_per_step": bms, "GBps": rate(total, bms),
+           "library_graph_GBps": rate(total, lms),
+           "launch_tuning": [list(r) for r in launch_table],
+           "chain_tuning": [list(r) for r in chain_table],
+           "launch_chosen": list(mcc.get_tuning(plan)),
            "one_call_per_field_GBps": rate(total, sms),
            "per_var": [[ebs[v], tuned[v]["R1"], tuned[v]["C1"], nsteps * n * 8 / sum(sizes[v])]
                        for v in range(nvars)], "per_var_cols": ["eb_rel", "R", "C", "ratio"]}
@@ -946,6 +1006,7 @@ def main():
     if st != 0 or st2 != 0:
         raise SystemExit(f"device status {st}/{st2}")
     size, err_over_tau = F.check(args.eb, "headline")
+    g_bytes, _ = component_bytes(F.out[:208].cpu().numpy())  # the grid component's share
     y_ref = F.y.clone()
 
     graph = torch.cuda.CUDAGraph()
@@ -1024,7 +1085,7 @@ def main():
         peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
         peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
         nbytes = x.numel() * 8
-        alg = algorithmic_bytes(len(n), x.numel(), int(np.prod(n)), 8, size)
+        alg = algorithmic_bytes(len(n), x.numel(), int(np.prod(n)), 8, size, g_bytes, tuple(prof))
         config = {"workload": WORKLOADS[args.config], "n_vertices": int(x.numel()),
                   "n_cells": n_cells, "grid": list(n), "eb_rel": args.eb, "grid_fraction": 0.5,
                   "zero_run": bool(args.zero_run), "compression_ratio": nbytes / size,

@@ -213,6 +213,26 @@ mcc_status mcc_grid_init(const mcc_mesh *mesh, double k_pct, double delta_pct, i
 void mcc_plan_destroy(mcc_plan plan);
 mcc_status mcc_plan_get_info(mcc_plan plan, mcc_plan_info *info);
 
+/* Launch configuration of a plan's kernels (no counterpart in the paper;
+ * chosen by timing, see the package's autotuner): the tile of the 2D grid
+ * kernel (MCC_TILE_64x16 by default, MCC_TILE_32x32, MCC_TILE_128x8), the
+ * blocks per SM and field of the vertex-streaming kernels (quantisation,
+ * the 3D grid codes, residuals, reconstruction: 2 .. 32, 8 by default), and
+ * the fields per launch chain of the batched calls (1 .. 64; 0, the
+ * default: as many as keep their gathered codes, 4 (n_grid + n_vertices)
+ * bytes each, within half the L2 cache, at least 1; the workspace may limit
+ * it further). Streams and decoded values never depend on it. Set it between
+ * calls (it is read when a call launches); MCC_ERR_INVALID_ARG outside the
+ * ranges. */
+typedef struct {
+  int tile2d;
+  int vertex_blocks_per_sm;
+  int batch_fields;
+} mcc_tuning;
+enum { MCC_TILE_64x16 = 0, MCC_TILE_32x32 = 1, MCC_TILE_128x8 = 2 };
+mcc_status mcc_plan_set_tuning(mcc_plan plan, const mcc_tuning *tuning);
+mcc_status mcc_plan_get_tuning(mcc_plan plan, mcc_tuning *tuning);
+
 /* Copy the plan tables to caller buffers (device pointers, any may be NULL):
  * vid [(dim+1)][n_grid] int32 (vid[0][j] = -1 outside the mesh), lam
  * [dim][n_grid] u16 (weights of vertices 1..dim in 2^-15 units), cell
@@ -324,6 +344,25 @@ size_t mcc_static_scratch_bytes(void);
 /* Synchronise the stream and read the status (and, after a compression, the
  * stream size; may be NULL) that the last call recorded in the workspace. */
 mcc_status mcc_workspace_result(const void *d_workspace, mcc_stream stream, size_t *out_size);
+
+/* ---- executable graphs of asynchronous calls ----------------------------
+ * No counterpart in the paper: the batching of many variables and timesteps
+ * on one plan (each a fixed sequence of launches) replayed as one CUDA graph.
+ * mcc_graph_begin starts recording the calls made on a NON-default stream
+ * (captured in this thread only); every call in between must be
+ * asynchronous (sync = 0, out_sizes = NULL; a synchronising call invalidates
+ * the recording and mcc_graph_end returns MCC_ERR_CUDA). mcc_graph_end
+ * instantiates the recorded work into *out (owned by the caller, released
+ * with mcc_graph_destroy); mcc_graph_launch replays it on a stream, with the
+ * same device pointers, parameters and workspaces as recorded. Make one
+ * uncaptured call of each kind first (the library sets kernel attributes on
+ * first use). Errors: MCC_ERR_INVALID_ARG for the default stream, a nested
+ * begin or an end without a begin; MCC_ERR_CUDA from the CUDA runtime. */
+typedef struct mcc_graph_s *mcc_graph;
+mcc_status mcc_graph_begin(mcc_stream stream);
+mcc_status mcc_graph_end(mcc_stream stream, mcc_graph *out);
+mcc_status mcc_graph_launch(mcc_graph graph, mcc_stream stream);
+void mcc_graph_destroy(mcc_graph graph);
 
 const char *mcc_status_string(mcc_status s);
 

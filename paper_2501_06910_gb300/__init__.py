@@ -79,6 +79,13 @@ class TrainCfg(C.Structure):
                 ("samples_per_field", C.c_int64), ("seed", C.c_uint64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("tile2d", C.c_int), ("vertex_blocks_per_sm", C.c_int), ("batch_fields", C.c_int)]
+
+
+TILE_64x16, TILE_32x32, TILE_128x8 = 0, 1, 2
+
+
 class _PlanInfo(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int32 * 3), ("lo", C.c_double * 3),
                 ("h", C.c_double * 3), ("n_vertices", C.c_int64), ("n_grid", C.c_int64),
@@ -127,6 +134,18 @@ def load():
             lib.mcc_compress_batch.restype = C.c_int
             lib.mcc_decompress_static.argtypes = [P, P, S, P, C.c_int, C.c_int, P]
             lib.mcc_decompress_static.restype = C.c_int
+            lib.mcc_plan_set_tuning.argtypes = [P, C.POINTER(Tuning)]
+            lib.mcc_plan_set_tuning.restype = C.c_int
+            lib.mcc_plan_get_tuning.argtypes = [P, C.POINTER(Tuning)]
+            lib.mcc_plan_get_tuning.restype = C.c_int
+            lib.mcc_graph_begin.argtypes = [P]
+            lib.mcc_graph_begin.restype = C.c_int
+            lib.mcc_graph_end.argtypes = [P, C.POINTER(C.c_void_p)]
+            lib.mcc_graph_end.restype = C.c_int
+            lib.mcc_graph_launch.argtypes = [P, P]
+            lib.mcc_graph_launch.restype = C.c_int
+            lib.mcc_graph_destroy.argtypes = [P]
+            lib.mcc_graph_destroy.restype = None
             lib.mcc_static_scratch_bytes.argtypes = []
             lib.mcc_static_scratch_bytes.restype = S
             lib.mcc_decompress_batch.restype = C.c_int
@@ -286,6 +305,18 @@ def plan_create(coords: torch.Tensor, cells: torch.Tensor, n, lo=None, hi=None,
     info = _PlanInfo()
     _check(load().mcc_plan_get_info(h, C.byref(info)), "plan_get_info")
     return Plan(h, info)
+
+
+def set_tuning(plan: "Plan", tile2d: int, vertex_blocks_per_sm: int, batch_fields: int = 0):
+    """mcc_plan_set_tuning: the launch configuration of the plan's kernels."""
+    t = Tuning(int(tile2d), int(vertex_blocks_per_sm), int(batch_fields))
+    _check(load().mcc_plan_set_tuning(plan.handle, C.byref(t)), "plan_set_tuning")
+
+
+def get_tuning(plan: "Plan"):
+    t = Tuning()
+    _check(load().mcc_plan_get_tuning(plan.handle, C.byref(t)), "plan_get_tuning")
+    return int(t.tile2d), int(t.vertex_blocks_per_sm), int(t.batch_fields)
 
 
 def grid_coarsen(plan: Plan, g_op="multilinear", stream=None):
@@ -457,6 +488,54 @@ def decompress_batch(plan: Plan, stream_bytes: torch.Tensor, slot_bytes: int, in
                                      dtype, _dptr(workspace), workspace.numel(), 1 if sync else 0,
                                      _stream(stream))
     _check(st, "decompress_batch")
+
+
+class Graph:
+    """An executable graph of recorded library calls (mcc_graph_*)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def launch(self, stream=None):
+        _check(load().mcc_graph_launch(self._h, _stream(stream)), "graph_launch")
+
+    def close(self):
+        if self._h:
+            load().mcc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
+
+
+def graph_begin(stream):
+    """mcc_graph_begin on ``stream`` (a torch.cuda.Stream, not the default)."""
+    _check(load().mcc_graph_begin(_stream(stream)), "graph_begin")
+
+
+def graph_end(stream) -> Graph:
+    """mcc_graph_end: the calls recorded on ``stream`` since graph_begin."""
+    h = C.c_void_p()
+    _check(load().mcc_graph_end(_stream(stream), C.byref(h)), "graph_end")
+    return Graph(h)
+
+
+def graph_capture(fn, stream) -> Graph:
+    """Record the asynchronous library calls ``fn()`` makes on ``stream``
+    (``fn`` passes ``stream`` to each call) into a Graph."""
+    graph_begin(stream)
+    try:
+        fn()
+    except BaseException:
+        try:
+            graph_end(stream)
+        except MCCError:
+            pass
+        raise
+    return graph_end(stream)
 
 
 def decompress_static(plan: Plan, stream_bytes: torch.Tensor, nbytes: int, out: torch.Tensor,

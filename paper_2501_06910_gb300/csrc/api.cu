@@ -143,6 +143,21 @@ static mcc_status read_batch_status(const unsigned char *ws0, size_t wss, int n,
   return r;
 }
 
+// Fields per batched launch chain: the plan's tuning, or as many fields as
+// keep their gathered codes (q1 and Q, 4 (n_g + n_v) bytes each) within half
+// of the L2 cache -- a chain's kernels run over all its fields at once, and
+// the vertex and grid kernels gather those codes at random places.
+static int chain_fields(const PlanView &pv) {
+  if (pv.batch_fields > 0) return pv.batch_fields;
+  int dev = 0, l2 = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0)
+    l2 = 64 << 20;
+  const int64_t per = 4 * (pv.n_g + pv.n_v);
+  const int64_t k = ((int64_t)l2 / 2) / (per > 0 ? per : 1);
+  return (int)(k < 1 ? 1 : (k > kMaxBatch ? kMaxBatch : k));
+}
+
 extern "C" mcc_status mcc_compress_batch(mcc_plan plan, int n, const void *const *d_values,
                                          const mcc_params *per_field, void *d_ws, size_t ws_bytes,
                                          void *d_out, size_t slot_bytes, size_t *out_sizes,
@@ -165,6 +180,7 @@ extern "C" mcc_status mcc_compress_batch(mcc_plan plan, int n, const void *const
   int chain = (int)(ws_bytes / wss);
   if (chain < 1) return MCC_ERR_CAPACITY;
   if (chain > kMaxBatch) chain = kMaxBatch;
+  if (chain > chain_fields(pv)) chain = chain_fields(pv);
   cudaStream_t stream = (cudaStream_t)s;
   unsigned char *out = (unsigned char *)d_out;
   for (int f0 = 0; f0 < n; f0 += chain) {
@@ -196,6 +212,7 @@ extern "C" mcc_status mcc_decompress_batch(mcc_plan plan, int n, const void *d_i
   int chain = (int)(ws_bytes / wss);
   if (chain < 1) return MCC_ERR_CAPACITY;
   if (chain > kMaxBatch) chain = kMaxBatch;
+  if (chain > chain_fields(pv)) chain = chain_fields(pv);
   cudaStream_t stream = (cudaStream_t)s;
   for (int f0 = 0; f0 < n; f0 += chain) {
     const int nf = n - f0 < chain ? n - f0 : chain;

@@ -108,10 +108,23 @@ struct PlanView {
   int dim;
   int32_t nx, ny, nz;
   int64_t n_v, n_g;
-  const int32_t *vid;   // [(dim+1)][n_g]
-  const uint16_t *lam;  // [dim][n_g]
+  // per grid point one 16-byte record of vertex ids (x, y, z(, w): vertices
+  // 0..dim, x = -1 outside the mesh) and the u16 weights of vertices 1..dim:
+  // in 2D in the record's w (lam1 | lam2 << 16), in 3D in an 8-byte record
+  // (x, y, z; w = 0); one or two loads per point
+  const int4 *vid4;     // [n_g]
+  const ushort4 *lam4;  // [n_g], 3D only
   const uint32_t *cell; // [n_v]
   const uint16_t *frac; // [dim][n_v]
+  // the same per vertex as one record for one vector load: 2D uint2 {cell,
+  // fx | fy << 16}, 3D uint4 {cell, fx | fy << 16, fz, 0}
+  const void *vrec;     // [n_v]
+  // host side only: the plan's second stream, its fork / join events and the
+  // mutex that keeps one call's fork and join together (all NULL: one stream)
+  void *side, *ev_fork, *ev_join, *mu;
+  int tile2d;  // MCC_TILE_* of the 2D grid kernel
+  int vbps;    // blocks per SM and field of the vertex-streaming kernels (0: 8)
+  int batch_fields;  // fields per batched launch chain (0: from the L2 size)
 };
 
 // ---------------------------------------------------------------------------
@@ -193,6 +206,28 @@ __device__ __forceinline__ long long rint_ll(float t) {
   return (b >> 31) ? -r : r;
 }
 
+// rint(u) (ties to even) as a 64-bit integer for |u| < 2^62, from the bits of
+// u with integer operations: u = m 2^e with a 53-bit m; for e < 0 the bits
+// below the binary point decide the rounding (above half, or exactly half
+// with an odd integer part, rounds up). The same value as the FP64 -> int64
+// conversion, which runs at a small fraction of the integer rate on this GPU.
+__device__ __forceinline__ long long rint_ll64(double u) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+  const int e = (int)((b >> 52) & 0x7FF) - 1075;
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  unsigned long long r;
+  if (e >= 0) {
+    r = m << e;
+  } else if (e < -53) {
+    r = 0;  // |u| < 1/4 (and zero, subnormals)
+  } else {
+    const int s = -e;  // 1 .. 53
+    const unsigned long long q = m >> s, rem = m & ((1ull << s) - 1), half = 1ull << (s - 1);
+    r = q + ((rem > half || (rem == half && (q & 1))) ? 1ull : 0ull);
+  }
+  return (b >> 63) ? -(long long)r : (long long)r;
+}
+
 // round(rho * (a + acc)), rho = rq 2^-40: integer part of a*rho from the exact
 // 128-bit product, 40-bit fraction plus FP32 correction acc*rho, one fused
 // multiply-add, round to nearest even. rescale_split returns the integer part
@@ -235,6 +270,29 @@ __device__ __forceinline__ long long rescale(int a, float acc, long long rq, flo
 
 __device__ __forceinline__ int wsub(int a, int b) { return (int)((unsigned)a - (unsigned)b); }
 __device__ __forceinline__ int wadd(int a, int b) { return (int)((unsigned)a + (unsigned)b); }
+
+// A vertex's cell and local coordinates (2^-15 units, as FP32) from its record.
+template <int DIM>
+__device__ __forceinline__ void vertex_record(const void *vrec, int64_t i, uint32_t &cell,
+                                              float (&fr)[3]) {
+  unsigned int f[3];
+  if (DIM == 2) {
+    const uint2 r = __ldg((const uint2 *)vrec + i);
+    cell = r.x;
+    f[0] = r.y & 0xFFFFu;
+    f[1] = r.y >> 16;
+    f[2] = 0;
+  } else {
+    const uint4 r = __ldg((const uint4 *)vrec + i);
+    cell = r.x;
+    f[0] = r.y & 0xFFFFu;
+    f[1] = r.y >> 16;
+    f[2] = r.z;
+  }
+#pragma unroll
+  for (int d = 0; d < 3; d++)
+    fr[d] = d < DIM ? __fmul_rn(__uint2float_rn(f[d]), 0x1p-15f) : 0.0f;
+}
 
 // Grid -> vertex interpolation g (bilinear / trilinear on the grid codes of
 // the vertex's cell) as acc = g - c_000 in grid bins. corner_codes gathers the

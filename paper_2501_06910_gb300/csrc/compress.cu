@@ -22,6 +22,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 #include "predictor.cuh"
@@ -61,6 +62,10 @@ struct CompArgs {
   unsigned char zr[kMaxBatch];            // zero-run stage per field
   int any_auto, any_zr;
   int one_d;  // the 1D coder: component 1 holds the vertex codes' differences
+  // logical index of the launch's first block along x (k_runs, k_codebook,
+  // k_group_len): the grid and residual components' blocks may come in
+  // separate launches (on two streams)
+  int bx0;
 };
 
 // Per-field pointers into the workspace and the output slot.
@@ -240,25 +245,33 @@ __global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ CompArgs
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // x is read with the default caching: k_prequant reads it again from L2
   if (sizeof(T) == 8) {
-    for (; i + 7 * stride < n; i += 8 * stride) {
-      double v[8];
-#pragma unroll
-      for (int u = 0; u < 8; u++) v[u] = (double)__ldg(x + i + u * stride);
-#pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const unsigned long long b = value_bits(v[u]);
-        bad |= ((b >> 52) & 0x7FF) == 0x7FF;
-        const unsigned long long k = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-        mn = max(mn, ~k);
-        mx = max(mx, k);
-      }
-    }
-    for (; i < n; i += stride) {
-      const unsigned long long b = value_bits((double)__ldg(x + i));
+    auto key = [&](double v) {
+      const unsigned long long b = value_bits(v);
       bad |= ((b >> 52) & 0x7FF) == 0x7FF;
       const unsigned long long k = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
       mn = max(mn, ~k);
       mx = max(mx, k);
+    };
+    if (((uintptr_t)x & 15) == 0) {
+      // pairs as 16-byte loads, four pairs in flight per thread
+      const double2 *x2 = (const double2 *)x;
+      const int64_t n2 = n / 2;
+      int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+      for (; j + 3 * stride < n2; j += 4 * stride) {
+        double2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = __ldg(x2 + j + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; u++) { key(v[u].x); key(v[u].y); }
+      }
+      for (; j < n2; j += stride) {
+        const double2 v = __ldg(x2 + j);
+        key(v.x);
+        key(v.y);
+      }
+      if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) key((double)__ldg(x + n - 1));
+    } else {
+      for (; i < n; i += stride) key((double)__ldg(x + i));
     }
   } else {
     // FP32: ordered 32-bit keys (no float -> double conversion per value,
@@ -341,7 +354,7 @@ __global__ void __launch_bounds__(256) k_prequant(const __grid_constant__ CompAr
     const int64_t sxy = (int64_t)pv.nx * pv.ny;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
       const double v = (double)__ldg(x + i);
-      const int q = (int)(__double2ll_rn(__dmul_rn(v, inv2)) - K);
+      const int q = (int)(rint_ll64(__dmul_rn(v, inv2)) - K);
       Q[i] = q;
       const uint32_t c = __ldg(pv.cell + i);
       const unsigned fx = __ldg(pv.frac + i), fy = __ldg(pv.frac + n + i);
@@ -352,9 +365,21 @@ __global__ void __launch_bounds__(256) k_prequant(const __grid_constant__ CompAr
     }
     return;
   }
+  if (sizeof(T) == 8 && ((uintptr_t)x & 15) == 0) {  // pairs: 16-byte loads, 8-byte stores
+    const double2 *x2 = (const double2 *)x;
+    int2 *Q2 = (int2 *)Q;  // the workspace's Q is 256-byte aligned
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n / 2; j += stride) {
+      const double2 v = __ldg(x2 + j);
+      Q2[j] = make_int2((int)(rint_ll64(__dmul_rn(v.x, inv2)) - K),
+                        (int)(rint_ll64(__dmul_rn(v.y, inv2)) - K));
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+      Q[n - 1] = (int)(rint_ll64(__dmul_rn((double)__ldg(x + n - 1), inv2)) - K);
+    return;
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
     const double v = (double)__ldg(x + i);
-    Q[i] = (int)(__double2ll_rn(__dmul_rn(v, inv2)) - K);
+    Q[i] = (int)(rint_ll64(__dmul_rn(v, inv2)) - K);
   }
 }
 
@@ -417,11 +442,23 @@ __device__ __forceinline__ void grid_codes(const int64_t (&j)[U], const bool (&o
 #pragma unroll
   for (int u = 0; u < U; u++) {
     const int64_t jj = ok[u] ? j[u] : 0;
+    const int4 vv = __ldg(pv.vid4 + jj);
+    unsigned int lk[3];
+    if (DIM == 2) {  // the weights share the record (lam1 | lam2 << 16)
+      lk[0] = (unsigned int)vv.w & 0xFFFFu;
+      lk[1] = (unsigned int)vv.w >> 16;
+      lk[2] = 0;
+    } else {
+      const ushort4 ll = __ldg(pv.lam4 + jj);
+      lk[0] = ll.x;
+      lk[1] = ll.y;
+      lk[2] = ll.z;
+    }
+    const int vk[4] = {vv.x, vv.y, vv.z, vv.w};
 #pragma unroll
-    for (int k = 0; k <= DIM; k++) v[u][k] = __ldg(pv.vid + k * pv.n_g + jj);
+    for (int k = 0; k <= DIM; k++) v[u][k] = vk[k];
 #pragma unroll
-    for (int k = 0; k < DIM; k++)
-      lf[u][k] = __fmul_rn(__uint2float_rn(__ldg(pv.lam + k * pv.n_g + jj)), 0x1p-15f);
+    for (int k = 0; k < DIM; k++) lf[u][k] = __fmul_rn(__uint2float_rn(lk[k]), 0x1p-15f);
     if (!ok[u]) v[u][0] = -1;
   }
   int qv[U][DIM + 1];
@@ -581,17 +618,17 @@ __global__ void __launch_bounds__(256) k_grid2d(const __grid_constant__ CompArgs
     if (shist[i]) atomicAdd(hist1 + i, shist[i]);
 }
 
-// 3D: tiles of TX x TY points walking a segment of SZ planes in z; the plane
-// below the segment is recomputed as halo.
-template <int TX, int TY, int SZ>
-__global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompArgs A) {
+// 3D grid codes: f and the rescale once per grid point (U points per thread,
+// their plan records and vertex-code gathers issued together); k_grid3d then
+// takes the Lorenzo differences from q1, halo included, with no point
+// computed twice. Four resident blocks per SM (64 registers, no spills)
+// keep more gathers in flight.
+__global__ void __launch_bounds__(256, 4) k_grid_codes3d(const __grid_constant__ CompArgs A) {
   pdl_trigger();
   pdl_wait();
   const Ctx c = ctx_of(A, blockIdx.x);
   const PlanView &pv = A.pv;
-  const int *__restrict__ Q = c.Q;
   Status *st = c.st;
-  const int R1 = A.R1;
   int *__restrict__ q1 = c.q1;
   double *__restrict__ x1v =
       A.open[blockIdx.x] ? (double *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.x1v) : nullptr;
@@ -599,6 +636,39 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
   const unsigned long long *csum =
       (const unsigned long long *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.csum);
   const unsigned int *ccnt = (const unsigned int *)(A.ws0 + (int64_t)blockIdx.x * A.wss + A.W.ccnt);
+  if (block_failed(st)) return;
+  const FieldParams f = st->f;
+  constexpr int U = 4;
+  const int64_t n_g = pv.n_g;
+  const int64_t stride = (int64_t)gridDim.y * blockDim.x;
+  for (int64_t j0 = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; j0 < n_g; j0 += U * stride) {
+    int64_t j[U];
+    bool ok[U];
+    int q[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      j[u] = j0 + u * stride;
+      ok[u] = j[u] < n_g;
+    }
+    if (cluster) grid_codes_cluster<U>(j, ok, csum, ccnt, f, st, q, x1v, ok);
+    else grid_codes<3, U>(j, ok, pv, c.Q, f, st, q, x1v, ok);
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (ok[u]) q1[j[u]] = q[u];
+  }
+}
+
+// 3D: tiles of TX x TY points walking a segment of SZ planes in z; the tile
+// and its halo (the plane below, the row and column before) are read from q1.
+template <int TX, int TY, int SZ>
+__global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompArgs A) {
+  pdl_trigger();
+  pdl_wait();
+  const Ctx c = ctx_of(A, blockIdx.x);
+  const PlanView &pv = A.pv;
+  Status *st = c.st;
+  const int R1 = A.R1;
+  int *__restrict__ q1 = c.q1;
   unsigned short *__restrict__ sym1 = c.sym1;
   int *__restrict__ val1 = c.val1;
   unsigned int *hist1 = c.hist1;
@@ -609,36 +679,28 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
   if (block_failed(st)) return;
   const int nsym = 2 * R1;
   for (int i = threadIdx.x; i < nsym; i += blockDim.x) shist[i] = 0;
-  const FieldParams f = st->f;
   const int nx = pv.nx, ny = pv.ny, nz = pv.nz;
   const int x0 = (blockIdx.y % txs) * TX, y0 = (blockIdx.y / txs) * TY, z0 = blockIdx.z * SZ;
   const int64_t sxy = (int64_t)nx * ny;
   constexpr int NP = (SZ + 1) * (TY + 1) * (TX + 1), U = 4;
   constexpr int NT = TX * TY;
   for (int base = 0; base < NP; base += U * NT) {  // U points per thread at once
-    int64_t j[U];
-    bool ok[U];
     int q[U];
-    bool own[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = base + threadIdx.x + NT * u;
       const int lz = idx / ((TY + 1) * (TX + 1)), rem = idx - lz * ((TY + 1) * (TX + 1));
       const int ly = rem / (TX + 1), lx = rem - ly * (TX + 1);
       const int gx = x0 - 1 + lx, gy = y0 - 1 + ly, gz = z0 - 1 + lz;
-      ok[u] = idx < NP && gx >= 0 && gy >= 0 && gz >= 0 && gx < nx && gy < ny && gz < nz;
-      own[u] = ok[u] && lx > 0 && ly > 0 && lz > 0;
-      j[u] = gx + (int64_t)nx * gy + sxy * gz;
+      const bool ok = idx < NP && gx >= 0 && gy >= 0 && gz >= 0 && gx < nx && gy < ny && gz < nz;
+      q[u] = ok ? __ldcg(q1 + gx + (int64_t)nx * gy + sxy * gz) : 0;  // 0 outside the grid
     }
-    if (cluster) grid_codes_cluster<U>(j, ok, csum, ccnt, f, st, q, x1v, own);
-    else grid_codes<3, U>(j, ok, pv, Q, f, st, q, x1v, own);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int idx = base + threadIdx.x + NT * u;
       if (idx >= NP) continue;
       const int lz = idx / ((TY + 1) * (TX + 1)), rem = idx - lz * ((TY + 1) * (TX + 1));
       const int ly = rem / (TX + 1), lx = rem - ly * (TX + 1);
-      if (own[u]) q1[j[u]] = q[u];
       s[lz][ly][lx] = q[u];
     }
   }
@@ -878,10 +940,7 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
     for (int u = 0; u < U; u++) {
       valid[u] = iv[u] < n;
       const int64_t i = valid[u] ? iv[u] : 0;
-      cl[u] = __ldg(pv.cell + i);
-      fr[u][0] = __fmul_rn(__uint2float_rn(__ldg(pv.frac + i)), 0x1p-15f);
-      fr[u][1] = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + i)), 0x1p-15f);
-      fr[u][2] = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + i)), 0x1p-15f) : 0.0f;
+      vertex_record<DIM>(pv.vrec, i, cl[u], fr[u]);
       Qv[u] = __ldg(Q + i);
     }
 #pragma unroll
@@ -968,10 +1027,11 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
   Status *st = c.st;
   const int lmax = AA.lmax;
   if (block_failed(st)) return;
-  const bool c1 = blockIdx.x == 0;
+  const int bx = (int)blockIdx.x + AA.bx0;
+  const bool c1 = bx == 0;
   // block 2: the learned side of an auto field; with auto, k_choose writes
   // the residual code lengths into the stream
-  const bool side_b = blockIdx.x == 2;
+  const bool side_b = bx == 2;
   const bool autof = AA.mode[blockIdx.y] == MCC_PRED_AUTO;
   if (side_b && !autof) return;
   unsigned char *ws = AA.ws0 + (int64_t)blockIdx.y * AA.wss;
@@ -1296,12 +1356,13 @@ __global__ void __launch_bounds__(256) k_runs(const __grid_constant__ CompArgs A
   pdl_wait();
   const int fi = blockIdx.y;
   const int64_t ng = A.ng1 + A.ng2;
-  const bool side_b = (int64_t)blockIdx.x >= ng;
+  const int64_t bx = (int64_t)blockIdx.x + A.bx0;
+  const bool side_b = bx >= ng;
   if (!A.zr[fi] || (side_b && A.mode[fi] != MCC_PRED_AUTO)) return;  // uniform per block
   const Ctx c = ctx_of(A, fi);
   if (block_failed(c.st)) return;
   unsigned char *ws = A.ws0 + (int64_t)fi * A.wss;
-  const int64_t gi = side_b ? (int64_t)blockIdx.x - A.ng2 : blockIdx.x;  // side b: ng1 + g
+  const int64_t gi = side_b ? bx - A.ng2 : bx;  // side b: ng1 + g
   const bool c1 = gi < A.ng1;
   const int64_t g = c1 ? gi : gi - A.ng1;
   const int C = c1 ? A.C1 : A.C2, R = c1 ? A.R1 : A.R2;
@@ -1405,7 +1466,7 @@ __global__ void __launch_bounds__(256) k_group_len(const __grid_constant__ CompA
   __shared__ unsigned int sbits[kParts][32];
   __shared__ unsigned int sesc[kParts], sraw[kParts];
   if (block_failed(st)) return;
-  const int64_t gi = blockIdx.x;
+  const int64_t gi = (int64_t)blockIdx.x + A.bx0;
   const bool c1 = gi < a.ng1;
   const int64_t g = c1 ? gi : gi - a.ng1;
   const int C = c1 ? a.C1 : a.C2;
@@ -1705,8 +1766,7 @@ __global__ void __launch_bounds__(256, ZR ? 5 : 6) k_pack(const __grid_constant_
                    A.pv.n_g, A.pv.n_v, A.ng1, A.ng2, A.C1, A.C2, A.nsym1, A.nsym2,
                    A.dtype == MCC_F64 ? 8 : 4, c.out, c.pb, c.pe, c.pr};
   extern __shared__ unsigned int stage[];
-  __shared__ unsigned int scode[2 * kMaxR];
-  __shared__ unsigned char slen[2 * kMaxR];
+  __shared__ unsigned int scl[2 * kMaxR];  // code << 5 | length (codes < 2^24, lengths <= 24)
   if (block_failed(st)) return;
   const Layout L = st->L;
   const int64_t gi = blockIdx.x;
@@ -1732,10 +1792,7 @@ __global__ void __launch_bounds__(256, ZR ? 5 : 6) k_pack(const __grid_constant_
 
   const unsigned int w0 = gtab[g], nw = gtab[g + 1] - w0;
   for (unsigned int i = threadIdx.x; i < nw; i += blockDim.x) stage[i] = 0;
-  for (int i = threadIdx.x; i < nsym; i += blockDim.x) {
-    scode[i] = csrc[i];
-    slen[i] = lsrc[i];
-  }
+  for (int i = threadIdx.x; i < nsym; i += blockDim.x) scl[i] = (csrc[i] << 5) | lsrc[i];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // bit offset of (part w, lane): lanes before this one, then earlier parts
   const unsigned int lb = ((unsigned int)ltg[0] | ((unsigned int)ltg[1] << 8)) + ltg[2 + lane];
@@ -1746,10 +1803,21 @@ __global__ void __launch_bounds__(256, ZR ? 5 : 6) k_pack(const __grid_constant_
   }
   unsigned int pos = incl - lb;
   unsigned int e_run = etab[g], r_run = c1 ? 0u : rtab[g];
-  for (int q = 0; q < w; q++) {
-    pos += a.pb[(gi * kParts + q) * 32 + lane];
-    e_run += a.pe[gi * kParts + q];
-    r_run += a.pr[gi * kParts + q];
+  {  // the earlier parts' totals, their loads issued together
+    unsigned int pb[kParts - 1], pe[kParts - 1], pr[kParts - 1];
+#pragma unroll
+    for (int q = 0; q < kParts - 1; q++) {
+      const bool before = q < w;
+      pb[q] = before ? a.pb[(gi * kParts + q) * 32 + lane] : 0u;
+      pe[q] = before ? a.pe[gi * kParts + q] : 0u;
+      pr[q] = before ? a.pr[gi * kParts + q] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < kParts - 1; q++) {
+      pos += pb[q];
+      e_run += pe[q];
+      r_run += pr[q];
+    }
   }
   // zero-run stage: the runs that end at this part's first other symbol and
   // at the lane's end (from k_runs)
@@ -1764,7 +1832,8 @@ __global__ void __launch_bounds__(256, ZR ? 5 : 6) k_pack(const __grid_constant_
   const int64_t base = g * 32 * (int64_t)C + lane;
   const unsigned lt = (1u << lane) - 1;
   // a code of cl >= 1 bits at the lane's bit position
-  auto put = [&](unsigned int code, unsigned int cl) {
+  auto put = [&](unsigned int packed) {
+    const unsigned int code = packed >> 5, cl = packed & 31u;
     const unsigned long long v = ((unsigned long long)code << (64 - cl)) >> (pos & 31);
     atomicOr(stage + (pos >> 5), (unsigned int)(v >> 32));
     if ((pos & 31) + cl > 32) atomicOr(stage + (pos >> 5) + 1, (unsigned int)v);
@@ -1777,7 +1846,7 @@ __global__ void __launch_bounds__(256, ZR ? 5 : 6) k_pack(const __grid_constant_
     const unsigned int v = r + 1, nd = 31 - __clz(v);
     for (unsigned int i = 0; i < nd; i++) {
       const int t = 2 * R + (int)((v >> i) & 1u);
-      put(scode[t], slen[t]);
+      put(scl[t]);
     }
   };
   unsigned int run = 0;
@@ -1796,7 +1865,7 @@ __global__ void __launch_bounds__(256, ZR ? 5 : 6) k_pack(const __grid_constant_
           seen = true;
           run = 0;
         }
-        put(scode[sy], slen[sy]);
+        put(scl[sy]);
       }
     }
     const unsigned em = __ballot_sync(0xffffffffu, sy == 0);
@@ -1979,8 +2048,9 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
       cudaMemset2DAsync(ws0 + A.W.csum, (size_t)wss, 0, A.W.total - A.W.csum, (size_t)nf,
                         stream) != cudaSuccess)
     return MCC_ERR_CUDA;
-  const unsigned int bpf = (unsigned int)((sms * 2 + nf - 1) / nf);  // reduce blocks per field
-  const unsigned int ppf = (unsigned int)((sms * 8 + nf - 1) / nf);  // prequant / node blocks per field
+  const unsigned int bpf = (unsigned int)((sms * 4 + nf - 1) / nf);  // reduce blocks per field
+  const int vbps = pv.vbps > 0 ? pv.vbps : 8;  // the plan's tuning (8 by default)
+  const unsigned int ppf = (unsigned int)((sms * vbps + nf - 1) / nf);  // prequant / node blocks per field
   {
     PROF_SCOPE("k_reduce", stream);
     if (p->dtype == MCC_F64) k_reduce<double><<<dim3(bpf, nf), 256, 0, stream>>>(A);
@@ -1997,14 +2067,59 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     launch_pdl(k_delta1d, dim3(ppf, nf), dim3(256), hsm1, stream, A);
   } else if (pv.dim == 2) {
     PROF_SCOPE("k_grid2d", stream);
-    launch_pdl(k_grid2d<64, 16>, dim3(nf, (pv.nx + 63) / 64, (pv.ny + 15) / 16), dim3(256), hsm1,
-               stream, A);
+    // the plan's tile (tuning): 64 x 16 by default, 32 x 32 or 128 x 8
+    if (pv.tile2d == MCC_TILE_32x32)
+      launch_pdl(k_grid2d<32, 32>, dim3(nf, (pv.nx + 31) / 32, (pv.ny + 31) / 32), dim3(256), hsm1,
+                 stream, A);
+    else if (pv.tile2d == MCC_TILE_128x8)
+      launch_pdl(k_grid2d<128, 8>, dim3(nf, (pv.nx + 127) / 128, (pv.ny + 7) / 8), dim3(256), hsm1,
+                 stream, A);
+    else
+      launch_pdl(k_grid2d<64, 16>, dim3(nf, (pv.nx + 63) / 64, (pv.ny + 15) / 16), dim3(256), hsm1,
+                 stream, A);
   } else {
+    {
+      PROF_SCOPE("k_grid_codes", stream);
+      launch_pdl(k_grid_codes3d, dim3(nf, ppf < 65535 ? ppf : 65535), dim3(256), 0, stream, A);
+    }
     PROF_SCOPE("k_grid3d", stream);
     const unsigned int txy = (unsigned int)(((pv.nx + 31) / 32) * ((pv.ny + 7) / 8));
     launch_pdl(k_grid3d<32, 8, 8>, dim3(nf, txy, (pv.nz + 7) / 8), dim3(256), hsm1, stream, A);
   }
   if (front_only) return cudaGetLastError() == cudaSuccess ? MCC_OK : MCC_ERR_CUDA;
+  // Two streams from here on (Algorithm 3 codes x1' and x2 independently once
+  // q1 exists): the grid component's run tokens, code book and group lengths
+  // on the plan's second stream, beside the residual stage on the caller's;
+  // they join before the bit packing (whose layout needs both components).
+  // Single large fields only: with a batch, or a small field, the grid
+  // coder's kernels slow the residual stage they run beside by more than
+  // they hide (measured on the 2D graded and batched workloads).
+  const bool fork = pv.side != nullptr && !A.one_d && nf == 1 &&
+                    pv.n_g + pv.n_v >= ((int64_t)1 << 23);
+  std::unique_lock<std::mutex> lock;
+  const cudaStream_t side = (cudaStream_t)pv.side;
+  if (fork) {
+    lock = std::unique_lock<std::mutex>(*(std::mutex *)pv.mu);
+    if (cudaEventRecord((cudaEvent_t)pv.ev_fork, stream) != cudaSuccess ||
+        cudaStreamWaitEvent(side, (cudaEvent_t)pv.ev_fork, 0) != cudaSuccess)
+      return MCC_ERR_CUDA;
+    CompArgs G = A;
+    G.bx0 = 0;
+    if (A.any_zr) {
+      PROF_SCOPE("k_runs_grid", side);
+      launch_pdl(k_runs, dim3((unsigned int)A.ng1, nf), dim3(256), 0, side, G);
+    }
+    {
+      PROF_SCOPE("k_codebook_grid", side);
+      const size_t cbsm = codebook_smem(A.nsym1);
+      launch_pdl(k_codebook, dim3(1, nf), dim3(1024), cbsm, side, G);
+    }
+    {
+      PROF_SCOPE("k_group_len_grid", side);
+      launch_pdl(k_group_len, dim3((unsigned int)A.ng1, nf), dim3(256), 0, side, G);
+    }
+    if (cudaEventRecord((cudaEvent_t)pv.ev_join, side) != cudaSuccess) return MCC_ERR_CUDA;
+  }
   if (!A.one_d && any_model) {  // learned corrections p at every vertex of the fields with a model
     PROF_SCOPE("k_predict", stream);
     PredArgs P;
@@ -2045,15 +2160,22 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     }
 #undef MCC_NODE
   }
+  // the residual component's (or, on one stream, both components') blocks:
+  // logical block indices from R.bx0
+  CompArgs R = A;
+  R.bx0 = fork ? (int)A.ng1 : 0;
   if (A.any_zr) {
     PROF_SCOPE("k_runs", stream);
-    launch_pdl(k_runs, dim3((unsigned int)(ng + (A.any_auto ? A.ng2 : 0)), nf), dim3(256), 0,
-               stream, A);
+    const int64_t nb = (fork ? A.ng2 : ng) + (A.any_auto ? A.ng2 : 0);
+    launch_pdl(k_runs, dim3((unsigned int)nb, nf), dim3(256), 0, stream, R);
   }
   {
     PROF_SCOPE("k_codebook", stream);
     const size_t cbsm = codebook_smem(A.nsym1 > A.nsym2 ? A.nsym1 : A.nsym2);
-    launch_pdl(k_codebook, dim3(A.any_auto ? 3 : 2, nf), dim3(1024), cbsm, stream, A);
+    CompArgs Rc = A;
+    Rc.bx0 = fork ? 1 : 0;
+    const unsigned int nb = (fork ? 1 : 2) + (A.any_auto ? 1 : 0);
+    launch_pdl(k_codebook, dim3(nb, nf), dim3(1024), cbsm, stream, Rc);
   }
   if (A.any_auto) {
     PROF_SCOPE("k_choose", stream);
@@ -2061,8 +2183,10 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   }
   {
     PROF_SCOPE("k_group_len", stream);
-    launch_pdl(k_group_len, dim3((unsigned int)ng, nf), dim3(256), 0, stream, A);
+    launch_pdl(k_group_len, dim3((unsigned int)(fork ? A.ng2 : ng), nf), dim3(256), 0, stream, R);
   }
+  if (fork && cudaStreamWaitEvent(stream, (cudaEvent_t)pv.ev_join, 0) != cudaSuccess)
+    return MCC_ERR_CUDA;
   {
     PROF_SCOPE("k_pack", stream);
     const int cmax = p->C1 > p->C2 ? p->C1 : p->C2;

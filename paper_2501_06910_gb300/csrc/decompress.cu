@@ -16,6 +16,8 @@
 // Every read of the stream is bounds-checked against the validated layout; a
 // corrupt stream records MCC_ERR_CORRUPT and the affected warp stops.
 #include <cuda_runtime.h>
+
+#include <mutex>
 #include <limits.h>
 #include <stdint.h>
 #include <string.h>
@@ -902,10 +904,7 @@ __global__ void __launch_bounds__(256, U == 2 ? (DIM == 3 ? 5 : 6) : 4) k_recon(
       const int64_t p = pv2[u] < n ? pv2[u] : p0;
       q2v[u] = __ldg(q2s + p);
       go[u] = pv2[u] < n && q2v[u] != INT_MIN;  // INT_MIN: raw value already in place
-      cl[u] = __ldg(pv.cell + p);
-      fr[u][0] = __fmul_rn(__uint2float_rn(__ldg(pv.frac + p)), 0x1p-15f);
-      fr[u][1] = __fmul_rn(__uint2float_rn(__ldg(pv.frac + n + p)), 0x1p-15f);
-      fr[u][2] = DIM == 3 ? __fmul_rn(__uint2float_rn(__ldg(pv.frac + 2 * n + p)), 0x1p-15f) : 0.0f;
+      vertex_record<DIM>(pv.vrec, p, cl[u], fr[u]);
     }
 #pragma unroll
     for (int u = 0; u < U; u++) corner_codes<DIM>(q1, cl[u], nx, sxy, cor[u]);
@@ -980,19 +979,43 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
   const unsigned int cap = (unsigned int)((sms * 2 + nf - 1) / nf) + 1;
   const unsigned int nb1 = nblk(max_g1, 8) < cap ? nblk(max_g1, 8) : cap;
   const unsigned int nb2 = nblk(max_g2, 8) < cap ? nblk(max_g2, 8) : cap;
+  const size_t dsm = (size_t)8 * kDecRound * 32 * sizeof(unsigned short);  // [warps][round][32]
   {
-    PROF_SCOPE("k_dec_syms", stream);
-    const size_t sm = (size_t)8 * kDecRound * 32 * sizeof(unsigned short);  // [warps][round][32]
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(k_dec_syms<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      cudaFuncSetAttribute(k_dec_syms<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_dec_syms<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+      cudaFuncSetAttribute(k_dec_syms<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
       attr = true;
     }
+  }
+  // Two streams (Algorithm 4 decodes the components independently): the
+  // residual component's symbols on the plan's second stream, beside the
+  // grid component's decoding and prefix sums on the caller's; they join
+  // before the reconstruction, which needs both.
+  // (single fields only: in a batch every launch already fills the GPU, and
+  // the measured batched rate drops with the fork)
+  const bool fork = pv.side != nullptr && pv.dim != 1 && nf == 1;
+  std::unique_lock<std::mutex> lock;
+  const cudaStream_t side = (cudaStream_t)pv.side;
+  if (fork) {
+    lock = std::unique_lock<std::mutex>(*(std::mutex *)pv.mu);
+    if (cudaEventRecord((cudaEvent_t)pv.ev_fork, stream) != cudaSuccess ||
+        cudaStreamWaitEvent(side, (cudaEvent_t)pv.ev_fork, 0) != cudaSuccess)
+      return MCC_ERR_CUDA;
+    {
+      PROF_SCOPE("k_dec_syms_res", side);  // blocks of the residual component only (nb1 = 0)
+      if (dtype == MCC_F64) launch_pdl(k_dec_syms<double>, dim3(nb2, nf), dim3(256), dsm, side, A, 0);
+      else launch_pdl(k_dec_syms<float>, dim3(nb2, nf), dim3(256), dsm, side, A, 0);
+    }
+    if (cudaEventRecord((cudaEvent_t)pv.ev_join, side) != cudaSuccess) return MCC_ERR_CUDA;
+  }
+  {
+    PROF_SCOPE("k_dec_syms", stream);
+    const unsigned int nb = fork ? nb1 : nb1 + nb2;
     if (dtype == MCC_F64)
-      launch_pdl(k_dec_syms<double>, dim3(nb1 + nb2, nf), dim3(256), sm, stream, A, (int)nb1);
+      launch_pdl(k_dec_syms<double>, dim3(nb, nf), dim3(256), dsm, stream, A, (int)nb1);
     else
-      launch_pdl(k_dec_syms<float>, dim3(nb1 + nb2, nf), dim3(256), sm, stream, A, (int)nb1);
+      launch_pdl(k_dec_syms<float>, dim3(nb, nf), dim3(256), dsm, stream, A, (int)nb1);
   }
   if (pv.dim == 1) {  // the 1D coder
     const int64_t nchunk = (pv.n_g + kScan1dChunk - 1) / kScan1dChunk;
@@ -1056,9 +1079,12 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
     }
     launch_predict(P, stream, true);
   }
+  if (fork && cudaStreamWaitEvent(stream, (cudaEvent_t)pv.ev_join, 0) != cudaSuccess)
+    return MCC_ERR_CUDA;
   {
     PROF_SCOPE("k_recon", stream);
-    unsigned int chunks = (unsigned int)((sms * 8 + nf - 1) / nf);
+    const int vbps = pv.vbps > 0 ? pv.vbps : 8;  // the plan's tuning (8 by default)
+    unsigned int chunks = (unsigned int)((sms * vbps + nf - 1) / nf);
     if (chunks > 65535) chunks = 65535;
     if (pv.dim == 2) {
       if (dtype == MCC_F64) launch_pdl(k_recon<2, double, 4>, dim3(nf, chunks), dim3(256), 0, stream, A);

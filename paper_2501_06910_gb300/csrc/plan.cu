@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -30,10 +31,20 @@ struct mcc_plan_s {
   int32_t n[3];
   double lo[3], h[3], inv_h[3];
   int64_t n_v, n_g, n_outside;
-  int32_t *vid;
-  uint16_t *lam;
+  int4 *vid;      // [n_g] vertex ids of the owning simplex (x = -1 outside)
+  ushort4 *lam;   // [n_g] u16 weights of vertices 1..dim
   uint32_t *cell;
   uint16_t *frac;
+  void *vrec;  // per vertex {cell, local coordinates} as one 8- (2D) or 16-byte (3D) record
+  // a second stream for the component that does not wait on the other (the
+  // grid coder beside the residual stage), its fork / join events, and the
+  // mutex that keeps one call's fork and join together
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
+  std::mutex mu;
+  int tile2d = MCC_TILE_64x16;  // launch configuration (mcc_plan_set_tuning)
+  int vbps = 8;
+  int batch_fields = 0;
 };
 
 namespace {
@@ -304,29 +315,36 @@ __global__ void k_raster(const double *__restrict__ coords, const int32_t *__res
 template <int DIM>
 __global__ void k_grid_tables(const double *__restrict__ coords, const int32_t *__restrict__ cells,
                               const unsigned int *__restrict__ owner, GridDev g, int64_t n_g,
-                              int32_t *vid, uint16_t *lam, unsigned long long *n_out) {
+                              int4 *vid, ushort4 *lam, unsigned long long *n_out) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n_g) return;
   const unsigned int t = owner[j];
   if (t == 0xFFFFFFFFu) {
-    vid[j] = -1;
-    for (int k = 1; k <= DIM; k++) vid[k * n_g + j] = 0;
-    for (int k = 0; k < DIM; k++) lam[k * n_g + j] = 0;
+    vid[j] = make_int4(-1, 0, 0, 0);
+    if (DIM == 3) lam[j] = make_ushort4(0, 0, 0, 0);
     atomicAdd(n_out, 1ull);
     return;
   }
   const int64_t nx = g.n[0], ny = g.n[1];
   const int32_t idx[3] = {(int32_t)(j % nx), (int32_t)((j / nx) % ny), (int32_t)(j / (nx * ny))};
   double V[4][3], P[3] = {0.0, 0.0, 0.0}, l[4];
+  int32_t v4[4] = {0, 0, 0, 0};
   for (int k = 0; k <= DIM; k++) {
     const int32_t v = cells[(int64_t)t * (DIM + 1) + k];
-    vid[k * n_g + j] = v;
+    v4[k] = v;
     for (int d = 0; d < 3; d++) V[k][d] = d < DIM ? coords[(int64_t)v * DIM + d] : 0.0;
   }
   for (int d = 0; d < DIM; d++)
     P[d] = __dadd_rn(g.lo[d], __dmul_rn((double)base_index(g, d, idx[d]), g.h[d]));
   inside64<DIM>(V, P, l);
-  for (int k = 0; k < DIM; k++) lam[k * n_g + j] = to_u16_unit(l[k + 1]);
+  unsigned short w[3] = {0, 0, 0};
+  for (int k = 0; k < DIM; k++) w[k] = to_u16_unit(l[k + 1]);
+  if (DIM == 2) {  // both weights in the record's fourth word
+    vid[j] = make_int4(v4[0], v4[1], v4[2], (int)((unsigned int)w[0] | ((unsigned int)w[1] << 16)));
+  } else {
+    vid[j] = make_int4(v4[0], v4[1], v4[2], v4[3]);
+    lam[j] = make_ushort4(w[0], w[1], w[2], 0);
+  }
 }
 
 template <int DIM>
@@ -368,6 +386,19 @@ __global__ void k_node_tables(const double *__restrict__ coords, int64_t n_v, Gr
     frac[(int64_t)d * n_v + i] = to_u16_unit(f);
   }
   cell[i] = (uint32_t)(ci[0] + (int64_t)g.n[0] * (ci[1] + (int64_t)g.n[1] * ci[2]));
+}
+
+// One record per vertex of its cell and u16 local coordinates (the vertex
+// kernels read it with one vector load).
+template <int DIM>
+__global__ void k_vertex_records(const uint32_t *__restrict__ cell, const uint16_t *__restrict__ frac,
+                                 int64_t n_v, void *vrec) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_v;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned int fx = frac[i], fy = frac[n_v + i];
+    if (DIM == 2) ((uint2 *)vrec)[i] = make_uint2(cell[i], fx | (fy << 16));
+    else ((uint4 *)vrec)[i] = make_uint4(cell[i], fx | (fy << 16), frac[2 * n_v + i], 0u);
+  }
 }
 
 // Grid_Coarsen (Algorithm 2): every vertex marks, per axis, the planes of
@@ -442,7 +473,11 @@ static mcc_status plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, c
   mcc_status st = MCC_OK;
   auto fail = [&](mcc_status s) {
     cudaFree(d_flag); cudaFree(d_keys); cudaFree(d_owner); cudaFree(d_rel); cudaFree(d_keep);
-    if (P) { cudaFree(P->vid); cudaFree(P->lam); cudaFree(P->cell); cudaFree(P->frac); delete P; }
+    if (P) {
+      cudaFree(P->vid); cudaFree(P->lam); cudaFree(P->cell); cudaFree(P->frac);
+      cudaFree(P->vrec);
+      delete P;
+    }
     return s;
   };
   if (cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess ||
@@ -500,10 +535,11 @@ static mcc_status plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, c
   }
   P->n_v = n_v;
   P->n_g = n_g;
-  if (cudaMalloc(&P->vid, sizeof(int32_t) * (dim + 1) * n_g) != cudaSuccess ||
-      cudaMalloc(&P->lam, sizeof(uint16_t) * dim * n_g) != cudaSuccess ||
+  if (cudaMalloc(&P->vid, sizeof(int4) * n_g) != cudaSuccess ||
+      (dim == 3 && cudaMalloc(&P->lam, sizeof(ushort4) * n_g) != cudaSuccess) ||
       cudaMalloc(&P->cell, sizeof(uint32_t) * n_v) != cudaSuccess ||
       cudaMalloc(&P->frac, sizeof(uint16_t) * dim * n_v) != cudaSuccess ||
+      cudaMalloc(&P->vrec, (dim == 2 ? sizeof(uint2) : sizeof(uint4)) * n_v) != cudaSuccess ||
       cudaMalloc(&d_owner, sizeof(unsigned int) * n_g) != cudaSuccess ||
       cudaMalloc(&d_rel, sizeof(float4) * n_v) != cudaSuccess)
     return fail(MCC_ERR_OOM);
@@ -515,11 +551,13 @@ static mcc_status plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, c
     k_grid_tables<2><<<nblocks(n_g, 256), 256, 0, stream>>>(mesh->coords, mesh->cells, d_owner, g, n_g,
                                                           P->vid, P->lam, d_keys);
     k_node_tables<2><<<nblocks(n_v, 256), 256, 0, stream>>>(mesh->coords, n_v, g, P->cell, P->frac);
+    k_vertex_records<2><<<nblocks(n_v, 256), 256, 0, stream>>>(P->cell, P->frac, n_v, P->vrec);
   } else {
     k_raster<3><<<nblocks(n_c, 128), 128, 0, stream>>>(mesh->coords, mesh->cells, n_c, d_rel, g, d_owner);
     k_grid_tables<3><<<nblocks(n_g, 256), 256, 0, stream>>>(mesh->coords, mesh->cells, d_owner, g, n_g,
                                                           P->vid, P->lam, d_keys);
     k_node_tables<3><<<nblocks(n_v, 256), 256, 0, stream>>>(mesh->coords, n_v, g, P->cell, P->frac);
+    k_vertex_records<3><<<nblocks(n_v, 256), 256, 0, stream>>>(P->cell, P->frac, n_v, P->vrec);
   }
   unsigned long long n_out = 0;
   if (cudaGetLastError() != cudaSuccess ||
@@ -528,6 +566,17 @@ static mcc_status plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, c
     return fail(MCC_ERR_CUDA);
   P->n_outside = (int64_t)n_out;
   cudaFree(d_flag); cudaFree(d_keys); cudaFree(d_owner); cudaFree(d_rel); cudaFree(d_keep);
+  // the second stream (without it every launch stays on the caller's stream)
+  if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    if (P->side) cudaStreamDestroy(P->side);
+    if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+    if (P->ev_join) cudaEventDestroy(P->ev_join);
+    P->side = nullptr;
+    P->ev_fork = P->ev_join = nullptr;
+    cudaGetLastError();
+  }
   *out = P;
   (void)st;
   return MCC_OK;
@@ -599,7 +648,30 @@ extern "C" mcc_status mcc_grid_coarsen(mcc_plan P, int g_op, int32_t *keep_out, 
 extern "C" void mcc_plan_destroy(mcc_plan P) {
   if (!P) return;
   cudaFree(P->vid); cudaFree(P->lam); cudaFree(P->cell); cudaFree(P->frac);
+  cudaFree(P->vrec);
+  if (P->side) cudaStreamDestroy(P->side);
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
   delete P;
+}
+
+extern "C" mcc_status mcc_plan_set_tuning(mcc_plan P, const mcc_tuning *t) {
+  if (!P || !t) return MCC_ERR_INVALID_ARG;
+  if (t->tile2d < MCC_TILE_64x16 || t->tile2d > MCC_TILE_128x8) return MCC_ERR_INVALID_ARG;
+  if (t->vertex_blocks_per_sm < 2 || t->vertex_blocks_per_sm > 32) return MCC_ERR_INVALID_ARG;
+  if (t->batch_fields < 0 || t->batch_fields > kMaxBatch) return MCC_ERR_INVALID_ARG;
+  P->tile2d = t->tile2d;
+  P->vbps = t->vertex_blocks_per_sm;
+  P->batch_fields = t->batch_fields;
+  return MCC_OK;
+}
+
+extern "C" mcc_status mcc_plan_get_tuning(mcc_plan P, mcc_tuning *t) {
+  if (!P || !t) return MCC_ERR_INVALID_ARG;
+  t->tile2d = P->tile2d;
+  t->vertex_blocks_per_sm = P->vbps;
+  t->batch_fields = P->batch_fields;
+  return MCC_OK;
 }
 
 extern "C" mcc_status mcc_plan_get_info(mcc_plan P, mcc_plan_info *info) {
@@ -613,16 +685,37 @@ extern "C" mcc_status mcc_plan_get_info(mcc_plan P, mcc_plan_info *info) {
   return MCC_OK;
 }
 
+namespace {
+// The grid tables in the ABI's layout, vid [(dim+1)][n_g] and lam [dim][n_g].
+__global__ void k_tables_soa(const int4 *__restrict__ vid4, const ushort4 *__restrict__ lam4,
+                             int64_t n_g, int dim, int32_t *vid, uint16_t *lam) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_g;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int4 v = vid4[j];
+    const ushort4 l = dim == 3 ? lam4[j]
+                               : make_ushort4((unsigned short)(v.w & 0xFFFF),
+                                              (unsigned short)((unsigned int)v.w >> 16), 0, 0);
+    const int32_t vv[4] = {v.x, v.y, v.z, v.w};
+    const uint16_t ll[3] = {l.x, l.y, l.z};
+    if (vid)
+      for (int k = 0; k <= dim; k++) vid[k * n_g + j] = vv[k];
+    if (lam)
+      for (int k = 0; k < dim; k++) lam[k * n_g + j] = ll[k];
+  }
+}
+}  // namespace
+
 extern "C" mcc_status mcc_plan_copy_tables(mcc_plan P, int32_t *d_vid, uint16_t *d_lam,
                                            uint32_t *d_cell, uint16_t *d_frac, mcc_stream s) {
   if (!P) return MCC_ERR_INVALID_ARG;
   cudaStream_t stream = (cudaStream_t)s;
   const int dim = P->dim;
   cudaError_t e = cudaSuccess;
-  if (d_vid && e == cudaSuccess)
-    e = cudaMemcpyAsync(d_vid, P->vid, sizeof(int32_t) * (dim + 1) * P->n_g, cudaMemcpyDeviceToDevice, stream);
-  if (d_lam && e == cudaSuccess)
-    e = cudaMemcpyAsync(d_lam, P->lam, sizeof(uint16_t) * dim * P->n_g, cudaMemcpyDeviceToDevice, stream);
+  if (d_vid || d_lam) {
+    k_tables_soa<<<(unsigned int)std::min<int64_t>((P->n_g + 255) / 256, 152 * 16), 256, 0, stream>>>(
+        P->vid, P->lam, P->n_g, dim, d_vid, d_lam);
+    e = cudaGetLastError();
+  }
   if (d_cell && e == cudaSuccess)
     e = cudaMemcpyAsync(d_cell, P->cell, sizeof(uint32_t) * P->n_v, cudaMemcpyDeviceToDevice, stream);
   if (d_frac && e == cudaSuccess)
@@ -636,6 +729,13 @@ PlanView mcc_plan_view(mcc_plan P) {
   v.dim = P->dim;
   v.nx = P->n[0]; v.ny = P->n[1]; v.nz = P->n[2];
   v.n_v = P->n_v; v.n_g = P->n_g;
-  v.vid = P->vid; v.lam = P->lam; v.cell = P->cell; v.frac = P->frac;
+  v.vid4 = P->vid; v.lam4 = P->lam; v.cell = P->cell; v.frac = P->frac; v.vrec = P->vrec;
+  v.side = P->side;
+  v.ev_fork = P->ev_fork;
+  v.ev_join = P->ev_join;
+  v.mu = P->side ? &P->mu : nullptr;
+  v.tile2d = P->tile2d;
+  v.vbps = P->vbps;
+  v.batch_fields = P->batch_fields;
   return v;
 }

@@ -9,7 +9,7 @@ import pytest
 
 def _stub_prof(steps):
     # name: (total ms over `steps` replays, launches)
-    per = {"k_reduce": 0.015, "k_prequant": 0.02, "k_grid3d": 0.25, "k_node": 0.16,
+    per = {"k_reduce": 0.015, "k_prequant": 0.02, "k_grid_codes": 0.25, "k_grid3d": 0.03, "k_node": 0.16,
            "k_codebook": 0.033, "k_group_len": 0.03, "k_pack": 0.04, "k_dec_prep": 0.012,
            "k_dec_syms": 0.12, "k_scan_rows": 0.03, "k_predict": 0.002, "k_recon": 0.16}
     prof = {k: (v * steps, steps) for k, v in per.items()}
@@ -37,13 +37,13 @@ def test_headline_is_compact_json_with_rooflines():
     d = json.loads(s)
     assert d["value"] == pytest.approx(n_v * 8 / 1e-3 / 1e9, rel=1e-4)
     r = d["roofline"]
-    assert r["kernel"] == "k_grid3d" and r["traffic"] == 123 and r["bound"] == "hbm"
-    assert r["frac"] == pytest.approx(alg["k_grid3d"] / 0.25e-3 / 1e9 / 6780.0, rel=1e-4)
+    assert r["kernel"] == "k_grid_codes" and r["traffic"] == 123 and r["bound"] == "hbm"
+    assert r["frac"] == pytest.approx(alg["k_grid_codes"] / 0.25e-3 / 1e9 / 6780.0, rel=1e-4)
     # the whole step: every kernel's bytes times its launches, over the step time
     sb = sum(alg[k] * (2 if k == "k_scan_axis" else 1) for k in prof)
     assert r["step_alg_bytes"] == pytest.approx(sb, rel=1e-4)
     assert r["step_frac"] == pytest.approx(sb / 1e-3 / 1e9 / 6780.0, rel=1e-4)
-    assert d["gpu_launches"] == 14 * steps
+    assert d["gpu_launches"] == 15 * steps
     for key in ("metric", "unit", "n_gpus", "ms_per_step", "cpu_baseline", "e2e", "clocks"):
         assert key in d
     assert d["cpu_baseline"]["cores"] == 16
