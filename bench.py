@@ -225,9 +225,16 @@ WORKLOADS = {
 }
 
 
-def load_mesh(config):
-    """(coords, cells, grid) of a workload (the field is made separately)."""
+def load_mesh(config, layers=None):
+    """(coords, cells, grid) of a workload (the field is made separately);
+    for the 3D annulus, ``layers`` < 244 keeps only its bottom node layers
+    (the same spacings, and a grid of the full grid's spacing over them: a
+    small case of the same kernels for profiling)."""
     if config == "c3":
+        if layers and layers < 244:
+            coords, cells = synth.mesh3d_annulus_slab(layers)
+            nz = int(round(float(coords[:, 2].max() - coords[:, 2].min()) / (2.0 / 255.0))) + 1
+            return coords, cells, (256, 256, nz)
         coords, cells = synth.mesh3d_annulus()
         return coords, cells, (256, 256, 256)
     if config == "c2":
@@ -952,6 +959,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mcc", choices=["mcc", "reference"])
     ap.add_argument("--config", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--layers", type=int, default=None,
+                    help="3D annulus cut to its bottom node layers (a small profiling case)")
     ap.add_argument("--eb", type=float, default=1e-4)
     ap.add_argument("--zero-run", action="store_true", help="headline with the zero-run stage")
     ap.add_argument("--side", default="all",
@@ -981,7 +990,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    coords, cells, n = load_mesh(args.config)
+    coords, cells, n = load_mesh(args.config, args.layers)
     n_cells = int(cells.shape[0])
     cd = torch.from_numpy(coords).to(dev)
     ed = torch.from_numpy(cells).to(dev)
@@ -1086,7 +1095,9 @@ def main():
         peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
         nbytes = x.numel() * 8
         alg = algorithmic_bytes(len(n), x.numel(), int(np.prod(n)), 8, size, g_bytes, tuple(prof))
-        config = {"workload": WORKLOADS[args.config], "n_vertices": int(x.numel()),
+        wname = WORKLOADS[args.config] if not args.layers else \
+            f"3d-annulus-slab-{args.layers}-layers-grid{n[0]}x{n[1]}x{n[2]}-f64"
+        config = {"workload": wname, "n_vertices": int(x.numel()),
                   "n_cells": n_cells, "grid": list(n), "eb_rel": args.eb, "grid_fraction": 0.5,
                   "zero_run": bool(args.zero_run), "compression_ratio": nbytes / size,
                   "stream_bytes": int(size), "max_abs_err_over_tau": err_over_tau,

@@ -706,22 +706,26 @@ __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompA
   }
   __syncthreads();
   unsigned int nesc = 0;
-  for (int idx = threadIdx.x; idx < SZ * NT; idx += NT) {
-    const int lz = idx / NT, rem = idx - lz * NT;
-    const int ly = rem / TX, lx = rem - ly * TX;
+  // each thread walks one (x, y) column of the tile along z: the 3D Lorenzo
+  // difference is the plane's 2D difference e(z) minus e(z - 1), the latter
+  // kept from the previous step (the same sum as the 7-neighbour form,
+  // wrapping int32 arithmetic)
+  const int ly = threadIdx.x / TX, lx = threadIdx.x - ly * TX;
+  auto plane_diff = [&](int zz) {  // 2D Lorenzo difference in tile plane zz
+    int e = s[zz][ly + 1][lx + 1];
+    e = wsub(e, s[zz][ly + 1][lx]);
+    e = wsub(e, s[zz][ly][lx + 1]);
+    return wadd(e, s[zz][ly][lx]);
+  };
+  int e_prev = plane_diff(0);
+  for (int lz = 0; lz < SZ; lz++) {
     const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
     const bool valid = gx < nx && gy < ny && gz < nz;
     int sym = 0;
+    const int e_cur = plane_diff(lz + 1);
+    const int d = wsub(e_cur, e_prev);
+    e_prev = e_cur;
     if (valid) {
-      const int zc = lz + 1, zp = lz;
-      int d = s[zc][ly + 1][lx + 1];
-      d = wsub(d, s[zc][ly + 1][lx]);
-      d = wsub(d, s[zc][ly][lx + 1]);
-      d = wsub(d, s[zp][ly + 1][lx + 1]);
-      d = wadd(d, s[zc][ly][lx]);
-      d = wadd(d, s[zp][ly + 1][lx]);
-      d = wadd(d, s[zp][ly][lx + 1]);
-      d = wsub(d, s[zp][ly][lx]);
       const int64_t j = gx + (int64_t)nx * gy + sxy * gz;
       if (d >= -(R1 - 1) && d <= R1 - 2) {
         sym = d + R1;

@@ -232,12 +232,98 @@ __global__ void k_rel32(const double *coords, int64_t n_v, GridDev g, float4 *ou
   }
 }
 
+// Binning of the simplices for the rasterisation: the grid tile (kBinTile^D
+// base-grid cells, x-fastest tile order) of each simplex's centroid, counts
+// per tile, their exclusive prefix sums, and a scatter of the simplex ids
+// (any order inside a tile).
+constexpr int kBinTile = 8;
+
+template <int DIM>
+__device__ __forceinline__ uint32_t centroid_tile(const int32_t *__restrict__ cells, int64_t t,
+                                                  const float4 *__restrict__ rel, const GridDev &g,
+                                                  const uint32_t (&nt)[3]) {
+  float c[3] = {0.f, 0.f, 0.f};
+  for (int k = 0; k <= DIM; k++) {
+    const float4 r = rel[cells[t * (DIM + 1) + k]];
+    c[0] += r.x; c[1] += r.y; c[2] += r.z;
+  }
+  uint32_t tile = 0, stride = 1;
+  for (int d = 0; d < DIM; d++) {
+    float u = c[d] / (float)(DIM + 1) / g.hf[d] / (float)kBinTile;
+    if (!(u >= 0.f)) u = 0.f;  // also NaN
+    uint32_t ti = u >= (float)(nt[d] - 1) ? nt[d] - 1 : (uint32_t)u;
+    tile += ti * stride;
+    stride *= nt[d];
+  }
+  return tile;
+}
+
+template <int DIM>
+__global__ void k_bin_count(const int32_t *__restrict__ cells, int64_t n_c,
+                            const float4 *__restrict__ rel, GridDev g, uint32_t ntx, uint32_t nty,
+                            uint32_t ntz, uint32_t *tile_of, unsigned int *count) {
+  const uint32_t nt[3] = {ntx, nty, ntz};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_c;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t tile = centroid_tile<DIM>(cells, t, rel, g, nt);
+    tile_of[t] = tile;
+    atomicAdd(count + tile, 1u);
+  }
+}
+
+// Exclusive prefix sums of n counts in place, one block of 1024 threads
+// (plan time; a few million tiles at most).
+__global__ void __launch_bounds__(1024) k_bin_scan(unsigned int *count, int64_t n) {
+  __shared__ unsigned int wsum[32];
+  __shared__ unsigned int carry;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    const unsigned int v = i < n ? count[i] : 0u;
+    unsigned int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const unsigned int sv = wsum[lane];
+      unsigned int si = sv;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int t = __shfl_up_sync(0xffffffffu, si, o);
+        if (lane >= o) si += t;
+      }
+      wsum[lane] = si - sv;  // exclusive over the warps
+    }
+    __syncthreads();
+    const unsigned int c0 = carry;
+    if (i < n) count[i] = c0 + wsum[w] + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = c0 + wsum[w] + incl;
+    __syncthreads();
+  }
+}
+
+__global__ void k_bin_scatter(const uint32_t *__restrict__ tile_of, int64_t n_c, unsigned int *cursor,
+                              uint32_t *order) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_c;
+       t += (int64_t)gridDim.x * blockDim.x)
+    order[atomicAdd(cursor + tile_of[t], 1u)] = (uint32_t)t;
+}
+
+// Simplices in the order of `order` (binned by the grid tile of their
+// centroid, so a warp rasterises neighbouring simplices: coherent loops and
+// nearby atomics); the owner is the minimum id whatever the order.
 template <int DIM>
 __global__ void k_raster(const double *__restrict__ coords, const int32_t *__restrict__ cells,
                          int64_t n_c, const float4 *__restrict__ rel, GridDev g,
-                         unsigned int *owner) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n_c) return;
+                         const uint32_t *__restrict__ order, unsigned int *owner) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n_c) return;
+  const int64_t t = order[q];
   int32_t v[DIM + 1];
   float vf[4][3];
   for (int k = 0; k <= DIM; k++) {
@@ -470,9 +556,12 @@ static mcc_status plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, c
   unsigned int *d_owner = nullptr;
   float4 *d_rel = nullptr;
   int32_t *d_keep = nullptr;
+  unsigned int *d_bins = nullptr;
+  uint32_t *d_tile_of = nullptr, *d_order = nullptr;
   mcc_status st = MCC_OK;
   auto fail = [&](mcc_status s) {
     cudaFree(d_flag); cudaFree(d_keys); cudaFree(d_owner); cudaFree(d_rel); cudaFree(d_keep);
+    cudaFree(d_bins); cudaFree(d_tile_of); cudaFree(d_order);
     if (P) {
       cudaFree(P->vid); cudaFree(P->lam); cudaFree(P->cell); cudaFree(P->frac);
       cudaFree(P->vrec);
@@ -546,14 +635,34 @@ static mcc_status plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, c
   cudaMemsetAsync(d_owner, 0xFF, sizeof(unsigned int) * n_g, stream);
   cudaMemsetAsync(d_keys, 0, sizeof(unsigned long long), stream);
   k_rel32<<<nblocks(n_v, 256), 256, 0, stream>>>(mesh->coords, n_v, g, d_rel);
+  // simplices binned by the base-grid tile of their centroid
+  uint32_t ntb[3] = {1, 1, 1};
+  for (int d = 0; d < dim; d++) ntb[d] = (uint32_t)((g.top[d] + kBinTile) / kBinTile);
+  const int64_t nbins = (int64_t)ntb[0] * ntb[1] * ntb[2];
+  if (cudaMalloc(&d_bins, sizeof(unsigned int) * nbins) != cudaSuccess ||
+      cudaMalloc(&d_tile_of, sizeof(uint32_t) * n_c) != cudaSuccess ||
+      cudaMalloc(&d_order, sizeof(uint32_t) * n_c) != cudaSuccess)
+    return fail(MCC_ERR_OOM);
+  cudaMemsetAsync(d_bins, 0, sizeof(unsigned int) * nbins, stream);
+  {
+    const unsigned int nb = (unsigned int)std::min<int64_t>(nblocks(n_c, 256), 152 * 16);
+    if (dim == 2)
+      k_bin_count<2><<<nb, 256, 0, stream>>>(mesh->cells, n_c, d_rel, g, ntb[0], ntb[1], ntb[2],
+                                            d_tile_of, d_bins);
+    else
+      k_bin_count<3><<<nb, 256, 0, stream>>>(mesh->cells, n_c, d_rel, g, ntb[0], ntb[1], ntb[2],
+                                            d_tile_of, d_bins);
+    k_bin_scan<<<1, 1024, 0, stream>>>(d_bins, nbins);
+    k_bin_scatter<<<nb, 256, 0, stream>>>(d_tile_of, n_c, d_bins, d_order);
+  }
   if (dim == 2) {
-    k_raster<2><<<nblocks(n_c, 128), 128, 0, stream>>>(mesh->coords, mesh->cells, n_c, d_rel, g, d_owner);
+    k_raster<2><<<nblocks(n_c, 128), 128, 0, stream>>>(mesh->coords, mesh->cells, n_c, d_rel, g, d_order, d_owner);
     k_grid_tables<2><<<nblocks(n_g, 256), 256, 0, stream>>>(mesh->coords, mesh->cells, d_owner, g, n_g,
                                                           P->vid, P->lam, d_keys);
     k_node_tables<2><<<nblocks(n_v, 256), 256, 0, stream>>>(mesh->coords, n_v, g, P->cell, P->frac);
     k_vertex_records<2><<<nblocks(n_v, 256), 256, 0, stream>>>(P->cell, P->frac, n_v, P->vrec);
   } else {
-    k_raster<3><<<nblocks(n_c, 128), 128, 0, stream>>>(mesh->coords, mesh->cells, n_c, d_rel, g, d_owner);
+    k_raster<3><<<nblocks(n_c, 128), 128, 0, stream>>>(mesh->coords, mesh->cells, n_c, d_rel, g, d_order, d_owner);
     k_grid_tables<3><<<nblocks(n_g, 256), 256, 0, stream>>>(mesh->coords, mesh->cells, d_owner, g, n_g,
                                                           P->vid, P->lam, d_keys);
     k_node_tables<3><<<nblocks(n_v, 256), 256, 0, stream>>>(mesh->coords, n_v, g, P->cell, P->frac);
@@ -566,6 +675,7 @@ static mcc_status plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, c
     return fail(MCC_ERR_CUDA);
   P->n_outside = (int64_t)n_out;
   cudaFree(d_flag); cudaFree(d_keys); cudaFree(d_owner); cudaFree(d_rel); cudaFree(d_keep);
+  cudaFree(d_bins); cudaFree(d_tile_of); cudaFree(d_order);
   // the second stream (without it every launch stays on the caller's stream)
   if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
