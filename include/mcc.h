@@ -217,7 +217,8 @@ mcc_status mcc_plan_get_info(mcc_plan plan, mcc_plan_info *info);
  * chosen by timing, see the package's autotuner): the tile of the 2D grid
  * kernel (MCC_TILE_64x16 by default, MCC_TILE_32x32, MCC_TILE_128x8), the
  * blocks per SM and field of the vertex-streaming kernels (quantisation,
- * the 3D grid codes, residuals, reconstruction: 2 .. 32, 8 by default), and
+ * the 3D grid codes, residuals, reconstruction: 2 .. 32, or 0, the
+ * default: one full wave of as many blocks as fit on the SMs at once), and
  * the fields per launch chain of the batched calls (1 .. 64; 0, the
  * default: as many as keep their gathered codes, 4 (n_grid + n_vertices)
  * bytes each, within half the L2 cache, at least 1; the workspace may limit

@@ -28,7 +28,7 @@ from . import (TILE_128x8, TILE_32x32, TILE_64x16, compress, compress_batch, com
 
 CANDIDATES = list(itertools.product((128, 512, 2048), (64, 128, 256)))
 TILES = (TILE_64x16, TILE_32x32, TILE_128x8)
-VERTEX_BLOCKS = (4, 8, 16)
+VERTEX_BLOCKS = (0, 4, 8, 16)  # 0: one full wave of resident blocks
 
 
 def _time_round_trip(plan, x, prm, wsc, wsd, out, y, reps):

@@ -276,14 +276,15 @@ template <int DIM>
 __device__ __forceinline__ void vertex_record(const void *vrec, int64_t i, uint32_t &cell,
                                               float (&fr)[3]) {
   unsigned int f[3];
+  // streamed once per call: evict-first, so the gathered grid codes stay in L2
   if (DIM == 2) {
-    const uint2 r = __ldg((const uint2 *)vrec + i);
+    const uint2 r = __ldcs((const uint2 *)vrec + i);
     cell = r.x;
     f[0] = r.y & 0xFFFFu;
     f[1] = r.y >> 16;
     f[2] = 0;
   } else {
-    const uint4 r = __ldg((const uint4 *)vrec + i);
+    const uint4 r = __ldcs((const uint4 *)vrec + i);
     cell = r.x;
     f[0] = r.y & 0xFFFFu;
     f[1] = r.y >> 16;

@@ -442,14 +442,16 @@ __device__ __forceinline__ void grid_codes(const int64_t (&j)[U], const bool (&o
 #pragma unroll
   for (int u = 0; u < U; u++) {
     const int64_t jj = ok[u] ? j[u] : 0;
-    const int4 vv = __ldg(pv.vid4 + jj);
+    // the plan records are streamed once per call (evict-first: the gathered
+    // vertex codes stay in L2)
+    const int4 vv = __ldcs(pv.vid4 + jj);
     unsigned int lk[3];
     if (DIM == 2) {  // the weights share the record (lam1 | lam2 << 16)
       lk[0] = (unsigned int)vv.w & 0xFFFFu;
       lk[1] = (unsigned int)vv.w >> 16;
       lk[2] = 0;
     } else {
-      const ushort4 ll = __ldg(pv.lam4 + jj);
+      const ushort4 ll = __ldcs(pv.lam4 + jj);
       lk[0] = ll.x;
       lk[1] = ll.y;
       lk[2] = ll.z;
@@ -945,7 +947,7 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
       valid[u] = iv[u] < n;
       const int64_t i = valid[u] ? iv[u] : 0;
       vertex_record<DIM>(pv.vrec, i, cl[u], fr[u]);
-      Qv[u] = __ldg(Q + i);
+      Qv[u] = __ldcs(Q + i);
     }
 #pragma unroll
     for (int u = 0; u < U; u++) corner_codes<DIM>(q1, cl[u], nx, sxy, cor[u]);
@@ -2053,8 +2055,10 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
                         stream) != cudaSuccess)
     return MCC_ERR_CUDA;
   const unsigned int bpf = (unsigned int)((sms * 4 + nf - 1) / nf);  // reduce blocks per field
-  const int vbps = pv.vbps > 0 ? pv.vbps : 8;  // the plan's tuning (8 by default)
-  const unsigned int ppf = (unsigned int)((sms * vbps + nf - 1) / nf);  // prequant / node blocks per field
+  // blocks per field of the grid-stride kernels: the plan's tuning, or one
+  // full wave of resident blocks (0, the default)
+  const int vbps = pv.vbps;
+  const unsigned int ppf = (unsigned int)((sms * 8 + nf - 1) / nf);  // the 1D coder's
   {
     PROF_SCOPE("k_reduce", stream);
     if (p->dtype == MCC_F64) k_reduce<double><<<dim3(bpf, nf), 256, 0, stream>>>(A);
@@ -2062,8 +2066,12 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   }
   {
     PROF_SCOPE("k_prequant", stream);
-    if (p->dtype == MCC_F64) launch_pdl(k_prequant<double>, dim3(ppf, nf), dim3(256), 0, stream, A);
-    else launch_pdl(k_prequant<float>, dim3(ppf, nf), dim3(256), 0, stream, A);
+    if (p->dtype == MCC_F64)
+      launch_pdl(k_prequant<double>, dim3(wave_blocks(k_prequant<double>, 256, 0, vbps, sms, nf), nf),
+                 dim3(256), 0, stream, A);
+    else
+      launch_pdl(k_prequant<float>, dim3(wave_blocks(k_prequant<float>, 256, 0, vbps, sms, nf), nf),
+                 dim3(256), 0, stream, A);
   }
   const size_t hsm1 = 4 * (size_t)A.nsym1, hsm2 = 4 * (size_t)A.nsym2 * (A.any_auto ? 2 : 1);
   if (A.one_d) {
@@ -2084,7 +2092,8 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   } else {
     {
       PROF_SCOPE("k_grid_codes", stream);
-      launch_pdl(k_grid_codes3d, dim3(nf, ppf < 65535 ? ppf : 65535), dim3(256), 0, stream, A);
+      launch_pdl(k_grid_codes3d, dim3(nf, wave_blocks(k_grid_codes3d, 256, 0, vbps, sms, nf)),
+                 dim3(256), 0, stream, A);
     }
     PROF_SCOPE("k_grid3d", stream);
     const unsigned int txy = (unsigned int)(((pv.nx + 31) / 32) * ((pv.ny + 7) / 8));
@@ -2144,16 +2153,15 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   }
   if (!A.one_d) {
     PROF_SCOPE("k_node", stream);
-    const unsigned int chunks = ppf < 65535 ? ppf : 65535;
-    const dim3 grid(nf, chunks);
     // variants: plain, with the learned predictor, with open-loop fields
     // (which also serves learned fields of the same batch)
+#define MCC_NODE_ONE(K)                                                                 \
+  launch_pdl(K, dim3(nf, wave_blocks(K, 256, hsm2, vbps, sms, nf)), dim3(256), hsm2, stream, A)
 #define MCC_NODE(D, T)                                                                  \
   do {                                                                                  \
-    if (any_open) launch_pdl(k_node<D, T, true, true>, grid, dim3(256), hsm2, stream, A); \
-    else if (any_model)                                                                 \
-      launch_pdl(k_node<D, T, true, false>, grid, dim3(256), hsm2, stream, A);          \
-    else launch_pdl(k_node<D, T, false, false>, grid, dim3(256), hsm2, stream, A);      \
+    if (any_open) MCC_NODE_ONE((k_node<D, T, true, true>));                            \
+    else if (any_model) MCC_NODE_ONE((k_node<D, T, true, false>));                     \
+    else MCC_NODE_ONE((k_node<D, T, false, false>));                                   \
   } while (0)
     if (pv.dim == 2) {
       if (p->dtype == MCC_F64) MCC_NODE(2, double);
@@ -2163,6 +2171,7 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
       else MCC_NODE(3, float);
     }
 #undef MCC_NODE
+#undef MCC_NODE_ONE
   }
   // the residual component's (or, on one stream, both components') blocks:
   // logical block indices from R.bx0

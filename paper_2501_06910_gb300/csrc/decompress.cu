@@ -902,7 +902,7 @@ __global__ void __launch_bounds__(256, U == 2 ? (DIM == 3 ? 5 : 6) : 4) k_recon(
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int64_t p = pv2[u] < n ? pv2[u] : p0;
-      q2v[u] = __ldg(q2s + p);
+      q2v[u] = __ldcs(q2s + p);
       go[u] = pv2[u] < n && q2v[u] != INT_MIN;  // INT_MIN: raw value already in place
       vertex_record<DIM>(pv.vrec, p, cl[u], fr[u]);
     }
@@ -917,7 +917,7 @@ __global__ void __launch_bounds__(256, U == 2 ? (DIM == 3 ? 5 : 6) : 4) k_recon(
       // prediction unchanged (t + 0 = t, and -0 + 0 = +0 rounds to the same 0)
       const float pc = I.use_model ? __ldg(pcor + p) : 0.0f;
       const long long P = rescale<true>(cor[u][0], acc, I.rho12_q, I.rho12_f, pc);
-      xo[p] = (T)__dmul_rn(I.s2, (double)(I.K + P + (long long)q2v[u]));
+      __stcs(xo + p, (T)__dmul_rn(I.s2, (double)(I.K + P + (long long)q2v[u])));  // streamed out
     }
   }
 }
@@ -976,7 +976,7 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
   // group counts depend on the streams' chunk sizes: size the decoder for the
   // smallest chunk and let warps stride over the groups that exist
   const int64_t max_g1 = ngroups(pv.n_g, 1), max_g2 = ngroups(pv.n_v, 1);
-  const unsigned int cap = (unsigned int)((sms * 2 + nf - 1) / nf) + 1;
+  const unsigned int cap = (unsigned int)((sms * 2 + nf - 1) / nf);  // one wave (2 per SM)
   const unsigned int nb1 = nblk(max_g1, 8) < cap ? nblk(max_g1, 8) : cap;
   const unsigned int nb2 = nblk(max_g2, 8) < cap ? nblk(max_g2, 8) : cap;
   const size_t dsm = (size_t)8 * kDecRound * 32 * sizeof(unsigned short);  // [warps][round][32]
@@ -1083,16 +1083,18 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
     return MCC_ERR_CUDA;
   {
     PROF_SCOPE("k_recon", stream);
-    const int vbps = pv.vbps > 0 ? pv.vbps : 8;  // the plan's tuning (8 by default)
-    unsigned int chunks = (unsigned int)((sms * vbps + nf - 1) / nf);
-    if (chunks > 65535) chunks = 65535;
+    // one full wave of resident blocks by default (the plan's tuning may set
+    // the blocks per SM)
+#define MCC_RECON(K) \
+  launch_pdl(K, dim3(nf, wave_blocks(K, 256, 0, pv.vbps, sms, nf)), dim3(256), 0, stream, A)
     if (pv.dim == 2) {
-      if (dtype == MCC_F64) launch_pdl(k_recon<2, double, 4>, dim3(nf, chunks), dim3(256), 0, stream, A);
-      else launch_pdl(k_recon<2, float, 4>, dim3(nf, chunks), dim3(256), 0, stream, A);
+      if (dtype == MCC_F64) MCC_RECON((k_recon<2, double, 4>));
+      else MCC_RECON((k_recon<2, float, 4>));
     } else {
-      if (dtype == MCC_F64) launch_pdl(k_recon<3, double, 2>, dim3(nf, chunks), dim3(256), 0, stream, A);
-      else launch_pdl(k_recon<3, float, 2>, dim3(nf, chunks), dim3(256), 0, stream, A);
+      if (dtype == MCC_F64) MCC_RECON((k_recon<3, double, 2>));
+      else MCC_RECON((k_recon<3, float, 2>));
     }
+#undef MCC_RECON
   }
   if (cudaGetLastError() != cudaSuccess) return MCC_ERR_CUDA;
   return MCC_OK;

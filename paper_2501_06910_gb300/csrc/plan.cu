@@ -43,7 +43,7 @@ struct mcc_plan_s {
   cudaEvent_t ev_fork, ev_join;
   std::mutex mu;
   int tile2d = MCC_TILE_64x16;  // launch configuration (mcc_plan_set_tuning)
-  int vbps = 8;
+  int vbps = 0;  // 0: one full wave of resident blocks
   int batch_fields = 0;
 };
 
@@ -768,7 +768,8 @@ extern "C" void mcc_plan_destroy(mcc_plan P) {
 extern "C" mcc_status mcc_plan_set_tuning(mcc_plan P, const mcc_tuning *t) {
   if (!P || !t) return MCC_ERR_INVALID_ARG;
   if (t->tile2d < MCC_TILE_64x16 || t->tile2d > MCC_TILE_128x8) return MCC_ERR_INVALID_ARG;
-  if (t->vertex_blocks_per_sm < 2 || t->vertex_blocks_per_sm > 32) return MCC_ERR_INVALID_ARG;
+  if (t->vertex_blocks_per_sm != 0 && (t->vertex_blocks_per_sm < 2 || t->vertex_blocks_per_sm > 32))
+    return MCC_ERR_INVALID_ARG;
   if (t->batch_fields < 0 || t->batch_fields > kMaxBatch) return MCC_ERR_INVALID_ARG;
   P->tile2d = t->tile2d;
   P->vbps = t->vertex_blocks_per_sm;

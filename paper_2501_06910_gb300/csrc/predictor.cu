@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include "predictor.cuh"
+#include "workspace.cuh"
 
 using namespace mcc;
 
@@ -268,7 +269,9 @@ cudaError_t launch_predict(const PredArgs &A, cudaStream_t stream, bool pdl) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t warps = (A.pv.n_v + 31) / 32;
-  int64_t chunks = (sms * 4 + A.nf - 1) / A.nf;
+  // one full wave of resident blocks (every block has the same share)
+  int64_t chunks = A.pv.dim == 2 ? wave_blocks(k_predict<2>, 256, 0, 0, sms, A.nf)
+                                 : wave_blocks(k_predict<3>, 256, 0, 0, sms, A.nf);
   if (chunks > (warps + 7) / 8) chunks = (warps + 7) / 8;
   if (chunks < 1) chunks = 1;
   if (chunks > 65535) chunks = 65535;

@@ -1,6 +1,8 @@
 // workspace.cuh -- workspace layouts and the launchers shared by api.cu.
 #pragma once
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace mcc {
@@ -46,6 +48,42 @@ struct DecInfo {
 struct DecompressWs {
   size_t info, tab1, tab2, q1, q2, p, total;
 };
+
+// Blocks per field of a grid-stride kernel: the plan's tuning (blocks per SM)
+// or, by default (0), exactly one wave of the blocks that fit on the SMs at
+// once -- a grid-stride kernel gives every block the same work, so a partial
+// second wave doubles the tail. The residency of each (kernel, threads,
+// shared memory) comes from the occupancy calculator once and is kept.
+template <typename K>
+unsigned int wave_blocks(K kernel, int threads, size_t smem, int per_sm_tuned, int sms, int nf) {
+  int per_sm = per_sm_tuned;
+  if (per_sm <= 0) {
+    static std::mutex mu;
+    static const void *keys[64];
+    static int vals[64];
+    static int nkeys = 0;
+    const void *key = (const void *)kernel;
+    std::lock_guard<std::mutex> lk(mu);
+    per_sm = 0;
+    for (int i = 0; i < nkeys; i++)
+      if (keys[i] == key && vals[i] > 0 && (vals[i] >> 24) == (int)(smem >> 10) + 1) {
+        per_sm = vals[i] & 0xFFFFFF;
+        break;
+      }
+    if (!per_sm) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+          per_sm < 1)
+        per_sm = 1;
+      if (nkeys < 64 && smem < (200u << 10)) {
+        keys[nkeys] = key;
+        vals[nkeys] = (((int)(smem >> 10) + 1) << 24) | per_sm;
+        nkeys++;
+      }
+    }
+  }
+  const int64_t b = ((int64_t)sms * per_sm + nf - 1) / nf;
+  return (unsigned int)(b < 1 ? 1 : (b > 65535 ? 65535 : b));
+}
 
 }  // namespace mcc
 

@@ -35,18 +35,18 @@ def test_tuned_launch_keeps_the_result(dim):
     dev = torch.device("cuda", 0)
     plan = mcc.plan_create(torch.from_numpy(coords).to(dev), torch.from_numpy(cells).to(dev), n)
     xd = torch.from_numpy(x).to(dev)
-    assert mcc.get_tuning(plan) == (mcc.TILE_64x16, 8, 0)
+    assert mcc.get_tuning(plan) == (mcc.TILE_64x16, 0, 0)
     base = dict(dtype=mcc.F64, eb=1e-3, grid_fraction=0.5)
     ref = _round_trip(plan, xd, mcc.params_default(**base))
     params, table = autotune.tune(plan, xd, base, candidates=[(512, 128)], reps=2)
     rows = autotune.tune.launch_table
-    assert len(rows) == (9 if dim == 2 else 3)
+    assert len(rows) == (12 if dim == 2 else 4)
     chosen = mcc.get_tuning(plan)
     assert chosen[:2] in {(r[0], r[1]) for r in rows} and chosen[2] == 0
     assert min(rows, key=lambda r: r[2])[:2] == chosen[:2]
     got = _round_trip(plan, xd, mcc.params_default(**params))
     assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
-    for bad in ((3, 8, 0), (-1, 8, 0), (0, 1, 0), (0, 33, 0), (0, 8, -1), (0, 8, 65)):
+    for bad in ((3, 8, 0), (-1, 8, 0), (0, 1, 0), (0, -1, 0), (0, 33, 0), (0, 8, -1), (0, 8, 65)):
         with pytest.raises(mcc.MCCError) as e:
             mcc.set_tuning(plan, *bad)
         assert e.value.status == mcc.INVALID_ARG
