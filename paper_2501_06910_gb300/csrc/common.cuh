@@ -299,18 +299,31 @@ __device__ __forceinline__ void vertex_record(const void *vrec, int64_t i, uint3
 // the vertex's cell) as acc = g - c_000 in grid bins. corner_codes gathers the
 // cell's codes (order 000, 100, 010, 110, 001, 101, 011, 111), interp_acc
 // evaluates the interpolation on their integer differences.
+//
+// The vertices come in the caller's order, so the cells of neighbouring
+// threads are unrelated and every load is a gather of its own: the L1 serves
+// one request per load and lane. row_pair reads a cell edge's two codes
+// q1[r], q1[r + 1] with one aligned 16-byte load, plus a 4-byte load when
+// r + 1 starts the next 16 bytes (one row in four): a 3D cell's eight codes
+// take five requests on average instead of eight, a 2D cell's four take
+// 2.5. Requires q1 16-byte aligned and readable 8 bytes past its last code
+// (the workspaces pad it); the extra words are never used.
+__device__ __forceinline__ void row_pair(const int *__restrict__ q1, int64_t r, int &lo, int &hi) {
+  const int s = (int)(r & 3);
+  const int4 v = __ldg((const int4 *)(q1 + (r - s)));
+  lo = s == 0 ? v.x : s == 1 ? v.y : s == 2 ? v.z : v.w;
+  hi = s == 0 ? v.y : s == 1 ? v.z : v.w;
+  if (s == 3) hi = __ldg(q1 + r + 1);
+}
+
 template <int DIM>
 __device__ __forceinline__ void corner_codes(const int *__restrict__ q1, uint32_t c, int nx,
                                              int64_t sxy, int (&k)[8]) {
-  k[0] = __ldg(q1 + c);
-  k[1] = __ldg(q1 + c + 1);
-  k[2] = __ldg(q1 + c + nx);
-  k[3] = __ldg(q1 + c + nx + 1);
+  row_pair(q1, (int64_t)c, k[0], k[1]);
+  row_pair(q1, (int64_t)c + nx, k[2], k[3]);
   if (DIM == 3) {
-    k[4] = __ldg(q1 + c + sxy);
-    k[5] = __ldg(q1 + c + sxy + 1);
-    k[6] = __ldg(q1 + c + sxy + nx);
-    k[7] = __ldg(q1 + c + sxy + nx + 1);
+    row_pair(q1, (int64_t)c + sxy, k[4], k[5]);
+    row_pair(q1, (int64_t)c + sxy + nx, k[6], k[7]);
   }
 }
 

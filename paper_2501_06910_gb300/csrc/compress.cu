@@ -925,9 +925,9 @@ __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A
   const int64_t sxy = (int64_t)pv.nx * pv.ny;
   const float *__restrict__ pcor = c.p;
   const int64_t stride = (int64_t)gridDim.y * blockDim.x;
-  // U vertices per thread and iteration (4 in 2D, 2 in 3D), their gathers
+  // U vertices per thread and iteration (2 in 2D, 1 in 3D), their gathers
   // issued together; uniform trip count per warp
-  constexpr int U = DIM == 2 ? 4 : 2;
+  constexpr int U = DIM == 2 ? 2 : 1;
   const int64_t nloop = (n + U * stride - 1) / (U * stride) * (U * stride);
   if (OPEN && A.open[fi]) node_open<DIM, T>(A, c, f, shist);
   else if (OPEN && A.gop[fi] == MCC_G_NEAREST) node_nearest<DIM, T>(A, c, f, shist);
@@ -1958,7 +1958,7 @@ CompressWs compress_ws_layout(const PlanView &pv, const mcc_params *p) {
   w.len1 = take(ns1);
   w.len2 = take(ns2);
   w.Q = take(4 * (size_t)pv.n_v);
-  w.q1 = take(4 * (size_t)pv.n_g);
+  w.q1 = take(4 * (size_t)pv.n_g + 16);  // + 16: the corner gathers' aligned 16-byte loads
   w.sym1 = take(2 * (size_t)pv.n_g);
   w.sym2 = take(2 * (size_t)pv.n_v);
   w.val1 = take(4 * (size_t)pv.n_g);
@@ -2089,26 +2089,29 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
     else
       launch_pdl(k_grid2d<64, 16>, dim3(nf, (pv.nx + 63) / 64, (pv.ny + 15) / 16), dim3(256), hsm1,
                  stream, A);
-  } else {
+  }
+  // Two streams once q1 exists (Algorithm 3 codes x1' and x2 independently):
+  // the grid component's coder (in 3D from its Lorenzo differences on: they
+  // read q1 only) on the plan's second stream, beside the residual stage on
+  // the caller's; they join before the bit packing (whose layout needs both
+  // components). Single large fields only: with a batch, or a small field,
+  // the grid coder's kernels slow the residual stage they run beside by more
+  // than they hide (measured on the 2D graded and batched workloads).
+  const bool fork = !front_only && pv.side != nullptr && !A.one_d && nf == 1 &&
+                    pv.n_g + pv.n_v >= ((int64_t)1 << 23);
+  const unsigned int txy = (unsigned int)(((pv.nx + 31) / 32) * ((pv.ny + 7) / 8));
+  if (pv.dim == 3 && !A.one_d) {
     {
       PROF_SCOPE("k_grid_codes", stream);
       launch_pdl(k_grid_codes3d, dim3(nf, wave_blocks(k_grid_codes3d, 256, 0, vbps, sms, nf)),
                  dim3(256), 0, stream, A);
     }
-    PROF_SCOPE("k_grid3d", stream);
-    const unsigned int txy = (unsigned int)(((pv.nx + 31) / 32) * ((pv.ny + 7) / 8));
-    launch_pdl(k_grid3d<32, 8, 8>, dim3(nf, txy, (pv.nz + 7) / 8), dim3(256), hsm1, stream, A);
+    if (!fork) {
+      PROF_SCOPE("k_grid3d", stream);
+      launch_pdl(k_grid3d<32, 8, 8>, dim3(nf, txy, (pv.nz + 7) / 8), dim3(256), hsm1, stream, A);
+    }
   }
   if (front_only) return cudaGetLastError() == cudaSuccess ? MCC_OK : MCC_ERR_CUDA;
-  // Two streams from here on (Algorithm 3 codes x1' and x2 independently once
-  // q1 exists): the grid component's run tokens, code book and group lengths
-  // on the plan's second stream, beside the residual stage on the caller's;
-  // they join before the bit packing (whose layout needs both components).
-  // Single large fields only: with a batch, or a small field, the grid
-  // coder's kernels slow the residual stage they run beside by more than
-  // they hide (measured on the 2D graded and batched workloads).
-  const bool fork = pv.side != nullptr && !A.one_d && nf == 1 &&
-                    pv.n_g + pv.n_v >= ((int64_t)1 << 23);
   std::unique_lock<std::mutex> lock;
   const cudaStream_t side = (cudaStream_t)pv.side;
   if (fork) {
@@ -2118,6 +2121,10 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
       return MCC_ERR_CUDA;
     CompArgs G = A;
     G.bx0 = 0;
+    if (pv.dim == 3) {
+      PROF_SCOPE("k_grid3d_grid", side);
+      launch_pdl(k_grid3d<32, 8, 8>, dim3(nf, txy, (pv.nz + 7) / 8), dim3(256), hsm1, side, G);
+    }
     if (A.any_zr) {
       PROF_SCOPE("k_runs_grid", side);
       launch_pdl(k_runs, dim3((unsigned int)A.ng1, nf), dim3(256), 0, side, G);

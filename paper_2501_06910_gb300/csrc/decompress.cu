@@ -863,7 +863,7 @@ __device__ __forceinline__ void recon_nearest(const DecArgs &A, const DecInfo &I
 }
 
 template <int DIM, typename T, int U>
-__global__ void __launch_bounds__(256, U == 2 ? (DIM == 3 ? 5 : 6) : 4) k_recon(const __grid_constant__ DecArgs A) {
+__global__ void __launch_bounds__(256) k_recon(const __grid_constant__ DecArgs A) {
   pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.x);
@@ -936,7 +936,7 @@ DecompressWs decompress_ws_layout(const PlanView &pv) {
   w.info = take(sizeof(DecInfo));
   w.tab1 = take(sizeof(DecTab));
   w.tab2 = take(sizeof(DecTab));
-  w.q1 = take(4 * (size_t)pv.n_g);
+  w.q1 = take(4 * (size_t)pv.n_g + 16);  // + 16: the corner gathers' aligned 16-byte loads
   w.q2 = take(4 * (size_t)pv.n_v);
   w.p = take(4 * (size_t)pv.n_v);
   w.total = o;
@@ -1088,11 +1088,11 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
 #define MCC_RECON(K) \
   launch_pdl(K, dim3(nf, wave_blocks(K, 256, 0, pv.vbps, sms, nf)), dim3(256), 0, stream, A)
     if (pv.dim == 2) {
-      if (dtype == MCC_F64) MCC_RECON((k_recon<2, double, 4>));
-      else MCC_RECON((k_recon<2, float, 4>));
+      if (dtype == MCC_F64) MCC_RECON((k_recon<2, double, 2>));
+      else MCC_RECON((k_recon<2, float, 2>));
     } else {
-      if (dtype == MCC_F64) MCC_RECON((k_recon<3, double, 2>));
-      else MCC_RECON((k_recon<3, float, 2>));
+      if (dtype == MCC_F64) MCC_RECON((k_recon<3, double, 1>));
+      else MCC_RECON((k_recon<3, float, 1>));
     }
 #undef MCC_RECON
   }
