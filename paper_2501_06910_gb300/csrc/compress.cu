@@ -223,7 +223,6 @@ __device__ void field_params(Status *st, RParams rp) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
   pdl_wait();
   const Ctx c = ctx_of(A, blockIdx.y);
   const T *__restrict__ x = (const T *)c.x;
@@ -333,7 +332,6 @@ __global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ CompArgs
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_prequant(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
   pdl_wait();
   const Ctx c = ctx_of(A, blockIdx.y);
   const T *__restrict__ x = (const T *)c.x;
@@ -390,7 +388,6 @@ __global__ void __launch_bounds__(256) k_prequant(const __grid_constant__ CompAr
 __device__ __forceinline__ void hist_add(unsigned int *sh, int sym, bool valid);
 
 __global__ void __launch_bounds__(256) k_delta1d(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
   pdl_wait();
   const Ctx c = ctx_of(A, blockIdx.y);
   Status *st = c.st;
@@ -541,7 +538,6 @@ __device__ __forceinline__ void hist_add(unsigned int *sh, int sym, bool valid) 
 
 template <int TX, int TY>
 __global__ void __launch_bounds__(256) k_grid2d(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
   pdl_wait();
   // blocks are field-fastest so that the fields of a batch share plan tiles in L2
   const Ctx c = ctx_of(A, blockIdx.x);
@@ -626,7 +622,6 @@ __global__ void __launch_bounds__(256) k_grid2d(const __grid_constant__ CompArgs
 // computed twice. Four resident blocks per SM (64 registers, no spills)
 // keep more gathers in flight.
 __global__ void __launch_bounds__(256, 4) k_grid_codes3d(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
   pdl_wait();
   const Ctx c = ctx_of(A, blockIdx.x);
   const PlanView &pv = A.pv;
@@ -664,7 +659,6 @@ __global__ void __launch_bounds__(256, 4) k_grid_codes3d(const __grid_constant__
 // and its halo (the plane below, the row and column before) are read from q1.
 template <int TX, int TY, int SZ>
 __global__ void __launch_bounds__(TX *TY) k_grid3d(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
   pdl_wait();
   const Ctx c = ctx_of(A, blockIdx.x);
   const PlanView &pv = A.pv;
@@ -897,7 +891,6 @@ __device__ __forceinline__ void node_nearest(const CompArgs &A, const Ctx &c, co
 // takes the open loop (node_open; such a field has no model).
 template <int DIM, typename T, bool HAS_P, bool OPEN>
 __global__ void __launch_bounds__(256) k_node(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
   pdl_wait();
   const int fi = blockIdx.x;
   const Ctx c = ctx_of(A, fi);
@@ -1026,7 +1019,6 @@ __device__ __forceinline__ unsigned long long node_w(int e, int m, const unsigne
 }
 
 __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompArgs AA) {
-  pdl_trigger();
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   const Ctx c = ctx_of(AA, blockIdx.y);
@@ -1275,7 +1267,6 @@ __global__ void __launch_bounds__(1024) k_codebook(const __grid_constant__ CompA
 // Writes the chosen code lengths into the stream.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_choose(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
   pdl_wait();
   const int fi = blockIdx.x;
   if (A.mode[fi] != MCC_PRED_AUTO) return;
@@ -1358,7 +1349,6 @@ __device__ __forceinline__ unsigned int run_bits(unsigned int r, unsigned int l1
 // take the learned side of an auto field.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_runs(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
   pdl_wait();
   const int fi = blockIdx.y;
   const int64_t ng = A.ng1 + A.ng2;
@@ -1461,7 +1451,6 @@ struct GroupArgs {
 __device__ void scan_field(const CompArgs &A, int fi);
 
 __global__ void __launch_bounds__(256) k_group_len(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
   pdl_wait();
   const Ctx c = ctx_of(A, blockIdx.y, true);
   const Status *st = c.st;
@@ -1764,7 +1753,6 @@ struct PackArgs {
 // the plain one's register count)
 template <bool ZR>
 __global__ void __launch_bounds__(256, ZR ? 5 : 6) k_pack(const __grid_constant__ CompArgs A) {
-  pdl_trigger();
   pdl_wait();
   const Ctx c = ctx_of(A, blockIdx.y, true);
   const Status *st = c.st;

@@ -171,7 +171,6 @@ __device__ bool parse_header(const PrepArgs &a, const unsigned char *h, DecInfo 
 }
 
 __global__ void __launch_bounds__(1024) k_dec_prep(const __grid_constant__ DecArgs A) {
-  pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.y);
   Status *st = c.st;
@@ -359,10 +358,12 @@ __device__ __forceinline__ bool group_setup(const unsigned char *in, uint64_t gt
 // from the group's prefixes and a ballot rank.
 // ---------------------------------------------------------------------------
 constexpr int kDecRound = 64;  // steps decoded per shared-memory round
+// block shape: kDecWarps warps (one group each at a time) sharing one copy
+// of the decode table, kDecBlocksPerSM resident blocks per SM
+constexpr int kDecWarps = 8, kDecBlocksPerSM = 2;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_dec_syms(const __grid_constant__ DecArgs A, int nb1) {
-  pdl_trigger();
+__global__ void __launch_bounds__(32 * kDecWarps, kDecBlocksPerSM) k_dec_syms(const __grid_constant__ DecArgs A, int nb1) {
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.y);
   const unsigned char *__restrict__ in = c.in;
@@ -599,7 +600,6 @@ __device__ __forceinline__ void load8(const int *r, int i0, int nx, bool vec, un
 }
 
 __global__ void __launch_bounds__(256) k_scan_rows(const __grid_constant__ DecArgs A) {
-  pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.y);
   int *q = c.q1;
@@ -650,7 +650,6 @@ __global__ void __launch_bounds__(256) k_scan_rows(const __grid_constant__ DecAr
 template <int W>
 __global__ void __launch_bounds__(32 * W) k_scan_axis(const __grid_constant__ DecArgs A, int64_t n_inner,
                                                       int64_t n_outer, int64_t plane, int L, int64_t S) {
-  pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.y);
   int *q = c.q1;
@@ -693,7 +692,6 @@ __global__ void __launch_bounds__(32 * W) k_scan_axis(const __grid_constant__ De
 constexpr int kScan1dChunk = 256 * 16;  // values per chunk (one block)
 
 __global__ void __launch_bounds__(256) k_scan1d_sums(const __grid_constant__ DecArgs A) {
-  pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.y);
   if (*(volatile const unsigned int *)&c.st->err) return;
@@ -726,7 +724,6 @@ __global__ void __launch_bounds__(256) k_scan1d_sums(const __grid_constant__ Dec
 
 // exclusive scan of the chunk sums, in place (one block per field)
 __global__ void __launch_bounds__(1024) k_scan1d_top(const __grid_constant__ DecArgs A) {
-  pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.y);
   if (*(volatile const unsigned int *)&c.st->err) return;
@@ -767,7 +764,6 @@ __global__ void __launch_bounds__(1024) k_scan1d_top(const __grid_constant__ Dec
 // each chunk scanned from its offset: Q, then x' = s (K + Q)
 template <typename T>
 __global__ void __launch_bounds__(256) k_recon1d(const __grid_constant__ DecArgs A) {
-  pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.y);
   if (*(volatile const unsigned int *)&c.st->err) return;
@@ -864,7 +860,6 @@ __device__ __forceinline__ void recon_nearest(const DecArgs &A, const DecInfo &I
 
 template <int DIM, typename T, int U>
 __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ DecArgs A) {
-  pdl_trigger();
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.x);
   const DecInfo *__restrict__ info = c.info;
@@ -976,10 +971,12 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
   // group counts depend on the streams' chunk sizes: size the decoder for the
   // smallest chunk and let warps stride over the groups that exist
   const int64_t max_g1 = ngroups(pv.n_g, 1), max_g2 = ngroups(pv.n_v, 1);
-  const unsigned int cap = (unsigned int)((sms * 2 + nf - 1) / nf);  // one wave (2 per SM)
-  const unsigned int nb1 = nblk(max_g1, 8) < cap ? nblk(max_g1, 8) : cap;
-  const unsigned int nb2 = nblk(max_g2, 8) < cap ? nblk(max_g2, 8) : cap;
-  const size_t dsm = (size_t)8 * kDecRound * 32 * sizeof(unsigned short);  // [warps][round][32]
+  const unsigned int cap =  // one wave of resident blocks
+      (unsigned int)((sms * kDecBlocksPerSM + nf - 1) / nf);
+  const unsigned int nb1 = nblk(max_g1, kDecWarps) < cap ? nblk(max_g1, kDecWarps) : cap;
+  const unsigned int nb2 = nblk(max_g2, kDecWarps) < cap ? nblk(max_g2, kDecWarps) : cap;
+  const size_t dsm =  // [warps][round][32]
+      (size_t)kDecWarps * kDecRound * 32 * sizeof(unsigned short);
   {
     static bool attr = false;
     if (!attr) {
@@ -1004,8 +1001,8 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
       return MCC_ERR_CUDA;
     {
       PROF_SCOPE("k_dec_syms_res", side);  // blocks of the residual component only (nb1 = 0)
-      if (dtype == MCC_F64) launch_pdl(k_dec_syms<double>, dim3(nb2, nf), dim3(256), dsm, side, A, 0);
-      else launch_pdl(k_dec_syms<float>, dim3(nb2, nf), dim3(256), dsm, side, A, 0);
+      if (dtype == MCC_F64) launch_pdl(k_dec_syms<double>, dim3(nb2, nf), dim3(32 * kDecWarps), dsm, side, A, 0);
+      else launch_pdl(k_dec_syms<float>, dim3(nb2, nf), dim3(32 * kDecWarps), dsm, side, A, 0);
     }
     if (cudaEventRecord((cudaEvent_t)pv.ev_join, side) != cudaSuccess) return MCC_ERR_CUDA;
   }
@@ -1013,9 +1010,9 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
     PROF_SCOPE("k_dec_syms", stream);
     const unsigned int nb = fork ? nb1 : nb1 + nb2;
     if (dtype == MCC_F64)
-      launch_pdl(k_dec_syms<double>, dim3(nb, nf), dim3(256), dsm, stream, A, (int)nb1);
+      launch_pdl(k_dec_syms<double>, dim3(nb, nf), dim3(32 * kDecWarps), dsm, stream, A, (int)nb1);
     else
-      launch_pdl(k_dec_syms<float>, dim3(nb, nf), dim3(256), dsm, stream, A, (int)nb1);
+      launch_pdl(k_dec_syms<float>, dim3(nb, nf), dim3(32 * kDecWarps), dsm, stream, A, (int)nb1);
   }
   if (pv.dim == 1) {  // the 1D coder
     const int64_t nchunk = (pv.n_g + kScan1dChunk - 1) / kScan1dChunk;

@@ -144,7 +144,6 @@ __device__ __forceinline__ void act_to_frag(const float (&h)[8][4], const float 
 
 template <int DIM>
 __global__ void __launch_bounds__(256) k_predict(const __grid_constant__ PredArgs A) {
-  pdl_trigger();
   pdl_wait();
   __shared__ SModel m;
   __shared__ __align__(16) uint16_t xs[8][32][kK + 8];
