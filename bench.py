@@ -673,7 +673,9 @@ def side_split(mcc, plan, cd, flush, stream, args):
 def side_learned(mcc, plan, cd, flush, stream, args):
     """The learned residual predictor on the 3D annulus: trained on the GPU on
     16 seeds of vortex + noise fields, evaluated on 2 unseen seeds at rel
-    1e-4 against the plain predictor (auto choice per field)."""
+    1e-4 against the plain predictor (auto choice per field); then one field
+    with the network on the tcgen05 path."""
+    import torch
     from synth import torchgen
     eb = 1e-4
     base = dict(dtype=mcc.F64, eb=eb, grid_fraction=0.5)
@@ -700,6 +702,21 @@ def side_learned(mcc, plan, cd, flush, stream, args):
         res[label] = {"ratio": 2 * n * 8 / sum(sizes), "ms_per_field": statistics.mean(mss),
                       "GBps": rate(n * 8, statistics.mean(mss)), "chosen": chosen}
     res["ratio_gain"] = res["learned"]["ratio"] / res["plain"]["ratio"]
+    # the same learned field with the network on tcgen05 (plan tuning): the
+    # stream must not change
+    prm = mcc.params_default(model=model, auto=True, **base)
+    f = Field(mcc, plan, torchgen.field_vortex(cd, seed=2000), prm)
+    size0, _ = f.check(eb, "learned line (mma.sync)")
+    ref = f.out[:size0].clone()
+    mcc.set_net_path(plan, mcc.NET_TCGEN05)
+    try:
+        size1, _ = f.check(eb, "learned line (tcgen05)")
+        same = size1 == size0 and bool(torch.equal(f.out[:size1], ref))
+        ms = time_replays(f.step, flush, max(5, args.steps // 4), args.warmup, stream)
+    finally:
+        mcc.set_net_path(plan, mcc.NET_MMA_SYNC)
+    res["learned_tcgen05"] = {"ms_per_field": ms, "GBps": rate(n * 8, ms), "same_stream": same}
+    del f
     return res
 
 

@@ -222,15 +222,23 @@ mcc_status mcc_plan_get_info(mcc_plan plan, mcc_plan_info *info);
  * the fields per launch chain of the batched calls (1 .. 64; 0, the
  * default: as many as keep their gathered codes, 4 (n_grid + n_vertices)
  * bytes each, within half the L2 cache, at least 1; the workspace may limit
- * it further). Streams and decoded values never depend on it. Set it between
- * calls (it is read when a call launches); MCC_ERR_INVALID_ARG outside the
- * ranges. */
+ * it further), and the tensor-core path of the learned predictor's network
+ * (MCC_NET_MMA_SYNC, the default: warp-level mma.sync, each warp's 32
+ * vertices kept in registers from layer to layer; MCC_NET_TCGEN05: one
+ * 128-vertex tile per 128-thread CTA, tcgen05.mma with BF16 operands in
+ * shared memory and FP32 accumulators in tensor memory, at most four CTAs
+ * per SM; measured slower, kept selectable). Streams and decoded values
+ * never depend on it (the network is integer-exact in any accumulation
+ * order). Set it between calls (it is read when a call launches);
+ * MCC_ERR_INVALID_ARG outside the ranges. */
 typedef struct {
   int tile2d;
   int vertex_blocks_per_sm;
   int batch_fields;
+  int net_path;
 } mcc_tuning;
 enum { MCC_TILE_64x16 = 0, MCC_TILE_32x32 = 1, MCC_TILE_128x8 = 2 };
+enum { MCC_NET_MMA_SYNC = 0, MCC_NET_TCGEN05 = 1 };
 mcc_status mcc_plan_set_tuning(mcc_plan plan, const mcc_tuning *tuning);
 mcc_status mcc_plan_get_tuning(mcc_plan plan, mcc_tuning *tuning);
 

@@ -80,10 +80,12 @@ class TrainCfg(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("tile2d", C.c_int), ("vertex_blocks_per_sm", C.c_int), ("batch_fields", C.c_int)]
+    _fields_ = [("tile2d", C.c_int), ("vertex_blocks_per_sm", C.c_int), ("batch_fields", C.c_int),
+                ("net_path", C.c_int)]
 
 
 TILE_64x16, TILE_32x32, TILE_128x8 = 0, 1, 2
+NET_MMA_SYNC, NET_TCGEN05 = 0, 1
 
 
 class _PlanInfo(C.Structure):
@@ -307,16 +309,36 @@ def plan_create(coords: torch.Tensor, cells: torch.Tensor, n, lo=None, hi=None,
     return Plan(h, info)
 
 
+def _tuning(plan: "Plan") -> Tuning:
+    t = Tuning()
+    _check(load().mcc_plan_get_tuning(plan.handle, C.byref(t)), "plan_get_tuning")
+    return t
+
+
 def set_tuning(plan: "Plan", tile2d: int, vertex_blocks_per_sm: int, batch_fields: int = 0):
-    """mcc_plan_set_tuning: the launch configuration of the plan's kernels."""
-    t = Tuning(int(tile2d), int(vertex_blocks_per_sm), int(batch_fields))
+    """mcc_plan_set_tuning: the launch configuration of the plan's kernels
+    (the network's tensor-core path stays as set by set_net_path)."""
+    t = _tuning(plan)
+    t.tile2d, t.vertex_blocks_per_sm, t.batch_fields = \
+        int(tile2d), int(vertex_blocks_per_sm), int(batch_fields)
     _check(load().mcc_plan_set_tuning(plan.handle, C.byref(t)), "plan_set_tuning")
 
 
 def get_tuning(plan: "Plan"):
-    t = Tuning()
-    _check(load().mcc_plan_get_tuning(plan.handle, C.byref(t)), "plan_get_tuning")
+    t = _tuning(plan)
     return int(t.tile2d), int(t.vertex_blocks_per_sm), int(t.batch_fields)
+
+
+def set_net_path(plan: "Plan", path: int):
+    """The learned predictor's tensor-core path on this plan (mcc_tuning
+    net_path): NET_MMA_SYNC (default) or NET_TCGEN05."""
+    t = _tuning(plan)
+    t.net_path = int(path)
+    _check(load().mcc_plan_set_tuning(plan.handle, C.byref(t)), "plan_set_tuning")
+
+
+def get_net_path(plan: "Plan") -> int:
+    return int(_tuning(plan).net_path)
 
 
 def grid_coarsen(plan: Plan, g_op="multilinear", stream=None):

@@ -125,6 +125,7 @@ struct PlanView {
   int tile2d;  // MCC_TILE_* of the 2D grid kernel
   int vbps;    // blocks per SM and field of the vertex-streaming kernels (0: 8)
   int batch_fields;  // fields per batched launch chain (0: from the L2 size)
+  int net_path;      // MCC_NET_*: the learned predictor's tensor-core path
 };
 
 // ---------------------------------------------------------------------------

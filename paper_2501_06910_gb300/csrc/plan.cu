@@ -45,6 +45,7 @@ struct mcc_plan_s {
   int tile2d = MCC_TILE_64x16;  // launch configuration (mcc_plan_set_tuning)
   int vbps = 0;  // 0: one full wave of resident blocks
   int batch_fields = 0;
+  int net_path = MCC_NET_MMA_SYNC;
 };
 
 namespace {
@@ -771,9 +772,11 @@ extern "C" mcc_status mcc_plan_set_tuning(mcc_plan P, const mcc_tuning *t) {
   if (t->vertex_blocks_per_sm != 0 && (t->vertex_blocks_per_sm < 2 || t->vertex_blocks_per_sm > 32))
     return MCC_ERR_INVALID_ARG;
   if (t->batch_fields < 0 || t->batch_fields > kMaxBatch) return MCC_ERR_INVALID_ARG;
+  if (t->net_path != MCC_NET_MMA_SYNC && t->net_path != MCC_NET_TCGEN05) return MCC_ERR_INVALID_ARG;
   P->tile2d = t->tile2d;
   P->vbps = t->vertex_blocks_per_sm;
   P->batch_fields = t->batch_fields;
+  P->net_path = t->net_path;
   return MCC_OK;
 }
 
@@ -782,6 +785,7 @@ extern "C" mcc_status mcc_plan_get_tuning(mcc_plan P, mcc_tuning *t) {
   t->tile2d = P->tile2d;
   t->vertex_blocks_per_sm = P->vbps;
   t->batch_fields = P->batch_fields;
+  t->net_path = P->net_path;
   return MCC_OK;
 }
 
@@ -848,5 +852,6 @@ PlanView mcc_plan_view(mcc_plan P) {
   v.tile2d = P->tile2d;
   v.vbps = P->vbps;
   v.batch_fields = P->batch_fields;
+  v.net_path = P->net_path;
   return v;
 }

@@ -217,3 +217,37 @@ def test_auto_in_a_mixed_batch():
         got = out[i * slot: i * slot + sizes[i]].cpu().numpy()
         want = oracle.compress(op, fields[i], eb=eb, eb_mode="abs", **okw[i])
         assert np.array_equal(got, want), i
+
+
+@pytest.mark.parametrize("name", ["jit2d", "ragged2d", "annulus_small", "annulus_mid"])
+def test_tcgen05_network_path_bit_exact(name):
+    """The tcgen05 tensor-core path of the network (plan tuning net_path):
+    learned and automatic streams and decoded values equal the oracle's,
+    as with the default mma.sync path; invalid models are still rejected."""
+    import gpu_helpers as G
+    import paper_2501_06910_gb300 as mcc
+    c, e, n, x, op, gp = _setup(name)
+    assert mcc.get_net_path(gp) == mcc.NET_MMA_SYNC
+    mcc.set_net_path(gp, mcc.NET_TCGEN05)
+    try:
+        assert mcc.get_net_path(gp) == mcc.NET_TCGEN05
+        for seed, kw in ((1, dict(eb=1e-3, grid_fraction=0.4)), (2, dict(eb=1e-4, auto=True))):
+            blob = pack(random_model(op.dim, seed))
+            want = oracle.compress(op, x, model=blob, **kw)
+            got = G.compress(gp, x, model=_dev(blob), **kw)
+            assert np.array_equal(got, want), seed
+            assert np.array_equal(G.decompress(gp, got, x.dtype), oracle.decompress(op, want))
+        for label, m in edge_models(op.dim)[:2]:
+            blob = pack(m)
+            want = oracle.compress(op, x, model=blob, eb=1e-4)
+            assert np.array_equal(G.compress(gp, x, model=_dev(blob), eb=1e-4), want), label
+        bad = pack(random_model(op.dim, 3))
+        bad[0] ^= 1
+        with pytest.raises(mcc.MCCError) as err:
+            G.compress(gp, x, model=_dev(bad), eb=1e-3)
+        assert err.value.status == mcc.INVALID_ARG
+    finally:
+        mcc.set_net_path(gp, mcc.NET_MMA_SYNC)
+    with pytest.raises(mcc.MCCError) as err:
+        mcc.set_net_path(gp, 2)
+    assert err.value.status == mcc.INVALID_ARG
