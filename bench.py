@@ -961,18 +961,18 @@ def side_c4(mcc, dev, flush, stream, args):
     return res
 
 
-def measure_e2e(mcc, F, x_host, flush, steps, warmup, world):
-    """End to end through the API with host buffers (pinned), two fields in
-    flight: steps alternate between two streams, each with its own device
-    buffers and workspaces, so one step's copies (on the copy engines)
-    overlap the other's kernels. Every step copies its field in, compresses
+def measure_e2e(mcc, F, x_host, flush, steps, warmup, world, nlanes=2):
+    """End to end through the API with host buffers (pinned), `nlanes` fields
+    in flight: steps rotate over that many streams, each with its own device
+    buffers and workspaces, so one step's copies (on the copy engines) and
+    host-side size read overlap the others' kernels. Every step copies its field in, compresses
     (the stream size is read back on that step's stream), copies the stream
     out and back in, decompresses and copies the values out. Returns (ms per
     step over the timed steps, h2d bytes, d2h bytes per step)."""
     import torch
     plan, prm = F.plan, F.prm
     lanes = []
-    for _ in range(2):
+    for _ in range(nlanes):
         lanes.append(dict(
             s=torch.cuda.Stream(), x=torch.empty_like(F.x), out=torch.empty_like(F.out),
             inb=torch.empty_like(F.out), y=torch.empty_like(F.x),
@@ -997,15 +997,15 @@ def measure_e2e(mcc, F, x_host, flush, steps, warmup, world):
         h2d = x_host.numel() * x_host.element_size() + n_out
         d2h = n_out + L["y_host"].numel() * L["y_host"].element_size()
 
-    for k in range(warmup):
-        one(lanes[k % 2])
+    for k in range(max(warmup, nlanes)):
+        one(lanes[k % nlanes])
     torch.cuda.synchronize()
     flush.fill_(1)  # the fields and streams are larger than L2 together; one flush up front
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     for k in range(steps):
-        one(lanes[k % 2])
+        one(lanes[k % nlanes])
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / steps
     barrier(world)
@@ -1032,6 +1032,8 @@ def main():
     ap.add_argument("--side-out", default=None, help="also write the side lines to this file")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-lanes", type=int, default=2,
+                    help="steps in flight in the end-to-end measurement (streams)")
     ap.add_argument("--no-kernel-times", action="store_true")
     ap.add_argument("--no-grid-init", action="store_true")
     ap.add_argument("--preroll", type=float, default=0.5, help="seconds of untimed steps")
@@ -1121,12 +1123,13 @@ def main():
     e2e = None
     if not args.no_e2e:
         x_host = x.cpu().pin_memory()
-        e_ms, h2d, d2h = measure_e2e(mcc, F, x_host, flush, args.steps, args.warmup, world)
+        e_ms, h2d, d2h = measure_e2e(mcc, F, x_host, flush, args.steps, args.warmup, world,
+                                     args.e2e_lanes)
         e_ms = max_over_ranks(e_ms, world, dev)
         e2e = {"value": job_value(world, x.numel() * 8, e_ms), "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e_ms,
                "how": "pinned host field in, compress, stream out and in, decompress, "
-                      "values out; C-ABI calls, two steps in flight"}
+                      f"values out; C-ABI calls, {args.e2e_lanes} steps in flight"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
