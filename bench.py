@@ -149,6 +149,7 @@ def _alg_both(dim, n_v, n_g, vsz, cbytes):
         "k_dec_syms": cbytes + 4 * (n_g + n_v),                # stream in; deltas, q2 out
         "k_scan_rows": 8 * n_g,                                # one read + one write per pass
         "k_scan_axis": 8 * n_g,
+        "k_scan_xy": 8 * n_g,                                  # 3D: rows and y in one pass
         "k_predict": 0,                                        # plain streams: returns at once
         "k_recon": (4 + 2 * dim + 4 + vsz) * n_v,              # cell, local coords, q2 in; x' out
     }

@@ -643,6 +643,90 @@ __global__ void __launch_bounds__(256) k_scan_rows(const __grid_constant__ DecAr
   }
 }
 
+// 3D, rows of at most 256 CH codes (nx a multiple of 4): the x and y passes
+// fused, one CTA per z-plane. Batches of 8 rows, one per warp: each warp
+// x-scans its row (as k_scan_rows), the rows go to shared memory, every
+// thread adds down its columns over the batch from the running column sums
+// of the rows above (the y prefix), and the warps store their rows. The rows
+// of the next two batches are in flight while a batch is scanned. One pass
+// over q1 instead of two (k_scan_rows, then k_scan_axis along y).
+template <int CH>
+__global__ void __launch_bounds__(256) k_scan_xy(const __grid_constant__ DecArgs A) {
+  pdl_wait();
+  const DCtx c = dctx_of(A, blockIdx.y);
+  if (*(volatile const unsigned int *)&c.st->err) return;
+  const int nx = A.pv.nx, ny = A.pv.ny;
+  int *plane = c.q1 + (int64_t)blockIdx.x * nx * ny;
+  extern __shared__ unsigned int sxy[];  // [8][nx] batch rows, then [nx] column sums
+  unsigned int *T = sxy, *colsum = sxy + 8 * nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) colsum[i] = 0u;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned int v[CH][8], nv[CH][8], nv2[CH][8];
+  auto load_row = [&](int r, unsigned int (&d)[CH][8]) {
+#pragma unroll
+    for (int k = 0; k < CH; k++) {
+      if (r < ny) load8(plane + (int64_t)r * nx, 256 * k + 8 * lane, nx, true, d[k]);
+      else
+#pragma unroll
+        for (int e = 0; e < 8; e++) d[k][e] = 0u;
+    }
+  };
+  load_row(w, v);
+  load_row(w + 8, nv);
+  for (int b = 0; b < ny; b += 8) {
+    const int r = b + w;
+    load_row(r + 16, nv2);  // two batches ahead
+    // x prefix of this warp's row, into the batch tile
+    unsigned int carry = 0;
+#pragma unroll
+    for (int k = 0; k < CH; k++) {
+#pragma unroll
+      for (int e = 1; e < 8; e++) v[k][e] += v[k][e - 1];
+      unsigned int incl = v[k][7];
+      for (int sft = 1; sft < 32; sft <<= 1) {
+        const unsigned int t = __shfl_up_sync(0xffffffffu, incl, sft);
+        if (lane >= sft) incl += t;
+      }
+      const unsigned int off = carry + incl - v[k][7];
+      const int i0 = 256 * k + 8 * lane;
+      if (i0 < nx) {
+        unsigned int *t = T + w * nx + i0;
+        if (i0 + 8 <= nx) {
+          *reinterpret_cast<uint4 *>(t) = make_uint4(v[k][0] + off, v[k][1] + off, v[k][2] + off, v[k][3] + off);
+          *reinterpret_cast<uint4 *>(t + 4) = make_uint4(v[k][4] + off, v[k][5] + off, v[k][6] + off, v[k][7] + off);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; e++)
+            if (i0 + e < nx) t[e] = v[k][e] + off;
+        }
+      }
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncthreads();
+    // y prefix down the batch's columns
+    const int nr = min(8, ny - b);
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      unsigned int run = colsum[x];
+      for (int q = 0; q < nr; q++) {
+        run += T[q * nx + x];
+        T[q * nx + x] = run;
+      }
+      colsum[x] = run;
+    }
+    __syncthreads();
+    if (r < ny) {
+      int *dst = plane + (int64_t)r * nx;
+      for (int i = 4 * lane; i < nx; i += 128)
+        *reinterpret_cast<uint4 *>(dst + i) = *reinterpret_cast<const uint4 *>(T + w * nx + i);
+    }
+    __syncthreads();  // the tile is rewritten by the next batch
+#pragma unroll
+    for (int k = 0; k < CH; k++)
+#pragma unroll
+      for (int e = 0; e < 8; e++) { v[k][e] = nv[k][e]; nv[k][e] = nv2[k][e]; }
+  }
+}
+
 // Inclusive scan along an axis of length L and stride S, for columns
 // base = outer * plane + inner (inner < n_inner contiguous). Block: 32
 // consecutive columns x W warps, each warp scanning one segment of the axis
@@ -1032,7 +1116,24 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
     }
     return cudaGetLastError() == cudaSuccess ? MCC_OK : MCC_ERR_CUDA;
   }
-  {
+  // 3D grids with rows of at most 1024 codes (a multiple of 4): x and y in
+  // one pass per z-plane, then z; otherwise rows, then y (and z)
+  const bool xy = pv.dim == 3 && (pv.nx & 3) == 0 && pv.nx <= 1024;
+  if (xy) {
+    PROF_SCOPE("k_scan_xy", stream);
+    const size_t sm = (size_t)9 * pv.nx * sizeof(unsigned int);
+    const dim3 g((unsigned int)pv.nz, nf);
+    if (pv.nx <= 256) launch_pdl(k_scan_xy<1>, g, dim3(256), sm, stream, A);
+    else if (pv.nx <= 512) launch_pdl(k_scan_xy<2>, g, dim3(256), sm, stream, A);
+    else {
+      static bool attr = false;  // 36 KB of shared memory
+      if (!attr) {
+        cudaFuncSetAttribute(k_scan_xy<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
+        attr = true;
+      }
+      launch_pdl(k_scan_xy<4>, g, dim3(256), sm, stream, A);
+    }
+  } else {
     PROF_SCOPE("k_scan_rows", stream);
     const int64_t nrows = (int64_t)pv.ny * pv.nz;
     launch_pdl(k_scan_rows, dim3(nblk(nrows, 8), nf), dim3(256), 0, stream, A);
@@ -1049,7 +1150,7 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
       launch_pdl(k_scan_axis<8>, dim3((unsigned int)blocks, nf), dim3(256), 0, stream, A, n_inner,
                  n_outer, plane, L, S);
   };
-  scan_axis((int64_t)pv.nx, (int64_t)pv.nz, (int64_t)pv.nx * pv.ny, pv.ny, (int64_t)pv.nx);
+  if (!xy) scan_axis((int64_t)pv.nx, (int64_t)pv.nz, (int64_t)pv.nx * pv.ny, pv.ny, (int64_t)pv.nx);
   if (pv.dim == 3) {
     const int64_t ninner = (int64_t)pv.nx * pv.ny;
     scan_axis(ninner, 1, 0, pv.nz, ninner);
