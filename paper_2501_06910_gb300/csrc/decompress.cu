@@ -644,21 +644,23 @@ __global__ void __launch_bounds__(256) k_scan_rows(const __grid_constant__ DecAr
 }
 
 // 3D, rows of at most 256 CH codes (nx a multiple of 4): the x and y passes
-// fused, one CTA per z-plane. Batches of 8 rows, one per warp: each warp
+// fused, one CTA per z-plane. Batches of RB rows, one per warp: each warp
 // x-scans its row (as k_scan_rows), the rows go to shared memory, every
 // thread adds down its columns over the batch from the running column sums
 // of the rows above (the y prefix), and the warps store their rows. The rows
 // of the next two batches are in flight while a batch is scanned. One pass
 // over q1 instead of two (k_scan_rows, then k_scan_axis along y).
-template <int CH>
-__global__ void __launch_bounds__(256) k_scan_xy(const __grid_constant__ DecArgs A) {
+constexpr int kScanRB = 16;  // rows per batch of the plane scan (rows of <= 256 codes)
+
+template <int CH, int RB>
+__global__ void __launch_bounds__(32 * RB) k_scan_xy(const __grid_constant__ DecArgs A) {
   pdl_wait();
   const DCtx c = dctx_of(A, blockIdx.y);
   if (*(volatile const unsigned int *)&c.st->err) return;
   const int nx = A.pv.nx, ny = A.pv.ny;
   int *plane = c.q1 + (int64_t)blockIdx.x * nx * ny;
-  extern __shared__ unsigned int sxy[];  // [8][nx] batch rows, then [nx] column sums
-  unsigned int *T = sxy, *colsum = sxy + 8 * nx;
+  extern __shared__ unsigned int sxy[];  // [RB][nx] batch rows, then [nx] column sums
+  unsigned int *T = sxy, *colsum = sxy + RB * nx;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) colsum[i] = 0u;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned int v[CH][8], nv[CH][8], nv2[CH][8];
@@ -672,10 +674,10 @@ __global__ void __launch_bounds__(256) k_scan_xy(const __grid_constant__ DecArgs
     }
   };
   load_row(w, v);
-  load_row(w + 8, nv);
-  for (int b = 0; b < ny; b += 8) {
+  load_row(w + RB, nv);
+  for (int b = 0; b < ny; b += RB) {
     const int r = b + w;
-    load_row(r + 16, nv2);  // two batches ahead
+    load_row(r + 2 * RB, nv2);  // two batches ahead
     // x prefix of this warp's row, into the batch tile
     unsigned int carry = 0;
 #pragma unroll
@@ -704,7 +706,7 @@ __global__ void __launch_bounds__(256) k_scan_xy(const __grid_constant__ DecArgs
     }
     __syncthreads();
     // y prefix down the batch's columns
-    const int nr = min(8, ny - b);
+    const int nr = min(RB, ny - b);
     for (int x = threadIdx.x; x < nx; x += blockDim.x) {
       unsigned int run = colsum[x];
       for (int q = 0; q < nr; q++) {
@@ -1121,17 +1123,21 @@ mcc_status launch_decompress_batch(const PlanView &pv, int nf, const unsigned ch
   const bool xy = pv.dim == 3 && (pv.nx & 3) == 0 && pv.nx <= 1024;
   if (xy) {
     PROF_SCOPE("k_scan_xy", stream);
-    const size_t sm = (size_t)9 * pv.nx * sizeof(unsigned int);
     const dim3 g((unsigned int)pv.nz, nf);
-    if (pv.nx <= 256) launch_pdl(k_scan_xy<1>, g, dim3(256), sm, stream, A);
-    else if (pv.nx <= 512) launch_pdl(k_scan_xy<2>, g, dim3(256), sm, stream, A);
-    else {
-      static bool attr = false;  // 36 KB of shared memory
-      if (!attr) {
-        cudaFuncSetAttribute(k_scan_xy<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
-        attr = true;
+    if (pv.nx <= 256) {
+      launch_pdl(k_scan_xy<1, kScanRB>, g, dim3(32 * kScanRB),
+                 (size_t)(kScanRB + 1) * pv.nx * sizeof(unsigned int), stream, A);
+    } else {
+      const size_t sm = (size_t)9 * pv.nx * sizeof(unsigned int);
+      if (pv.nx <= 512) launch_pdl(k_scan_xy<2, 8>, g, dim3(256), sm, stream, A);
+      else {
+        static bool attr = false;  // 36 KB of shared memory
+        if (!attr) {
+          cudaFuncSetAttribute(k_scan_xy<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
+          attr = true;
+        }
+        launch_pdl(k_scan_xy<4, 8>, g, dim3(256), sm, stream, A);
       }
-      launch_pdl(k_scan_xy<4>, g, dim3(256), sm, stream, A);
     }
   } else {
     PROF_SCOPE("k_scan_rows", stream);
