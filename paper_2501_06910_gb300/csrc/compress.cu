@@ -2149,9 +2149,16 @@ mcc_status launch_compress_batch(const PlanView &pv, int nf, const void *const *
   if (!A.one_d) {
     PROF_SCOPE("k_node", stream);
     // variants: plain, with the learned predictor, with open-loop fields
-    // (which also serves learned fields of the same batch)
+    // (which also serves learned fields of the same batch). With the fork,
+    // one wave less two SMs' worth of blocks: room for the second stream's
+    // kernels beside k_node (measured on the 3D field: step 0.870 -> 0.853 ms
+    // with 2 SMs' worth left, 0.856 with 4, 0.865 with 16, none: 0.870)
 #define MCC_NODE_ONE(K)                                                                 \
-  launch_pdl(K, dim3(nf, wave_blocks(K, 256, hsm2, vbps, sms, nf)), dim3(256), hsm2, stream, A)
+  do {                                                                                  \
+    unsigned int nb = wave_blocks(K, 256, hsm2, vbps, sms, nf);                         \
+    if (fork && vbps == 0 && nb > 4u * (unsigned int)sms) nb -= 2u * (nb / (unsigned int)sms); \
+    launch_pdl(K, dim3(nf, nb), dim3(256), hsm2, stream, A);                            \
+  } while (0)
 #define MCC_NODE(D, T)                                                                  \
   do {                                                                                  \
     if (any_open) MCC_NODE_ONE((k_node<D, T, true, true>));                            \
