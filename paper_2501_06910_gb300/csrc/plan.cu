@@ -234,39 +234,62 @@ __global__ void k_rel32(const double *coords, int64_t n_v, GridDev g, float4 *ou
 }
 
 // Binning of the simplices for the rasterisation: the grid tile (kBinTile^D
-// base-grid cells, x-fastest tile order) of each simplex's centroid, counts
-// per tile, their exclusive prefix sums, and a scatter of the simplex ids
-// (any order inside a tile).
+// base-grid cells) of each simplex's centroid, counts per tile, their
+// exclusive prefix sums, and a scatter of the simplex ids (any order inside
+// a tile). Tiles are numbered in Morton (Z) order of their coordinates, so
+// consecutive bins, and the rasterising CTAs that take them in turn, cover
+// compact blocks of the grid; x-fastest numbering when the Morton range of
+// the tile counts would exceed kMortonMaxBins counters.
 constexpr int kBinTile = 8;
+constexpr int64_t kMortonMaxBins = (int64_t)1 << 24;
+
+// bit interleaving: bits 0, 1, 2 .. of x to bits 0, 2, 4 .. (2D) or 0, 3, 6 .. (3D)
+__host__ __device__ inline uint32_t spread2(uint32_t x) {
+  x &= 0xFFFFu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+__host__ __device__ inline uint32_t spread3(uint32_t x) {
+  x &= 0x3FFu;
+  x = (x | (x << 16)) & 0x030000FFu;
+  x = (x | (x << 8)) & 0x0300F00Fu;
+  x = (x | (x << 4)) & 0x030C30C3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
 
 template <int DIM>
 __device__ __forceinline__ uint32_t centroid_tile(const int32_t *__restrict__ cells, int64_t t,
                                                   const float4 *__restrict__ rel, const GridDev &g,
-                                                  const uint32_t (&nt)[3]) {
+                                                  const uint32_t (&nt)[3], bool morton) {
   float c[3] = {0.f, 0.f, 0.f};
   for (int k = 0; k <= DIM; k++) {
     const float4 r = rel[cells[t * (DIM + 1) + k]];
     c[0] += r.x; c[1] += r.y; c[2] += r.z;
   }
-  uint32_t tile = 0, stride = 1;
+  uint32_t ti[3] = {0, 0, 0};
   for (int d = 0; d < DIM; d++) {
     float u = c[d] / (float)(DIM + 1) / g.hf[d] / (float)kBinTile;
     if (!(u >= 0.f)) u = 0.f;  // also NaN
-    uint32_t ti = u >= (float)(nt[d] - 1) ? nt[d] - 1 : (uint32_t)u;
-    tile += ti * stride;
-    stride *= nt[d];
+    ti[d] = u >= (float)(nt[d] - 1) ? nt[d] - 1 : (uint32_t)u;
   }
-  return tile;
+  if (morton)
+    return DIM == 2 ? spread2(ti[0]) | (spread2(ti[1]) << 1)
+                    : spread3(ti[0]) | (spread3(ti[1]) << 1) | (spread3(ti[2]) << 2);
+  return ti[0] + nt[0] * (ti[1] + nt[1] * ti[2]);
 }
 
 template <int DIM>
 __global__ void k_bin_count(const int32_t *__restrict__ cells, int64_t n_c,
                             const float4 *__restrict__ rel, GridDev g, uint32_t ntx, uint32_t nty,
-                            uint32_t ntz, uint32_t *tile_of, unsigned int *count) {
+                            uint32_t ntz, int morton, uint32_t *tile_of, unsigned int *count) {
   const uint32_t nt[3] = {ntx, nty, ntz};
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_c;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t tile = centroid_tile<DIM>(cells, t, rel, g, nt);
+    const uint32_t tile = centroid_tile<DIM>(cells, t, rel, g, nt, morton != 0);
     tile_of[t] = tile;
     atomicAdd(count + tile, 1u);
   }
@@ -639,7 +662,13 @@ static mcc_status plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, c
   // simplices binned by the base-grid tile of their centroid
   uint32_t ntb[3] = {1, 1, 1};
   for (int d = 0; d < dim; d++) ntb[d] = (uint32_t)((g.top[d] + kBinTile) / kBinTile);
-  const int64_t nbins = (int64_t)ntb[0] * ntb[1] * ntb[2];
+  // Morton numbering: the bins span the next power of two of the largest
+  // tile count in every dimension
+  uint32_t p2 = 1;
+  while (p2 < std::max(ntb[0], std::max(ntb[1], ntb[2]))) p2 <<= 1;
+  const int64_t mbins = dim == 2 ? (int64_t)p2 * p2 : (int64_t)p2 * p2 * p2;
+  const int morton = (dim == 2 ? p2 <= 65536u : p2 <= 1024u) && mbins <= kMortonMaxBins ? 1 : 0;
+  const int64_t nbins = morton ? mbins : (int64_t)ntb[0] * ntb[1] * ntb[2];
   if (cudaMalloc(&d_bins, sizeof(unsigned int) * nbins) != cudaSuccess ||
       cudaMalloc(&d_tile_of, sizeof(uint32_t) * n_c) != cudaSuccess ||
       cudaMalloc(&d_order, sizeof(uint32_t) * n_c) != cudaSuccess)
@@ -649,10 +678,10 @@ static mcc_status plan_create(const mcc_mesh *mesh, const mcc_grid_spec *grid, c
     const unsigned int nb = (unsigned int)std::min<int64_t>(nblocks(n_c, 256), 152 * 16);
     if (dim == 2)
       k_bin_count<2><<<nb, 256, 0, stream>>>(mesh->cells, n_c, d_rel, g, ntb[0], ntb[1], ntb[2],
-                                            d_tile_of, d_bins);
+                                            morton, d_tile_of, d_bins);
     else
       k_bin_count<3><<<nb, 256, 0, stream>>>(mesh->cells, n_c, d_rel, g, ntb[0], ntb[1], ntb[2],
-                                            d_tile_of, d_bins);
+                                            morton, d_tile_of, d_bins);
     k_bin_scan<<<1, 1024, 0, stream>>>(d_bins, nbins);
     k_bin_scatter<<<nb, 256, 0, stream>>>(d_tile_of, n_c, d_bins, d_order);
   }
