@@ -1,10 +1,14 @@
 // compress.cu -- Algorithm 3 of Gong et al. (multi-component compression),
-// closed loop, as a chain of kernels on one stream:
+// closed loop, as a chain of kernels (for a large single field the grid
+// component's Lorenzo stage, code book and group lengths run on the plan's
+// second stream beside k_node and the residual's code book, joined before
+// k_pack):
 //
 //   k_reduce     min / max / finiteness of x; the last block derives the
 //                bound split tau = tau1 + tau2 (Sec. III) and the bin widths
 //   k_prequant   vertex codes Q = round(x / s2) - K            (FP64, 2 ops)
-//   k_grid       x1 = f(x): barycentric interpolation of Q at every grid
+//   k_grid2d / k_grid_codes3d + k_grid3d
+//                x1 = f(x): barycentric interpolation of Q at every grid
 //                point (Sec. IV-D), grid codes q1, N-D Lorenzo difference,
 //                symbols + histogram (C(x1))
 //   k_predict    (learned predictor only) the network's correction p at

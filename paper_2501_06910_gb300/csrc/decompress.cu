@@ -5,9 +5,11 @@
 //                 canonical decode tables of both components (one CTA each)
 //   k_dec_syms    Huffman decode of both components (one warp per group of
 //                 32 lane chunks): grid Lorenzo differences, residual codes,
-//                 escapes and raw values
-//   k_scan_rows / k_scan_axis
-//                 inverse Lorenzo: inclusive prefix sums along x, y (, z)
+//                 escapes and raw values; for a single field the residual
+//                 component's launch runs on the plan's second stream
+//   k_scan_xy / k_scan_rows / k_scan_axis
+//                 inverse Lorenzo: inclusive prefix sums along x, y (, z);
+//                 in 3D x and y in one pass per z-plane (rows of <= 1024)
 //   k_predict     learned correction p at every vertex (streams with a
 //                 model; returns at once for the others)
 //   k_recon       reconstruction x' = s2 (K + P + q2), P = round(rho12 g(q1)
