@@ -1801,6 +1801,9 @@ __global__ void __launch_bounds__(256, ZR ? 5 : 6) k_pack(const __grid_constant_
   }
   unsigned int pos = incl - lb;
   unsigned int e_run = etab[g], r_run = c1 ? 0u : rtab[g];
+  // groups without escapes / raw values (most) skip their ballots
+  const bool any_esc = etab[g + 1] != e_run;
+  const bool any_raw = !c1 && rtab[g + 1] != r_run;
   {  // the earlier parts' totals, their loads issued together
     unsigned int pb[kParts - 1], pe[kParts - 1], pr[kParts - 1];
 #pragma unroll
@@ -1866,10 +1869,12 @@ __global__ void __launch_bounds__(256, ZR ? 5 : 6) k_pack(const __grid_constant_
         put(scl[sy]);
       }
     }
-    const unsigned em = __ballot_sync(0xffffffffu, sy == 0);
-    if (sy == 0) outv[e_run + __popc(em & lt)] = __ldg(val + p);
-    e_run += __popc(em);
-    if (!c1) {
+    if (any_esc) {
+      const unsigned em = __ballot_sync(0xffffffffu, sy == 0);
+      if (sy == 0) outv[e_run + __popc(em & lt)] = __ldg(val + p);
+      e_run += __popc(em);
+    }
+    if (any_raw) {
       const unsigned rm = __ballot_sync(0xffffffffu, sy == rawsym);
       if (sy == rawsym) {
         unsigned char *dst = o + L.raw + (uint64_t)a.vsz * (r_run + __popc(rm & lt));
